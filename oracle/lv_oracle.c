@@ -1,0 +1,1104 @@
+/*
+ * lv_oracle.c -- plain, slow CPU oracle for the LiteVoxel rasterizer hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header, table or constant with the
+ * CUDA library; both sides are written independently from the paper.
+ *
+ * What each part follows (LiteVoxel, arXiv 2511.02510):
+ *   ora_render / ora_render_backward : Sec. III, Eq. 1 (rays), Eq. 2-4 (front-to-back
+ *       alpha compositing), Eq. 5 (w_max), delta_v "local inter-ray spacing".
+ *       FP64, one ray per pixel, every voxel the ray crosses, ordered by the
+ *       depth key.  The backward pass is plain reverse-mode of Eq. 2-4 over
+ *       stored per-sample values.
+ *   ora_pairs   : the (tile, depth-key) pair list and the per-voxel depth
+ *       statistics, FP32 with a fixed operation order (the binning step of the
+ *       "differentiable tile rasterizer", Sec. II-A / Fig. 1).
+ *   ora_prune   : Sec. IV-C, Eq. 11-12 (per-bin empirical-CDF quantile) with
+ *       guard i (EMA + hysteresis) and guard iii (per-step cap); Eq. 14 depth
+ *       normalisation for the bins.  FP32, fixed operation order.
+ *   ora_subdivide : Sec. IV-D, Eq. 13 (footprint eligibility), Eq. 14-16
+ *       (depth-normalised far bias on the usefulness score), budgeted top-k
+ *       and optimizer-state re-initialisation.  FP32, fixed operation order.
+ *   ora_lf_loss : Sec. IV-B, Eq. 7-10 and Eq. 18 (inverse-Sobel weight, mean
+ *       normalisation, gamma ramp).  FP64.
+ *
+ * Readings of points the paper leaves open (all listed in the design notes):
+ *   - opacity: 8 corner densities per voxel, sigma = max(0, trilinear at the
+ *     segment midpoint), alpha = 1 - exp(-sigma * l), l = ray-box chord length
+ *     with t >= 0;
+ *   - order along the ray: camera-space z of the voxel centre (FP32 bits),
+ *     ties by voxel id;
+ *   - a pixel stops after the first sample whose T falls below t_stop;
+ *   - depth = sum_k w_k * t_mid_k;
+ *   - colour: real SH of degree <= 3 evaluated towards the voxel centre,
+ *     c = max(0, sum + 0.5);
+ *   - a voxel all of whose corners lie in front of z_near (camera z < z_near)
+ *     is culled in that view;
+ *   - w_max ties go to the smallest global pixel id;
+ *   - delta_v = max(z_v, z_near) / f_x, z_v the camera depth of the centre,
+ *     both as minima over views.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared.
+ * -ffp-contract=off is required: the FP32 parts must round every operation.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float w2c[12]; /* row-major 3x4 [R | t]: x_cam = R x_world + t */
+  float z_near;
+} ora_cam;
+
+/* ------------------------------------------------------------------ */
+/* small helpers                                                       */
+/* ------------------------------------------------------------------ */
+
+static int ora_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int ora_num_threads(void) { return ora_threads(); }
+
+static int ora_tid(void) {
+#ifdef _OPENMP
+  return omp_get_thread_num();
+#else
+  return 0;
+#endif
+}
+
+/* ceil(a * b / 1e6) for non-negative integers */
+static int64_t ppm_ceil(int64_t ppm, int64_t n) { return (ppm * n + 999999) / 1000000; }
+static int64_t ppm_floor(int64_t ppm, int64_t n) { return (ppm * n) / 1000000; }
+
+/* order-preserving map from float bits to unsigned (negative floats first) */
+static uint32_t f32_order_key(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+static uint32_t f32_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+
+/* ------------------------------------------------------------------ */
+/* real spherical harmonics up to degree 3 (orthonormal on the sphere) */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Y_l^m for the real basis, written from the associated Legendre functions:
+ *   l=0: 1/(2 sqrt(pi))
+ *   l=1: sqrt(3/(4pi)) * {y, z, x}
+ *   l=2: sqrt(15/(4pi)) {xy, yz, xz}, sqrt(5/(16pi)) (3z^2-1), sqrt(15/(16pi)) (x^2-y^2)
+ *   l=3: sqrt(35/(32pi)) y(3x^2-y^2), sqrt(105/(4pi)) xyz, sqrt(21/(32pi)) y(5z^2-1),
+ *        sqrt(7/(16pi)) z(5z^2-3), sqrt(21/(32pi)) x(5z^2-1), sqrt(105/(16pi)) z(x^2-y^2),
+ *        sqrt(35/(32pi)) x(x^2-3y^2)
+ */
+void ora_sh_basis(const double* dir, double* Y) {
+  const double pi = 3.14159265358979323846;
+  double x = dir[0], y = dir[1], z = dir[2];
+  Y[0] = 0.5 / sqrt(pi);
+  double c1 = sqrt(3.0 / (4.0 * pi));
+  Y[1] = c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = c1 * x;
+  double c2a = sqrt(15.0 / (4.0 * pi));
+  double c2b = sqrt(5.0 / (16.0 * pi));
+  double c2c = sqrt(15.0 / (16.0 * pi));
+  Y[4] = c2a * x * y;
+  Y[5] = c2a * y * z;
+  Y[6] = c2b * (3.0 * z * z - 1.0);
+  Y[7] = c2a * x * z;
+  Y[8] = c2c * (x * x - y * y);
+  double c3a = sqrt(35.0 / (32.0 * pi));
+  double c3b = sqrt(105.0 / (4.0 * pi));
+  double c3c = sqrt(21.0 / (32.0 * pi));
+  double c3d = sqrt(7.0 / (16.0 * pi));
+  double c3e = sqrt(105.0 / (16.0 * pi));
+  Y[9] = c3a * y * (3.0 * x * x - y * y);
+  Y[10] = c3b * x * y * z;
+  Y[11] = c3c * y * (5.0 * z * z - 1.0);
+  Y[12] = c3d * z * (5.0 * z * z - 3.0);
+  Y[13] = c3c * x * (5.0 * z * z - 1.0);
+  Y[14] = c3e * z * (x * x - y * y);
+  Y[15] = c3a * x * (x * x - 3.0 * y * y);
+}
+
+static int sh_count(int degree) { return (degree + 1) * (degree + 1); }
+
+/* colour of voxel v seen along unit direction dir; raw[] receives the pre-clamp values */
+static void sh_color(const float* sh, int degree, const double* dir, double* rgb, double* raw) {
+  double Y[16];
+  ora_sh_basis(dir, Y);
+  int nb = sh_count(degree);
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (int j = 0; j < nb; ++j) s += (double)sh[j * 3 + c] * Y[j];
+    raw[c] = s + 0.5;
+    rgb[c] = raw[c] > 0.0 ? raw[c] : 0.0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* camera                                                              */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  double R[9], t[3], o[3];
+  double fx, fy, cx, cy, z_near;
+  int W, H;
+} cam64;
+
+static void cam_derive(const ora_cam* c, cam64* d) {
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) d->R[r * 3 + k] = (double)c->w2c[r * 4 + k];
+    d->t[r] = (double)c->w2c[r * 4 + 3];
+  }
+  /* camera centre o = -R^T t */
+  for (int k = 0; k < 3; ++k)
+    d->o[k] = -(d->R[0 * 3 + k] * d->t[0] + d->R[1 * 3 + k] * d->t[1] + d->R[2 * 3 + k] * d->t[2]);
+  d->fx = c->fx; d->fy = c->fy; d->cx = c->cx; d->cy = c->cy; d->z_near = c->z_near;
+  d->W = c->width; d->H = c->height;
+}
+
+/* world-space unit direction of the ray through the centre of pixel (x, y) (Eq. 1) */
+static void cam_ray(const cam64* c, int x, int y, double* d) {
+  double dc[3] = {((double)x + 0.5 - c->cx) / c->fx, ((double)y + 0.5 - c->cy) / c->fy, 1.0};
+  double n = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    d[k] = c->R[0 * 3 + k] * dc[0] + c->R[1 * 3 + k] * dc[1] + c->R[2 * 3 + k] * dc[2];
+    n += d[k] * d[k];
+  }
+  n = sqrt(n);
+  for (int k = 0; k < 3; ++k) d[k] /= n;
+}
+
+static void cam_point64(const cam64* c, const double* p, double* q) {
+  for (int r = 0; r < 3; ++r)
+    q[r] = c->R[r * 3 + 0] * p[0] + c->R[r * 3 + 1] * p[1] + c->R[r * 3 + 2] * p[2] + c->t[r];
+}
+
+/* FP32 camera transform with every product and sum rounded, left to right */
+static void cam_point32(const ora_cam* c, float X, float Y, float Z, float* q) {
+  for (int r = 0; r < 3; ++r) {
+    float a = c->w2c[r * 4 + 0] * X;
+    float b = c->w2c[r * 4 + 1] * Y;
+    float e = c->w2c[r * 4 + 2] * Z;
+    float s = a + b;
+    s = s + e;
+    q[r] = s + c->w2c[r * 4 + 3];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* FP32 binning rule: cull test, tile rectangle, depth key             */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int culled;       /* all 8 corners in front of the near plane */
+  int tx0, tx1, ty0, ty1;
+  int64_t count;    /* tiles covered */
+  float zc;         /* camera z of the centre */
+} bin32;
+
+static void bin_voxel32(const float* g, const ora_cam* c, int ts, bin32* b) {
+  int tiles_x = (c->width + ts - 1) / ts, tiles_y = (c->height + ts - 1) / ts;
+  float cx = g[0], cy = g[1], cz = g[2], h = g[3];
+  float q[3];
+  cam_point32(c, cx, cy, cz, q);
+  b->zc = q[2];
+  int n_front = 0, n_behind = 0;
+  float umin = 0, umax = 0, vmin = 0, vmax = 0;
+  float us[8], vs[8], zs[8];
+  for (int i = 0; i < 8; ++i) {
+    float X = (i & 1) ? cx + h : cx - h;
+    float Y = (i & 2) ? cy + h : cy - h;
+    float Z = (i & 4) ? cz + h : cz - h;
+    float p[3];
+    cam_point32(c, X, Y, Z, p);
+    zs[i] = p[2];
+    if (p[2] < c->z_near) ++n_behind; else ++n_front;
+    if (p[2] >= c->z_near) {
+      float rx = p[0] / p[2];
+      float ry = p[1] / p[2];
+      float u = c->fx * rx;
+      float v = c->fy * ry;
+      us[i] = u + c->cx;
+      vs[i] = v + c->cy;
+    }
+  }
+  (void)zs;
+  b->culled = (n_front == 0);
+  if (b->culled) {
+    b->tx0 = b->tx1 = b->ty0 = b->ty1 = 0;
+    b->count = 0;
+    return;
+  }
+  if (n_behind > 0) {
+    b->tx0 = 0; b->tx1 = tiles_x; b->ty0 = 0; b->ty1 = tiles_y;
+  } else {
+    umin = umax = us[0]; vmin = vmax = vs[0];
+    for (int i = 1; i < 8; ++i) {
+      umin = fminf(umin, us[i]); umax = fmaxf(umax, us[i]);
+      vmin = fminf(vmin, vs[i]); vmax = fmaxf(vmax, vs[i]);
+    }
+    float fts = (float)ts;
+    float a0 = floorf((umin - 1.0f) / fts), a1 = ceilf((umax + 1.0f) / fts);
+    float b0 = floorf((vmin - 1.0f) / fts), b1 = ceilf((vmax + 1.0f) / fts);
+    b->tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)tiles_x);
+    b->tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)tiles_x);
+    b->ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)tiles_y);
+    b->ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)tiles_y);
+  }
+  int64_t wx = b->tx1 - b->tx0, wy = b->ty1 - b->ty0;
+  b->count = (wx > 0 && wy > 0) ? wx * wy : 0;
+}
+
+typedef struct { uint64_t key; uint32_t val; } kv;
+
+static int kv_cmp(const void* a, const void* b) {
+  const kv* x = (const kv*)a;
+  const kv* y = (const kv*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->val != y->val) return x->val < y->val ? -1 : 1;
+  return 0;
+}
+
+/*
+ * Sorted (tile, depth-key) pairs for all views, plus per-voxel statistics.
+ *   keys[p] = (global_tile << 32) | order_key(z_center); vals[p] = voxel id
+ *   global_tile = tile_off[view] + ty * tiles_x + tx
+ *   ranges[2*g .. 2*g+1] = [start, end) of global tile g in the sorted list
+ *   z_min / delta_min: minimum over views where the voxel covers >= 1 tile of
+ *     max(z_center, z_near) and max(z_center, z_near) / fx  (caller sets +inf)
+ *   seen: 1 if the voxel covers >= 1 tile in some view (caller zeroes)
+ * Returns 0, or -1 when more than `cap` pairs would be produced (n_pairs then
+ * holds the required count and nothing else is written).
+ */
+int ora_pairs(int64_t n, const float* geom, int n_views, const ora_cam* cams, int ts, int64_t cap,
+              uint64_t* keys, uint32_t* vals, int64_t* n_pairs, uint32_t* ranges,
+              float* z_min, float* delta_min, uint8_t* seen) {
+  int64_t total = 0;
+  int64_t tiles_total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    for (int64_t i = 0; i < n; ++i) {
+      bin32 b;
+      bin_voxel32(geom + 4 * i, &cams[v], ts, &b);
+      total += b.count;
+    }
+    tiles_total += (int64_t)((cams[v].width + ts - 1) / ts) * ((cams[v].height + ts - 1) / ts);
+  }
+  *n_pairs = total;
+  if (total > cap) return -1;
+  kv* list = (kv*)malloc(sizeof(kv) * (size_t)(total > 0 ? total : 1));
+  int64_t p = 0, tile_off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const ora_cam* c = &cams[v];
+    int tiles_x = (c->width + ts - 1) / ts, tiles_y = (c->height + ts - 1) / ts;
+    for (int64_t i = 0; i < n; ++i) {
+      bin32 b;
+      bin_voxel32(geom + 4 * i, c, ts, &b);
+      if (b.count == 0) continue;
+      float zs = fmaxf(b.zc, c->z_near);
+      float dl = zs / c->fx;
+      if (zs < z_min[i]) z_min[i] = zs;
+      if (dl < delta_min[i]) delta_min[i] = dl;
+      seen[i] = 1;
+      uint32_t dk = f32_order_key(b.zc);
+      for (int ty = b.ty0; ty < b.ty1; ++ty)
+        for (int tx = b.tx0; tx < b.tx1; ++tx) {
+          uint64_t g = (uint64_t)(tile_off + (int64_t)ty * tiles_x + tx);
+          list[p].key = (g << 32) | dk;
+          list[p].val = (uint32_t)i;
+          ++p;
+        }
+    }
+    tile_off += (int64_t)tiles_x * tiles_y;
+  }
+  qsort(list, (size_t)total, sizeof(kv), kv_cmp);
+  for (int64_t g = 0; g < 2 * tiles_total; ++g) ranges[g] = 0;
+  for (int64_t q = 0; q < total; ++q) {
+    keys[q] = list[q].key;
+    vals[q] = list[q].val;
+    uint64_t g = list[q].key >> 32;
+    if (q == 0 || (list[q - 1].key >> 32) != g) ranges[2 * g] = (uint32_t)q;
+    if (q == total - 1 || (list[q + 1].key >> 32) != g) ranges[2 * g + 1] = (uint32_t)(q + 1);
+  }
+  free(list);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 ray marching                                                   */
+/* ------------------------------------------------------------------ */
+
+/* ray-box chord: returns 1 and the entry/exit parameters when l = t_out - t_in > 0 (t >= 0) */
+static int slab64(const double* o, const double* d, const float* g, double* t_in, double* t_out) {
+  double lo_t = -INFINITY, hi_t = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    double lo = (double)g[a] - (double)g[3], hi = (double)g[a] + (double)g[3];
+    if (d[a] == 0.0) {
+      if (o[a] < lo || o[a] > hi) return 0;
+      continue;
+    }
+    double t1 = (lo - o[a]) / d[a], t2 = (hi - o[a]) / d[a];
+    double tn = t1 < t2 ? t1 : t2, tf = t1 < t2 ? t2 : t1;
+    if (tn > lo_t) lo_t = tn;
+    if (tf < hi_t) hi_t = tf;
+  }
+  if (lo_t < 0.0) lo_t = 0.0;
+  *t_in = lo_t;
+  *t_out = hi_t;
+  return hi_t - lo_t > 0.0;
+}
+
+/* trilinear weights of the 8 corners at local coordinates u in [0,1]^3 */
+static void trilinear_weights(const double* u, double* w) {
+  for (int i = 0; i < 8; ++i) {
+    double wx = (i & 1) ? u[0] : 1.0 - u[0];
+    double wy = (i & 2) ? u[1] : 1.0 - u[1];
+    double wz = (i & 4) ? u[2] : 1.0 - u[2];
+    w[i] = wx * wy * wz;
+  }
+}
+
+typedef struct {
+  uint32_t key;
+  uint32_t id;
+} cand;
+
+static int cand_cmp(const void* a, const void* b) {
+  const cand* x = (const cand*)a;
+  const cand* y = (const cand*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->id != y->id) return x->id < y->id ? -1 : 1;
+  return 0;
+}
+
+/* per-view candidate lists: voxels whose conservative FP64 footprint covers the pixel */
+typedef struct {
+  int64_t* start; /* W*H+1 */
+  cand* items;
+} pixlists;
+
+static void build_lists(int64_t n, const float* geom, const ora_cam* c, const cam64* cd, int brute,
+                        const int* crop, pixlists* L) {
+  int W = cd->W, H = cd->H;
+  int x0 = crop ? crop[0] : 0, y0 = crop ? crop[1] : 0;
+  int x1 = crop ? crop[2] : W, y1 = crop ? crop[3] : H;
+  int64_t npx = (int64_t)W * H;
+  int* rect = (int*)malloc(sizeof(int) * 4 * (size_t)(n > 0 ? n : 1));
+  uint32_t* dkey = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    const float* g = geom + 4 * i;
+    bin32 b;
+    bin_voxel32(g, c, 16, &b);
+    dkey[i] = f32_order_key(b.zc);
+    int* r = rect + 4 * i;
+    if (b.culled) { r[0] = r[1] = r[2] = r[3] = 0; continue; }
+    if (brute) { r[0] = x0; r[1] = y0; r[2] = x1; r[3] = y1; continue; }
+    /* FP64 projection of the corners with a 2-pixel margin; any corner near or
+       behind the camera plane -> whole image */
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    int full = 0;
+    for (int k = 0; k < 8; ++k) {
+      double p[3] = {(double)g[0] + ((k & 1) ? 1.0 : -1.0) * (double)g[3],
+                     (double)g[1] + ((k & 2) ? 1.0 : -1.0) * (double)g[3],
+                     (double)g[2] + ((k & 4) ? 1.0 : -1.0) * (double)g[3]};
+      double q[3];
+      cam_point64(cd, p, q);
+      if (q[2] < 0.5 * cd->z_near) { full = 1; break; }
+      double u = cd->fx * q[0] / q[2] + cd->cx, v = cd->fy * q[1] / q[2] + cd->cy;
+      if (u < umin) umin = u;
+      if (u > umax) umax = u;
+      if (v < vmin) vmin = v;
+      if (v > vmax) vmax = v;
+    }
+    if (full) { r[0] = x0; r[1] = y0; r[2] = x1; r[3] = y1; continue; }
+    double a0 = floor(umin - 2.0), a1 = ceil(umax + 2.0), b0 = floor(vmin - 2.0), b1 = ceil(vmax + 2.0);
+    r[0] = (int)fmax(a0, (double)x0); r[1] = (int)fmax(b0, (double)y0);
+    r[2] = (int)fmin(a1, (double)x1); r[3] = (int)fmin(b1, (double)y1);
+    if (r[2] < r[0]) r[2] = r[0];
+    if (r[3] < r[1]) r[3] = r[1];
+  }
+  L->start = (int64_t*)calloc((size_t)npx + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) {
+    int* r = rect + 4 * i;
+    for (int y = r[1]; y < r[3]; ++y)
+      for (int x = r[0]; x < r[2]; ++x) L->start[(int64_t)y * W + x + 1] += 1;
+  }
+  for (int64_t p = 0; p < npx; ++p) L->start[p + 1] += L->start[p];
+  int64_t tot = L->start[npx];
+  L->items = (cand*)malloc(sizeof(cand) * (size_t)(tot > 0 ? tot : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npx > 0 ? npx : 1));
+  memcpy(fill, L->start, sizeof(int64_t) * (size_t)npx);
+  for (int64_t i = 0; i < n; ++i) {
+    int* r = rect + 4 * i;
+    for (int y = r[1]; y < r[3]; ++y)
+      for (int x = r[0]; x < r[2]; ++x) {
+        int64_t p = (int64_t)y * W + x;
+        L->items[fill[p]].key = dkey[i];
+        L->items[fill[p]].id = (uint32_t)i;
+        fill[p]++;
+      }
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t p = 0; p < npx; ++p)
+    qsort(L->items + L->start[p], (size_t)(L->start[p + 1] - L->start[p]), sizeof(cand), cand_cmp);
+  free(fill);
+  free(rect);
+  free(dkey);
+}
+
+static void free_lists(pixlists* L) {
+  free(L->start);
+  free(L->items);
+}
+
+typedef struct {
+  uint32_t id;
+  double l, t_mid, sigma_raw, alpha, T_before;
+  double u[3];
+} sample;
+
+/* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null */
+static int64_t march(const double* o, const double* d, const cand* items, int64_t cnt, const float* geom,
+                     const float* dens, const double* colors, double t_stop, sample* s, double* rgb,
+                     double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid) {
+  double T = 1.0;
+  int64_t k = 0;
+  rgb[0] = rgb[1] = rgb[2] = 0.0;
+  *depth = 0.0;
+  *near_stop = 0;
+  for (int64_t j = 0; j < cnt; ++j) {
+    uint32_t id = items[j].id;
+    const float* g = geom + 4 * (int64_t)id;
+    double t_in, t_out;
+    if (!slab64(o, d, g, &t_in, &t_out)) continue;
+    double l = t_out - t_in;
+    double tm = 0.5 * (t_in + t_out);
+    double u[3];
+    for (int a = 0; a < 3; ++a) {
+      double pa = o[a] + tm * d[a];
+      double lo = (double)g[a] - (double)g[3];
+      double v = (pa - lo) / (2.0 * (double)g[3]);
+      u[a] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    }
+    double w8[8];
+    trilinear_weights(u, w8);
+    double sr = 0.0;
+    for (int i = 0; i < 8; ++i) sr += w8[i] * (double)dens[8 * (int64_t)id + i];
+    double sigma = sr > 0.0 ? sr : 0.0;
+    double alpha = -expm1(-sigma * l);
+    double w = T * alpha;
+    if (wmax) {
+      if (w > wmax[id] || (w == wmax[id] && (warg[id] < 0 || gid < warg[id]))) {
+        wmax[id] = w;
+        warg[id] = gid;
+      }
+    }
+    const double* c = colors + 3 * (int64_t)id;
+    rgb[0] += w * c[0];
+    rgb[1] += w * c[1];
+    rgb[2] += w * c[2];
+    *depth += w * tm;
+    if (s) {
+      s[k].id = id; s[k].l = l; s[k].t_mid = tm; s[k].sigma_raw = sr; s[k].alpha = alpha; s[k].T_before = T;
+      s[k].u[0] = u[0]; s[k].u[1] = u[1]; s[k].u[2] = u[2];
+    }
+    T = T * exp(-sigma * l);
+    ++k;
+    if (fabs(T - t_stop) <= 1e-4 * t_stop) *near_stop = 1;
+    if (T < t_stop) break;
+  }
+  *T_out = T;
+  return k;
+}
+
+static void view_colors(int64_t n, const float* geom, const float* sh, int degree, const cam64* cd,
+                        double* colors, double* raw, double* dirs) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double d[3] = {(double)geom[4 * i] - cd->o[0], (double)geom[4 * i + 1] - cd->o[1],
+                   (double)geom[4 * i + 2] - cd->o[2]};
+    double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (nn > 0) { d[0] /= nn; d[1] /= nn; d[2] /= nn; } else { d[0] = 0; d[1] = 0; d[2] = 1; }
+    double r[3];
+    sh_color(sh + 48 * i, degree, d, colors + 3 * i, raw ? raw + 3 * i : r);
+    if (dirs) { dirs[3 * i] = d[0]; dirs[3 * i + 1] = d[1]; dirs[3 * i + 2] = d[2]; }
+  }
+}
+
+/*
+ * Forward render of n_views views (Eq. 1-5), FP64.
+ *   rgb[3*P], depth[P], T[P], n_hit[P], near_stop[P] over all views' pixels
+ *   (P = sum W*H, view-major, row-major), only pixels inside `crop`
+ *   (x0,y0,x1,y1 per view, or NULL for all) are written;
+ *   w_max[n] / w_arg[n]: maximum of T_{k-1} alpha over every processed sample
+ *   and the smallest global pixel id attaining it (-1 if never hit); the
+ *   caller initialises w_max to 0 and w_arg to -1 and they accumulate.
+ *   brute != 0: every non-culled voxel is a candidate of every pixel.
+ */
+int ora_render(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
+               const ora_cam* cams, double t_stop, int brute, const int* crop, double* rgb, double* depth,
+               double* T, int32_t* n_hit, uint8_t* near_stop, double* w_max, int64_t* w_arg) {
+  int nt = ora_threads();
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double* twm = NULL;
+  int64_t* twa = NULL;
+  if (w_max) {
+    twm = (double*)malloc(sizeof(double) * (size_t)nt * (size_t)(n > 0 ? n : 1));
+    twa = (int64_t*)malloc(sizeof(int64_t) * (size_t)nt * (size_t)(n > 0 ? n : 1));
+    for (int64_t q = 0; q < (int64_t)nt * n; ++q) { twm[q] = 0.0; twa[q] = -1; }
+  }
+  int64_t pix_off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    cam64 cd;
+    cam_derive(&cams[v], &cd);
+    view_colors(n, geom, sh, sh_degree, &cd, colors, NULL, NULL);
+    const int* cr = crop ? crop + 4 * v : NULL;
+    pixlists L;
+    build_lists(n, geom, &cams[v], &cd, brute, cr, &L);
+    int x0 = cr ? cr[0] : 0, y0 = cr ? cr[1] : 0, x1 = cr ? cr[2] : cd.W, y1 = cr ? cr[3] : cd.H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = y0; y < y1; ++y) {
+      int tid = ora_tid();
+      for (int x = x0; x < x1; ++x) {
+        int64_t p = (int64_t)y * cd.W + x;
+        int64_t gp = pix_off + p;
+        double d[3];
+        cam_ray(&cd, x, y, d);
+        int ns;
+        double Tp;
+        int64_t k = march(cd.o, d, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, dens, colors,
+                          t_stop, NULL, rgb + 3 * gp, depth + gp, &Tp, &ns, twm ? twm + (int64_t)tid * n : NULL,
+                          twa ? twa + (int64_t)tid * n : NULL, gp);
+        T[gp] = Tp;
+        if (n_hit) n_hit[gp] = (int32_t)k;
+        if (near_stop) near_stop[gp] = (uint8_t)ns;
+      }
+    }
+    free_lists(&L);
+    pix_off += (int64_t)cd.W * cd.H;
+  }
+  if (w_max) {
+    for (int t = 0; t < nt; ++t)
+      for (int64_t i = 0; i < n; ++i) {
+        double w = twm[(int64_t)t * n + i];
+        int64_t a = twa[(int64_t)t * n + i];
+        if (a < 0) continue;
+        if (w_arg[i] < 0 || w > w_max[i] || (w == w_max[i] && a < w_arg[i])) {
+          w_max[i] = w;
+          w_arg[i] = a;
+        }
+      }
+    free(twm);
+    free(twa);
+  }
+  free(colors);
+  return 0;
+}
+
+static void atomic_add(double* p, double v) {
+#pragma omp atomic
+  *p += v;
+}
+
+/*
+ * Reverse-mode of ora_render for the loss gradients dL/drgb (3 per pixel),
+ * dL/ddepth and dL/dT (nullable).  Writes (accumulates into, caller zeroes)
+ * d_density[8n] and d_sh[48n].  The per-pixel samples of the forward pass are
+ * stored and walked back to front:
+ *   dL/dsigma_k = l_k * ( T_k * a_k - sum_{j>k} w_j a_j - T_final * g_T ),
+ *   a_k = g_C . c_k + g_D * t_mid_k,
+ * then through sigma = max(0, trilinear) to the corners and through
+ * c = max(0, SH + 0.5) to the SH coefficients.
+ */
+int ora_render_backward(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
+                        int n_views, const ora_cam* cams, double t_stop, const double* dL_drgb,
+                        const double* dL_ddepth, const double* dL_dT, double* d_density, double* d_sh) {
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double* raw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double* dcol = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  int64_t pix_off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    cam64 cd;
+    cam_derive(&cams[v], &cd);
+    view_colors(n, geom, sh, sh_degree, &cd, colors, raw, dirs);
+    for (int64_t i = 0; i < 3 * n; ++i) dcol[i] = 0.0;
+    pixlists L;
+    build_lists(n, geom, &cams[v], &cd, 0, NULL, &L);
+#pragma omp parallel
+    {
+      int64_t cap = 64;
+      sample* s = (sample*)malloc(sizeof(sample) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+      for (int y = 0; y < cd.H; ++y) {
+        for (int x = 0; x < cd.W; ++x) {
+          int64_t p = (int64_t)y * cd.W + x;
+          int64_t gp = pix_off + p;
+          int64_t cnt = L.start[p + 1] - L.start[p];
+          if (cnt > cap) {
+            cap = cnt;
+            s = (sample*)realloc(s, sizeof(sample) * (size_t)cap);
+          }
+          double d[3], rgbp[3], dp, Tf;
+          int ns;
+          cam_ray(&cd, x, y, d);
+          int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf,
+                            &ns, NULL, NULL, gp);
+          const double* gC = dL_drgb + 3 * gp;
+          double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
+          double gT = dL_dT ? dL_dT[gp] : 0.0;
+          double S = 0.0;
+          for (int64_t k = K - 1; k >= 0; --k) {
+            const sample* q = &s[k];
+            const double* c = colors + 3 * (int64_t)q->id;
+            double a = gC[0] * c[0] + gC[1] * c[1] + gC[2] * c[2] + gD * q->t_mid;
+            double w = q->T_before * q->alpha;
+            double Tk = q->T_before * (1.0 - q->alpha);
+            double ds = q->l * (Tk * a - S - Tf * gT);
+            S += w * a;
+            for (int ch = 0; ch < 3; ++ch) atomic_add(&dcol[3 * (int64_t)q->id + ch], w * gC[ch]);
+            if (q->sigma_raw > 0.0) {
+              double w8[8];
+              trilinear_weights(q->u, w8);
+              for (int i = 0; i < 8; ++i) atomic_add(&d_density[8 * (int64_t)q->id + i], ds * w8[i]);
+            }
+          }
+        }
+      }
+      free(s);
+    }
+    free_lists(&L);
+    int nb = sh_count(sh_degree);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      double Y[16];
+      ora_sh_basis(dirs + 3 * i, Y);
+      for (int ch = 0; ch < 3; ++ch) {
+        if (!(raw[3 * i + ch] > 0.0)) continue;
+        double g = dcol[3 * i + ch];
+        for (int j = 0; j < nb; ++j) d_sh[48 * i + 3 * j + ch] += Y[j] * g;
+      }
+    }
+    pix_off += (int64_t)cd.W * cd.H;
+  }
+  free(colors);
+  free(raw);
+  free(dirs);
+  free(dcol);
+  return 0;
+}
+
+/* one pixel's samples, for invariant checks (T after each sample, and w) */
+int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
+                    const ora_cam* cam, double t_stop, int x, int y, int64_t max_out, uint32_t* ids,
+                    double* w_out, double* T_after, double* l_out, int64_t* n_out) {
+  cam64 cd;
+  cam_derive(cam, &cd);
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  view_colors(n, geom, sh, sh_degree, &cd, colors, NULL, NULL);
+  int crop[4] = {x, y, x + 1, y + 1};
+  pixlists L;
+  build_lists(n, geom, cam, &cd, 0, crop, &L);
+  int64_t p = (int64_t)y * cd.W + x;
+  int64_t cnt = L.start[p + 1] - L.start[p];
+  sample* s = (sample*)malloc(sizeof(sample) * (size_t)(cnt > 0 ? cnt : 1));
+  double d[3], rgbp[3], dp, Tf;
+  int ns;
+  cam_ray(&cd, x, y, d);
+  int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf, &ns, NULL,
+                    NULL, 0);
+  int64_t m = K < max_out ? K : max_out;
+  for (int64_t k = 0; k < m; ++k) {
+    ids[k] = s[k].id;
+    w_out[k] = s[k].T_before * s[k].alpha;
+    T_after[k] = s[k].T_before * (1.0 - s[k].alpha);
+    l_out[k] = s[k].l;
+  }
+  *n_out = K;
+  free(s);
+  free_lists(&L);
+  free(colors);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* selection helpers                                                   */
+/* ------------------------------------------------------------------ */
+
+static int f32_cmp(const void* a, const void* b) {
+  float x = *(const float*)a, y = *(const float*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* k-th smallest (1-based) of m floats */
+static float kth_smallest(float* buf, int64_t m, int64_t k) {
+  qsort(buf, (size_t)m, sizeof(float), f32_cmp);
+  return buf[k - 1];
+}
+
+/* nearest-rank percentiles (ppm) of z over the flagged voxels; returns count */
+static int64_t percentiles(int64_t n, const float* z, const uint8_t* flag, int64_t lo_ppm, int64_t hi_ppm,
+                           float* p_lo, float* p_hi) {
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) m += flag[i] ? 1 : 0;
+  *p_lo = 0.0f;
+  *p_hi = 0.0f;
+  if (m == 0) return 0;
+  float* buf = (float*)malloc(sizeof(float) * (size_t)m);
+  int64_t q = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (flag[i]) buf[q++] = z[i];
+  qsort(buf, (size_t)m, sizeof(float), f32_cmp);
+  int64_t k_lo = ppm_ceil(lo_ppm, m), k_hi = ppm_ceil(hi_ppm, m);
+  if (k_lo < 1) k_lo = 1;
+  if (k_hi < 1) k_hi = 1;
+  if (k_lo > m) k_lo = m;
+  if (k_hi > m) k_hi = m;
+  *p_lo = buf[k_lo - 1];
+  *p_hi = buf[k_hi - 1];
+  free(buf);
+  return m;
+}
+
+/* Eq. 14 in FP32: clip((z - p5) / (p95 - p5), 0, 1); 0 when p95 <= p5 */
+static float depth_norm32(float z, float p_lo, float p_hi) {
+  float den = p_hi - p_lo;
+  if (!(den > 0.0f)) return 0.0f;
+  float num = z - p_lo;
+  float r = num / den;
+  return fminf(fmaxf(r, 0.0f), 1.0f);
+}
+
+/*
+ * Depth-quantile pruning (Eq. 11-12, guards i and iii), FP32 decisions.
+ *   Over the seen voxels: z~ from nearest-rank p_lo/p_hi of z (Eq. 14),
+ *   bin b = min(nb-1, floor(nb * z~)); tau_b = k-th smallest w_max in bin b,
+ *   k = max(1, ceil(q * |V_b|)) (Eq. 12 as nearest rank on the empirical CDF
+ *   of Eq. 11); inside score x = [w_max > tau_b]; m <- (1-alpha) m + alpha x;
+ *   s <- out if m < m_low, in if m > m_high, else unchanged (guard i);
+ *   candidates: seen and s == out; at most floor(cap * n) of them, those with
+ *   the smallest (w_max, id), are pruned (guard iii).
+ *   s: 1 = in, 0 = out.  Unseen voxels keep m and s and are never pruned.
+ *   one_minus_alpha is (1 - alpha) rounded to FP32 by the caller.
+ */
+int ora_prune(int64_t n, const float* w_max, const uint8_t* seen, const float* z, float* m, uint8_t* s,
+              int n_bins, int64_t q_ppm, float alpha, float one_minus_alpha, float m_low, float m_high,
+              int64_t cap_ppm, int64_t lo_ppm, int64_t hi_ppm, uint8_t* prune_mask, int64_t* n_pruned,
+              float* tau_out, float* pct_out) {
+  for (int64_t i = 0; i < n; ++i) prune_mask[i] = 0;
+  *n_pruned = 0;
+  float p_lo, p_hi;
+  int64_t ns = percentiles(n, z, seen, lo_ppm, hi_ppm, &p_lo, &p_hi);
+  if (pct_out) { pct_out[0] = p_lo; pct_out[1] = p_hi; }
+  if (ns == 0) return 0;
+  int* bin = (int*)malloc(sizeof(int) * (size_t)n);
+  int64_t* cnt = (int64_t*)calloc((size_t)n_bins, sizeof(int64_t));
+  float nbf = (float)n_bins;
+  for (int64_t i = 0; i < n; ++i) {
+    bin[i] = -1;
+    if (!seen[i]) continue;
+    float zt = depth_norm32(z[i], p_lo, p_hi);
+    float sc = nbf * zt;
+    int b = (int)floorf(sc);
+    if (b > n_bins - 1) b = n_bins - 1;
+    bin[i] = b;
+    cnt[b]++;
+  }
+  float* tau = (float*)malloc(sizeof(float) * (size_t)n_bins);
+  float* buf = (float*)malloc(sizeof(float) * (size_t)ns);
+  for (int b = 0; b < n_bins; ++b) {
+    tau[b] = 0.0f;
+    if (cnt[b] == 0) continue;
+    int64_t q = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (bin[i] == b) buf[q++] = w_max[i];
+    int64_t k = ppm_ceil(q_ppm, cnt[b]);
+    if (k < 1) k = 1;
+    tau[b] = kth_smallest(buf, q, k);
+  }
+  if (tau_out)
+    for (int b = 0; b < n_bins; ++b) tau_out[b] = tau[b];
+  int64_t n_cand = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (bin[i] < 0) continue;
+    float x = (w_max[i] > tau[bin[i]]) ? 1.0f : 0.0f;
+    float a = one_minus_alpha * m[i];
+    float c = alpha * x;
+    float mm = a + c;
+    m[i] = mm;
+    if (mm < m_low) s[i] = 0;
+    else if (mm > m_high) s[i] = 1;
+    if (s[i] == 0) n_cand++;
+  }
+  int64_t cap = ppm_floor(cap_ppm, n);
+  if (n_cand <= cap) {
+    for (int64_t i = 0; i < n; ++i)
+      if (bin[i] >= 0 && s[i] == 0) prune_mask[i] = 1;
+    *n_pruned = n_cand;
+  } else if (cap > 0) {
+    kv* list = (kv*)malloc(sizeof(kv) * (size_t)n_cand);
+    int64_t q = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (bin[i] >= 0 && s[i] == 0) {
+        list[q].key = f32_bits(w_max[i]); /* w_max >= 0: bits order = value order */
+        list[q].val = (uint32_t)i;
+        ++q;
+      }
+    qsort(list, (size_t)n_cand, sizeof(kv), kv_cmp);
+    for (int64_t r = 0; r < cap; ++r) prune_mask[list[r].val] = 1;
+    *n_pruned = cap;
+    free(list);
+  }
+  free(bin);
+  free(cnt);
+  free(tau);
+  free(buf);
+  return 0;
+}
+
+/* lerp with the product/sum rounding fixed: a * (1 - t) + b * t */
+static float lerp32(float a, float b, float t) {
+  float omt = 1.0f - t;
+  float x = a * omt;
+  float y = b * t;
+  return x + y;
+}
+
+/* parent trilinear field at parent-local coordinates q in {0, 1/2, 1}^3: x, then y, then z */
+static float trilerp32(const float* d, const float* q) {
+  float cx[4];
+  for (int yz = 0; yz < 4; ++yz) cx[yz] = lerp32(d[yz * 2 + 0], d[yz * 2 + 1], q[0]);
+  float cy0 = lerp32(cx[0], cx[1], q[1]);
+  float cy1 = lerp32(cx[2], cx[3], q[1]);
+  return lerp32(cy0, cy1, q[2]);
+}
+
+typedef struct { float key; uint32_t id; } pk;
+
+static int pk_cmp_desc(const void* a, const void* b) {
+  const pk* x = (const pk*)a;
+  const pk* y = (const pk*)b;
+  if (x->key != y->key) return x->key > y->key ? -1 : 1;
+  return x->id < y->id ? -1 : (x->id > y->id ? 1 : 0);
+}
+
+/*
+ * Priority-driven subdivision (Eq. 13-16 and the budgeted selection), FP32.
+ *   alive = !prune_mask (prune_mask nullable);
+ *   z~ from nearest-rank p_lo / p_hi of z over alive & seen voxels (Eq. 14);
+ *   eligible = alive & seen & level < l_max & h > kappa * delta (Eq. 13);
+ *   p = u * (1 + beta * z~) (Eq. 15-16);
+ *   k = min(floor(top * n_alive), floor((budget - n_alive) / 7) (0 if budget <= n_alive), #eligible);
+ *   the k eligible voxels with the largest (p, then smallest id) are split.
+ * Output (capacity >= n_alive + 7k): survivors (alive, not split) in id
+ * order, then 8 children per split parent in parent-id order, child i at
+ * centre + (h/2) * (+-1 per bit: bit0 x, bit1 y, bit2 z), half-size h/2,
+ * level + 1, corners = parent trilinear field at parent-local (bit_i + bit_j) / 2,
+ * SH copied.  Auxiliary per-voxel arrays (aux_in[a] -> aux_out[a], aux_width[a]
+ * elements of aux_bytes[a] bytes each) are copied for survivors and filled with
+ * the fill pattern aux_fill[a] (bit pattern of one element) for children.
+ */
+int ora_subdivide(int64_t n, const float* geom, const uint8_t* level, const float* dens, const float* sh,
+                  const float* delta, const float* z, const float* u, const uint8_t* seen,
+                  const uint8_t* prune_mask, float kappa, float beta, int64_t top_ppm, int64_t budget, int l_max,
+                  int64_t lo_ppm, int64_t hi_ppm, int64_t capacity, float* out_geom, uint8_t* out_level,
+                  float* out_dens, float* out_sh, uint8_t* selected, int64_t* n_new, int64_t* k_out,
+                  int n_aux, void* const* aux_in, void* const* aux_out, const int32_t* aux_width,
+                  const int32_t* aux_bytes, const uint32_t* aux_fill) {
+  uint8_t* flag = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int64_t n_alive = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int alive = prune_mask ? !prune_mask[i] : 1;
+    n_alive += alive;
+    flag[i] = (uint8_t)(alive && seen[i]);
+    selected[i] = 0;
+  }
+  float p_lo, p_hi;
+  percentiles(n, z, flag, lo_ppm, hi_ppm, &p_lo, &p_hi);
+  pk* list = (pk*)malloc(sizeof(pk) * (size_t)(n > 0 ? n : 1));
+  int64_t n_el = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!flag[i]) continue;
+    if (!((int)level[i] < l_max)) continue;
+    float thr = kappa * delta[i];
+    if (!(geom[4 * i + 3] > thr)) continue;
+    float zt = depth_norm32(z[i], p_lo, p_hi);
+    float bz = beta * zt;
+    float b = 1.0f + bz;
+    list[n_el].key = u[i] * b;
+    list[n_el].id = (uint32_t)i;
+    ++n_el;
+  }
+  int64_t k = ppm_floor(top_ppm, n_alive);
+  int64_t kb = budget > n_alive ? (budget - n_alive) / 7 : 0;
+  if (kb < k) k = kb;
+  if (n_el < k) k = n_el;
+  *k_out = k;
+  if (n_alive + 7 * k > capacity) {
+    free(flag);
+    free(list);
+    *n_new = n_alive + 7 * k;
+    return -1;
+  }
+  qsort(list, (size_t)n_el, sizeof(pk), pk_cmp_desc);
+  for (int64_t r = 0; r < k; ++r) selected[list[r].id] = 1;
+  int64_t o = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int alive = prune_mask ? !prune_mask[i] : 1;
+    if (!alive || selected[i]) continue;
+    memcpy(out_geom + 4 * o, geom + 4 * i, 16);
+    out_level[o] = level[i];
+    memcpy(out_dens + 8 * o, dens + 8 * i, 32);
+    memcpy(out_sh + 48 * o, sh + 48 * i, 192);
+    for (int a = 0; a < n_aux; ++a) {
+      size_t eb = (size_t)aux_bytes[a] * (size_t)aux_width[a];
+      memcpy((char*)aux_out[a] + eb * (size_t)o, (const char*)aux_in[a] + eb * (size_t)i, eb);
+    }
+    ++o;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (!selected[i]) continue;
+    const float* g = geom + 4 * i;
+    float hc = g[3] * 0.5f;
+    for (int c = 0; c < 8; ++c) {
+      float* og = out_geom + 4 * o;
+      og[0] = g[0] + ((c & 1) ? hc : -hc);
+      og[1] = g[1] + ((c & 2) ? hc : -hc);
+      og[2] = g[2] + ((c & 4) ? hc : -hc);
+      og[3] = hc;
+      out_level[o] = (uint8_t)(level[i] + 1);
+      for (int j = 0; j < 8; ++j) {
+        float q[3];
+        q[0] = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
+        q[1] = (float)(((c >> 1) & 1) + ((j >> 1) & 1)) * 0.5f;
+        q[2] = (float)(((c >> 2) & 1) + ((j >> 2) & 1)) * 0.5f;
+        out_dens[8 * o + j] = trilerp32(dens + 8 * i, q);
+      }
+      memcpy(out_sh + 48 * o, sh + 48 * i, 192);
+      for (int a = 0; a < n_aux; ++a) {
+        size_t w = (size_t)aux_width[a];
+        for (size_t e = 0; e < w; ++e) {
+          char* dst = (char*)aux_out[a] + (size_t)aux_bytes[a] * (w * (size_t)o + e);
+          if (aux_bytes[a] == 4) memcpy(dst, &aux_fill[a], 4);
+          else if (aux_bytes[a] == 2) { uint16_t f = (uint16_t)aux_fill[a]; memcpy(dst, &f, 2); }
+          else { uint8_t f = (uint8_t)aux_fill[a]; memcpy(dst, &f, 1); }
+        }
+      }
+      ++o;
+    }
+  }
+  *n_new = o;
+  free(flag);
+  free(list);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* LF-weighted photometric loss (Eq. 7-10, 18), FP64                    */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 9 */
+double ora_lf_gamma(double t, double t0, double t1, double gamma_max) {
+  if (t < t0) return 0.0;
+  if (t < t1) return gamma_max * (t - t0) / (t1 - t0);
+  return gamma_max;
+}
+
+static int d_cmp(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/*
+ * Per view v (pixels P_v):
+ *   Y = (R + G + B) / 3 of the ground truth; 3x3 Sobel with replicated border;
+ *   s = clip(|grad Y| / P_pctl(|grad Y|), 0, 1) (0 where the percentile is 0),
+ *   nearest rank k = max(1, ceil(pctl * |P_v|));
+ *   w = (eps + 1 - s)^gamma, w~ = w / mean(w) (Eq. 7-8);
+ *   loss[v] = 1/|P_v| sum w~ * rho(r), rho(r) = mean over channels of r^2 (Eq. 18);
+ *   dL/drgb = 2 / (3 |P_v|) * w~ * r.
+ * sobel_s (nullable) receives s, weights (nullable) receives w~.
+ */
+int ora_lf_loss(int n_views, const int32_t* widths, const int32_t* heights, const double* rgb, const double* gt,
+                double gamma, double eps, int64_t pctl_ppm, double* loss, double* dL_drgb, double* sobel_s,
+                double* weights) {
+  int64_t off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    int W = widths[v], H = heights[v];
+    int64_t np = (int64_t)W * H;
+    const double* G = gt + 3 * off;
+    const double* R = rgb + 3 * off;
+    double* Y = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+    double* mag = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+    double* srt = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+    double* w = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+    for (int64_t p = 0; p < np; ++p) Y[p] = (G[3 * p] + G[3 * p + 1] + G[3 * p + 2]) / 3.0;
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        int xm = x > 0 ? x - 1 : 0, xp = x < W - 1 ? x + 1 : W - 1;
+        int ym = y > 0 ? y - 1 : 0, yp = y < H - 1 ? y + 1 : H - 1;
+#define YY(a, b) Y[(int64_t)(b) * W + (a)]
+        double gx = (YY(xp, ym) + 2.0 * YY(xp, y) + YY(xp, yp)) - (YY(xm, ym) + 2.0 * YY(xm, y) + YY(xm, yp));
+        double gy = (YY(xm, yp) + 2.0 * YY(x, yp) + YY(xp, yp)) - (YY(xm, ym) + 2.0 * YY(x, ym) + YY(xp, ym));
+#undef YY
+        mag[(int64_t)y * W + x] = sqrt(gx * gx + gy * gy);
+      }
+    memcpy(srt, mag, sizeof(double) * (size_t)np);
+    qsort(srt, (size_t)np, sizeof(double), d_cmp);
+    int64_t k = ppm_ceil(pctl_ppm, np);
+    if (k < 1) k = 1;
+    if (k > np) k = np;
+    double P = np > 0 ? srt[k - 1] : 0.0;
+    double sw = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+      double s = 0.0;
+      if (P > 0.0) {
+        s = mag[p] / P;
+        s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+      }
+      if (sobel_s) sobel_s[off + p] = s;
+      w[p] = pow(eps + 1.0 - s, gamma);
+      sw += w[p];
+    }
+    double mean = np > 0 ? sw / (double)np : 1.0;
+    double L = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+      double wt = w[p] / mean;
+      if (weights) weights[off + p] = wt;
+      double rho = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double r = R[3 * p + c] - G[3 * p + c];
+        rho += r * r;
+        if (dL_drgb) dL_drgb[3 * (off + p) + c] = 2.0 / (3.0 * (double)np) * wt * r;
+      }
+      L += wt * rho / 3.0;
+    }
+    loss[v] = np > 0 ? L / (double)np : 0.0;
+    free(Y);
+    free(mag);
+    free(srt);
+    free(w);
+    off += np;
+  }
+  return 0;
+}

@@ -1,0 +1,321 @@
+"""Pins for the oracle's renderer (Eq. 1-5) and its backward pass.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant of Eq. 2-4, a brute-force construction, or finite
+differences.  No GPU is used.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_02510_gb300 import synth
+
+
+def axis_camera(W=3, H=3, f=2.0, eye=(0.0, 0.0, 0.0)):
+    """Camera at ``eye`` looking down +z with identity rotation; the centre pixel ray is exactly +z."""
+    e = np.asarray(eye, np.float64)
+    w2c = [1, 0, 0, -e[0], 0, 1, 0, -e[1], 0, 0, 1, -e[2]]
+    return {"width": W, "height": H, "fx": f, "fy": f, "cx": W / 2.0, "cy": H / 2.0, "w2c": w2c, "z_near": 0.05}
+
+
+def ray_of(cam, x, y):
+    R = np.asarray(cam["w2c"], np.float64).reshape(3, 4)[:, :3]
+    t = np.asarray(cam["w2c"], np.float64).reshape(3, 4)[:, 3]
+    o = -R.T @ t
+    dc = np.array([(x + 0.5 - cam["cx"]) / cam["fx"], (y + 0.5 - cam["cy"]) / cam["fy"], 1.0])
+    d = R.T @ dc
+    return o, d / np.linalg.norm(d)
+
+
+def chord_by_bisection(o, d, center, h, t_max=100.0, steps=200000):
+    """Entry/exit of a ray through an axis-aligned box by dense sampling + bisection.
+
+    Independent of any slab formula: it only evaluates the point-in-box predicate.
+    """
+    inside = lambda t: bool(np.all(np.abs(o + t * d - center) <= h))
+    ts = np.linspace(0.0, t_max, steps)
+    pts = o[None, :] + ts[:, None] * d[None, :]
+    ins = np.all(np.abs(pts - center[None, :]) <= h, axis=1)
+    if not ins.any():
+        return None
+    i0 = int(np.argmax(ins))
+    i1 = len(ins) - 1 - int(np.argmax(ins[::-1]))
+
+    def bis(a, b, want_in_at_b):
+        for _ in range(80):
+            m = 0.5 * (a + b)
+            if inside(m) == want_in_at_b:
+                b = m
+            else:
+                a = m
+        return 0.5 * (a + b)
+
+    t_in = 0.0 if i0 == 0 else bis(ts[i0 - 1], ts[i0], True)
+    t_out = bis(ts[min(i1 + 1, len(ts) - 1)], ts[i1], True)
+    return t_in, t_out
+
+
+def test_single_voxel_axis_aligned(ora):
+    # Centre pixel ray is +z; voxel of half-size 0.5 at z=5: chord l = 2h = 1 exactly.
+    cam = axis_camera()
+    c = 2.0
+    col = (0.25, 0.5, 0.75)
+    sc = synth.constant_voxel_scene([[0.0, 0.0, 5.0]], 0.5, [c], [col])
+    r = ora.render(sc, [cam], sh_degree=0)
+    p = 1 * 3 + 1
+    alpha = 1.0 - math.exp(-c * 1.0)
+    np.testing.assert_allclose(r["T"][p], 1.0 - alpha, rtol=0, atol=1e-6)  # colour stored as FP32 SH
+    np.testing.assert_allclose(r["rgb"][p], alpha * np.asarray(col), rtol=0, atol=1e-6)
+    np.testing.assert_allclose(r["depth"][p], alpha * 5.0, rtol=1e-12)
+    assert r["n_hit"][p] == 1
+    assert r["w_arg"][0] >= 0
+    np.testing.assert_allclose(r["w_max"][0], alpha, rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_voxel_oblique_chord(ora, seed):
+    # alpha = 1 - exp(-sigma * l) with l measured by bisection on the inside predicate.
+    rng = np.random.default_rng(seed)
+    center = rng.uniform(-0.3, 0.3, 3)
+    h = 0.4
+    cam = synth.look_at_camera(rng.uniform(-1, 1, 3) + np.array([0, 0, -4.0]), center + rng.uniform(-.1, .1, 3),
+                               16, 16, 40.0)
+    c = 1.7
+    sc = synth.constant_voxel_scene([center], h, [c], [(1.0, 1.0, 1.0)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    hits = 0
+    for y in range(16):
+        for x in range(16):
+            o, d = ray_of(cam, x, y)
+            ch = chord_by_bisection(o, d, center.astype(np.float32).astype(np.float64), np.float64(np.float32(h)),
+                                    t_max=8.0, steps=4001)
+            p = y * 16 + x
+            if ch is None:
+                assert r["n_hit"][p] == 0 and r["T"][p] == 1.0
+                continue
+            hits += 1
+            l = ch[1] - ch[0]
+            alpha = 1.0 - math.exp(-np.float32(c) * l)
+            assert abs(r["T"][p] - (1.0 - alpha)) < 1e-9
+            assert abs(r["depth"][p] - alpha * 0.5 * (ch[0] + ch[1])) < 1e-8
+            assert abs(r["rgb"][p][0] - alpha) < 1e-6
+    assert hits > 20
+
+
+def test_linear_density_field(ora):
+    # Corners sampled from sigma(x) = a.x + b; trilinear reproduces it, so the
+    # midpoint density is a.p_mid + b with p_mid from the bisected chord.
+    center = np.array([0.1, -0.05, 0.0])
+    h = 0.5
+    a = np.array([0.8, -0.6, 1.1])
+    b = 3.0
+    corners = np.array([[(i & 1) * 2 - 1, ((i >> 1) & 1) * 2 - 1, ((i >> 2) & 1) * 2 - 1] for i in range(8)], float)
+    dens = (corners * h + center) @ a + b
+    sc = synth.constant_voxel_scene([center], h, [0.0], [(1, 1, 1)])
+    sc["density"][0] = dens.astype(np.float32)
+    cam = synth.look_at_camera([0.7, 0.4, -3.5], center, 12, 12, 35.0)
+    r = ora.render(sc, [cam], sh_degree=0)
+    checked = 0
+    for y in range(12):
+        for x in range(12):
+            o, d = ray_of(cam, x, y)
+            ch = chord_by_bisection(o, d, center.astype(np.float32).astype(np.float64), h, t_max=7.0, steps=3001)
+            if ch is None:
+                continue
+            pm = o + 0.5 * (ch[0] + ch[1]) * d
+            # the corners were sampled from field(p) = p . a + b
+            sigma = max(0.0, float(pm @ a + b))
+            alpha = 1.0 - math.exp(-sigma * (ch[1] - ch[0]))
+            assert abs(r["T"][y * 12 + x] - (1 - alpha)) < 2e-6
+            checked += 1
+    assert checked > 10
+
+
+def test_stacked_voxels_product(ora):
+    # Three voxels on the centre ray: T = prod (1 - alpha_k), C = sum T_{k-1} alpha_k c_k in depth order.
+    cam = axis_camera()
+    zs = [7.0, 4.0, 5.5]          # deliberately not in id order
+    dens = [0.7, 1.3, 0.4]
+    cols = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    sc = synth.constant_voxel_scene([[0, 0, z] for z in zs], 0.25, dens, cols)
+    r = ora.render(sc, [cam], sh_degree=0)
+    order = np.argsort(zs)
+    T = 1.0
+    C = np.zeros(3)
+    D = 0.0
+    for k in order:
+        al = 1.0 - math.exp(-float(np.float32(dens[k])) * 0.5)   # densities are stored as FP32
+        C += T * al * np.asarray(cols[k], float)
+        D += T * al * zs[k]
+        T *= 1.0 - al
+    p = 4
+    assert abs(r["T"][p] - T) < 1e-12
+    np.testing.assert_allclose(r["rgb"][p], C, atol=1e-6)
+    assert abs(r["depth"][p] - D) < 1e-6
+    assert r["n_hit"][p] == 3
+
+
+def test_white_scene_partition_of_unity(ora):
+    # With every colour = 1, Eq. 2-4 telescope: sum_k w_k + T_final = 1 for every ray.
+    sc = synth.scene_tiny()
+    sc["sh"][:] = 0.0
+    sc["sh"][:, 0:3] = np.float32(0.5 / (0.5 / math.sqrt(math.pi)))
+    cam = synth.orbit_camera(48, 48, 60.0, 1.6, 30.0, 25.0, target=(0.5, 0.4, 0.5))
+    r = ora.render(sc, [cam])
+    s = r["rgb"][:, 0] + r["T"]
+    np.testing.assert_allclose(s, 1.0, atol=1e-6)
+    assert (r["n_hit"] > 0).mean() > 0.2
+    assert np.all(r["w_max"] <= 1.0) and np.all(r["w_max"] >= 0.0)
+
+
+def test_transmittance_monotone_and_weights(ora):
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(32, 32, 60.0, 1.6, 200.0, 35.0, target=(0.5, 0.4, 0.5))
+    n_checked = 0
+    for (x, y) in [(16, 16), (10, 20), (20, 8), (5, 5), (28, 30)]:
+        tr = ora.trace_pixel(sc, cam, x, y)
+        if tr["n"] == 0:
+            continue
+        T = np.concatenate([[1.0], tr["T_after"]])
+        assert np.all(np.diff(T) <= 1e-15)
+        # w_k = T_{k-1} - T_k  (Eq. 2-3)
+        np.testing.assert_allclose(tr["w"], T[:-1] - T[1:], atol=1e-15)
+        n_checked += 1
+    assert n_checked >= 3
+
+
+def test_empty_scene(ora):
+    sc = synth.constant_voxel_scene(np.zeros((0, 3)), 0.1, np.zeros(0), np.zeros((0, 3)))
+    cam = axis_camera(8, 8)
+    r = ora.render(sc, [cam])
+    assert np.all(r["rgb"] == 0) and np.all(r["T"] == 1) and np.all(r["n_hit"] == 0)
+
+
+def test_early_stop_rule(ora):
+    # The sample that crosses t_stop is included; nothing behind it is processed.
+    cam = axis_camera()
+    sc = synth.constant_voxel_scene([[0, 0, 4.0], [0, 0, 6.0]], 0.5, [20.0, 1.0], [(1, 1, 1), (1, 1, 1)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    p = 4
+    assert r["n_hit"][p] == 1
+    assert abs(r["T"][p] - math.exp(-20.0)) < 1e-15
+    assert r["w_arg"][1] == -1 or r["w_arg"][1] != p
+    # a t_stop below T keeps marching
+    r2 = ora.render(sc, [cam], sh_degree=0, t_stop=1e-12)
+    assert r2["n_hit"][p] == 2
+
+
+def test_culling_near_plane(ora):
+    # A voxel entirely in front of z_near is culled even though the ray (t >= 0) crosses it.
+    cam = axis_camera()
+    cam["z_near"] = 0.5
+    sc = synth.constant_voxel_scene([[0, 0, 0.2]], 0.1, [5.0], [(1, 1, 1)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    assert np.all(r["T"] == 1.0)
+    cam["z_near"] = 0.05
+    r = ora.render(sc, [cam], sh_degree=0)
+    assert r["T"][4] < 1.0
+
+
+def test_binned_equals_brute_force(ora):
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(40, 40, 60.0, 1.7, 60.0, 20.0, target=(0.5, 0.4, 0.5))
+    a = ora.render(sc, [cam])
+    b = ora.render(sc, [cam], brute=True)
+    for k in ("rgb", "depth", "T", "n_hit", "w_max", "w_arg"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_w_max_brute_force(ora):
+    # Eq. 5: the max over every ray of T_{k-1} alpha, recomputed from per-pixel traces.
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(20, 20, 50.0, 1.5, 120.0, 30.0, target=(0.5, 0.4, 0.5))
+    r = ora.render(sc, [cam])
+    best = {}
+    for y in range(20):
+        for x in range(20):
+            tr = ora.trace_pixel(sc, cam, x, y)
+            for i, w in zip(tr["ids"], tr["w"]):
+                g = y * 20 + x
+                if int(i) not in best or w > best[int(i)][0]:
+                    best[int(i)] = (w, g)
+    assert len(best) > 20
+    for i, (w, g) in best.items():
+        assert r["w_max"][i] == w
+        assert r["w_arg"][i] == g
+    untouched = np.setdiff1d(np.arange(len(r["w_arg"])), list(best.keys()))
+    assert np.all(r["w_arg"][untouched] == -1)
+
+
+def test_sh_orthonormal(ora):
+    # Gauss-Legendre in cos(theta) x uniform phi integrates degree <= 6 products exactly.
+    xs, ws = np.polynomial.legendre.leggauss(16)
+    nphi = 32
+    G = np.zeros((16, 16))
+    for ct, wt in zip(xs, ws):
+        st = math.sqrt(1 - ct * ct)
+        for j in range(nphi):
+            ph = 2 * math.pi * j / nphi
+            Y = ora.sh_basis([st * math.cos(ph), st * math.sin(ph), ct])
+            G += np.outer(Y, Y) * wt * (2 * math.pi / nphi)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_subdivision_invariance_of_render(ora):
+    # A constant-density, constant-colour voxel split into 8 children renders the same image:
+    # the children's chords partition the parent's chord.
+    cam = synth.look_at_camera([0.6, 0.5, -3.0], [0, 0, 0], 24, 24, 40.0)
+    sc = synth.constant_voxel_scene([[0.0, 0.0, 0.0]], 0.5, [2.5], [(0.3, 0.6, 0.9)])
+    r0 = ora.render(sc, [cam], sh_degree=0)
+    u = np.ones(1, np.float32)
+    sub = ora.subdivide(sc, delta=np.zeros(1, np.float32), z=np.ones(1, np.float32), u=u,
+                        seen=np.ones(1, np.uint8), top_ppm=1000000, kappa=1.0)
+    assert sub["n_new"] == 8
+    r1 = ora.render(sub, [cam], sh_degree=0)
+    np.testing.assert_allclose(r1["T"], r0["T"], atol=1e-12)
+    np.testing.assert_allclose(r1["rgb"], r0["rgb"], atol=1e-6)
+
+
+def _loss(ora, sc, cam, gC, gD, gT, t_stop):
+    r = ora.render(sc, [cam], t_stop=t_stop)
+    return float((r["rgb"] * gC).sum() + (r["depth"] * gD).sum() + (r["T"] * gT).sum())
+
+
+def test_backward_matches_central_differences(ora):
+    # Central FP64 differences of L = sum(g_C.rgb + g_D depth + g_T T) against the reverse pass.
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(24, 24, 45.0, 1.4, 75.0, 30.0, target=(0.5, 0.3, 0.5))
+    rng = np.random.default_rng(7)
+    P = 24 * 24
+    gC = rng.normal(size=(P, 3))
+    gD = rng.normal(size=P) * 0.1
+    gT = rng.normal(size=P)
+    t_stop = 1e-4
+    r = ora.render(sc, [cam], t_stop=t_stop)
+    bw = ora.render_backward(sc, [cam], gC, gD, gT, t_stop=t_stop)
+    hit = np.where(r["w_arg"] >= 0)[0]
+    assert len(hit) > 30
+    pick = rng.choice(hit, size=12, replace=False)
+    checked = 0
+    for v in pick:
+        for kind, idx in (("density", int(rng.integers(8))), ("sh", int(rng.integers(48)))):
+            arr = sc[kind]
+            x0 = float(arr[v, idx])
+            eps = 1e-3 * max(1.0, abs(x0))
+            vals = []
+            for s_ in (+1, -1, +2, -2):
+                sc2 = {k: np.array(a, copy=True) for k, a in sc.items()}
+                sc2[kind][v, idx] = np.float32(x0 + s_ * eps)
+                actual = float(sc2[kind][v, idx]) - x0
+                vals.append((actual, _loss(ora, sc2, cam, gC, gD, gT, t_stop)))
+            (hp, lp), (hm, lm), (hp2, lp2), (hm2, lm2) = vals
+            fd1 = (lp - lm) / (hp - hm)
+            fd2 = (lp2 - lm2) / (hp2 - hm2)
+            an = bw["d_density" if kind == "density" else "d_sh"][v, idx]
+            scale = max(1e-6, abs(fd1), abs(an))
+            if abs(fd1 - fd2) > 1e-3 * scale:
+                continue            # a kink (ReLU, clamp or early stop) lies within the step
+            assert abs(fd1 - an) <= 1e-4 * scale + 1e-9, (kind, v, idx, fd1, an)
+            checked += 1
+    assert checked >= 16
