@@ -1,0 +1,294 @@
+/*
+ * litevoxel.h -- C ABI of the GB300 (sm_103a) sparse-voxel tile rasterizer.
+ *
+ * The library implements the data-parallel hot path of LiteVoxel's training
+ * loop (arXiv 2511.02510): forward and backward passes of the differentiable
+ * tile rasterizer for sparse octree voxels (Sec. III, Eq. 1-5), depth-quantile
+ * pruning (Sec. IV-C, Eq. 11-12 with guards i and iii), priority-driven
+ * subdivision (Sec. IV-D, Eq. 13-16) and the low-frequency-weighted
+ * photometric loss (Sec. IV-B, Eq. 7-10 and Eq. 18).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers named d_* or documented as "device" point to CUDA device
+ *    memory on the current device.  The caller owns every buffer; the library
+ *    never allocates device memory.  Calls that need scratch space take a
+ *    caller-allocated workspace whose size comes from the matching
+ *    *_workspace_size() query (bytes; 256-byte aligned base required).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *    asynchronous on that stream unless `LV_FLAG_SYNC_CHECK` is set in the
+ *    options, in which case the call synchronises the stream and returns the
+ *    device-side status.
+ *  - Host-detectable argument errors return LV_ERR_INVALID_ARG (nothing is
+ *    launched); `lv_last_error()` describes the most recent failure of the
+ *    calling thread.  Errors found on the device (pair or voxel capacity
+ *    overflow) are written to `d_status` (int32 device word, first error
+ *    wins, the caller zeroes it) and the affected outputs are left
+ *    unspecified.  A launch failure returns LV_ERR_CUDA.
+ *  - Pixels of all views are concatenated view-major, each view row-major:
+ *    pixel (view v, x, y) has global id pix_off[v] + y * width_v + x.
+ *  - Voxel arrays are structure-of-arrays, one row per voxel:
+ *      geom     float32 [n][4]  centre x, y, z and half-size h
+ *      level    uint8   [n]     octree depth (edge = root_edge / 2^level)
+ *      density  [n][8]          corner densities, corner i at
+ *                               centre + h * (+-1, +-1, +-1) with bit0 = x,
+ *                               bit1 = y, bit2 = z set meaning "+"
+ *      sh       [n][48]         real SH coefficients [coef 0..15][r, g, b]
+ */
+#ifndef LITEVOXEL_H
+#define LITEVOXEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LV_VERSION_MAJOR 0
+#define LV_VERSION_MINOR 1
+#define LV_MAX_VIEWS 64
+
+typedef enum {
+  LV_OK = 0,
+  LV_ERR_INVALID_ARG = 1,  /* bad pointer, size, dtype or option (host check) */
+  LV_ERR_WORKSPACE = 2,    /* workspace smaller than the size query returned */
+  LV_ERR_CAPACITY = 3,     /* pair / slot / output-voxel capacity exceeded (device) */
+  LV_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+  LV_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  LV_ERR_UNSUPPORTED = 6   /* option combination not built in */
+} lv_status;
+
+typedef enum { LV_F32 = 0, LV_F16 = 1, LV_BF16 = 2 } lv_dtype;
+
+#define LV_FLAG_SYNC_CHECK 1u  /* synchronise and return the device status */
+
+/* Voxel set (all device pointers). density_dtype: LV_F32 or LV_F16; sh_dtype: LV_F32 or LV_BF16. */
+typedef struct {
+  int64_t n;
+  const float* geom;
+  const uint8_t* level; /* only read by lv_subdivide_priority */
+  const void* density;
+  int32_t density_dtype;
+  const void* sh;
+  int32_t sh_dtype;
+  int32_t sh_degree; /* 0..3; coefficients beyond (degree+1)^2 are ignored */
+} lv_voxels;
+
+/* Pinhole camera (host struct, passed by value to the kernels).
+ * x_cam = R x_world + t with w2c = [R | t] row-major 3x4; OpenCV axes
+ * (x right, y down, z forward).  Pixel (x, y) is sampled at its centre
+ * (x + 0.5, y + 0.5); u = fx * x_cam / z_cam + cx (Eq. 1). */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float w2c[12];
+  float z_near; /* voxels whose 8 corners all have z_cam < z_near are culled */
+} lv_camera;
+
+typedef struct {
+  int32_t tile;           /* tile edge in pixels: 8, 16 or 32 */
+  int32_t batch;          /* voxel records staged per shared-memory batch: 64, 128 or 256 */
+  int32_t threads_per_px; /* 1 (reserved) */
+  float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
+  uint32_t flags;         /* LV_FLAG_* */
+} lv_raster_opts;
+
+/* Forward outputs (device).  P = total pixels of all views. */
+typedef struct {
+  float* rgb;                        /* [P][3] composited colour, Eq. 4 */
+  float* depth;                      /* [P] sum_k w_k t_mid_k (nullable) */
+  float* T;                          /* [P] final transmittance, Eq. 3 */
+  uint32_t* n_contrib;               /* [P] tile-list entries up to the last sample used (backward needs it) */
+  unsigned long long* wmax_packed;   /* [n] max-accumulated (f32 bits(w_max) << 32) | (0xffffffff - pixel id),
+                                        Eq. 5; caller zeroes; nullable */
+  float* z_min;                      /* [n] min over views of max(z_centre, z_near); caller sets +inf; nullable */
+  float* delta_min;                  /* [n] min over views of max(z_centre, z_near) / fx, the inter-ray
+                                        spacing at the voxel (Sec. III); caller sets +inf; nullable */
+  uint8_t* seen;                     /* [n] set to 1 when the voxel covers >= 1 tile of some view; nullable */
+} lv_fwd_out;
+
+/* ------------------------------------------------------------------ */
+/* rasterizer (Sec. III, Eq. 1-5)                                       */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of forward/backward workspace for n voxels, the given views and at
+ * most pair_capacity (tile, voxel) pairs.  The same workspace must be passed
+ * unchanged from lv_rasterize_forward to lv_rasterize_backward. */
+size_t lv_forward_workspace_size(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                                 int64_t pair_capacity);
+
+/* Forward pass: per voxel and view, cull / project / bin to tiles (FP32 with
+ * a fixed operation order), emit (tile << 32 | depth key, voxel) pairs,
+ * radix-sort them, find tile ranges and alpha-composite every pixel front to
+ * back (Eq. 2-4): slab-test chord l, sigma = max(0, trilinear corner density
+ * at the chord midpoint), alpha = 1 - exp(-sigma l), colour from SH towards
+ * the voxel centre c = max(0, SH + 0.5).  w_max (Eq. 5) is fused in.
+ * Sorted pairs, tile ranges and the per-pixel optical depth stay in the
+ * workspace for the backward pass.  More than pair_capacity pairs sets
+ * LV_ERR_CAPACITY in d_status (see lv_workspace_counters for the count). */
+lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                               const lv_fwd_out* out, void* workspace, size_t ws_bytes, int64_t pair_capacity,
+                               int32_t* d_status, void* stream);
+
+/* Synchronously read the forward counters from a workspace: out2[0] = pairs
+ * the last forward emitted (may exceed its capacity), out2[1] = visible
+ * (voxel, view) slots. */
+lv_status lv_workspace_counters(const void* workspace, size_t ws_bytes, int64_t* out2, void* stream);
+
+/* Backward pass (reverse-mode of Eq. 2-4), walking each pixel's samples
+ * back to front from n_contrib and recomputing transmittance from the stored
+ * final optical depth (no per-sample storage):
+ *   dL/dsigma_k = l_k (T_k a_k - sum_{j>k} w_j a_j - T_final g_T),
+ *   a_k = g_C . c_k + g_D t_mid_k,
+ * then to the 8 corners through the trilinear weights (zero where the raw
+ * density is negative) and to the SH through c = max(0, SH + 0.5).
+ * dL_ddepth and dL_dT may be NULL.  d_density [n][8] and d_sh [n][48] are
+ * FP32; with accumulate = 0 they are overwritten, else added to.  vox, cams,
+ * n_views, opts, workspace and pair_capacity must be those of the forward
+ * call (the workspace's colour-gradient scratch is reused). */
+lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera* cams, int n_views,
+                                const lv_raster_opts* opts, const lv_fwd_out* fwd, void* workspace, size_t ws_bytes,
+                                int64_t pair_capacity, const float* dL_drgb, const float* dL_ddepth,
+                                const float* dL_dT, float* d_density, float* d_sh, int accumulate,
+                                int32_t* d_status, void* stream);
+
+/* Unpack lv_fwd_out.wmax_packed: w_max[i] (0 if never hit) and the smallest
+ * global pixel id attaining it (-1 if never hit).  argmax is nullable. */
+lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n, float* w_max, int64_t* argmax, void* stream);
+
+/* Copy the sorted pair list of a forward workspace to device buffers:
+ * keys[i] = (global tile << 32) | order-preserving f32 bits of z_centre,
+ * voxel[i] = voxel id; ranges [tiles][2] = [start, end) per global tile.
+ * keys / voxel hold at least min(pairs, pair_capacity) entries.  Any of the
+ * outputs may be NULL.  n, cams, n_views, opts and pair_capacity are those
+ * of the forward call.  For tests and debugging. */
+lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                         const void* workspace, size_t ws_bytes, int64_t pair_capacity, uint64_t* keys,
+                         uint32_t* voxel, uint32_t* ranges, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* depth-quantile pruning (Sec. IV-C, Eq. 11-12, guards i and iii)      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t n_bins;   /* depth bins V_b (16) */
+  int32_t q_ppm;    /* quantile q_b in parts per million (50000 = 5 %) */
+  float ema_alpha;  /* EMA rate alpha (0.1 for a decay of 0.9) */
+  float m_low;      /* hysteresis: state -> out when m < m_low */
+  float m_high;     /*             state -> in  when m > m_high */
+  int32_t cap_ppm;  /* per-step cap on pruned voxels, ppm of n (10000 = 1 %) */
+  int32_t lo_ppm;   /* depth normalisation percentiles (Eq. 14): 50000 */
+  int32_t hi_ppm;   /*                                            950000 */
+} lv_prune_params;
+
+size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p);
+
+/* Over seen voxels: z~ = clip((z - p_lo) / (p_hi - p_lo), 0, 1) with
+ * nearest-rank percentiles of z (Eq. 14), bin = min(nb - 1, floor(nb z~)),
+ * tau_b = nearest-rank q-quantile of w_max in the bin (Eq. 11-12), inside
+ * score x = [w_max > tau_b], m <- (1 - alpha) m + alpha x, hysteresis state
+ * s (1 = in, 0 = out) (guard i); candidates are seen voxels with s = out and
+ * at most floor(cap n) of them, the smallest (w_max, id), are pruned
+ * (guard iii).  Decisions are FP32 with a fixed operation order.  ema_m and
+ * state are updated in place; prune_mask [n] u8 is written; d_n_pruned (int64
+ * device) receives the count.  Unseen voxels are unchanged and never pruned. */
+lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
+                                  float* ema_m, uint8_t* state, const lv_prune_params* p, uint8_t* prune_mask,
+                                  int64_t* d_n_pruned, void* workspace, size_t ws_bytes, int32_t* d_status,
+                                  void* stream);
+
+/* ------------------------------------------------------------------ */
+/* priority-driven subdivision (Sec. IV-D, Eq. 13-16)                   */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  float kappa;      /* eligibility h > kappa * delta (Eq. 13), ~1 */
+  float beta;       /* far bias b(z) = 1 + beta z~ (Eq. 15), 0.1-0.3 */
+  int32_t top_ppm;  /* at most floor(top * n_alive) splits per step (50000 = 5 %) */
+  int32_t l_max;    /* finest level: voxels at l_max are not split */
+  int64_t budget;   /* global growth cap on the voxel count; each split adds 7 */
+  int32_t lo_ppm;   /* depth percentiles for Eq. 14 (50000 / 950000) */
+  int32_t hi_ppm;
+} lv_subdiv_params;
+
+/* One per-voxel auxiliary array carried through topology changes (Adam
+ * moments, EMA state...): survivors copy their row, children get `fill`
+ * (bit pattern of one element) in every element. */
+typedef struct {
+  const void* in;      /* device [n][width] */
+  void* out;           /* device [capacity][width] */
+  int32_t width;       /* elements per voxel */
+  int32_t elem_bytes;  /* 1, 2 or 4 */
+  uint32_t fill;       /* child fill bit pattern (0 for optimizer moments) */
+} lv_aux_array;
+
+#define LV_MAX_AUX 16
+
+size_t lv_subdivide_workspace_size(int64_t n, const lv_subdiv_params* p);
+
+/* alive = !prune_mask (prune_mask nullable); z~ from the nearest-rank
+ * percentiles of z over alive & seen voxels; eligible = alive & seen &
+ * level < l_max & h > kappa * delta; priority p = u (1 + beta z~) (Eq. 15-16);
+ * k = min(floor(top n_alive), floor((budget - n_alive) / 7), #eligible);
+ * the k eligible voxels with the largest (p, then smallest id) are split.
+ * Output (capacity out->n >= n_alive + 7 k, else LV_ERR_CAPACITY in
+ * d_status): survivors in id order, then 8 children per split parent in
+ * parent order, child c at centre + (h/2)(+-1 by bits of c), half-size h/2,
+ * level + 1, corners = the parent's trilinear field at the child corners
+ * (FP32, lerp a(1-t)+bt along x, then y, then z), SH copied (in the input
+ * dtypes).  Auxiliary arrays follow the same order.  selected [n] u8 marks
+ * split parents; d_n_new (int64 device) receives the new count.  `out` must
+ * use the same dtypes as `in`; out->geom / level / density / sh are written
+ * through the (const-qualified) pointers of `out`.  n_aux <= LV_MAX_AUX.
+ * FP16 corner densities are interpolated in FP32 and rounded back to FP16. */
+lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const float* z, const float* u,
+                                const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
+                                const lv_aux_array* aux, int n_aux, const lv_voxels* out, uint8_t* selected,
+                                int64_t* d_n_new, void* workspace, size_t ws_bytes, int32_t* d_status,
+                                void* stream);
+
+/* ------------------------------------------------------------------ */
+/* LF-weighted photometric loss (Sec. IV-B, Eq. 7-10, 18)               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  float eps;        /* Eq. 7 epsilon (1e-3) */
+  float gamma_max;  /* Eq. 9 */
+  float t0, t1;     /* Eq. 9 ramp start / end (iterations) */
+  int32_t pctl_ppm; /* Sobel magnitude normalisation percentile (990000 = P99) */
+} lv_lf_params;
+
+/* gamma(t) of Eq. 9 (host scalar). */
+float lv_lf_gamma(float t, const lv_lf_params* p);
+
+size_t lv_lf_workspace_size(const int32_t* widths, const int32_t* heights, int n_views);
+
+/* Per view: Y = (R + G + B) / 3 of gt, 3x3 Sobel with replicated border,
+ * s = clip(|grad| / P_pctl(|grad|), 0, 1) (0 if the percentile is 0,
+ * nearest rank), w = (eps + 1 - s)^gamma(t), w~ = w / mean(w) (Eq. 7-8),
+ * loss[v] = mean over pixels of w~ * mean_c (rgb - gt)^2 (Eq. 10, 18) and
+ * dL_drgb = 2 / (3 |P_v|) w~ (rgb - gt).  rgb, gt, dL_drgb: [P][3] FP32;
+ * loss: [n_views] FP32 device; dL_drgb nullable. */
+lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* widths, const int32_t* heights,
+                              int n_views, float t, const lv_lf_params* p, float* loss, float* dL_drgb,
+                              void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* misc                                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Human-readable description of the calling thread's last error ("" if none). */
+const char* lv_last_error(void);
+
+/* (major << 16) | minor */
+int32_t lv_version(void);
+
+/* Kernels launched by this library since load (all threads), for reporting. */
+int64_t lv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LITEVOXEL_H */

@@ -348,24 +348,61 @@ int ora_pairs(int64_t n, const float* geom, int n_views, const ora_cam* cams, in
 /* FP64 ray marching                                                   */
 /* ------------------------------------------------------------------ */
 
-/* ray-box chord: returns 1 and the entry/exit parameters when l = t_out - t_in > 0 (t >= 0) */
-static int slab64(const double* o, const double* d, const float* g, double* t_in, double* t_out) {
-  double lo_t = -INFINITY, hi_t = INFINITY;
+/* ray-box chord: returns 1 and the entry/exit parameters when l = t_out - t_in > 0 (t >= 0).
+ * d_in / d_out receive |d| along the axis whose slab sets the entry / exit
+ * (d_in = 0 when the entry is clamped at t = 0); t_in / t_out are written even
+ * for a miss, as long as every axis admits the ray. */
+static int slab64x(const double* o, const double* d, const float* g, double* t_in, double* t_out, double* d_in,
+                   double* d_out) {
+  double lo_t = -INFINITY, hi_t = INFINITY, din = 0.0, dout = 1.0;
   for (int a = 0; a < 3; ++a) {
     double lo = (double)g[a] - (double)g[3], hi = (double)g[a] + (double)g[3];
     if (d[a] == 0.0) {
-      if (o[a] < lo || o[a] > hi) return 0;
+      if (o[a] < lo || o[a] > hi) { *t_in = 1.0; *t_out = -1.0; *d_in = 0.0; *d_out = 1.0; return 0; }
       continue;
     }
     double t1 = (lo - o[a]) / d[a], t2 = (hi - o[a]) / d[a];
     double tn = t1 < t2 ? t1 : t2, tf = t1 < t2 ? t2 : t1;
-    if (tn > lo_t) lo_t = tn;
-    if (tf < hi_t) hi_t = tf;
+    if (tn > lo_t) { lo_t = tn; din = fabs(d[a]); }
+    if (tf < hi_t) { hi_t = tf; dout = fabs(d[a]); }
   }
-  if (lo_t < 0.0) lo_t = 0.0;
+  if (lo_t < 0.0) { lo_t = 0.0; din = 0.0; }
   *t_in = lo_t;
   *t_out = hi_t;
+  *d_in = din;
+  *d_out = dout;
   return hi_t - lo_t > 0.0;
+}
+
+static int slab64(const double* o, const double* d, const float* g, double* t_in, double* t_out) {
+  double a, b;
+  return slab64x(o, d, g, t_in, t_out, &a, &b);
+}
+
+/*
+ * Sensitivity of one sample to FP32 geometry.  An FP32 implementation sees a
+ * ray and voxel positions perturbed by a few units of the last place: a
+ * lateral displacement of about U * t at distance t, U = 2^-21.  A slab plane
+ * crossing t_a = (p_a - o_a) / d_a then moves by U t / |d_a|, so the chord
+ * moves by up to dl = U (t_in / |d_in| + t_out / |d_out| + t_out), and the
+ * midpoint by dp = U (t_mid + t_in / |d_in| + t_out / |d_out|).  The optical
+ * depth x = sigma l moves by dx <= sigma dl + l |grad sigma| dp with
+ * |grad sigma| <= sqrt(3) (max - min corner) / (2h).  Used only to bound the
+ * admissible FP32-vs-FP64 difference of a pixel; it changes no result.
+ */
+#define ORA_FP32_U (1.0 / 2097152.0)
+static double fp32_dx(const float* g, const float* dens8, double sigma, double l, double t_in, double t_out,
+                      double din, double dout) {
+  double S = (din > 0.0 ? t_in / din : 0.0) + (dout > 0.0 ? t_out / dout : 0.0);
+  double dl = ORA_FP32_U * (S + t_out);
+  double dmin = dens8[0], dmax = dens8[0];
+  for (int i = 1; i < 8; ++i) {
+    if (dens8[i] < dmin) dmin = dens8[i];
+    if (dens8[i] > dmax) dmax = dens8[i];
+  }
+  double grad = 1.7320508075688772 * (dmax - dmin) / (2.0 * (double)g[3]);
+  double dp = ORA_FP32_U * (0.5 * (t_in + t_out) + S);
+  return sigma * dl + (l > 0.0 ? l : dl) * grad * dp;
 }
 
 /* trilinear weights of the 8 corners at local coordinates u in [0,1]^3 */
@@ -477,20 +514,36 @@ typedef struct {
   double u[3];
 } sample;
 
-/* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null */
+/* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null.
+ * bnd (nullable) receives the FP32 sensitivity bound of rgb, depth and T
+ * (see fp32_dx); cmax is the largest colour channel of the view. */
 static int64_t march(const double* o, const double* d, const cand* items, int64_t cnt, const float* geom,
                      const float* dens, const double* colors, double t_stop, sample* s, double* rgb,
-                     double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid) {
+                     double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid,
+                     double cmax, double* bnd) {
   double T = 1.0;
   int64_t k = 0;
+  double A = 0.0, X = 0.0, tmax = 0.0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
   *depth = 0.0;
   *near_stop = 0;
   for (int64_t j = 0; j < cnt; ++j) {
     uint32_t id = items[j].id;
     const float* g = geom + 4 * (int64_t)id;
-    double t_in, t_out;
-    if (!slab64(o, d, g, &t_in, &t_out)) continue;
+    const float* d8 = dens + 8 * (int64_t)id;
+    double t_in, t_out, din, dout;
+    if (!slab64x(o, d, g, &t_in, &t_out, &din, &dout)) {
+      /* a near miss that FP32 could count as a hit */
+      if (bnd && t_out > 0.0 && t_in - t_out <= ORA_FP32_U * 4.0 * (t_out + 1.0) / (dout > 0.0 ? dout : 1.0)) {
+        double dm = 0.0;
+        for (int i = 0; i < 8; ++i) dm = d8[i] > dm ? d8[i] : dm;
+        double dx = dm * ORA_FP32_U * 4.0 * (t_out + 1.0) / (dout > 0.0 ? dout : 1.0);
+        A += T * dx;
+        X += dx;
+        if (t_out > tmax) tmax = t_out;
+      }
+      continue;
+    }
     double l = t_out - t_in;
     double tm = 0.5 * (t_in + t_out);
     double u[3];
@@ -503,7 +556,7 @@ static int64_t march(const double* o, const double* d, const cand* items, int64_
     double w8[8];
     trilinear_weights(u, w8);
     double sr = 0.0;
-    for (int i = 0; i < 8; ++i) sr += w8[i] * (double)dens[8 * (int64_t)id + i];
+    for (int i = 0; i < 8; ++i) sr += w8[i] * (double)d8[i];
     double sigma = sr > 0.0 ? sr : 0.0;
     double alpha = -expm1(-sigma * l);
     double w = T * alpha;
@@ -522,12 +575,23 @@ static int64_t march(const double* o, const double* d, const cand* items, int64_
       s[k].id = id; s[k].l = l; s[k].t_mid = tm; s[k].sigma_raw = sr; s[k].alpha = alpha; s[k].T_before = T;
       s[k].u[0] = u[0]; s[k].u[1] = u[1]; s[k].u[2] = u[2];
     }
+    if (bnd) {
+      double dx = fp32_dx(g, d8, sigma, l, t_in, t_out, din, dout);
+      A += T * dx;
+      X += dx;
+      if (t_out > tmax) tmax = t_out;
+    }
     T = T * exp(-sigma * l);
     ++k;
-    if (fabs(T - t_stop) <= 1e-4 * t_stop) *near_stop = 1;
+    if (fabs(log(T / t_stop)) <= 1e-4 + X) *near_stop = 1;
     if (T < t_stop) break;
   }
   *T_out = T;
+  if (bnd) {
+    bnd[0] = 2.0 * cmax * A;
+    bnd[1] = 2.0 * tmax * A;
+    bnd[2] = T * X;
+  }
   return k;
 }
 
@@ -554,10 +618,14 @@ static void view_colors(int64_t n, const float* geom, const float* sh, int degre
  *   and the smallest global pixel id attaining it (-1 if never hit); the
  *   caller initialises w_max to 0 and w_arg to -1 and they accumulate.
  *   brute != 0: every non-culled voxel is a candidate of every pixel.
+ *   bound[3*P] (nullable): per pixel, how far an FP32 evaluation of the same
+ *   pixel may legitimately differ in rgb (max channel), depth and T, from the
+ *   sensitivity of each sample to FP32 geometry rounding (fp32_dx); near_stop
+ *   marks pixels where such a perturbation can change the stop decision.
  */
 int ora_render(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
                const ora_cam* cams, double t_stop, int brute, const int* crop, double* rgb, double* depth,
-               double* T, int32_t* n_hit, uint8_t* near_stop, double* w_max, int64_t* w_arg) {
+               double* T, int32_t* n_hit, uint8_t* near_stop, double* w_max, int64_t* w_arg, double* bound) {
   int nt = ora_threads();
   double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   double* twm = NULL;
@@ -572,6 +640,8 @@ int ora_render(int64_t n, const float* geom, const float* dens, const float* sh,
     cam64 cd;
     cam_derive(&cams[v], &cd);
     view_colors(n, geom, sh, sh_degree, &cd, colors, NULL, NULL);
+    double cmax = 0.0;
+    for (int64_t q = 0; q < 3 * n; ++q) cmax = colors[q] > cmax ? colors[q] : cmax;
     const int* cr = crop ? crop + 4 * v : NULL;
     pixlists L;
     build_lists(n, geom, &cams[v], &cd, brute, cr, &L);
@@ -588,7 +658,7 @@ int ora_render(int64_t n, const float* geom, const float* dens, const float* sh,
         double Tp;
         int64_t k = march(cd.o, d, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, dens, colors,
                           t_stop, NULL, rgb + 3 * gp, depth + gp, &Tp, &ns, twm ? twm + (int64_t)tid * n : NULL,
-                          twa ? twa + (int64_t)tid * n : NULL, gp);
+                          twa ? twa + (int64_t)tid * n : NULL, gp, cmax, bound ? bound + 3 * gp : NULL);
         T[gp] = Tp;
         if (n_hit) n_hit[gp] = (int32_t)k;
         if (near_stop) near_stop[gp] = (uint8_t)ns;
@@ -663,7 +733,7 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
           int ns;
           cam_ray(&cd, x, y, d);
           int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf,
-                            &ns, NULL, NULL, gp);
+                            &ns, NULL, NULL, gp, 0.0, NULL);
           const double* gC = dL_drgb + 3 * gp;
           double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
           double gT = dL_dT ? dL_dT[gp] : 0.0;
@@ -726,7 +796,7 @@ int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float
   int ns;
   cam_ray(&cd, x, y, d);
   int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf, &ns, NULL,
-                    NULL, 0);
+                    NULL, 0, 0.0, NULL);
   int64_t m = K < max_out ? K : max_out;
   for (int64_t k = 0; k < m; ++k) {
     ids[k] = s[k].id;

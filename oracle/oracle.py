@@ -63,7 +63,7 @@ def lib():
             P = C.c_void_p
             I64, I32, D, F = C.c_int64, C.c_int, C.c_double, C.c_float
             _lib.ora_pairs.argtypes = [I64, P, I32, P, I32, I64, P, P, P, P, P, P, P]
-            _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P]
+            _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P]
             _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P]
             _lib.ora_trace_pixel.argtypes = [I64, P, P, P, I32, P, D, I32, I32, I64, P, P, P, P, P]
             _lib.ora_prune.argtypes = [I64, P, P, P, P, P, I32, I64, F, F, F, F, I64, I64, I64, P, P, P, P]
@@ -137,7 +137,12 @@ def _npix(cams):
 
 def render(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, brute: bool = False,
            crop=None) -> dict:
-    """FP64 forward render (Eq. 1-5) of all views; outputs over all views' pixels."""
+    """FP64 forward render (Eq. 1-5) of all views; outputs over all views' pixels.
+
+    bound_rgb / bound_depth / bound_T: admissible FP32-vs-FP64 difference of
+    each pixel from the sensitivity of its samples to FP32 geometry rounding;
+    near_stop: pixels whose stop decision such rounding can change.
+    """
     geom = _c(scene["geom"], np.float32)
     dens = _c(scene["density"], np.float32)
     sh = _c(scene["sh"], np.float32)
@@ -150,10 +155,12 @@ def render(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, br
     ns = np.zeros(P, np.uint8)
     wm = np.zeros(n, np.float64)
     wa = np.full(n, -1, np.int64)
+    bnd = np.zeros((P, 3), np.float64)
     cr = None if crop is None else _c(np.asarray(crop).reshape(-1, 4), np.int32)
     lib().ora_render(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, int(brute),
-                     _p(cr), _p(rgb), _p(depth), _p(T), _p(nh), _p(ns), _p(wm), _p(wa))
-    return {"rgb": rgb, "depth": depth, "T": T, "n_hit": nh, "near_stop": ns, "w_max": wm, "w_arg": wa}
+                     _p(cr), _p(rgb), _p(depth), _p(T), _p(nh), _p(ns), _p(wm), _p(wa), _p(bnd))
+    return {"rgb": rgb, "depth": depth, "T": T, "n_hit": nh, "near_stop": ns, "w_max": wm, "w_arg": wa,
+            "bound_rgb": bnd[:, 0], "bound_depth": bnd[:, 1], "bound_T": bnd[:, 2]}
 
 
 def render_backward(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None, t_stop: float = 1e-4,

@@ -1,0 +1,576 @@
+// lv_adapt.cu -- depth-quantile pruning (LiteVoxel Sec. IV-C, Eq. 11-12 with
+// guards i and iii) and priority-driven subdivision (Sec. IV-D, Eq. 13-16)
+// for sm_103a.  Every selection (percentiles, per-bin quantiles, the cap, the
+// top-k) is an exact radix select on order-preserving 32-bit keys, so the
+// integer outputs do not depend on thread scheduling; all FP32 decisions use
+// a fixed operation order (__fmul_rn / __fadd_rn / __fdiv_rn).
+#include "lv_prims.cuh"
+
+namespace lv {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int blocks_for(int64_t n) {
+  int64_t b = (n + TPB - 1) / TPB;
+  return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ float key_to_float(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// nearest rank: max(1, ceil(ppm * m / 1e6)), 0 when m == 0
+__device__ __forceinline__ uint32_t rank_ppm(uint32_t ppm, uint32_t m) {
+  if (m == 0) return 0;
+  unsigned long long k = ((unsigned long long)ppm * m + 999999ull) / 1000000ull;
+  if (k < 1) k = 1;
+  if (k > m) k = m;
+  return (uint32_t)k;
+}
+
+// Eq. 14 in FP32: clip((z - p_lo) / (p_hi - p_lo), 0, 1); 0 when p_hi <= p_lo
+__device__ __forceinline__ float depth_norm(float z, float p_lo, float p_hi) {
+  float den = __fsub_rn(p_hi, p_lo);
+  if (!(den > 0.f)) return 0.f;
+  float r = __fdiv_rn(__fsub_rn(z, p_lo), den);
+  return fminf(fmaxf(r, 0.f), 1.f);
+}
+
+// ------------------------------------------------------------------ pruning
+struct PruneState {
+  uint32_t ns;            // seen voxels
+  uint32_t n_cand;        // out-state candidates after the update
+  uint32_t c_lt;          // candidates strictly below the cap threshold
+  uint32_t all;           // 1 when every candidate is pruned (n_cand <= cap)
+  uint32_t bin_cnt[SELECT_MAX_QUERIES];
+};
+
+struct PruneWs {
+  PruneState* st;
+  SelectQuery* q;
+  void* sel_tmp;
+  uint16_t* grp;
+  uint32_t* zkey;
+  uint32_t* wkey;
+  size_t bytes;
+};
+
+PruneWs carve_prune(void* base, int64_t n) {
+  PruneWs w;
+  Carve c(base);
+  w.st = c.take<PruneState>(1);
+  w.q = c.take<SelectQuery>(SELECT_MAX_QUERIES);
+  w.sel_tmp = c.take<char>(select_tmp_bytes(SELECT_MAX_QUERIES));
+  w.grp = c.take<uint16_t>(n);
+  w.zkey = c.take<uint32_t>(n);
+  w.wkey = c.take<uint32_t>(n);
+  w.bytes = c.off + 256;
+  return w;
+}
+
+__global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z,
+                          const float* __restrict__ w_max, uint16_t* grp, uint32_t* zkey, uint32_t* wkey,
+                          PruneState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool s = false;
+  if (i < n) {
+    s = seen[i] != 0;
+    grp[i] = s ? 0 : GROUP_NONE;
+    zkey[i] = order_key(z[i]);
+    wkey[i] = order_key(w_max[i]);
+  }
+  unsigned b = __ballot_sync(FULL, s);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->ns, (unsigned)__popc(b));
+}
+
+__global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm) {
+  if (threadIdx.x == 0) {
+    q[0].group = 0; q[0].k = rank_ppm(lo_ppm, st->ns);
+    q[1].group = 0; q[1].k = rank_ppm(hi_ppm, st->ns);
+  }
+}
+
+__global__ void k_pr_bin(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z, int nb,
+                         const SelectQuery* pct, uint16_t* grp, PruneState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i >= n || !seen[i]) return;
+  const float p_lo = key_to_float(pct[0].result), p_hi = key_to_float(pct[1].result);
+  const float zt = depth_norm(z[i], p_lo, p_hi);
+  int b = (int)floorf(__fmul_rn((float)nb, zt));
+  if (b > nb - 1) b = nb - 1;
+  grp[i] = (uint16_t)b;
+  atomicAdd(&st->bin_cnt[b], 1u);
+}
+
+__global__ void k_pr_tau_queries(SelectQuery* q, const PruneState* st, int nb, uint32_t q_ppm) {
+  int b = threadIdx.x;
+  if (b < nb) { q[b].group = b; q[b].k = rank_ppm(q_ppm, st->bin_cnt[b]); }
+}
+
+// guard i: EMA of the inside score and hysteresis; collects the candidates
+__global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const uint32_t* __restrict__ wkey,
+                            const SelectQuery* tau, float alpha, float oma, float m_low, float m_high, float* ema_m,
+                            uint8_t* state, uint16_t* cand_grp, PruneState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool cand = false;
+  if (i < n) {
+    uint16_t b = grp[i];
+    if (b != GROUP_NONE) {
+      const float x = wkey[i] > tau[b].result ? 1.f : 0.f;
+      const float m = __fadd_rn(__fmul_rn(oma, ema_m[i]), __fmul_rn(alpha, x));
+      ema_m[i] = m;
+      uint8_t s = state[i];
+      if (m < m_low) s = 0;
+      else if (m > m_high) s = 1;
+      state[i] = s;
+      cand = s == 0;
+    }
+    cand_grp[i] = cand ? 0 : GROUP_NONE;
+  }
+  unsigned bl = __ballot_sync(FULL, cand);
+  if ((threadIdx.x & 31) == 0 && bl) atomicAdd(&st->n_cand, (unsigned)__popc(bl));
+}
+
+__global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
+  if (threadIdx.x == 0) {
+    st->all = st->n_cand <= cap ? 1u : 0u;
+    q[0].group = 0;
+    q[0].k = st->all ? 0u : cap;  // cap-th smallest w_max among the candidates
+  }
+}
+
+// candidates strictly below the threshold; the ties at it compete by id
+__global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr, uint16_t* cand_grp,
+                          PruneState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool lt = false;
+  if (i < n && cand_grp[i] == 0 && thr[0].k != 0) {
+    const uint32_t v = thr[0].result;
+    lt = wkey[i] < v;
+    cand_grp[i] = wkey[i] == v ? 0 : GROUP_NONE;
+  }
+  unsigned bl = __ballot_sync(FULL, lt);
+  if ((threadIdx.x & 31) == 0 && bl) atomicAdd(&st->c_lt, (unsigned)__popc(bl));
+}
+
+__global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, const PruneState* st, uint32_t cap) {
+  if (threadIdx.x == 0) {
+    q[0].group = 0;
+    q[0].k = (thr[0].k != 0 && cap > st->c_lt) ? cap - st->c_lt : 0u;
+  }
+}
+
+__global__ void k_pr_mask(int64_t n, const uint16_t* __restrict__ grp, const uint8_t* __restrict__ state,
+                          const uint32_t* __restrict__ wkey, const SelectQuery* thr, const SelectQuery* tie,
+                          const PruneState* st, uint8_t* mask, int64_t* n_pruned, uint32_t cap) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i < n) {
+    bool p = false;
+    if (grp[i] != GROUP_NONE && state[i] == 0) {
+      if (st->all) p = true;
+      else if (thr[0].k != 0) {
+        const uint32_t v = thr[0].result;
+        p = wkey[i] < v || (wkey[i] == v && tie[0].k != 0 && (uint32_t)i <= tie[0].result);
+      }
+    }
+    mask[i] = p ? 1 : 0;
+  }
+  if (i == 0 && n_pruned) *n_pruned = st->all ? (int64_t)st->n_cand : (int64_t)cap;
+}
+
+// ------------------------------------------------------------------ subdivision
+struct SubState {
+  uint32_t n_alive;
+  uint32_t n_el;
+  uint32_t k;
+  uint32_t c_gt;  // eligible voxels with a strictly higher priority than the k-th
+  uint32_t fits;  // output capacity suffices
+};
+
+struct SubWs {
+  SubState* st;
+  SelectQuery* q;   // [0..1] percentiles, [2] k-th priority, [3] tie id
+  void* sel_tmp;
+  uint16_t* grp;
+  uint32_t* zkey;
+  uint32_t* pkey;
+  uint32_t* surv;
+  uint32_t* sel;
+  unsigned long long* surv_pos;
+  uint32_t* sel_rank;
+  unsigned long long* totals;
+  void* scan_tmp;
+  size_t bytes;
+};
+
+SubWs carve_sub(void* base, int64_t n) {
+  SubWs w;
+  Carve c(base);
+  w.st = c.take<SubState>(1);
+  w.q = c.take<SelectQuery>(8);
+  w.sel_tmp = c.take<char>(select_tmp_bytes(SELECT_MAX_QUERIES));
+  w.grp = c.take<uint16_t>(n);
+  w.zkey = c.take<uint32_t>(n);
+  w.pkey = c.take<uint32_t>(n);
+  w.surv = c.take<uint32_t>(n);
+  w.sel = c.take<uint32_t>(n);
+  w.surv_pos = c.take<unsigned long long>(n);
+  w.sel_rank = c.take<uint32_t>(n);
+  w.totals = c.take<unsigned long long>(4);
+  w.scan_tmp = c.take<char>(scan2_tmp_bytes());
+  w.bytes = c.off + 256;
+  return w;
+}
+
+__global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
+                           const float* __restrict__ z, uint16_t* grp, uint32_t* zkey, SubState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool alive = false;
+  if (i < n) {
+    alive = pm ? pm[i] == 0 : true;
+    grp[i] = (alive && seen[i]) ? 0 : GROUP_NONE;
+    zkey[i] = order_key(z[i]);
+  }
+  unsigned b = __ballot_sync(FULL, alive);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->n_alive, (unsigned)__popc(b));
+}
+
+__global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter) {
+  if (threadIdx.x == 0) {
+    uint32_t m = *counter;
+    q[0].group = 0; q[0].k = rank_ppm(lo_ppm, m);
+    q[1].group = 0; q[1].k = rank_ppm(hi_ppm, m);
+  }
+}
+
+__global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, uint32_t* counter) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool f = i < n && grp[i] == 0;
+  unsigned b = __ballot_sync(FULL, f);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(counter, (unsigned)__popc(b));
+}
+
+// Eq. 13 eligibility and Eq. 15-16 priority; pkey orders by descending priority
+__global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const uint8_t* __restrict__ level,
+                              const float* __restrict__ delta, const float* __restrict__ z,
+                              const float* __restrict__ u, const SelectQuery* pct, float kappa, float beta, int l_max,
+                              uint16_t* grp, uint32_t* pkey, SubState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool el = false;
+  if (i < n) {
+    if (grp[i] == 0 && (int)level[i] < l_max) {
+      const float thr = __fmul_rn(kappa, delta[i]);
+      if (geom[i].w > thr) {
+        el = true;
+        const float zt = depth_norm(z[i], key_to_float(pct[0].result), key_to_float(pct[1].result));
+        const float b = __fadd_rn(1.0f, __fmul_rn(beta, zt));
+        const float p = __fmul_rn(u[i], b);
+        pkey[i] = ~order_key(p);
+      }
+    }
+    grp[i] = el ? 0 : GROUP_NONE;
+  }
+  unsigned b = __ballot_sync(FULL, el);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->n_el, (unsigned)__popc(b));
+}
+
+__global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget) {
+  if (threadIdx.x == 0) {
+    const unsigned long long na = st->n_alive;
+    unsigned long long k = (unsigned long long)top_ppm * na / 1000000ull;
+    const unsigned long long kb = budget > (long long)na ? (unsigned long long)(budget - (long long)na) / 7ull : 0ull;
+    if (kb < k) k = kb;
+    if (st->n_el < k) k = st->n_el;
+    st->k = (uint32_t)k;
+    q[2].group = 0;
+    q[2].k = (uint32_t)k;
+  }
+}
+
+__global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const SelectQuery* thr, uint16_t* grp,
+                          SubState* st) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  bool gt = false;
+  if (i < n && grp[i] == 0) {
+    if (thr->k != 0) {
+      gt = pkey[i] < thr->result;
+      grp[i] = pkey[i] == thr->result ? 0 : GROUP_NONE;
+    } else {
+      grp[i] = GROUP_NONE;
+    }
+  }
+  unsigned b = __ballot_sync(FULL, gt);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->c_gt, (unsigned)__popc(b));
+}
+
+__global__ void k_sd_tie_query(SelectQuery* q, const SubState* st) {
+  if (threadIdx.x == 0) {
+    q[3].group = 0;
+    q[3].k = (q[2].k != 0 && st->k > st->c_gt) ? st->k - st->c_gt : 0u;
+  }
+}
+
+__global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
+                            const uint8_t* __restrict__ level, const float4* __restrict__ geom,
+                            const float* __restrict__ delta, const uint32_t* __restrict__ pkey,
+                            const SelectQuery* q, float kappa, int l_max, uint8_t* selected, uint32_t* surv,
+                            uint32_t* sel) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i >= n) return;
+  const bool alive = pm ? pm[i] == 0 : true;
+  bool s = false;
+  if (alive && seen[i] && q[2].k != 0 && (int)level[i] < l_max && geom[i].w > __fmul_rn(kappa, delta[i])) {
+    const uint32_t v = q[2].result;
+    s = pkey[i] < v || (pkey[i] == v && q[3].k != 0 && (uint32_t)i <= q[3].result);
+  }
+  selected[i] = s ? 1 : 0;
+  sel[i] = s ? 1u : 0u;
+  surv[i] = (alive && !s) ? 1u : 0u;
+}
+
+__global__ void k_sd_check(const unsigned long long* totals, SubState* st, int64_t capacity, int64_t* n_new,
+                           int32_t* status) {
+  if (threadIdx.x == 0) {
+    const long long nn = (long long)totals[0] + 8ll * (long long)totals[1];
+    st->fits = nn <= capacity ? 1u : 0u;
+    if (!st->fits) report(status, LV_ERR_CAPACITY);
+    if (n_new) *n_new = nn;
+  }
+}
+
+struct AuxSet {
+  int n;
+  lv_aux_array a[LV_MAX_AUX];
+};
+
+__device__ __forceinline__ void aux_copy(const lv_aux_array& a, int64_t src, int64_t dst) {
+  const size_t row = (size_t)a.width * a.elem_bytes;
+  const char* s = (const char*)a.in + row * (size_t)src;
+  char* d = (char*)a.out + row * (size_t)dst;
+  if ((row & 3) == 0 && (((uintptr_t)s | (uintptr_t)d) & 3) == 0) {
+    for (size_t k = 0; k < row / 4; ++k) ((uint32_t*)d)[k] = ((const uint32_t*)s)[k];
+  } else {
+    for (size_t k = 0; k < row; ++k) d[k] = s[k];
+  }
+}
+
+__device__ __forceinline__ void aux_fill(const lv_aux_array& a, int64_t dst) {
+  char* d = (char*)a.out + (size_t)a.width * a.elem_bytes * (size_t)dst;
+  for (int e = 0; e < a.width; ++e) {
+    if (a.elem_bytes == 4) ((uint32_t*)d)[e] = a.fill;
+    else if (a.elem_bytes == 2) ((uint16_t*)d)[e] = (uint16_t)a.fill;
+    else ((uint8_t*)d)[e] = (uint8_t)a.fill;
+  }
+}
+
+template <typename DT, typename ST>
+__global__ void k_sd_write_survivors(int64_t n, const uint32_t* __restrict__ surv,
+                                     const unsigned long long* __restrict__ pos, const SubState* st,
+                                     const float4* __restrict__ geom, const uint8_t* __restrict__ level,
+                                     const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
+                                     uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
+  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i >= n || !surv[i] || !st->fits) return;
+  const int64_t o = (int64_t)pos[i];
+  ogeom[o] = geom[i];
+  olevel[o] = level[i];
+  // density rows are 32 B (f32) or 16 B (f16), SH rows 192 B or 96 B: copy as 16-byte words
+  const uint4* ds = (const uint4*)(dens + 8 * i);
+  uint4* dd = (uint4*)(odens + 8 * o);
+  for (int k = 0; k < (int)(8 * sizeof(DT) / 16); ++k) dd[k] = ds[k];
+  const uint4* ss = (const uint4*)(sh + 48 * i);
+  uint4* sd = (uint4*)(osh + 48 * o);
+  for (int k = 0; k < (int)(48 * sizeof(ST) / 16); ++k) sd[k] = ss[k];
+  for (int a = 0; a < aux.n; ++a) aux_copy(aux.a[a], i, o);
+}
+
+template <typename DT>
+__device__ __forceinline__ DT from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// a (1 - t) + b t with every product and the sum rounded
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+  return __fadd_rn(__fmul_rn(a, __fsub_rn(1.0f, t)), __fmul_rn(b, t));
+}
+
+template <typename DT, typename ST>
+__global__ void k_sd_write_children(int64_t n, const uint32_t* __restrict__ sel,
+                                    const uint32_t* __restrict__ rank, const unsigned long long* totals,
+                                    const SubState* st, const float4* __restrict__ geom,
+                                    const uint8_t* __restrict__ level, const DT* __restrict__ dens,
+                                    const ST* __restrict__ sh, float4* ogeom, uint8_t* olevel, DT* odens, ST* osh,
+                                    const __grid_constant__ AuxSet aux) {
+  // one thread per (parent, child)
+  int64_t t = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  int64_t i = t >> 3;
+  int c = (int)(t & 7);
+  if (i >= n || !sel[i] || !st->fits) return;
+  const int64_t o = (int64_t)totals[0] + 8 * (int64_t)rank[i] + c;
+  const float4 g = geom[i];
+  const float hc = __fmul_rn(g.w, 0.5f);
+  ogeom[o] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
+                         __fadd_rn(g.z, (c & 4) ? hc : -hc), hc);
+  olevel[o] = (uint8_t)(level[i] + 1);
+  float d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * i + k]);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
+    const float qy = (float)(((c >> 1) & 1) + ((j >> 1) & 1)) * 0.5f;
+    const float qz = (float)(((c >> 2) & 1) + ((j >> 2) & 1)) * 0.5f;
+    const float x0 = lerp_rn(d[0], d[1], qx), x1 = lerp_rn(d[2], d[3], qx);
+    const float x2 = lerp_rn(d[4], d[5], qx), x3 = lerp_rn(d[6], d[7], qx);
+    const float y0 = lerp_rn(x0, x1, qy), y1 = lerp_rn(x2, x3, qy);
+    odens[8 * o + j] = from_f32<DT>(lerp_rn(y0, y1, qz));
+  }
+  const uint4* ss = (const uint4*)(sh + 48 * i);
+  uint4* sd = (uint4*)(osh + 48 * o);
+  for (int k = 0; k < (int)(48 * sizeof(ST) / 16); ++k) sd[k] = ss[k];
+  for (int a = 0; a < aux.n; ++a) aux_fill(aux.a[a], o);
+}
+
+}  // namespace
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p) {
+  if (n < 0 || !p) return 0;
+  return carve_prune(nullptr, n).bytes;
+}
+
+extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
+                                             float* ema_m, uint8_t* state, const lv_prune_params* p,
+                                             uint8_t* prune_mask, int64_t* d_n_pruned, void* workspace,
+                                             size_t ws_bytes, int32_t* d_status, void* stream) {
+  (void)d_status;
+  if (!p || n < 0 || n > 0x7fffffffLL) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (n > 0 && (!w_max || !seen || !z || !ema_m || !state || !prune_mask)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
+  if (p->n_bins < 1 || p->n_bins > SELECT_MAX_QUERIES) { set_error("n_bins must be 1..%d", SELECT_MAX_QUERIES); return LV_ERR_INVALID_ARG; }
+  if (p->q_ppm < 0 || p->q_ppm > 1000000 || p->cap_ppm < 0 || p->cap_ppm > 1000000 || p->lo_ppm < 0 ||
+      p->lo_ppm > 1000000 || p->hi_ppm < 0 || p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->ema_alpha >= 0.f && p->ema_alpha <= 1.f)) { set_error("ema_alpha must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  PruneWs w = carve_prune(workspace, n);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (d_n_pruned) cudaMemsetAsync(d_n_pruned, 0, sizeof(int64_t), s);
+    return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
+  }
+  const int nb = p->n_bins;
+  const uint32_t cap = (uint32_t)(((unsigned long long)p->cap_ppm * (unsigned long long)n) / 1000000ull);
+  const float alpha = p->ema_alpha;
+  const float oma = 1.0f - alpha;  // rounded to FP32 once, as the oracle does
+  const int blocks = blocks_for(n);
+  cudaMemsetAsync(w.st, 0, sizeof(PruneState), s);
+  k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w_max, w.grp, w.zkey, w.wkey, w.st);
+  k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
+  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, nb, w.q, w.grp, w.st);
+  // the percentiles in q[0..1] are consumed by the binning: q is reused per bin
+  k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm);
+  select_kth(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
+  // candidates get their own group array (zkey is free now: reuse it as u16 storage)
+  uint16_t* cand = (uint16_t*)w.zkey;
+  k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, cand,
+                                      w.st);
+  SelectQuery* qc = w.q + SELECT_MAX_QUERIES - 2;  // cap threshold
+  SelectQuery* qi = w.q + SELECT_MAX_QUERIES - 1;  // tie id
+  k_pr_cap_query<<<1, 32, 0, s>>>(qc, w.st, cap);
+  select_kth(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
+  k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, cand, w.st);
+  k_pr_tie_query<<<1, 32, 0, s>>>(qi, qc, w.st, cap);
+  select_kth(nullptr, cand, n, qi, 1, w.sel_tmp, s);
+  k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.grp, state, w.wkey, qc, qi, w.st, prune_mask, d_n_pruned, cap);
+  count_launch(8);
+  return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
+}
+
+extern "C" size_t lv_subdivide_workspace_size(int64_t n, const lv_subdiv_params* p) {
+  if (n < 0 || !p) return 0;
+  return carve_sub(nullptr, n).bytes;
+}
+
+extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const float* z, const float* u,
+                                           const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
+                                           const lv_aux_array* aux, int n_aux, const lv_voxels* out,
+                                           uint8_t* selected, int64_t* d_n_new, void* workspace, size_t ws_bytes,
+                                           int32_t* d_status, void* stream) {
+  if (!in || !out || !p) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  const int64_t n = in->n;
+  if (n < 0 || n > 0x7fffffffLL || out->n < 0) { set_error("bad voxel counts"); return LV_ERR_INVALID_ARG; }
+  if (n > 0 && (!in->geom || !in->level || !in->density || !in->sh || !delta || !z || !u || !seen || !selected)) {
+    set_error("null array"); return LV_ERR_INVALID_ARG;
+  }
+  if (out->n > 0 && (!out->geom || !out->level || !out->density || !out->sh)) { set_error("null output array"); return LV_ERR_INVALID_ARG; }
+  if (in->density_dtype != out->density_dtype || in->sh_dtype != out->sh_dtype) { set_error("output dtypes must match the input"); return LV_ERR_INVALID_ARG; }
+  if (in->density_dtype != LV_F32 && in->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
+  if (in->sh_dtype != LV_F32 && in->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
+  if (n_aux < 0 || n_aux > LV_MAX_AUX || (n_aux > 0 && !aux)) { set_error("n_aux must be 0..%d", LV_MAX_AUX); return LV_ERR_INVALID_ARG; }
+  if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||
+      p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  AuxSet as;
+  as.n = n_aux;
+  for (int a = 0; a < n_aux; ++a) {
+    as.a[a] = aux[a];
+    const int eb = aux[a].elem_bytes;
+    if ((eb != 1 && eb != 2 && eb != 4) || aux[a].width < 1 || (n > 0 && (!aux[a].in || !aux[a].out))) {
+      set_error("aux array %d: bad description", a); return LV_ERR_INVALID_ARG;
+    }
+  }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  SubWs w = carve_sub(workspace, n);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
+    return cuda_check(cudaGetLastError(), "lv_subdivide_priority");
+  }
+  const int blocks = blocks_for(n);
+  cudaMemsetAsync(w.st, 0, sizeof(SubState), s);
+  k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st);
+  uint32_t* cnt_seen = &w.st->n_el;  // temporarily counts alive & seen voxels
+  k_sd_count_group0<<<blocks, TPB, 0, s>>>(n, w.grp, cnt_seen);
+  k_sd_pct_queries<<<1, 32, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, cnt_seen);
+  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  cudaMemsetAsync(cnt_seen, 0, sizeof(uint32_t), s);
+  k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, w.q, p->kappa, p->beta,
+                                        p->l_max, w.grp, w.pkey, w.st);
+  k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);
+  select_kth(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
+  k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.st);
+  k_sd_tie_query<<<1, 32, 0, s>>>(w.q, w.st);
+  select_kth(nullptr, w.grp, n, w.q + 3, 1, w.sel_tmp, s);
+  k_sd_select<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, in->level, (const float4*)in->geom, delta, w.pkey, w.q,
+                                      p->kappa, p->l_max, selected, w.surv, w.sel);
+  scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
+  k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out->n, d_n_new, d_status ? d_status : (int32_t*)nullptr);
+  const int cblocks = blocks_for(8 * n);
+#define LV_SUB(DT, ST)                                                                                                \
+  do {                                                                                                                \
+    k_sd_write_survivors<DT, ST><<<blocks, TPB, 0, s>>>(n, w.surv, w.surv_pos, w.st, (const float4*)in->geom,        \
+                                                        in->level, (const DT*)in->density, (const ST*)in->sh,         \
+                                                        (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
+                                                        (ST*)out->sh, as);                                            \
+    k_sd_write_children<DT, ST><<<cblocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.totals, w.st, (const float4*)in->geom, \
+                                                        in->level, (const DT*)in->density, (const ST*)in->sh,         \
+                                                        (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
+                                                        (ST*)out->sh, as);                                            \
+  } while (0)
+  if (in->density_dtype == LV_F32 && in->sh_dtype == LV_F32) LV_SUB(float, float);
+  else if (in->density_dtype == LV_F16 && in->sh_dtype == LV_F32) LV_SUB(__half, float);
+  else if (in->density_dtype == LV_F32 && in->sh_dtype == LV_BF16) LV_SUB(float, __nv_bfloat16);
+  else LV_SUB(__half, __nv_bfloat16);
+#undef LV_SUB
+  count_launch(12);
+  return cuda_check(cudaGetLastError(), "lv_subdivide_priority");
+}

@@ -1,0 +1,35 @@
+// lv_api.cu -- error reporting, version and launch accounting of the C ABI.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+
+#include "lv_common.cuh"
+
+namespace lv {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+lv_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LV_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return LV_ERR_CUDA;
+}
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace lv
+
+extern "C" const char* lv_last_error(void) { return lv::g_err; }
+
+extern "C" int32_t lv_version(void) { return (LV_VERSION_MAJOR << 16) | LV_VERSION_MINOR; }
+
+extern "C" int64_t lv_launch_count(void) { return (int64_t)lv::g_launches.load(); }

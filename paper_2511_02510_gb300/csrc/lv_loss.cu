@@ -1,0 +1,212 @@
+// lv_loss.cu -- low-frequency-weighted photometric loss (LiteVoxel Sec. IV-B,
+// Eq. 7-10 and Eq. 18) for sm_103a.  Per view: Sobel magnitude of the ground
+// truth luma (stop-gradient), exact nearest-rank percentile normalisation by a
+// radix select, inverse-Sobel weight (eps + 1 - s)^gamma, mean normalisation,
+// weighted squared error and its gradient.  Sums are accumulated in FP64.
+#include "lv_prims.cuh"
+
+namespace lv {
+
+namespace {
+
+constexpr int TPB = 256;
+
+struct ViewPix {
+  int n;
+  int W[LV_MAX_VIEWS];
+  int H[LV_MAX_VIEWS];
+  long long off[LV_MAX_VIEWS + 1];
+  uint32_t k[LV_MAX_VIEWS];  // nearest-rank index of the percentile
+};
+
+struct LfWs {
+  SelectQuery* q;
+  void* sel_tmp;
+  double* wsum;   // [views]
+  double* lsum;   // [views]
+  uint16_t* grp;  // [pixels]
+  uint32_t* mkey; // [pixels] Sobel magnitude bits
+  float* w;       // [pixels] unnormalised weight
+  size_t bytes;
+};
+
+LfWs carve_lf(void* base, int nv, int64_t pixels) {
+  LfWs w;
+  Carve c(base);
+  w.q = c.take<SelectQuery>(SELECT_MAX_QUERIES);
+  w.sel_tmp = c.take<char>(select_tmp_bytes(SELECT_MAX_QUERIES));
+  w.wsum = c.take<double>(LV_MAX_VIEWS);
+  w.lsum = c.take<double>(LV_MAX_VIEWS);
+  w.grp = c.take<uint16_t>(pixels);
+  w.mkey = c.take<uint32_t>(pixels);
+  w.w = c.take<float>(pixels);
+  w.bytes = c.off + 256;
+  return w;
+}
+
+__device__ __forceinline__ int view_of(const ViewPix& vp, long long p) {
+  int v = 0;
+  while (v + 1 < vp.n && p >= vp.off[v + 1]) ++v;
+  return v;
+}
+
+__device__ __forceinline__ float luma(const float* __restrict__ gt, long long p) {
+  return (gt[3 * p] + gt[3 * p + 1] + gt[3 * p + 2]) * (1.0f / 3.0f);
+}
+
+// Eq. 7 input: |Sobel(Y)| with replicated border
+__global__ void k_lf_sobel(const float* __restrict__ gt, const __grid_constant__ ViewPix vp, uint16_t* grp,
+                           uint32_t* mkey) {
+  long long p = blockIdx.x * (long long)TPB + threadIdx.x;
+  if (p >= vp.off[vp.n]) return;
+  const int v = view_of(vp, p);
+  const long long loc = p - vp.off[v];
+  const int W = vp.W[v], H = vp.H[v];
+  const int x = (int)(loc % W), y = (int)(loc / W);
+  const int xm = max(x - 1, 0), xp = min(x + 1, W - 1), ym = max(y - 1, 0), yp = min(y + 1, H - 1);
+  const float* g = gt + 3 * vp.off[v];
+#define Y_(a, b) luma(g, (long long)(b) * W + (a))
+  const float gx = (Y_(xp, ym) + 2.f * Y_(xp, y) + Y_(xp, yp)) - (Y_(xm, ym) + 2.f * Y_(xm, y) + Y_(xm, yp));
+  const float gy = (Y_(xm, yp) + 2.f * Y_(x, yp) + Y_(xp, yp)) - (Y_(xm, ym) + 2.f * Y_(x, ym) + Y_(xp, ym));
+#undef Y_
+  const float mag = sqrtf(gx * gx + gy * gy);
+  grp[p] = (uint16_t)v;
+  mkey[p] = __float_as_uint(mag);  // non-negative: bit order == value order
+}
+
+__global__ void k_lf_queries(SelectQuery* q, const __grid_constant__ ViewPix vp) {
+  int v = threadIdx.x;
+  if (v < vp.n) { q[v].group = v; q[v].k = vp.k[v]; }
+}
+
+__device__ __forceinline__ void block_add_f64(double v, double* dst) {
+  __shared__ double sred[TPB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  if (lane == 0) sred[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < TPB / 32 ? sred[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+  }
+  __syncthreads();
+}
+
+// Eq. 7: w = (eps + 1 - s)^gamma, s = clip(|grad| / P, 0, 1); blocks never span views
+__global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery* q, const __grid_constant__ ViewPix vp,
+                            int v, float eps, float gamma, float* w, double* wsum) {
+  const long long p = vp.off[v] + blockIdx.x * (long long)TPB + threadIdx.x;
+  float wv = 0.f;
+  if (p < vp.off[v + 1]) {
+    const float P = __uint_as_float(q[v].result);
+    float s = 0.f;
+    if (q[v].k != 0 && P > 0.f) s = fminf(fmaxf(__uint_as_float(mkey[p]) / P, 0.f), 1.f);
+    wv = gamma == 0.f ? 1.f : powf(eps + 1.f - s, gamma);
+    w[p] = wv;
+  }
+  block_add_f64((double)wv, &wsum[v]);
+}
+
+// Eq. 8 + Eq. 18: w~ = w / <w>, L = 1/|P| sum w~ mean_c r^2, dL/drgb = 2/(3|P|) w~ r
+__global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict__ gt, const float* __restrict__ w,
+                          const __grid_constant__ ViewPix vp, int v, const double* wsum, double* lsum,
+                          float* __restrict__ grad) {
+  const long long p = vp.off[v] + blockIdx.x * (long long)TPB + threadIdx.x;
+  const long long np = vp.off[v + 1] - vp.off[v];
+  double contrib = 0.0;
+  if (p < vp.off[v + 1]) {
+    const float mean = (float)(wsum[v] / (double)np);
+    const float wt = w[p] / mean;
+    const float r0 = rgb[3 * p] - gt[3 * p], r1 = rgb[3 * p + 1] - gt[3 * p + 1], r2 = rgb[3 * p + 2] - gt[3 * p + 2];
+    contrib = (double)wt * ((double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2) / 3.0;
+    if (grad) {
+      const float c = (float)(2.0 / (3.0 * (double)np)) * wt;
+      grad[3 * p] = c * r0;
+      grad[3 * p + 1] = c * r1;
+      grad[3 * p + 2] = c * r2;
+    }
+  }
+  block_add_f64(contrib, &lsum[v]);
+}
+
+__global__ void k_lf_finish(const __grid_constant__ ViewPix vp, const double* lsum, float* loss) {
+  int v = threadIdx.x;
+  if (v < vp.n) {
+    const long long np = vp.off[v + 1] - vp.off[v];
+    loss[v] = np > 0 ? (float)(lsum[v] / (double)np) : 0.f;
+  }
+}
+
+bool make_viewpix(const int32_t* widths, const int32_t* heights, int nv, int32_t pctl_ppm, ViewPix* vp) {
+  if (nv < 1 || nv > LV_MAX_VIEWS || !widths || !heights) return false;
+  vp->n = nv;
+  long long off = 0;
+  for (int v = 0; v < nv; ++v) {
+    if (widths[v] < 1 || heights[v] < 1) return false;
+    vp->W[v] = widths[v];
+    vp->H[v] = heights[v];
+    vp->off[v] = off;
+    const long long np = (long long)widths[v] * heights[v];
+    unsigned long long k = ((unsigned long long)pctl_ppm * (unsigned long long)np + 999999ull) / 1000000ull;
+    if (k < 1) k = 1;
+    if (k > (unsigned long long)np) k = np;
+    vp->k[v] = (uint32_t)k;
+    off += np;
+  }
+  vp->off[nv] = off;
+  return off < 0xffffffffLL;
+}
+
+}  // namespace
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" float lv_lf_gamma(float t, const lv_lf_params* p) {
+  if (!p) return 0.f;
+  if (t < p->t0) return 0.f;
+  if (t < p->t1) return p->gamma_max * (t - p->t0) / (p->t1 - p->t0);
+  return p->gamma_max;
+}
+
+extern "C" size_t lv_lf_workspace_size(const int32_t* widths, const int32_t* heights, int n_views) {
+  ViewPix vp;
+  if (!make_viewpix(widths, heights, n_views, 990000, &vp)) return 0;
+  return carve_lf(nullptr, n_views, vp.off[n_views]).bytes;
+}
+
+extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* widths,
+                                         const int32_t* heights, int n_views, float t, const lv_lf_params* p,
+                                         float* loss, float* dL_drgb, void* workspace, size_t ws_bytes,
+                                         void* stream) {
+  if (!rgb || !gt || !p || !loss) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (p->pctl_ppm < 0 || p->pctl_ppm > 1000000) { set_error("pctl_ppm must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->eps > 0.f) || !(p->t1 > p->t0) || !(p->gamma_max >= 0.f)) { set_error("need eps > 0, t1 > t0, gamma_max >= 0"); return LV_ERR_INVALID_ARG; }
+  ViewPix vp;
+  if (!make_viewpix(widths, heights, n_views, p->pctl_ppm, &vp)) { set_error("bad view sizes"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  const int64_t P = vp.off[n_views];
+  LfWs w = carve_lf(workspace, n_views, P);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const float gamma = lv_lf_gamma(t, p);
+  cudaMemsetAsync(w.wsum, 0, sizeof(double) * 2 * LV_MAX_VIEWS, s);
+  k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
+  k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
+  select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
+  for (int v = 0; v < n_views; ++v) {
+    const long long np = vp.off[v + 1] - vp.off[v];
+    k_lf_weight<<<(unsigned)((np + TPB - 1) / TPB), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum);
+  }
+  for (int v = 0; v < n_views; ++v) {
+    const long long np = vp.off[v + 1] - vp.off[v];
+    k_lf_loss<<<(unsigned)((np + TPB - 1) / TPB), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
+  }
+  k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
+  count_launch(3 + 2 * n_views);
+  return cuda_check(cudaGetLastError(), "lv_lf_weighted_loss");
+}

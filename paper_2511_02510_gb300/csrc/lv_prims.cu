@@ -1,0 +1,390 @@
+// lv_prims.cu -- scan, radix sort and radix select kernels (sm_103a).
+#include "lv_prims.cuh"
+
+namespace lv {
+
+// ============================================================ two-channel scan
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+
+__device__ __forceinline__ void block_exclusive_scan2(unsigned long long& a, uint32_t& b, unsigned long long* sa,
+                                                      uint32_t* sb, unsigned long long& tot_a, uint32_t& tot_b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long ia = a;
+  uint32_t ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long ta = __shfl_up_sync(FULL, ia, o);
+    uint32_t tb = __shfl_up_sync(FULL, ib, o);
+    if (lane >= o) { ia += ta; ib += tb; }
+  }
+  if (lane == 31) { sa[warp] = ia; sb[warp] = ib; }
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long wa = lane < SCAN_THREADS / 32 ? sa[lane] : 0ull;
+    uint32_t wb = lane < SCAN_THREADS / 32 ? sb[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long ta = __shfl_up_sync(FULL, wa, o);
+      uint32_t tb = __shfl_up_sync(FULL, wb, o);
+      if (lane >= o) { wa += ta; wb += tb; }
+    }
+    if (lane < SCAN_THREADS / 32) { sa[lane] = wa; sb[lane] = wb; }
+  }
+  __syncthreads();
+  tot_a = sa[SCAN_THREADS / 32 - 1];
+  tot_b = sb[SCAN_THREADS / 32 - 1];
+  unsigned long long pa = warp ? sa[warp - 1] : 0ull;
+  uint32_t pb = warp ? sb[warp - 1] : 0u;
+  a = pa + ia - a;
+  b = pb + ib - b;
+  __syncthreads();
+}
+
+__global__ void k_scan2_reduce(const uint32_t* a, const uint32_t* b, int64_t n, int64_t chunk,
+                               unsigned long long* bsa, uint32_t* bsb) {
+  __shared__ unsigned long long sa[32];
+  __shared__ uint32_t sb[32];
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  unsigned long long ta = 0;
+  uint32_t tb = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += SCAN_THREADS) {
+    ta += a[i];
+    tb += b[i];
+  }
+  unsigned long long xa = ta, tot_a;
+  uint32_t xb = tb, tot_b;
+  block_exclusive_scan2(xa, xb, sa, sb, tot_a, tot_b);
+  if (threadIdx.x == 0) { bsa[blockIdx.x] = tot_a; bsb[blockIdx.x] = tot_b; }
+}
+
+__global__ void k_scan2_blocks(unsigned long long* bsa, uint32_t* bsb, int nb, unsigned long long* totals) {
+  __shared__ unsigned long long sa[32];
+  __shared__ uint32_t sb[32];
+  // nb <= SCAN_BLOCKS = 2 * SCAN_THREADS: two items per thread
+  int i0 = threadIdx.x * 2;
+  unsigned long long a0 = i0 < nb ? bsa[i0] : 0, a1 = i0 + 1 < nb ? bsa[i0 + 1] : 0;
+  uint32_t b0 = i0 < nb ? bsb[i0] : 0, b1 = i0 + 1 < nb ? bsb[i0 + 1] : 0;
+  unsigned long long xa = a0 + a1, ta;
+  uint32_t xb = b0 + b1, tb;
+  block_exclusive_scan2(xa, xb, sa, sb, ta, tb);
+  if (i0 < nb) { bsa[i0] = xa; bsb[i0] = xb; }
+  if (i0 + 1 < nb) { bsa[i0 + 1] = xa + a0; bsb[i0 + 1] = xb + b0; }
+  if (threadIdx.x == 0) { totals[0] = ta; totals[1] = tb; }
+}
+
+__global__ void k_scan2_apply(const uint32_t* a, const uint32_t* b, int64_t n, int64_t chunk,
+                              const unsigned long long* bsa, const uint32_t* bsb, unsigned long long* out_a,
+                              uint32_t* out_b) {
+  __shared__ unsigned long long sa[32];
+  __shared__ uint32_t sb[32];
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  unsigned long long carry_a = bsa[blockIdx.x];
+  uint32_t carry_b = bsb[blockIdx.x];
+  for (int64_t base = lo; base < hi; base += SCAN_THREADS) {
+    int64_t i = base + threadIdx.x;
+    unsigned long long va = i < hi ? a[i] : 0;
+    uint32_t vb = i < hi ? b[i] : 0;
+    unsigned long long xa = va, ta;
+    uint32_t xb = vb, tb;
+    block_exclusive_scan2(xa, xb, sa, sb, ta, tb);
+    if (i < hi) { out_a[i] = carry_a + xa; out_b[i] = carry_b + xb; }
+    carry_a += ta;
+    carry_b += tb;
+  }
+}
+
+}  // namespace
+
+size_t scan2_tmp_bytes() { return SCAN_BLOCKS * (sizeof(unsigned long long) + sizeof(uint32_t)) + 256; }
+
+void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* out_a, uint32_t* out_b,
+           unsigned long long* totals, void* tmp, cudaStream_t s) {
+  unsigned long long* bsa = (unsigned long long*)tmp;
+  uint32_t* bsb = (uint32_t*)(bsa + SCAN_BLOCKS);
+  int64_t chunk = (n + SCAN_BLOCKS - 1) / SCAN_BLOCKS;
+  if (chunk < 1) chunk = 1;
+  k_scan2_reduce<<<SCAN_BLOCKS, SCAN_THREADS, 0, s>>>(a, b, n, chunk, bsa, bsb);
+  k_scan2_blocks<<<1, SCAN_THREADS, 0, s>>>(bsa, bsb, SCAN_BLOCKS, totals);
+  k_scan2_apply<<<SCAN_BLOCKS, SCAN_THREADS, 0, s>>>(a, b, n, chunk, bsa, bsb, out_a, out_b);
+  count_launch(3);
+}
+
+// ============================================================ radix sort
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;                       // per lane per sub-tile
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2048 items
+constexpr int RADIX = 256;
+
+// On overflow (more pairs than capacity) the list is treated as empty: the
+// emit step then left holes in the buffers, and the caller's status word
+// carries LV_ERR_CAPACITY.
+__device__ __forceinline__ int64_t rs_count(const unsigned long long* d_count, int64_t cap) {
+  unsigned long long c = *d_count;
+  return c <= (unsigned long long)cap ? (int64_t)c : 0;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t* keys, const unsigned long long* d_count,
+                                                          int64_t cap, int shift, uint32_t* hist) {
+  __shared__ uint32_t sh[RS_WARPS][RADIX];
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  int64_t n = rs_count(d_count, cap);
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
+    uint32_t d = (uint32_t)(keys[i] >> shift) & (RADIX - 1);
+    atomicAdd(&sh[warp][d], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) t += sh[w][d];
+    hist[d * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// exclusive scan in place over RADIX * blocks counters (digit-major)
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* hist, int total) {
+  __shared__ uint32_t sw[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int per = (total + 1023) / 1024;
+  int lo = t * per, hi = min(total, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += hist[i];
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = sw[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, w, o);
+      if (lane >= o) w += y;
+    }
+    sw[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? sw[warp - 1] : 0u) + x - s;
+  for (int i = lo; i < hi; ++i) {
+    uint32_t c = hist[i];
+    hist[i] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin, const uint32_t* vin,
+                                                            uint64_t* kout, uint32_t* vout,
+                                                            const unsigned long long* d_count, int64_t cap,
+                                                            int shift, const uint32_t* hist) {
+  __shared__ uint32_t s_goff[RADIX];          // next global slot per digit for this block
+  __shared__ uint32_t s_wh[RS_WARPS][RADIX];  // per-warp digit counts -> warp prefixes
+  __shared__ uint32_t s_cnt[RADIX];           // sub-tile digit counts
+  __shared__ uint32_t s_start[RADIX];         // sub-tile digit start offsets
+  __shared__ uint64_t s_k[RS_TILE];
+  __shared__ uint32_t s_v[RS_TILE];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int d = t; d < RADIX; d += RS_THREADS) s_goff[d] = hist[d * gridDim.x + blockIdx.x];
+  int64_t n = rs_count(d_count, cap);
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (int64_t base = lo; base < hi; base += RS_TILE) {
+    for (int i = t; i < RS_WARPS * RADIX; i += RS_THREADS) (&s_wh[0][0])[i] = 0;
+    __syncthreads();
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
+    const int64_t wbase = base + (int64_t)warp * (32 * RS_ITEMS);
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      int64_t i = wbase + j * 32 + lane;
+      bool ok = i < hi;
+      k[j] = ok ? kin[i] : 0ull;
+      v[j] = ok ? vin[i] : 0u;
+      dg[j] = ok ? ((uint32_t)(k[j] >> shift) & (RADIX - 1)) : RADIX;
+    }
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      uint32_t peers = __match_any_sync(FULL, dg[j]);
+      uint32_t before = __popc(peers & lt_mask);
+      uint32_t cur = dg[j] < RADIX ? s_wh[warp][dg[j]] : 0u;
+      rk[j] = cur + before;
+      __syncwarp();
+      if (dg[j] < RADIX && before == 0) s_wh[warp][dg[j]] = cur + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int d = t; d < RADIX; d += RS_THREADS) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < RS_WARPS; ++w) {
+        uint32_t c = s_wh[w][d];
+        s_wh[w][d] = run;
+        run += c;
+      }
+      s_cnt[d] = run;
+    }
+    __syncthreads();
+    // exclusive scan of s_cnt over the 256 digits (RS_THREADS == RADIX)
+    {
+      uint32_t c = s_cnt[t];
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      __shared__ uint32_t sw[RS_WARPS];
+      if (lane == 31) sw[warp] = x;
+      __syncthreads();
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += sw[w];
+      s_start[t] = pre + x - c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      if (dg[j] < RADIX) {
+        uint32_t pos = s_start[dg[j]] + s_wh[warp][dg[j]] + rk[j];
+        s_k[pos] = k[j];
+        s_v[pos] = v[j];
+      }
+    }
+    __syncthreads();
+    int m = (int)min((int64_t)RS_TILE, hi - base);
+    for (int q = t; q < m; q += RS_THREADS) {
+      uint64_t kk = s_k[q];
+      uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
+      uint32_t g = s_goff[d] + (uint32_t)q - s_start[d];
+      kout[g] = kk;
+      vout[g] = s_v[q];
+    }
+    __syncthreads();
+    for (int d = t; d < RADIX; d += RS_THREADS) s_goff[d] += s_cnt[d];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t sort_hist_bytes() { return sizeof(uint32_t) * RADIX * SORT_BLOCKS; }
+int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
+
+int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t* hist,
+                     const unsigned long long* d_count, int64_t cap, int end_bit, cudaStream_t s) {
+  int passes = sort_passes(end_bit);
+  uint64_t* kb[2] = {k0, k1};
+  uint32_t* vb[2] = {v0, v1};
+  for (int p = 0; p < passes; ++p) {
+    int src = p & 1, dst = src ^ 1;
+    k_rs_upsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], d_count, cap, 8 * p, hist);
+    k_rs_scan<<<1, 1024, 0, s>>>(hist, RADIX * SORT_BLOCKS);
+    k_rs_downsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_count, cap, 8 * p,
+                                                      hist);
+  }
+  count_launch(3 * passes);
+  return passes & 1;
+}
+
+// ============================================================ grouped select
+namespace {
+
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_BLOCKS = 304;
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, const uint16_t* grp, int64_t n,
+                                                         const SelectQuery* q, int nq, int shift, uint32_t* hist) {
+  extern __shared__ uint32_t sh[];  // nq * 256
+  __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
+  for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS) sh[i] = 0;
+  for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
+  __syncthreads();
+  const uint32_t hi_mask = shift >= 24 ? 0u : (0xffffffffu << (shift + 8));
+  for (int64_t i = blockIdx.x * (int64_t)SEL_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SEL_THREADS) {
+    uint32_t g = grp[i];
+    if (g == GROUP_NONE) continue;
+    uint32_t key = keys ? keys[i] : (uint32_t)i;
+    uint32_t d = (key >> shift) & 255u;
+    for (int j = 0; j < nq; ++j) {
+      if (sq[j].group != g || sq[j].k == 0) continue;
+      if ((key & hi_mask) != sq[j].prefix) continue;
+      atomicAdd(&sh[j * 256 + d], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
+  int j = threadIdx.x;
+  if (j < nq) {
+    SelectQuery s = q[j];
+    if (s.k != 0) {
+      uint32_t cum = 0;
+      int found = -1;
+      for (int d = 0; d < 256; ++d) {
+        uint32_t c = hist[j * 256 + d];
+        if (cum + c >= s.k) { found = d; break; }
+        cum += c;
+      }
+      if (found < 0) {
+        s.k = 0;
+        s.result = 0xffffffffu;
+      } else {
+        s.k -= cum;
+        s.prefix |= (uint32_t)found << shift;
+        if (shift == 0) s.result = s.prefix;
+      }
+    } else {
+      s.result = 0xffffffffu;
+    }
+    q[j] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nq * 256; i += blockDim.x) hist[i] = 0;
+}
+
+__global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist) {
+  int j = threadIdx.x;
+  if (j < nq) { q[j].prefix = 0; q[j].result = 0xffffffffu; }
+  for (int i = threadIdx.x; i < nq * 256; i += blockDim.x) hist[i] = 0;
+}
+
+}  // namespace
+
+size_t select_tmp_bytes(int n_queries) { return sizeof(uint32_t) * 256 * (size_t)n_queries + 256; }
+
+void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                void* tmp, cudaStream_t s) {
+  uint32_t* hist = (uint32_t*)tmp;
+  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist);
+  int64_t want = (n + SEL_THREADS - 1) / SEL_THREADS;
+  int blocks = (int)(want < SEL_BLOCKS ? want : SEL_BLOCKS);
+  if (blocks < 1) blocks = 1;
+  size_t smem = sizeof(uint32_t) * 256 * n_queries;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sel_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint32_t) * 256 * SELECT_MAX_QUERIES));
+    attr_set = true;
+  }
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    k_sel_hist<<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, d_queries, n_queries, shift, hist);
+    k_sel_pick<<<1, 256, 0, s>>>(d_queries, n_queries, shift, hist);
+  }
+  count_launch(1 + 8);
+}
+
+}  // namespace lv

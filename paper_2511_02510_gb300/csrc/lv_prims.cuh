@@ -1,0 +1,47 @@
+// lv_prims.cuh -- device primitives: two-channel exclusive scan, LSD radix sort
+// of (u64 key, u32 value) pairs, grouped radix select.  No CUB: every kernel
+// here is written for this library (reduce-then-scan, no inter-block waits).
+#pragma once
+
+#include "lv_common.cuh"
+
+namespace lv {
+
+// ---------------------------------------------------------------- scan
+// out_a[i] = sum_{j<i} a[j] (64-bit), out_b[i] = sum_{j<i} b[j] (32-bit);
+// totals[0] = sum a, totals[1] = sum b.  n is known on the host.
+constexpr int SCAN_BLOCKS = 512;
+size_t scan2_tmp_bytes();
+void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* out_a, uint32_t* out_b,
+           unsigned long long* totals, void* tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD sort of the first *d_count pairs on bits [0, end_bit); nothing is
+// sorted when *d_count > cap (an overflowed emit leaves holes).
+// Returns 0 when the result is in (k0, v0) and 1 when it is in (k1, v1).
+constexpr int SORT_BLOCKS = 512;
+size_t sort_hist_bytes();
+int sort_passes(int end_bit);
+int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t* hist,
+                     const unsigned long long* d_count, int64_t cap, int end_bit, cudaStream_t s);
+
+// ---------------------------------------------------------------- grouped select
+// For each query q (group g_q, 1-based rank k_q), find the k-th smallest
+// 32-bit key among the items i with grp[i] == g_q (0xffff = excluded).
+// Queries live in device memory so that k can be computed on the device.
+// After select_kth, queries[q].result holds the key, or 0xffffffff when
+// k == 0 or the group has fewer than k items (queries[q].k is then 0).
+// keys == nullptr ranks the items by their index (key = i).
+constexpr int SELECT_MAX_QUERIES = 64;
+constexpr uint16_t GROUP_NONE = 0xffff;
+struct SelectQuery {
+  uint32_t group;
+  uint32_t k;
+  uint32_t prefix;
+  uint32_t result;
+};
+size_t select_tmp_bytes(int n_queries);
+void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                void* tmp, cudaStream_t s);
+
+}  // namespace lv

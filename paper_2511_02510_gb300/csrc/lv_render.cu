@@ -1,0 +1,926 @@
+// lv_render.cu -- forward / backward passes of the sparse-voxel tile
+// rasterizer (LiteVoxel Sec. III, Eq. 1-5) for sm_103a.
+//
+// Pipeline of lv_rasterize_forward (one stream, no host synchronisation):
+//   k_bin       per (voxel, view): FP32 cull / corner projection / tile rect /
+//               depth key with a fixed operation order; depth statistics.
+//   scan2       pair offsets and visible-slot ids (two-channel scan).
+//   k_emit      per visible (voxel, view): 64-byte render record (centre
+//               relative to the camera, half-size, 8 corner densities, SH
+//               colour, voxel id) and its (tile << 32 | depth key, slot) pairs.
+//   radix sort  CUB-free LSD sort of the pairs on (tile bits + 32) bits.
+//   k_ranges    [start, end) of every tile in the sorted list.
+//   k_fwd       per tile: records staged through shared memory in batches,
+//               one thread per pixel marching front to back (Eq. 2-4), w_max
+//               (Eq. 5) reduced per warp then per block before one global
+//               atomicMax per (tile, voxel), warp / block early exit at T < t_stop.
+// lv_rasterize_backward walks the same lists back to front (k_bwd) and
+// reduces the SH colour gradient per voxel (k_sh_bwd).
+#include <math.h>
+#include <stdio.h>
+
+#include "lv_prims.cuh"
+
+namespace lv {
+
+// ------------------------------------------------------------------ views
+struct DevView {
+  float R[9];  // w2c rotation, row-major
+  float t[3];
+  float o[3];  // camera centre in world coordinates
+  float fx, fy, cx, cy, z_near;
+  int W, H, tiles_x, tiles_y;
+  int tile_off;       // first global tile of the view
+  long long pix_off;  // first global pixel of the view
+};
+struct ViewSet {
+  int n;
+  int ts;
+  DevView v[LV_MAX_VIEWS];
+};
+
+static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64_t* tiles, int64_t* pixels) {
+  vs->n = nv;
+  vs->ts = ts;
+  int64_t to = 0, po = 0;
+  for (int i = 0; i < nv; ++i) {
+    const lv_camera& c = cams[i];
+    DevView& d = vs->v[i];
+    for (int r = 0; r < 3; ++r) {
+      for (int k = 0; k < 3; ++k) d.R[r * 3 + k] = c.w2c[r * 4 + k];
+      d.t[r] = c.w2c[r * 4 + 3];
+    }
+    for (int k = 0; k < 3; ++k) {
+      double s = 0;
+      for (int r = 0; r < 3; ++r) s += (double)c.w2c[r * 4 + k] * (double)c.w2c[r * 4 + 3];
+      d.o[k] = (float)(-s);
+    }
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy; d.z_near = c.z_near;
+    d.W = c.width; d.H = c.height;
+    d.tiles_x = (c.width + ts - 1) / ts;
+    d.tiles_y = (c.height + ts - 1) / ts;
+    d.tile_off = (int)to;
+    d.pix_off = po;
+    to += (int64_t)d.tiles_x * d.tiles_y;
+    po += (int64_t)c.width * c.height;
+  }
+  *tiles = to;
+  *pixels = po;
+}
+
+// ------------------------------------------------------------------ workspace
+struct FwdWs {
+  unsigned long long* counters;  // [0] pairs, [1] slots
+  uint32_t* cnt;                 // [items] tiles covered
+  uint32_t* vis;                 // [items] 1 if cnt > 0
+  uint2* rect;                   // [items] (tx0 | tx1 << 16, ty0 | ty1 << 16)
+  uint32_t* dkey;                // [items] order key of z_centre
+  unsigned long long* pair_off;  // [items]
+  uint32_t* slot;                // [items]
+  void* scan_tmp;
+  float4* rec;                   // [slots][4]
+  float* d_rgb;                  // [slots][3] backward scratch
+  uint32_t* ranges;              // [tiles][2]
+  float* tau;                    // [pixels] final optical depth
+  uint32_t* hist;
+  int32_t* status;               // fallback status word
+  uint64_t* k0;
+  uint32_t* v0;
+  uint64_t* k1;
+  uint32_t* v1;
+  size_t bytes;
+};
+
+static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pixels, int64_t pair_cap) {
+  FwdWs w;
+  Carve c(base);
+  int64_t items = n * nv;
+  w.counters = c.take<unsigned long long>(8);
+  w.status = c.take<int32_t>(4);
+  w.cnt = c.take<uint32_t>(items);
+  w.vis = c.take<uint32_t>(items);
+  w.rect = c.take<uint2>(items);
+  w.dkey = c.take<uint32_t>(items);
+  w.pair_off = c.take<unsigned long long>(items);
+  w.slot = c.take<uint32_t>(items);
+  w.scan_tmp = c.take<char>(scan2_tmp_bytes());
+  w.rec = c.take<float4>(items * 4);
+  w.d_rgb = c.take<float>(items * 3);
+  w.ranges = c.take<uint32_t>(tiles * 2);
+  w.tau = c.take<float>(pixels);
+  w.hist = c.take<uint32_t>(sort_hist_bytes() / 4);
+  w.k0 = c.take<uint64_t>(pair_cap);
+  w.v0 = c.take<uint32_t>(pair_cap);
+  w.k1 = c.take<uint64_t>(pair_cap);
+  w.v1 = c.take<uint32_t>(pair_cap);
+  w.bytes = c.off + 256;
+  return w;
+}
+
+static int tile_bits(int64_t tiles) {
+  int b = 0;
+  while (b < 32 && ((int64_t)1 << b) < tiles) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------------ binning (FP32, fixed op order)
+__device__ __forceinline__ void cam_point32(const DevView& c, float X, float Y, float Z, float* q) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float a = __fmul_rn(c.R[r * 3 + 0], X);
+    float b = __fmul_rn(c.R[r * 3 + 1], Y);
+    float e = __fmul_rn(c.R[r * 3 + 2], Z);
+    float s = __fadd_rn(a, b);
+    s = __fadd_rn(s, e);
+    q[r] = __fadd_rn(s, c.t[r]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, int64_t n,
+                                             const __grid_constant__ ViewSet vs, uint32_t* cnt, uint32_t* vis,
+                                             uint2* rect, uint32_t* dkey, float* z_min, float* delta_min,
+                                             uint8_t* seen) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * vs.n) return;
+  int64_t vox = i / vs.n;
+  int view = (int)(i - vox * vs.n);
+  const DevView& c = vs.v[view];
+  const int ts = vs.ts;
+  float4 g = geom[vox];
+  float qc[3];
+  cam_point32(c, g.x, g.y, g.z, qc);
+  int n_front = 0, n_behind = 0;
+  float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
+  bool first = true;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float X = (k & 1) ? __fadd_rn(g.x, g.w) : __fsub_rn(g.x, g.w);
+    float Y = (k & 2) ? __fadd_rn(g.y, g.w) : __fsub_rn(g.y, g.w);
+    float Z = (k & 4) ? __fadd_rn(g.z, g.w) : __fsub_rn(g.z, g.w);
+    float p[3];
+    cam_point32(c, X, Y, Z, p);
+    if (p[2] < c.z_near) {
+      ++n_behind;
+    } else {
+      ++n_front;
+      float u = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(p[0], p[2])), c.cx);
+      float v = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(p[1], p[2])), c.cy);
+      if (first) { umin = umax = u; vmin = vmax = v; first = false; }
+      else { umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v); }
+    }
+  }
+  int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+  if (n_front > 0) {
+    if (n_behind > 0) {
+      tx1 = c.tiles_x;
+      ty1 = c.tiles_y;
+    } else {
+      float fts = (float)ts;
+      float a0 = floorf(__fdiv_rn(__fsub_rn(umin, 1.0f), fts));
+      float a1 = ceilf(__fdiv_rn(__fadd_rn(umax, 1.0f), fts));
+      float b0 = floorf(__fdiv_rn(__fsub_rn(vmin, 1.0f), fts));
+      float b1 = ceilf(__fdiv_rn(__fadd_rn(vmax, 1.0f), fts));
+      tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)c.tiles_x);
+      tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)c.tiles_x);
+      ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)c.tiles_y);
+      ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)c.tiles_y);
+    }
+  }
+  uint32_t count = (tx1 > tx0 && ty1 > ty0) ? (uint32_t)(tx1 - tx0) * (uint32_t)(ty1 - ty0) : 0u;
+  cnt[i] = count;
+  vis[i] = count ? 1u : 0u;
+  rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+  dkey[i] = order_key(qc[2]);
+  if (count) {
+    float zs = fmaxf(qc[2], c.z_near);
+    float dl = __fdiv_rn(zs, c.fx);
+    if (z_min) atomicMin((unsigned int*)&z_min[vox], __float_as_uint(zs));
+    if (delta_min) atomicMin((unsigned int*)&delta_min[vox], __float_as_uint(dl));
+    if (seen) seen[vox] = 1;
+  }
+}
+
+// ------------------------------------------------------------------ SH (real, degree <= 3)
+// Orthonormal real spherical harmonics written from the associated Legendre
+// functions: Y0 = 1/(2 sqrt(pi)); l=1 sqrt(3/4pi) {y, z, x}; l=2 sqrt(15/4pi)
+// {xy, yz, xz}, sqrt(5/16pi)(3z^2-1), sqrt(15/16pi)(x^2-y^2); l=3
+// sqrt(35/32pi) y(3x^2-y^2), sqrt(105/4pi) xyz, sqrt(21/32pi) y(5z^2-1),
+// sqrt(7/16pi) z(5z^2-3), sqrt(21/32pi) x(5z^2-1), sqrt(105/16pi) z(x^2-y^2),
+// sqrt(35/32pi) x(x^2-3y^2).
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+  const float C0 = 0.28209479177387814f;
+  const float C1 = 0.48860251190291992f;
+  const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.54627421529603959f;
+  const float C3a = 0.59004358992664352f, C3b = 2.8906114426405538f, C3c = 0.45704579946446572f;
+  const float C3d = 0.37317633259011540f, C3e = 1.4453057213202769f;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = C0;
+  Y[1] = C1 * y;
+  Y[2] = C1 * z;
+  Y[3] = C1 * x;
+  Y[4] = C2a * x * y;
+  Y[5] = C2a * y * z;
+  Y[6] = C2b * (3.f * zz - 1.f);
+  Y[7] = C2a * x * z;
+  Y[8] = C2c * (xx - yy);
+  Y[9] = C3a * y * (3.f * xx - yy);
+  Y[10] = C3b * x * y * z;
+  Y[11] = C3c * y * (5.f * zz - 1.f);
+  Y[12] = C3d * z * (5.f * zz - 3.f);
+  Y[13] = C3c * x * (5.f * zz - 1.f);
+  Y[14] = C3e * z * (xx - yy);
+  Y[15] = C3a * x * (xx - 3.f * yy);
+}
+
+template <typename ST>
+__device__ __forceinline__ void sh_raw(const ST* __restrict__ sh, int nb, const float* Y, float* raw) {
+  float r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j < nb) {
+      r = fmaf(to_f32(sh[3 * j + 0]), Y[j], r);
+      g = fmaf(to_f32(sh[3 * j + 1]), Y[j], g);
+      b = fmaf(to_f32(sh[3 * j + 2]), Y[j], b);
+    }
+  }
+  raw[0] = r + 0.5f;
+  raw[1] = g + 0.5f;
+  raw[2] = b + 0.5f;
+}
+
+__device__ __forceinline__ void unit_dir(float rx, float ry, float rz, float* d) {
+  float nn = rx * rx + ry * ry + rz * rz;
+  if (nn > 0.f) {
+    float inv = rsqrtf(nn);
+    d[0] = rx * inv; d[1] = ry * inv; d[2] = rz * inv;
+  } else {
+    d[0] = 0.f; d[1] = 0.f; d[2] = 1.f;
+  }
+}
+
+// ------------------------------------------------------------------ emit
+template <typename DT, typename ST>
+__global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, const DT* __restrict__ dens,
+                                              const ST* __restrict__ sh, int sh_nb, int64_t n,
+                                              const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ cnt,
+                                              const uint32_t* __restrict__ vis, const uint2* __restrict__ rect,
+                                              const uint32_t* __restrict__ dkey,
+                                              const unsigned long long* __restrict__ pair_off,
+                                              const uint32_t* __restrict__ slot, float4* __restrict__ rec,
+                                              float* __restrict__ d_rgb, uint64_t* __restrict__ keys,
+                                              uint32_t* __restrict__ vals,
+                                              int64_t pair_cap, int32_t* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * vs.n) return;
+  if (!vis[i]) return;
+  int64_t vox = i / vs.n;
+  int view = (int)(i - vox * vs.n);
+  const DevView& c = vs.v[view];
+  uint32_t s = slot[i];
+  float4 g = geom[vox];
+  float rx = g.x - c.o[0], ry = g.y - c.o[1], rz = g.z - c.o[2];
+  float dir[3];
+  unit_dir(rx, ry, rz, dir);
+  float Y[16];
+  sh_basis(dir[0], dir[1], dir[2], Y);
+  float raw[3];
+  sh_raw(sh + 48 * vox, sh_nb, Y, raw);
+  float d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * vox + k]);
+  float4* r = rec + 4 * (int64_t)s;
+  r[0] = make_float4(rx, ry, rz, g.w);
+  r[1] = make_float4(d[0], d[1], d[2], d[3]);
+  r[2] = make_float4(d[4], d[5], d[6], d[7]);
+  r[3] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), __uint_as_float((uint32_t)vox));
+  d_rgb[3 * (size_t)s + 0] = 0.f;
+  d_rgb[3 * (size_t)s + 1] = 0.f;
+  d_rgb[3 * (size_t)s + 2] = 0.f;
+  unsigned long long off = pair_off[i];
+  uint32_t count = cnt[i];
+  if (off + count > (unsigned long long)pair_cap) {
+    report(status, LV_ERR_CAPACITY);
+    return;
+  }
+  uint2 rc = rect[i];
+  int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff;
+  int wx = tx1 - tx0;
+  uint32_t dk = dkey[i];
+  for (uint32_t q = 0; q < count; ++q) {
+    int ty = ty0 + (int)(q / (uint32_t)wx), tx = tx0 + (int)(q % (uint32_t)wx);
+    uint64_t gt = (uint64_t)(c.tile_off + ty * c.tiles_x + tx);
+    keys[off + q] = (gt << 32) | dk;
+    vals[off + q] = s;
+  }
+}
+
+// pairs usable by the later stages: all of them, or none after an overflow
+__device__ __forceinline__ int64_t usable_pairs(const unsigned long long* d_count, int64_t cap) {
+  unsigned long long c = *d_count;
+  return c <= (unsigned long long)cap ? (int64_t)c : 0;
+}
+
+__global__ void k_ranges(const uint64_t* __restrict__ keys, const unsigned long long* d_count, int64_t cap,
+                         int64_t tiles, uint32_t* ranges) {
+  const int64_t n = usable_pairs(d_count, cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (t >= tiles) continue;
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
+    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+  }
+}
+
+// ------------------------------------------------------------------ per-pixel ray
+struct Ray {
+  float dx, dy, dz;     // unit direction
+  float ix, iy, iz;     // 1 / direction (1e30 for a zero component)
+  float ax, ay, az;     // |1 / direction|
+};
+
+__device__ __forceinline__ Ray make_ray(const DevView& c, int px, int py) {
+  float dcx = __fdiv_rn((float)px + 0.5f - c.cx, c.fx);
+  float dcy = __fdiv_rn((float)py + 0.5f - c.cy, c.fy);
+  float wx = c.R[0] * dcx + c.R[3] * dcy + c.R[6];
+  float wy = c.R[1] * dcx + c.R[4] * dcy + c.R[7];
+  float wz = c.R[2] * dcx + c.R[5] * dcy + c.R[8];
+  float inv = rsqrtf(wx * wx + wy * wy + wz * wz);
+  Ray r;
+  r.dx = wx * inv; r.dy = wy * inv; r.dz = wz * inv;
+  r.ix = r.dx != 0.f ? __frcp_rn(r.dx) : 1e30f;
+  r.iy = r.dy != 0.f ? __frcp_rn(r.dy) : 1e30f;
+  r.iz = r.dz != 0.f ? __frcp_rn(r.dz) : 1e30f;
+  r.ax = fabsf(r.ix); r.ay = fabsf(r.iy); r.az = fabsf(r.iz);
+  return r;
+}
+
+// Chord of the ray (origin at the camera) through the box centred at rc
+// (relative to the camera) with half-size h.  Identical code in the forward
+// and backward kernels, so both take the same hit decisions.
+__device__ __forceinline__ bool chord(const Ray& r, float4 g, float& t_in, float& t_out) {
+  float qx = g.x * r.ix, qy = g.y * r.iy, qz = g.z * r.iz;
+  float ex = g.w * r.ax, ey = g.w * r.ay, ez = g.w * r.az;
+  t_in = fmaxf(fmaxf(qx - ex, qy - ey), fmaxf(qz - ez, 0.f));
+  t_out = fminf(fminf(qx + ex, qy + ey), qz + ez);
+  return t_out > t_in;
+}
+
+// local coordinates of the chord midpoint in [0,1]^3 and the trilinear density
+__device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, float4 d1, float tm, float* u) {
+  float i2h = __frcp_rn(g.w + g.w);
+  u[0] = __saturatef((fmaf(tm, r.dx, -g.x) + g.w) * i2h);
+  u[1] = __saturatef((fmaf(tm, r.dy, -g.y) + g.w) * i2h);
+  u[2] = __saturatef((fmaf(tm, r.dz, -g.z) + g.w) * i2h);
+  float c00 = fmaf(u[0], d0.y - d0.x, d0.x);
+  float c10 = fmaf(u[0], d0.w - d0.z, d0.z);
+  float c01 = fmaf(u[0], d1.y - d1.x, d1.x);
+  float c11 = fmaf(u[0], d1.w - d1.z, d1.z);
+  float c0 = fmaf(u[1], c10 - c00, c00);
+  float c1 = fmaf(u[1], c11 - c01, c01);
+  return fmaf(u[2], c1 - c0, c0);
+}
+
+// 1 - exp(-x) accurate for small x (Taylor series below 1/8)
+__device__ __forceinline__ float one_minus_exp(float x, float e) {
+  if (x < 0.125f) {
+    float p = fmaf(x, -1.f / 5040.f, 1.f / 720.f);
+    p = fmaf(x, p, -1.f / 120.f);
+    p = fmaf(x, p, 1.f / 24.f);
+    p = fmaf(x, p, -1.f / 6.f);
+    p = fmaf(x, p, 0.5f);
+    p = fmaf(x, p, -1.f);
+    return -x * p;
+  }
+  return 1.f - e;
+}
+
+__device__ __forceinline__ int find_view(const ViewSet& vs, int gtile) {
+  int v = 0;
+  while (v + 1 < vs.n && gtile >= vs.v[v + 1].tile_off) ++v;
+  return v;
+}
+
+// ------------------------------------------------------------------ forward composite
+template <int TS, int B>
+__global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
+                                                const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
+                                                float t_stop, float* __restrict__ rgb, float* __restrict__ depth,
+                                                float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
+                                                float* __restrict__ tau_out, unsigned long long* __restrict__ wmax) {
+  constexpr int NT = TS * TS;
+  __shared__ float4 s_rec[B * 4];
+  __shared__ unsigned long long s_wm[B];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gtile = blockIdx.x;
+  const int view = find_view(vs, gtile);
+  const DevView& c = vs.v[view];
+  const int lt = gtile - c.tile_off;
+  const int px = (lt % c.tiles_x) * TS + tid % TS, py = (lt / c.tiles_x) * TS + tid / TS;
+  const bool inside = px < c.W && py < c.H;
+  const Ray r = make_ray(c, px, py);
+  const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
+  const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
+  const unsigned long long gid_key = 0xffffffffull - (gid & 0xffffffffull);
+  float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
+  uint32_t last = 0;
+  bool done = !inside;
+  for (uint32_t base = start; base < end; base += B) {
+    const int cntb = (int)min((uint32_t)B, end - base);
+    for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[base + (q >> 2)] + (q & 3)];
+    for (int q = tid; q < cntb; q += NT) s_wm[q] = 0ull;
+    __syncthreads();
+    if (!__all_sync(FULL, done)) {
+      for (int j = 0; j < cntb; ++j) {
+        const float4 g = s_rec[4 * j];
+        float t_in, t_out;
+        bool hit = !done && chord(r, g, t_in, t_out);
+        float w = 0.f;
+        if (hit) {
+          const float4 d0 = s_rec[4 * j + 1], d1 = s_rec[4 * j + 2], col = s_rec[4 * j + 3];
+          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+          float u[3];
+          const float sigma = fmaxf(mid_density(r, g, d0, d1, tm, u), 0.f);
+          const float x = sigma * l;
+          const float e = __expf(-x);
+          const float alpha = one_minus_exp(x, e);
+          w = T * alpha;
+          cr = fmaf(w, col.x, cr);
+          cg = fmaf(w, col.y, cg);
+          cb = fmaf(w, col.z, cb);
+          dep = fmaf(w, tm, dep);
+          tau += x;
+          T *= e;
+          last = base + j - start + 1;
+        }
+        if (__any_sync(FULL, hit)) {
+          const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
+          const uint32_t mx = __reduce_max_sync(FULL, v);
+          const uint32_t who = __ballot_sync(FULL, v == mx);
+          if (lane == __ffs(who) - 1)
+            atomicMax(&s_wm[j], ((unsigned long long)(mx - 1u) << 32) | gid_key);
+        }
+        if (hit && T < t_stop) done = true;
+      }
+    }
+    __syncthreads();
+    if (wmax) {
+      for (int q = tid; q < cntb; q += NT) {
+        unsigned long long m = s_wm[q];
+        if (m) atomicMax(&wmax[__float_as_uint(s_rec[4 * q + 3].w)], m);
+      }
+    }
+    if (__syncthreads_count(!done) == 0) break;
+  }
+  if (inside) {
+    const size_t p = (size_t)gid;
+    rgb[3 * p + 0] = cr;
+    rgb[3 * p + 1] = cg;
+    rgb[3 * p + 2] = cb;
+    if (depth) depth[p] = dep;
+    T_out[p] = T;
+    n_contrib[p] = last;
+    tau_out[p] = tau;
+  }
+}
+
+// ------------------------------------------------------------------ backward composite
+// Transposed butterfly: after 16 shuffles even lane l holds the warp sum of
+// value (l >> 1) of the 16 inputs (instead of 16 * 5 shuffles).
+__device__ __forceinline__ float warp_reduce16(float* v, int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool up = lane & 16;
+    float send = up ? v[i] : v[i + 8];
+    float keep = up ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool up = lane & 8;
+    float send = up ? v[i] : v[i + 4];
+    float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool up = lane & 4;
+    float send = up ? v[i] : v[i + 2];
+    float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(FULL, send, 4);
+  }
+  {
+    const bool up = lane & 2;
+    float send = up ? v[0] : v[1];
+    float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(FULL, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(FULL, v[0], 1);
+}
+
+template <int TS, int B>
+__global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
+                                                const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
+                                                const float* __restrict__ T_fwd, const float* __restrict__ tau_in,
+                                                const uint32_t* __restrict__ n_contrib,
+                                                const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
+                                                const float* __restrict__ dL_dT, float* __restrict__ d_density,
+                                                float* __restrict__ d_rgb) {
+  constexpr int NT = TS * TS;
+  constexpr int NV = 12;  // 8 corners + 3 colour + 1 flag
+  __shared__ float4 s_rec[B * 4];
+  __shared__ uint32_t s_slot[B];
+  __shared__ float s_acc[B * NV];
+  __shared__ uint32_t s_max;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gtile = blockIdx.x;
+  const int view = find_view(vs, gtile);
+  const DevView& c = vs.v[view];
+  const int lt = gtile - c.tile_off;
+  const int px = (lt % c.tiles_x) * TS + tid % TS, py = (lt / c.tiles_x) * TS + tid / TS;
+  const bool inside = px < c.W && py < c.H;
+  const Ray r = make_ray(c, px, py);
+  const uint32_t start = ranges[2 * gtile];
+  const size_t p = (size_t)(c.pix_off + (long long)py * c.W + px);
+  uint32_t nc = 0;
+  float tau = 0.f, Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gD = 0.f, gT = 0.f;
+  if (inside) {
+    nc = n_contrib[p];
+    tau = tau_in[p];
+    Tf = T_fwd[p];
+    gr = dL_drgb[3 * p + 0];
+    gg = dL_drgb[3 * p + 1];
+    gb = dL_drgb[3 * p + 2];
+    if (dL_ddepth) gD = dL_ddepth[p];
+    if (dL_dT) gT = dL_dT[p];
+  }
+  if (tid == 0) s_max = 0;
+  __syncthreads();
+  {
+    uint32_t m = __reduce_max_sync(FULL, nc);
+    if (lane == 0 && m) atomicMax(&s_max, m);
+  }
+  __syncthreads();
+  const uint32_t top_all = start + s_max;
+  const float tgT = Tf * gT;
+  float S = 0.f;
+  for (uint32_t top = top_all; top > start; top -= min((uint32_t)B, top - start)) {
+    const uint32_t lo = top - min((uint32_t)B, top - start);
+    const int cntb = (int)(top - lo);
+    for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[lo + (q >> 2)] + (q & 3)];
+    for (int q = tid; q < cntb; q += NT) s_slot[q] = svals[lo + q];
+    for (int q = tid; q < cntb * NV; q += NT) s_acc[q] = 0.f;
+    __syncthreads();
+    const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
+    if (__any_sync(FULL, lo < my_hi)) {
+      for (int j = cntb - 1; j >= 0; --j) {
+        const float4 g = s_rec[4 * j];
+        float t_in, t_out;
+        bool hit = (lo + j) < my_hi && chord(r, g, t_in, t_out);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        if (hit) {
+          const float4 d0 = s_rec[4 * j + 1], d1 = s_rec[4 * j + 2], col = s_rec[4 * j + 3];
+          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+          float u[3];
+          const float sraw = mid_density(r, g, d0, d1, tm, u);
+          const float sigma = fmaxf(sraw, 0.f);
+          const float x = sigma * l;
+          const float Tk = __expf(-tau);
+          const float tau_prev = fmaxf(tau - x, 0.f);
+          const float T_prev = __expf(-tau_prev);
+          const float alpha = one_minus_exp(x, __expf(-x));
+          const float w = T_prev * alpha;
+          const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
+          const float ds = l * (Tk * a - S - tgT);
+          S = fmaf(w, a, S);
+          tau = tau_prev;
+          const float dr = sraw > 0.f ? ds : 0.f;
+          const float ux = u[0], uy = u[1], uz = u[2];
+          const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
+          const float a00 = my * mz, a10 = uy * mz, a01 = my * uz, a11 = uy * uz;
+          v[0] = dr * mx * a00;
+          v[1] = dr * ux * a00;
+          v[2] = dr * mx * a10;
+          v[3] = dr * ux * a10;
+          v[4] = dr * mx * a01;
+          v[5] = dr * ux * a01;
+          v[6] = dr * mx * a11;
+          v[7] = dr * ux * a11;
+          v[8] = w * gr;
+          v[9] = w * gg;
+          v[10] = w * gb;
+          v[11] = 1.f;
+        }
+        if (__any_sync(FULL, hit)) {
+          const float sum = warp_reduce16(v, lane);
+          const int idx = lane >> 1;
+          if (!(lane & 1) && idx < NV) atomicAdd(&s_acc[j * NV + idx], sum);
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < cntb; q += NT) {
+      const float* a = &s_acc[q * NV];
+      if (a[11] == 0.f) continue;
+      const uint32_t vox = __float_as_uint(s_rec[4 * q + 3].w);
+      float* dd = d_density + 8 * (size_t)vox;
+      red_add_v4(dd, a[0], a[1], a[2], a[3]);
+      red_add_v4(dd + 4, a[4], a[5], a[6], a[7]);
+      float* dc = d_rgb + 3 * (size_t)s_slot[q];
+      red_add(dc + 0, a[8]);
+      red_add(dc + 1, a[9]);
+      red_add(dc + 2, a[10]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ SH backward
+template <typename ST>
+__global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, const ST* __restrict__ sh, int sh_nb,
+                                                int64_t n, const __grid_constant__ ViewSet vs,
+                                                const uint32_t* __restrict__ vis, const uint32_t* __restrict__ slot,
+                                                float* __restrict__ d_rgb, float* __restrict__ d_sh,
+                                                int accumulate) {
+  int64_t vox = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (vox >= n) return;
+  float acc[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) acc[k] = 0.f;
+  const float4 g = geom[vox];
+  bool any = false;
+  for (int view = 0; view < vs.n; ++view) {
+    const int64_t i = vox * vs.n + view;
+    if (!vis[i]) continue;
+    const DevView& c = vs.v[view];
+    const uint32_t s = slot[i];
+    float dir[3];
+    unit_dir(g.x - c.o[0], g.y - c.o[1], g.z - c.o[2], dir);
+    float Y[16];
+    sh_basis(dir[0], dir[1], dir[2], Y);
+    float raw[3];
+    sh_raw(sh + 48 * vox, sh_nb, Y, raw);
+    float* dc = d_rgb + 3 * (size_t)s;
+    const float dr = raw[0] > 0.f ? dc[0] : 0.f;
+    const float dg = raw[1] > 0.f ? dc[1] : 0.f;
+    const float db = raw[2] > 0.f ? dc[2] : 0.f;
+    dc[0] = 0.f;  // leave the scratch cleared for the next backward call
+    dc[1] = 0.f;
+    dc[2] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j < sh_nb) {
+        acc[3 * j + 0] = fmaf(Y[j], dr, acc[3 * j + 0]);
+        acc[3 * j + 1] = fmaf(Y[j], dg, acc[3 * j + 1]);
+        acc[3 * j + 2] = fmaf(Y[j], db, acc[3 * j + 2]);
+      }
+    }
+    any = true;
+  }
+  float4* out = (float4*)(d_sh + 48 * vox);
+  if (accumulate) {
+    if (!any) return;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float4 o = out[k];
+      o.x += acc[4 * k]; o.y += acc[4 * k + 1]; o.z += acc[4 * k + 2]; o.w += acc[4 * k + 3];
+      out[k] = o;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+  }
+}
+
+__global__ void k_unpack_wmax(const unsigned long long* __restrict__ packed, int64_t n, float* __restrict__ w,
+                              int64_t* __restrict__ arg) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long v = packed[i];
+  if (v == 0ull) {
+    w[i] = 0.f;
+    if (arg) arg[i] = -1;
+  } else {
+    w[i] = __uint_as_float((uint32_t)(v >> 32));
+    if (arg) arg[i] = (int64_t)(0xffffffffull - (v & 0xffffffffull));
+  }
+}
+
+__global__ void k_debug_pairs(const uint64_t* __restrict__ k, const uint32_t* __restrict__ v,
+                              const float4* __restrict__ rec, const unsigned long long* d_count, int64_t cap,
+                              uint64_t* ko, uint32_t* vo) {
+  const int64_t n = usable_pairs(d_count, cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (ko) ko[i] = k[i];
+    if (vo) vo[i] = __float_as_uint(rec[4 * (size_t)v[i] + 3].w);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int nv, const lv_raster_opts* o) {
+  if (!vox || !cams || !o) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (nv < 1 || nv > LV_MAX_VIEWS) { set_error("n_views %d outside [1, %d]", nv, LV_MAX_VIEWS); return LV_ERR_INVALID_ARG; }
+  if (vox->n < 0 || vox->n > 0x7fffffffLL) { set_error("voxel count %lld out of range", (long long)vox->n); return LV_ERR_INVALID_ARG; }
+  if (vox->n > 0 && (!vox->geom || !vox->density || !vox->sh)) { set_error("null voxel array"); return LV_ERR_INVALID_ARG; }
+  if (vox->density_dtype != LV_F32 && vox->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
+  if (vox->sh_dtype != LV_F32 && vox->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
+  if (vox->sh_degree < 0 || vox->sh_degree > 3) { set_error("sh_degree must be 0..3"); return LV_ERR_INVALID_ARG; }
+  if (o->tile != 8 && o->tile != 16 && o->tile != 32) { set_error("tile must be 8, 16 or 32"); return LV_ERR_INVALID_ARG; }
+  if (o->batch != 64 && o->batch != 128 && o->batch != 256) { set_error("batch must be 64, 128 or 256"); return LV_ERR_INVALID_ARG; }
+  if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) { set_error("t_stop must be in [0, 1)"); return LV_ERR_INVALID_ARG; }
+  int64_t tiles = 0, pixels = 0;
+  for (int i = 0; i < nv; ++i) {
+    const lv_camera& c = cams[i];
+    if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768) { set_error("view %d: bad size", i); return LV_ERR_INVALID_ARG; }
+    if (!(c.fx > 0.f && c.fy > 0.f && c.z_near > 0.f)) { set_error("view %d: fx, fy, z_near must be > 0", i); return LV_ERR_INVALID_ARG; }
+    tiles += (int64_t)((c.width + o->tile - 1) / o->tile) * ((c.height + o->tile - 1) / o->tile);
+    pixels += (int64_t)c.width * c.height;
+  }
+  if (tiles > 0x7fffffffLL || pixels > 0xfffffffeLL) { set_error("too many tiles or pixels"); return LV_ERR_INVALID_ARG; }
+  if (vox->n * nv > 0x7fffffffLL) { set_error("voxels x views exceeds 2^31"); return LV_ERR_INVALID_ARG; }
+  return LV_OK;
+}
+
+static lv_status finish(lv_status st, uint32_t flags, int32_t* d_status, cudaStream_t s, const char* what) {
+  if (st != LV_OK) return st;
+  lv_status e = cuda_check(cudaGetLastError(), what);
+  if (e != LV_OK) return e;
+  if (flags & LV_FLAG_SYNC_CHECK) {
+    e = cuda_check(cudaStreamSynchronize(s), what);
+    if (e != LV_OK) return e;
+    int32_t h = 0;
+    e = cuda_check(cudaMemcpy(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost), "status readback");
+    if (e != LV_OK) return e;
+    if (h != 0) { set_error("%s: device reported status %d", what, h); return (lv_status)h; }
+  }
+  return LV_OK;
+}
+
+template <int TS>
+static void launch_fwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+                       float t_stop, const lv_fwd_out* out) {
+  dim3 grid((unsigned)tiles), block(TS * TS);
+#define LV_FWD(BB) k_fwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, t_stop, out->rgb, out->depth, out->T, \
+                                                       out->n_contrib, w.tau, out->wmax_packed)
+  if (B == 64) LV_FWD(64);
+  else if (B == 128) LV_FWD(128);
+  else LV_FWD(256);
+#undef LV_FWD
+}
+
+template <int TS>
+static void launch_bwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+                       const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
+  dim3 grid((unsigned)tiles), block(TS * TS);
+#define LV_BWD(BB) k_bwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, fwd->T, w.tau, fwd->n_contrib, gC, gD, \
+                                                       gT, dd, w.d_rgb)
+  if (B == 64) LV_BWD(64);
+  else if (B == 128) LV_BWD(128);
+  else LV_BWD(256);
+#undef LV_BWD
+}
+
+}  // namespace lv
+
+using namespace lv;
+
+extern "C" size_t lv_forward_workspace_size(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                                            int64_t pair_capacity) {
+  if (!cams || !opts || n_views < 1 || n_views > LV_MAX_VIEWS || n < 0 || pair_capacity < 0) return 0;
+  ViewSet vs;
+  int64_t tiles, pixels;
+  int ts = opts->tile == 8 || opts->tile == 32 ? opts->tile : 16;
+  make_views(cams, n_views, ts, &vs, &tiles, &pixels);
+  return carve_fwd(nullptr, n, n_views, tiles, pixels, pair_capacity).bytes;
+}
+
+extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera* cams, int n_views,
+                                          const lv_raster_opts* opts, const lv_fwd_out* out, void* workspace,
+                                          size_t ws_bytes, int64_t pair_capacity, int32_t* d_status, void* stream) {
+  lv_status st = check_common(vox, cams, n_views, opts);
+  if (st != LV_OK) return st;
+  if (!out || !out->rgb || !out->T || !out->n_contrib) { set_error("rgb, T and n_contrib outputs are required"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  if (pair_capacity < 0 || pair_capacity > 0xffffffffLL) { set_error("pair_capacity out of range"); return LV_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  ViewSet vs;
+  int64_t tiles, pixels;
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
+  FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  if (!d_status) d_status = w.status;
+  const int64_t n = vox->n, items = n * n_views;
+  cudaMemsetAsync(w.counters, 0, 8 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(w.ranges, 0, sizeof(uint32_t) * 2 * tiles, s);
+  if (!d_status || d_status == w.status) cudaMemsetAsync(w.status, 0, sizeof(int32_t), s);
+  if (items > 0) {
+    int blocks = (int)((items + 255) / 256);
+    k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.dkey, out->z_min,
+                                 out->delta_min, out->seen);
+    scan2(w.cnt, w.vis, items, w.pair_off, w.slot, w.counters, w.scan_tmp, s);
+    const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
+#define LV_EMIT(DT, ST)                                                                                               \
+  k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
+                                        vs, w.cnt, w.vis, w.rect, w.dkey, w.pair_off, w.slot, w.rec, w.d_rgb, w.k0,   \
+                                        w.v0, pair_capacity, d_status)
+    if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
+    else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
+    else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
+    else LV_EMIT(__half, __nv_bfloat16);
+#undef LV_EMIT
+    count_launch(2);
+  }
+  int bits = 32 + tile_bits(tiles);
+  int which = radix_sort_pairs(w.k0, w.v0, w.k1, w.v1, w.hist, w.counters, pair_capacity, bits, s);
+  const uint64_t* sk = which ? w.k1 : w.k0;
+  const uint32_t* sv = which ? w.v1 : w.v0;
+  k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
+  if (opts->tile == 8) launch_fwd<8>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
+  else if (opts->tile == 16) launch_fwd<16>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
+  else launch_fwd<32>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
+  count_launch(2);
+  return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
+}
+
+extern "C" lv_status lv_workspace_counters(const void* workspace, size_t ws_bytes, int64_t* out2, void* stream) {
+  if (!workspace || !out2 || ws_bytes < 64) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  unsigned long long h[2];
+  cudaStream_t s = (cudaStream_t)stream;
+  lv_status e = cuda_check(cudaMemcpyAsync(h, workspace, sizeof(h), cudaMemcpyDeviceToHost, s), "counters");
+  if (e != LV_OK) return e;
+  e = cuda_check(cudaStreamSynchronize(s), "counters");
+  if (e != LV_OK) return e;
+  out2[0] = (int64_t)h[0];
+  out2[1] = (int64_t)h[1];
+  return LV_OK;
+}
+
+extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera* cams, int n_views,
+                                           const lv_raster_opts* opts, const lv_fwd_out* fwd, void* workspace,
+                                           size_t ws_bytes, int64_t pair_capacity, const float* dL_drgb,
+                                           const float* dL_ddepth, const float* dL_dT, float* d_density, float* d_sh,
+                                           int accumulate, int32_t* d_status, void* stream) {
+  lv_status st = check_common(vox, cams, n_views, opts);
+  if (st != LV_OK) return st;
+  if (!fwd || !fwd->T || !fwd->n_contrib || !dL_drgb || !d_density || !d_sh) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  if (pair_capacity < 0 || pair_capacity > 0xffffffffLL) { set_error("pair_capacity out of range"); return LV_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  ViewSet vs;
+  int64_t tiles, pixels;
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
+  FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  if (!d_status) d_status = w.status;
+  const int64_t n = vox->n;
+  const int which = sort_passes(32 + tile_bits(tiles)) & 1;
+  const uint32_t* sv = which ? w.v1 : w.v0;
+  if (!accumulate && n > 0) cudaMemsetAsync(d_density, 0, sizeof(float) * 8 * n, s);
+  if (opts->tile == 8) launch_bwd<8>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  else if (opts->tile == 16) launch_bwd<16>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  else launch_bwd<32>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  count_launch(1);
+  if (n > 0) {
+    const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
+    const int blocks = (int)((n + 127) / 128);
+    if (vox->sh_dtype == LV_F32)
+      k_sh_bwd<float><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const float*)vox->sh, nb, n, vs, w.vis,
+                                             w.slot, w.d_rgb, d_sh, accumulate);
+    else
+      k_sh_bwd<__nv_bfloat16><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const __nv_bfloat16*)vox->sh, nb, n,
+                                                     vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
+    count_launch(1);
+  }
+  return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_backward");
+}
+
+extern "C" lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n, float* w_max, int64_t* argmax,
+                                    void* stream) {
+  if (n < 0 || (n > 0 && (!packed || !w_max))) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (n == 0) return LV_OK;
+  k_unpack_wmax<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(packed, n, w_max, argmax);
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_unpack_wmax");
+}
+
+extern "C" lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                                    const void* workspace, size_t ws_bytes, int64_t pair_capacity, uint64_t* keys,
+                                    uint32_t* voxel, uint32_t* ranges, void* stream) {
+  if (!cams || !opts || !workspace || n_views < 1 || n_views > LV_MAX_VIEWS || n < 0) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (opts->tile != 8 && opts->tile != 16 && opts->tile != 32) { set_error("bad tile"); return LV_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  ViewSet vs;
+  int64_t tiles, pixels;
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
+  FwdWs w = carve_fwd((void*)workspace, n, n_views, tiles, pixels, pair_capacity);
+  if (ws_bytes < w.bytes) { set_error("workspace too small"); return LV_ERR_WORKSPACE; }
+  const int which = sort_passes(32 + tile_bits(tiles)) & 1;
+  if (keys || voxel) {
+    k_debug_pairs<<<608, 256, 0, s>>>(which ? w.k1 : w.k0, which ? w.v1 : w.v0, w.rec, w.counters, pair_capacity,
+                                       keys, voxel);
+    count_launch(1);
+  }
+  if (ranges) cudaMemcpyAsync(ranges, w.ranges, sizeof(uint32_t) * 2 * tiles, cudaMemcpyDeviceToDevice, s);
+  return cuda_check(cudaGetLastError(), "lv_debug_pairs");
+}

@@ -1,0 +1,270 @@
+"""Python binding of ``liblitevoxel.so`` (the C ABI in include/litevoxel.h).
+
+Argument marshalling only: every function forwards torch CUDA tensors'
+device pointers and the current CUDA stream to the library; all arithmetic
+runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblitevoxel.so")
+
+LV_OK, LV_ERR_INVALID_ARG, LV_ERR_WORKSPACE, LV_ERR_CAPACITY, LV_ERR_CUDA, LV_ERR_TIMEOUT, LV_ERR_UNSUPPORTED = range(7)
+LV_F32, LV_F16, LV_BF16 = 0, 1, 2
+LV_FLAG_SYNC_CHECK = 1
+LV_MAX_VIEWS = 64
+STATUS_NAMES = {0: "LV_OK", 1: "LV_ERR_INVALID_ARG", 2: "LV_ERR_WORKSPACE", 3: "LV_ERR_CAPACITY", 4: "LV_ERR_CUDA",
+                5: "LV_ERR_TIMEOUT", 6: "LV_ERR_UNSUPPORTED"}
+
+
+class LvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------------ structs
+class lv_voxels(C.Structure):
+    _fields_ = [("n", C.c_int64), ("geom", C.c_void_p), ("level", C.c_void_p), ("density", C.c_void_p),
+                ("density_dtype", C.c_int32), ("sh", C.c_void_p), ("sh_dtype", C.c_int32), ("sh_degree", C.c_int32)]
+
+
+class lv_camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("w2c", C.c_float * 12), ("z_near", C.c_float)]
+
+
+class lv_raster_opts(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("threads_per_px", C.c_int32), ("t_stop", C.c_float),
+                ("flags", C.c_uint32)]
+
+
+class lv_fwd_out(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("T", C.c_void_p), ("n_contrib", C.c_void_p),
+                ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p)]
+
+
+class lv_prune_params(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("q_ppm", C.c_int32), ("ema_alpha", C.c_float), ("m_low", C.c_float),
+                ("m_high", C.c_float), ("cap_ppm", C.c_int32), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32)]
+
+
+class lv_subdiv_params(C.Structure):
+    _fields_ = [("kappa", C.c_float), ("beta", C.c_float), ("top_ppm", C.c_int32), ("l_max", C.c_int32),
+                ("budget", C.c_int64), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32)]
+
+
+class lv_aux_array(C.Structure):
+    _fields_ = [("in_", C.c_void_p), ("out", C.c_void_p), ("width", C.c_int32), ("elem_bytes", C.c_int32),
+                ("fill", C.c_uint32)]
+
+
+class lv_lf_params(C.Structure):
+    _fields_ = [("eps", C.c_float), ("gamma_max", C.c_float), ("t0", C.c_float), ("t1", C.c_float),
+                ("pctl_ppm", C.c_int32)]
+
+
+# ------------------------------------------------------------------ loading
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_P, _I64, _I32, _F, _SZ = C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_size_t
+_PV = C.POINTER(lv_voxels)
+_PC = C.POINTER(lv_camera)
+_PO = C.POINTER(lv_raster_opts)
+_PF = C.POINTER(lv_fwd_out)
+SIGNATURES = {
+    "lv_forward_workspace_size": (_SZ, [_I64, _PC, C.c_int, _PO, _I64]),
+    "lv_rasterize_forward": (C.c_int, [_PV, _PC, C.c_int, _PO, _PF, _P, _SZ, _I64, _P, _P]),
+    "lv_workspace_counters": (C.c_int, [_P, _SZ, C.POINTER(C.c_int64), _P]),
+    "lv_rasterize_backward": (C.c_int, [_PV, _PC, C.c_int, _PO, _PF, _P, _SZ, _I64, _P, _P, _P, _P, _P, C.c_int, _P,
+                                        _P]),
+    "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
+    "lv_debug_pairs": (C.c_int, [_I64, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _P, _P, _P]),
+    "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
+    "lv_prune_depth_quantile": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.POINTER(lv_prune_params), _P, _P, _P, _SZ, _P,
+                                          _P]),
+    "lv_subdivide_workspace_size": (_SZ, [_I64, C.POINTER(lv_subdiv_params)]),
+    "lv_subdivide_priority": (C.c_int, [_PV, _P, _P, _P, _P, _P, C.POINTER(lv_subdiv_params),
+                                        C.POINTER(lv_aux_array), C.c_int, _PV, _P, _P, _P, _SZ, _P, _P]),
+    "lv_lf_gamma": (_F, [_F, C.POINTER(lv_lf_params)]),
+    "lv_lf_workspace_size": (_SZ, [_P, _P, C.c_int]),
+    "lv_lf_weighted_loss": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P, _SZ, _P]),
+    "lv_last_error": (C.c_char_p, []),
+    "lv_version": (C.c_int32, []),
+    "lv_launch_count": (C.c_int64, []),
+}
+
+
+def load():
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2511_02510_gb300.build.build()")
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue          # a missing export raises when it is called
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def last_error() -> str:
+    return load().lv_last_error().decode()
+
+
+def launch_count() -> int:
+    return int(load().lv_launch_count())
+
+
+def _check(status: int, what: str):
+    if status != LV_OK:
+        raise LvError(status, f"{what}: {last_error()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------------ marshalling helpers
+_DT = {torch.float32: LV_F32, torch.float16: LV_F16, torch.bfloat16: LV_BF16}
+
+
+def make_voxels(geom, density, sh, level=None, sh_degree=3) -> lv_voxels:
+    v = lv_voxels()
+    v.n = int(geom.shape[0])
+    v.geom = _ptr(geom)
+    v.level = _ptr(level)
+    v.density = _ptr(density)
+    v.density_dtype = _DT[density.dtype]
+    v.sh = _ptr(sh)
+    v.sh_dtype = _DT[sh.dtype]
+    v.sh_degree = int(sh_degree)
+    return v
+
+
+def make_cameras(cams) -> C.Array:
+    arr = (lv_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].width, arr[i].height = int(c["width"]), int(c["height"])
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = c["fx"], c["fy"], c["cx"], c["cy"]
+        for k in range(12):
+            arr[i].w2c[k] = float(c["w2c"][k])
+        arr[i].z_near = c["z_near"]
+    return arr
+
+
+def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False) -> lv_raster_opts:
+    o = lv_raster_opts()
+    o.tile, o.batch, o.threads_per_px, o.t_stop = tile, batch, 1, t_stop
+    o.flags = LV_FLAG_SYNC_CHECK if sync_check else 0
+    return o
+
+
+def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None) -> lv_fwd_out:
+    o = lv_fwd_out()
+    o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
+    o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)
+    return o
+
+
+# ------------------------------------------------------------------ C-ABI calls (same names)
+def lv_forward_workspace_size(n, cams_arr, n_views, opts, pair_capacity) -> int:
+    return int(load().lv_forward_workspace_size(n, cams_arr, n_views, C.byref(opts), pair_capacity))
+
+
+def lv_rasterize_forward(vox, cams_arr, n_views, opts, out, workspace, pair_capacity, d_status=None):
+    _check(load().lv_rasterize_forward(C.byref(vox), cams_arr, n_views, C.byref(opts), C.byref(out), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), pair_capacity, _ptr(d_status),
+                                       _stream()), "lv_rasterize_forward")
+
+
+def lv_workspace_counters(workspace):
+    out = (C.c_int64 * 2)()
+    _check(load().lv_workspace_counters(_ptr(workspace), workspace.numel() * workspace.element_size(), out,
+                                        _stream()), "lv_workspace_counters")
+    return int(out[0]), int(out[1])
+
+
+def lv_rasterize_backward(vox, cams_arr, n_views, opts, fwd, workspace, pair_capacity, dL_drgb, dL_ddepth, dL_dT,
+                          d_density, d_sh, accumulate=False, d_status=None):
+    _check(load().lv_rasterize_backward(C.byref(vox), cams_arr, n_views, C.byref(opts), C.byref(fwd),
+                                        _ptr(workspace), workspace.numel() * workspace.element_size(), pair_capacity,
+                                        _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dT), _ptr(d_density), _ptr(d_sh),
+                                        int(bool(accumulate)), _ptr(d_status), _stream()), "lv_rasterize_backward")
+
+
+def lv_unpack_wmax(packed, w_max, argmax=None):
+    _check(load().lv_unpack_wmax(_ptr(packed), int(packed.numel()), _ptr(w_max), _ptr(argmax), _stream()),
+           "lv_unpack_wmax")
+
+
+def lv_debug_pairs(n, cams_arr, n_views, opts, workspace, pair_capacity, keys=None, voxel=None, ranges=None):
+    _check(load().lv_debug_pairs(n, cams_arr, n_views, C.byref(opts), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), pair_capacity, _ptr(keys), _ptr(voxel),
+                                 _ptr(ranges), _stream()), "lv_debug_pairs")
+
+
+def lv_prune_workspace_size(n, params) -> int:
+    return int(load().lv_prune_workspace_size(n, C.byref(params)))
+
+
+def lv_prune_depth_quantile(w_max, seen, z, ema_m, state, params, prune_mask, n_pruned, workspace, d_status=None):
+    _check(load().lv_prune_depth_quantile(int(w_max.numel()), _ptr(w_max), _ptr(seen), _ptr(z), _ptr(ema_m),
+                                          _ptr(state), C.byref(params), _ptr(prune_mask), _ptr(n_pruned),
+                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                          _ptr(d_status), _stream()), "lv_prune_depth_quantile")
+
+
+def lv_subdivide_workspace_size(n, params) -> int:
+    return int(load().lv_subdivide_workspace_size(n, C.byref(params)))
+
+
+def lv_subdivide_priority(vin, delta, z, u, seen, prune_mask, params, aux, vout, selected, n_new, workspace,
+                          d_status=None):
+    aux_arr = (lv_aux_array * max(1, len(aux)))(*aux)
+    _check(load().lv_subdivide_priority(C.byref(vin), _ptr(delta), _ptr(z), _ptr(u), _ptr(seen), _ptr(prune_mask),
+                                        C.byref(params), aux_arr, len(aux), C.byref(vout), _ptr(selected),
+                                        _ptr(n_new), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                        _ptr(d_status), _stream()), "lv_subdivide_priority")
+
+
+def lv_lf_gamma(t, params) -> float:
+    return float(load().lv_lf_gamma(float(t), C.byref(params)))
+
+
+def lv_lf_workspace_size(widths, heights) -> int:
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    return int(load().lv_lf_workspace_size(w, h, len(widths)))
+
+
+def lv_lf_weighted_loss(rgb, gt, widths, heights, t, params, loss, dL_drgb, workspace):
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    _check(load().lv_lf_weighted_loss(_ptr(rgb), _ptr(gt), w, h, len(widths), float(t), C.byref(params), _ptr(loss),
+                                      _ptr(dL_drgb), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                      _stream()), "lv_lf_weighted_loss")

@@ -1,0 +1,169 @@
+"""High-level rasterizer API over the C ABI: workspace management, forward,
+backward and a torch.autograd.Function.
+
+Everything numeric runs in liblitevoxel.so; this module only allocates
+caller-owned device buffers (through torch) and forwards pointers.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import litevoxel as L
+
+
+class RasterContext:
+    """Workspace and outputs for one camera set and a voxel count.
+
+    The pair capacity (sorted (tile, voxel) pairs) is sized once, with
+    headroom, by :meth:`fit_capacity`; a later forward that overflows it
+    reports LV_ERR_CAPACITY (checked by :meth:`check`).
+    """
+
+    def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda"):
+        self.cams = list(cams)
+        self.n_views = len(self.cams)
+        self.cams_arr = L.make_cameras(self.cams)
+        self.opts = L.make_opts(tile, batch, t_stop)
+        self.device = torch.device(device)
+        self.n = int(n_voxels)
+        self.sizes = [(int(c["width"]), int(c["height"])) for c in self.cams]
+        self.n_pix = sum(w * h for w, h in self.sizes)
+        self.pair_capacity = int(pair_capacity) if pair_capacity is not None else max(1024, 4 * self.n * self.n_views)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self._alloc_outputs()
+        self._alloc_workspace()
+
+    # ---------------------------------------------------------------- buffers
+    def _alloc_outputs(self):
+        d, P, n = self.device, self.n_pix, self.n
+        self.rgb = torch.empty((P, 3), dtype=torch.float32, device=d)
+        self.depth = torch.empty(P, dtype=torch.float32, device=d)
+        self.T = torch.empty(P, dtype=torch.float32, device=d)
+        self.n_contrib = torch.empty(P, dtype=torch.int32, device=d)
+        self.wmax_packed = torch.zeros(n, dtype=torch.int64, device=d)
+        self.z_min = torch.full((n,), math.inf, dtype=torch.float32, device=d)
+        self.delta_min = torch.full((n,), math.inf, dtype=torch.float32, device=d)
+        self.seen = torch.zeros(n, dtype=torch.uint8, device=d)
+
+    def _alloc_workspace(self):
+        nb = L.lv_forward_workspace_size(self.n, self.cams_arr, self.n_views, self.opts, self.pair_capacity)
+        if nb == 0:
+            raise ValueError("invalid rasterizer configuration")
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
+
+    def set_pair_capacity(self, cap):
+        self.pair_capacity = int(cap)
+        self.workspace = None
+        self._alloc_workspace()
+
+    def reset_stats(self):
+        """Zero w_max and reset z_min / delta_min / seen before a new accumulation window."""
+        self.wmax_packed.zero_()
+        self.z_min.fill_(math.inf)
+        self.delta_min.fill_(math.inf)
+        self.seen.zero_()
+
+    def fwd_struct(self, stats=True):
+        return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
+                              self.wmax_packed if stats else None, self.z_min if stats else None,
+                              self.delta_min if stats else None, self.seen if stats else None)
+
+    # ---------------------------------------------------------------- calls
+    def forward(self, vox: L.lv_voxels, stats=True):
+        """Launch the forward pass (asynchronous).  Returns (rgb, depth, T)."""
+        L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(stats), self.workspace,
+                               self.pair_capacity, self.status)
+        return self.rgb, self.depth, self.T
+
+    def backward(self, vox: L.lv_voxels, dL_drgb, dL_ddepth=None, dL_dT=None, d_density=None, d_sh=None,
+                 accumulate=False):
+        if d_density is None:
+            d_density = torch.empty((self.n, 8), dtype=torch.float32, device=self.device)
+        if d_sh is None:
+            d_sh = torch.empty((self.n, 48), dtype=torch.float32, device=self.device)
+        L.lv_rasterize_backward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(False), self.workspace,
+                                self.pair_capacity, dL_drgb.contiguous(),
+                                None if dL_ddepth is None else dL_ddepth.contiguous(),
+                                None if dL_dT is None else dL_dT.contiguous(), d_density, d_sh, accumulate,
+                                self.status)
+        return d_density, d_sh
+
+    def counters(self):
+        """(pairs emitted by the last forward, visible slots); synchronises."""
+        return L.lv_workspace_counters(self.workspace)
+
+    def check(self):
+        """Synchronise and raise if a kernel reported an error (e.g. pair capacity)."""
+        st = int(self.status.item())
+        if st != 0:
+            self.status.zero_()
+            raise L.LvError(st, "device-side status")
+
+    def fit_capacity(self, vox: L.lv_voxels, headroom=1.25):
+        """Run one forward, grow the pair capacity if needed (with headroom) and re-run."""
+        self.status.zero_()
+        self.forward(vox, stats=False)
+        pairs, _ = self.counters()
+        need = int(pairs * headroom) + 1024
+        if pairs > self.pair_capacity or need > 2 * self.pair_capacity:
+            self.set_pair_capacity(max(need, 1024))
+            self.status.zero_()
+            self.forward(vox, stats=False)
+        self.status.zero_()
+        return pairs
+
+    def unpack_wmax(self):
+        w = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        a = torch.empty(self.n, dtype=torch.int64, device=self.device)
+        L.lv_unpack_wmax(self.wmax_packed, w, a)
+        return w, a
+
+
+class Scene:
+    """Voxel arrays on the device (structure of arrays)."""
+
+    def __init__(self, geom, level, density, sh, sh_degree=3):
+        self.geom, self.level, self.density, self.sh, self.sh_degree = geom, level, density, sh, sh_degree
+
+    @staticmethod
+    def from_numpy(arrs, device="cuda", density_dtype=torch.float32, sh_dtype=torch.float32, sh_degree=3):
+        return Scene(torch.as_tensor(arrs["geom"]).to(device).contiguous(),
+                     torch.as_tensor(arrs["level"]).to(device).contiguous(),
+                     torch.as_tensor(arrs["density"]).to(device=device, dtype=density_dtype).contiguous(),
+                     torch.as_tensor(arrs["sh"]).to(device=device, dtype=sh_dtype).contiguous(), sh_degree)
+
+    @property
+    def n(self):
+        return int(self.geom.shape[0])
+
+    def voxels(self) -> L.lv_voxels:
+        return L.make_voxels(self.geom, self.density, self.sh, self.level, self.sh_degree)
+
+
+class _RasterFn(torch.autograd.Function):
+    """rgb, depth, T = raster(density, sh); the backward re-walks the sorted
+    lists back to front (no per-sample storage), using only the context's
+    workspace, T and n_contrib."""
+
+    @staticmethod
+    def forward(ctx, density, sh, scene, rctx):
+        vox = L.make_voxels(scene.geom, density, sh, scene.level, scene.sh_degree)
+        rgb, depth, T = rctx.forward(vox, stats=True)
+        ctx.scene, ctx.rctx, ctx.vox_keep = scene, rctx, (density, sh)
+        return rgb.clone(), depth.clone(), T.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_T):
+        density, sh = ctx.vox_keep
+        vox = L.make_voxels(ctx.scene.geom, density, sh, ctx.scene.level, ctx.scene.sh_degree)
+        g_rgb = torch.zeros_like(ctx.rctx.rgb) if g_rgb is None else g_rgb.float().contiguous()
+        dd, ds = ctx.rctx.backward(vox, g_rgb, None if g_depth is None else g_depth.float().contiguous(),
+                                   None if g_T is None else g_T.float().contiguous())
+        return dd.to(density.dtype), ds.to(sh.dtype), None, None
+
+
+def rasterize(density, sh, scene: Scene, rctx: RasterContext):
+    """Differentiable forward: returns (rgb [P,3], depth [P], T [P])."""
+    return _RasterFn.apply(density, sh, scene, rctx)

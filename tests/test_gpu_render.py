@@ -1,0 +1,293 @@
+"""GPU parity of the rasterizer (forward, w_max, statistics, pair lists,
+backward) against the CPU oracle, through the C ABI.
+
+Tolerances (from the arithmetic):
+ - images: within 1e-5 max-abs of the FP64 oracle, plus the oracle's per-pixel
+   FP32 sensitivity bound (a chord's length moves with sub-ulp shifts of the
+   ray at grazing incidence and at large distances); pixels whose bound is
+   below 1e-6 must meet 1e-5 outright, and at most 1 % of pixels may exceed it;
+ - integer outputs (pair lists, tile ranges, seen, FP32-pinned statistics):
+   bit-exact;
+ - gradients: within 1e-4 of the oracle's, relative to the largest gradient
+   magnitude (FP32 atomics reorder the sums).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dequantized, gpu_forward, gpu_pairs, np_
+from paper_2511_02510_gb300 import litevoxel as L
+from paper_2511_02510_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def cam_far(W=128, H=128, az=30.0):
+    return synth.orbit_camera(W, H, 60.0, 3.0, az, 20.0, target=(0.5, 0.5, 0.5))
+
+
+def cam_near(W=128, H=128, az=30.0, el=25.0, r=1.6):
+    return synth.orbit_camera(W, H, 60.0, r, az, el, target=(0.5, 0.4, 0.5))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.scene_tiny()
+
+
+def compare_images(ora_r, ctx, tol=IMG_TOL, rgb=None, T=None, depth=None, mask=None):
+    ok = ora_r["near_stop"] == 0
+    if mask is not None:
+        ok &= mask
+    assert ok.sum() > 0.99 * (mask.sum() if mask is not None else ok.size)
+    rgb = np_(ctx.rgb) if rgb is None else rgb
+    T = np_(ctx.T) if T is None else T
+    depth = np_(ctx.depth) if depth is None else depth
+    e_rgb = np.abs(rgb - ora_r["rgb"]).max(axis=1)
+    e_T = np.abs(T - ora_r["T"])
+    e_d = np.abs(depth - ora_r["depth"])
+    dscale = max(1.0, float(np.abs(ora_r["depth"]).max()))
+    # every pixel within 1e-5 plus its FP32 sensitivity bound
+    assert np.all(e_rgb[ok] <= tol + ora_r["bound_rgb"][ok]), (e_rgb - ora_r["bound_rgb"])[ok].max()
+    assert np.all(e_T[ok] <= tol + ora_r["bound_T"][ok]), (e_T - ora_r["bound_T"])[ok].max()
+    assert np.all(e_d[ok] <= tol * dscale + ora_r["bound_depth"][ok])
+    # well-conditioned pixels meet 1e-5 outright; few pixels exceed it at all
+    well = ok & (ora_r["bound_rgb"] < 1e-6) & (ora_r["bound_T"] < 1e-6)
+    if well.any():
+        assert e_rgb[well].max() < tol and e_T[well].max() < tol
+    assert (e_rgb[ok] > tol).mean() <= 0.01 and (e_T[ok] > tol).mean() <= 0.01
+    return float(e_rgb[ok].max()), float(e_T[ok].max())
+
+
+def compare_wmax(ora, sc, cams, ora_r, ctx):
+    w, a = ctx.unpack_wmax()
+    w, a = np_(w), np_(a)
+    hit_o, hit_g = ora_r["w_arg"] >= 0, a >= 0
+    # grazing chords can flip a hit decision between FP32 and FP64: allow a handful
+    assert (hit_o != hit_g).sum() <= max(2, 0.002 * hit_o.sum())
+    both = hit_o & hit_g
+    assert np.abs(w[both] - ora_r["w_max"][both]).max() < IMG_TOL
+    mism = np.where(both & (a != ora_r["w_arg"]))[0]
+    assert len(mism) <= 0.02 * both.sum() + 2
+    # every differing argmax must be a ray whose weight is within FP32 error of the maximum
+    sizes = [(c["width"], c["height"]) for c in cams]
+    offs = np.cumsum([0] + [w_ * h_ for w_, h_ in sizes])
+    for v in mism[:40]:
+        g = int(a[v])
+        view = int(np.searchsorted(offs, g, side="right") - 1)
+        loc = g - offs[view]
+        tr = ora.trace_pixel(sc, cams[view], int(loc % sizes[view][0]), int(loc // sizes[view][0]))
+        ws = tr["w"][tr["ids"] == v]
+        assert len(ws) == 1 and ws[0] >= ora_r["w_max"][v] - 2e-6, (v, ws, ora_r["w_max"][v])
+
+
+@pytest.mark.parametrize("which", ["far", "near"])
+def test_forward_parity_tiny(ora, tiny, which):
+    cams = [cam_far()] if which == "far" else [cam_near()]
+    scene, ctx, vox = gpu_forward(tiny, cams)
+    r = ora.render(tiny, cams)
+    compare_images(r, ctx)
+    compare_wmax(ora, tiny, cams, r, ctx)
+
+
+def test_pairs_and_stats_bit_exact(ora, tiny):
+    cams = [cam_near(), cam_near(96, 72, az=150.0), cam_far(70, 50, az=250.0)]
+    scene, ctx, vox = gpu_forward(tiny, cams)
+    keys, vox_ids, ranges, pairs = gpu_pairs(ctx, scene.n)
+    ref = ora.pairs(tiny, cams, ts=16)
+    assert pairs == ref["n_pairs"]
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(vox_ids, ref["vals"])
+    np.testing.assert_array_equal(ranges, ref["ranges"])
+    np.testing.assert_array_equal(np_(ctx.seen), ref["seen"])
+    np.testing.assert_array_equal(np_(ctx.z_min).view(np.uint32), ref["z_min"].view(np.uint32))
+    np.testing.assert_array_equal(np_(ctx.delta_min).view(np.uint32), ref["delta_min"].view(np.uint32))
+
+
+@pytest.mark.parametrize("tile,batch", [(8, 64), (16, 128), (32, 256), (32, 64)])
+def test_forward_tiles_batches_ragged(ora, tiny, tile, batch):
+    cams = [cam_near(100, 70, az=80.0), cam_near(37, 53, az=200.0, el=40.0)]
+    scene, ctx, vox = gpu_forward(tiny, cams, tile=tile, batch=batch)
+    r = ora.render(tiny, cams)
+    compare_images(r, ctx)
+    keys, vox_ids, ranges, pairs = gpu_pairs(ctx, scene.n)
+    ref = ora.pairs(tiny, cams, ts=tile)
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(vox_ids, ref["vals"])
+
+
+def test_mixed_precision_storage(ora, tiny):
+    cams = [cam_near(), cam_near(64, 48, az=300.0)]
+    scene, ctx, vox = gpu_forward(tiny, cams, density_dtype=torch.float16, sh_dtype=torch.bfloat16)
+    ref_scene = dequantized(tiny, torch.float16, torch.bfloat16)
+    r = ora.render(ref_scene, cams)
+    compare_images(r, ctx)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_sh_degrees(ora, tiny, deg):
+    cams = [cam_near(64, 64)]
+    scene, ctx, vox = gpu_forward(tiny, cams, sh_degree=deg)
+    r = ora.render(tiny, cams, sh_degree=deg)
+    compare_images(r, ctx)
+
+
+def _loss_grads(P, seed, near_stop):
+    rng = np.random.default_rng(seed)
+    gC = rng.normal(size=(P, 3)).astype(np.float32)
+    gD = (0.1 * rng.normal(size=P)).astype(np.float32)
+    gT = rng.normal(size=P).astype(np.float32)
+    # pixels whose stop decision is within rounding of t_stop are excluded
+    gC[near_stop == 1] = 0
+    gD[near_stop == 1] = 0
+    gT[near_stop == 1] = 0
+    return gC, gD, gT
+
+
+def _grad_err(g, ref):
+    scale = np.abs(ref).max()
+    return np.abs(g - ref).max() / max(scale, 1e-30)
+
+
+@pytest.mark.parametrize("cfg", ["near16", "multi8", "mixed32"])
+def test_backward_parity(ora, tiny, cfg):
+    if cfg == "near16":
+        cams, tile, dd, sd = [cam_near()], 16, torch.float32, torch.float32
+    elif cfg == "multi8":
+        cams, tile, dd, sd = [cam_near(80, 60), cam_far(64, 64, az=120.0)], 8, torch.float32, torch.float32
+    else:
+        cams, tile, dd, sd = [cam_near(90, 90, az=250.0)], 32, torch.float16, torch.bfloat16
+    scene, ctx, vox = gpu_forward(tiny, cams, tile=tile, density_dtype=dd, sh_dtype=sd)
+    ref_scene = dequantized(tiny, dd, sd)
+    r = ora.render(ref_scene, cams)
+    P = ctx.n_pix
+    gC, gD, gT = _loss_grads(P, 3, r["near_stop"])
+    d_dens, d_sh = ctx.backward(vox, torch.from_numpy(gC).cuda(), torch.from_numpy(gD).cuda(),
+                                torch.from_numpy(gT).cuda())
+    torch.cuda.synchronize()
+    ref = ora.render_backward(ref_scene, cams, gC.astype(np.float64), gD.astype(np.float64), gT.astype(np.float64))
+    e_d = _grad_err(np_(d_dens), ref["d_density"])
+    e_s = _grad_err(np_(d_sh), ref["d_sh"])
+    assert e_d < GRAD_TOL and e_s < GRAD_TOL, (e_d, e_s)
+    # accumulate = True adds onto existing gradients
+    d2, s2 = ctx.backward(vox, torch.from_numpy(gC).cuda(), torch.from_numpy(gD).cuda(), torch.from_numpy(gT).cuda(),
+                          d_density=d_dens.clone(), d_sh=d_sh.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert _grad_err(np_(d2), 2 * ref["d_density"]) < GRAD_TOL
+    assert _grad_err(np_(s2), 2 * ref["d_sh"]) < GRAD_TOL
+
+
+def test_backward_matches_fd_of_gpu_forward(tiny):
+    # Central differences of the GPU forward itself (FP32, larger steps) agree with the GPU backward.
+    cams = [cam_near(48, 48)]
+    scene, ctx, vox = gpu_forward(tiny, cams)
+    rng = np.random.default_rng(9)
+    P = ctx.n_pix
+    gC = torch.from_numpy(rng.normal(size=(P, 3)).astype(np.float32)).cuda()
+    d_dens, d_sh = ctx.backward(vox, gC)
+    w, a = ctx.unpack_wmax()
+    hit = np.where(np_(a) >= 0)[0]
+    pick = rng.choice(hit, size=8, replace=False)
+
+    def loss():
+        ctx.forward(scene.voxels(), stats=False)
+        return float((ctx.rgb.double() * gC.double()).sum())
+
+    n_ok = 0
+    for v in pick:
+        i = int(rng.integers(8))
+        x0 = float(scene.density[v, i])
+        h = 1e-2
+        scene.density[v, i] = x0 + h
+        lp = loss()
+        scene.density[v, i] = x0 - h
+        lm = loss()
+        scene.density[v, i] = x0
+        fd = (lp - lm) / (2 * h)
+        an = float(d_dens[v, i])
+        if abs(fd - an) <= 2e-2 * max(abs(fd), abs(an), 1e-3):
+            n_ok += 1
+    assert n_ok >= 6
+
+
+def test_empty_and_culled(ora):
+    empty = synth.constant_voxel_scene(np.zeros((0, 3)), 0.1, np.zeros(0), np.zeros((0, 3)))
+    cams = [cam_near(40, 30)]
+    scene, ctx, vox = gpu_forward(empty, cams, pair_capacity=16)
+    assert np.all(np_(ctx.rgb) == 0) and np.all(np_(ctx.T) == 1)
+    # everything behind the camera
+    sc = synth.constant_voxel_scene([[0.5, 0.5, 0.5]], 0.2, [3.0], [(1, 1, 1)])
+    cam = synth.look_at_camera([0.5, 0.5, 2.0], [0.5, 0.5, 5.0], 32, 32, 60.0)
+    scene, ctx, vox = gpu_forward(sc, [cam], pair_capacity=16)
+    assert np.all(np_(ctx.T) == 1) and int(np_(ctx.seen)[0]) == 0
+    # a voxel straddling the near plane covers the whole image and still matches the oracle
+    cam = synth.look_at_camera([0.5, 0.5, 0.45], [0.5, 0.5, 5.0], 24, 20, 60.0)
+    scene, ctx, vox = gpu_forward(sc, [cam])
+    r = ora.render(sc, [cam])
+    compare_images(r, ctx)
+
+
+def test_capacity_overflow_reported(tiny):
+    from gpu_helpers import to_scene
+    from paper_2511_02510_gb300.raster import RasterContext
+    cams = [cam_near()]
+    scene = to_scene(tiny)
+    ctx = RasterContext(cams, scene.n, pair_capacity=100)           # far too small
+    vox = scene.voxels()
+    opts = L.make_opts(16, 256, 1e-4, sync_check=True)
+    with pytest.raises(L.LvError) as ei:
+        L.lv_rasterize_forward(vox, ctx.cams_arr, 1, opts, ctx.fwd_struct(), ctx.workspace, 100, None)
+    assert ei.value.status == L.LV_ERR_CAPACITY
+    pairs, _ = ctx.counters()
+    assert pairs > 100
+
+
+def test_invalid_arguments_rejected(tiny):
+    cams = [cam_near()]
+    scene, ctx, vox = gpu_forward(tiny, cams)
+    bad = L.make_opts(12, 256)
+    with pytest.raises(L.LvError) as ei:
+        L.lv_rasterize_forward(vox, ctx.cams_arr, 1, bad, ctx.fwd_struct(), ctx.workspace, ctx.pair_capacity)
+    assert ei.value.status == L.LV_ERR_INVALID_ARG
+    small = ctx.workspace[:1024]
+    with pytest.raises(L.LvError) as ei:
+        L.lv_rasterize_forward(vox, ctx.cams_arr, 1, ctx.opts, ctx.fwd_struct(), small, ctx.pair_capacity)
+    assert ei.value.status == L.LV_ERR_WORKSPACE
+
+
+def test_deterministic_integer_outputs(tiny):
+    cams = [cam_near(), cam_near(72, 40, az=10.0)]
+    a = gpu_forward(tiny, cams)[1]
+    ka, va, ra, _ = gpu_pairs(a, tiny["geom"].shape[0])
+    wa = np_(a.wmax_packed).copy()
+    b = gpu_forward(tiny, cams)[1]
+    kb, vb, rb, _ = gpu_pairs(b, tiny["geom"].shape[0])
+    np.testing.assert_array_equal(ka, kb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(wa, np_(b.wmax_packed))
+    np.testing.assert_array_equal(np_(a.n_contrib), np_(b.n_contrib))
+
+
+@pytest.mark.slow
+def test_full_size_360_sampled_crops(ora):
+    # The 2M-voxel 1237x822 workload at full size: oracle pixels on three crops.
+    sc = synth.scene_360()
+    cam = synth.orbit_camera(1237, 822, 60.0, 3.0, 37.0, 15.0)
+    scene, ctx, vox = gpu_forward(sc, [cam])
+    crops = [(100, 100, 124, 116), (600, 400, 624, 420), (1200, 780, 1237, 822)]
+    rgb, T, depth = np_(ctx.rgb), np_(ctx.T), np_(ctx.depth)
+    for (x0, y0, x1, y1) in crops:
+        r = ora.render(sc, [cam], crop=[x0, y0, x1, y1])
+        m = np.zeros((822, 1237), bool)
+        m[y0:y1, x0:x1] = True
+        compare_images(r, ctx, rgb=rgb, T=T, depth=depth, mask=m.ravel())
+    # statistics are FP32-pinned: compare against the oracle binning bit for bit
+    ref = ora.pairs(sc, [cam])
+    np.testing.assert_array_equal(np_(ctx.seen), ref["seen"])
+    np.testing.assert_array_equal(np_(ctx.z_min).view(np.uint32), ref["z_min"].view(np.uint32))

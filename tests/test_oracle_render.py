@@ -319,3 +319,28 @@ def test_backward_matches_central_differences(ora):
             assert abs(fd1 - an) <= 1e-4 * scale + 1e-9, (kind, v, idx, fd1, an)
             checked += 1
     assert checked >= 16
+
+
+def test_fp32_sensitivity_bound_covers_ulp_perturbations(ora):
+    # The per-pixel bound must cover what one-ulp FP32 perturbations of the voxel
+    # positions and of the camera actually do to the FP64 image.
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(40, 40, 60.0, 1.6, 200.0, 40.0, target=(0.5, 0.4, 0.5))
+    r0 = ora.render(sc, [cam])
+    rng = np.random.default_rng(4)
+    for trial in range(3):
+        sc2 = {k: np.array(v, copy=True) for k, v in sc.items()}
+        g = sc2["geom"]
+        sgn = rng.choice([-1.0, 1.0], size=g[:, :3].shape).astype(np.float32)
+        g[:, :3] = np.nextafter(g[:, :3], g[:, :3] + sgn * np.float32(1e30))
+        cam2 = dict(cam)
+        w = np.asarray(cam["w2c"], np.float32)
+        w = np.nextafter(w, w + rng.choice([-1.0, 1.0], size=w.shape).astype(np.float32) * np.float32(1e30))
+        cam2["w2c"] = w.tolist()
+        r1 = ora.render(sc2, [cam2])
+        ok = (r0["near_stop"] == 0) & (r1["near_stop"] == 0)
+        d_rgb = np.abs(r1["rgb"] - r0["rgb"]).max(axis=1)
+        d_T = np.abs(r1["T"] - r0["T"])
+        assert np.all(d_rgb[ok] <= r0["bound_rgb"][ok] + 1e-12), (trial, (d_rgb - r0["bound_rgb"])[ok].max())
+        assert np.all(d_T[ok] <= r0["bound_T"][ok] + 1e-12)
+        assert d_rgb[ok].max() > 0            # the perturbation did change the image
