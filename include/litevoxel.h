@@ -83,7 +83,8 @@ typedef struct {
   int32_t width, height;
   float fx, fy, cx, cy;
   float w2c[12];
-  float z_near; /* voxels whose 8 corners all have z_cam < z_near are culled */
+  float z_near; /* near plane: chords start at camera depth z_near; voxels whose 8 corners all
+                   have z_cam < z_near are culled, voxels crossing it are clipped */
 } lv_camera;
 
 typedef struct {
@@ -121,7 +122,7 @@ size_t lv_forward_workspace_size(int64_t n, const lv_camera* cams, int n_views, 
 /* Forward pass: per voxel and view, cull / project / bin to tiles (FP32 with
  * a fixed operation order), emit (tile << 32 | depth key, voxel) pairs,
  * radix-sort them, find tile ranges and alpha-composite every pixel front to
- * back (Eq. 2-4): slab-test chord l, sigma = max(0, trilinear corner density
+ * back (Eq. 2-4): slab-test chord l (starting at the near plane), sigma = max(0, trilinear corner density
  * at the chord midpoint), alpha = 1 - exp(-sigma l), colour from SH towards
  * the voxel centre c = max(0, SH + 0.5).  w_max (Eq. 5) is fused in.
  * Sorted pairs, tile ranges and the per-pixel optical depth stay in the
@@ -146,12 +147,23 @@ lv_status lv_workspace_counters(const void* workspace, size_t ws_bytes, int64_t*
  * dL_ddepth and dL_dT may be NULL.  d_density [n][8] and d_sh [n][48] are
  * FP32; with accumulate = 0 they are overwritten, else added to.  vox, cams,
  * n_views, opts, workspace and pair_capacity must be those of the forward
- * call (the workspace's colour-gradient scratch is reused). */
+ * call (the workspace's colour-gradient scratch is reused).  With d_sh = NULL
+ * the per-(voxel, view) colour gradients stay in the workspace and
+ * lv_sh_backward finishes the SH part later (same arguments). */
 lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera* cams, int n_views,
                                 const lv_raster_opts* opts, const lv_fwd_out* fwd, void* workspace, size_t ws_bytes,
                                 int64_t pair_capacity, const float* dL_drgb, const float* dL_ddepth,
                                 const float* dL_dT, float* d_density, float* d_sh, int accumulate,
                                 int32_t* d_status, void* stream);
+
+/* SH part of the backward pass: d_sh [n][48] (FP32) from the colour
+ * gradients a preceding lv_rasterize_backward(d_sh = NULL) left in the
+ * workspace, through c = max(0, SH(dir) + 0.5) with dir the unit vector from
+ * the camera centre to the voxel centre; sums over views.  Clears the
+ * workspace's colour gradients.  accumulate as in lv_rasterize_backward. */
+lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                         void* workspace, size_t ws_bytes, int64_t pair_capacity, float* d_sh, int accumulate,
+                         void* stream);
 
 /* Unpack lv_fwd_out.wmax_packed: w_max[i] (0 if never hit) and the smallest
  * global pixel id attaining it (-1 if never hit).  argmax is nullable. */

@@ -34,8 +34,10 @@
  *   - depth = sum_k w_k * t_mid_k;
  *   - colour: real SH of degree <= 3 evaluated towards the voxel centre,
  *     c = max(0, sum + 0.5);
- *   - a voxel all of whose corners lie in front of z_near (camera z < z_near)
- *     is culled in that view;
+ *   - near-plane clipping: a ray's chord starts where its camera depth
+ *     reaches z_near (Eq. 1's t >= 0 becomes z_cam >= z_near), so a voxel all
+ *     of whose corners have camera z < z_near is culled, and one that crosses
+ *     the plane covers the tiles of its part beyond it;
  *   - w_max ties go to the smallest global pixel id;
  *   - delta_v = max(z_v, z_near) / f_x, z_v the camera depth of the centre,
  *     both as minima over views.
@@ -177,8 +179,9 @@ static void cam_derive(const ora_cam* c, cam64* d) {
   d->W = c->width; d->H = c->height;
 }
 
-/* world-space unit direction of the ray through the centre of pixel (x, y) (Eq. 1) */
-static void cam_ray(const cam64* c, int x, int y, double* d) {
+/* world-space unit direction of the ray through the centre of pixel (x, y) (Eq. 1); returns
+ * t_near, the ray parameter at which the camera depth reaches z_near (near-plane clipping) */
+static double cam_ray(const cam64* c, int x, int y, double* d) {
   double dc[3] = {((double)x + 0.5 - c->cx) / c->fx, ((double)y + 0.5 - c->cy) / c->fy, 1.0};
   double n = 0.0;
   for (int k = 0; k < 3; ++k) {
@@ -187,6 +190,8 @@ static void cam_ray(const cam64* c, int x, int y, double* d) {
   }
   n = sqrt(n);
   for (int k = 0; k < 3; ++k) d[k] /= n;
+  double dz = c->R[6] * d[0] + c->R[7] * d[1] + c->R[8] * d[2];
+  return c->z_near / dz;
 }
 
 static void cam_point64(const cam64* c, const double* p, double* q) {
@@ -223,49 +228,68 @@ static void bin_voxel32(const float* g, const ora_cam* c, int ts, bin32* b) {
   float q[3];
   cam_point32(c, cx, cy, cz, q);
   b->zc = q[2];
-  int n_front = 0, n_behind = 0;
+  int n_front = 0;
   float umin = 0, umax = 0, vmin = 0, vmax = 0;
-  float us[8], vs[8], zs[8];
+  int have = 0;
+  float px[8], py[8], pz[8];
   for (int i = 0; i < 8; ++i) {
     float X = (i & 1) ? cx + h : cx - h;
     float Y = (i & 2) ? cy + h : cy - h;
     float Z = (i & 4) ? cz + h : cz - h;
     float p[3];
     cam_point32(c, X, Y, Z, p);
-    zs[i] = p[2];
-    if (p[2] < c->z_near) ++n_behind; else ++n_front;
+    px[i] = p[0]; py[i] = p[1]; pz[i] = p[2];
     if (p[2] >= c->z_near) {
+      ++n_front;
       float rx = p[0] / p[2];
       float ry = p[1] / p[2];
       float u = c->fx * rx;
       float v = c->fy * ry;
-      us[i] = u + c->cx;
-      vs[i] = v + c->cy;
+      u = u + c->cx;
+      v = v + c->cy;
+      if (!have) { umin = umax = u; vmin = vmax = v; have = 1; }
+      else { umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v); }
     }
   }
-  (void)zs;
   b->culled = (n_front == 0);
   if (b->culled) {
     b->tx0 = b->tx1 = b->ty0 = b->ty1 = 0;
     b->count = 0;
     return;
   }
-  if (n_behind > 0) {
-    b->tx0 = 0; b->tx1 = tiles_x; b->ty0 = 0; b->ty1 = tiles_y;
-  } else {
-    umin = umax = us[0]; vmin = vmax = vs[0];
-    for (int i = 1; i < 8; ++i) {
-      umin = fminf(umin, us[i]); umax = fmaxf(umax, us[i]);
-      vmin = fminf(vmin, vs[i]); vmax = fmaxf(vmax, vs[i]);
-    }
-    float fts = (float)ts;
-    float a0 = floorf((umin - 1.0f) / fts), a1 = ceilf((umax + 1.0f) / fts);
-    float b0 = floorf((vmin - 1.0f) / fts), b1 = ceilf((vmax + 1.0f) / fts);
-    b->tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)tiles_x);
-    b->tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)tiles_x);
-    b->ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)tiles_y);
-    b->ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)tiles_y);
+  if (n_front < 8) {
+    /* near-plane clipping: the box edges that cross z = z_near add their
+       crossing points (edge (i, i|bit), lower index first) */
+    for (int i = 0; i < 8; ++i)
+      for (int bit = 1; bit < 8; bit <<= 1) {
+        if (i & bit) continue;
+        int j = i | bit;
+        int fi = pz[i] >= c->z_near, fj = pz[j] >= c->z_near;
+        if (fi == fj) continue;
+        float dz = pz[j] - pz[i];
+        float f = (c->z_near - pz[i]) / dz;
+        float dx = px[j] - px[i];
+        float dy = py[j] - py[i];
+        float mx = f * dx;
+        float my = f * dy;
+        float x = px[i] + mx;
+        float y = py[i] + my;
+        float rx = x / c->z_near;
+        float ry = y / c->z_near;
+        float u = c->fx * rx;
+        float v = c->fy * ry;
+        u = u + c->cx;
+        v = v + c->cy;
+        umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+      }
   }
+  float fts = (float)ts;
+  float a0 = floorf((umin - 1.0f) / fts), a1 = ceilf((umax + 1.0f) / fts);
+  float b0 = floorf((vmin - 1.0f) / fts), b1 = ceilf((vmax + 1.0f) / fts);
+  b->tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)tiles_x);
+  b->tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)tiles_x);
+  b->ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)tiles_y);
+  b->ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)tiles_y);
   int64_t wx = b->tx1 - b->tx0, wy = b->ty1 - b->ty0;
   b->count = (wx > 0 && wy > 0) ? wx * wy : 0;
 }
@@ -348,12 +372,13 @@ int ora_pairs(int64_t n, const float* geom, int n_views, const ora_cam* cams, in
 /* FP64 ray marching                                                   */
 /* ------------------------------------------------------------------ */
 
-/* ray-box chord: returns 1 and the entry/exit parameters when l = t_out - t_in > 0 (t >= 0).
+/* ray-box chord: returns 1 and the entry/exit parameters when l = t_out - t_in > 0, the chord
+ * starting at the near plane (t >= t_near, where the ray's camera depth reaches z_near).
  * d_in / d_out receive |d| along the axis whose slab sets the entry / exit
  * (d_in = 0 when the entry is clamped at t = 0); t_in / t_out are written even
  * for a miss, as long as every axis admits the ray. */
-static int slab64x(const double* o, const double* d, const float* g, double* t_in, double* t_out, double* d_in,
-                   double* d_out) {
+static int slab64x(const double* o, const double* d, double t_near, const float* g, double* t_in, double* t_out,
+                   double* d_in, double* d_out) {
   double lo_t = -INFINITY, hi_t = INFINITY, din = 0.0, dout = 1.0;
   for (int a = 0; a < 3; ++a) {
     double lo = (double)g[a] - (double)g[3], hi = (double)g[a] + (double)g[3];
@@ -366,17 +391,12 @@ static int slab64x(const double* o, const double* d, const float* g, double* t_i
     if (tn > lo_t) { lo_t = tn; din = fabs(d[a]); }
     if (tf < hi_t) { hi_t = tf; dout = fabs(d[a]); }
   }
-  if (lo_t < 0.0) { lo_t = 0.0; din = 0.0; }
+  if (lo_t < t_near) { lo_t = t_near; din = 0.0; }
   *t_in = lo_t;
   *t_out = hi_t;
   *d_in = din;
   *d_out = dout;
   return hi_t - lo_t > 0.0;
-}
-
-static int slab64(const double* o, const double* d, const float* g, double* t_in, double* t_out) {
-  double a, b;
-  return slab64x(o, d, g, t_in, t_out, &a, &b);
 }
 
 /*
@@ -450,24 +470,38 @@ static void build_lists(int64_t n, const float* geom, const ora_cam* c, const ca
     int* r = rect + 4 * i;
     if (b.culled) { r[0] = r[1] = r[2] = r[3] = 0; continue; }
     if (brute) { r[0] = x0; r[1] = y0; r[2] = x1; r[3] = y1; continue; }
-    /* FP64 projection of the corners with a 2-pixel margin; any corner near or
-       behind the camera plane -> whole image */
+    /* FP64 projection of the part of the box beyond the near plane (in-front
+       corners and edge crossings of z = z_near), 2-pixel margin */
     double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-    int full = 0;
+    double pc[8][3];
     for (int k = 0; k < 8; ++k) {
       double p[3] = {(double)g[0] + ((k & 1) ? 1.0 : -1.0) * (double)g[3],
                      (double)g[1] + ((k & 2) ? 1.0 : -1.0) * (double)g[3],
                      (double)g[2] + ((k & 4) ? 1.0 : -1.0) * (double)g[3]};
-      double q[3];
-      cam_point64(cd, p, q);
-      if (q[2] < 0.5 * cd->z_near) { full = 1; break; }
-      double u = cd->fx * q[0] / q[2] + cd->cx, v = cd->fy * q[1] / q[2] + cd->cy;
-      if (u < umin) umin = u;
-      if (u > umax) umax = u;
-      if (v < vmin) vmin = v;
-      if (v > vmax) vmax = v;
+      cam_point64(cd, p, pc[k]);
     }
-    if (full) { r[0] = x0; r[1] = y0; r[2] = x1; r[3] = y1; continue; }
+    for (int k = 0; k < 8; ++k) {
+      double pts[4][3];
+      int np = 0;
+      if (pc[k][2] >= cd->z_near) { pts[np][0] = pc[k][0]; pts[np][1] = pc[k][1]; pts[np][2] = pc[k][2]; ++np; }
+      for (int bit = 1; bit < 8; bit <<= 1) {
+        if (k & bit) continue;
+        int j = k | bit;
+        if ((pc[k][2] >= cd->z_near) == (pc[j][2] >= cd->z_near)) continue;
+        double f = (cd->z_near - pc[k][2]) / (pc[j][2] - pc[k][2]);
+        pts[np][0] = pc[k][0] + f * (pc[j][0] - pc[k][0]);
+        pts[np][1] = pc[k][1] + f * (pc[j][1] - pc[k][1]);
+        pts[np][2] = cd->z_near;
+        ++np;
+      }
+      for (int q = 0; q < np; ++q) {
+        double u = cd->fx * pts[q][0] / pts[q][2] + cd->cx, v = cd->fy * pts[q][1] / pts[q][2] + cd->cy;
+        if (u < umin) umin = u;
+        if (u > umax) umax = u;
+        if (v < vmin) vmin = v;
+        if (v > vmax) vmax = v;
+      }
+    }
     double a0 = floor(umin - 2.0), a1 = ceil(umax + 2.0), b0 = floor(vmin - 2.0), b1 = ceil(vmax + 2.0);
     r[0] = (int)fmax(a0, (double)x0); r[1] = (int)fmax(b0, (double)y0);
     r[2] = (int)fmin(a1, (double)x1); r[3] = (int)fmin(b1, (double)y1);
@@ -517,7 +551,8 @@ typedef struct {
 /* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null.
  * bnd (nullable) receives the FP32 sensitivity bound of rgb, depth and T
  * (see fp32_dx); cmax is the largest colour channel of the view. */
-static int64_t march(const double* o, const double* d, const cand* items, int64_t cnt, const float* geom,
+static int64_t march(const double* o, const double* d, double t_near, const cand* items, int64_t cnt,
+                     const float* geom,
                      const float* dens, const double* colors, double t_stop, sample* s, double* rgb,
                      double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid,
                      double cmax, double* bnd) {
@@ -532,7 +567,7 @@ static int64_t march(const double* o, const double* d, const cand* items, int64_
     const float* g = geom + 4 * (int64_t)id;
     const float* d8 = dens + 8 * (int64_t)id;
     double t_in, t_out, din, dout;
-    if (!slab64x(o, d, g, &t_in, &t_out, &din, &dout)) {
+    if (!slab64x(o, d, t_near, g, &t_in, &t_out, &din, &dout)) {
       /* a near miss that FP32 could count as a hit */
       if (bnd && t_out > 0.0 && t_in - t_out <= ORA_FP32_U * 4.0 * (t_out + 1.0) / (dout > 0.0 ? dout : 1.0)) {
         double dm = 0.0;
@@ -653,10 +688,10 @@ int ora_render(int64_t n, const float* geom, const float* dens, const float* sh,
         int64_t p = (int64_t)y * cd.W + x;
         int64_t gp = pix_off + p;
         double d[3];
-        cam_ray(&cd, x, y, d);
+        double tn = cam_ray(&cd, x, y, d);
         int ns;
         double Tp;
-        int64_t k = march(cd.o, d, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, dens, colors,
+        int64_t k = march(cd.o, d, tn, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, dens, colors,
                           t_stop, NULL, rgb + 3 * gp, depth + gp, &Tp, &ns, twm ? twm + (int64_t)tid * n : NULL,
                           twa ? twa + (int64_t)tid * n : NULL, gp, cmax, bound ? bound + 3 * gp : NULL);
         T[gp] = Tp;
@@ -692,7 +727,8 @@ static void atomic_add(double* p, double v) {
 
 /*
  * Reverse-mode of ora_render for the loss gradients dL/drgb (3 per pixel),
- * dL/ddepth and dL/dT (nullable).  Writes (accumulates into, caller zeroes)
+ * dL/ddepth and dL/dT (nullable); crop (x0,y0,x1,y1 per view, nullable)
+ * restricts the pixels that contribute.  Writes (accumulates into, caller zeroes)
  * d_density[8n] and d_sh[48n].  The per-pixel samples of the forward pass are
  * stored and walked back to front:
  *   dL/dsigma_k = l_k * ( T_k * a_k - sum_{j>k} w_j a_j - T_final * g_T ),
@@ -701,7 +737,7 @@ static void atomic_add(double* p, double v) {
  * c = max(0, SH + 0.5) to the SH coefficients.
  */
 int ora_render_backward(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
-                        int n_views, const ora_cam* cams, double t_stop, const double* dL_drgb,
+                        int n_views, const ora_cam* cams, double t_stop, const int* crop, const double* dL_drgb,
                         const double* dL_ddepth, const double* dL_dT, double* d_density, double* d_sh) {
   double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   double* raw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -713,15 +749,17 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
     cam_derive(&cams[v], &cd);
     view_colors(n, geom, sh, sh_degree, &cd, colors, raw, dirs);
     for (int64_t i = 0; i < 3 * n; ++i) dcol[i] = 0.0;
+    const int* cr = crop ? crop + 4 * v : NULL;
+    int x0 = cr ? cr[0] : 0, y0 = cr ? cr[1] : 0, x1 = cr ? cr[2] : cd.W, y1 = cr ? cr[3] : cd.H;
     pixlists L;
-    build_lists(n, geom, &cams[v], &cd, 0, NULL, &L);
+    build_lists(n, geom, &cams[v], &cd, 0, cr, &L);
 #pragma omp parallel
     {
       int64_t cap = 64;
       sample* s = (sample*)malloc(sizeof(sample) * (size_t)cap);
 #pragma omp for schedule(dynamic, 1)
-      for (int y = 0; y < cd.H; ++y) {
-        for (int x = 0; x < cd.W; ++x) {
+      for (int y = y0; y < y1; ++y) {
+        for (int x = x0; x < x1; ++x) {
           int64_t p = (int64_t)y * cd.W + x;
           int64_t gp = pix_off + p;
           int64_t cnt = L.start[p + 1] - L.start[p];
@@ -731,8 +769,8 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
           }
           double d[3], rgbp[3], dp, Tf;
           int ns;
-          cam_ray(&cd, x, y, d);
-          int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf,
+          double tn = cam_ray(&cd, x, y, d);
+          int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf,
                             &ns, NULL, NULL, gp, 0.0, NULL);
           const double* gC = dL_drgb + 3 * gp;
           double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
@@ -794,8 +832,8 @@ int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float
   sample* s = (sample*)malloc(sizeof(sample) * (size_t)(cnt > 0 ? cnt : 1));
   double d[3], rgbp[3], dp, Tf;
   int ns;
-  cam_ray(&cd, x, y, d);
-  int64_t K = march(cd.o, d, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf, &ns, NULL,
+  double tn = cam_ray(&cd, x, y, d);
+  int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf, &ns, NULL,
                     NULL, 0, 0.0, NULL);
   int64_t m = K < max_out ? K : max_out;
   for (int64_t k = 0; k < m; ++k) {

@@ -64,7 +64,7 @@ def lib():
             I64, I32, D, F = C.c_int64, C.c_int, C.c_double, C.c_float
             _lib.ora_pairs.argtypes = [I64, P, I32, P, I32, I64, P, P, P, P, P, P, P]
             _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P]
-            _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P]
+            _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P, P]
             _lib.ora_trace_pixel.argtypes = [I64, P, P, P, I32, P, D, I32, I32, I64, P, P, P, P, P]
             _lib.ora_prune.argtypes = [I64, P, P, P, P, P, I32, I64, F, F, F, F, I64, I64, I64, P, P, P, P]
             _lib.ora_subdivide.argtypes = [I64, P, P, P, P, P, P, P, P, P, F, F, I64, I64, I32, I64, I64, I64,
@@ -164,7 +164,7 @@ def render(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, br
 
 
 def render_backward(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None, t_stop: float = 1e-4,
-                    sh_degree: int = 3) -> dict:
+                    sh_degree: int = 3, crop=None) -> dict:
     """FP64 gradients of sum(g_C . rgb + g_D depth + g_T T) w.r.t. corner densities and SH."""
     geom = _c(scene["geom"], np.float32)
     dens = _c(scene["density"], np.float32)
@@ -175,8 +175,9 @@ def render_backward(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None
     gT = None if dL_dT is None else _c(dL_dT, np.float64)
     dd = np.zeros((n, 8), np.float64)
     ds = np.zeros((n, 48), np.float64)
-    lib().ora_render_backward(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, _p(gC),
-                              _p(gD), _p(gT), _p(dd), _p(ds))
+    cr = None if crop is None else _c(np.asarray(crop).reshape(-1, 4), np.int32)
+    lib().ora_render_backward(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, _p(cr),
+                              _p(gC), _p(gD), _p(gT), _p(dd), _p(ds))
     return {"d_density": dd, "d_sh": ds}
 
 

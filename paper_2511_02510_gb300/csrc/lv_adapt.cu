@@ -93,16 +93,23 @@ __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t 
   }
 }
 
+// bin counts go through a block-local histogram (one global add per bin and block)
 __global__ void k_pr_bin(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z, int nb,
                          const SelectQuery* pct, uint16_t* grp, PruneState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i >= n || !seen[i]) return;
+  __shared__ uint32_t sh[SELECT_MAX_QUERIES];
+  if (threadIdx.x < SELECT_MAX_QUERIES) sh[threadIdx.x] = 0;
+  __syncthreads();
   const float p_lo = key_to_float(pct[0].result), p_hi = key_to_float(pct[1].result);
-  const float zt = depth_norm(z[i], p_lo, p_hi);
-  int b = (int)floorf(__fmul_rn((float)nb, zt));
-  if (b > nb - 1) b = nb - 1;
-  grp[i] = (uint16_t)b;
-  atomicAdd(&st->bin_cnt[b], 1u);
+  for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
+    if (!seen[i]) continue;
+    const float zt = depth_norm(z[i], p_lo, p_hi);
+    int b = (int)floorf(__fmul_rn((float)nb, zt));
+    if (b > nb - 1) b = nb - 1;
+    grp[i] = (uint16_t)b;
+    atomicAdd(&sh[b], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < nb && sh[threadIdx.x]) atomicAdd(&st->bin_cnt[threadIdx.x], sh[threadIdx.x]);
 }
 
 __global__ void k_pr_tau_queries(SelectQuery* q, const PruneState* st, int nb, uint32_t q_ppm) {
@@ -346,17 +353,6 @@ struct AuxSet {
   lv_aux_array a[LV_MAX_AUX];
 };
 
-__device__ __forceinline__ void aux_copy(const lv_aux_array& a, int64_t src, int64_t dst) {
-  const size_t row = (size_t)a.width * a.elem_bytes;
-  const char* s = (const char*)a.in + row * (size_t)src;
-  char* d = (char*)a.out + row * (size_t)dst;
-  if ((row & 3) == 0 && (((uintptr_t)s | (uintptr_t)d) & 3) == 0) {
-    for (size_t k = 0; k < row / 4; ++k) ((uint32_t*)d)[k] = ((const uint32_t*)s)[k];
-  } else {
-    for (size_t k = 0; k < row; ++k) d[k] = s[k];
-  }
-}
-
 __device__ __forceinline__ void aux_fill(const lv_aux_array& a, int64_t dst) {
   char* d = (char*)a.out + (size_t)a.width * a.elem_bytes * (size_t)dst;
   for (int e = 0; e < a.width; ++e) {
@@ -366,25 +362,59 @@ __device__ __forceinline__ void aux_fill(const lv_aux_array& a, int64_t dst) {
   }
 }
 
+// Copy the surviving rows of 32 consecutive voxels (one warp) of an array
+// whose rows are `row` bytes: the survivors of the group land on consecutive
+// output rows starting at `base`, so lanes stride over the group's bytes in
+// 16-, 4- or 1-byte words and both reads and writes coalesce.
+__device__ __forceinline__ void warp_copy_rows(const char* __restrict__ in, char* __restrict__ out, size_t row,
+                                               int64_t i0, int nrows, uint32_t keep, int64_t base, int lane) {
+  if (row % 16 == 0 && ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0) {
+    const int wpr = (int)(row / 16);
+    const uint4* s = (const uint4*)in + (size_t)i0 * wpr;
+    uint4* d = (uint4*)out;
+    for (int w = lane; w < nrows * wpr; w += 32) {
+      const int r = w / wpr, cw = w - r * wpr;
+      if ((keep >> r) & 1u) d[(size_t)(base + __popc(keep & ((1u << r) - 1u))) * wpr + cw] = s[w];
+    }
+  } else if (row % 4 == 0 && ((((uintptr_t)in) | ((uintptr_t)out)) & 3) == 0) {
+    const int wpr = (int)(row / 4);
+    const uint32_t* s = (const uint32_t*)in + (size_t)i0 * wpr;
+    uint32_t* d = (uint32_t*)out;
+    for (int w = lane; w < nrows * wpr; w += 32) {
+      const int r = w / wpr, cw = w - r * wpr;
+      if ((keep >> r) & 1u) d[(size_t)(base + __popc(keep & ((1u << r) - 1u))) * wpr + cw] = s[w];
+    }
+  } else {
+    const int wpr = (int)row;
+    const char* s = in + (size_t)i0 * wpr;
+    for (int w = lane; w < nrows * wpr; w += 32) {
+      const int r = w / wpr, cw = w - r * wpr;
+      if ((keep >> r) & 1u) out[(size_t)(base + __popc(keep & ((1u << r) - 1u))) * wpr + cw] = s[w];
+    }
+  }
+}
+
 template <typename DT, typename ST>
 __global__ void k_sd_write_survivors(int64_t n, const uint32_t* __restrict__ surv,
                                      const unsigned long long* __restrict__ pos, const SubState* st,
                                      const float4* __restrict__ geom, const uint8_t* __restrict__ level,
                                      const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
                                      uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i >= n || !surv[i] || !st->fits) return;
-  const int64_t o = (int64_t)pos[i];
-  ogeom[o] = geom[i];
-  olevel[o] = level[i];
-  // density rows are 32 B (f32) or 16 B (f16), SH rows 192 B or 96 B: copy as 16-byte words
-  const uint4* ds = (const uint4*)(dens + 8 * i);
-  uint4* dd = (uint4*)(odens + 8 * o);
-  for (int k = 0; k < (int)(8 * sizeof(DT) / 16); ++k) dd[k] = ds[k];
-  const uint4* ss = (const uint4*)(sh + 48 * i);
-  uint4* sd = (uint4*)(osh + 48 * o);
-  for (int k = 0; k < (int)(48 * sizeof(ST) / 16); ++k) sd[k] = ss[k];
-  for (int a = 0; a < aux.n; ++a) aux_copy(aux.a[a], i, o);
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = (blockIdx.x * (int64_t)TPB + threadIdx.x) & ~(int64_t)31;
+  if (i0 >= n || !st->fits) return;  // warp-uniform
+  const int64_t i = i0 + lane;
+  const uint32_t keep = __ballot_sync(FULL, i < n && surv[i] != 0);
+  if (!keep) return;
+  const int nrows = (int)min((int64_t)32, n - i0);
+  const int64_t base = (int64_t)pos[i0];
+  warp_copy_rows((const char*)geom, (char*)ogeom, 16, i0, nrows, keep, base, lane);
+  warp_copy_rows((const char*)level, (char*)olevel, 1, i0, nrows, keep, base, lane);
+  warp_copy_rows((const char*)dens, (char*)odens, 8 * sizeof(DT), i0, nrows, keep, base, lane);
+  warp_copy_rows((const char*)sh, (char*)osh, 48 * sizeof(ST), i0, nrows, keep, base, lane);
+  for (int a = 0; a < aux.n; ++a)
+    warp_copy_rows((const char*)aux.a[a].in, (char*)aux.a[a].out, (size_t)aux.a[a].width * aux.a[a].elem_bytes, i0,
+                   nrows, keep, base, lane);
 }
 
 template <typename DT>
@@ -475,7 +505,7 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w_max, w.grp, w.zkey, w.wkey, w.st);
   k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
-  k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, nb, w.q, w.grp, w.st);
+  k_pr_bin<<<blocks < 1216 ? blocks : 1216, TPB, 0, s>>>(n, seen, z, nb, w.q, w.grp, w.st);
   // the percentiles in q[0..1] are consumed by the binning: q is reused per bin
   k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm);
   select_kth(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);

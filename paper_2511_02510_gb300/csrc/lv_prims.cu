@@ -150,15 +150,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t* keys,
   }
 }
 
-// exclusive scan in place over RADIX * blocks counters (digit-major)
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* hist, int total) {
-  __shared__ uint32_t sw[32];
+// Per digit d (one block each): exclusive scan over the blocks' counts
+// hist[d * G + b] in place, and the digit's total in digit_tot[d].  The
+// downsweep adds the exclusive scan of the digit totals itself.
+__global__ void __launch_bounds__(SORT_BLOCKS) k_rs_scan_digits(uint32_t* hist, uint32_t* digit_tot) {
+  constexpr int NW = SORT_BLOCKS / 32;
+  __shared__ uint32_t sw[NW];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  int per = (total + 1023) / 1024;
-  int lo = t * per, hi = min(total, lo + per);
-  uint32_t s = 0;
-  for (int i = lo; i < hi; ++i) s += hist[i];
-  uint32_t x = s;
+  uint32_t* h = hist + (size_t)blockIdx.x * SORT_BLOCKS;
+  const uint32_t c = h[t];
+  uint32_t x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(FULL, x, o);
@@ -167,27 +168,24 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* hist, int total) {
   if (lane == 31) sw[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = sw[lane];
+    uint32_t w = lane < NW ? sw[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(FULL, w, o);
       if (lane >= o) w += y;
     }
-    sw[lane] = w;
+    if (lane < NW) sw[lane] = w;
   }
   __syncthreads();
-  uint32_t run = (warp ? sw[warp - 1] : 0u) + x - s;
-  for (int i = lo; i < hi; ++i) {
-    uint32_t c = hist[i];
-    hist[i] = run;
-    run += c;
-  }
+  h[t] = (warp ? sw[warp - 1] : 0u) + x - c;
+  if (t == SORT_BLOCKS - 1) digit_tot[blockIdx.x] = sw[NW - 1];
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin, const uint32_t* vin,
                                                             uint64_t* kout, uint32_t* vout,
                                                             const unsigned long long* d_count, int64_t cap,
-                                                            int shift, const uint32_t* hist) {
+                                                            int shift, const uint32_t* hist,
+                                                            const uint32_t* digit_tot) {
   __shared__ uint32_t s_goff[RADIX];          // next global slot per digit for this block
   __shared__ uint32_t s_wh[RS_WARPS][RADIX];  // per-warp digit counts -> warp prefixes
   __shared__ uint32_t s_cnt[RADIX];           // sub-tile digit counts
@@ -196,7 +194,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
   __shared__ uint32_t s_v[RS_TILE];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int d = t; d < RADIX; d += RS_THREADS) s_goff[d] = hist[d * gridDim.x + blockIdx.x];
+  {
+    // digit base = exclusive scan of the digit totals (RS_THREADS == RADIX)
+    __shared__ uint32_t sw0[RS_WARPS];
+    const uint32_t c = digit_tot[t];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sw0[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += sw0[w];
+    s_goff[t] = pre + x - c + hist[t * gridDim.x + blockIdx.x];
+  }
   int64_t n = rs_count(d_count, cap);
   int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
 
 }  // namespace
 
-size_t sort_hist_bytes() { return sizeof(uint32_t) * RADIX * SORT_BLOCKS; }
+size_t sort_hist_bytes() { return sizeof(uint32_t) * (RADIX * SORT_BLOCKS + RADIX); }
 int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 
 int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t* hist,
@@ -286,12 +299,13 @@ int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uin
   int passes = sort_passes(end_bit);
   uint64_t* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
+  uint32_t* digit_tot = hist + RADIX * SORT_BLOCKS;
   for (int p = 0; p < passes; ++p) {
     int src = p & 1, dst = src ^ 1;
     k_rs_upsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], d_count, cap, 8 * p, hist);
-    k_rs_scan<<<1, 1024, 0, s>>>(hist, RADIX * SORT_BLOCKS);
+    k_rs_scan_digits<<<RADIX, SORT_BLOCKS, 0, s>>>(hist, digit_tot);
     k_rs_downsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_count, cap, 8 * p,
-                                                      hist);
+                                                      hist, digit_tot);
   }
   count_launch(3 * passes);
   return passes & 1;

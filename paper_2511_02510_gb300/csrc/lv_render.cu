@@ -2,8 +2,9 @@
 // rasterizer (LiteVoxel Sec. III, Eq. 1-5) for sm_103a.
 //
 // Pipeline of lv_rasterize_forward (one stream, no host synchronisation):
-//   k_bin       per (voxel, view): FP32 cull / corner projection / tile rect /
-//               depth key with a fixed operation order; depth statistics.
+//   k_bin       per (voxel, view): FP32 cull / near-plane clipping / corner
+//               projection / tile rect / depth key with a fixed operation
+//               order; depth statistics.
 //   scan2       pair offsets and visible-slot ids (two-channel scan).
 //   k_emit      per visible (voxel, view): 64-byte render record (centre
 //               relative to the camera, half-size, 8 corner densities, SH
@@ -74,12 +75,14 @@ struct FwdWs {
   uint32_t* cnt;                 // [items] tiles covered
   uint32_t* vis;                 // [items] 1 if cnt > 0
   uint2* rect;                   // [items] (tx0 | tx1 << 16, ty0 | ty1 << 16)
+  uint2* pbox;                   // [items] conservative pixel box (x0 | x1 << 16, y0 | y1 << 16), [x0, x1)
+  uint2* rec_bb;                 // [slots] pixel box of the render record
   uint32_t* dkey;                // [items] order key of z_centre
   unsigned long long* pair_off;  // [items]
   uint32_t* slot;                // [items]
   void* scan_tmp;
   float4* rec;                   // [slots][4]
-  float* d_rgb;                  // [slots][3] backward scratch
+  float4* d_rgb;                 // [slots] colour gradient (xyz) scratch of the backward
   uint32_t* ranges;              // [tiles][2]
   float* tau;                    // [pixels] final optical depth
   uint32_t* hist;
@@ -100,12 +103,14 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   w.cnt = c.take<uint32_t>(items);
   w.vis = c.take<uint32_t>(items);
   w.rect = c.take<uint2>(items);
+  w.pbox = c.take<uint2>(items);
+  w.rec_bb = c.take<uint2>(items);
   w.dkey = c.take<uint32_t>(items);
   w.pair_off = c.take<unsigned long long>(items);
   w.slot = c.take<uint32_t>(items);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.rec = c.take<float4>(items * 4);
-  w.d_rgb = c.take<float>(items * 3);
+  w.d_rgb = c.take<float4>(items);
   w.ranges = c.take<uint32_t>(tiles * 2);
   w.tau = c.take<float>(pixels);
   w.hist = c.take<uint32_t>(sort_hist_bytes() / 4);
@@ -138,8 +143,8 @@ __device__ __forceinline__ void cam_point32(const DevView& c, float X, float Y, 
 
 __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, int64_t n,
                                              const __grid_constant__ ViewSet vs, uint32_t* cnt, uint32_t* vis,
-                                             uint2* rect, uint32_t* dkey, float* z_min, float* delta_min,
-                                             uint8_t* seen) {
+                                             uint2* rect, uint2* pbox, uint32_t* dkey, float* z_min,
+                                             float* delta_min, uint8_t* seen) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * vs.n) return;
   int64_t vox = i / vs.n;
@@ -149,9 +154,10 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
   float4 g = geom[vox];
   float qc[3];
   cam_point32(c, g.x, g.y, g.z, qc);
-  int n_front = 0, n_behind = 0;
+  int n_front = 0;
   float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
   bool first = true;
+  float px[8], py[8], pz[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     float X = (k & 1) ? __fadd_rn(g.x, g.w) : __fsub_rn(g.x, g.w);
@@ -159,9 +165,8 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     float Z = (k & 4) ? __fadd_rn(g.z, g.w) : __fsub_rn(g.z, g.w);
     float p[3];
     cam_point32(c, X, Y, Z, p);
-    if (p[2] < c.z_near) {
-      ++n_behind;
-    } else {
+    px[k] = p[0]; py[k] = p[1]; pz[k] = p[2];
+    if (p[2] >= c.z_near) {
       ++n_front;
       float u = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(p[0], p[2])), c.cx);
       float v = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(p[1], p[2])), c.cy);
@@ -170,26 +175,45 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     }
   }
   int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+  int px0 = 0, px1 = 0, py0 = 0, py1 = 0;  // pixels x in [px0, px1) may be hit (1-pixel margin)
   if (n_front > 0) {
-    if (n_behind > 0) {
-      tx1 = c.tiles_x;
-      ty1 = c.tiles_y;
-    } else {
-      float fts = (float)ts;
-      float a0 = floorf(__fdiv_rn(__fsub_rn(umin, 1.0f), fts));
-      float a1 = ceilf(__fdiv_rn(__fadd_rn(umax, 1.0f), fts));
-      float b0 = floorf(__fdiv_rn(__fsub_rn(vmin, 1.0f), fts));
-      float b1 = ceilf(__fdiv_rn(__fadd_rn(vmax, 1.0f), fts));
-      tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)c.tiles_x);
-      tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)c.tiles_x);
-      ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)c.tiles_y);
-      ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)c.tiles_y);
+    if (n_front < 8) {
+      // near-plane clipping: crossing points of the box edges (k, k|bit) with z = z_near
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int bit = 1; bit < 8; bit <<= 1) {
+          if (k & bit) continue;
+          const int j = k | bit;
+          if ((pz[k] >= c.z_near) == (pz[j] >= c.z_near)) continue;
+          const float f = __fdiv_rn(__fsub_rn(c.z_near, pz[k]), __fsub_rn(pz[j], pz[k]));
+          const float x = __fadd_rn(px[k], __fmul_rn(f, __fsub_rn(px[j], px[k])));
+          const float y = __fadd_rn(py[k], __fmul_rn(f, __fsub_rn(py[j], py[k])));
+          const float u = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(x, c.z_near)), c.cx);
+          const float v = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(y, c.z_near)), c.cy);
+          umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+        }
+      }
     }
+    const float fts = (float)ts;
+    const float a0 = floorf(__fdiv_rn(__fsub_rn(umin, 1.0f), fts));
+    const float a1 = ceilf(__fdiv_rn(__fadd_rn(umax, 1.0f), fts));
+    const float b0 = floorf(__fdiv_rn(__fsub_rn(vmin, 1.0f), fts));
+    const float b1 = ceilf(__fdiv_rn(__fadd_rn(vmax, 1.0f), fts));
+    tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)c.tiles_x);
+    tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)c.tiles_x);
+    ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)c.tiles_y);
+    ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)c.tiles_y);
+    px0 = (int)fminf(fmaxf(floorf(__fsub_rn(umin, 1.0f)), 0.0f), (float)c.W);
+    px1 = (int)fminf(fmaxf(ceilf(__fadd_rn(umax, 1.0f)), 0.0f), (float)c.W);
+    py0 = (int)fminf(fmaxf(floorf(__fsub_rn(vmin, 1.0f)), 0.0f), (float)c.H);
+    py1 = (int)fminf(fmaxf(ceilf(__fadd_rn(vmax, 1.0f)), 0.0f), (float)c.H);
   }
   uint32_t count = (tx1 > tx0 && ty1 > ty0) ? (uint32_t)(tx1 - tx0) * (uint32_t)(ty1 - ty0) : 0u;
   cnt[i] = count;
   vis[i] = count ? 1u : 0u;
   rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+  pbox[i] = make_uint2((uint32_t)px0 | ((uint32_t)px1 << 16), (uint32_t)py0 | ((uint32_t)py1 << 16));
   dkey[i] = order_key(qc[2]);
   if (count) {
     float zs = fmaxf(qc[2], c.z_near);
@@ -264,10 +288,11 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const ST* __restrict__ sh, int sh_nb, int64_t n,
                                               const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ cnt,
                                               const uint32_t* __restrict__ vis, const uint2* __restrict__ rect,
+                                              const uint2* __restrict__ pbox, uint2* __restrict__ rec_bb,
                                               const uint32_t* __restrict__ dkey,
                                               const unsigned long long* __restrict__ pair_off,
                                               const uint32_t* __restrict__ slot, float4* __restrict__ rec,
-                                              float* __restrict__ d_rgb, uint64_t* __restrict__ keys,
+                                              float4* __restrict__ d_rgb, uint64_t* __restrict__ keys,
                                               uint32_t* __restrict__ vals,
                                               int64_t pair_cap, int32_t* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -293,9 +318,8 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   r[1] = make_float4(d[0], d[1], d[2], d[3]);
   r[2] = make_float4(d[4], d[5], d[6], d[7]);
   r[3] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), __uint_as_float((uint32_t)vox));
-  d_rgb[3 * (size_t)s + 0] = 0.f;
-  d_rgb[3 * (size_t)s + 1] = 0.f;
-  d_rgb[3 * (size_t)s + 2] = 0.f;
+  d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  rec_bb[s] = pbox[i];
   unsigned long long off = pair_off[i];
   uint32_t count = cnt[i];
   if (off + count > (unsigned long long)pair_cap) {
@@ -336,6 +360,7 @@ struct Ray {
   float dx, dy, dz;     // unit direction
   float ix, iy, iz;     // 1 / direction (1e30 for a zero component)
   float ax, ay, az;     // |1 / direction|
+  float tnear;          // ray parameter of the near plane (camera depth z_near)
 };
 
 __device__ __forceinline__ Ray make_ray(const DevView& c, int px, int py) {
@@ -351,16 +376,18 @@ __device__ __forceinline__ Ray make_ray(const DevView& c, int px, int py) {
   r.iy = r.dy != 0.f ? __frcp_rn(r.dy) : 1e30f;
   r.iz = r.dz != 0.f ? __frcp_rn(r.dz) : 1e30f;
   r.ax = fabsf(r.ix); r.ay = fabsf(r.iy); r.az = fabsf(r.iz);
+  r.tnear = c.z_near * (wx * wx + wy * wy + wz * wz) * inv;  // z_near * |(dcx, dcy, 1)|
   return r;
 }
 
 // Chord of the ray (origin at the camera) through the box centred at rc
-// (relative to the camera) with half-size h.  Identical code in the forward
-// and backward kernels, so both take the same hit decisions.
+// (relative to the camera) with half-size h, clipped to start at the near
+// plane.  Identical code in the forward and backward kernels, so both take
+// the same hit decisions.
 __device__ __forceinline__ bool chord(const Ray& r, float4 g, float& t_in, float& t_out) {
   float qx = g.x * r.ix, qy = g.y * r.iy, qz = g.z * r.iz;
   float ex = g.w * r.ax, ey = g.w * r.ay, ez = g.w * r.az;
-  t_in = fmaxf(fmaxf(qx - ex, qy - ey), fmaxf(qz - ez, 0.f));
+  t_in = fmaxf(fmaxf(qx - ex, qy - ey), fmaxf(qz - ez, r.tnear));
   t_out = fminf(fminf(qx + ex, qy + ey), qz + ez);
   return t_out > t_in;
 }
@@ -400,23 +427,48 @@ __device__ __forceinline__ int find_view(const ViewSet& vs, int gtile) {
   return v;
 }
 
+// The pixels of a warp form a strip of the tile: 32 consecutive pixels in
+// row-major order (TS = 8: 4 rows of 8, 16: 2 rows of 16, 32: 1 row of 32).
+// A record whose conservative pixel box misses the strip cannot be hit by any
+// lane, so the whole warp skips it (a warp-uniform branch); the hit decisions
+// are exactly those of the per-lane chord test.
+template <int TS>
+struct Strip {
+  uint32_t x0, x1, y0, y1;  // [x0, x1) x [y0, y1) in image pixels
+  __device__ __forceinline__ Strip(int tile_x, int tile_y, int warp) {
+    constexpr int ROWS = 32 / TS;
+    x0 = (uint32_t)(tile_x * TS);
+    x1 = x0 + TS;
+    y0 = (uint32_t)(tile_y * TS + warp * ROWS);
+    y1 = y0 + ROWS;
+  }
+  // box: (bx0 | bx1 << 16, by0 | by1 << 16)
+  __device__ __forceinline__ bool misses(uint2 box) const {
+    return (box.x >> 16) <= x0 || (box.x & 0xffffu) >= x1 || (box.y >> 16) <= y0 || (box.y & 0xffffu) >= y1;
+  }
+};
+
 // ------------------------------------------------------------------ forward composite
 template <int TS, int B>
 __global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
-                                                float t_stop, float* __restrict__ rgb, float* __restrict__ depth,
+                                                const uint2* __restrict__ rec_bb, float t_stop,
+                                                float* __restrict__ rgb, float* __restrict__ depth,
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
                                                 float* __restrict__ tau_out, unsigned long long* __restrict__ wmax) {
   constexpr int NT = TS * TS;
   __shared__ float4 s_rec[B * 4];
+  __shared__ uint2 s_bb[B];
   __shared__ unsigned long long s_wm[B];
   const int tid = threadIdx.x, lane = tid & 31;
   const int gtile = blockIdx.x;
   const int view = find_view(vs, gtile);
   const DevView& c = vs.v[view];
   const int lt = gtile - c.tile_off;
-  const int px = (lt % c.tiles_x) * TS + tid % TS, py = (lt / c.tiles_x) * TS + tid / TS;
+  const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
+  const int px = tile_x * TS + tid % TS, py = tile_y * TS + tid / TS;
   const bool inside = px < c.W && py < c.H;
+  const Strip<TS> strip(tile_x, tile_y, tid >> 5);
   const Ray r = make_ray(c, px, py);
   const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
   const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
@@ -427,13 +479,17 @@ __global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet 
   for (uint32_t base = start; base < end; base += B) {
     const int cntb = (int)min((uint32_t)B, end - base);
     for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[base + (q >> 2)] + (q & 3)];
-    for (int q = tid; q < cntb; q += NT) s_wm[q] = 0ull;
+    for (int q = tid; q < cntb; q += NT) {
+      s_bb[q] = rec_bb[svals[base + q]];
+      s_wm[q] = 0ull;
+    }
     __syncthreads();
     if (!__all_sync(FULL, done)) {
       for (int j = 0; j < cntb; ++j) {
+        if (strip.misses(s_bb[j])) continue;  // warp-uniform
         const float4 g = s_rec[4 * j];
         float t_in, t_out;
-        bool hit = !done && chord(r, g, t_in, t_out);
+        const bool hit = !done && chord(r, g, t_in, t_out);
         float w = 0.f;
         if (hit) {
           const float4 d0 = s_rec[4 * j + 1], d1 = s_rec[4 * j + 2], col = s_rec[4 * j + 3];
@@ -452,20 +508,20 @@ __global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet 
           T *= e;
           last = base + j - start + 1;
         }
-        if (__any_sync(FULL, hit)) {
+        const unsigned any = __ballot_sync(FULL, hit);
+        if (any) {
           const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
           const uint32_t mx = __reduce_max_sync(FULL, v);
           const uint32_t who = __ballot_sync(FULL, v == mx);
-          if (lane == __ffs(who) - 1)
-            atomicMax(&s_wm[j], ((unsigned long long)(mx - 1u) << 32) | gid_key);
+          if (lane == __ffs(who) - 1) atomicMax(&s_wm[j], ((unsigned long long)(mx - 1u) << 32) | gid_key);
+          if (hit && T < t_stop) done = true;
         }
-        if (hit && T < t_stop) done = true;
       }
     }
     __syncthreads();
     if (wmax) {
       for (int q = tid; q < cntb; q += NT) {
-        unsigned long long m = s_wm[q];
+        const unsigned long long m = s_wm[q];
         if (m) atomicMax(&wmax[__float_as_uint(s_rec[4 * q + 3].w)], m);
       }
     }
@@ -520,14 +576,16 @@ __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
 template <int TS, int B>
 __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
-                                                const float* __restrict__ T_fwd, const float* __restrict__ tau_in,
+                                                const uint2* __restrict__ rec_bb, const float* __restrict__ T_fwd,
+                                                const float* __restrict__ tau_in,
                                                 const uint32_t* __restrict__ n_contrib,
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
-                                                float* __restrict__ d_rgb) {
+                                                float4* __restrict__ d_rgb) {
   constexpr int NT = TS * TS;
-  constexpr int NV = 12;  // 8 corners + 3 colour + 1 flag
+  constexpr int NV = 12;  // 8 corners + 3 colour + 1 "touched" flag
   __shared__ float4 s_rec[B * 4];
+  __shared__ uint2 s_bb[B];
   __shared__ uint32_t s_slot[B];
   __shared__ float s_acc[B * NV];
   __shared__ uint32_t s_max;
@@ -536,8 +594,10 @@ __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet 
   const int view = find_view(vs, gtile);
   const DevView& c = vs.v[view];
   const int lt = gtile - c.tile_off;
-  const int px = (lt % c.tiles_x) * TS + tid % TS, py = (lt / c.tiles_x) * TS + tid / TS;
+  const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
+  const int px = tile_x * TS + tid % TS, py = tile_y * TS + tid / TS;
   const bool inside = px < c.W && py < c.H;
+  const Strip<TS> strip(tile_x, tile_y, tid >> 5);
   const Ray r = make_ray(c, px, py);
   const uint32_t start = ranges[2 * gtile];
   const size_t p = (size_t)(c.pix_off + (long long)py * c.W + px);
@@ -556,26 +616,34 @@ __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet 
   if (tid == 0) s_max = 0;
   __syncthreads();
   {
-    uint32_t m = __reduce_max_sync(FULL, nc);
+    const uint32_t m = __reduce_max_sync(FULL, nc);
     if (lane == 0 && m) atomicMax(&s_max, m);
   }
   __syncthreads();
   const uint32_t top_all = start + s_max;
+  const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
+  const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
   const float tgT = Tf * gT;
   float S = 0.f;
   for (uint32_t top = top_all; top > start; top -= min((uint32_t)B, top - start)) {
     const uint32_t lo = top - min((uint32_t)B, top - start);
     const int cntb = (int)(top - lo);
     for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[lo + (q >> 2)] + (q & 3)];
-    for (int q = tid; q < cntb; q += NT) s_slot[q] = svals[lo + q];
+    for (int q = tid; q < cntb; q += NT) {
+      const uint32_t sl = svals[lo + q];
+      s_slot[q] = sl;
+      s_bb[q] = rec_bb[sl];
+    }
     for (int q = tid; q < cntb * NV; q += NT) s_acc[q] = 0.f;
     __syncthreads();
-    const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
-    if (__any_sync(FULL, lo < my_hi)) {
-      for (int j = cntb - 1; j >= 0; --j) {
+    if (lo < warp_hi) {
+      const int jmax = (int)min((uint32_t)cntb, warp_hi - lo);
+      for (int j = jmax - 1; j >= 0; --j) {
+        if (strip.misses(s_bb[j])) continue;  // warp-uniform
         const float4 g = s_rec[4 * j];
         float t_in, t_out;
-        bool hit = (lo + j) < my_hi && chord(r, g, t_in, t_out);
+        const bool hit = (lo + j) < my_hi && chord(r, g, t_in, t_out);
+        if (!__any_sync(FULL, hit)) continue;
         float v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = 0.f;
@@ -598,25 +666,23 @@ __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet 
           const float dr = sraw > 0.f ? ds : 0.f;
           const float ux = u[0], uy = u[1], uz = u[2];
           const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
-          const float a00 = my * mz, a10 = uy * mz, a01 = my * uz, a11 = uy * uz;
-          v[0] = dr * mx * a00;
-          v[1] = dr * ux * a00;
-          v[2] = dr * mx * a10;
-          v[3] = dr * ux * a10;
-          v[4] = dr * mx * a01;
-          v[5] = dr * ux * a01;
-          v[6] = dr * mx * a11;
-          v[7] = dr * ux * a11;
+          const float a00 = dr * my * mz, a10 = dr * uy * mz, a01 = dr * my * uz, a11 = dr * uy * uz;
+          v[0] = mx * a00;
+          v[1] = ux * a00;
+          v[2] = mx * a10;
+          v[3] = ux * a10;
+          v[4] = mx * a01;
+          v[5] = ux * a01;
+          v[6] = mx * a11;
+          v[7] = ux * a11;
           v[8] = w * gr;
           v[9] = w * gg;
           v[10] = w * gb;
           v[11] = 1.f;
         }
-        if (__any_sync(FULL, hit)) {
-          const float sum = warp_reduce16(v, lane);
-          const int idx = lane >> 1;
-          if (!(lane & 1) && idx < NV) atomicAdd(&s_acc[j * NV + idx], sum);
-        }
+        const float sum = warp_reduce16(v, lane);
+        const int idx = lane >> 1;
+        if (!(lane & 1) && idx < NV) atomicAdd(&s_acc[j * NV + idx], sum);
       }
     }
     __syncthreads();
@@ -627,10 +693,7 @@ __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet 
       float* dd = d_density + 8 * (size_t)vox;
       red_add_v4(dd, a[0], a[1], a[2], a[3]);
       red_add_v4(dd + 4, a[4], a[5], a[6], a[7]);
-      float* dc = d_rgb + 3 * (size_t)s_slot[q];
-      red_add(dc + 0, a[8]);
-      red_add(dc + 1, a[9]);
-      red_add(dc + 2, a[10]);
+      red_add_v4((float*)(d_rgb + s_slot[q]), a[8], a[9], a[10], 0.f);
     }
     __syncthreads();
   }
@@ -641,7 +704,7 @@ template <typename ST>
 __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, const ST* __restrict__ sh, int sh_nb,
                                                 int64_t n, const __grid_constant__ ViewSet vs,
                                                 const uint32_t* __restrict__ vis, const uint32_t* __restrict__ slot,
-                                                float* __restrict__ d_rgb, float* __restrict__ d_sh,
+                                                float4* __restrict__ d_rgb, float* __restrict__ d_sh,
                                                 int accumulate) {
   int64_t vox = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (vox >= n) return;
@@ -661,13 +724,11 @@ __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom,
     sh_basis(dir[0], dir[1], dir[2], Y);
     float raw[3];
     sh_raw(sh + 48 * vox, sh_nb, Y, raw);
-    float* dc = d_rgb + 3 * (size_t)s;
-    const float dr = raw[0] > 0.f ? dc[0] : 0.f;
-    const float dg = raw[1] > 0.f ? dc[1] : 0.f;
-    const float db = raw[2] > 0.f ? dc[2] : 0.f;
-    dc[0] = 0.f;  // leave the scratch cleared for the next backward call
-    dc[1] = 0.f;
-    dc[2] = 0.f;
+    const float4 dc = d_rgb[s];
+    const float dr = raw[0] > 0.f ? dc.x : 0.f;
+    const float dg = raw[1] > 0.f ? dc.y : 0.f;
+    const float db = raw[2] > 0.f ? dc.z : 0.f;
+    d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);  // leave the scratch cleared for the next backward call
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       if (j < sh_nb) {
@@ -761,8 +822,9 @@ template <int TS>
 static void launch_fwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                        float t_stop, const lv_fwd_out* out) {
   dim3 grid((unsigned)tiles), block(TS * TS);
-#define LV_FWD(BB) k_fwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, t_stop, out->rgb, out->depth, out->T, \
-                                                       out->n_contrib, w.tau, out->wmax_packed)
+#define LV_FWD(BB)                                                                                          \
+  k_fwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, t_stop, out->rgb, out->depth, out->T, \
+                                       out->n_contrib, w.tau, out->wmax_packed)
   if (B == 64) LV_FWD(64);
   else if (B == 128) LV_FWD(128);
   else LV_FWD(256);
@@ -773,8 +835,9 @@ template <int TS>
 static void launch_bwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                        const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
   dim3 grid((unsigned)tiles), block(TS * TS);
-#define LV_BWD(BB) k_bwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, fwd->T, w.tau, fwd->n_contrib, gC, gD, \
-                                                       gT, dd, w.d_rgb)
+#define LV_BWD(BB)                                                                                              \
+  k_bwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, fwd->T, w.tau, fwd->n_contrib, gC, gD, gT, \
+                                       dd, w.d_rgb)
   if (B == 64) LV_BWD(64);
   else if (B == 128) LV_BWD(128);
   else LV_BWD(256);
@@ -816,14 +879,14 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   if (!d_status || d_status == w.status) cudaMemsetAsync(w.status, 0, sizeof(int32_t), s);
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
-    k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.dkey, out->z_min,
+    k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.dkey, out->z_min,
                                  out->delta_min, out->seen);
     scan2(w.cnt, w.vis, items, w.pair_off, w.slot, w.counters, w.scan_tmp, s);
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                               \
   k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
-                                        vs, w.cnt, w.vis, w.rect, w.dkey, w.pair_off, w.slot, w.rec, w.d_rgb, w.k0,   \
-                                        w.v0, pair_capacity, d_status)
+                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.dkey, w.pair_off, w.slot,      \
+                                        w.rec, w.d_rgb, w.k0, w.v0, pair_capacity, d_status)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
@@ -856,6 +919,22 @@ extern "C" lv_status lv_workspace_counters(const void* workspace, size_t ws_byte
   return LV_OK;
 }
 
+static lv_status launch_sh_bwd(const lv_voxels* vox, const ViewSet& vs, const FwdWs& w, float* d_sh, int accumulate,
+                               cudaStream_t s) {
+  const int64_t n = vox->n;
+  if (n == 0) return LV_OK;
+  const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
+  const int blocks = (int)((n + 127) / 128);
+  if (vox->sh_dtype == LV_F32)
+    k_sh_bwd<float><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const float*)vox->sh, nb, n, vs, w.vis, w.slot,
+                                           w.d_rgb, d_sh, accumulate);
+  else
+    k_sh_bwd<__nv_bfloat16><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const __nv_bfloat16*)vox->sh, nb, n,
+                                                   vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
+  count_launch(1);
+  return LV_OK;
+}
+
 extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera* cams, int n_views,
                                            const lv_raster_opts* opts, const lv_fwd_out* fwd, void* workspace,
                                            size_t ws_bytes, int64_t pair_capacity, const float* dL_drgb,
@@ -863,7 +942,7 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
                                            int accumulate, int32_t* d_status, void* stream) {
   lv_status st = check_common(vox, cams, n_views, opts);
   if (st != LV_OK) return st;
-  if (!fwd || !fwd->T || !fwd->n_contrib || !dL_drgb || !d_density || !d_sh) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (!fwd || !fwd->T || !fwd->n_contrib || !dL_drgb || !d_density) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
   if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
   if (pair_capacity < 0 || pair_capacity > 0xffffffffLL) { set_error("pair_capacity out of range"); return LV_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -881,18 +960,24 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
   else if (opts->tile == 16) launch_bwd<16>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
   else launch_bwd<32>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
   count_launch(1);
-  if (n > 0) {
-    const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
-    const int blocks = (int)((n + 127) / 128);
-    if (vox->sh_dtype == LV_F32)
-      k_sh_bwd<float><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const float*)vox->sh, nb, n, vs, w.vis,
-                                             w.slot, w.d_rgb, d_sh, accumulate);
-    else
-      k_sh_bwd<__nv_bfloat16><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const __nv_bfloat16*)vox->sh, nb, n,
-                                                     vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
-    count_launch(1);
-  }
+  if (d_sh) launch_sh_bwd(vox, vs, w, d_sh, accumulate, s);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_backward");
+}
+
+extern "C" lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_views,
+                                    const lv_raster_opts* opts, void* workspace, size_t ws_bytes,
+                                    int64_t pair_capacity, float* d_sh, int accumulate, void* stream) {
+  lv_status st = check_common(vox, cams, n_views, opts);
+  if (st != LV_OK) return st;
+  if (!d_sh || !workspace || ((uintptr_t)workspace & 255)) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  ViewSet vs;
+  int64_t tiles, pixels;
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
+  FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  launch_sh_bwd(vox, vs, w, d_sh, accumulate, s);
+  return cuda_check(cudaGetLastError(), "lv_sh_backward");
 }
 
 extern "C" lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n, float* w_max, int64_t* argmax,

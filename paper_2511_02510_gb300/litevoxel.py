@@ -87,6 +87,7 @@ SIGNATURES = {
     "lv_workspace_counters": (C.c_int, [_P, _SZ, C.POINTER(C.c_int64), _P]),
     "lv_rasterize_backward": (C.c_int, [_PV, _PC, C.c_int, _PO, _PF, _P, _SZ, _I64, _P, _P, _P, _P, _P, C.c_int, _P,
                                         _P]),
+    "lv_sh_backward": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, C.c_int, _P]),
     "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
     "lv_debug_pairs": (C.c_int, [_I64, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _P, _P, _P]),
     "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
@@ -215,6 +216,12 @@ def lv_rasterize_backward(vox, cams_arr, n_views, opts, fwd, workspace, pair_cap
                                         _ptr(workspace), workspace.numel() * workspace.element_size(), pair_capacity,
                                         _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dT), _ptr(d_density), _ptr(d_sh),
                                         int(bool(accumulate)), _ptr(d_status), _stream()), "lv_rasterize_backward")
+
+
+def lv_sh_backward(vox, cams_arr, n_views, opts, workspace, pair_capacity, d_sh, accumulate=False):
+    _check(load().lv_sh_backward(C.byref(vox), cams_arr, n_views, C.byref(opts), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), pair_capacity, _ptr(d_sh),
+                                 int(bool(accumulate)), _stream()), "lv_sh_backward")
 
 
 def lv_unpack_wmax(packed, w_max, argmax=None):

@@ -5,7 +5,7 @@ Tolerances (from the arithmetic):
  - images: within 1e-5 max-abs of the FP64 oracle, plus the oracle's per-pixel
    FP32 sensitivity bound (a chord's length moves with sub-ulp shifts of the
    ray at grazing incidence and at large distances); pixels whose bound is
-   below 1e-6 must meet 1e-5 outright, and at most 1 % of pixels may exceed it;
+   below 1e-6 must meet 1e-5 outright, and the mean error stays below 2e-6;
  - integer outputs (pair lists, tile ranges, seen, FP32-pinned statistics):
    bit-exact;
  - gradients: within 1e-4 of the oracle's, relative to the largest gradient
@@ -56,11 +56,11 @@ def compare_images(ora_r, ctx, tol=IMG_TOL, rgb=None, T=None, depth=None, mask=N
     assert np.all(e_rgb[ok] <= tol + ora_r["bound_rgb"][ok]), (e_rgb - ora_r["bound_rgb"])[ok].max()
     assert np.all(e_T[ok] <= tol + ora_r["bound_T"][ok]), (e_T - ora_r["bound_T"])[ok].max()
     assert np.all(e_d[ok] <= tol * dscale + ora_r["bound_depth"][ok])
-    # well-conditioned pixels meet 1e-5 outright; few pixels exceed it at all
+    # well-conditioned pixels meet 1e-5 outright, and the typical error is far below it
     well = ok & (ora_r["bound_rgb"] < 1e-6) & (ora_r["bound_T"] < 1e-6)
     if well.any():
         assert e_rgb[well].max() < tol and e_T[well].max() < tol
-    assert (e_rgb[ok] > tol).mean() <= 0.01 and (e_T[ok] > tol).mean() <= 0.01
+    assert e_rgb[ok].mean() < 0.2 * tol and e_T[ok].mean() < 0.2 * tol
     return float(e_rgb[ok].max()), float(e_T[ok].max())
 
 

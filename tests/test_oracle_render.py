@@ -344,3 +344,50 @@ def test_fp32_sensitivity_bound_covers_ulp_perturbations(ora):
         assert np.all(d_rgb[ok] <= r0["bound_rgb"][ok] + 1e-12), (trial, (d_rgb - r0["bound_rgb"])[ok].max())
         assert np.all(d_T[ok] <= r0["bound_T"][ok] + 1e-12)
         assert d_rgb[ok].max() > 0            # the perturbation did change the image
+
+
+def test_near_plane_clips_the_chord(ora):
+    # A voxel crossing the near plane contributes only its part beyond it:
+    # on the axis ray the chord runs from z_near to the far face.
+    cam = axis_camera()
+    cam["z_near"] = 0.5
+    sc = synth.constant_voxel_scene([[0.0, 0.0, 0.6]], 0.3, [2.0], [(1, 1, 1)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    l = 0.9 - 0.5
+    assert abs(r["T"][4] - math.exp(-2.0 * l)) < 1e-7   # z_near and h are FP32 values
+    assert r["n_hit"][4] == 1
+
+
+def test_near_plane_straddler_tiles_cover_hits(ora):
+    # The clipped FP32 rectangle of voxels crossing the near plane still covers every
+    # pixel whose ray meets the voxel beyond the plane (dense sampling of the inside predicate).
+    rng = np.random.default_rng(12)
+    n = 30
+    centers = np.c_[rng.uniform(-0.4, 0.4, n), rng.uniform(-0.3, 0.3, n), rng.uniform(0.1, 0.5, n)]
+    half = rng.uniform(0.05, 0.25, n)
+    sc = synth.constant_voxel_scene(centers, half, np.ones(n), np.ones((n, 3)) * 0.5)
+    cam = axis_camera(48, 40, 30.0)
+    cam["z_near"] = 0.3
+    pr = ora.pairs(sc, [cam], ts=8)
+    tiles_x = (48 + 7) // 8
+    cover = {}
+    for k, v in zip(pr["keys"], pr["vals"]):
+        cover.setdefault(int(v), set()).add(int(k >> np.uint64(32)))
+    g = sc["geom"].astype(np.float64)
+    checked, straddlers = 0, set()
+    for i in range(n):
+        if g[i, 2] - g[i, 3] < 0.3 < g[i, 2] + g[i, 3]:
+            straddlers.add(i)
+    for y in range(40):
+        for x in range(48):
+            o, d = ray_of(cam, x, y)
+            t = np.linspace(0.3 / d[2], 3.0, 2701)            # beyond the near plane only
+            pts = o[None] + t[:, None] * d[None]
+            inside = np.all(np.abs(pts[:, None, :] - g[None, :, :3]) < g[None, :, 3:4], axis=2).any(axis=0)
+            tile = (y // 8) * tiles_x + x // 8
+            for i in np.where(inside)[0]:
+                assert tile in cover.get(int(i), set()), (i, x, y)
+                checked += int(i) in straddlers
+    assert checked > 50
+    # and a straddler no longer covers the whole image
+    assert any(len(cover.get(i, ())) < ((48 + 7) // 8) * ((40 + 7) // 8) for i in straddlers)
