@@ -286,6 +286,29 @@ lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* 
                               int n_views, float t, const lv_lf_params* p, float* loss, float* dL_drgb,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of lv_lf_weighted_loss.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory
+ * themselves -- for instance code running as a plugin inside a host
+ * application that owns every device allocation, or a latency-critical loop
+ * that must not call cudaMalloc, which can synchronise the whole device.
+ * The caller still passes the inputs and outputs; the scratch space lives in
+ * one fixed device array of LV_LF_NOALLOC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *  - Limit: the call needs lv_lf_workspace_size(widths, heights, n_views)
+ *    <= LV_LF_NOALLOC_SCRATCH_BYTES (about 1.6 million pixels over all
+ *    views); larger requests return LV_ERR_INVALID_ARG without launching.
+ *  - The first call on each device looks up the array's device address once
+ *    (with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array: calls that overlap on the GPU (for
+ *    example on two streams at once) race and give wrong results.  Each call
+ *    clears the parts of the array that must start at zero.
+ * Arguments and results are those of lv_lf_weighted_loss. */
+#define LV_LF_NOALLOC_SCRATCH_BYTES (16u << 20)
+lv_status lv_lf_weighted_loss_noalloc(const float* rgb, const float* gt, const int32_t* widths,
+                                      const int32_t* heights, int n_views, float t, const lv_lf_params* p,
+                                      float* loss, float* dL_drgb, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* misc                                                                 */
 /* ------------------------------------------------------------------ */

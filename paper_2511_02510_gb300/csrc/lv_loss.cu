@@ -3,6 +3,8 @@
 // truth luma (stop-gradient), exact nearest-rank percentile normalisation by a
 // radix select, inverse-Sobel weight (eps + 1 - s)^gamma, mean normalisation,
 // weighted squared error and its gradient.  Sums are accumulated in FP64.
+#include <mutex>
+
 #include "lv_prims.cuh"
 
 namespace lv {
@@ -209,4 +211,53 @@ extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, cons
   k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
   count_launch(3 + 2 * n_views);
   return cuda_check(cudaGetLastError(), "lv_lf_weighted_loss");
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// For callers that cannot allocate device memory themselves: the scratch that
+// lv_lf_weighted_loss takes from a caller workspace comes from this fixed
+// array instead.  Every device that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_lf_scratch[LV_LF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_lf_scratch_mu;
+void* g_lf_scratch_ptr[256] = {};  // device address of g_lf_scratch per device ordinal
+
+// The array's name is a host-side stand-in in host code; its device address is
+// looked up once per device, with that device current.
+lv_status lf_scratch_address(void** out) {
+  int dev = 0;
+  lv_status e = cuda_check(cudaGetDevice(&dev), "lv_lf_weighted_loss_noalloc: cudaGetDevice");
+  if (e != LV_OK) return e;
+  if (dev < 0 || dev >= 256) { set_error("lv_lf_weighted_loss_noalloc: device ordinal %d unsupported", dev); return LV_ERR_UNSUPPORTED; }
+  std::lock_guard<std::mutex> lock(g_lf_scratch_mu);
+  if (!g_lf_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cuda_check(cudaGetSymbolAddress(&ptr, g_lf_scratch), "lv_lf_weighted_loss_noalloc: cudaGetSymbolAddress");
+    if (e != LV_OK) return e;
+    g_lf_scratch_ptr[dev] = ptr;
+  }
+  *out = g_lf_scratch_ptr[dev];
+  return LV_OK;
+}
+}  // namespace
+
+extern "C" lv_status lv_lf_weighted_loss_noalloc(const float* rgb, const float* gt, const int32_t* widths,
+                                                 const int32_t* heights, int n_views, float t, const lv_lf_params* p,
+                                                 float* loss, float* dL_drgb, void* stream) {
+  const size_t need = lv_lf_workspace_size(widths, heights, n_views);
+  if (need == 0) { set_error("lv_lf_weighted_loss_noalloc: bad view sizes"); return LV_ERR_INVALID_ARG; }
+  if (need > sizeof(g_lf_scratch)) {
+    set_error("lv_lf_weighted_loss_noalloc: these views need %zu bytes of scratch, the fixed array holds %zu "
+              "(about 1.6 million pixels); use lv_lf_weighted_loss with a workspace instead",
+              need, sizeof(g_lf_scratch));
+    return LV_ERR_INVALID_ARG;
+  }
+  void* scratch = nullptr;
+  lv_status e = lf_scratch_address(&scratch);
+  if (e != LV_OK) return e;
+  // lv_lf_weighted_loss clears its accumulators and selection histograms in the
+  // scratch at the start of every call, so nothing else has to be zeroed here.
+  return lv_lf_weighted_loss(rgb, gt, widths, heights, n_views, t, p, loss, dL_drgb, scratch, sizeof(g_lf_scratch),
+                             stream);
 }

@@ -99,6 +99,7 @@ SIGNATURES = {
     "lv_lf_gamma": (_F, [_F, C.POINTER(lv_lf_params)]),
     "lv_lf_workspace_size": (_SZ, [_P, _P, C.c_int]),
     "lv_lf_weighted_loss": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P, _SZ, _P]),
+    "lv_lf_weighted_loss_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P]),
     "lv_last_error": (C.c_char_p, []),
     "lv_version": (C.c_int32, []),
     "lv_launch_count": (C.c_int64, []),
@@ -275,3 +276,14 @@ def lv_lf_weighted_loss(rgb, gt, widths, heights, t, params, loss, dL_drgb, work
     _check(load().lv_lf_weighted_loss(_ptr(rgb), _ptr(gt), w, h, len(widths), float(t), C.byref(params), _ptr(loss),
                                       _ptr(dL_drgb), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                       _stream()), "lv_lf_weighted_loss")
+
+
+LV_LF_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def lv_lf_weighted_loss_noalloc(rgb, gt, widths, heights, t, params, loss, dL_drgb):
+    """Allocation-free LF loss: the library's fixed scratch array replaces the workspace."""
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    _check(load().lv_lf_weighted_loss_noalloc(_ptr(rgb), _ptr(gt), w, h, len(widths), float(t), C.byref(params),
+                                              _ptr(loss), _ptr(dL_drgb), _stream()), "lv_lf_weighted_loss_noalloc")
