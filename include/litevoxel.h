@@ -89,7 +89,7 @@ typedef struct {
 
 typedef struct {
   int32_t tile;           /* tile edge in pixels: 8, 16 or 32 */
-  int32_t batch;          /* voxel records staged per shared-memory batch: 64, 128 or 256 */
+  int32_t batch;          /* reserved (64, 128 or 256): records are staged in 32-entry chunks per warp */
   int32_t threads_per_px; /* 1 (reserved) */
   float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
   uint32_t flags;         /* LV_FLAG_* */
@@ -107,6 +107,7 @@ typedef struct {
   float* delta_min;                  /* [n] min over views of max(z_centre, z_near) / fx, the inter-ray
                                         spacing at the voxel (Sec. III); caller sets +inf; nullable */
   uint8_t* seen;                     /* [n] set to 1 when the voxel covers >= 1 tile of some view; nullable */
+  uint32_t* n_samples;               /* [P] samples composited per pixel (hits of Eq. 2-4); nullable */
 } lv_fwd_out;
 
 /* ------------------------------------------------------------------ */

@@ -82,8 +82,9 @@ __global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const flo
     zkey[i] = order_key(z[i]);
     wkey[i] = order_key(w_max[i]);
   }
-  unsigned b = __ballot_sync(FULL, s);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->ns, (unsigned)__popc(b));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int b = __syncthreads_count(s);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->ns, (unsigned)b);
 }
 
 __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm) {
@@ -137,8 +138,9 @@ __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const u
     }
     cand_grp[i] = cand ? 0 : GROUP_NONE;
   }
-  unsigned bl = __ballot_sync(FULL, cand);
-  if ((threadIdx.x & 31) == 0 && bl) atomicAdd(&st->n_cand, (unsigned)__popc(bl));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int bl = __syncthreads_count(cand);
+  if (threadIdx.x == 0 && bl) atomicAdd(&st->n_cand, (unsigned)bl);
 }
 
 __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
@@ -159,8 +161,9 @@ __global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const Se
     lt = wkey[i] < v;
     cand_grp[i] = wkey[i] == v ? 0 : GROUP_NONE;
   }
-  unsigned bl = __ballot_sync(FULL, lt);
-  if ((threadIdx.x & 31) == 0 && bl) atomicAdd(&st->c_lt, (unsigned)__popc(bl));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int bl = __syncthreads_count(lt);
+  if (threadIdx.x == 0 && bl) atomicAdd(&st->c_lt, (unsigned)bl);
 }
 
 __global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, const PruneState* st, uint32_t cap) {
@@ -208,6 +211,7 @@ struct SubWs {
   uint32_t* sel;
   unsigned long long* surv_pos;
   uint32_t* sel_rank;
+  uint32_t* sel_list;  // [k] selected parent ids in id order
   unsigned long long* totals;
   void* scan_tmp;
   size_t bytes;
@@ -226,6 +230,7 @@ SubWs carve_sub(void* base, int64_t n) {
   w.sel = c.take<uint32_t>(n);
   w.surv_pos = c.take<unsigned long long>(n);
   w.sel_rank = c.take<uint32_t>(n);
+  w.sel_list = c.take<uint32_t>(n);
   w.totals = c.take<unsigned long long>(4);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.bytes = c.off + 256;
@@ -241,8 +246,9 @@ __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const ui
     grp[i] = (alive && seen[i]) ? 0 : GROUP_NONE;
     zkey[i] = order_key(z[i]);
   }
-  unsigned b = __ballot_sync(FULL, alive);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->n_alive, (unsigned)__popc(b));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int b = __syncthreads_count(alive);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->n_alive, (unsigned)b);
 }
 
 __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter) {
@@ -256,8 +262,9 @@ __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_pp
 __global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, uint32_t* counter) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool f = i < n && grp[i] == 0;
-  unsigned b = __ballot_sync(FULL, f);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(counter, (unsigned)__popc(b));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int b = __syncthreads_count(f);
+  if (threadIdx.x == 0 && b) atomicAdd(counter, (unsigned)b);
 }
 
 // Eq. 13 eligibility and Eq. 15-16 priority; pkey orders by descending priority
@@ -280,8 +287,9 @@ __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const 
     }
     grp[i] = el ? 0 : GROUP_NONE;
   }
-  unsigned b = __ballot_sync(FULL, el);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->n_el, (unsigned)__popc(b));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int b = __syncthreads_count(el);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->n_el, (unsigned)b);
 }
 
 __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget) {
@@ -309,8 +317,9 @@ __global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const Se
       grp[i] = GROUP_NONE;
     }
   }
-  unsigned b = __ballot_sync(FULL, gt);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->c_gt, (unsigned)__popc(b));
+  // one atomic per block (a same-address atomic per warp serialises at the L2)
+  const int b = __syncthreads_count(gt);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->c_gt, (unsigned)b);
 }
 
 __global__ void k_sd_tie_query(SelectQuery* q, const SubState* st) {
@@ -354,7 +363,13 @@ struct AuxSet {
 };
 
 __device__ __forceinline__ void aux_fill(const lv_aux_array& a, int64_t dst) {
-  char* d = (char*)a.out + (size_t)a.width * a.elem_bytes * (size_t)dst;
+  const size_t row = (size_t)a.width * a.elem_bytes;
+  char* d = (char*)a.out + row * (size_t)dst;
+  if (a.elem_bytes == 4 && (row & 15) == 0 && ((uintptr_t)d & 15) == 0) {
+    const uint4 f = make_uint4(a.fill, a.fill, a.fill, a.fill);
+    for (size_t k = 0; k < row / 16; ++k) ((uint4*)d)[k] = f;
+    return;
+  }
   for (int e = 0; e < a.width; ++e) {
     if (a.elem_bytes == 4) ((uint32_t*)d)[e] = a.fill;
     else if (a.elem_bytes == 2) ((uint16_t*)d)[e] = (uint16_t)a.fill;
@@ -429,19 +444,26 @@ __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
   return __fadd_rn(__fmul_rn(a, __fsub_rn(1.0f, t)), __fmul_rn(b, t));
 }
 
+__global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uint32_t* __restrict__ rank,
+                          uint32_t* __restrict__ list) {
+  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i < n && sel[i]) list[rank[i]] = (uint32_t)i;
+}
+
+// one thread per child: consecutive threads write consecutive output rows
 template <typename DT, typename ST>
-__global__ void k_sd_write_children(int64_t n, const uint32_t* __restrict__ sel,
-                                    const uint32_t* __restrict__ rank, const unsigned long long* totals,
-                                    const SubState* st, const float4* __restrict__ geom,
-                                    const uint8_t* __restrict__ level, const DT* __restrict__ dens,
-                                    const ST* __restrict__ sh, float4* ogeom, uint8_t* olevel, DT* odens, ST* osh,
-                                    const __grid_constant__ AuxSet aux) {
-  // one thread per (parent, child)
-  int64_t t = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  int64_t i = t >> 3;
-  int c = (int)(t & 7);
-  if (i >= n || !sel[i] || !st->fits) return;
-  const int64_t o = (int64_t)totals[0] + 8 * (int64_t)rank[i] + c;
+__global__ void k_sd_write_children(int64_t max_children, const uint32_t* __restrict__ list,
+                                    const unsigned long long* totals, const SubState* st,
+                                    const float4* __restrict__ geom, const uint8_t* __restrict__ level,
+                                    const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
+                                    uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
+  const int64_t t = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (t >= max_children || !st->fits) return;
+  const int64_t k = (int64_t)totals[1];
+  if (t >= 8 * k) return;
+  const int64_t i = list[t >> 3];
+  const int c = (int)(t & 7);
+  const int64_t o = (int64_t)totals[0] + t;
   const float4 g = geom[i];
   const float hc = __fmul_rn(g.w, 0.5f);
   ogeom[o] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
@@ -449,7 +471,7 @@ __global__ void k_sd_write_children(int64_t n, const uint32_t* __restrict__ sel,
   olevel[o] = (uint8_t)(level[i] + 1);
   float d[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * i + k]);
+  for (int q = 0; q < 8; ++q) d[q] = to_f32(dens[8 * i + q]);
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
@@ -462,7 +484,8 @@ __global__ void k_sd_write_children(int64_t n, const uint32_t* __restrict__ sel,
   }
   const uint4* ss = (const uint4*)(sh + 48 * i);
   uint4* sd = (uint4*)(osh + 48 * o);
-  for (int k = 0; k < (int)(48 * sizeof(ST) / 16); ++k) sd[k] = ss[k];
+#pragma unroll
+  for (int q = 0; q < (int)(48 * sizeof(ST) / 16); ++q) sd[q] = ss[q];
   for (int a = 0; a < aux.n; ++a) aux_fill(aux.a[a], o);
 }
 
@@ -584,14 +607,18 @@ extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* del
                                       p->kappa, p->l_max, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out->n, d_n_new, d_status ? d_status : (int32_t*)nullptr);
-  const int cblocks = blocks_for(8 * n);
+  // children: at most floor(top * n) splits
+  const int64_t max_children = 8 * (int64_t)(((unsigned long long)p->top_ppm * (unsigned long long)n) / 1000000ull);
+  const int cblocks = blocks_for(max_children);
+  k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
 #define LV_SUB(DT, ST)                                                                                                \
   do {                                                                                                                \
     k_sd_write_survivors<DT, ST><<<blocks, TPB, 0, s>>>(n, w.surv, w.surv_pos, w.st, (const float4*)in->geom,        \
                                                         in->level, (const DT*)in->density, (const ST*)in->sh,         \
                                                         (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
                                                         (ST*)out->sh, as);                                            \
-    k_sd_write_children<DT, ST><<<cblocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.totals, w.st, (const float4*)in->geom, \
+    k_sd_write_children<DT, ST><<<cblocks, TPB, 0, s>>>(max_children, w.sel_list, w.totals, w.st,                    \
+                                                        (const float4*)in->geom,                                      \
                                                         in->level, (const DT*)in->density, (const ST*)in->sh,         \
                                                         (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
                                                         (ST*)out->sh, as);                                            \
@@ -601,6 +628,6 @@ extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* del
   else if (in->density_dtype == LV_F32 && in->sh_dtype == LV_BF16) LV_SUB(float, __nv_bfloat16);
   else LV_SUB(__half, __nv_bfloat16);
 #undef LV_SUB
-  count_launch(12);
+  count_launch(13);
   return cuda_check(cudaGetLastError(), "lv_subdivide_priority");
 }

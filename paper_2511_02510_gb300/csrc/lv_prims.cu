@@ -316,24 +316,55 @@ namespace {
 
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_BLOCKS = 304;
+constexpr int SEL_MAX_Q_PER_GROUP = 2;
+constexpr int SEL_ITEMS = 4;  // items per thread per iteration, loads issued together
 
+// Histogram of the current 8-bit digit of every item whose higher digits match
+// its query's prefix.  Queries of a group are contiguous (at most two per
+// group); lanes of a warp that add to the same (query, digit) bin combine
+// first (__match_any_sync), so clustered keys do not serialise on one bin.
 __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, const uint16_t* grp, int64_t n,
                                                          const SelectQuery* q, int nq, int shift, uint32_t* hist) {
   extern __shared__ uint32_t sh[];  // nq * 256
   __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
+  __shared__ uint8_t qfirst[SELECT_MAX_QUERIES], qcount[SELECT_MAX_QUERIES];
   for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS) sh[i] = 0;
+  for (int i = threadIdx.x; i < SELECT_MAX_QUERIES; i += SEL_THREADS) qcount[i] = 0;
   for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
   __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = nq - 1; j >= 0; --j) {
+      const uint32_t g = sq[j].group;
+      if (g < SELECT_MAX_QUERIES) { qfirst[g] = (uint8_t)j; qcount[g]++; }
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
   const uint32_t hi_mask = shift >= 24 ? 0u : (0xffffffffu << (shift + 8));
-  for (int64_t i = blockIdx.x * (int64_t)SEL_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SEL_THREADS) {
-    uint32_t g = grp[i];
-    if (g == GROUP_NONE) continue;
-    uint32_t key = keys ? keys[i] : (uint32_t)i;
-    uint32_t d = (key >> shift) & 255u;
-    for (int j = 0; j < nq; ++j) {
-      if (sq[j].group != g || sq[j].k == 0) continue;
-      if ((key & hi_mask) != sq[j].prefix) continue;
-      atomicAdd(&sh[j * 256 + d], 1u);
+  const int64_t stride = (int64_t)gridDim.x * SEL_THREADS * SEL_ITEMS;
+  for (int64_t base = blockIdx.x * (int64_t)SEL_THREADS * SEL_ITEMS; base < n; base += stride) {  // warp-uniform
+    uint32_t gv[SEL_ITEMS], kv[SEL_ITEMS];
+#pragma unroll
+    for (int u = 0; u < SEL_ITEMS; ++u) {  // issue all loads first
+      const int64_t i = base + u * SEL_THREADS + threadIdx.x;
+      gv[u] = i < n ? grp[i] : GROUP_NONE;
+      kv[u] = i < n ? (keys ? keys[i] : (uint32_t)i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < SEL_ITEMS; ++u) {
+      const uint32_t g = gv[u], key = kv[u];
+      const int cnt = g < SELECT_MAX_QUERIES ? qcount[g] : 0;
+      const uint32_t d = (key >> shift) & 255u;
+#pragma unroll
+      for (int a = 0; a < SEL_MAX_Q_PER_GROUP; ++a) {
+        int h = -1;
+        if (a < cnt) {
+          const int j = qfirst[g] + a;
+          if (sq[j].k != 0 && (key & hi_mask) == sq[j].prefix) h = j * 256 + (int)d;
+        }
+        const uint32_t peers = __match_any_sync(FULL, h);
+        if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
+      }
     }
   }
   __syncthreads();
@@ -341,33 +372,57 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+// One warp per query: find the digit holding the k-th item (warp scan over
+// 8 digits per lane), extend the prefix, clear the query's histogram row.
 __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
-  int j = threadIdx.x;
-  if (j < nq) {
-    SelectQuery s = q[j];
-    if (s.k != 0) {
-      uint32_t cum = 0;
-      int found = -1;
-      for (int d = 0; d < 256; ++d) {
-        uint32_t c = hist[j * 256 + d];
-        if (cum + c >= s.k) { found = d; break; }
-        cum += c;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= nq) return;  // warp-uniform
+  SelectQuery s = q[j];
+  uint32_t* hrow = hist + (size_t)j * 256;
+  uint32_t c[8];
+  uint32_t lsum = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    c[i] = hrow[lane * 8 + i];
+    lsum += c[i];
+  }
+  uint32_t incl = lsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t excl = incl - lsum;
+  const uint32_t ball = __ballot_sync(FULL, s.k != 0 && incl >= s.k);
+  int digit = -1;
+  uint32_t newk = 0;
+  if (ball) {
+    const int L = __ffs(ball) - 1;
+    if (lane == L) {
+      uint32_t cum = excl;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (digit < 0 && cum + c[i] >= s.k) { digit = lane * 8 + i; newk = s.k - cum; }
+        cum += c[i];
       }
-      if (found < 0) {
-        s.k = 0;
-        s.result = 0xffffffffu;
-      } else {
-        s.k -= cum;
-        s.prefix |= (uint32_t)found << shift;
-        if (shift == 0) s.result = s.prefix;
-      }
-    } else {
+    }
+    digit = __shfl_sync(FULL, digit, L);
+    newk = __shfl_sync(FULL, newk, L);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hrow[lane * 8 + i] = 0u;
+  if (lane == 0) {
+    if (s.k == 0 || digit < 0) {
+      s.k = 0;
       s.result = 0xffffffffu;
+    } else {
+      s.k = newk;
+      s.prefix |= (uint32_t)digit << shift;
+      if (shift == 0) s.result = s.prefix;
     }
     q[j] = s;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nq * 256; i += blockDim.x) hist[i] = 0;
 }
 
 __global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist) {
@@ -384,8 +439,11 @@ void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuer
                 void* tmp, cudaStream_t s) {
   uint32_t* hist = (uint32_t*)tmp;
   k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist);
-  int64_t want = (n + SEL_THREADS - 1) / SEL_THREADS;
-  int blocks = (int)(want < SEL_BLOCKS ? want : SEL_BLOCKS);
+  // enough blocks to keep many loads in flight; fewer when every block must
+  // clear and flush a large (many-query) histogram
+  const int64_t want = (n + SEL_THREADS * SEL_ITEMS - 1) / (SEL_THREADS * SEL_ITEMS);
+  const int64_t cap_blocks = n_queries <= 2 ? 2048 : 4 * SEL_BLOCKS;
+  int blocks = (int)(want < cap_blocks ? want : cap_blocks);
   if (blocks < 1) blocks = 1;
   size_t smem = sizeof(uint32_t) * 256 * n_queries;
   static bool attr_set = false;
@@ -396,7 +454,7 @@ void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuer
   }
   for (int shift = 24; shift >= 0; shift -= 8) {
     k_sel_hist<<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, d_queries, n_queries, shift, hist);
-    k_sel_pick<<<1, 256, 0, s>>>(d_queries, n_queries, shift, hist);
+    k_sel_pick<<<(n_queries + 7) / 8, 256, 0, s>>>(d_queries, n_queries, shift, hist);
   }
   count_launch(1 + 8);
 }

@@ -31,7 +31,8 @@ int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uin
 // Queries live in device memory so that k can be computed on the device.
 // After select_kth, queries[q].result holds the key, or 0xffffffff when
 // k == 0 or the group has fewer than k items (queries[q].k is then 0).
-// keys == nullptr ranks the items by their index (key = i).
+// keys == nullptr ranks the items by their index (key = i).  Queries of one
+// group must be contiguous, at most two per group, groups < 64.
 constexpr int SELECT_MAX_QUERIES = 64;
 constexpr uint16_t GROUP_NONE = 0xffff;
 struct SelectQuery {

@@ -8,13 +8,15 @@
 //   scan2       pair offsets and visible-slot ids (two-channel scan).
 //   k_emit      per visible (voxel, view): 64-byte render record (centre
 //               relative to the camera, half-size, 8 corner densities, SH
-//               colour, voxel id) and its (tile << 32 | depth key, slot) pairs.
+//               colour, 1 / (2 h)), its pixel box and voxel id, and its
+//               (tile << 32 | depth key, slot) pairs.
 //   radix sort  CUB-free LSD sort of the pairs on (tile bits + 32) bits.
 //   k_ranges    [start, end) of every tile in the sorted list.
-//   k_fwd       per tile: records staged through shared memory in batches,
-//               one thread per pixel marching front to back (Eq. 2-4), w_max
-//               (Eq. 5) reduced per warp then per block before one global
-//               atomicMax per (tile, voxel), warp / block early exit at T < t_stop.
+//   k_fwd       per tile, one thread per pixel: each warp stages the records
+//               that meet its pixel strip through shared memory and marches
+//               front to back (Eq. 2-4); w_max (Eq. 5) is reduced over the
+//               warp before one global atomicMax; a warp stops when all its
+//               pixels have T < t_stop.
 // lv_rasterize_backward walks the same lists back to front (k_bwd) and
 // reduces the SH colour gradient per voxel (k_sh_bwd).
 #include <math.h>
@@ -77,6 +79,7 @@ struct FwdWs {
   uint2* rect;                   // [items] (tx0 | tx1 << 16, ty0 | ty1 << 16)
   uint2* pbox;                   // [items] conservative pixel box (x0 | x1 << 16, y0 | y1 << 16), [x0, x1)
   uint2* rec_bb;                 // [slots] pixel box of the render record
+  uint32_t* slot_vox;            // [slots] voxel id of the render record
   uint32_t* dkey;                // [items] order key of z_centre
   unsigned long long* pair_off;  // [items]
   uint32_t* slot;                // [items]
@@ -105,6 +108,7 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   w.rect = c.take<uint2>(items);
   w.pbox = c.take<uint2>(items);
   w.rec_bb = c.take<uint2>(items);
+  w.slot_vox = c.take<uint32_t>(items);
   w.dkey = c.take<uint32_t>(items);
   w.pair_off = c.take<unsigned long long>(items);
   w.slot = c.take<uint32_t>(items);
@@ -289,6 +293,7 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ cnt,
                                               const uint32_t* __restrict__ vis, const uint2* __restrict__ rect,
                                               const uint2* __restrict__ pbox, uint2* __restrict__ rec_bb,
+                                              uint32_t* __restrict__ slot_vox,
                                               const uint32_t* __restrict__ dkey,
                                               const unsigned long long* __restrict__ pair_off,
                                               const uint32_t* __restrict__ slot, float4* __restrict__ rec,
@@ -317,7 +322,8 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   r[0] = make_float4(rx, ry, rz, g.w);
   r[1] = make_float4(d[0], d[1], d[2], d[3]);
   r[2] = make_float4(d[4], d[5], d[6], d[7]);
-  r[3] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), __uint_as_float((uint32_t)vox));
+  r[3] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), __fdiv_rn(0.5f, g.w));
+  slot_vox[s] = (uint32_t)vox;
   d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);
   rec_bb[s] = pbox[i];
   unsigned long long off = pair_off[i];
@@ -393,8 +399,8 @@ __device__ __forceinline__ bool chord(const Ray& r, float4 g, float& t_in, float
 }
 
 // local coordinates of the chord midpoint in [0,1]^3 and the trilinear density
-__device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, float4 d1, float tm, float* u) {
-  float i2h = __frcp_rn(g.w + g.w);
+__device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, float4 d1, float i2h, float tm,
+                                             float* u) {
   u[0] = __saturatef((fmaf(tm, r.dx, -g.x) + g.w) * i2h);
   u[1] = __saturatef((fmaf(tm, r.dy, -g.y) + g.w) * i2h);
   u[2] = __saturatef((fmaf(tm, r.dz, -g.z) + g.w) * i2h);
@@ -427,21 +433,24 @@ __device__ __forceinline__ int find_view(const ViewSet& vs, int gtile) {
   return v;
 }
 
-// The pixels of a warp form a strip of the tile: 32 consecutive pixels in
-// row-major order (TS = 8: 4 rows of 8, 16: 2 rows of 16, 32: 1 row of 32).
-// A record whose conservative pixel box misses the strip cannot be hit by any
-// lane, so the whole warp skips it (a warp-uniform branch); the hit decisions
-// are exactly those of the per-lane chord test.
+// The pixels of a warp form a 4 x 8 block of its tile (rows x columns; the
+// warps of a TS x TS tile are laid out TS/8 across and TS/4 down, lanes
+// row-major inside the block, so pixel ids grow with the lane).  Compared with
+// a 2 x 16 strip, a small voxel's footprint meets fewer warps and more lanes
+// of each.  A record whose conservative pixel box misses the block cannot be
+// hit by any lane, so the whole warp skips it (a warp-uniform branch); the hit
+// decisions are exactly those of the per-lane chord test.
 template <int TS>
 struct Strip {
   uint32_t x0, x1, y0, y1;  // [x0, x1) x [y0, y1) in image pixels
   __device__ __forceinline__ Strip(int tile_x, int tile_y, int warp) {
-    constexpr int ROWS = 32 / TS;
-    x0 = (uint32_t)(tile_x * TS);
-    x1 = x0 + TS;
-    y0 = (uint32_t)(tile_y * TS + warp * ROWS);
-    y1 = y0 + ROWS;
+    x0 = (uint32_t)(tile_x * TS + (warp % (TS / 8)) * 8);
+    x1 = x0 + 8;
+    y0 = (uint32_t)(tile_y * TS + (warp / (TS / 8)) * 4);
+    y1 = y0 + 4;
   }
+  __device__ __forceinline__ int px(int lane) const { return (int)x0 + (lane & 7); }
+  __device__ __forceinline__ int py(int lane) const { return (int)y0 + (lane >> 3); }
   // box: (bx0 | bx1 << 16, by0 | by1 << 16)
   __device__ __forceinline__ bool misses(uint2 box) const {
     return (box.x >> 16) <= x0 || (box.x & 0xffffu) >= x1 || (box.y >> 16) <= y0 || (box.y & 0xffffu) >= y1;
@@ -449,83 +458,102 @@ struct Strip {
 };
 
 // ------------------------------------------------------------------ forward composite
-template <int TS, int B>
-__global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
+// Each warp walks its strip's tile list on its own: 32 list entries at a
+// time, the entries whose pixel box meets the strip are compacted with a
+// ballot and their 64-byte records staged in the warp's slice of shared
+// memory, then every lane marches its pixel through them front to back.  No
+// block-wide barrier: a warp stops as soon as all its pixels have stopped.
+// per-warp staging slice: 32 records (64 B) + voxel id + list entry (+ slot id in the backward)
+constexpr size_t FWD_SLICE = 32 * 64 + 32 * 4 * 2;
+constexpr size_t BWD_SLICE = 32 * 64 + 32 * 4 * 3;
+template <int TS>
+constexpr int min_blocks() { return TS == 16 ? 5 : (TS == 8 ? 16 : 1); }
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
-                                                const uint2* __restrict__ rec_bb, float t_stop,
+                                                const uint2* __restrict__ rec_bb,
+                                                const uint32_t* __restrict__ slot_vox, float t_stop,
                                                 float* __restrict__ rgb, float* __restrict__ depth,
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
-                                                float* __restrict__ tau_out, unsigned long long* __restrict__ wmax) {
-  constexpr int NT = TS * TS;
-  __shared__ float4 s_rec[B * 4];
-  __shared__ uint2 s_bb[B];
-  __shared__ unsigned long long s_wm[B];
-  const int tid = threadIdx.x, lane = tid & 31;
+                                                uint32_t* __restrict__ n_samples, float* __restrict__ tau_out,
+                                                unsigned long long* __restrict__ wmax) {
+  extern __shared__ float4 smem_f4[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* wr = (float4*)((char*)smem_f4 + FWD_SLICE * warp);
+  uint32_t* w_vox = (uint32_t*)(wr + 128);
+  uint32_t* w_ent = w_vox + 32;
   const int gtile = blockIdx.x;
   const int view = find_view(vs, gtile);
   const DevView& c = vs.v[view];
   const int lt = gtile - c.tile_off;
   const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
-  const int px = tile_x * TS + tid % TS, py = tile_y * TS + tid / TS;
+  const Strip<TS> strip(tile_x, tile_y, warp);
+  const int px = strip.px(lane), py = strip.py(lane);
   const bool inside = px < c.W && py < c.H;
-  const Strip<TS> strip(tile_x, tile_y, tid >> 5);
   const Ray r = make_ray(c, px, py);
   const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
   const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
   const unsigned long long gid_key = 0xffffffffull - (gid & 0xffffffffull);
   float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
-  uint32_t last = 0;
+  uint32_t last = 0, nsamp = 0;
   bool done = !inside;
-  for (uint32_t base = start; base < end; base += B) {
-    const int cntb = (int)min((uint32_t)B, end - base);
-    for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[base + (q >> 2)] + (q & 3)];
-    for (int q = tid; q < cntb; q += NT) {
-      s_bb[q] = rec_bb[svals[base + q]];
-      s_wm[q] = 0ull;
+  for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += 32) {
+    const uint32_t e = base + lane;
+    uint32_t sl = 0;
+    bool ov = false;
+    if (e < end) {
+      sl = svals[e];
+      ov = !strip.misses(rec_bb[sl]);
     }
-    __syncthreads();
-    if (!__all_sync(FULL, done)) {
-      for (int j = 0; j < cntb; ++j) {
-        if (strip.misses(s_bb[j])) continue;  // warp-uniform
-        const float4 g = s_rec[4 * j];
-        float t_in, t_out;
-        const bool hit = !done && chord(r, g, t_in, t_out);
-        float w = 0.f;
-        if (hit) {
-          const float4 d0 = s_rec[4 * j + 1], d1 = s_rec[4 * j + 2], col = s_rec[4 * j + 3];
-          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-          float u[3];
-          const float sigma = fmaxf(mid_density(r, g, d0, d1, tm, u), 0.f);
-          const float x = sigma * l;
-          const float e = __expf(-x);
-          const float alpha = one_minus_exp(x, e);
-          w = T * alpha;
-          cr = fmaf(w, col.x, cr);
-          cg = fmaf(w, col.y, cg);
-          cb = fmaf(w, col.z, cb);
-          dep = fmaf(w, tm, dep);
-          tau += x;
-          T *= e;
-          last = base + j - start + 1;
-        }
-        const unsigned any = __ballot_sync(FULL, hit);
-        if (any) {
-          const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
-          const uint32_t mx = __reduce_max_sync(FULL, v);
-          const uint32_t who = __ballot_sync(FULL, v == mx);
-          if (lane == __ffs(who) - 1) atomicMax(&s_wm[j], ((unsigned long long)(mx - 1u) << 32) | gid_key);
-          if (hit && T < t_stop) done = true;
-        }
+    const uint32_t mask = __ballot_sync(FULL, ov);
+    if (!mask) continue;
+    if (ov) {
+      const int pos = __popc(mask & ((1u << lane) - 1u));
+      const float4* src = rec + 4 * (size_t)sl;
+      wr[4 * pos + 0] = src[0];
+      wr[4 * pos + 1] = src[1];
+      wr[4 * pos + 2] = src[2];
+      wr[4 * pos + 3] = src[3];
+      w_vox[pos] = slot_vox[sl];
+      w_ent[pos] = e;
+    }
+    __syncwarp();
+    const int m = __popc(mask);
+    for (int j = 0; j < m; ++j) {
+      const float4 g = wr[4 * j];
+      float t_in, t_out;
+      const bool hit = !done && chord(r, g, t_in, t_out);
+      float w = 0.f;
+      if (hit) {
+        const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
+        const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+        float u[3];
+        const float sigma = fmaxf(mid_density(r, g, d0, d1, col.w, tm, u), 0.f);
+        const float x = sigma * l;
+        const float ex = __expf(-x);
+        const float alpha = one_minus_exp(x, ex);
+        w = T * alpha;
+        cr = fmaf(w, col.x, cr);
+        cg = fmaf(w, col.y, cg);
+        cb = fmaf(w, col.z, cb);
+        dep = fmaf(w, tm, dep);
+        tau += x;
+        T *= ex;
+        last = w_ent[j] - start + 1;
+        ++nsamp;
+      }
+      if (__any_sync(FULL, hit)) {
+        // the warp's largest w (ties to the lowest lane = smallest pixel id), one global atomic
+        const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
+        const uint32_t mx = __reduce_max_sync(FULL, v);
+        const uint32_t who = __ballot_sync(FULL, v == mx);
+        if (wmax && lane == __ffs(who) - 1)
+          atomicMax(&wmax[w_vox[j]], ((unsigned long long)(mx - 1u) << 32) | gid_key);
+        if (hit && T < t_stop) done = true;
       }
     }
-    __syncthreads();
-    if (wmax) {
-      for (int q = tid; q < cntb; q += NT) {
-        const unsigned long long m = s_wm[q];
-        if (m) atomicMax(&wmax[__float_as_uint(s_rec[4 * q + 3].w)], m);
-      }
-    }
-    if (__syncthreads_count(!done) == 0) break;
+    __syncwarp();
   }
   if (inside) {
     const size_t p = (size_t)gid;
@@ -535,6 +563,7 @@ __global__ void __launch_bounds__(TS* TS) k_fwd(const __grid_constant__ ViewSet 
     if (depth) depth[p] = dep;
     T_out[p] = T;
     n_contrib[p] = last;
+    if (n_samples) n_samples[p] = nsamp;
     tau_out[p] = tau;
   }
 }
@@ -573,31 +602,34 @@ __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
   return v[0] + __shfl_xor_sync(FULL, v[0], 1);
 }
 
-template <int TS, int B>
-__global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
+// Backward: each warp walks its strip's list back to front from the last entry
+// any of its pixels used, in the same 32-entry chunks and with the same
+// compaction as the forward; the per-record gradients (8 corners + colour) are
+// reduced over the warp and sent with three 16-byte global reductions.
+template <int TS>
+__global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
-                                                const uint2* __restrict__ rec_bb, const float* __restrict__ T_fwd,
+                                                const uint2* __restrict__ rec_bb,
+                                                const uint32_t* __restrict__ slot_vox, const float* __restrict__ T_fwd,
                                                 const float* __restrict__ tau_in,
                                                 const uint32_t* __restrict__ n_contrib,
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
                                                 float4* __restrict__ d_rgb) {
-  constexpr int NT = TS * TS;
-  constexpr int NV = 12;  // 8 corners + 3 colour + 1 "touched" flag
-  __shared__ float4 s_rec[B * 4];
-  __shared__ uint2 s_bb[B];
-  __shared__ uint32_t s_slot[B];
-  __shared__ float s_acc[B * NV];
-  __shared__ uint32_t s_max;
-  const int tid = threadIdx.x, lane = tid & 31;
+  extern __shared__ float4 smem_f4[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* wr = (float4*)((char*)smem_f4 + BWD_SLICE * warp);
+  uint32_t* w_vox = (uint32_t*)(wr + 128);
+  uint32_t* w_slot = w_vox + 32;
+  uint32_t* w_ent = w_slot + 32;
   const int gtile = blockIdx.x;
   const int view = find_view(vs, gtile);
   const DevView& c = vs.v[view];
   const int lt = gtile - c.tile_off;
   const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
-  const int px = tile_x * TS + tid % TS, py = tile_y * TS + tid / TS;
+  const Strip<TS> strip(tile_x, tile_y, warp);
+  const int px = strip.px(lane), py = strip.py(lane);
   const bool inside = px < c.W && py < c.H;
-  const Strip<TS> strip(tile_x, tile_y, tid >> 5);
   const Ray r = make_ray(c, px, py);
   const uint32_t start = ranges[2 * gtile];
   const size_t p = (size_t)(c.pix_off + (long long)py * c.W + px);
@@ -613,89 +645,98 @@ __global__ void __launch_bounds__(TS* TS) k_bwd(const __grid_constant__ ViewSet 
     if (dL_ddepth) gD = dL_ddepth[p];
     if (dL_dT) gT = dL_dT[p];
   }
-  if (tid == 0) s_max = 0;
-  __syncthreads();
-  {
-    const uint32_t m = __reduce_max_sync(FULL, nc);
-    if (lane == 0 && m) atomicMax(&s_max, m);
-  }
-  __syncthreads();
-  const uint32_t top_all = start + s_max;
   const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
   const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
   const float tgT = Tf * gT;
   float S = 0.f;
-  for (uint32_t top = top_all; top > start; top -= min((uint32_t)B, top - start)) {
-    const uint32_t lo = top - min((uint32_t)B, top - start);
-    const int cntb = (int)(top - lo);
-    for (int q = tid; q < cntb * 4; q += NT) s_rec[q] = rec[4 * (size_t)svals[lo + (q >> 2)] + (q & 3)];
-    for (int q = tid; q < cntb; q += NT) {
-      const uint32_t sl = svals[lo + q];
-      s_slot[q] = sl;
-      s_bb[q] = rec_bb[sl];
+  // chunks aligned as in the forward: [start + 32 k, start + 32 k + 32)
+  for (uint32_t cb = start + ((warp_hi - start + 31u) & ~31u); cb > start; cb -= 32) {
+    const uint32_t base = cb - 32;
+    const uint32_t e = base + lane;
+    uint32_t sl = 0;
+    bool ov = false;
+    if (e < warp_hi) {
+      sl = svals[e];
+      ov = !strip.misses(rec_bb[sl]);
     }
-    for (int q = tid; q < cntb * NV; q += NT) s_acc[q] = 0.f;
-    __syncthreads();
-    if (lo < warp_hi) {
-      const int jmax = (int)min((uint32_t)cntb, warp_hi - lo);
-      for (int j = jmax - 1; j >= 0; --j) {
-        if (strip.misses(s_bb[j])) continue;  // warp-uniform
-        const float4 g = s_rec[4 * j];
-        float t_in, t_out;
-        const bool hit = (lo + j) < my_hi && chord(r, g, t_in, t_out);
-        if (!__any_sync(FULL, hit)) continue;
-        float v[16];
+    const uint32_t mask = __ballot_sync(FULL, ov);
+    if (!mask) continue;
+    if (ov) {
+      const int pos = __popc(mask & ((1u << lane) - 1u));
+      const float4* src = rec + 4 * (size_t)sl;
+      wr[4 * pos + 0] = src[0];
+      wr[4 * pos + 1] = src[1];
+      wr[4 * pos + 2] = src[2];
+      wr[4 * pos + 3] = src[3];
+      w_vox[pos] = slot_vox[sl];
+      w_slot[pos] = sl;
+      w_ent[pos] = e;
+    }
+    __syncwarp();
+    for (int j = __popc(mask) - 1; j >= 0; --j) {
+      const float4 g = wr[4 * j];
+      float t_in, t_out;
+      const bool hit = w_ent[j] < my_hi && chord(r, g, t_in, t_out);
+      const unsigned hb = __ballot_sync(FULL, hit);
+      if (!hb) continue;
+      float v[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      if (hit) {
+        const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
+        const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+        float u[3];
+        const float sraw = mid_density(r, g, d0, d1, col.w, tm, u);
+        const float sigma = fmaxf(sraw, 0.f);
+        const float x = sigma * l;
+        const float Tk = __expf(-tau);
+        const float tau_prev = fmaxf(tau - x, 0.f);
+        const float T_prev = __expf(-tau_prev);
+        const float alpha = one_minus_exp(x, __expf(-x));
+        const float w = T_prev * alpha;
+        const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
+        const float ds = l * (Tk * a - S - tgT);
+        S = fmaf(w, a, S);
+        tau = tau_prev;
+        const float dr = sraw > 0.f ? ds : 0.f;
+        const float ux = u[0], uy = u[1], uz = u[2];
+        const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
+        const float a00 = dr * my * mz, a10 = dr * uy * mz, a01 = dr * my * uz, a11 = dr * uy * uz;
+        v[0] = mx * a00;
+        v[1] = ux * a00;
+        v[2] = mx * a10;
+        v[3] = ux * a10;
+        v[4] = mx * a01;
+        v[5] = ux * a01;
+        v[6] = mx * a11;
+        v[7] = ux * a11;
+        v[8] = w * gr;
+        v[9] = w * gg;
+        v[10] = w * gb;
+      }
+      float* dd = d_density + 8 * (size_t)w_vox[j];
+      float* dc = (float*)(d_rgb + w_slot[j]);
+      if (__popc(hb) <= 2) {
+        // one or two lanes: each sends its own values, cheaper than the butterfly
         if (hit) {
-          const float4 d0 = s_rec[4 * j + 1], d1 = s_rec[4 * j + 2], col = s_rec[4 * j + 3];
-          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-          float u[3];
-          const float sraw = mid_density(r, g, d0, d1, tm, u);
-          const float sigma = fmaxf(sraw, 0.f);
-          const float x = sigma * l;
-          const float Tk = __expf(-tau);
-          const float tau_prev = fmaxf(tau - x, 0.f);
-          const float T_prev = __expf(-tau_prev);
-          const float alpha = one_minus_exp(x, __expf(-x));
-          const float w = T_prev * alpha;
-          const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
-          const float ds = l * (Tk * a - S - tgT);
-          S = fmaf(w, a, S);
-          tau = tau_prev;
-          const float dr = sraw > 0.f ? ds : 0.f;
-          const float ux = u[0], uy = u[1], uz = u[2];
-          const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
-          const float a00 = dr * my * mz, a10 = dr * uy * mz, a01 = dr * my * uz, a11 = dr * uy * uz;
-          v[0] = mx * a00;
-          v[1] = ux * a00;
-          v[2] = mx * a10;
-          v[3] = ux * a10;
-          v[4] = mx * a01;
-          v[5] = ux * a01;
-          v[6] = mx * a11;
-          v[7] = ux * a11;
-          v[8] = w * gr;
-          v[9] = w * gg;
-          v[10] = w * gb;
-          v[11] = 1.f;
+          red_add_v4(dd, v[0], v[1], v[2], v[3]);
+          red_add_v4(dd + 4, v[4], v[5], v[6], v[7]);
+          red_add_v4(dc, v[8], v[9], v[10], 0.f);
         }
-        const float sum = warp_reduce16(v, lane);
-        const int idx = lane >> 1;
-        if (!(lane & 1) && idx < NV) atomicAdd(&s_acc[j * NV + idx], sum);
+      } else {
+        const float sum = warp_reduce16(v, lane);  // value (l >> 1) on even lane l
+        // gather four values each into lanes 0 (corners 0-3), 1 (corners 4-7) and 2 (colour)
+        const int src0 = lane == 0 ? 0 : (lane == 1 ? 8 : 16);
+        const float q0 = __shfl_sync(FULL, sum, src0 + 0);
+        const float q1 = __shfl_sync(FULL, sum, src0 + 2);
+        const float q2 = __shfl_sync(FULL, sum, src0 + 4);
+        const float q3 = __shfl_sync(FULL, sum, src0 + 6);
+        if (lane == 0) red_add_v4(dd, q0, q1, q2, q3);
+        else if (lane == 1) red_add_v4(dd + 4, q0, q1, q2, q3);
+        else if (lane == 2) red_add_v4(dc, q0, q1, q2, 0.f);
       }
     }
-    __syncthreads();
-    for (int q = tid; q < cntb; q += NT) {
-      const float* a = &s_acc[q * NV];
-      if (a[11] == 0.f) continue;
-      const uint32_t vox = __float_as_uint(s_rec[4 * q + 3].w);
-      float* dd = d_density + 8 * (size_t)vox;
-      red_add_v4(dd, a[0], a[1], a[2], a[3]);
-      red_add_v4(dd + 4, a[4], a[5], a[6], a[7]);
-      red_add_v4((float*)(d_rgb + s_slot[q]), a[8], a[9], a[10], 0.f);
-    }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -769,12 +810,12 @@ __global__ void k_unpack_wmax(const unsigned long long* __restrict__ packed, int
 }
 
 __global__ void k_debug_pairs(const uint64_t* __restrict__ k, const uint32_t* __restrict__ v,
-                              const float4* __restrict__ rec, const unsigned long long* d_count, int64_t cap,
+                              const uint32_t* __restrict__ slot_vox, const unsigned long long* d_count, int64_t cap,
                               uint64_t* ko, uint32_t* vo) {
   const int64_t n = usable_pairs(d_count, cap);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (ko) ko[i] = k[i];
-    if (vo) vo[i] = __float_as_uint(rec[4 * (size_t)v[i] + 3].w);
+    if (vo) vo[i] = slot_vox[v[i]];
   }
 }
 
@@ -819,29 +860,30 @@ static lv_status finish(lv_status st, uint32_t flags, int32_t* d_status, cudaStr
 }
 
 template <int TS>
-static void launch_fwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+static void launch_fwd(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                        float t_stop, const lv_fwd_out* out) {
-  dim3 grid((unsigned)tiles), block(TS * TS);
-#define LV_FWD(BB)                                                                                          \
-  k_fwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, t_stop, out->rgb, out->depth, out->T, \
-                                       out->n_contrib, w.tau, out->wmax_packed)
-  if (B == 64) LV_FWD(64);
-  else if (B == 128) LV_FWD(128);
-  else LV_FWD(256);
-#undef LV_FWD
+  const size_t smem = FWD_SLICE * (TS * TS / 32);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_fwd<TS><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop, out->rgb,
+                                                 out->depth, out->T, out->n_contrib, out->n_samples, w.tau,
+                                                 out->wmax_packed);
 }
 
 template <int TS>
-static void launch_bwd(int B, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+static void launch_bwd(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                        const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
-  dim3 grid((unsigned)tiles), block(TS * TS);
-#define LV_BWD(BB)                                                                                              \
-  k_bwd<TS, BB><<<grid, block, 0, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, fwd->T, w.tau, fwd->n_contrib, gC, gD, gT, \
-                                       dd, w.d_rgb)
-  if (B == 64) LV_BWD(64);
-  else if (B == 128) LV_BWD(128);
-  else LV_BWD(256);
-#undef LV_BWD
+  const size_t smem = BWD_SLICE * (TS * TS / 32);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_bwd<TS><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T, w.tau,
+                                                 fwd->n_contrib, gC, gD, gT, dd, w.d_rgb);
 }
 
 }  // namespace lv
@@ -885,8 +927,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                               \
   k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
-                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.dkey, w.pair_off, w.slot,      \
-                                        w.rec, w.d_rgb, w.k0, w.v0, pair_capacity, d_status)
+                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey, w.pair_off,  \
+                                        w.slot, w.rec, w.d_rgb, w.k0, w.v0, pair_capacity, d_status)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
@@ -899,9 +941,9 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   const uint64_t* sk = which ? w.k1 : w.k0;
   const uint32_t* sv = which ? w.v1 : w.v0;
   k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
-  if (opts->tile == 8) launch_fwd<8>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
-  else if (opts->tile == 16) launch_fwd<16>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
-  else launch_fwd<32>(opts->batch, tiles, s, vs, w, sv, opts->t_stop, out);
+  if (opts->tile == 8) launch_fwd<8>(tiles, s, vs, w, sv, opts->t_stop, out);
+  else if (opts->tile == 16) launch_fwd<16>(tiles, s, vs, w, sv, opts->t_stop, out);
+  else launch_fwd<32>(tiles, s, vs, w, sv, opts->t_stop, out);
   count_launch(2);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
 }
@@ -956,9 +998,9 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
   const int which = sort_passes(32 + tile_bits(tiles)) & 1;
   const uint32_t* sv = which ? w.v1 : w.v0;
   if (!accumulate && n > 0) cudaMemsetAsync(d_density, 0, sizeof(float) * 8 * n, s);
-  if (opts->tile == 8) launch_bwd<8>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
-  else if (opts->tile == 16) launch_bwd<16>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
-  else launch_bwd<32>(opts->batch, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  if (opts->tile == 8) launch_bwd<8>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  else if (opts->tile == 16) launch_bwd<16>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  else launch_bwd<32>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
   count_launch(1);
   if (d_sh) launch_sh_bwd(vox, vs, w, d_sh, accumulate, s);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_backward");
@@ -1002,7 +1044,7 @@ extern "C" lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_view
   if (ws_bytes < w.bytes) { set_error("workspace too small"); return LV_ERR_WORKSPACE; }
   const int which = sort_passes(32 + tile_bits(tiles)) & 1;
   if (keys || voxel) {
-    k_debug_pairs<<<608, 256, 0, s>>>(which ? w.k1 : w.k0, which ? w.v1 : w.v0, w.rec, w.counters, pair_capacity,
+    k_debug_pairs<<<608, 256, 0, s>>>(which ? w.k1 : w.k0, which ? w.v1 : w.v0, w.slot_vox, w.counters, pair_capacity,
                                        keys, voxel);
     count_launch(1);
   }

@@ -48,7 +48,8 @@ class lv_raster_opts(C.Structure):
 
 class lv_fwd_out(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("T", C.c_void_p), ("n_contrib", C.c_void_p),
-                ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p)]
+                ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p),
+                ("n_samples", C.c_void_p)]
 
 
 class lv_prune_params(C.Structure):
@@ -186,10 +187,12 @@ def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False) -> lv_raster_op
     return o
 
 
-def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None) -> lv_fwd_out:
+def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None,
+                 n_samples=None) -> lv_fwd_out:
     o = lv_fwd_out()
     o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
     o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)
+    o.n_samples = _ptr(n_samples)
     return o
 
 

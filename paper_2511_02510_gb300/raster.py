@@ -42,6 +42,7 @@ class RasterContext:
         self.depth = torch.empty(P, dtype=torch.float32, device=d)
         self.T = torch.empty(P, dtype=torch.float32, device=d)
         self.n_contrib = torch.empty(P, dtype=torch.int32, device=d)
+        self.n_samples = torch.empty(P, dtype=torch.int32, device=d)
         self.wmax_packed = torch.zeros(n, dtype=torch.int64, device=d)
         self.z_min = torch.full((n,), math.inf, dtype=torch.float32, device=d)
         self.delta_min = torch.full((n,), math.inf, dtype=torch.float32, device=d)
@@ -68,7 +69,8 @@ class RasterContext:
     def fwd_struct(self, stats=True):
         return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
                               self.wmax_packed if stats else None, self.z_min if stats else None,
-                              self.delta_min if stats else None, self.seen if stats else None)
+                              self.delta_min if stats else None, self.seen if stats else None,
+                              self.n_samples if stats else None)
 
     # ---------------------------------------------------------------- calls
     def forward(self, vox: L.lv_voxels, stats=True):
