@@ -34,7 +34,8 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd Mpix/s at 1 GB300, batched/mixed vs plain FP32; % HBM roofline"
 UNIT = "Mpix/s"
 W_IMG, H_IMG = 1237, 822
-WORKLOAD = "360-scene 2M voxels (levels 6-12, background shell r 12-16), 1 view 1237x822, FP32 storage"
+WORKLOAD = ("360-scene 2M voxels (levels 6-12, background shell r 12-16, opaque surfaces), 1 view 1237x822, "
+            "FP32 storage")
 
 
 def parse():
@@ -342,18 +343,22 @@ def run_reference(args, rank):
           flush=True)
 
 
-def run_variant(torch, synth, kind, steps=10, warmup=3):
-    """Batched / mixed-precision variants measured beside the plain path (same GPU)."""
+def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
+    """Batched / mixed-precision / semi-transparent variants measured beside the plain path (same GPU)."""
     from paper_2511_02510_gb300 import litevoxel as L
     from paper_2511_02510_gb300.raster import RasterContext, Scene
     if kind == "batched16_fp32":
-        sc = synth.scene_360()
+        sc = scene_np
         cams = synth.uneven_views(16, seed=2)
         dd, sd = torch.float32, torch.float32
-    else:  # batched8_mixed: the 2M scene, 8 views of 980x545, BF16 SH + FP16 corners
-        sc = synth.scene_360()
+    elif kind == "batched8_mixed":  # the 2M scene, 8 views of 980x545, BF16 SH + FP16 corners
+        sc = scene_np
         cams = [synth.orbit_camera(980, 545, 60.0, 3.0, 45.0 * i, 15.0) for i in range(8)]
         dd, sd = torch.float16, torch.bfloat16
+    else:  # semi_transparent_fp32: the plain view of the same octree with peak density 10 per unit
+        sc = synth.scene_360(opaque=False)
+        cams = [camera_for(0)]
+        dd, sd = torch.float32, torch.float32
     scene = Scene.from_numpy(sc, "cuda", dd, sd)
     ctx = RasterContext(cams, scene.n)
     vox = scene.voxels()
@@ -489,7 +494,8 @@ def run_ours(args, rank, world, local):
                "step_counters": cnt}
         if not args.no_variants:
             try:
-                out["variants"] = {k: run_variant(torch, synth, k) for k in ("batched16_fp32", "batched8_mixed")}
+                out["variants"] = {k: run_variant(torch, synth, k, scene_np)
+                                   for k in ("batched16_fp32", "batched8_mixed", "semi_transparent_fp32")}
                 out["variants"]["plain_fp32_fwd_bwd_only"] = {
                     "value": wl.npix / ((stage_ms["forward"] + stage_ms["backward"] + stage_ms["sh_backward"] +
                                          stage_ms["reset"]) / 1e3) / 1e6, "unit": UNIT}

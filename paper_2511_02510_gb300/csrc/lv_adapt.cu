@@ -450,43 +450,68 @@ __global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uin
   if (i < n && sel[i]) list[rank[i]] = (uint32_t)i;
 }
 
-// one thread per child: consecutive threads write consecutive output rows
+// A warp writes 32 consecutive children (output rows o0 .. o0 + 31): one lane
+// per child for the geometry, level and interpolated corners; the SH rows and
+// the auxiliary rows are written cooperatively in 16-byte words so that the
+// stores coalesce (the 8 children of a parent read the same parent row).
 template <typename DT, typename ST>
 __global__ void k_sd_write_children(int64_t max_children, const uint32_t* __restrict__ list,
                                     const unsigned long long* totals, const SubState* st,
                                     const float4* __restrict__ geom, const uint8_t* __restrict__ level,
                                     const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
                                     uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
-  const int64_t t = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (t >= max_children || !st->fits) return;
-  const int64_t k = (int64_t)totals[1];
-  if (t >= 8 * k) return;
-  const int64_t i = list[t >> 3];
-  const int c = (int)(t & 7);
-  const int64_t o = (int64_t)totals[0] + t;
-  const float4 g = geom[i];
-  const float hc = __fmul_rn(g.w, 0.5f);
-  ogeom[o] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
-                         __fadd_rn(g.z, (c & 4) ? hc : -hc), hc);
-  olevel[o] = (uint8_t)(level[i] + 1);
-  float d[8];
+  const int lane = threadIdx.x & 31;
+  const int64_t t0 = (blockIdx.x * (int64_t)TPB + threadIdx.x) & ~(int64_t)31;
+  if (t0 >= max_children || !st->fits) return;  // warp-uniform
+  const int64_t nchild = 8 * (int64_t)totals[1];
+  if (t0 >= nchild) return;
+  const int nrows = (int)min((int64_t)32, nchild - t0);
+  const int64_t o0 = (int64_t)totals[0] + t0;
+  if (lane < nrows) {
+    const int64_t t = t0 + lane;
+    const int64_t i = list[t >> 3];
+    const int c = (int)(t & 7);
+    const int64_t o = o0 + lane;
+    const float4 g = geom[i];
+    const float hc = __fmul_rn(g.w, 0.5f);
+    ogeom[o] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
+                           __fadd_rn(g.z, (c & 4) ? hc : -hc), hc);
+    olevel[o] = (uint8_t)(level[i] + 1);
+    float d[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d[q] = to_f32(dens[8 * i + q]);
+    for (int q = 0; q < 8; ++q) d[q] = to_f32(dens[8 * i + q]);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
-    const float qy = (float)(((c >> 1) & 1) + ((j >> 1) & 1)) * 0.5f;
-    const float qz = (float)(((c >> 2) & 1) + ((j >> 2) & 1)) * 0.5f;
-    const float x0 = lerp_rn(d[0], d[1], qx), x1 = lerp_rn(d[2], d[3], qx);
-    const float x2 = lerp_rn(d[4], d[5], qx), x3 = lerp_rn(d[6], d[7], qx);
-    const float y0 = lerp_rn(x0, x1, qy), y1 = lerp_rn(x2, x3, qy);
-    odens[8 * o + j] = from_f32<DT>(lerp_rn(y0, y1, qz));
+    for (int j = 0; j < 8; ++j) {
+      const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
+      const float qy = (float)(((c >> 1) & 1) + ((j >> 1) & 1)) * 0.5f;
+      const float qz = (float)(((c >> 2) & 1) + ((j >> 2) & 1)) * 0.5f;
+      const float x0 = lerp_rn(d[0], d[1], qx), x1 = lerp_rn(d[2], d[3], qx);
+      const float x2 = lerp_rn(d[4], d[5], qx), x3 = lerp_rn(d[6], d[7], qx);
+      const float y0 = lerp_rn(x0, x1, qy), y1 = lerp_rn(x2, x3, qy);
+      odens[8 * o + j] = from_f32<DT>(lerp_rn(y0, y1, qz));
+    }
   }
-  const uint4* ss = (const uint4*)(sh + 48 * i);
-  uint4* sd = (uint4*)(osh + 48 * o);
-#pragma unroll
-  for (int q = 0; q < (int)(48 * sizeof(ST) / 16); ++q) sd[q] = ss[q];
-  for (int a = 0; a < aux.n; ++a) aux_fill(aux.a[a], o);
+  // SH rows: copied from the parent
+  constexpr int WPR = (int)(48 * sizeof(ST) / 16);
+  const uint4* ssrc = (const uint4*)sh;
+  uint4* sdst = (uint4*)osh + (size_t)o0 * WPR;
+  for (int w = lane; w < nrows * WPR; w += 32) {
+    const int r = w / WPR, k = w - r * WPR;
+    sdst[w] = __ldg(ssrc + (size_t)list[(t0 + r) >> 3] * WPR + k);
+  }
+  // auxiliary rows: the child fill pattern
+  for (int a = 0; a < aux.n; ++a) {
+    const lv_aux_array& A = aux.a[a];
+    const size_t row = (size_t)A.width * A.elem_bytes;
+    char* base = (char*)A.out + row * (size_t)o0;
+    if (A.elem_bytes == 4 && (row & 15) == 0 && ((uintptr_t)base & 15) == 0) {
+      const uint4 f = make_uint4(A.fill, A.fill, A.fill, A.fill);
+      const int words = (int)(row / 16) * nrows;
+      for (int w = lane; w < words; w += 32) ((uint4*)base)[w] = f;
+    } else {
+      for (int r = lane; r < nrows; r += 32) aux_fill(A, o0 + r);
+    }
+  }
 }
 
 }  // namespace

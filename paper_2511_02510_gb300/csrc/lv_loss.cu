@@ -97,41 +97,46 @@ __device__ __forceinline__ void block_add_f64(double v, double* dst) {
   __syncthreads();
 }
 
-// Eq. 7: w = (eps + 1 - s)^gamma, s = clip(|grad| / P, 0, 1); blocks never span views
+// Eq. 7: w = (eps + 1 - s)^gamma, s = clip(|grad| / P, 0, 1); blocks never span views.
+// Grid-stride over the view's pixels with a bounded block count: one FP64
+// atomic per block (a per-256-pixel atomic would serialise at the L2).
 __global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery* q, const __grid_constant__ ViewPix vp,
                             int v, float eps, float gamma, float* w, double* wsum) {
-  const long long p = vp.off[v] + blockIdx.x * (long long)TPB + threadIdx.x;
-  float wv = 0.f;
-  if (p < vp.off[v + 1]) {
-    const float P = __uint_as_float(q[v].result);
+  const long long lo = vp.off[v], hi = vp.off[v + 1];
+  const float P = __uint_as_float(q[v].result);
+  const bool norm = q[v].k != 0 && P > 0.f;
+  double acc = 0.0;
+  for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     float s = 0.f;
-    if (q[v].k != 0 && P > 0.f) s = fminf(fmaxf(__uint_as_float(mkey[p]) / P, 0.f), 1.f);
-    wv = gamma == 0.f ? 1.f : powf(eps + 1.f - s, gamma);
+    if (norm) s = fminf(fmaxf(__uint_as_float(mkey[p]) / P, 0.f), 1.f);
+    const float wv = gamma == 0.f ? 1.f : powf(eps + 1.f - s, gamma);
     w[p] = wv;
+    acc += (double)wv;
   }
-  block_add_f64((double)wv, &wsum[v]);
+  block_add_f64(acc, &wsum[v]);
 }
 
 // Eq. 8 + Eq. 18: w~ = w / <w>, L = 1/|P| sum w~ mean_c r^2, dL/drgb = 2/(3|P|) w~ r
 __global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict__ gt, const float* __restrict__ w,
                           const __grid_constant__ ViewPix vp, int v, const double* wsum, double* lsum,
                           float* __restrict__ grad) {
-  const long long p = vp.off[v] + blockIdx.x * (long long)TPB + threadIdx.x;
-  const long long np = vp.off[v + 1] - vp.off[v];
-  double contrib = 0.0;
-  if (p < vp.off[v + 1]) {
-    const float mean = (float)(wsum[v] / (double)np);
+  const long long lo = vp.off[v], hi = vp.off[v + 1];
+  const long long np = hi - lo;
+  const float mean = (float)(wsum[v] / (double)np);
+  const float gscale = (float)(2.0 / (3.0 * (double)np));
+  double acc = 0.0;
+  for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     const float wt = w[p] / mean;
     const float r0 = rgb[3 * p] - gt[3 * p], r1 = rgb[3 * p + 1] - gt[3 * p + 1], r2 = rgb[3 * p + 2] - gt[3 * p + 2];
-    contrib = (double)wt * ((double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2) / 3.0;
+    acc += (double)wt * ((double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2) / 3.0;
     if (grad) {
-      const float c = (float)(2.0 / (3.0 * (double)np)) * wt;
+      const float c = gscale * wt;
       grad[3 * p] = c * r0;
       grad[3 * p + 1] = c * r1;
       grad[3 * p + 2] = c * r2;
     }
   }
-  block_add_f64(contrib, &lsum[v]);
+  block_add_f64(acc, &lsum[v]);
 }
 
 __global__ void k_lf_finish(const __grid_constant__ ViewPix vp, const double* lsum, float* loss) {
@@ -200,13 +205,17 @@ extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, cons
   k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
   k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
   select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
+  auto blocks_for = [](long long np) {
+    const long long b = (np + 4 * TPB - 1) / (4 * TPB);  // about four pixels per thread
+    return (unsigned)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+  };
   for (int v = 0; v < n_views; ++v) {
     const long long np = vp.off[v + 1] - vp.off[v];
-    k_lf_weight<<<(unsigned)((np + TPB - 1) / TPB), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum);
+    k_lf_weight<<<blocks_for(np), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum);
   }
   for (int v = 0; v < n_views; ++v) {
     const long long np = vp.off[v + 1] - vp.off[v];
-    k_lf_loss<<<(unsigned)((np + TPB - 1) / TPB), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
+    k_lf_loss<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
   }
   k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
   count_launch(3 + 2 * n_views);

@@ -260,15 +260,38 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
   Y[15] = C3a * x * (xx - 3.f * yy);
 }
 
-template <typename ST>
-__device__ __forceinline__ void sh_raw(const ST* __restrict__ sh, int nb, const float* Y, float* raw) {
+// one voxel's 48 SH coefficients into registers with 16-byte loads
+__device__ __forceinline__ void load_sh_row(const float* __restrict__ row, float* c) {
+  const float4* v = (const float4*)row;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 q = __ldg(v + k);
+    c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
+  }
+}
+__device__ __forceinline__ void load_sh_row(const __nv_bfloat16* __restrict__ row, float* c) {
+  const uint4* v = (const uint4*)row;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint4 q = __ldg(v + k);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      c[8 * k + 2 * h] = __uint_as_float(w[h] << 16);
+      c[8 * k + 2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
+    }
+  }
+}
+
+// c = max(0, raw) with raw = sum_j coef[j] Y_j + 0.5 per channel; coef laid out [j][rgb] with stride cs
+__device__ __forceinline__ void sh_raw(const float* coef, int cs, int nb, const float* Y, float* raw) {
   float r = 0.f, g = 0.f, b = 0.f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     if (j < nb) {
-      r = fmaf(to_f32(sh[3 * j + 0]), Y[j], r);
-      g = fmaf(to_f32(sh[3 * j + 1]), Y[j], g);
-      b = fmaf(to_f32(sh[3 * j + 2]), Y[j], b);
+      r = fmaf(coef[(3 * j + 0) * cs], Y[j], r);
+      g = fmaf(coef[(3 * j + 1) * cs], Y[j], g);
+      b = fmaf(coef[(3 * j + 2) * cs], Y[j], b);
     }
   }
   raw[0] = r + 0.5f;
@@ -313,8 +336,10 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   unit_dir(rx, ry, rz, dir);
   float Y[16];
   sh_basis(dir[0], dir[1], dir[2], Y);
+  float coef[48];
+  load_sh_row(sh + 48 * vox, coef);
   float raw[3];
-  sh_raw(sh + 48 * vox, sh_nb, Y, raw);
+  sh_raw(coef, 1, sh_nb, Y, raw);
   float d[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * vox + k]);
@@ -386,24 +411,36 @@ __device__ __forceinline__ Ray make_ray(const DevView& c, int px, int py) {
   return r;
 }
 
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // Chord of the ray (origin at the camera) through the box centred at rc
 // (relative to the camera) with half-size h, clipped to start at the near
-// plane.  Identical code in the forward and backward kernels, so both take
-// the same hit decisions.
+// plane: slab a enters at (rc_a - h sign) / d_a and leaves at (rc_a + h sign) / d_a.
+// Identical code in the forward and backward kernels, so both take the same
+// hit decisions.
 __device__ __forceinline__ bool chord(const Ray& r, float4 g, float& t_in, float& t_out) {
-  float qx = g.x * r.ix, qy = g.y * r.iy, qz = g.z * r.iz;
-  float ex = g.w * r.ax, ey = g.w * r.ay, ez = g.w * r.az;
-  t_in = fmaxf(fmaxf(qx - ex, qy - ey), fmaxf(qz - ez, r.tnear));
-  t_out = fminf(fminf(qx + ex, qy + ey), qz + ez);
+  const float qx = g.x * r.ix, qy = g.y * r.iy, qz = g.z * r.iz;
+  t_in = fmaxf(max3(fmaf(-g.w, r.ax, qx), fmaf(-g.w, r.ay, qy), fmaf(-g.w, r.az, qz)), r.tnear);
+  t_out = min3(fmaf(g.w, r.ax, qx), fmaf(g.w, r.ay, qy), fmaf(g.w, r.az, qz));
   return t_out > t_in;
 }
 
-// local coordinates of the chord midpoint in [0,1]^3 and the trilinear density
+// local coordinates u = (p - (c - h)) / (2h) = (t d - rc) / (2h) + 1/2 of the
+// chord midpoint, clamped to [0,1]^3, and the trilinear density there
 __device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, float4 d1, float i2h, float tm,
                                              float* u) {
-  u[0] = __saturatef((fmaf(tm, r.dx, -g.x) + g.w) * i2h);
-  u[1] = __saturatef((fmaf(tm, r.dy, -g.y) + g.w) * i2h);
-  u[2] = __saturatef((fmaf(tm, r.dz, -g.z) + g.w) * i2h);
+  u[0] = __saturatef(fmaf(fmaf(tm, r.dx, -g.x), i2h, 0.5f));
+  u[1] = __saturatef(fmaf(fmaf(tm, r.dy, -g.y), i2h, 0.5f));
+  u[2] = __saturatef(fmaf(fmaf(tm, r.dz, -g.z), i2h, 0.5f));
   float c00 = fmaf(u[0], d0.y - d0.x, d0.x);
   float c10 = fmaf(u[0], d0.w - d0.z, d0.z);
   float c01 = fmaf(u[0], d1.y - d1.x, d1.x);
@@ -413,18 +450,15 @@ __device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, 
   return fmaf(u[2], c1 - c0, c0);
 }
 
-// 1 - exp(-x) accurate for small x (Taylor series below 1/8)
+// 1 - exp(-x) given e = exp(-x): a 5-term series below 1/8 (relative error
+// < 5e-8 there), 1 - e above; branch-free
 __device__ __forceinline__ float one_minus_exp(float x, float e) {
-  if (x < 0.125f) {
-    float p = fmaf(x, -1.f / 5040.f, 1.f / 720.f);
-    p = fmaf(x, p, -1.f / 120.f);
-    p = fmaf(x, p, 1.f / 24.f);
-    p = fmaf(x, p, -1.f / 6.f);
-    p = fmaf(x, p, 0.5f);
-    p = fmaf(x, p, -1.f);
-    return -x * p;
-  }
-  return 1.f - e;
+  float p = fmaf(x, -1.f / 120.f, 1.f / 24.f);
+  p = fmaf(x, p, -1.f / 6.f);
+  p = fmaf(x, p, 0.5f);
+  p = fmaf(x, -p, 1.f);
+  p *= x;
+  return x < 0.125f ? p : 1.f - e;
 }
 
 __device__ __forceinline__ int find_view(const ViewSet& vs, int gtile) {
@@ -649,6 +683,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
   const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
   const float tgT = Tf * gT;
   float S = 0.f;
+  float Tcur = __expf(-tau);  // T after the last sample, from the stored optical depth
   // chunks aligned as in the forward: [start + 32 k, start + 32 k + 32)
   for (uint32_t cb = start + ((warp_hi - start + 31u) & ~31u); cb > start; cb -= 32) {
     const uint32_t base = cb - 32;
@@ -689,9 +724,10 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
         const float sraw = mid_density(r, g, d0, d1, col.w, tm, u);
         const float sigma = fmaxf(sraw, 0.f);
         const float x = sigma * l;
-        const float Tk = __expf(-tau);
+        const float Tk = Tcur;  // transmittance after this sample: the previous step's T_prev
         const float tau_prev = fmaxf(tau - x, 0.f);
         const float T_prev = __expf(-tau_prev);
+        Tcur = T_prev;
         const float alpha = one_minus_exp(x, __expf(-x));
         const float w = T_prev * alpha;
         const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
@@ -741,57 +777,93 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
 }
 
 // ------------------------------------------------------------------ SH backward
+// A warp handles 32 consecutive voxels: their SH rows are staged through shared
+// memory with coalesced 16-byte loads (row stride 49 floats: conflict-free per
+// lane), each lane sums its voxel's colour gradients over the views through
+// c = max(0, SH + 0.5), and the 32 gradient rows leave through shared memory as
+// coalesced 16-byte stores.
 template <typename ST>
 __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, const ST* __restrict__ sh, int sh_nb,
                                                 int64_t n, const __grid_constant__ ViewSet vs,
                                                 const uint32_t* __restrict__ vis, const uint32_t* __restrict__ slot,
                                                 float4* __restrict__ d_rgb, float* __restrict__ d_sh,
                                                 int accumulate) {
-  int64_t vox = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (vox >= n) return;
+  constexpr int RS = 49;
+  __shared__ float s_rows[4][32 * RS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t v0 = (blockIdx.x * 4 + warp) * (int64_t)32;
+  if (v0 >= n) return;  // warp-uniform
+  const int nrows = (int)min((int64_t)32, n - v0);
+  float* buf = s_rows[warp];
+  if constexpr (sizeof(ST) == 4) {
+    const float4* src = (const float4*)(sh + 48 * v0);
+    for (int w = lane; w < nrows * 12; w += 32) {
+      const float4 q = __ldg(src + w);
+      float* d = buf + (w / 12) * RS + (w % 12) * 4;
+      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
+    }
+  } else {
+    const uint4* src = (const uint4*)(sh + 48 * v0);
+    for (int w = lane; w < nrows * 6; w += 32) {
+      const uint4 q = __ldg(src + w);
+      float* d = buf + (w / 6) * RS + (w % 6) * 8;
+      const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        d[2 * h] = __uint_as_float(u[h] << 16);
+        d[2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+      }
+    }
+  }
+  __syncwarp();
   float acc[48];
 #pragma unroll
   for (int k = 0; k < 48; ++k) acc[k] = 0.f;
-  const float4 g = geom[vox];
-  bool any = false;
-  for (int view = 0; view < vs.n; ++view) {
-    const int64_t i = vox * vs.n + view;
-    if (!vis[i]) continue;
-    const DevView& c = vs.v[view];
-    const uint32_t s = slot[i];
-    float dir[3];
-    unit_dir(g.x - c.o[0], g.y - c.o[1], g.z - c.o[2], dir);
-    float Y[16];
-    sh_basis(dir[0], dir[1], dir[2], Y);
-    float raw[3];
-    sh_raw(sh + 48 * vox, sh_nb, Y, raw);
-    const float4 dc = d_rgb[s];
-    const float dr = raw[0] > 0.f ? dc.x : 0.f;
-    const float dg = raw[1] > 0.f ? dc.y : 0.f;
-    const float db = raw[2] > 0.f ? dc.z : 0.f;
-    d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);  // leave the scratch cleared for the next backward call
+  if (lane < nrows) {
+    const int64_t vox = v0 + lane;
+    const float4 g = geom[vox];
+    const float* row = buf + lane * RS;
+    for (int view = 0; view < vs.n; ++view) {
+      const int64_t i = vox * vs.n + view;
+      if (!vis[i]) continue;
+      const DevView& c = vs.v[view];
+      const uint32_t s = slot[i];
+      float dir[3];
+      unit_dir(g.x - c.o[0], g.y - c.o[1], g.z - c.o[2], dir);
+      float Y[16];
+      sh_basis(dir[0], dir[1], dir[2], Y);
+      float raw[3];
+      sh_raw(row, 1, sh_nb, Y, raw);
+      const float4 dc = d_rgb[s];
+      const float dr = raw[0] > 0.f ? dc.x : 0.f;
+      const float dg = raw[1] > 0.f ? dc.y : 0.f;
+      const float db = raw[2] > 0.f ? dc.z : 0.f;
+      d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);  // leave the scratch cleared for the next backward call
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (j < sh_nb) {
-        acc[3 * j + 0] = fmaf(Y[j], dr, acc[3 * j + 0]);
-        acc[3 * j + 1] = fmaf(Y[j], dg, acc[3 * j + 1]);
-        acc[3 * j + 2] = fmaf(Y[j], db, acc[3 * j + 2]);
+      for (int j = 0; j < 16; ++j) {
+        if (j < sh_nb) {
+          acc[3 * j + 0] = fmaf(Y[j], dr, acc[3 * j + 0]);
+          acc[3 * j + 1] = fmaf(Y[j], dg, acc[3 * j + 1]);
+          acc[3 * j + 2] = fmaf(Y[j], db, acc[3 * j + 2]);
+        }
       }
     }
-    any = true;
   }
-  float4* out = (float4*)(d_sh + 48 * vox);
-  if (accumulate) {
-    if (!any) return;
+  __syncwarp();
+  if (lane < nrows) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      float4 o = out[k];
-      o.x += acc[4 * k]; o.y += acc[4 * k + 1]; o.z += acc[4 * k + 2]; o.w += acc[4 * k + 3];
-      out[k] = o;
+    for (int k = 0; k < 48; ++k) buf[lane * RS + k] = acc[k];
+  }
+  __syncwarp();
+  float4* dst = (float4*)(d_sh + 48 * v0);
+  for (int w = lane; w < nrows * 12; w += 32) {
+    const float* a = buf + (w / 12) * RS + (w % 12) * 4;
+    float4 o = make_float4(a[0], a[1], a[2], a[3]);
+    if (accumulate) {
+      const float4 p = dst[w];
+      o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    dst[w] = o;
   }
 }
 
@@ -966,7 +1038,7 @@ static lv_status launch_sh_bwd(const lv_voxels* vox, const ViewSet& vs, const Fw
   const int64_t n = vox->n;
   if (n == 0) return LV_OK;
   const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
-  const int blocks = (int)((n + 127) / 128);
+  const int blocks = (int)((n + 127) / 128);  // 4 warps x 32 voxels
   if (vox->sh_dtype == LV_F32)
     k_sh_bwd<float><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const float*)vox->sh, nb, n, vs, w.vis, w.slot,
                                            w.d_rgb, d_sh, accumulate);

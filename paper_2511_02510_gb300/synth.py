@@ -176,24 +176,42 @@ def _spec_360(seed: int, band: float, halo: float) -> SceneSpec:
                      shell=(12.0, 16.0))
 
 
-def scene_360(seed: int = 0, band: float = 2.0, halo: float = 1.0) -> dict:
-    """Mip-NeRF-360-shaped scene: ~2M voxels, levels 6-12, coarse background shell r in [12, 16]."""
-    return make_scene(_spec_360(seed, band, halo))
+def _opaque_peak(spec: SceneSpec, tau_finest: float = 2.5) -> float:
+    """Peak density giving optical depth ``tau_finest`` across one finest-level voxel."""
+    return tau_finest / (spec.root_edge / (1 << spec.l_max_fg))
 
 
-def scene_tt(seed: int = 0, band: float = 1.0, halo: float = 0.6) -> dict:
+def scene_360(seed: int = 0, band: float = 2.0, halo: float = 1.0, opaque: bool = True) -> dict:
+    """Mip-NeRF-360-shaped scene: ~2M voxels, levels 6-12, coarse background shell r in [12, 16].
+
+    opaque=True scales the peak corner density so that a finest-level voxel
+    inside a solid has optical depth 2.5 (surfaces stop rays within a few
+    voxels, as in a trained scene); opaque=False keeps the peak of 10 per unit
+    length of the unit-cube recipe (semi-transparent objects).
+    """
+    spec = _spec_360(seed, band, halo)
+    if opaque:
+        spec.density_peak = _opaque_peak(spec)
+    return make_scene(spec)
+
+
+def scene_tt(seed: int = 0, band: float = 1.0, halo: float = 0.6, opaque: bool = True) -> dict:
     """Tanks-and-Temples-shaped scene: ~6M voxels, levels 6-13, wider foreground extent."""
     spec = SceneSpec(seed=seed, root_min=(-16, -16, -16), root_edge=32.0, l_min=6, l_max_fg=13, l_max_bg=8,
                      band=band, halo=halo, fg_center=(0.0, 0.0, 0.0), fg_scale=3.0, fg_box_half=0.5,
                      shell=(12.0, 16.0))
+    if opaque:
+        spec.density_peak = _opaque_peak(spec)
     return make_scene(spec)
 
 
-def scene_stress(seed: int = 0, band: float = 1.2, halo: float = 0.7) -> dict:
+def scene_stress(seed: int = 0, band: float = 1.2, halo: float = 0.7, opaque: bool = True) -> dict:
     """Growth-budget stress scene: ~10M voxels, levels 6-13."""
     spec = SceneSpec(seed=seed, root_min=(-16, -16, -16), root_edge=32.0, l_min=6, l_max_fg=13, l_max_bg=8,
                      band=band, halo=halo, fg_center=(0.0, 0.0, 0.0), fg_scale=3.0, fg_box_half=0.5,
                      shell=(12.0, 16.0))
+    if opaque:
+        spec.density_peak = _opaque_peak(spec)
     return make_scene(spec)
 
 
