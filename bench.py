@@ -141,7 +141,8 @@ class Workload:
             self.aux.append(a)
 
     # stage boundaries, for the per-kernel breakdown
-    STAGES = ["reset", "forward", "loss", "backward", "sh_backward", "unpack", "prune", "subdivide"]
+    STAGES = ["reset", "forward", "loss", "backward", "sh_backward", "unpack", "prune", "subdivide_select",
+              "subdivide_apply"]
 
     def step(self, ev=None):
         L, r = self.L, self.rctx
@@ -168,9 +169,11 @@ class Workload:
         L.lv_prune_depth_quantile(self.w_max, r.seen, r.z_min, self.ema, self.state, self.pp, self.pmask,
                                   self.n_pruned, self.pr_ws)
         mark(7)
-        L.lv_subdivide_priority(self.vox, r.delta_min, r.z_min, self.w_max, r.seen, self.pmask, self.sp, self.aux,
-                                self.vout, self.selected, self.n_new, self.sd_ws, self.status)
+        L.lv_subdivide_select(self.vox, r.delta_min, r.z_min, self.w_max, r.seen, self.pmask, self.sp, self.cap,
+                              self.selected, self.n_new, self.sd_ws, self.status)
         mark(8)
+        L.lv_subdivide_apply(self.vox, self.sp, self.aux, self.vout, self.sd_ws)
+        mark(9)
 
     def e2e_step(self):
         """The same step through the public API with host buffers: the step's ground-truth
@@ -185,7 +188,13 @@ class Workload:
         pairs, slots = self.rctx.counters()
         return {"pairs": pairs, "visible_slots": slots, "n_pruned": int(self.n_pruned.item()),
                 "n_new": int(self.n_new.item()), "status": int(self.status.item() | self.rctx.status.item()),
-                "samples": int(self.rctx.n_samples.to(self.torch.int64).sum().item())}
+                "samples": int(self.rctx.n_samples.to(self.torch.int64).sum().item()),
+                "split": int(self.selected.to(self.torch.int64).sum().item())}
+
+    def row_bytes(self):
+        """Bytes of one voxel's state rows: geometry, level, corners, SH and the auxiliary arrays."""
+        b = 16 + 1 + 8 * self.scene.density.element_size() + 48 * self.scene.sh.element_size()
+        return b + sum(t[0].numel() * t.element_size() for t in self.aux_in)
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -261,14 +270,16 @@ def alu_peak_tflops(sm_mhz):
     return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
-def algorithmic_bytes(stage, n, pairs, slots, npix):
+def algorithmic_bytes(stage, n, pairs, slots, npix, n_new=0, split=0, row=0, parent_row=0):
     """Bytes a stage must move at least once (inputs read, outputs written) for one step."""
     if stage == "backward_composite":
         # per pair: the slot index and the 64-byte record; per pixel: dL/drgb, T, n_contrib and the
         # optical depth (24); d_density (32 n) and the colour gradients (16 per slot) accumulated
         return pairs * (4 + 64) + npix * 24 + 32 * n + 16 * slots
-    if stage == "subdivide":
-        return n * (16 + 1 + 32 + 192 + 4 * 3 + 1 + 2 * (32 + 192) + 4 + 1) * 2
+    if stage == "subdivide_apply":
+        # survivors' rows read and written, children's rows written, split parents' rows read once
+        survivors = n_new - 8 * split
+        return survivors * row * 2 + 8 * split * row + split * parent_row
     return 0
 
 
@@ -417,25 +428,40 @@ def run_ours(args, rank, world, local):
     if cnt["status"] != 0:
         raise RuntimeError(f"device status {cnt['status']} during warm-up")
 
-    # ---- timed region: K steps, device time with CUDA events, per-stage events
+    # ---- per-stage breakdown: K eager steps with an event at every stage boundary
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(Workload.STAGES) + 1)] for _ in range(K)]
+    launches0 = L.launch_count()
+    wl.step()
+    launches_per_step = L.launch_count() - launches0
+    torch.cuda.synchronize()
+    for k in range(K):
+        wl.step(evs[k])
+    torch.cuda.synchronize()
+    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]))
+                for i, s in enumerate(Workload.STAGES)}
+    eager_ms = float(np.mean([evs[k][0].elapsed_time(evs[k][-1]) for k in range(K)]))
+
+    # ---- timed region: K replays of the step captured in one CUDA graph
+    from paper_2511_02510_gb300.raster import CapturedStep
+    graph_step = CapturedStep(wl.step)
+    for _ in range(max(3, args.warmup)):
+        graph_step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clk.start()
     time.sleep(0.2)
-    launches0 = L.launch_count()
+    e0.record()
     for k in range(K):
-        wl.step(evs[k])
-    launches = L.launch_count() - launches0
+        graph_step()
+    e1.record()
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    ms_steps = [evs[k][0].elapsed_time(evs[k][-1]) for k in range(K)]
-    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]))
-                for i, s in enumerate(Workload.STAGES)}
-    ms = float(np.sum(ms_steps)) / K
+    launches = launches_per_step * K
+    ms = e0.elapsed_time(e1) / K
     t = torch.tensor([ms], device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -458,18 +484,23 @@ def run_ours(args, rank, world, local):
     cnt = wl.counters()
     if rank == 0:
         hbm_peak, peak_src = peaks()
-        # dominant kernel: the backward composite (alone in the "backward" stage); it is bound by
-        # FP32 instruction issue, not by memory: report it against the FP32 ALU peak
-        t_bwd = stage_ms["backward"]
-        sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
-        flops = cnt["samples"] * FLOPS_PER_SAMPLE["backward_composite"]
-        achieved = flops / (t_bwd / 1e3) / 1e12
-        peak = alu_peak_tflops(sm_mhz)
-        bytes_bwd = algorithmic_bytes("backward_composite", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix)
+        # dominant kernel: the subdivision write (one launch, alone in the "subdivide_apply" stage),
+        # an HBM-bound copy of every surviving voxel's state plus the children
+        t_apply = stage_ms["subdivide_apply"]
+        row = wl.row_bytes()
+        parent_row = 16 + 1 + 8 * wl.scene.density.element_size() + 48 * wl.scene.sh.element_size()
+        bytes_apply = algorithmic_bytes("subdivide_apply", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix,
+                                        cnt["n_new"], cnt["split"], row, parent_row)
+        achieved = bytes_apply / (t_apply / 1e3) / 1e9
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
-            traffic = json.load(open(tp)).get("backward_composite")
+            traffic = json.load(open(tp)).get("subdivide_apply")
+        # the composite kernels are bound by FP32 instruction issue: reported beside it
+        sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+        t_bwd = stage_ms["backward"]
+        bwd_flops = cnt["samples"] * FLOPS_PER_SAMPLE["backward_composite"]
+        bytes_bwd = algorithmic_bytes("backward_composite", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic",
@@ -478,15 +509,20 @@ def run_ours(args, rank, world, local):
                           "voxels": wl.n, "pixels_per_rank": wl.npix, "pairs": cnt["pairs"],
                           "visible_slots": cnt["visible_slots"], "tile": 16, "batch": 256,
                           "l2": "inputs larger than L2 (scene arrays 480 MB, per-step outputs > 600 MB)"},
-               "roofline": {"bound": "alu", "kernel": "k_bwd (backward composite)", "achieved": achieved,
-                            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                            "samples": cnt["samples"], "flops_per_sample": FLOPS_PER_SAMPLE["backward_composite"],
-                            "hbm": {"algorithmic_bytes": bytes_bwd,
-                                    "achieved_gbs": bytes_bwd / (t_bwd / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                                    "frac": bytes_bwd / (t_bwd / 1e3) / 1e9 / hbm_peak,
-                                    "peak_source": peak_src}},
-               "stages_ms": stage_ms,
+               "roofline": {"bound": "hbm", "kernel": "k_sd_write (subdivision: survivor and child rows)",
+                            "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                            "traffic": traffic, "peak_source": peak_src, "algorithmic_bytes": bytes_apply,
+                            "row_bytes": row,
+                            "backward_composite": {
+                                "bound": "alu", "achieved_tflops": bwd_flops / (t_bwd / 1e3) / 1e12,
+                                "peak_tflops": alu_peak_tflops(sm_mhz),
+                                "frac": bwd_flops / (t_bwd / 1e3) / 1e12 / alu_peak_tflops(sm_mhz),
+                                "samples": cnt["samples"], "flops_per_sample": FLOPS_PER_SAMPLE["backward_composite"],
+                                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                                "hbm_achieved_gbs": bytes_bwd / (t_bwd / 1e3) / 1e9}},
+               "stages_ms": stage_ms, "eager_ms_per_step": eager_ms,
+               "timing": "device time of K replays of the step captured in one CUDA graph (CUDA events); "
+                         "stages_ms from K eager steps with an event at every stage boundary",
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(wl.gt_host.numel() * 4),
                        "d2h_bytes_per_step": 4},
                "gpu_launches": int(launches),

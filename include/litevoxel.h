@@ -261,6 +261,20 @@ lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const f
                                 int64_t* d_n_new, void* workspace, size_t ws_bytes, int32_t* d_status,
                                 void* stream);
 
+/* The two halves of lv_subdivide_priority, for callers that want to look at
+ * the selection (selected, d_n_new) before the arrays are written, or to time
+ * the halves separately.  lv_subdivide_select takes the selection and
+ * checks that out_capacity >= n_alive + 7 k (else LV_ERR_CAPACITY in d_status
+ * and the apply step writes nothing); lv_subdivide_apply writes the survivors
+ * and children into `out` (one kernel).  Both take the same `in`, `p` and
+ * workspace, select first; the workspace carries the selection between them. */
+lv_status lv_subdivide_select(const lv_voxels* in, const float* delta, const float* z, const float* u,
+                              const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
+                              int64_t out_capacity, uint8_t* selected, int64_t* d_n_new, void* workspace,
+                              size_t ws_bytes, int32_t* d_status, void* stream);
+lv_status lv_subdivide_apply(const lv_voxels* in, const lv_subdiv_params* p, const lv_aux_array* aux, int n_aux,
+                             const lv_voxels* out, void* workspace, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* LF-weighted photometric loss (Sec. IV-B, Eq. 7-10, 18)               */
 /* ------------------------------------------------------------------ */

@@ -410,14 +410,12 @@ __device__ __forceinline__ void warp_copy_rows(const char* __restrict__ in, char
 }
 
 template <typename DT, typename ST>
-__global__ void k_sd_write_survivors(int64_t n, const uint32_t* __restrict__ surv,
-                                     const unsigned long long* __restrict__ pos, const SubState* st,
-                                     const float4* __restrict__ geom, const uint8_t* __restrict__ level,
-                                     const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
-                                     uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
+__device__ __forceinline__ void write_survivors(int64_t i0, int64_t n, const uint32_t* __restrict__ surv,
+                                                const unsigned long long* __restrict__ pos,
+                                                const float4* __restrict__ geom, const uint8_t* __restrict__ level,
+                                                const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
+                                                uint8_t* olevel, DT* odens, ST* osh, const AuxSet& aux) {
   const int lane = threadIdx.x & 31;
-  const int64_t i0 = (blockIdx.x * (int64_t)TPB + threadIdx.x) & ~(int64_t)31;
-  if (i0 >= n || !st->fits) return;  // warp-uniform
   const int64_t i = i0 + lane;
   const uint32_t keep = __ballot_sync(FULL, i < n && surv[i] != 0);
   if (!keep) return;
@@ -455,14 +453,12 @@ __global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uin
 // the auxiliary rows are written cooperatively in 16-byte words so that the
 // stores coalesce (the 8 children of a parent read the same parent row).
 template <typename DT, typename ST>
-__global__ void k_sd_write_children(int64_t max_children, const uint32_t* __restrict__ list,
-                                    const unsigned long long* totals, const SubState* st,
-                                    const float4* __restrict__ geom, const uint8_t* __restrict__ level,
-                                    const DT* __restrict__ dens, const ST* __restrict__ sh, float4* ogeom,
-                                    uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
+__device__ __forceinline__ void write_children(int64_t t0, const uint32_t* __restrict__ list,
+                                               const unsigned long long* totals, const float4* __restrict__ geom,
+                                               const uint8_t* __restrict__ level, const DT* __restrict__ dens,
+                                               const ST* __restrict__ sh, float4* ogeom, uint8_t* olevel, DT* odens,
+                                               ST* osh, const AuxSet& aux) {
   const int lane = threadIdx.x & 31;
-  const int64_t t0 = (blockIdx.x * (int64_t)TPB + threadIdx.x) & ~(int64_t)31;
-  if (t0 >= max_children || !st->fits) return;  // warp-uniform
   const int64_t nchild = 8 * (int64_t)totals[1];
   if (t0 >= nchild) return;
   const int nrows = (int)min((int64_t)32, nchild - t0);
@@ -511,6 +507,26 @@ __global__ void k_sd_write_children(int64_t max_children, const uint32_t* __rest
     } else {
       for (int r = lane; r < nrows; r += 32) aux_fill(A, o0 + r);
     }
+  }
+}
+
+// All the writes of a topology change in one launch: warps [0, sw) copy the
+// survivors of 32 consecutive voxels each, warps [sw, ...) write 32 children each.
+template <typename DT, typename ST>
+__global__ void k_sd_write(int64_t n, int64_t max_children, const uint32_t* __restrict__ surv,
+                           const unsigned long long* __restrict__ pos, const uint32_t* __restrict__ list,
+                           const unsigned long long* totals, const SubState* st, const float4* __restrict__ geom,
+                           const uint8_t* __restrict__ level, const DT* __restrict__ dens, const ST* __restrict__ sh,
+                           float4* ogeom, uint8_t* olevel, DT* odens, ST* osh, const __grid_constant__ AuxSet aux) {
+  if (!st->fits) return;
+  const int64_t gw = (blockIdx.x * (int64_t)TPB + threadIdx.x) >> 5;  // global warp
+  const int64_t sw = (n + 31) / 32;
+  if (gw < sw) {
+    write_survivors<DT, ST>(gw * 32, n, surv, pos, geom, level, dens, sh, ogeom, olevel, odens, osh, aux);
+  } else {
+    const int64_t t0 = (gw - sw) * 32;
+    if (t0 < max_children)
+      write_children<DT, ST>(t0, list, totals, geom, level, dens, sh, ogeom, olevel, odens, osh, aux);
   }
 }
 
@@ -578,43 +594,51 @@ extern "C" size_t lv_subdivide_workspace_size(int64_t n, const lv_subdiv_params*
   return carve_sub(nullptr, n).bytes;
 }
 
-extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const float* z, const float* u,
-                                           const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
-                                           const lv_aux_array* aux, int n_aux, const lv_voxels* out,
-                                           uint8_t* selected, int64_t* d_n_new, void* workspace, size_t ws_bytes,
-                                           int32_t* d_status, void* stream) {
-  if (!in || !out || !p) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+static lv_status check_sub(const lv_voxels* in, const lv_subdiv_params* p, int n_aux, const lv_aux_array* aux,
+                           const lv_voxels* out) {
+  if (!in || !p) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
   const int64_t n = in->n;
-  if (n < 0 || n > 0x7fffffffLL || out->n < 0) { set_error("bad voxel counts"); return LV_ERR_INVALID_ARG; }
-  if (n > 0 && (!in->geom || !in->level || !in->density || !in->sh || !delta || !z || !u || !seen || !selected)) {
-    set_error("null array"); return LV_ERR_INVALID_ARG;
-  }
-  if (out->n > 0 && (!out->geom || !out->level || !out->density || !out->sh)) { set_error("null output array"); return LV_ERR_INVALID_ARG; }
-  if (in->density_dtype != out->density_dtype || in->sh_dtype != out->sh_dtype) { set_error("output dtypes must match the input"); return LV_ERR_INVALID_ARG; }
+  if (n < 0 || n > 0x7fffffffLL) { set_error("bad voxel count"); return LV_ERR_INVALID_ARG; }
+  if (n > 0 && (!in->geom || !in->level || !in->density || !in->sh)) { set_error("null voxel array"); return LV_ERR_INVALID_ARG; }
   if (in->density_dtype != LV_F32 && in->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
   if (in->sh_dtype != LV_F32 && in->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
-  if (n_aux < 0 || n_aux > LV_MAX_AUX || (n_aux > 0 && !aux)) { set_error("n_aux must be 0..%d", LV_MAX_AUX); return LV_ERR_INVALID_ARG; }
   if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||
       p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
-  AuxSet as;
-  as.n = n_aux;
+  if (out) {
+    if (out->n < 0) { set_error("bad output capacity"); return LV_ERR_INVALID_ARG; }
+    if (out->n > 0 && (!out->geom || !out->level || !out->density || !out->sh)) { set_error("null output array"); return LV_ERR_INVALID_ARG; }
+    if (in->density_dtype != out->density_dtype || in->sh_dtype != out->sh_dtype) { set_error("output dtypes must match the input"); return LV_ERR_INVALID_ARG; }
+  }
+  if (n_aux < 0 || n_aux > LV_MAX_AUX || (n_aux > 0 && !aux)) { set_error("n_aux must be 0..%d", LV_MAX_AUX); return LV_ERR_INVALID_ARG; }
   for (int a = 0; a < n_aux; ++a) {
-    as.a[a] = aux[a];
     const int eb = aux[a].elem_bytes;
     if ((eb != 1 && eb != 2 && eb != 4) || aux[a].width < 1 || (n > 0 && (!aux[a].in || !aux[a].out))) {
       set_error("aux array %d: bad description", a); return LV_ERR_INVALID_ARG;
     }
   }
+  return LV_OK;
+}
+
+extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta, const float* z, const float* u,
+                                         const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
+                                         int64_t out_capacity, uint8_t* selected, int64_t* d_n_new, void* workspace,
+                                         size_t ws_bytes, int32_t* d_status, void* stream) {
+  lv_status e = check_sub(in, p, 0, nullptr, nullptr);
+  if (e != LV_OK) return e;
+  const int64_t n = in->n;
+  if (n > 0 && (!delta || !z || !u || !seen || !selected)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
+  if (out_capacity < 0) { set_error("bad output capacity"); return LV_ERR_INVALID_ARG; }
   if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
   SubWs w = carve_sub(workspace, n);
   if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(w.st, 0, sizeof(SubState), s);
   if (n == 0) {
+    cudaMemsetAsync(w.totals, 0, 4 * sizeof(unsigned long long), s);
     if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
-    return cuda_check(cudaGetLastError(), "lv_subdivide_priority");
+    return cuda_check(cudaGetLastError(), "lv_subdivide_select");
   }
   const int blocks = blocks_for(n);
-  cudaMemsetAsync(w.st, 0, sizeof(SubState), s);
   k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st);
   uint32_t* cnt_seen = &w.st->n_el;  // temporarily counts alive & seen voxels
   k_sd_count_group0<<<blocks, TPB, 0, s>>>(n, w.grp, cnt_seen);
@@ -631,28 +655,55 @@ extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* del
   k_sd_select<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, in->level, (const float4*)in->geom, delta, w.pkey, w.q,
                                       p->kappa, p->l_max, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
-  k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out->n, d_n_new, d_status ? d_status : (int32_t*)nullptr);
+  k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
+  k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
+  count_launch(12);
+  return cuda_check(cudaGetLastError(), "lv_subdivide_select");
+}
+
+extern "C" lv_status lv_subdivide_apply(const lv_voxels* in, const lv_subdiv_params* p, const lv_aux_array* aux,
+                                        int n_aux, const lv_voxels* out, void* workspace, size_t ws_bytes,
+                                        void* stream) {
+  lv_status e = check_sub(in, p, n_aux, aux, out);
+  if (e != LV_OK) return e;
+  if (!out) { set_error("null output"); return LV_ERR_INVALID_ARG; }
+  const int64_t n = in->n;
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  SubWs w = carve_sub(workspace, n);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  if (n == 0) return LV_OK;
+  AuxSet as;
+  as.n = n_aux;
+  for (int a = 0; a < n_aux; ++a) as.a[a] = aux[a];
+  cudaStream_t s = (cudaStream_t)stream;
   // children: at most floor(top * n) splits
   const int64_t max_children = 8 * (int64_t)(((unsigned long long)p->top_ppm * (unsigned long long)n) / 1000000ull);
-  const int cblocks = blocks_for(max_children);
-  k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
-#define LV_SUB(DT, ST)                                                                                                \
-  do {                                                                                                                \
-    k_sd_write_survivors<DT, ST><<<blocks, TPB, 0, s>>>(n, w.surv, w.surv_pos, w.st, (const float4*)in->geom,        \
-                                                        in->level, (const DT*)in->density, (const ST*)in->sh,         \
-                                                        (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
-                                                        (ST*)out->sh, as);                                            \
-    k_sd_write_children<DT, ST><<<cblocks, TPB, 0, s>>>(max_children, w.sel_list, w.totals, w.st,                    \
-                                                        (const float4*)in->geom,                                      \
-                                                        in->level, (const DT*)in->density, (const ST*)in->sh,         \
-                                                        (float4*)out->geom, (uint8_t*)out->level, (DT*)out->density,  \
-                                                        (ST*)out->sh, as);                                            \
-  } while (0)
+  const int64_t warps = (n + 31) / 32 + (max_children + 31) / 32;
+  const unsigned grid = (unsigned)((warps * 32 + TPB - 1) / TPB);
+#define LV_SUB(DT, ST)                                                                                                 \
+  k_sd_write<DT, ST><<<grid, TPB, 0, s>>>(n, max_children, w.surv, w.surv_pos, w.sel_list, w.totals, w.st,           \
+                                          (const float4*)in->geom, in->level, (const DT*)in->density,                \
+                                          (const ST*)in->sh, (float4*)out->geom, (uint8_t*)out->level,               \
+                                          (DT*)out->density, (ST*)out->sh, as)
   if (in->density_dtype == LV_F32 && in->sh_dtype == LV_F32) LV_SUB(float, float);
   else if (in->density_dtype == LV_F16 && in->sh_dtype == LV_F32) LV_SUB(__half, float);
   else if (in->density_dtype == LV_F32 && in->sh_dtype == LV_BF16) LV_SUB(float, __nv_bfloat16);
   else LV_SUB(__half, __nv_bfloat16);
 #undef LV_SUB
-  count_launch(13);
-  return cuda_check(cudaGetLastError(), "lv_subdivide_priority");
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_subdivide_apply");
+}
+
+extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const float* z, const float* u,
+                                           const uint8_t* seen, const uint8_t* prune_mask, const lv_subdiv_params* p,
+                                           const lv_aux_array* aux, int n_aux, const lv_voxels* out,
+                                           uint8_t* selected, int64_t* d_n_new, void* workspace, size_t ws_bytes,
+                                           int32_t* d_status, void* stream) {
+  lv_status e = check_sub(in, p, n_aux, aux, out);
+  if (e != LV_OK) return e;
+  if (!out) { set_error("null output"); return LV_ERR_INVALID_ARG; }
+  e = lv_subdivide_select(in, delta, z, u, seen, prune_mask, p, out->n, selected, d_n_new, workspace, ws_bytes,
+                          d_status, stream);
+  if (e != LV_OK) return e;
+  return lv_subdivide_apply(in, p, aux, n_aux, out, workspace, ws_bytes, stream);
 }

@@ -97,6 +97,10 @@ SIGNATURES = {
     "lv_subdivide_workspace_size": (_SZ, [_I64, C.POINTER(lv_subdiv_params)]),
     "lv_subdivide_priority": (C.c_int, [_PV, _P, _P, _P, _P, _P, C.POINTER(lv_subdiv_params),
                                         C.POINTER(lv_aux_array), C.c_int, _PV, _P, _P, _P, _SZ, _P, _P]),
+    "lv_subdivide_select": (C.c_int, [_PV, _P, _P, _P, _P, _P, C.POINTER(lv_subdiv_params), _I64, _P, _P, _P, _SZ,
+                                      _P, _P]),
+    "lv_subdivide_apply": (C.c_int, [_PV, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array), C.c_int, _PV, _P,
+                                     _SZ, _P]),
     "lv_lf_gamma": (_F, [_F, C.POINTER(lv_lf_params)]),
     "lv_lf_workspace_size": (_SZ, [_P, _P, C.c_int]),
     "lv_lf_weighted_loss": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P, _SZ, _P]),
@@ -261,6 +265,21 @@ def lv_subdivide_priority(vin, delta, z, u, seen, prune_mask, params, aux, vout,
                                         C.byref(params), aux_arr, len(aux), C.byref(vout), _ptr(selected),
                                         _ptr(n_new), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                         _ptr(d_status), _stream()), "lv_subdivide_priority")
+
+
+def lv_subdivide_select(vin, delta, z, u, seen, prune_mask, params, out_capacity, selected, n_new, workspace,
+                        d_status=None):
+    _check(load().lv_subdivide_select(C.byref(vin), _ptr(delta), _ptr(z), _ptr(u), _ptr(seen), _ptr(prune_mask),
+                                      C.byref(params), int(out_capacity), _ptr(selected), _ptr(n_new),
+                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(d_status),
+                                      _stream()), "lv_subdivide_select")
+
+
+def lv_subdivide_apply(vin, params, aux, vout, workspace):
+    aux_arr = (lv_aux_array * max(1, len(aux)))(*aux)
+    _check(load().lv_subdivide_apply(C.byref(vin), C.byref(params), aux_arr, len(aux), C.byref(vout),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+           "lv_subdivide_apply")
 
 
 def lv_lf_gamma(t, params) -> float:

@@ -169,3 +169,24 @@ class _RasterFn(torch.autograd.Function):
 def rasterize(density, sh, scene: Scene, rctx: RasterContext):
     """Differentiable forward: returns (rgb [P,3], depth [P], T [P])."""
     return _RasterFn.apply(density, sh, scene, rctx)
+
+
+class CapturedStep:
+    """A step function captured once into a CUDA graph and replayed.
+
+    ``fn`` must only launch work on the current stream (the library's calls
+    and torch tensor ops do) and must have run once before capture, so that
+    one-time set-up (kernel attributes) happens outside the capture.
+    """
+
+    def __init__(self, fn, warmup=1):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            fn()
+        torch.cuda.synchronize()
+
+    def __call__(self):
+        self.graph.replay()
