@@ -57,6 +57,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the step time of the slowest replica)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def camera_for(rank: int):
     from paper_2511_02510_gb300 import synth
     return synth.orbit_camera(W_IMG, H_IMG, 60.0, 3.0, 37.0 + 45.0 * rank, 15.0)
@@ -284,11 +295,8 @@ def algorithmic_bytes(stage, n, pairs, slots, npix, n_new=0, split=0, row=0, par
 
 
 # ---------------------------------------------------------------------------- CPU baseline (oracle)
-def oracle_step_time(scene_np, cam, gt_np, crop_px=128):
-    """Oracle time of one step, extrapolated from a bounded sample: the per-pixel work
-    (render + loss + backward) on a crop_px x crop_px crop, the per-voxel work (prune,
-    subdivide) on the full arrays."""
-    from oracle import oracle as O
+def _oracle_pixel_work(O, scene_np, cam, gt_np, crop_px):
+    """Oracle render + LF loss + backward restricted to a centred crop; returns seconds."""
     x0, y0 = (W_IMG - crop_px) // 2, (H_IMG - crop_px) // 2
     crop = [x0, y0, x0 + crop_px, y0 + crop_px]
     t0 = time.perf_counter()
@@ -301,7 +309,24 @@ def oracle_step_time(scene_np, cam, gt_np, crop_px=128):
     g = np.zeros((H_IMG * W_IMG, 3))
     g[m.ravel()] = lf["dL_drgb"]
     O.render_backward(scene_np, [cam], g, crop=crop)
-    t_px = time.perf_counter() - t0
+    return time.perf_counter() - t0, r
+
+
+def oracle_step_time(scene_np, cam, gt_np, crops=(32, 160)):
+    """Oracle time of one step, extrapolated from a bounded sample.
+
+    The per-pixel work (render, LF loss, backward) is timed on two centred
+    crops; a line through the two (fixed per-view cost of binning all voxels +
+    cost per pixel) extrapolates it to the whole view.  The per-voxel work
+    (prune, subdivide) runs on the full arrays.
+    """
+    from oracle import oracle as O
+    a, b = crops
+    ta, _ = _oracle_pixel_work(O, scene_np, cam, gt_np, a)
+    tb, r = _oracle_pixel_work(O, scene_np, cam, gt_np, b)
+    slope = max((tb - ta) / float(b * b - a * a), 1e-9)
+    fixed = max(ta - slope * a * a, 0.0)
+    t_px = fixed + slope * W_IMG * H_IMG
     n = scene_np["geom"].shape[0]
     t1 = time.perf_counter()
     rng = np.random.default_rng(0)
@@ -311,10 +336,10 @@ def oracle_step_time(scene_np, cam, gt_np, crop_px=128):
     pr = O.prune(w, seen, z, np.ones(n, np.float32), np.ones(n, np.uint8))
     O.subdivide(scene_np, (z / 1071.0).astype(np.float32), z, w, seen, prune_mask=pr["mask"])
     t_vox = time.perf_counter() - t1
-    step = t_px * (W_IMG * H_IMG) / float(crop_px * crop_px) + t_vox
-    sample = (f"per-pixel work (render, LF loss, backward) on a {crop_px}x{crop_px} crop "
-              f"({t_px:.2f} s), scaled by pixel count to the 1237x822 view; prune + subdivide on all {n} voxels "
-              f"({t_vox:.2f} s)")
+    step = t_px + t_vox
+    sample = (f"render + LF loss + backward on centred {a}x{a} and {b}x{b} crops ({ta:.2f} s, {tb:.2f} s), "
+              f"extrapolated linearly (fixed {fixed:.2f} s + {slope * 1e6:.2f} us/pixel) to the 1237x822 view; "
+              f"prune + subdivide on all {n} voxels ({t_vox:.2f} s)")
     return step, sample
 
 
@@ -338,7 +363,7 @@ def run_reference(args, rank):
     times = []
     sample = ""
     for i in range(args.warmup + args.steps):
-        st, sample = oracle_step_time(scene_np, cam, gt_np, crop_px=48)
+        st, sample = oracle_step_time(scene_np, cam, gt_np)
         if i >= args.warmup:
             times.append(st)
     ms = 1e3 * float(np.mean(times))
@@ -349,7 +374,7 @@ def run_reference(args, rank):
                       "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None,
                                  "parallelism": "cpu oracle"},
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                                       "sample": sample + " (48x48 crop per step)"},
+                                       "sample": sample + " (measured anew each step)"},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
           flush=True)
 
@@ -462,10 +487,7 @@ def run_ours(args, rank, world, local):
     clocks = clk.stop()
     launches = launches_per_step * K
     ms = e0.elapsed_time(e1) / K
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     value = world * wl.npix / (ms_max / 1e3) / 1e6
 
     # ---- end to end through the API with host buffers
@@ -476,10 +498,7 @@ def run_ours(args, rank, world, local):
     for _ in range(K):
         wl.e2e_step()
     e2e_s = (time.perf_counter() - t0) / K
-    te = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = world * wl.npix / float(te.item()) / 1e6
+    e2e_val = world * wl.npix / max_over_ranks(e2e_s, world, "cuda") / 1e6
 
     cnt = wl.counters()
     if rank == 0:

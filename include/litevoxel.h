@@ -180,6 +180,18 @@ lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_views, const lv
                          const void* workspace, size_t ws_bytes, int64_t pair_capacity, uint64_t* keys,
                          uint32_t* voxel, uint32_t* ranges, void* stream);
 
+/* FP64 re-render of chosen pixels for finite-difference gradient checks (the
+ * only FP64 arithmetic of the library): pixels [n_px] are global pixel ids
+ * (device int64); for each, the tile list of a forward workspace is walked
+ * front to back (Eq. 2-4) in FP64 from the voxel arrays, with the same chord,
+ * near-plane, ordering, colour and stop rules as the forward.  The lists
+ * depend on geometry only, so corner densities and SH may be changed between
+ * the forward and this call.  rgb [n_px][3] and T [n_px] (nullable) are FP64
+ * device outputs. */
+lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
+                               const void* workspace, size_t ws_bytes, int64_t pair_capacity, const int64_t* pixels,
+                               int64_t n_px, double* rgb, double* T, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* depth-quantile pruning (Sec. IV-C, Eq. 11-12, guards i and iii)      */
 /* ------------------------------------------------------------------ */

@@ -891,6 +891,105 @@ __global__ void k_debug_pairs(const uint64_t* __restrict__ k, const uint32_t* __
   }
 }
 
+// ------------------------------------------------------------------ FP64 re-render (gradient checks)
+// One thread per listed pixel: the pixel's tile list (from a forward
+// workspace) is walked front to back in FP64 from the original voxel arrays
+// (geometry, corner densities and SH converted exactly to double): the FP64
+// counterpart of k_fwd, used only to take finite differences of the loss.
+__device__ __forceinline__ void sh_basis64(double x, double y, double z, double* Y) {
+  const double pi = 3.14159265358979323846;
+  Y[0] = 0.5 / sqrt(pi);
+  const double c1 = sqrt(3.0 / (4.0 * pi));
+  Y[1] = c1 * y; Y[2] = c1 * z; Y[3] = c1 * x;
+  const double c2a = sqrt(15.0 / (4.0 * pi)), c2b = sqrt(5.0 / (16.0 * pi)), c2c = sqrt(15.0 / (16.0 * pi));
+  Y[4] = c2a * x * y; Y[5] = c2a * y * z; Y[6] = c2b * (3.0 * z * z - 1.0); Y[7] = c2a * x * z;
+  Y[8] = c2c * (x * x - y * y);
+  const double c3a = sqrt(35.0 / (32.0 * pi)), c3b = sqrt(105.0 / (4.0 * pi)), c3c = sqrt(21.0 / (32.0 * pi));
+  const double c3d = sqrt(7.0 / (16.0 * pi)), c3e = sqrt(105.0 / (16.0 * pi));
+  Y[9] = c3a * y * (3.0 * x * x - y * y); Y[10] = c3b * x * y * z; Y[11] = c3c * y * (5.0 * z * z - 1.0);
+  Y[12] = c3d * z * (5.0 * z * z - 3.0); Y[13] = c3c * x * (5.0 * z * z - 1.0); Y[14] = c3e * z * (x * x - y * y);
+  Y[15] = c3a * x * (x * x - 3.0 * y * y);
+}
+
+template <typename DT, typename ST>
+__global__ void k_render_f64(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
+                             const uint32_t* __restrict__ svals, const uint32_t* __restrict__ slot_vox,
+                             const float4* __restrict__ geom, const DT* __restrict__ dens, const ST* __restrict__ sh,
+                             int sh_nb, const int64_t* __restrict__ pixels, int64_t n_px, double t_stop,
+                             double* __restrict__ rgb_out, double* __restrict__ T_out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n_px) return;
+  const long long gp = pixels[q];
+  int view = 0;
+  while (view + 1 < vs.n && gp >= vs.v[view + 1].pix_off) ++view;
+  const DevView& c = vs.v[view];
+  const long long loc = gp - c.pix_off;
+  const int px = (int)(loc % c.W), py = (int)(loc / c.W);
+  const int ts = vs.ts;
+  const int gtile = c.tile_off + (py / ts) * c.tiles_x + px / ts;
+  double o[3], d[3];
+  for (int k = 0; k < 3; ++k)
+    o[k] = -((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]);
+  const double dcx = ((double)px + 0.5 - (double)c.cx) / (double)c.fx;
+  const double dcy = ((double)py + 0.5 - (double)c.cy) / (double)c.fy;
+  double nn = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    d[k] = (double)c.R[k] * dcx + (double)c.R[3 + k] * dcy + (double)c.R[6 + k];
+    nn += d[k] * d[k];
+  }
+  nn = sqrt(nn);
+  for (int k = 0; k < 3; ++k) d[k] /= nn;
+  const double t_near = (double)c.z_near * nn;  // camera depth z_near along this ray
+  double T = 1.0, cr = 0.0, cg = 0.0, cb = 0.0;
+  const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
+  for (uint32_t e = start; e < end; ++e) {
+    const uint32_t vox = slot_vox[svals[e]];
+    const float4 g = geom[vox];
+    const double h = (double)g.w, cc[3] = {(double)g.x, (double)g.y, (double)g.z};
+    double lo_t = t_near, hi_t = 1e300;
+    bool miss = false;
+    for (int a = 0; a < 3; ++a) {
+      const double lo = cc[a] - h, hi = cc[a] + h;
+      if (d[a] == 0.0) {
+        if (o[a] < lo || o[a] > hi) miss = true;
+        continue;
+      }
+      const double t1 = (lo - o[a]) / d[a], t2 = (hi - o[a]) / d[a];
+      lo_t = fmax(lo_t, fmin(t1, t2));
+      hi_t = fmin(hi_t, fmax(t1, t2));
+    }
+    if (miss || !(hi_t - lo_t > 0.0)) continue;
+    const double l = hi_t - lo_t, tm = 0.5 * (lo_t + hi_t);
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = fmin(fmax((o[a] + tm * d[a] - (cc[a] - h)) / (2.0 * h), 0.0), 1.0);
+    double sr = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      const double w = ((i & 1) ? u[0] : 1.0 - u[0]) * ((i & 2) ? u[1] : 1.0 - u[1]) * ((i & 4) ? u[2] : 1.0 - u[2]);
+      sr += w * (double)to_f32(dens[8 * (size_t)vox + i]);
+    }
+    const double sigma = fmax(sr, 0.0);
+    const double alpha = -expm1(-sigma * l);
+    double dir[3] = {cc[0] - o[0], cc[1] - o[1], cc[2] - o[2]};
+    const double dn = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    for (int k = 0; k < 3; ++k) dir[k] = dn > 0.0 ? dir[k] / dn : (k == 2 ? 1.0 : 0.0);
+    double Y[16];
+    sh_basis64(dir[0], dir[1], dir[2], Y);
+    double col[3] = {0.5, 0.5, 0.5};
+    for (int j = 0; j < sh_nb; ++j)
+      for (int ch = 0; ch < 3; ++ch) col[ch] += (double)to_f32(sh[48 * (size_t)vox + 3 * j + ch]) * Y[j];
+    const double w = T * alpha;
+    cr += w * fmax(col[0], 0.0);
+    cg += w * fmax(col[1], 0.0);
+    cb += w * fmax(col[2], 0.0);
+    T *= exp(-sigma * l);
+    if (T < t_stop) break;
+  }
+  rgb_out[3 * q + 0] = cr;
+  rgb_out[3 * q + 1] = cg;
+  rgb_out[3 * q + 2] = cb;
+  if (T_out) T_out[q] = T;
+}
+
 // ------------------------------------------------------------------ host side
 static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int nv, const lv_raster_opts* o) {
   if (!vox || !cams || !o) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
@@ -1122,4 +1221,34 @@ extern "C" lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_view
   }
   if (ranges) cudaMemcpyAsync(ranges, w.ranges, sizeof(uint32_t) * 2 * tiles, cudaMemcpyDeviceToDevice, s);
   return cuda_check(cudaGetLastError(), "lv_debug_pairs");
+}
+
+extern "C" lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera* cams, int n_views,
+                                          const lv_raster_opts* opts, const void* workspace, size_t ws_bytes,
+                                          int64_t pair_capacity, const int64_t* pixels, int64_t n_px, double* rgb,
+                                          double* T, void* stream) {
+  lv_status st = check_common(vox, cams, n_views, opts);
+  if (st != LV_OK) return st;
+  if (n_px < 0 || (n_px > 0 && (!pixels || !rgb)) || !workspace) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (n_px == 0) return LV_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  ViewSet vs;
+  int64_t tiles, npix;
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &npix);
+  FwdWs w = carve_fwd((void*)workspace, vox->n, n_views, tiles, npix, pair_capacity);
+  if (ws_bytes < w.bytes) { set_error("workspace too small"); return LV_ERR_WORKSPACE; }
+  const uint32_t* sv = (sort_passes(32 + tile_bits(tiles)) & 1) ? w.v1 : w.v0;
+  const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
+  const unsigned grid = (unsigned)((n_px + 127) / 128);
+#define LV_F64(DT, ST)                                                                                            \
+  k_render_f64<DT, ST><<<grid, 128, 0, s>>>(vs, w.ranges, sv, w.slot_vox, (const float4*)vox->geom,              \
+                                            (const DT*)vox->density, (const ST*)vox->sh, nb, pixels, n_px,       \
+                                            (double)opts->t_stop, rgb, T)
+  if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_F64(float, float);
+  else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_F64(__half, float);
+  else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_F64(float, __nv_bfloat16);
+  else LV_F64(__half, __nv_bfloat16);
+#undef LV_F64
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_render_pixels_f64");
 }

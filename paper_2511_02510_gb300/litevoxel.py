@@ -91,6 +91,7 @@ SIGNATURES = {
     "lv_sh_backward": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, C.c_int, _P]),
     "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
     "lv_debug_pairs": (C.c_int, [_I64, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _P, _P, _P]),
+    "lv_render_pixels_f64": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _I64, _P, _P, _P]),
     "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
     "lv_prune_depth_quantile": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.POINTER(lv_prune_params), _P, _P, _P, _SZ, _P,
                                           _P]),
@@ -241,6 +242,12 @@ def lv_debug_pairs(n, cams_arr, n_views, opts, workspace, pair_capacity, keys=No
     _check(load().lv_debug_pairs(n, cams_arr, n_views, C.byref(opts), _ptr(workspace),
                                  workspace.numel() * workspace.element_size(), pair_capacity, _ptr(keys), _ptr(voxel),
                                  _ptr(ranges), _stream()), "lv_debug_pairs")
+
+
+def lv_render_pixels_f64(vox, cams_arr, n_views, opts, workspace, pair_capacity, pixels, rgb, T=None):
+    _check(load().lv_render_pixels_f64(C.byref(vox), cams_arr, n_views, C.byref(opts), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), pair_capacity, _ptr(pixels),
+                                       int(pixels.numel()), _ptr(rgb), _ptr(T), _stream()), "lv_render_pixels_f64")
 
 
 def lv_prune_workspace_size(n, params) -> int:

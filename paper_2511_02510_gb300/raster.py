@@ -6,7 +6,9 @@ caller-owned device buffers (through torch) and forwards pointers.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 
 import torch
 
@@ -190,3 +192,47 @@ class CapturedStep:
 
     def __call__(self):
         self.graph.replay()
+
+
+def autotune_tile(scene: Scene, cams, tiles=(8, 16, 32), steps=5, cache_path=None, t_stop=1e-4):
+    """Pick the tile size with the fastest forward + backward for this scene and camera set.
+
+    Each candidate is timed with CUDA events over ``steps`` forward + backward
+    passes after one warm-up.  With ``cache_path`` the choice is stored in a
+    JSON file keyed by the GPU name, voxel count and view sizes, and reused.
+    Returns (best_tile, {tile: ms per forward + backward}).
+    """
+    key = "|".join([torch.cuda.get_device_name(), str(scene.n)] +
+                   [f"{int(c['width'])}x{int(c['height'])}" for c in cams])
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return int(cache[key]["tile"]), {int(k): v for k, v in cache[key]["ms"].items()}
+    vox = scene.voxels()
+    times = {}
+    for ts in tiles:
+        ctx = RasterContext(cams, scene.n, tile=ts, t_stop=t_stop)
+        ctx.fit_capacity(vox)
+        g = torch.full((ctx.n_pix, 3), 1e-3, device=ctx.device)
+        dd = torch.empty((scene.n, 8), device=ctx.device)
+        ds = torch.empty((scene.n, 48), device=ctx.device)
+        ctx.forward(vox)
+        ctx.backward(vox, g, d_density=dd, d_sh=ds)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            ctx.forward(vox)
+            ctx.backward(vox, g, d_density=dd, d_sh=ds)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.check()
+        times[ts] = e0.elapsed_time(e1) / steps
+        del ctx
+    best = min(times, key=times.get)
+    if cache_path:
+        cache[key] = {"tile": best, "ms": times}
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best, times

@@ -1,0 +1,157 @@
+"""Parity at the sizes of the batched, mixed-precision and stress configurations.
+
+The oracle cannot render these workloads whole in test time, so each test
+renders full size on the GPU and compares sampled crops (images), crop-limited
+gradients (the loss weights are zero outside the crops, so both sides sum the
+same contributions) and the FP32-pinned statistics bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dequantized, gpu_forward, np_
+from paper_2511_02510_gb300 import litevoxel as L
+from paper_2511_02510_gb300 import synth
+
+from test_gpu_render import compare_images
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def view_offsets(cams):
+    return np.cumsum([0] + [int(c["width"]) * int(c["height"]) for c in cams])
+
+
+def crop_masks(cams, picks, size=20):
+    """Centred size x size crops in the views listed in `picks`; returns (crop array, pixel mask)."""
+    offs = view_offsets(cams)
+    crops = np.zeros((len(cams), 4), np.int32)
+    mask = np.zeros(offs[-1], bool)
+    for v in picks:
+        W, H = int(cams[v]["width"]), int(cams[v]["height"])
+        x0, y0 = W // 2 - size // 2 + 7 * v % 13, H // 2 - size // 2 + 3 * v % 11
+        crops[v] = [x0, y0, x0 + size, y0 + size]
+        m = np.zeros((H, W), bool)
+        m[y0:y0 + size, x0:x0 + size] = True
+        mask[offs[v]:offs[v + 1]] = m.ravel()
+    return crops, mask
+
+
+def crop_gradient_parity(ora, sc_ref, cams, crops, mask, ctx, vox, seed=0):
+    rng = np.random.default_rng(seed)
+    P = ctx.n_pix
+    r = ora.render(sc_ref, cams, crop=crops)
+    gC = np.zeros((P, 3), np.float32)
+    gC[mask] = rng.normal(size=(mask.sum(), 3))
+    gC[r["near_stop"] == 1] = 0
+    d_dens, d_sh = ctx.backward(vox, torch.from_numpy(gC).cuda())
+    torch.cuda.synchronize()
+    ref = ora.render_backward(sc_ref, cams, gC.astype(np.float64), crop=crops)
+    for g, rr in ((np_(d_dens), ref["d_density"]), (np_(d_sh), ref["d_sh"])):
+        scale = np.abs(rr).max()
+        assert scale > 0
+        assert np.abs(g - rr).max() <= 1e-4 * scale
+    return r
+
+
+def test_batched_16_uneven_views(ora):
+    # 2M-voxel 360 scene, 16 views 640x480 .. 1600x1060 in one launch.
+    sc = synth.scene_360()
+    cams = synth.uneven_views(16, seed=2)
+    scene, ctx, vox = gpu_forward(sc, cams)
+    crops, mask = crop_masks(cams, [0, 5, 10, 15])
+    r = crop_gradient_parity(ora, sc, cams, crops, mask, ctx, vox)
+    compare_images(r, ctx, mask=mask)
+    ref = ora.pairs(sc, cams)
+    np.testing.assert_array_equal(np_(ctx.seen), ref["seen"])
+    np.testing.assert_array_equal(np_(ctx.z_min).view(np.uint32), ref["z_min"].view(np.uint32))
+    np.testing.assert_array_equal(np_(ctx.delta_min).view(np.uint32), ref["delta_min"].view(np.uint32))
+
+
+def psnr(a, b):
+    return 10 * math.log10(1.0 / max(float(np.mean((a - b) ** 2)), 1e-30))
+
+
+def test_mixed_precision_tt_8_views(ora):
+    # ~6M-voxel T&T-shaped scene, 8 views of 980x545, FP16 corners and BF16 SH.
+    sc = synth.scene_tt()
+    assert 5.0e6 < sc["geom"].shape[0] < 7.0e6
+    cams = [synth.orbit_camera(980, 545, 60.0, 4.0, 45.0 * i + 10.0, 12.0) for i in range(8)]
+    scene, ctx, vox = gpu_forward(sc, cams, density_dtype=torch.float16, sh_dtype=torch.bfloat16)
+    crops, mask = crop_masks(cams, [1, 4, 6])
+    ref_mixed = dequantized(sc, torch.float16, torch.bfloat16)
+    r = crop_gradient_parity(ora, ref_mixed, cams, crops, mask, ctx, vox)
+    compare_images(r, ctx, mask=mask)
+    # precision loss against the FP64 image of the FP32 scene: the fit to a target
+    # (that image plus N(0, 0.02) noise) changes by less than 0.05 dB
+    r32 = ora.render(sc, cams, crop=crops)
+    rng = np.random.default_rng(5)
+    clean = r32["rgb"][mask]
+    target = clean + rng.normal(0, 0.02, clean.shape)
+    mixed = np_(ctx.rgb)[mask].astype(np.float64)
+    loss_db = psnr(clean, target) - psnr(mixed, target)
+    assert abs(loss_db) < 0.05, loss_db
+    assert psnr(mixed, clean) > 40.0
+
+
+def test_stress_growth_budget_steps(ora):
+    # ~10M voxels, 8 views of 1600x1060, mixed precision: forward, LF loss (gamma ramp 0 -> 1 over 50
+    # steps), backward, prune and subdivide under a 12M budget for a few steps; checks parity of
+    # the adaptation decisions on the GPU's own statistics and the budget invariant.
+    sc = synth.scene_stress()
+    n0 = sc["geom"].shape[0]
+    assert 9.0e6 < n0 < 11.5e6
+    cams = [synth.orbit_camera(1600, 1060, 60.0, 4.0, 45.0 * i, 15.0) for i in range(8)]
+    budget = 12_000_000
+    scene, ctx, vox = gpu_forward(sc, cams, density_dtype=torch.float16, sh_dtype=torch.bfloat16)
+    P = ctx.n_pix
+    gt = torch.from_numpy(np.concatenate([synth.smooth_image(1600, 1060, seed=i) for i in range(8)])).cuda()
+    lp = L.lv_lf_params()
+    lp.eps, lp.gamma_max, lp.t0, lp.t1, lp.pctl_ppm = 1e-3, 1.0, 15.0, 30.0, 990000
+    lf_ws = torch.empty(L.lv_lf_workspace_size([1600] * 8, [1060] * 8), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(8, device="cuda")
+    dL = torch.empty((P, 3), device="cuda")
+    L.lv_lf_weighted_loss(ctx.rgb, gt, [1600] * 8, [1060] * 8, 20.0, lp, loss, dL, lf_ws)
+    d_dens, d_sh = ctx.backward(vox, dL)
+    w, _ = ctx.unpack_wmax()
+    torch.cuda.synchronize()
+    peak_gb = torch.cuda.max_memory_allocated() / 1e9
+    assert np.all(np.isfinite(np_(loss))) and np.all(np.isfinite(np_(d_dens)))
+    # adaptation on the GPU's statistics, decided identically by the oracle from the same FP32 inputs
+    n = scene.n
+    w_np, z_np, dl_np, seen_np = np_(w), np_(ctx.z_min), np_(ctx.delta_min), np_(ctx.seen)
+    pp = L.lv_prune_params()
+    pp.n_bins, pp.q_ppm, pp.ema_alpha, pp.m_low, pp.m_high, pp.cap_ppm = 16, 50000, 0.1, 0.3, 0.7, 10000
+    pp.lo_ppm, pp.hi_ppm = 50000, 950000
+    ema = torch.full((n,), 0.32, device="cuda")
+    st = torch.ones(n, dtype=torch.uint8, device="cuda")
+    mask = torch.empty(n, dtype=torch.uint8, device="cuda")
+    npr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pws = torch.empty(L.lv_prune_workspace_size(n, pp), dtype=torch.uint8, device="cuda")
+    L.lv_prune_depth_quantile(w, ctx.seen, ctx.z_min, ema, st, pp, mask, npr, pws)
+    torch.cuda.synchronize()
+    rp = ora.prune(w_np, seen_np, z_np, np.full(n, 0.32, np.float32), np.ones(n, np.uint8), cap_ppm=10000)
+    np.testing.assert_array_equal(np_(mask), rp["mask"])
+    sp = L.lv_subdiv_params()
+    sp.kappa, sp.beta, sp.top_ppm, sp.l_max, sp.budget, sp.lo_ppm, sp.hi_ppm = 1.0, 0.2, 50000, 16, budget, 50000, 950000
+    cap = budget + 8
+    o = [torch.empty((cap, 4), device="cuda"), torch.empty(cap, dtype=torch.uint8, device="cuda"),
+         torch.empty((cap, 8), dtype=torch.float16, device="cuda"),
+         torch.empty((cap, 48), dtype=torch.bfloat16, device="cuda")]
+    vout = L.make_voxels(o[0], o[2], o[3], o[1])
+    vout.n = cap
+    sel = torch.empty(n, dtype=torch.uint8, device="cuda")
+    nn = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sws = torch.empty(L.lv_subdivide_workspace_size(n, sp), dtype=torch.uint8, device="cuda")
+    L.lv_subdivide_priority(vox, ctx.delta_min, ctx.z_min, w, ctx.seen, mask, sp, [], vout, sel, nn, sws)
+    torch.cuda.synchronize()
+    n_new = int(nn.item())
+    ref_sc = dequantized(sc, torch.float16, torch.bfloat16)
+    rs = ora.subdivide(ref_sc, dl_np, z_np, w_np, seen_np, prune_mask=rp["mask"], budget=budget)
+    assert n_new == rs["n_new"] and n_new <= budget
+    np.testing.assert_array_equal(np_(sel), rs["selected"])
+    np.testing.assert_array_equal(np_(o[0][:n_new]).view(np.uint32), rs["geom"].view(np.uint32))
+    np.testing.assert_array_equal(np_(o[2][:n_new].float()), rs["density"].astype(np.float16).astype(np.float32))
+    print(f"stress: n0={n0} pruned={int(npr.item())} n_new={n_new} peak={peak_gb:.1f} GB")
