@@ -44,7 +44,9 @@ struct PruneState {
   uint32_t ns;            // seen voxels
   uint32_t n_cand;        // out-state candidates after the update
   uint32_t c_lt;          // candidates strictly below the cap threshold
+  uint32_t c_eq;          // candidates at the cap threshold
   uint32_t all;           // 1 when every candidate is pruned (n_cand <= cap)
+  uint32_t all_ties;      // 1 when every candidate at the threshold is pruned
   uint32_t bin_cnt[SELECT_MAX_QUERIES];
 };
 
@@ -155,21 +157,27 @@ __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
 __global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr, uint16_t* cand_grp,
                           PruneState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool lt = false;
+  bool lt = false, eq = false;
   if (i < n && cand_grp[i] == 0 && thr[0].k != 0) {
     const uint32_t v = thr[0].result;
     lt = wkey[i] < v;
-    cand_grp[i] = wkey[i] == v ? 0 : GROUP_NONE;
+    eq = wkey[i] == v;
+    cand_grp[i] = eq ? 0 : GROUP_NONE;
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const int bl = __syncthreads_count(lt);
+  const int be = __syncthreads_count(eq);
   if (threadIdx.x == 0 && bl) atomicAdd(&st->c_lt, (unsigned)bl);
+  if (threadIdx.x == 0 && be) atomicAdd(&st->c_eq, (unsigned)be);
 }
 
-__global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, const PruneState* st, uint32_t cap) {
+// need = cap - c_lt ties are pruned; when that is all of them no id selection is needed
+__global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, PruneState* st, uint32_t cap) {
   if (threadIdx.x == 0) {
+    const uint32_t need = (thr[0].k != 0 && cap > st->c_lt) ? cap - st->c_lt : 0u;
+    st->all_ties = (need != 0 && need == st->c_eq) ? 1u : 0u;
     q[0].group = 0;
-    q[0].k = (thr[0].k != 0 && cap > st->c_lt) ? cap - st->c_lt : 0u;
+    q[0].k = st->all_ties ? 0u : need;
   }
 }
 
@@ -183,7 +191,7 @@ __global__ void k_pr_mask(int64_t n, const uint16_t* __restrict__ grp, const uin
       if (st->all) p = true;
       else if (thr[0].k != 0) {
         const uint32_t v = thr[0].result;
-        p = wkey[i] < v || (wkey[i] == v && tie[0].k != 0 && (uint32_t)i <= tie[0].result);
+        p = wkey[i] < v || (wkey[i] == v && (st->all_ties || (tie[0].k != 0 && (uint32_t)i <= tie[0].result)));
       }
     }
     mask[i] = p ? 1 : 0;
@@ -196,8 +204,10 @@ struct SubState {
   uint32_t n_alive;
   uint32_t n_el;
   uint32_t k;
-  uint32_t c_gt;  // eligible voxels with a strictly higher priority than the k-th
-  uint32_t fits;  // output capacity suffices
+  uint32_t c_gt;      // eligible voxels with a strictly higher priority than the k-th
+  uint32_t c_eq;      // eligible voxels tied with the k-th
+  uint32_t all_ties;  // 1 when every tie is split
+  uint32_t fits;      // output capacity suffices
 };
 
 struct SubWs {
@@ -308,39 +318,45 @@ __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long
 __global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const SelectQuery* thr, uint16_t* grp,
                           SubState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool gt = false;
+  bool gt = false, eq = false;
   if (i < n && grp[i] == 0) {
     if (thr->k != 0) {
       gt = pkey[i] < thr->result;
-      grp[i] = pkey[i] == thr->result ? 0 : GROUP_NONE;
+      eq = pkey[i] == thr->result;
+      grp[i] = eq ? 0 : GROUP_NONE;
     } else {
       grp[i] = GROUP_NONE;
     }
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int b = __syncthreads_count(gt);
-  if (threadIdx.x == 0 && b) atomicAdd(&st->c_gt, (unsigned)b);
+  const int bg = __syncthreads_count(gt);
+  const int be = __syncthreads_count(eq);
+  if (threadIdx.x == 0 && bg) atomicAdd(&st->c_gt, (unsigned)bg);
+  if (threadIdx.x == 0 && be) atomicAdd(&st->c_eq, (unsigned)be);
 }
 
-__global__ void k_sd_tie_query(SelectQuery* q, const SubState* st) {
+// need = k - c_gt ties are split; when that is all of them no id selection is needed
+__global__ void k_sd_tie_query(SelectQuery* q, SubState* st) {
   if (threadIdx.x == 0) {
+    const uint32_t need = (q[2].k != 0 && st->k > st->c_gt) ? st->k - st->c_gt : 0u;
+    st->all_ties = (need != 0 && need == st->c_eq) ? 1u : 0u;
     q[3].group = 0;
-    q[3].k = (q[2].k != 0 && st->k > st->c_gt) ? st->k - st->c_gt : 0u;
+    q[3].k = st->all_ties ? 0u : need;
   }
 }
 
 __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
                             const uint8_t* __restrict__ level, const float4* __restrict__ geom,
                             const float* __restrict__ delta, const uint32_t* __restrict__ pkey,
-                            const SelectQuery* q, float kappa, int l_max, uint8_t* selected, uint32_t* surv,
-                            uint32_t* sel) {
+                            const SelectQuery* q, const SubState* st, float kappa, int l_max, uint8_t* selected,
+                            uint32_t* surv, uint32_t* sel) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   if (i >= n) return;
   const bool alive = pm ? pm[i] == 0 : true;
   bool s = false;
   if (alive && seen[i] && q[2].k != 0 && (int)level[i] < l_max && geom[i].w > __fmul_rn(kappa, delta[i])) {
     const uint32_t v = q[2].result;
-    s = pkey[i] < v || (pkey[i] == v && q[3].k != 0 && (uint32_t)i <= q[3].result);
+    s = pkey[i] < v || (pkey[i] == v && (st->all_ties || (q[3].k != 0 && (uint32_t)i <= q[3].result)));
   }
   selected[i] = s ? 1 : 0;
   sel[i] = s ? 1u : 0u;
@@ -653,7 +669,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_tie_query<<<1, 32, 0, s>>>(w.q, w.st);
   select_kth(nullptr, w.grp, n, w.q + 3, 1, w.sel_tmp, s);
   k_sd_select<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, in->level, (const float4*)in->geom, delta, w.pkey, w.q,
-                                      p->kappa, p->l_max, selected, w.surv, w.sel);
+                                      w.st, p->kappa, p->l_max, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
   k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);

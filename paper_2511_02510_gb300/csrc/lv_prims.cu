@@ -328,6 +328,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
   extern __shared__ uint32_t sh[];  // nq * 256
   __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
   __shared__ uint8_t qfirst[SELECT_MAX_QUERIES], qcount[SELECT_MAX_QUERIES];
+  // nothing to do when every query is finished (k == 0): skip the whole pass
+  int active = 0;
+  for (int j = 0; j < nq; ++j) active |= q[j].k != 0;
+  if (!active) return;  // uniform over the grid
   for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS) sh[i] = 0;
   for (int i = threadIdx.x; i < SELECT_MAX_QUERIES; i += SEL_THREADS) qcount[i] = 0;
   for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
