@@ -366,6 +366,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
           const int j = qfirst[g] + a;
           if (sq[j].k != 0 && (key & hi_mask) == sq[j].prefix) h = j * 256 + (int)d;
         }
+        // after the first digit most items miss their query's prefix: whole warps skip the match
+        if (!__any_sync(FULL, h >= 0)) continue;
         const uint32_t peers = __match_any_sync(FULL, h);
         if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
       }

@@ -349,7 +349,10 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   r[2] = make_float4(d[4], d[5], d[6], d[7]);
   r[3] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), __fdiv_rn(0.5f, g.w));
   slot_vox[s] = (uint32_t)vox;
-  d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // colour-gradient scratch: xyz cleared, w = which channels passed the clamp
+  // (bit c set when raw_c > 0) as a small exact float, read by the SH backward
+  d_rgb[s] = make_float4(0.f, 0.f, 0.f,
+                         (float)((raw[0] > 0.f ? 1 : 0) | (raw[1] > 0.f ? 2 : 0) | (raw[2] > 0.f ? 4 : 0)));
   rec_bb[s] = pbox[i];
   unsigned long long off = pair_off[i];
   uint32_t count = cnt[i];
@@ -777,14 +780,15 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
 }
 
 // ------------------------------------------------------------------ SH backward
-// A warp handles 32 consecutive voxels: their SH rows are staged through shared
-// memory with coalesced 16-byte loads (row stride 49 floats: conflict-free per
-// lane), each lane sums its voxel's colour gradients over the views through
-// c = max(0, SH + 0.5), and the 32 gradient rows leave through shared memory as
-// coalesced 16-byte stores.
-template <typename ST>
-__global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, const ST* __restrict__ sh, int sh_nb,
-                                                int64_t n, const __grid_constant__ ViewSet vs,
+// A warp handles 32 consecutive voxels, one per lane.  d c / d SH_j = Y_j(dir)
+// where the clamp c = max(0, SH + 0.5) passed; the forward left that per-channel
+// mask in the w component of the slot's colour-gradient scratch, so the SH rows
+// themselves are not read again.  Each lane sums its voxel's gradients over the
+// views; the 32 rows leave through shared memory as coalesced 16-byte stores
+// (row stride 49 floats: conflict-free per lane).  With `accumulate`, warps
+// without any visible voxel touch nothing.
+__global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, int sh_nb, int64_t n,
+                                                const __grid_constant__ ViewSet vs,
                                                 const uint32_t* __restrict__ vis, const uint32_t* __restrict__ slot,
                                                 float4* __restrict__ d_rgb, float* __restrict__ d_sh,
                                                 int accumulate) {
@@ -795,50 +799,29 @@ __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom,
   if (v0 >= n) return;  // warp-uniform
   const int nrows = (int)min((int64_t)32, n - v0);
   float* buf = s_rows[warp];
-  if constexpr (sizeof(ST) == 4) {
-    const float4* src = (const float4*)(sh + 48 * v0);
-    for (int w = lane; w < nrows * 12; w += 32) {
-      const float4 q = __ldg(src + w);
-      float* d = buf + (w / 12) * RS + (w % 12) * 4;
-      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
-    }
-  } else {
-    const uint4* src = (const uint4*)(sh + 48 * v0);
-    for (int w = lane; w < nrows * 6; w += 32) {
-      const uint4 q = __ldg(src + w);
-      float* d = buf + (w / 6) * RS + (w % 6) * 8;
-      const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        d[2 * h] = __uint_as_float(u[h] << 16);
-        d[2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
-      }
-    }
-  }
-  __syncwarp();
   float acc[48];
 #pragma unroll
   for (int k = 0; k < 48; ++k) acc[k] = 0.f;
+  bool any_vis = false;
   if (lane < nrows) {
     const int64_t vox = v0 + lane;
-    const float4 g = geom[vox];
-    const float* row = buf + lane * RS;
     for (int view = 0; view < vs.n; ++view) {
       const int64_t i = vox * vs.n + view;
       if (!vis[i]) continue;
+      any_vis = true;
       const DevView& c = vs.v[view];
       const uint32_t s = slot[i];
+      const float4 g = geom[vox];
       float dir[3];
       unit_dir(g.x - c.o[0], g.y - c.o[1], g.z - c.o[2], dir);
       float Y[16];
       sh_basis(dir[0], dir[1], dir[2], Y);
-      float raw[3];
-      sh_raw(row, 1, sh_nb, Y, raw);
       const float4 dc = d_rgb[s];
-      const float dr = raw[0] > 0.f ? dc.x : 0.f;
-      const float dg = raw[1] > 0.f ? dc.y : 0.f;
-      const float db = raw[2] > 0.f ? dc.z : 0.f;
-      d_rgb[s] = make_float4(0.f, 0.f, 0.f, 0.f);  // leave the scratch cleared for the next backward call
+      const int m = (int)dc.w;
+      const float dr = (m & 1) ? dc.x : 0.f;
+      const float dg = (m & 2) ? dc.y : 0.f;
+      const float db = (m & 4) ? dc.z : 0.f;
+      d_rgb[s] = make_float4(0.f, 0.f, 0.f, dc.w);  // cleared for the next backward call; mask kept
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         if (j < sh_nb) {
@@ -849,7 +832,7 @@ __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom,
       }
     }
   }
-  __syncwarp();
+  if (accumulate && !__any_sync(FULL, any_vis)) return;  // nothing to add for these 32 voxels
   if (lane < nrows) {
 #pragma unroll
     for (int k = 0; k < 48; ++k) buf[lane * RS + k] = acc[k];
@@ -1138,12 +1121,7 @@ static lv_status launch_sh_bwd(const lv_voxels* vox, const ViewSet& vs, const Fw
   if (n == 0) return LV_OK;
   const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
   const int blocks = (int)((n + 127) / 128);  // 4 warps x 32 voxels
-  if (vox->sh_dtype == LV_F32)
-    k_sh_bwd<float><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const float*)vox->sh, nb, n, vs, w.vis, w.slot,
-                                           w.d_rgb, d_sh, accumulate);
-  else
-    k_sh_bwd<__nv_bfloat16><<<blocks, 128, 0, s>>>((const float4*)vox->geom, (const __nv_bfloat16*)vox->sh, nb, n,
-                                                   vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
+  k_sh_bwd<<<blocks, 128, 0, s>>>((const float4*)vox->geom, nb, n, vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
   count_launch(1);
   return LV_OK;
 }
