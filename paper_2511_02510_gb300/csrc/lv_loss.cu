@@ -105,15 +105,17 @@ __global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery
   const long long lo = vp.off[v], hi = vp.off[v + 1];
   const float P = __uint_as_float(q[v].result);
   const bool norm = q[v].k != 0 && P > 0.f;
-  double acc = 0.0;
+  // a thread sums its few pixels in FP32; blocks combine in FP64 (the GPU's FP64
+  // rate is low, so no per-pixel FP64 arithmetic)
+  float acc = 0.f;
   for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     float s = 0.f;
     if (norm) s = fminf(fmaxf(__uint_as_float(mkey[p]) / P, 0.f), 1.f);
     const float wv = gamma == 0.f ? 1.f : powf(eps + 1.f - s, gamma);
     w[p] = wv;
-    acc += (double)wv;
+    acc += wv;
   }
-  block_add_f64(acc, &wsum[v]);
+  block_add_f64((double)acc, &wsum[v]);
 }
 
 // Eq. 8 + Eq. 18: w~ = w / <w>, L = 1/|P| sum w~ mean_c r^2, dL/drgb = 2/(3|P|) w~ r
@@ -124,11 +126,11 @@ __global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict
   const long long np = hi - lo;
   const float mean = (float)(wsum[v] / (double)np);
   const float gscale = (float)(2.0 / (3.0 * (double)np));
-  double acc = 0.0;
+  float acc = 0.f;  // sum of w~ (r0^2 + r1^2 + r2^2) over this thread's pixels; the 1/3 is applied at the end
   for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     const float wt = w[p] / mean;
     const float r0 = rgb[3 * p] - gt[3 * p], r1 = rgb[3 * p + 1] - gt[3 * p + 1], r2 = rgb[3 * p + 2] - gt[3 * p + 2];
-    acc += (double)wt * ((double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2) / 3.0;
+    acc += wt * (r0 * r0 + r1 * r1 + r2 * r2);
     if (grad) {
       const float c = gscale * wt;
       grad[3 * p] = c * r0;
@@ -136,14 +138,14 @@ __global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict
       grad[3 * p + 2] = c * r2;
     }
   }
-  block_add_f64(acc, &lsum[v]);
+  block_add_f64((double)acc, &lsum[v]);
 }
 
 __global__ void k_lf_finish(const __grid_constant__ ViewPix vp, const double* lsum, float* loss) {
   int v = threadIdx.x;
   if (v < vp.n) {
     const long long np = vp.off[v + 1] - vp.off[v];
-    loss[v] = np > 0 ? (float)(lsum[v] / (double)np) : 0.f;
+    loss[v] = np > 0 ? (float)(lsum[v] / (3.0 * (double)np)) : 0.f;
   }
 }
 
