@@ -51,7 +51,7 @@ __global__ void k_scan2_reduce(const uint32_t* a, const uint32_t* b, int64_t n, 
   uint32_t tb = 0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += SCAN_THREADS) {
     ta += a[i];
-    tb += b[i];
+    if (b) tb += b[i];
   }
   unsigned long long xa = ta, tot_a;
   uint32_t xb = tb, tot_b;
@@ -74,24 +74,65 @@ __global__ void k_scan2_blocks(unsigned long long* bsa, uint32_t* bsb, int nb, u
   if (threadIdx.x == 0) { totals[0] = ta; totals[1] = tb; }
 }
 
-__global__ void k_scan2_apply(const uint32_t* a, const uint32_t* b, int64_t n, int64_t chunk,
-                              const unsigned long long* bsa, const uint32_t* bsb, unsigned long long* out_a,
-                              uint32_t* out_b) {
+// Each block scans its chunk in tiles of SCAN_THREADS x SCAN_ITEMS items.  A
+// tile is loaded coalesced into shared memory, each thread then scans
+// SCAN_ITEMS consecutive items serially, one block scan of the per-thread
+// totals places them, and the results leave through shared memory as
+// coalesced stores.
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan2_apply(const uint32_t* a, const uint32_t* b, int64_t n,
+                                                             int64_t chunk, const unsigned long long* bsa,
+                                                             const uint32_t* bsb, unsigned long long* out_a,
+                                                             uint32_t* out_b) {
   __shared__ unsigned long long sa[32];
   __shared__ uint32_t sb[32];
+  // one pad word per 8 items: a thread's 8 consecutive items then sit in
+  // distinct banks across the warp
+  __shared__ unsigned long long ta_s[SCAN_TILE + SCAN_TILE / 8];  // a in, then out_a
+  __shared__ uint32_t tb_s[SCAN_TILE + SCAN_TILE / 8];            // b in, then out_b
   int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   unsigned long long carry_a = bsa[blockIdx.x];
   uint32_t carry_b = bsb[blockIdx.x];
-  for (int64_t base = lo; base < hi; base += SCAN_THREADS) {
-    int64_t i = base + threadIdx.x;
-    unsigned long long va = i < hi ? a[i] : 0;
-    uint32_t vb = i < hi ? b[i] : 0;
-    unsigned long long xa = va, ta;
-    uint32_t xb = vb, tb;
-    block_exclusive_scan2(xa, xb, sa, sb, ta, tb);
-    if (i < hi) { out_a[i] = carry_a + xa; out_b[i] = carry_b + xb; }
-    carry_a += ta;
-    carry_b += tb;
+  for (int64_t base = lo; base < hi; base += SCAN_TILE) {
+    const int m = (int)min((int64_t)SCAN_TILE, hi - base);
+    for (int q = threadIdx.x; q < SCAN_TILE; q += SCAN_THREADS) {
+      ta_s[q + (q >> 3)] = q < m ? a[base + q] : 0ull;
+      tb_s[q + (q >> 3)] = (b && q < m) ? b[base + q] : 0u;
+    }
+    __syncthreads();
+    const int q0 = threadIdx.x * (SCAN_ITEMS + 1);  // padded index of item threadIdx.x * 8
+    unsigned long long va[SCAN_ITEMS];
+    uint32_t vb[SCAN_ITEMS];
+    unsigned long long ta = 0;
+    uint32_t tb = 0;
+#pragma unroll
+    for (int u = 0; u < SCAN_ITEMS; ++u) {
+      va[u] = ta_s[q0 + u];
+      vb[u] = tb_s[q0 + u];
+      ta += va[u];
+      tb += vb[u];
+    }
+    unsigned long long xa = ta, tot_a;
+    uint32_t xb = tb, tot_b;
+    block_exclusive_scan2(xa, xb, sa, sb, tot_a, tot_b);  // ends with a barrier
+    unsigned long long ra = carry_a + xa;
+    uint32_t rb = carry_b + xb;
+#pragma unroll
+    for (int u = 0; u < SCAN_ITEMS; ++u) {
+      ta_s[q0 + u] = ra;
+      tb_s[q0 + u] = rb;
+      ra += va[u];
+      rb += vb[u];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += SCAN_THREADS) {
+      if (out_a) out_a[base + q] = ta_s[q + (q >> 3)];
+      if (out_b) out_b[base + q] = tb_s[q + (q >> 3)];
+    }
+    __syncthreads();
+    carry_a += tot_a;
+    carry_b += tot_b;
   }
 }
 
@@ -128,7 +169,7 @@ __device__ __forceinline__ int64_t rs_count(const unsigned long long* d_count, i
   return c <= (unsigned long long)cap ? (int64_t)c : 0;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t* keys, const unsigned long long* d_count,
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* keys, const unsigned long long* d_count,
                                                           int64_t cap, int shift, uint32_t* hist) {
   __shared__ uint32_t sh[RS_WARPS][RADIX];
   const int warp = threadIdx.x >> 5;
@@ -138,7 +179,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t* keys,
   int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   for (int64_t i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
-    uint32_t d = (uint32_t)(keys[i] >> shift) & (RADIX - 1);
+    uint32_t d = (keys[i] >> shift) & (RADIX - 1);
     atomicAdd(&sh[warp][d], 1u);
   }
   __syncthreads();
@@ -181,8 +222,8 @@ __global__ void __launch_bounds__(SORT_BLOCKS) k_rs_scan_digits(uint32_t* hist, 
   if (t == SORT_BLOCKS - 1) digit_tot[blockIdx.x] = sw[NW - 1];
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin, const uint32_t* vin,
-                                                            uint64_t* kout, uint32_t* vout,
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* kin, const uint32_t* vin,
+                                                            uint32_t* kout, uint32_t* vout,
                                                             const unsigned long long* d_count, int64_t cap,
                                                             int shift, const uint32_t* hist,
                                                             const uint32_t* digit_tot) {
@@ -190,7 +231,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
   __shared__ uint32_t s_wh[RS_WARPS][RADIX];  // per-warp digit counts -> warp prefixes
   __shared__ uint32_t s_cnt[RADIX];           // sub-tile digit counts
   __shared__ uint32_t s_start[RADIX];         // sub-tile digit start offsets
-  __shared__ uint64_t s_k[RS_TILE];
+  __shared__ uint32_t s_k[RS_TILE];
   __shared__ uint32_t s_v[RS_TILE];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -216,16 +257,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
   for (int64_t base = lo; base < hi; base += RS_TILE) {
     for (int i = t; i < RS_WARPS * RADIX; i += RS_THREADS) (&s_wh[0][0])[i] = 0;
     __syncthreads();
-    uint64_t k[RS_ITEMS];
-    uint32_t v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
+    uint32_t k[RS_ITEMS], v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
     const int64_t wbase = base + (int64_t)warp * (32 * RS_ITEMS);
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
       int64_t i = wbase + j * 32 + lane;
       bool ok = i < hi;
-      k[j] = ok ? kin[i] : 0ull;
-      v[j] = ok ? vin[i] : 0u;
-      dg[j] = ok ? ((uint32_t)(k[j] >> shift) & (RADIX - 1)) : RADIX;
+      k[j] = ok ? kin[i] : 0u;
+      v[j] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;  // no values: the item's position
+      dg[j] = ok ? ((k[j] >> shift) & (RADIX - 1)) : RADIX;
     }
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
@@ -277,8 +317,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
     __syncthreads();
     int m = (int)min((int64_t)RS_TILE, hi - base);
     for (int q = t; q < m; q += RS_THREADS) {
-      uint64_t kk = s_k[q];
-      uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
+      uint32_t kk = s_k[q];
+      uint32_t d = (kk >> shift) & (RADIX - 1);
       uint32_t g = s_goff[d] + (uint32_t)q - s_start[d];
       kout[g] = kk;
       vout[g] = s_v[q];
@@ -294,18 +334,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t* kin
 size_t sort_hist_bytes() { return sizeof(uint32_t) * (RADIX * SORT_BLOCKS + RADIX); }
 int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 
-int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, uint32_t* hist,
-                     const unsigned long long* d_count, int64_t cap, int end_bit, cudaStream_t s) {
-  int passes = sort_passes(end_bit);
-  uint64_t* kb[2] = {k0, k1};
+int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     cudaStream_t s) {
+  const int passes = sort_passes(end_bit);
+  uint32_t* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
   uint32_t* digit_tot = hist + RADIX * SORT_BLOCKS;
   for (int p = 0; p < passes; ++p) {
-    int src = p & 1, dst = src ^ 1;
-    k_rs_upsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], d_count, cap, 8 * p, hist);
+    // pass 0 reads the input (kept intact unless it is k0 / v0), pass p writes buffer (p + 1) & 1
+    const uint32_t* ks = p == 0 ? kin : kb[p & 1];
+    const uint32_t* vs = p == 0 ? vin : vb[p & 1];
+    const int dst = (p + 1) & 1;
+    k_rs_upsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, d_count, cap, 8 * p, hist);
     k_rs_scan_digits<<<RADIX, SORT_BLOCKS, 0, s>>>(hist, digit_tot);
-    k_rs_downsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_count, cap, 8 * p,
-                                                      hist, digit_tot);
+    k_rs_downsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, 8 * p, hist,
+                                                      digit_tot);
   }
   count_launch(3 * passes);
   return passes & 1;
@@ -317,81 +361,24 @@ namespace {
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_BLOCKS = 304;
 constexpr int SEL_MAX_Q_PER_GROUP = 2;
-constexpr int SEL_ITEMS = 4;  // items per thread per iteration, loads issued together
-
-// Histogram of the current 8-bit digit of every item whose higher digits match
-// its query's prefix.  Queries of a group are contiguous (at most two per
-// group); lanes of a warp that add to the same (query, digit) bin combine
-// first (__match_any_sync), so clustered keys do not serialise on one bin.
-__global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, const uint16_t* grp, int64_t n,
-                                                         const SelectQuery* q, int nq, int shift, uint32_t* hist) {
-  extern __shared__ uint32_t sh[];  // nq * 256
-  __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
-  __shared__ uint8_t qfirst[SELECT_MAX_QUERIES], qcount[SELECT_MAX_QUERIES];
-  // nothing to do when every query is finished (k == 0): skip the whole pass
-  int active = 0;
-  for (int j = 0; j < nq; ++j) active |= q[j].k != 0;
-  if (!active) return;  // uniform over the grid
-  for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS) sh[i] = 0;
-  for (int i = threadIdx.x; i < SELECT_MAX_QUERIES; i += SEL_THREADS) qcount[i] = 0;
-  for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = nq - 1; j >= 0; --j) {
-      const uint32_t g = sq[j].group;
-      if (g < SELECT_MAX_QUERIES) { qfirst[g] = (uint8_t)j; qcount[g]++; }
-    }
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const uint32_t hi_mask = shift >= 24 ? 0u : (0xffffffffu << (shift + 8));
-  const int64_t stride = (int64_t)gridDim.x * SEL_THREADS * SEL_ITEMS;
-  for (int64_t base = blockIdx.x * (int64_t)SEL_THREADS * SEL_ITEMS; base < n; base += stride) {  // warp-uniform
-    uint32_t gv[SEL_ITEMS], kv[SEL_ITEMS];
-#pragma unroll
-    for (int u = 0; u < SEL_ITEMS; ++u) {  // issue all loads first
-      const int64_t i = base + u * SEL_THREADS + threadIdx.x;
-      gv[u] = i < n ? grp[i] : GROUP_NONE;
-      kv[u] = i < n ? (keys ? keys[i] : (uint32_t)i) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < SEL_ITEMS; ++u) {
-      const uint32_t g = gv[u], key = kv[u];
-      const int cnt = g < SELECT_MAX_QUERIES ? qcount[g] : 0;
-      const uint32_t d = (key >> shift) & 255u;
-#pragma unroll
-      for (int a = 0; a < SEL_MAX_Q_PER_GROUP; ++a) {
-        int h = -1;
-        if (a < cnt) {
-          const int j = qfirst[g] + a;
-          if (sq[j].k != 0 && (key & hi_mask) == sq[j].prefix) h = j * 256 + (int)d;
-        }
-        // after the first digit most items miss their query's prefix: whole warps skip the match
-        if (!__any_sync(FULL, h >= 0)) continue;
-        const uint32_t peers = __match_any_sync(FULL, h);
-        if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nq * 256; i += SEL_THREADS)
-    if (sh[i]) atomicAdd(&hist[i], sh[i]);
-}
+constexpr int SEL_ITEMS = 4;        // items per thread per iteration, loads issued together
+constexpr int SEL_WIDE_MAX_Q = 4;   // up to this many queries use 11-bit digits
 
 // One warp per query: find the digit holding the k-th item (warp scan over
-// 8 digits per lane), extend the prefix, clear the query's histogram row.
+// RADIX / 32 digits per lane), extend the prefix, clear the query's histogram row.
+template <int RADIX>
 __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
+  constexpr int PER = RADIX / 32;  // 8 or 64 digits per lane, contiguous
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= nq) return;  // warp-uniform
   SelectQuery s = q[j];
-  uint32_t* hrow = hist + (size_t)j * 256;
-  uint32_t c[8];
+  uint4* hrow = (uint4*)(hist + (size_t)j * RADIX + lane * PER);
   uint32_t lsum = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    c[i] = hrow[lane * 8 + i];
-    lsum += c[i];
+#pragma unroll 4
+  for (int i = 0; i < PER / 4; ++i) {
+    const uint4 c = hrow[i];
+    lsum += c.x + c.y + c.z + c.w;
   }
   uint32_t incl = lsum;
 #pragma unroll
@@ -407,17 +394,18 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
     const int L = __ffs(ball) - 1;
     if (lane == L) {
       uint32_t cum = excl;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (digit < 0 && cum + c[i] >= s.k) { digit = lane * 8 + i; newk = s.k - cum; }
-        cum += c[i];
+      const uint32_t* h = (const uint32_t*)hrow;
+      for (int i = 0; i < PER; ++i) {
+        const uint32_t c = h[i];
+        if (cum + c >= s.k) { digit = lane * PER + i; newk = s.k - cum; break; }
+        cum += c;
       }
     }
     digit = __shfl_sync(FULL, digit, L);
     newk = __shfl_sync(FULL, newk, L);
   }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) hrow[lane * 8 + i] = 0u;
+#pragma unroll 4
+  for (int i = 0; i < PER / 4; ++i) hrow[i] = make_uint4(0u, 0u, 0u, 0u);
   if (lane == 0) {
     if (s.k == 0 || digit < 0) {
       s.k = 0;
@@ -431,38 +419,166 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
   }
 }
 
-__global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist) {
+// Histogram of the current digit (bits [shift, shift + width)) of every item
+// whose bits above the digit match its query's prefix.  Lanes of a warp that
+// add to the same (query, digit) bin combine first (__match_any_sync), so
+// clustered keys do not serialise on one bin.  When
+// every query is in group 0 (at most two queries) a lean per-item path runs;
+// otherwise queries of a group are contiguous, at most two per group.
+template <int RADIX>
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, const uint16_t* grp, int64_t n,
+                                                         const SelectQuery* q, int nq, int shift, int width,
+                                                         uint32_t* hist) {
+  extern __shared__ uint4 sh4[];  // nq * RADIX counters
+  uint32_t* sh = (uint32_t*)sh4;
+  __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
+  __shared__ uint8_t qfirst[SELECT_MAX_QUERIES], qcount[SELECT_MAX_QUERIES];
+  // nothing to do when every query is finished (k == 0): skip the whole pass
+  int active = 0, all0 = nq <= SEL_MAX_Q_PER_GROUP;
+  for (int j = 0; j < nq; ++j) {
+    active |= q[j].k != 0;
+    all0 &= q[j].group == 0;
+  }
+  if (!active) return;  // uniform over the grid
+  for (int i = threadIdx.x; i < nq * RADIX / 4; i += SEL_THREADS) sh4[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = threadIdx.x; i < SELECT_MAX_QUERIES; i += SEL_THREADS) qcount[i] = 0;
+  for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = nq - 1; j >= 0; --j) {
+      const uint32_t g = sq[j].group;
+      if (g < SELECT_MAX_QUERIES) { qfirst[g] = (uint8_t)j; qcount[g]++; }
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int top = shift + width;
+  const uint32_t hi_mask = top >= 32 ? 0u : (0xffffffffu << top);
+  const uint32_t dmask = (1u << width) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * SEL_THREADS * SEL_ITEMS;
+  if (all0) {
+    // lean path: one group, queries 0 (and 1) in registers
+    const uint32_t k0 = sq[0].k, p0 = sq[0].prefix;
+    const uint32_t k1 = nq > 1 ? sq[1].k : 0u, p1 = nq > 1 ? sq[1].prefix : 0u;
+    for (int64_t base = blockIdx.x * (int64_t)SEL_THREADS * SEL_ITEMS; base < n; base += stride) {  // warp-uniform
+      uint32_t gv[SEL_ITEMS], kv[SEL_ITEMS];
+#pragma unroll
+      for (int u = 0; u < SEL_ITEMS; ++u) {  // issue all loads first
+        const int64_t i = base + u * SEL_THREADS + threadIdx.x;
+        gv[u] = i < n ? grp[i] : GROUP_NONE;
+        kv[u] = i < n ? (keys ? keys[i] : (uint32_t)i) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < SEL_ITEMS; ++u) {
+        const bool in = gv[u] == 0;
+        const uint32_t key = kv[u], hk = key & hi_mask, d = (key >> shift) & dmask;
+        int h = (in && k0 != 0 && hk == p0) ? (int)d : -1;
+        if (__any_sync(FULL, h >= 0)) {
+          const uint32_t peers = __match_any_sync(FULL, h);
+          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
+        }
+        h = (in && k1 != 0 && hk == p1) ? RADIX + (int)d : -1;
+        if (__any_sync(FULL, h >= 0)) {
+          const uint32_t peers = __match_any_sync(FULL, h);
+          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
+        }
+      }
+    }
+  } else {
+    for (int64_t base = blockIdx.x * (int64_t)SEL_THREADS * SEL_ITEMS; base < n; base += stride) {  // warp-uniform
+      uint32_t gv[SEL_ITEMS], kv[SEL_ITEMS];
+#pragma unroll
+      for (int u = 0; u < SEL_ITEMS; ++u) {  // issue all loads first
+        const int64_t i = base + u * SEL_THREADS + threadIdx.x;
+        gv[u] = i < n ? grp[i] : GROUP_NONE;
+        kv[u] = i < n ? (keys ? keys[i] : (uint32_t)i) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < SEL_ITEMS; ++u) {
+        const uint32_t g = gv[u], key = kv[u];
+        const int cnt = g < SELECT_MAX_QUERIES ? qcount[g] : 0;
+        const uint32_t d = (key >> shift) & dmask;
+#pragma unroll
+        for (int a = 0; a < SEL_MAX_Q_PER_GROUP; ++a) {
+          int h = -1;
+          if (a < cnt) {
+            const int j = qfirst[g] + a;
+            if (sq[j].k != 0 && (key & hi_mask) == sq[j].prefix) h = j * RADIX + (int)d;
+          }
+          // after the first digit most items miss their query's prefix: whole warps skip the match
+          if (!__any_sync(FULL, h >= 0)) continue;
+          const uint32_t peers = __match_any_sync(FULL, h);
+          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nq * RADIX / 4; i += SEL_THREADS) {
+    const uint4 c = sh4[i];
+    if (c.x) atomicAdd(&hist[4 * i], c.x);
+    if (c.y) atomicAdd(&hist[4 * i + 1], c.y);
+    if (c.z) atomicAdd(&hist[4 * i + 2], c.z);
+    if (c.w) atomicAdd(&hist[4 * i + 3], c.w);
+  }
+}
+
+__global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist, int hist_words) {
   int j = threadIdx.x;
   if (j < nq) { q[j].prefix = 0; q[j].result = 0xffffffffu; }
-  for (int i = threadIdx.x; i < nq * 256; i += blockDim.x) hist[i] = 0;
+  for (int i = threadIdx.x; i < hist_words; i += blockDim.x) hist[i] = 0;
+}
+
+template <int RADIX>
+void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int nq,
+                   uint32_t* hist, int key_bits, int width, cudaStream_t s) {
+  // enough blocks to keep many loads in flight; fewer when every block must
+  // clear and flush a large histogram (wide digits or many queries)
+  const int64_t want = (n + SEL_THREADS * SEL_ITEMS - 1) / (SEL_THREADS * SEL_ITEMS);
+  const int64_t cap_blocks = nq * RADIX <= 512 ? 2048 : 2 * SEL_BLOCKS;
+  int blocks = (int)(want < cap_blocks ? want : cap_blocks);
+  if (blocks < 1) blocks = 1;
+  const size_t smem = sizeof(uint32_t) * RADIX * nq;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sel_hist<RADIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint32_t) * 256 * SELECT_MAX_QUERIES));
+    attr_set = true;
+  }
+  // digits from the top: the first one takes the remainder bits, the rest `width` each
+  const int npass = (key_bits + width - 1) / width;
+  int shift = key_bits;
+  for (int p = 0; p < npass; ++p) {
+    const int wbits = p == 0 ? key_bits - width * (npass - 1) : width;
+    shift -= wbits;
+    k_sel_hist<RADIX><<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, d_queries, nq, shift, wbits, hist);
+    k_sel_pick<RADIX><<<(nq + 7) / 8, 256, 0, s>>>(d_queries, nq, shift, hist);
+  }
+  count_launch(2 * npass);
 }
 
 }  // namespace
 
-size_t select_tmp_bytes(int n_queries) { return sizeof(uint32_t) * 256 * (size_t)n_queries + 256; }
+size_t select_tmp_bytes(int n_queries) {
+  const size_t narrow = 256 * (size_t)n_queries;
+  const size_t wide = 2048 * (size_t)(n_queries < SEL_WIDE_MAX_Q ? n_queries : SEL_WIDE_MAX_Q);
+  return sizeof(uint32_t) * (narrow > wide ? narrow : wide) + 256;
+}
 
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s) {
   uint32_t* hist = (uint32_t*)tmp;
-  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist);
-  // enough blocks to keep many loads in flight; fewer when every block must
-  // clear and flush a large (many-query) histogram
-  const int64_t want = (n + SEL_THREADS * SEL_ITEMS - 1) / (SEL_THREADS * SEL_ITEMS);
-  const int64_t cap_blocks = n_queries <= 2 ? 2048 : 4 * SEL_BLOCKS;
-  int blocks = (int)(want < cap_blocks ? want : cap_blocks);
-  if (blocks < 1) blocks = 1;
-  size_t smem = sizeof(uint32_t) * 256 * n_queries;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sel_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(uint32_t) * 256 * SELECT_MAX_QUERIES));
-    attr_set = true;
+  const bool wide = n_queries <= SEL_WIDE_MAX_Q;
+  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist, (wide ? 2048 : 256) * n_queries);
+  count_launch(1);
+  // ranking by index needs only the bits of n - 1 (at least one)
+  int key_bits = 32;
+  if (!keys) {
+    key_bits = 1;
+    while (key_bits < 32 && ((int64_t)1 << key_bits) < n) ++key_bits;
   }
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    k_sel_hist<<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, d_queries, n_queries, shift, hist);
-    k_sel_pick<<<(n_queries + 7) / 8, 256, 0, s>>>(d_queries, n_queries, shift, hist);
-  }
-  count_launch(1 + 8);
+  if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, key_bits, 11, s);
+  else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, key_bits, 8, s);
 }
 
 }  // namespace lv

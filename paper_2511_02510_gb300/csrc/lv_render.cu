@@ -5,12 +5,17 @@
 //   k_bin       per (voxel, view): FP32 cull / near-plane clipping / corner
 //               projection / tile rect / depth key with a fixed operation
 //               order; depth statistics.
-//   scan2       pair offsets and visible-slot ids (two-channel scan).
+//   scan2       visible-slot ids and the total pair count.
 //   k_emit      per visible (voxel, view): 64-byte render record (centre
 //               relative to the camera, half-size, 8 corner densities, SH
-//               colour, 1 / (2 h)), its pixel box and voxel id, and its
-//               (tile << 32 | depth key, slot) pairs.
-//   radix sort  CUB-free LSD sort of the pairs on (tile bits + 32) bits.
+//               colour, 1 / (2 h)), its pixel box, voxel id, tile rectangle
+//               and depth key.
+//   radix sort  the slots by depth key (32 bits, stable: ties by voxel id).
+//   k_emit_pairs  (tile, slot) pairs written in that depth order after a scan
+//               of the tile counts; a stable radix sort on the tile bits then
+//               leaves every tile's list front to back.  This sorts the
+//               depth keys once per slot rather than once per pair, and
+//               moves 8-byte pairs instead of 12-byte (tile << 32 | key) ones.
 //   k_ranges    [start, end) of every tile in the sorted list.
 //   k_fwd       per tile, one thread per pixel: each warp stages the records
 //               that meet its pixel strip through shared memory and marches
@@ -73,27 +78,28 @@ static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64
 
 // ------------------------------------------------------------------ workspace
 struct FwdWs {
-  unsigned long long* counters;  // [0] pairs, [1] slots
+  unsigned long long* counters;  // [0] pairs, [1] slots, [2..3] totals of the depth-order scan
   uint32_t* cnt;                 // [items] tiles covered
   uint32_t* vis;                 // [items] 1 if cnt > 0
   uint2* rect;                   // [items] (tx0 | tx1 << 16, ty0 | ty1 << 16)
   uint2* pbox;                   // [items] conservative pixel box (x0 | x1 << 16, y0 | y1 << 16), [x0, x1)
+  uint32_t* dkey;                // [items] order key of z_centre
+  uint32_t* slot;                // [items] render slot of a visible item
   uint2* rec_bb;                 // [slots] pixel box of the render record
   uint32_t* slot_vox;            // [slots] voxel id of the render record
-  uint32_t* dkey;                // [items] order key of z_centre
-  unsigned long long* pair_off;  // [items]
-  uint32_t* slot;                // [items]
+  uint4* s_tiles;                // [slots] (rect.x, rect.y, view, tile count)
+  uint32_t* s_dkey;              // [slots] order key
+  uint32_t *sk0, *sv0, *sk1, *sv1;  // [slots] depth sort of the slots (keys, slot ids)
+  uint32_t* scnt;                // [slots] tile counts in depth order
+  unsigned long long* poff;      // [slots] first pair of each slot in depth order
   void* scan_tmp;
   float4* rec;                   // [slots][4]
-  float4* d_rgb;                 // [slots] colour gradient (xyz) scratch of the backward
+  float4* d_rgb;                 // [slots] colour gradient (xyz) scratch of the backward; w = clamp mask
   uint32_t* ranges;              // [tiles][2]
   float* tau;                    // [pixels] final optical depth
   uint32_t* hist;
   int32_t* status;               // fallback status word
-  uint64_t* k0;
-  uint32_t* v0;
-  uint64_t* k1;
-  uint32_t* v1;
+  uint32_t *k0, *v0, *k1, *v1;   // [pair capacity] (tile, slot) pairs, sorted by tile
   size_t bytes;
 };
 
@@ -107,30 +113,45 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   w.vis = c.take<uint32_t>(items);
   w.rect = c.take<uint2>(items);
   w.pbox = c.take<uint2>(items);
+  w.dkey = c.take<uint32_t>(items);
+  w.slot = c.take<uint32_t>(items);
   w.rec_bb = c.take<uint2>(items);
   w.slot_vox = c.take<uint32_t>(items);
-  w.dkey = c.take<uint32_t>(items);
-  w.pair_off = c.take<unsigned long long>(items);
-  w.slot = c.take<uint32_t>(items);
+  w.s_tiles = c.take<uint4>(items);
+  w.s_dkey = c.take<uint32_t>(items);
+  w.sk0 = c.take<uint32_t>(items);
+  w.sv0 = c.take<uint32_t>(items);
+  w.sk1 = c.take<uint32_t>(items);
+  w.sv1 = c.take<uint32_t>(items);
+  w.scnt = c.take<uint32_t>(items);
+  w.poff = c.take<unsigned long long>(items);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.rec = c.take<float4>(items * 4);
   w.d_rgb = c.take<float4>(items);
   w.ranges = c.take<uint32_t>(tiles * 2);
   w.tau = c.take<float>(pixels);
   w.hist = c.take<uint32_t>(sort_hist_bytes() / 4);
-  w.k0 = c.take<uint64_t>(pair_cap);
+  w.k0 = c.take<uint32_t>(pair_cap);
   w.v0 = c.take<uint32_t>(pair_cap);
-  w.k1 = c.take<uint64_t>(pair_cap);
+  w.k1 = c.take<uint32_t>(pair_cap);
   w.v1 = c.take<uint32_t>(pair_cap);
   w.bytes = c.off + 256;
   return w;
 }
 
+// the sorted (tile, slot) pairs: in (k0, v0) after an even number of tile-digit passes
 static int tile_bits(int64_t tiles) {
   int b = 0;
   while (b < 32 && ((int64_t)1 << b) < tiles) ++b;
   return b;
 }
+static const uint32_t* sorted_pair_slots(const FwdWs& w, int64_t tiles) {
+  return (sort_passes(tile_bits(tiles)) & 1) ? w.v1 : w.v0;
+}
+static const uint32_t* sorted_pair_tiles(const FwdWs& w, int64_t tiles) {
+  return (sort_passes(tile_bits(tiles)) & 1) ? w.k1 : w.k0;
+}
+
 
 // ------------------------------------------------------------------ binning (FP32, fixed op order)
 __device__ __forceinline__ void cam_point32(const DevView& c, float X, float Y, float Z, float* q) {
@@ -310,6 +331,10 @@ __device__ __forceinline__ void unit_dir(float rx, float ry, float rz, float* d)
 }
 
 // ------------------------------------------------------------------ emit
+// One thread per visible (voxel, view) item: the render record of its slot
+// (camera-relative centre and h | 8 corner densities | clamped SH colour and
+// 1/(2h)), the slot's tile rectangle and order key for the depth sort, and the
+// colour-gradient scratch (cleared; w = clamp mask).
 template <typename DT, typename ST>
 __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, const DT* __restrict__ dens,
                                               const ST* __restrict__ sh, int sh_nb, int64_t n,
@@ -318,11 +343,9 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const uint2* __restrict__ pbox, uint2* __restrict__ rec_bb,
                                               uint32_t* __restrict__ slot_vox,
                                               const uint32_t* __restrict__ dkey,
-                                              const unsigned long long* __restrict__ pair_off,
                                               const uint32_t* __restrict__ slot, float4* __restrict__ rec,
-                                              float4* __restrict__ d_rgb, uint64_t* __restrict__ keys,
-                                              uint32_t* __restrict__ vals,
-                                              int64_t pair_cap, int32_t* status) {
+                                              float4* __restrict__ d_rgb, uint4* __restrict__ s_tiles,
+                                              uint32_t* __restrict__ s_dkey) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * vs.n) return;
   if (!vis[i]) return;
@@ -354,21 +377,109 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   d_rgb[s] = make_float4(0.f, 0.f, 0.f,
                          (float)((raw[0] > 0.f ? 1 : 0) | (raw[1] > 0.f ? 2 : 0) | (raw[2] > 0.f ? 4 : 0)));
   rec_bb[s] = pbox[i];
-  unsigned long long off = pair_off[i];
-  uint32_t count = cnt[i];
-  if (off + count > (unsigned long long)pair_cap) {
-    report(status, LV_ERR_CAPACITY);
+  const uint2 rc = rect[i];
+  s_tiles[s] = make_uint4(rc.x, rc.y, (uint32_t)view, cnt[i]);
+  s_dkey[s] = dkey[i];
+}
+
+// Tile counts of the slots in depth order (zero past the last slot).
+__global__ void k_slot_counts(const uint32_t* __restrict__ sorted_slot, const uint4* __restrict__ s_tiles,
+                              const unsigned long long* __restrict__ n_slots, int64_t items, uint32_t* scnt) {
+  const int64_t ns = (int64_t)*n_slots;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < items; r += (int64_t)gridDim.x * blockDim.x)
+    scnt[r] = r < ns ? s_tiles[sorted_slot[r]].w : 0u;
+}
+
+// The (tile, slot) pairs of every slot, written in depth order so that the
+// stable sort by tile keeps each tile's list front to back (ties in the order
+// key by slot, i.e. by voxel id).  Pairs are shared out evenly: each warp owns
+// a contiguous range of pair positions, finds the slot holding its first pair
+// by a 32-way search over the slot offsets, then writes 32 consecutive pairs
+// per step (coalesced).  A step's pairs lie in at most 32 consecutive slots
+// from the slot of its first pair, whose offsets, rectangles and ids sit in a
+// per-warp window in shared memory;
+// each lane finds its slot there by a 5-step binary search.  So neither a slot
+// with thousands of tiles nor a run of such slots serialises one lane or one
+// warp.  More pairs than capacity: nothing is written and the status word says
+// LV_ERR_CAPACITY.
+constexpr int EP_WARPS = 8;
+
+// largest s in [0, ns) with poff[s] <= p; poff strictly increases, poff[0] = 0
+__device__ __forceinline__ int64_t warp_find_slot(const unsigned long long* __restrict__ poff, int64_t ns,
+                                                  unsigned long long p, int lane) {
+  int64_t lo = 0, hi = ns;
+  while (hi - lo > 1) {  // warp-uniform
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t probe = lo + lane * step;
+    const bool le = probe < hi && poff[probe] <= p;
+    const int k = __popc(__ballot_sync(FULL, le));  // lanes 0..k-1 (lane 0 always)
+    const int64_t nlo = lo + (int64_t)(k - 1) * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(EP_WARPS * 32) k_emit_pairs(const __grid_constant__ ViewSet vs,
+                                                            const uint32_t* __restrict__ sorted_slot,
+                                                            const uint4* __restrict__ s_tiles,
+                                                            const unsigned long long* __restrict__ poff,
+                                                            const unsigned long long* __restrict__ counters,
+                                                            int64_t pair_cap, uint32_t* __restrict__ keys,
+                                                            uint32_t* __restrict__ vals, int32_t* status) {
+  __shared__ unsigned long long w_start[EP_WARPS][33];  // [32]: start of the slot after the window
+  __shared__ uint4 w_rect[EP_WARPS][32];  // (rect.x, rect.y, tile offset of the view, tiles_x)
+  __shared__ uint32_t w_slot[EP_WARPS][32];
+  const unsigned long long total = counters[0];
+  if (total > (unsigned long long)pair_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) report(status, LV_ERR_CAPACITY);
     return;
   }
-  uint2 rc = rect[i];
-  int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff;
-  int wx = tx1 - tx0;
-  uint32_t dk = dkey[i];
-  for (uint32_t q = 0; q < count; ++q) {
-    int ty = ty0 + (int)(q / (uint32_t)wx), tx = tx0 + (int)(q % (uint32_t)wx);
-    uint64_t gt = (uint64_t)(c.tile_off + ty * c.tiles_x + tx);
-    keys[off + q] = (gt << 32) | dk;
-    vals[off + q] = s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ns = (int64_t)counters[1];
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * EP_WARPS;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * EP_WARPS + warp;
+  const unsigned long long chunk = ((total + nwarps - 1) / nwarps + 31) & ~31ull;
+  const unsigned long long p_begin = gw * chunk;
+  const unsigned long long p_end = min(total, p_begin + chunk);
+  if (p_begin >= p_end) return;  // warp-uniform
+  int64_t s0 = warp_find_slot(poff, ns, p_begin, lane);
+  int64_t loaded = -1;
+  for (unsigned long long p0 = p_begin; p0 < p_end; p0 += 32) {  // warp-uniform
+    if (s0 != loaded) {
+      __syncwarp();
+      const int64_t r = s0 + lane;
+      unsigned long long st = ~0ull;
+      if (r < ns) {
+        const uint32_t sl = sorted_slot[r];
+        const uint4 t = s_tiles[sl];
+        const DevView& c = vs.v[t.z];
+        st = poff[r];
+        w_rect[warp][lane] = make_uint4(t.x, t.y, (uint32_t)c.tile_off, (uint32_t)c.tiles_x);
+        w_slot[warp][lane] = sl;
+      }
+      w_start[warp][lane] = st;
+      if (lane == 0) w_start[warp][32] = s0 + 32 < ns ? poff[s0 + 32] : ~0ull;
+      __syncwarp();
+      loaded = s0;
+    }
+    const unsigned long long e = p0 + lane;
+    int j = 0;  // largest j with w_start[j] <= e; w_start[0] <= p0 <= e
+#pragma unroll
+    for (int step = 16; step; step >>= 1)
+      if (w_start[warp][j + step] <= e) j += step;
+    if (e < p_end) {
+      const uint4 rc = w_rect[warp][j];
+      const uint32_t q = (uint32_t)(e - w_start[warp][j]);
+      const int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff;
+      const uint32_t wx = (uint32_t)(tx1 - tx0);
+      const int ty = ty0 + (int)(q / wx), tx = tx0 + (int)(q % wx);
+      keys[e] = rc.z + (uint32_t)(ty * (int)rc.w + tx);
+      vals[e] = w_slot[warp][j];
+    }
+    // the next window starts at the slot of pair p0 + 32: this step's last slot, or the one after it
+    const int j31 = __shfl_sync(FULL, j, 31);
+    s0 += j31 + (w_start[warp][j31 + 1] <= p0 + 32 ? 1 : 0);
   }
 }
 
@@ -378,14 +489,14 @@ __device__ __forceinline__ int64_t usable_pairs(const unsigned long long* d_coun
   return c <= (unsigned long long)cap ? (int64_t)c : 0;
 }
 
-__global__ void k_ranges(const uint64_t* __restrict__ keys, const unsigned long long* d_count, int64_t cap,
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_count, int64_t cap,
                          int64_t tiles, uint32_t* ranges) {
   const int64_t n = usable_pairs(d_count, cap);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t t = (uint32_t)(keys[i] >> 32);
+    const uint32_t t = keys[i];
     if (t >= tiles) continue;
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = (uint32_t)i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+    if (i == 0 || keys[i - 1] != t) ranges[2 * t] = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
   }
 }
 
@@ -864,12 +975,12 @@ __global__ void k_unpack_wmax(const unsigned long long* __restrict__ packed, int
   }
 }
 
-__global__ void k_debug_pairs(const uint64_t* __restrict__ k, const uint32_t* __restrict__ v,
-                              const uint32_t* __restrict__ slot_vox, const unsigned long long* d_count, int64_t cap,
-                              uint64_t* ko, uint32_t* vo) {
+__global__ void k_debug_pairs(const uint32_t* __restrict__ k, const uint32_t* __restrict__ v,
+                              const uint32_t* __restrict__ slot_vox, const uint32_t* __restrict__ s_dkey,
+                              const unsigned long long* d_count, int64_t cap, uint64_t* ko, uint32_t* vo) {
   const int64_t n = usable_pairs(d_count, cap);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (ko) ko[i] = k[i];
+    if (ko) ko[i] = ((uint64_t)k[i] << 32) | s_dkey[v[i]];
     if (vo) vo[i] = slot_vox[v[i]];
   }
 }
@@ -1077,23 +1188,34 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     int blocks = (int)((items + 255) / 256);
     k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.dkey, out->z_min,
                                  out->delta_min, out->seen);
-    scan2(w.cnt, w.vis, items, w.pair_off, w.slot, w.counters, w.scan_tmp, s);
+    scan2(w.cnt, w.vis, items, nullptr, w.slot, w.counters, w.scan_tmp, s);
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                               \
   k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
-                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey, w.pair_off,  \
-                                        w.slot, w.rec, w.d_rgb, w.k0, w.v0, pair_capacity, d_status)
+                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey, w.slot,      \
+                                        w.rec, w.d_rgb, w.s_tiles, w.s_dkey)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
     else LV_EMIT(__half, __nv_bfloat16);
 #undef LV_EMIT
     count_launch(2);
+    // 1) the slots front to back: stable sort by order key (ties keep slot = voxel-id order)
+    const int ws_ = radix_sort_pairs(w.s_dkey, nullptr, w.sk0, w.sv0, w.sk1, w.sv1, w.hist, w.counters + 1, items,
+                                     32, s);
+    const uint32_t* sorted_slot = ws_ ? w.sv1 : w.sv0;
+    // 2) pair offsets in that order, then the pairs themselves
+    const int gb = (int)std::min<int64_t>((items + 255) / 256, 4 * 1216);
+    k_slot_counts<<<gb, 256, 0, s>>>(sorted_slot, w.s_tiles, w.counters + 1, items, w.scnt);
+    scan2(w.scnt, nullptr, items, w.poff, nullptr, w.counters + 2, w.scan_tmp, s);
+    k_emit_pairs<<<8 * 152, EP_WARPS * 32, 0, s>>>(vs, sorted_slot, w.s_tiles, w.poff, w.counters, pair_capacity,
+                                                  w.k0, w.v0, d_status);
+    count_launch(2);
   }
-  int bits = 32 + tile_bits(tiles);
-  int which = radix_sort_pairs(w.k0, w.v0, w.k1, w.v1, w.hist, w.counters, pair_capacity, bits, s);
-  const uint64_t* sk = which ? w.k1 : w.k0;
-  const uint32_t* sv = which ? w.v1 : w.v0;
+  // 3) stable sort by tile: each tile's list stays front to back
+  radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.hist, w.counters, pair_capacity, tile_bits(tiles), s);
+  const uint32_t* sk = sorted_pair_tiles(w, tiles);
+  const uint32_t* sv = sorted_pair_slots(w, tiles);
   k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
   if (opts->tile == 8) launch_fwd<8>(tiles, s, vs, w, sv, opts->t_stop, out);
   else if (opts->tile == 16) launch_fwd<16>(tiles, s, vs, w, sv, opts->t_stop, out);
@@ -1144,8 +1266,7 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
   const int64_t n = vox->n;
-  const int which = sort_passes(32 + tile_bits(tiles)) & 1;
-  const uint32_t* sv = which ? w.v1 : w.v0;
+  const uint32_t* sv = sorted_pair_slots(w, tiles);
   if (!accumulate && n > 0) cudaMemsetAsync(d_density, 0, sizeof(float) * 8 * n, s);
   if (opts->tile == 8) launch_bwd<8>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
   else if (opts->tile == 16) launch_bwd<16>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
@@ -1191,10 +1312,9 @@ extern "C" lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_view
   make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
   FwdWs w = carve_fwd((void*)workspace, n, n_views, tiles, pixels, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace too small"); return LV_ERR_WORKSPACE; }
-  const int which = sort_passes(32 + tile_bits(tiles)) & 1;
   if (keys || voxel) {
-    k_debug_pairs<<<608, 256, 0, s>>>(which ? w.k1 : w.k0, which ? w.v1 : w.v0, w.slot_vox, w.counters, pair_capacity,
-                                       keys, voxel);
+    k_debug_pairs<<<608, 256, 0, s>>>(sorted_pair_tiles(w, tiles), sorted_pair_slots(w, tiles), w.slot_vox, w.s_dkey,
+                                       w.counters, pair_capacity, keys, voxel);
     count_launch(1);
   }
   if (ranges) cudaMemcpyAsync(ranges, w.ranges, sizeof(uint32_t) * 2 * tiles, cudaMemcpyDeviceToDevice, s);
@@ -1215,7 +1335,7 @@ extern "C" lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera*
   make_views(cams, n_views, opts->tile, &vs, &tiles, &npix);
   FwdWs w = carve_fwd((void*)workspace, vox->n, n_views, tiles, npix, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace too small"); return LV_ERR_WORKSPACE; }
-  const uint32_t* sv = (sort_passes(32 + tile_bits(tiles)) & 1) ? w.v1 : w.v0;
+  const uint32_t* sv = sorted_pair_slots(w, tiles);
   const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
   const unsigned grid = (unsigned)((n_px + 127) / 128);
 #define LV_F64(DT, ST)                                                                                            \

@@ -47,5 +47,6 @@ def test_host_only_queries_work_without_gpu(lib):
     opts = L.make_opts()
     a = L.lv_forward_workspace_size(1000, cams, 1, opts, 0)
     b = L.lv_forward_workspace_size(1000, cams, 1, opts, 10000)
-    assert a > 0 and b >= a + 10000 * 24 - 4096
+    # a pair of the capacity costs 16 bytes: (tile, slot) in two ping-pong buffers
+    assert a > 0 and a + 10000 * 16 - 1024 <= b <= a + 10000 * 16 + 1024
     assert L.lv_forward_workspace_size(1000, cams, 0, opts, 0) == 0
