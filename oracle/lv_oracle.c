@@ -898,27 +898,77 @@ static float depth_norm32(float z, float p_lo, float p_hi) {
 }
 
 /*
- * Depth-quantile pruning (Eq. 11-12, guards i and iii), FP32 decisions.
- *   Over the seen voxels: z~ from nearest-rank p_lo/p_hi of z (Eq. 14),
- *   bin b = min(nb-1, floor(nb * z~)); tau_b = k-th smallest w_max in bin b,
- *   k = max(1, ceil(q * |V_b|)) (Eq. 12 as nearest rank on the empirical CDF
- *   of Eq. 11); inside score x = [w_max > tau_b]; m <- (1-alpha) m + alpha x;
- *   s <- out if m < m_low, in if m > m_high, else unchanged (guard i);
- *   candidates: seen and s == out; at most floor(cap * n) of them, those with
- *   the smallest (w_max, id), are pruned (guard iii).
+ * Running depth percentiles (Eq. 14: "running" 5th / 95th percentiles): an
+ * EMA over adaptation steps, p <- (1 - r) p + r p_step in FP32 with the two
+ * products rounded separately; a state holding NaN (never updated) takes the
+ * step's value.  r == 0 or no state: the step's percentiles are used as they
+ * are.
+ */
+static void running_pct(float* p_lo, float* p_hi, float r, float one_minus_r, float* state) {
+  if (!(r > 0.0f) || !state) return;
+  if (isnan(state[0]) || isnan(state[1])) {
+    state[0] = *p_lo;
+    state[1] = *p_hi;
+    return;
+  }
+  float a0 = one_minus_r * state[0], b0 = r * *p_lo;
+  float a1 = one_minus_r * state[1], b1 = r * *p_hi;
+  state[0] = a0 + b0;
+  state[1] = a1 + b1;
+  *p_lo = state[0];
+  *p_hi = state[1];
+}
+
+/*
+ * Per-bin quantile q_b in ppm (Sec. IV-C: q_b "annealed over training with a
+ * mild near/far relaxation"), in integers so both sides agree exactly:
+ *   q_b = q * a * (1 - relax * |2 c_b - 1|),  c_b = (b + 1/2) / n_bins,
+ * with a (the schedule value) and relax in ppm: qa = floor(q a / 1e6), then
+ * q_b = floor(qa (1e6 n_bins - relax |2b + 1 - n_bins|) / (1e6 n_bins)).
+ * The relaxation lowers the quantile towards the nearest and farthest bins.
+ */
+int64_t ora_prune_q_bin(int64_t q_ppm, int64_t anneal_ppm, int64_t relax_ppm, int b, int n_bins) {
+  int64_t qa = q_ppm * anneal_ppm / 1000000;
+  int64_t dist = 2 * (int64_t)b + 1 - n_bins;
+  if (dist < 0) dist = -dist;
+  int64_t den = 1000000 * (int64_t)n_bins;
+  return qa * (den - relax_ppm * dist) / den;
+}
+
+/*
+ * Depth-quantile pruning (Eq. 11-12, guards i-iii), FP32 decisions.
+ *   Over the seen voxels: z~ from nearest-rank p_lo/p_hi of z (Eq. 14, or
+ *   their running EMA), bin b = min(nb-1, floor(nb * z~)); per bin the
+ *   quantile q_b (q, or the annealed/relaxed q_b); tau_b = k-th smallest w_max
+ *   in bin b, k = max(1, ceil(q_b * |V_b|)) (Eq. 12 as nearest rank on the
+ *   empirical CDF of Eq. 11); q_b = 0 sets no threshold (every voxel of the
+ *   bin votes in).  Inside score x = [w_max > tau_b]; m <- (1-alpha) m +
+ *   alpha x; s <- out if m < m_low, in if m > m_high, else unchanged (guard
+ *   i).  Keep-halo (guard ii): a voxel is protected this step when it is small
+ *   against the ray footprint (h < halo_small * delta, halo_small > 0 and
+ *   h/delta given) or carries a high weight near an image edge (w_max >=
+ *   halo_w and edge >= halo_edge, edge given).  Candidates: seen, s == out,
+ *   not protected; at most floor(cap * n) of them, those with the smallest
+ *   (w_max, id), are pruned (guard iii).
  *   s: 1 = in, 0 = out.  Unseen voxels keep m and s and are never pruned.
- *   one_minus_alpha is (1 - alpha) rounded to FP32 by the caller.
+ *   one_minus_alpha / one_minus_pct_ema are rounded to FP32 by the caller.
  */
 int ora_prune(int64_t n, const float* w_max, const uint8_t* seen, const float* z, float* m, uint8_t* s,
               int n_bins, int64_t q_ppm, float alpha, float one_minus_alpha, float m_low, float m_high,
               int64_t cap_ppm, int64_t lo_ppm, int64_t hi_ppm, uint8_t* prune_mask, int64_t* n_pruned,
-              float* tau_out, float* pct_out) {
+              float* tau_out, float* pct_out, int anneal, int64_t anneal_ppm, int64_t relax_ppm,
+              const float* h, const float* delta, float halo_small, const float* edge, float halo_w,
+              float halo_edge, float pct_ema, float one_minus_pct_ema, float* pct_state) {
   for (int64_t i = 0; i < n; ++i) prune_mask[i] = 0;
   *n_pruned = 0;
   float p_lo, p_hi;
   int64_t ns = percentiles(n, z, seen, lo_ppm, hi_ppm, &p_lo, &p_hi);
+  if (ns == 0) {
+    if (pct_out) { pct_out[0] = p_lo; pct_out[1] = p_hi; }
+    return 0;
+  }
+  running_pct(&p_lo, &p_hi, pct_ema, one_minus_pct_ema, pct_state);
   if (pct_out) { pct_out[0] = p_lo; pct_out[1] = p_hi; }
-  if (ns == 0) return 0;
   int* bin = (int*)malloc(sizeof(int) * (size_t)n);
   int64_t* cnt = (int64_t*)calloc((size_t)n_bins, sizeof(int64_t));
   float nbf = (float)n_bins;
@@ -933,41 +983,55 @@ int ora_prune(int64_t n, const float* w_max, const uint8_t* seen, const float* z
     cnt[b]++;
   }
   float* tau = (float*)malloc(sizeof(float) * (size_t)n_bins);
+  int* has_tau = (int*)calloc((size_t)n_bins, sizeof(int));
   float* buf = (float*)malloc(sizeof(float) * (size_t)ns);
   for (int b = 0; b < n_bins; ++b) {
     tau[b] = 0.0f;
     if (cnt[b] == 0) continue;
+    int64_t qb = anneal ? ora_prune_q_bin(q_ppm, anneal_ppm, relax_ppm, b, n_bins) : q_ppm;
+    if (qb <= 0) continue; /* no threshold: every voxel of the bin votes in */
     int64_t q = 0;
     for (int64_t i = 0; i < n; ++i)
       if (bin[i] == b) buf[q++] = w_max[i];
-    int64_t k = ppm_ceil(q_ppm, cnt[b]);
+    int64_t k = ppm_ceil(qb, cnt[b]);
     if (k < 1) k = 1;
     tau[b] = kth_smallest(buf, q, k);
+    has_tau[b] = 1;
   }
   if (tau_out)
     for (int b = 0; b < n_bins; ++b) tau_out[b] = tau[b];
   int64_t n_cand = 0;
+  uint8_t* cand = (uint8_t*)calloc((size_t)n, 1);
   for (int64_t i = 0; i < n; ++i) {
     if (bin[i] < 0) continue;
-    float x = (w_max[i] > tau[bin[i]]) ? 1.0f : 0.0f;
+    float x = (!has_tau[bin[i]] || w_max[i] > tau[bin[i]]) ? 1.0f : 0.0f;
     float a = one_minus_alpha * m[i];
     float c = alpha * x;
     float mm = a + c;
     m[i] = mm;
     if (mm < m_low) s[i] = 0;
     else if (mm > m_high) s[i] = 1;
-    if (s[i] == 0) n_cand++;
+    int prot = 0;
+    if (halo_small > 0.0f && h && delta) {
+      float lim = halo_small * delta[i];
+      prot |= h[4 * i + 3] < lim;
+    }
+    if (edge) prot |= (w_max[i] >= halo_w && edge[i] >= halo_edge);
+    if (s[i] == 0 && !prot) {
+      cand[i] = 1;
+      n_cand++;
+    }
   }
   int64_t cap = ppm_floor(cap_ppm, n);
   if (n_cand <= cap) {
     for (int64_t i = 0; i < n; ++i)
-      if (bin[i] >= 0 && s[i] == 0) prune_mask[i] = 1;
+      if (cand[i]) prune_mask[i] = 1;
     *n_pruned = n_cand;
   } else if (cap > 0) {
     kv* list = (kv*)malloc(sizeof(kv) * (size_t)n_cand);
     int64_t q = 0;
     for (int64_t i = 0; i < n; ++i)
-      if (bin[i] >= 0 && s[i] == 0) {
+      if (cand[i]) {
         list[q].key = f32_bits(w_max[i]); /* w_max >= 0: bits order = value order */
         list[q].val = (uint32_t)i;
         ++q;
@@ -977,9 +1041,11 @@ int ora_prune(int64_t n, const float* w_max, const uint8_t* seen, const float* z
     *n_pruned = cap;
     free(list);
   }
+  free(cand);
   free(bin);
   free(cnt);
   free(tau);
+  free(has_tau);
   free(buf);
   return 0;
 }
@@ -1032,7 +1098,8 @@ int ora_subdivide(int64_t n, const float* geom, const uint8_t* level, const floa
                   int64_t lo_ppm, int64_t hi_ppm, int64_t capacity, float* out_geom, uint8_t* out_level,
                   float* out_dens, float* out_sh, uint8_t* selected, int64_t* n_new, int64_t* k_out,
                   int n_aux, void* const* aux_in, void* const* aux_out, const int32_t* aux_width,
-                  const int32_t* aux_bytes, const uint32_t* aux_fill) {
+                  const int32_t* aux_bytes, const uint32_t* aux_fill, float pct_ema, float one_minus_pct_ema,
+                  float* pct_state) {
   uint8_t* flag = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
   int64_t n_alive = 0;
   for (int64_t i = 0; i < n; ++i) {
@@ -1042,7 +1109,8 @@ int ora_subdivide(int64_t n, const float* geom, const uint8_t* level, const floa
     selected[i] = 0;
   }
   float p_lo, p_hi;
-  percentiles(n, z, flag, lo_ppm, hi_ppm, &p_lo, &p_hi);
+  if (percentiles(n, z, flag, lo_ppm, hi_ppm, &p_lo, &p_hi) > 0)
+    running_pct(&p_lo, &p_hi, pct_ema, one_minus_pct_ema, pct_state);
   pk* list = (pk*)malloc(sizeof(pk) * (size_t)(n > 0 ? n : 1));
   int64_t n_el = 0;
   for (int64_t i = 0; i < n; ++i) {

@@ -12,6 +12,7 @@ follow in ``lv_oracle.c``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -66,9 +67,12 @@ def lib():
             _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P]
             _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P, P]
             _lib.ora_trace_pixel.argtypes = [I64, P, P, P, I32, P, D, I32, I32, I64, P, P, P, P, P]
-            _lib.ora_prune.argtypes = [I64, P, P, P, P, P, I32, I64, F, F, F, F, I64, I64, I64, P, P, P, P]
+            _lib.ora_prune.argtypes = [I64, P, P, P, P, P, I32, I64, F, F, F, F, I64, I64, I64, P, P, P, P,
+                                       I32, I64, I64, P, P, F, P, F, F, F, F, P]
+            _lib.ora_prune_q_bin.argtypes = [I64, I64, I64, I32, I32]
+            _lib.ora_prune_q_bin.restype = I64
             _lib.ora_subdivide.argtypes = [I64, P, P, P, P, P, P, P, P, P, F, F, I64, I64, I32, I64, I64, I64,
-                                           P, P, P, P, P, P, P, I32, P, P, P, P, P]
+                                           P, P, P, P, P, P, P, I32, P, P, P, P, P, F, F, P]
             _lib.ora_lf_loss.argtypes = [I32, P, P, P, P, D, D, I64, P, P, P, P]
             _lib.ora_lf_gamma.argtypes = [D, D, D, D]
             _lib.ora_lf_gamma.restype = D
@@ -199,8 +203,14 @@ def trace_pixel(scene: dict, cam: dict, x: int, y: int, t_stop: float = 1e-4, sh
 
 
 def prune(w_max, seen, z, m, s, n_bins=16, q_ppm=50000, ema_alpha=0.1, m_low=0.3, m_high=0.7, cap_ppm=10000,
-          lo_ppm=50000, hi_ppm=950000) -> dict:
-    """Depth-quantile pruning (Eq. 11-12, guards i and iii). m, s are returned updated (copies)."""
+          lo_ppm=50000, hi_ppm=950000, anneal_ppm=None, relax_ppm=0, geom=None, delta=None, halo_small=0.0,
+          edge=None, halo_w=0.0, halo_edge=0.0, pct_ema=0.0, pct_state=None) -> dict:
+    """Depth-quantile pruning (Eq. 11-12, guards i-iii). m, s are returned updated (copies).
+
+    anneal_ppm: the q_b schedule value a(t) in ppm (None: q_b = q in every bin);
+    relax_ppm: near/far relaxation; geom/delta/halo_small and edge/halo_w/halo_edge:
+    keep-halo tests (guard ii); pct_ema/pct_state: running percentiles (state is a
+    float32[2] updated in place, NaN = uninitialised)."""
     w_max = _c(w_max, np.float32)
     seen = _c(seen, np.uint8)
     z = _c(z, np.float32)
@@ -213,14 +223,38 @@ def prune(w_max, seen, z, m, s, n_bins=16, q_ppm=50000, ema_alpha=0.1, m_low=0.3
     npr = C.c_int64(0)
     a = np.float32(ema_alpha)
     oma = np.float32(np.float32(1.0) - a)
+    r = np.float32(pct_ema)
+    omr = np.float32(np.float32(1.0) - r)
+    g = None if geom is None else _c(geom, np.float32)
+    d = None if delta is None else _c(delta, np.float32)
+    e = None if edge is None else _c(edge, np.float32)
+    if pct_state is not None:
+        assert pct_state.dtype == np.float32 and pct_state.flags.c_contiguous and pct_state.size == 2
     lib().ora_prune(n, _p(w_max), _p(seen), _p(z), _p(m), _p(s), n_bins, q_ppm, float(a), float(oma),
                     float(np.float32(m_low)), float(np.float32(m_high)), cap_ppm, lo_ppm, hi_ppm, _p(mask),
-                    C.byref(npr), _p(tau), _p(pct))
+                    C.byref(npr), _p(tau), _p(pct), 0 if anneal_ppm is None else 1,
+                    0 if anneal_ppm is None else int(anneal_ppm), int(relax_ppm), _p(g), _p(d),
+                    float(np.float32(halo_small)), _p(e), float(np.float32(halo_w)), float(np.float32(halo_edge)),
+                    float(r), float(omr), _p(pct_state))
     return {"mask": mask, "n_pruned": npr.value, "m": m, "s": s, "tau": tau, "p_lo": pct[0], "p_hi": pct[1]}
 
 
+def prune_q_bin(q_ppm, anneal_ppm, relax_ppm, b, n_bins) -> int:
+    """The annealed, near/far-relaxed per-bin quantile q_b in ppm."""
+    return int(lib().ora_prune_q_bin(int(q_ppm), int(anneal_ppm), int(relax_ppm), int(b), int(n_bins)))
+
+
+def anneal_ppm(t, t0, t1) -> int:
+    """a(t) = clip((t - t0) / (t1 - t0), 0, 1) in ppm (floor), 1e6 when t1 <= t0."""
+    if t1 <= t0:
+        return 1000000
+    x = (float(t) - float(t0)) / (float(t1) - float(t0))
+    return int(math.floor(1e6 * min(max(x, 0.0), 1.0)))
+
+
 def subdivide(scene: dict, delta, z, u, seen, prune_mask=None, kappa=1.0, beta=0.2, top_ppm=50000,
-              budget=1 << 62, l_max=16, lo_ppm=50000, hi_ppm=950000, aux=None) -> dict:
+              budget=1 << 62, l_max=16, lo_ppm=50000, hi_ppm=950000, aux=None, pct_ema=0.0,
+              pct_state=None) -> dict:
     """Priority-driven subdivision (Eq. 13-16, budgeted top-k, child init).
 
     aux: list of (array [n, width] or [n], fill_value) copied for survivors and
@@ -265,7 +299,9 @@ def subdivide(scene: dict, delta, z, u, seen, prune_mask=None, kappa=1.0, beta=0
     rc = lib().ora_subdivide(n, _p(geom), _p(level), _p(dens), _p(sh), _p(delta), _p(z), _p(u), _p(seen), _p(pm),
                              float(np.float32(kappa)), float(np.float32(beta)), top_ppm, budget, l_max, lo_ppm,
                              hi_ppm, cap, _p(out["geom"]), _p(out["level"]), _p(out["density"]), _p(out["sh"]),
-                             _p(sel), C.byref(nn), C.byref(kk), na, ain, aout, aw, ab, af)
+                             _p(sel), C.byref(nn), C.byref(kk), na, ain, aout, aw, ab, af,
+                             float(np.float32(pct_ema)), float(np.float32(np.float32(1.0) - np.float32(pct_ema))),
+                             _p(pct_state))
     if rc != 0:
         raise RuntimeError("subdivide capacity")
     m = nn.value
