@@ -170,6 +170,14 @@ lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_view
  * global pixel id attaining it (-1 if never hit).  argmax is nullable. */
 lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n, float* w_max, int64_t* argmax, void* stream);
 
+/* Per-voxel edge score for the keep-halo guard: edge[i] = edge_map[argmax[i]]
+ * (the normalised Sobel magnitude of Eq. 7 at the pixel where the voxel's
+ * w_max was attained, see lv_lf_params.edge_out), 0 when argmax[i] < 0 or
+ * >= n_pix.  argmax: device [n] int64 (lv_unpack_wmax); edge_map: device
+ * [n_pix]; edge: device [n]. */
+lv_status lv_gather_edge(const int64_t* argmax, int64_t n, const float* edge_map, int64_t n_pix, float* edge,
+                         void* stream);
+
 /* Copy the sorted pair list of a forward workspace to device buffers:
  * keys[i] = (global tile << 32) | order-preserving f32 bits of z_centre,
  * voxel[i] = voxel id; ranges [tiles][2] = [start, end) per global tile.
@@ -205,19 +213,53 @@ typedef struct {
   int32_t cap_ppm;  /* per-step cap on pruned voxels, ppm of n (10000 = 1 %) */
   int32_t lo_ppm;   /* depth normalisation percentiles (Eq. 14): 50000 */
   int32_t hi_ppm;   /*                                            950000 */
+  /* --- optional guards; all-zero fields leave them off ----------------- */
+  /* q_b schedule (Sec. IV-C: q_b annealed over training with a mild
+   * near/far relaxation).  anneal != 0: q_b = q a (1 - relax |2 c_b - 1|),
+   * c_b = (b + 1/2) / n_bins, evaluated in integers (ppm):
+   * qa = floor(q anneal_ppm / 1e6), q_b = floor(qa (1e6 nb - relax_ppm
+   * |2b + 1 - nb|) / (1e6 nb)).  anneal_ppm = a(t), see lv_prune_anneal_ppm.
+   * A bin whose q_b is 0 has no threshold (its voxels all vote in). */
+  int32_t anneal;
+  int32_t anneal_ppm;
+  int32_t relax_ppm;   /* 0..1e6 */
+  /* keep-halo (guard ii): a voxel is protected this step (its EMA and state
+   * still update) when halo_small > 0 and h_v < halo_small * delta_v (small
+   * against the ray footprint; needs geom and delta), or when edge is given
+   * and w_max_v >= halo_w and edge_v >= halo_edge (a strong weight on an
+   * image edge).  FP32 comparisons. */
+  float halo_small;
+  float halo_w;
+  float halo_edge;
+  const float* geom;   /* device N x 4 (cx, cy, cz, h), nullable */
+  const float* delta;  /* device N, footprint delta_v (lv_fwd_out.delta_min), nullable */
+  const float* edge;   /* device N, edge score in [0, 1] (lv_gather_edge), nullable */
+  /* running depth percentiles (Eq. 14 "running"): pct_ema > 0 and pct_state
+   * given: p <- (1 - r) p + r p_step (FP32, products rounded separately) over
+   * calls; a state holding NaN takes the step's value.  pct_state is a device
+   * float[2] (p_lo, p_hi) that the caller initialises to NaN once. */
+  float pct_ema;
+  float* pct_state;
 } lv_prune_params;
+
+/* a(t) = clip((t - t0) / (t1 - t0), 0, 1) in ppm (floor, computed in double);
+ * 1000000 when t1 <= t0.  Host only. */
+int32_t lv_prune_anneal_ppm(double t, double t0, double t1);
 
 size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p);
 
 /* Over seen voxels: z~ = clip((z - p_lo) / (p_hi - p_lo), 0, 1) with
- * nearest-rank percentiles of z (Eq. 14), bin = min(nb - 1, floor(nb z~)),
- * tau_b = nearest-rank q-quantile of w_max in the bin (Eq. 11-12), inside
- * score x = [w_max > tau_b], m <- (1 - alpha) m + alpha x, hysteresis state
- * s (1 = in, 0 = out) (guard i); candidates are seen voxels with s = out and
- * at most floor(cap n) of them, the smallest (w_max, id), are pruned
- * (guard iii).  Decisions are FP32 with a fixed operation order.  ema_m and
- * state are updated in place; prune_mask [n] u8 is written; d_n_pruned (int64
- * device) receives the count.  Unseen voxels are unchanged and never pruned. */
+ * nearest-rank percentiles of z (Eq. 14; or their running EMA), bin =
+ * min(nb - 1, floor(nb z~)), tau_b = nearest-rank q_b-quantile of w_max in
+ * the bin (Eq. 11-12; q_b = q unless annealed), inside score x = [w_max >
+ * tau_b] (x = 1 in a bin without threshold), m <- (1 - alpha) m + alpha x,
+ * hysteresis state s (1 = in, 0 = out) (guard i); candidates are seen voxels
+ * with s = out that the keep-halo guard does not protect (guard ii), and at
+ * most floor(cap n) of them, the smallest (w_max, id), are pruned (guard
+ * iii).  Decisions are FP32 with a fixed operation order.  ema_m and state
+ * are updated in place; prune_mask [n] u8 is written; d_n_pruned (int64
+ * device) receives the count.  Unseen voxels are unchanged and never pruned.
+ * With no seen voxel nothing changes (pct_state included). */
 lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
                                   float* ema_m, uint8_t* state, const lv_prune_params* p, uint8_t* prune_mask,
                                   int64_t* d_n_pruned, void* workspace, size_t ws_bytes, int32_t* d_status,
@@ -235,6 +277,9 @@ typedef struct {
   int64_t budget;   /* global growth cap on the voxel count; each split adds 7 */
   int32_t lo_ppm;   /* depth percentiles for Eq. 14 (50000 / 950000) */
   int32_t hi_ppm;
+  /* running depth percentiles, as in lv_prune_params (0 / NULL: off) */
+  float pct_ema;
+  float* pct_state;  /* device float[2], NaN = uninitialised */
 } lv_subdiv_params;
 
 /* One per-voxel auxiliary array carried through topology changes (Adam
@@ -296,6 +341,8 @@ typedef struct {
   float gamma_max;  /* Eq. 9 */
   float t0, t1;     /* Eq. 9 ramp start / end (iterations) */
   int32_t pctl_ppm; /* Sobel magnitude normalisation percentile (990000 = P99) */
+  float* edge_out;  /* optional device [P] FP32: the normalised edge magnitude s
+                     * of every pixel (Eq. 7), e.g. for the keep-halo guard */
 } lv_lf_params;
 
 /* gamma(t) of Eq. 9 (host scalar). */
@@ -335,6 +382,49 @@ lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* 
 lv_status lv_lf_weighted_loss_noalloc(const float* rgb, const float* gt, const int32_t* widths,
                                       const int32_t* heights, int n_views, float t, const lv_lf_params* p,
                                       float* loss, float* dL_drgb, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* rest of the training step (Eq. 17 auxiliaries, Adam; Sec. IV-D)     */
+/* ------------------------------------------------------------------ */
+
+/* Workspace for lv_transmittance_loss and lv_adam_voxels (a few bytes of
+ * reduction scratch; one buffer may serve both calls on one stream). */
+size_t lv_train_workspace_size(void);
+
+/* Transmittance concentration of Eq. 17 (final T near 0 or 1), read as
+ * L_Tc = weight / n_pix * sum_p T_p (1 - T_p).  loss: device float (written);
+ * dL_dT: device [n_pix] FP32, nullable, weight (1 - 2 T_p) / n_pix written or,
+ * with accumulate != 0, added -- it feeds lv_rasterize_backward's dL_dT. */
+lv_status lv_transmittance_loss(const float* T, int64_t n_pix, float weight, float* loss, float* dL_dT,
+                                int accumulate, void* workspace, size_t ws_bytes, void* stream);
+
+typedef struct {
+  float lr_density;  /* learning rates */
+  float lr_sh;
+  float beta1;       /* Adam moment decays, in [0, 1) */
+  float beta2;
+  float eps;
+  int64_t step;      /* global step t >= 1 for the bias corrections 1 / (1 - beta^t) */
+  float tv_weight;   /* lambda of the density total variation of Eq. 17 (0: none) */
+} lv_adam_params;
+
+/* One Adam step on the voxel parameters, in place.  The density gradient is
+ * d_density plus the gradient of L_tv = tv_weight / n * sum_v sum over the
+ * 12 edges (i, j) of the voxel's corner cube (corner c = x + 2y + 4z) of
+ * (d_i - d_j)^2 -- Eq. 17's total variation of the density field, read on the
+ * 8 corner densities -- then for every parameter: m <- b1 m + (1 - b1) g,
+ * v <- b2 v + (1 - b2) g^2, p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 -
+ * b2^t)) + eps).  FP32 arithmetic; FP16 / BF16 parameter storage is rounded
+ * to nearest after the update.  density: device [n][8] (F32 or F16); sh:
+ * device [n][48] (F32 or BF16), updated only when d_sh is given; gradients
+ * and moments: device FP32 arrays of the same shapes, 16-byte aligned.
+ * tv_loss: nullable device float receiving L_tv of the densities before the
+ * update.  Children of a subdivision start from zero moments (the optimizer
+ * refresh of Sec. IV-D: lv_subdivide_apply fills them). */
+lv_status lv_adam_voxels(int64_t n, void* density, lv_dtype density_dtype, void* sh, lv_dtype sh_dtype,
+                         const float* d_density, const float* d_sh, float* m_density, float* v_density,
+                         float* m_sh, float* v_sh, const lv_adam_params* p, float* tv_loss, void* workspace,
+                         size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* misc                                                                 */

@@ -47,6 +47,7 @@ struct PruneState {
   uint32_t c_eq;          // candidates at the cap threshold
   uint32_t all;           // 1 when every candidate is pruned (n_cand <= cap)
   uint32_t all_ties;      // 1 when every candidate at the threshold is pruned
+  float p_lo, p_hi;       // depth normalisation of this step (Eq. 14, running or not)
   uint32_t bin_cnt[SELECT_MAX_QUERIES];
 };
 
@@ -96,13 +97,37 @@ __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t 
   }
 }
 
+// Running percentiles (Eq. 14 "running"): p <- (1 - r) p + r p_step over
+// calls, FP32 with the products rounded separately; a NaN state takes the
+// step's value.  Leaves this step's (p_lo, p_hi) in *lo_hi.
+__device__ __forceinline__ void running_pct(const SelectQuery* pct, float* state, float r, float omr, float* lo_hi) {
+  float p_lo = key_to_float(pct[0].result), p_hi = key_to_float(pct[1].result);
+  if (state && r > 0.f) {
+    if (isnan(state[0]) || isnan(state[1])) {
+      state[0] = p_lo;
+      state[1] = p_hi;
+    } else {
+      state[0] = __fadd_rn(__fmul_rn(omr, state[0]), __fmul_rn(r, p_lo));
+      state[1] = __fadd_rn(__fmul_rn(omr, state[1]), __fmul_rn(r, p_hi));
+      p_lo = state[0];
+      p_hi = state[1];
+    }
+  }
+  lo_hi[0] = p_lo;
+  lo_hi[1] = p_hi;
+}
+
+__global__ void k_pr_pct_apply(const SelectQuery* pct, PruneState* st, float* state, float r, float omr) {
+  if (threadIdx.x == 0 && st->ns > 0) running_pct(pct, state, r, omr, &st->p_lo);
+}
+
 // bin counts go through a block-local histogram (one global add per bin and block)
 __global__ void k_pr_bin(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z, int nb,
-                         const SelectQuery* pct, uint16_t* grp, PruneState* st) {
+                         uint16_t* grp, PruneState* st) {
   __shared__ uint32_t sh[SELECT_MAX_QUERIES];
   if (threadIdx.x < SELECT_MAX_QUERIES) sh[threadIdx.x] = 0;
   __syncthreads();
-  const float p_lo = key_to_float(pct[0].result), p_hi = key_to_float(pct[1].result);
+  const float p_lo = st->p_lo, p_hi = st->p_hi;
   for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
     if (!seen[i]) continue;
     const float zt = depth_norm(z[i], p_lo, p_hi);
@@ -115,30 +140,61 @@ __global__ void k_pr_bin(int64_t n, const uint8_t* __restrict__ seen, const floa
   if (threadIdx.x < nb && sh[threadIdx.x]) atomicAdd(&st->bin_cnt[threadIdx.x], sh[threadIdx.x]);
 }
 
-__global__ void k_pr_tau_queries(SelectQuery* q, const PruneState* st, int nb, uint32_t q_ppm) {
-  int b = threadIdx.x;
-  if (b < nb) { q[b].group = b; q[b].k = rank_ppm(q_ppm, st->bin_cnt[b]); }
+// q_b in ppm: q, or the annealed quantile with its near/far relaxation
+// (integers: qa = floor(q a / 1e6), q_b = floor(qa (1e6 nb - relax |2b+1-nb|) / (1e6 nb)))
+__device__ __forceinline__ long long q_bin(long long q_ppm, long long anneal_ppm, long long relax_ppm, int b, int nb) {
+  const long long qa = q_ppm * anneal_ppm / 1000000ll;
+  long long dist = 2ll * b + 1 - nb;
+  if (dist < 0) dist = -dist;
+  const long long den = 1000000ll * nb;
+  return qa * (den - relax_ppm * dist) / den;
 }
 
-// guard i: EMA of the inside score and hysteresis; collects the candidates
+// a bin with q_b = 0 gets k = 0: no threshold (result stays 0xffffffff)
+__global__ void k_pr_tau_queries(SelectQuery* q, const PruneState* st, int nb, uint32_t q_ppm, int anneal,
+                                 uint32_t anneal_ppm, uint32_t relax_ppm) {
+  int b = threadIdx.x;
+  if (b < nb) {
+    const long long qb = anneal ? q_bin(q_ppm, anneal_ppm, relax_ppm, b, nb) : (long long)q_ppm;
+    q[b].group = b;
+    q[b].k = qb > 0 ? rank_ppm((uint32_t)qb, st->bin_cnt[b]) : 0u;
+  }
+}
+
+// guard i: EMA of the inside score and hysteresis; guard ii: keep-halo
+// protection; the candidates (out state, not protected) are flagged in mask
+// and grouped in cand_grp
+struct Halo {
+  float small, w, edge;
+  const float4* geom;
+  const float* delta;
+  const float* edge_score;
+  const float* w_max;
+};
+
 __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const uint32_t* __restrict__ wkey,
                             const SelectQuery* tau, float alpha, float oma, float m_low, float m_high, float* ema_m,
-                            uint8_t* state, uint16_t* cand_grp, PruneState* st) {
+                            uint8_t* state, const Halo halo, uint8_t* mask, uint16_t* cand_grp, PruneState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool cand = false;
   if (i < n) {
     uint16_t b = grp[i];
     if (b != GROUP_NONE) {
-      const float x = wkey[i] > tau[b].result ? 1.f : 0.f;
+      const uint32_t t = tau[b].result;
+      const float x = (t == 0xffffffffu || wkey[i] > t) ? 1.f : 0.f;  // no threshold: votes in
       const float m = __fadd_rn(__fmul_rn(oma, ema_m[i]), __fmul_rn(alpha, x));
       ema_m[i] = m;
       uint8_t s = state[i];
       if (m < m_low) s = 0;
       else if (m > m_high) s = 1;
       state[i] = s;
-      cand = s == 0;
+      bool prot = false;
+      if (halo.small > 0.f && halo.geom && halo.delta) prot = halo.geom[i].w < __fmul_rn(halo.small, halo.delta[i]);
+      if (halo.edge_score) prot = prot || (halo.w_max[i] >= halo.w && halo.edge_score[i] >= halo.edge);
+      cand = s == 0 && !prot;
     }
     cand_grp[i] = cand ? 0 : GROUP_NONE;
+    mask[i] = cand ? 1 : 0;
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const int bl = __syncthreads_count(cand);
@@ -181,13 +237,14 @@ __global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, PruneStat
   }
 }
 
-__global__ void k_pr_mask(int64_t n, const uint16_t* __restrict__ grp, const uint8_t* __restrict__ state,
-                          const uint32_t* __restrict__ wkey, const SelectQuery* thr, const SelectQuery* tie,
-                          const PruneState* st, uint8_t* mask, int64_t* n_pruned, uint32_t cap) {
+// mask holds the candidate flags on entry and the pruning decision on exit
+__global__ void k_pr_mask(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
+                          const SelectQuery* tie, const PruneState* st, uint8_t* mask, int64_t* n_pruned,
+                          uint32_t cap) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   if (i < n) {
     bool p = false;
-    if (grp[i] != GROUP_NONE && state[i] == 0) {
+    if (mask[i]) {
       if (st->all) p = true;
       else if (thr[0].k != 0) {
         const uint32_t v = thr[0].result;
@@ -208,6 +265,7 @@ struct SubState {
   uint32_t c_eq;      // eligible voxels tied with the k-th
   uint32_t all_ties;  // 1 when every tie is split
   uint32_t fits;      // output capacity suffices
+  float p_lo, p_hi;   // depth normalisation of this step (Eq. 14, running or not)
 };
 
 struct SubWs {
@@ -269,6 +327,11 @@ __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_pp
   }
 }
 
+__global__ void k_sd_pct_apply(const SelectQuery* pct, SubState* st, const uint32_t* n_seen, float* state, float r,
+                               float omr) {
+  if (threadIdx.x == 0 && *n_seen > 0) running_pct(pct, state, r, omr, &st->p_lo);
+}
+
 __global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, uint32_t* counter) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool f = i < n && grp[i] == 0;
@@ -280,8 +343,8 @@ __global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, u
 // Eq. 13 eligibility and Eq. 15-16 priority; pkey orders by descending priority
 __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const uint8_t* __restrict__ level,
                               const float* __restrict__ delta, const float* __restrict__ z,
-                              const float* __restrict__ u, const SelectQuery* pct, float kappa, float beta, int l_max,
-                              uint16_t* grp, uint32_t* pkey, SubState* st) {
+                              const float* __restrict__ u, float kappa, float beta, int l_max, uint16_t* grp,
+                              uint32_t* pkey, SubState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool el = false;
   if (i < n) {
@@ -289,7 +352,7 @@ __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const 
       const float thr = __fmul_rn(kappa, delta[i]);
       if (geom[i].w > thr) {
         el = true;
-        const float zt = depth_norm(z[i], key_to_float(pct[0].result), key_to_float(pct[1].result));
+        const float zt = depth_norm(z[i], st->p_lo, st->p_hi);
         const float b = __fadd_rn(1.0f, __fmul_rn(beta, zt));
         const float p = __fmul_rn(u[i], b);
         pkey[i] = ~order_key(p);
@@ -552,6 +615,13 @@ __global__ void k_sd_write(int64_t n, int64_t max_children, const uint32_t* __re
 
 using namespace lv;
 
+extern "C" int32_t lv_prune_anneal_ppm(double t, double t0, double t1) {
+  if (!(t1 > t0)) return 1000000;
+  double x = (t - t0) / (t1 - t0);
+  x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+  return (int32_t)floor(1e6 * x);
+}
+
 extern "C" size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p) {
   if (n < 0 || !p) return 0;
   return carve_prune(nullptr, n).bytes;
@@ -568,6 +638,11 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   if (p->q_ppm < 0 || p->q_ppm > 1000000 || p->cap_ppm < 0 || p->cap_ppm > 1000000 || p->lo_ppm < 0 ||
       p->lo_ppm > 1000000 || p->hi_ppm < 0 || p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
   if (!(p->ema_alpha >= 0.f && p->ema_alpha <= 1.f)) { set_error("ema_alpha must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
+  if (p->anneal && (p->anneal_ppm < 0 || p->anneal_ppm > 1000000 || p->relax_ppm < 0 || p->relax_ppm > 1000000)) {
+    set_error("anneal_ppm and relax_ppm must be in [0, 1e6]"); return LV_ERR_INVALID_ARG;
+  }
+  if (!(p->pct_ema >= 0.f && p->pct_ema <= 1.f)) { set_error("pct_ema must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->halo_small >= 0.f) || isnan(p->halo_w) || isnan(p->halo_edge)) { set_error("bad keep-halo parameters"); return LV_ERR_INVALID_ARG; }
   if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
   PruneWs w = carve_prune(workspace, n);
   if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
@@ -585,14 +660,25 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w_max, w.grp, w.zkey, w.wkey, w.st);
   k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
-  k_pr_bin<<<blocks < 1216 ? blocks : 1216, TPB, 0, s>>>(n, seen, z, nb, w.q, w.grp, w.st);
-  // the percentiles in q[0..1] are consumed by the binning: q is reused per bin
-  k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm);
+  const float r = p->pct_ema, omr = 1.0f - r;  // rounded to FP32 once, as the oracle does
+  k_pr_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, r, omr);
+  k_pr_bin<<<blocks < 1216 ? blocks : 1216, TPB, 0, s>>>(n, seen, z, nb, w.grp, w.st);
+  // the percentiles in q[0..1] are consumed: q is reused per bin
+  k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal,
+                                                    (uint32_t)p->anneal_ppm, (uint32_t)p->relax_ppm);
   select_kth(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
   // candidates get their own group array (zkey is free now: reuse it as u16 storage)
   uint16_t* cand = (uint16_t*)w.zkey;
-  k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, cand,
-                                      w.st);
+  Halo halo;
+  halo.small = p->halo_small;
+  halo.w = p->halo_w;
+  halo.edge = p->halo_edge;
+  halo.geom = (const float4*)p->geom;
+  halo.delta = p->delta;
+  halo.edge_score = p->edge;
+  halo.w_max = w_max;
+  k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, halo,
+                                      prune_mask, cand, w.st);
   SelectQuery* qc = w.q + SELECT_MAX_QUERIES - 2;  // cap threshold
   SelectQuery* qi = w.q + SELECT_MAX_QUERIES - 1;  // tie id
   k_pr_cap_query<<<1, 32, 0, s>>>(qc, w.st, cap);
@@ -600,8 +686,8 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, cand, w.st);
   k_pr_tie_query<<<1, 32, 0, s>>>(qi, qc, w.st, cap);
   select_kth(nullptr, cand, n, qi, 1, w.sel_tmp, s);
-  k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.grp, state, w.wkey, qc, qi, w.st, prune_mask, d_n_pruned, cap);
-  count_launch(8);
+  k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, qi, w.st, prune_mask, d_n_pruned, cap);
+  count_launch(9);
   return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
 }
 
@@ -620,6 +706,7 @@ static lv_status check_sub(const lv_voxels* in, const lv_subdiv_params* p, int n
   if (in->sh_dtype != LV_F32 && in->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
   if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||
       p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->pct_ema >= 0.f && p->pct_ema <= 1.f)) { set_error("pct_ema must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
   if (out) {
     if (out->n < 0) { set_error("bad output capacity"); return LV_ERR_INVALID_ARG; }
     if (out->n > 0 && (!out->geom || !out->level || !out->density || !out->sh)) { set_error("null output array"); return LV_ERR_INVALID_ARG; }
@@ -660,8 +747,9 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_count_group0<<<blocks, TPB, 0, s>>>(n, w.grp, cnt_seen);
   k_sd_pct_queries<<<1, 32, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, cnt_seen);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  k_sd_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, cnt_seen, p->pct_state, p->pct_ema, 1.0f - p->pct_ema);
   cudaMemsetAsync(cnt_seen, 0, sizeof(uint32_t), s);
-  k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, w.q, p->kappa, p->beta,
+  k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, p->kappa, p->beta,
                                         p->l_max, w.grp, w.pkey, w.st);
   k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);
   select_kth(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
@@ -673,7 +761,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
   k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
-  count_launch(12);
+  count_launch(13);
   return cuda_check(cudaGetLastError(), "lv_subdivide_select");
 }
 

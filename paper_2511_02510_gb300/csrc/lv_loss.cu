@@ -101,7 +101,7 @@ __device__ __forceinline__ void block_add_f64(double v, double* dst) {
 // Grid-stride over the view's pixels with a bounded block count: one FP64
 // atomic per block (a per-256-pixel atomic would serialise at the L2).
 __global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery* q, const __grid_constant__ ViewPix vp,
-                            int v, float eps, float gamma, float* w, double* wsum) {
+                            int v, float eps, float gamma, float* w, double* wsum, float* edge_out) {
   const long long lo = vp.off[v], hi = vp.off[v + 1];
   const float P = __uint_as_float(q[v].result);
   const bool norm = q[v].k != 0 && P > 0.f;
@@ -111,6 +111,7 @@ __global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery
   for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     float s = 0.f;
     if (norm) s = fminf(fmaxf(__uint_as_float(mkey[p]) / P, 0.f), 1.f);
+    if (edge_out) edge_out[p] = s;
     const float wv = gamma == 0.f ? 1.f : powf(eps + 1.f - s, gamma);
     w[p] = wv;
     acc += wv;
@@ -213,7 +214,7 @@ extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, cons
   };
   for (int v = 0; v < n_views; ++v) {
     const long long np = vp.off[v + 1] - vp.off[v];
-    k_lf_weight<<<blocks_for(np), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum);
+    k_lf_weight<<<blocks_for(np), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum, p->edge_out);
   }
   for (int v = 0; v < n_views; ++v) {
     const long long np = vp.off[v + 1] - vp.off[v];

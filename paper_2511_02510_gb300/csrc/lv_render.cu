@@ -975,6 +975,14 @@ __global__ void k_unpack_wmax(const unsigned long long* __restrict__ packed, int
   }
 }
 
+__global__ void k_gather_edge(const int64_t* __restrict__ argmax, int64_t n, const float* __restrict__ edge_map,
+                              int64_t n_pix, float* __restrict__ edge) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t a = argmax[i];
+  edge[i] = (a >= 0 && a < n_pix) ? edge_map[a] : 0.f;
+}
+
 __global__ void k_debug_pairs(const uint32_t* __restrict__ k, const uint32_t* __restrict__ v,
                               const uint32_t* __restrict__ slot_vox, const uint32_t* __restrict__ s_dkey,
                               const unsigned long long* d_count, int64_t cap, uint64_t* ko, uint32_t* vo) {
@@ -1299,6 +1307,18 @@ extern "C" lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n,
   k_unpack_wmax<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(packed, n, w_max, argmax);
   count_launch(1);
   return cuda_check(cudaGetLastError(), "lv_unpack_wmax");
+}
+
+extern "C" lv_status lv_gather_edge(const int64_t* argmax, int64_t n, const float* edge_map, int64_t n_pix,
+                                    float* edge, void* stream) {
+  if (n < 0 || n_pix < 0 || (n > 0 && (!argmax || !edge || (n_pix > 0 && !edge_map)))) {
+    set_error("bad arguments");
+    return LV_ERR_INVALID_ARG;
+  }
+  if (n == 0) return LV_OK;
+  k_gather_edge<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(argmax, n, edge_map, n_pix, edge);
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_gather_edge");
 }
 
 extern "C" lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,

@@ -54,12 +54,17 @@ class lv_fwd_out(C.Structure):
 
 class lv_prune_params(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("q_ppm", C.c_int32), ("ema_alpha", C.c_float), ("m_low", C.c_float),
-                ("m_high", C.c_float), ("cap_ppm", C.c_int32), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32)]
+                ("m_high", C.c_float), ("cap_ppm", C.c_int32), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32),
+                ("anneal", C.c_int32), ("anneal_ppm", C.c_int32), ("relax_ppm", C.c_int32),
+                ("halo_small", C.c_float), ("halo_w", C.c_float), ("halo_edge", C.c_float),
+                ("geom", C.c_void_p), ("delta", C.c_void_p), ("edge", C.c_void_p),
+                ("pct_ema", C.c_float), ("pct_state", C.c_void_p)]
 
 
 class lv_subdiv_params(C.Structure):
     _fields_ = [("kappa", C.c_float), ("beta", C.c_float), ("top_ppm", C.c_int32), ("l_max", C.c_int32),
-                ("budget", C.c_int64), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32)]
+                ("budget", C.c_int64), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32),
+                ("pct_ema", C.c_float), ("pct_state", C.c_void_p)]
 
 
 class lv_aux_array(C.Structure):
@@ -67,9 +72,14 @@ class lv_aux_array(C.Structure):
                 ("fill", C.c_uint32)]
 
 
+class lv_adam_params(C.Structure):
+    _fields_ = [("lr_density", C.c_float), ("lr_sh", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("step", C.c_int64), ("tv_weight", C.c_float)]
+
+
 class lv_lf_params(C.Structure):
     _fields_ = [("eps", C.c_float), ("gamma_max", C.c_float), ("t0", C.c_float), ("t1", C.c_float),
-                ("pctl_ppm", C.c_int32)]
+                ("pctl_ppm", C.c_int32), ("edge_out", C.c_void_p)]
 
 
 # ------------------------------------------------------------------ loading
@@ -90,6 +100,12 @@ SIGNATURES = {
                                         _P]),
     "lv_sh_backward": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, C.c_int, _P]),
     "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
+    "lv_gather_edge": (C.c_int, [_P, _I64, _P, _I64, _P, _P]),
+    "lv_train_workspace_size": (_SZ, []),
+    "lv_transmittance_loss": (C.c_int, [_P, _I64, _F, _P, _P, C.c_int, _P, _SZ, _P]),
+    "lv_adam_voxels": (C.c_int, [_I64, _P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P,
+                                 C.POINTER(lv_adam_params), _P, _P, _SZ, _P]),
+    "lv_prune_anneal_ppm": (_I32, [C.c_double, C.c_double, C.c_double]),
     "lv_debug_pairs": (C.c_int, [_I64, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _P, _P, _P]),
     "lv_render_pixels_f64": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _I64, _P, _P, _P]),
     "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
@@ -236,6 +252,36 @@ def lv_sh_backward(vox, cams_arr, n_views, opts, workspace, pair_capacity, d_sh,
 def lv_unpack_wmax(packed, w_max, argmax=None):
     _check(load().lv_unpack_wmax(_ptr(packed), int(packed.numel()), _ptr(w_max), _ptr(argmax), _stream()),
            "lv_unpack_wmax")
+
+
+def lv_gather_edge(argmax, edge_map, edge):
+    _check(load().lv_gather_edge(_ptr(argmax), int(argmax.numel()), _ptr(edge_map), int(edge_map.numel()),
+                                 _ptr(edge), _stream()), "lv_gather_edge")
+
+
+def lv_train_workspace_size():
+    return int(load().lv_train_workspace_size())
+
+
+def lv_transmittance_loss(T, weight, loss, dL_dT, workspace, accumulate=False):
+    _check(load().lv_transmittance_loss(_ptr(T), int(T.numel()), float(weight), _ptr(loss), _ptr(dL_dT),
+                                        int(bool(accumulate)), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), _stream()),
+           "lv_transmittance_loss")
+
+
+def lv_adam_voxels(density, sh, d_density, d_sh, m_density, v_density, m_sh, v_sh, params, workspace,
+                   tv_loss=None):
+    """One Adam step (with the density TV gradient) on density [n, 8] and sh [n, 48], in place."""
+    _check(load().lv_adam_voxels(int(density.shape[0]), _ptr(density), _DT[density.dtype], _ptr(sh),
+                                 _DT[sh.dtype] if sh is not None else LV_F32, _ptr(d_density), _ptr(d_sh),
+                                 _ptr(m_density), _ptr(v_density), _ptr(m_sh), _ptr(v_sh), C.byref(params),
+                                 _ptr(tv_loss), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                 _stream()), "lv_adam_voxels")
+
+
+def lv_prune_anneal_ppm(t, t0, t1):
+    return int(load().lv_prune_anneal_ppm(float(t), float(t0), float(t1)))
 
 
 def lv_debug_pairs(n, cams_arr, n_views, opts, workspace, pair_capacity, keys=None, voxel=None, ranges=None):
