@@ -440,6 +440,84 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
             "step": "stats reset + forward + backward (composite + SH)"}
 
 
+def _time_ms(torch, fn, reps, warm=3):
+    """Mean device time of fn() over reps launches (CUDA events on the current stream)."""
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_next_rows(torch, L, wl, reps, hbm_peak):
+    """The rows beyond the per-step hot path, each timed on its own on the same scene and view:
+    the Adam update with the fused density TV gradient, the transmittance-concentration loss, and
+    the pruning guards (keep-halo with the edge map, annealed q_b, running percentiles)."""
+    n, dev = wl.n, "cuda"
+    out = {}
+    # Adam + TV: in place on copies of the parameters, FP32 moments
+    dens, sh = wl.scene.density.clone(), wl.scene.sh.clone()
+    md, vd = torch.zeros((n, 8), device=dev), torch.zeros((n, 8), device=dev)
+    ms, vs = torch.zeros((n, 48), device=dev), torch.zeros((n, 48), device=dev)
+    tws = torch.empty(L.lv_train_workspace_size(), dtype=torch.uint8, device=dev)
+    tvl = torch.zeros(1, device=dev)
+    p = L.lv_adam_params()
+    p.lr_density, p.lr_sh, p.beta1, p.beta2, p.eps, p.step, p.tv_weight = 1e-2, 2.5e-3, 0.9, 0.999, 1e-15, 10, 1e-4
+    ms_adam = _time_ms(torch, lambda: L.lv_adam_voxels(dens, sh, wl.d_dens, wl.d_sh, md, vd, ms, vs, p, tws,
+                                                       tv_loss=tvl), reps)
+    row = 7 * 8 * 4 + 7 * 48 * 4            # param, grad, m, v read; param, m, v written (FP32)
+    gbs = n * row / (ms_adam / 1e3) / 1e9
+    out["adam_tv"] = {"ms": ms_adam, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": gbs / hbm_peak, "bytes_per_voxel": row, "voxels": n,
+                      "kernels": "k_adam_density (fused L_tv gradient) + k_adam_flat (SH)"}
+    # transmittance concentration on the view's final T
+    dT = torch.empty(wl.npix, device=dev)
+    tcl = torch.zeros(1, device=dev)
+    ms_tc = _time_ms(torch, lambda: L.lv_transmittance_loss(wl.rctx.T, 0.01, tcl, dT, tws), reps)
+    gbs = wl.npix * 8 / (ms_tc / 1e3) / 1e9
+    out["transmittance_loss"] = {"ms": ms_tc, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs / hbm_peak, "pixels": wl.npix}
+    # pruning with every guard on: edge map from the loss, per-voxel gather, keep-halo, q_b, running pct
+    edge_map = torch.empty(wl.npix, device=dev)
+    edge = torch.empty(n, device=dev)
+    pct = torch.full((2,), float("nan"), device=dev)
+    ema, state = wl.ema.clone(), wl.state.clone()
+    pg = L.lv_prune_params()
+    for f, _ in L.lv_prune_params._fields_[:8]:
+        setattr(pg, f, getattr(wl.pp, f))
+    pg.anneal, pg.anneal_ppm, pg.relax_ppm = 1, L.lv_prune_anneal_ppm(wl.t_iter, 0.0, 900.0), 200000
+    pg.halo_small, pg.halo_w, pg.halo_edge = 0.5, 0.5, 0.5
+    pg.geom, pg.delta, pg.edge = wl.scene.geom.data_ptr(), wl.rctx.delta_min.data_ptr(), edge.data_ptr()
+    pg.pct_ema, pg.pct_state = 0.1, pct.data_ptr()
+    lf_edge = L.lv_lf_params()
+    for f, _ in L.lv_lf_params._fields_[:5]:
+        setattr(lf_edge, f, getattr(wl.lfp, f))
+    lf_edge.edge_out = edge_map.data_ptr()
+
+    def plain():
+        L.lv_lf_weighted_loss(wl.rctx.rgb, wl.gt, [W_IMG], [H_IMG], wl.t_iter, wl.lfp, wl.loss, wl.dL, wl.lf_ws)
+        L.lv_prune_depth_quantile(wl.w_max, wl.rctx.seen, wl.rctx.z_min, ema, state, wl.pp, wl.pmask,
+                                  wl.n_pruned, wl.pr_ws)
+
+    def guarded():
+        L.lv_lf_weighted_loss(wl.rctx.rgb, wl.gt, [W_IMG], [H_IMG], wl.t_iter, lf_edge, wl.loss, wl.dL, wl.lf_ws)
+        L.lv_gather_edge(wl.w_arg, edge_map, edge)
+        L.lv_prune_depth_quantile(wl.w_max, wl.rctx.seen, wl.rctx.z_min, ema, state, pg, wl.pmask, wl.n_pruned,
+                                  wl.pr_ws)
+
+    ms_plain = _time_ms(torch, plain, reps)
+    ms_guard = _time_ms(torch, guarded, reps)
+    out["prune_guards"] = {"ms_loss_and_prune": ms_plain, "ms_loss_and_prune_with_guards": ms_guard,
+                           "overhead_ms": ms_guard - ms_plain,
+                           "guards": "keep-halo (size + edge), annealed relaxed q_b, running percentiles"}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -582,6 +660,11 @@ def run_ours(args, rank, world, local):
                                          stage_ms["reset"]) / 1e3) / 1e6, "unit": UNIT}
             except Exception as e:  # keep the main line even if a variant fails
                 out["variants"] = {"error": repr(e)}
+        if not args.no_variants:
+            try:
+                out["next_rows"] = run_next_rows(torch, L, wl, K, hbm_peak)
+            except Exception as e:  # keep the main line even if a row fails
+                out["next_rows"] = {"error": repr(e)}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(scene_np, cam, gt_np)
         print(json.dumps(out), flush=True)
