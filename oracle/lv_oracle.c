@@ -25,6 +25,9 @@
  *       normalisation, gamma ramp).  FP64.
  *
  * Readings of points the paper leaves open (all listed in the design notes):
+ *   - exact segment integration (the variant, segment = 1): sigma = max(0,
+ *     mean of the trilinear field over the chord), Simpson's rule being exact
+ *     for the cubic profile of a trilinear field along a line;
  *   - opacity: 8 corner densities per voxel, sigma = max(0, trilinear at the
  *     segment midpoint), alpha = 1 - exp(-sigma * l), l = ray-box chord length
  *     with t >= 0;
@@ -545,14 +548,47 @@ static void free_lists(pixlists* L) {
 typedef struct {
   uint32_t id;
   double l, t_mid, sigma_raw, alpha, T_before;
-  double u[3];
+  double w8[8]; /* d sigma_raw / d corner_i */
 } sample;
+
+/* local coordinates (clamped to [0,1]^3) of the point o + t d in the voxel g */
+static void local_coords(const double* o, const double* d, double t, const float* g, double* u) {
+  for (int a = 0; a < 3; ++a) {
+    double pa = o[a] + t * d[a];
+    double lo = (double)g[a] - (double)g[3];
+    double v = (pa - lo) / (2.0 * (double)g[3]);
+    u[a] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+  }
+}
+
+/*
+ * Weights of the 8 corners in the sample's raw density.
+ *   segment == 0 (the default reading): the trilinear field at the chord
+ *   midpoint.
+ *   segment == 1 (the "exact segment integration" variant): the mean of the
+ *   trilinear field over the chord.  Along a line the trilinear field is a
+ *   cubic polynomial in t, so Simpson's rule is exact:
+ *   (1/l) int f dt = (f(t_in) + 4 f(t_mid) + f(t_out)) / 6.
+ */
+static void sample_weights(const double* o, const double* d, double t_in, double t_out, const float* g, int segment,
+                           double* w8) {
+  double u[3];
+  local_coords(o, d, 0.5 * (t_in + t_out), g, u);
+  trilinear_weights(u, w8);
+  if (!segment) return;
+  double wa[8], wb[8];
+  local_coords(o, d, t_in, g, u);
+  trilinear_weights(u, wa);
+  local_coords(o, d, t_out, g, u);
+  trilinear_weights(u, wb);
+  for (int i = 0; i < 8; ++i) w8[i] = (wa[i] + 4.0 * w8[i] + wb[i]) / 6.0;
+}
 
 /* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null.
  * bnd (nullable) receives the FP32 sensitivity bound of rgb, depth and T
  * (see fp32_dx); cmax is the largest colour channel of the view. */
 static int64_t march(const double* o, const double* d, double t_near, const cand* items, int64_t cnt,
-                     const float* geom,
+                     const float* geom, int segment,
                      const float* dens, const double* colors, double t_stop, sample* s, double* rgb,
                      double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid,
                      double cmax, double* bnd) {
@@ -581,15 +617,8 @@ static int64_t march(const double* o, const double* d, double t_near, const cand
     }
     double l = t_out - t_in;
     double tm = 0.5 * (t_in + t_out);
-    double u[3];
-    for (int a = 0; a < 3; ++a) {
-      double pa = o[a] + tm * d[a];
-      double lo = (double)g[a] - (double)g[3];
-      double v = (pa - lo) / (2.0 * (double)g[3]);
-      u[a] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-    }
     double w8[8];
-    trilinear_weights(u, w8);
+    sample_weights(o, d, t_in, t_out, g, segment, w8);
     double sr = 0.0;
     for (int i = 0; i < 8; ++i) sr += w8[i] * (double)d8[i];
     double sigma = sr > 0.0 ? sr : 0.0;
@@ -608,7 +637,7 @@ static int64_t march(const double* o, const double* d, double t_near, const cand
     *depth += w * tm;
     if (s) {
       s[k].id = id; s[k].l = l; s[k].t_mid = tm; s[k].sigma_raw = sr; s[k].alpha = alpha; s[k].T_before = T;
-      s[k].u[0] = u[0]; s[k].u[1] = u[1]; s[k].u[2] = u[2];
+      for (int i = 0; i < 8; ++i) s[k].w8[i] = w8[i];
     }
     if (bnd) {
       double dx = fp32_dx(g, d8, sigma, l, t_in, t_out, din, dout);
@@ -660,7 +689,8 @@ static void view_colors(int64_t n, const float* geom, const float* sh, int degre
  */
 int ora_render(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
                const ora_cam* cams, double t_stop, int brute, const int* crop, double* rgb, double* depth,
-               double* T, int32_t* n_hit, uint8_t* near_stop, double* w_max, int64_t* w_arg, double* bound) {
+               double* T, int32_t* n_hit, uint8_t* near_stop, double* w_max, int64_t* w_arg, double* bound,
+               int segment) {
   int nt = ora_threads();
   double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   double* twm = NULL;
@@ -691,7 +721,7 @@ int ora_render(int64_t n, const float* geom, const float* dens, const float* sh,
         double tn = cam_ray(&cd, x, y, d);
         int ns;
         double Tp;
-        int64_t k = march(cd.o, d, tn, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, dens, colors,
+        int64_t k = march(cd.o, d, tn, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, segment, dens, colors,
                           t_stop, NULL, rgb + 3 * gp, depth + gp, &Tp, &ns, twm ? twm + (int64_t)tid * n : NULL,
                           twa ? twa + (int64_t)tid * n : NULL, gp, cmax, bound ? bound + 3 * gp : NULL);
         T[gp] = Tp;
@@ -738,7 +768,7 @@ static void atomic_add(double* p, double v) {
  */
 int ora_render_backward(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
                         int n_views, const ora_cam* cams, double t_stop, const int* crop, const double* dL_drgb,
-                        const double* dL_ddepth, const double* dL_dT, double* d_density, double* d_sh) {
+                        const double* dL_ddepth, const double* dL_dT, double* d_density, double* d_sh, int segment) {
   double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   double* raw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
   double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -770,8 +800,8 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
           double d[3], rgbp[3], dp, Tf;
           int ns;
           double tn = cam_ray(&cd, x, y, d);
-          int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf,
-                            &ns, NULL, NULL, gp, 0.0, NULL);
+          int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp, &dp,
+                            &Tf, &ns, NULL, NULL, gp, 0.0, NULL);
           const double* gC = dL_drgb + 3 * gp;
           double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
           double gT = dL_dT ? dL_dT[gp] : 0.0;
@@ -785,11 +815,8 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
             double ds = q->l * (Tk * a - S - Tf * gT);
             S += w * a;
             for (int ch = 0; ch < 3; ++ch) atomic_add(&dcol[3 * (int64_t)q->id + ch], w * gC[ch]);
-            if (q->sigma_raw > 0.0) {
-              double w8[8];
-              trilinear_weights(q->u, w8);
-              for (int i = 0; i < 8; ++i) atomic_add(&d_density[8 * (int64_t)q->id + i], ds * w8[i]);
-            }
+            if (q->sigma_raw > 0.0)
+              for (int i = 0; i < 8; ++i) atomic_add(&d_density[8 * (int64_t)q->id + i], ds * q->w8[i]);
           }
         }
       }
@@ -819,7 +846,7 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
 /* one pixel's samples, for invariant checks (T after each sample, and w) */
 int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
                     const ora_cam* cam, double t_stop, int x, int y, int64_t max_out, uint32_t* ids,
-                    double* w_out, double* T_after, double* l_out, int64_t* n_out) {
+                    double* w_out, double* T_after, double* l_out, int64_t* n_out, int segment) {
   cam64 cd;
   cam_derive(cam, &cd);
   double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -833,8 +860,8 @@ int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float
   double d[3], rgbp[3], dp, Tf;
   int ns;
   double tn = cam_ray(&cd, x, y, d);
-  int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, dens, colors, t_stop, s, rgbp, &dp, &Tf, &ns, NULL,
-                    NULL, 0, 0.0, NULL);
+  int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp, &dp, &Tf,
+                    &ns, NULL, NULL, 0, 0.0, NULL);
   int64_t m = K < max_out ? K : max_out;
   for (int64_t k = 0; k < m; ++k) {
     ids[k] = s[k].id;

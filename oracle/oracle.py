@@ -64,9 +64,9 @@ def lib():
             P = C.c_void_p
             I64, I32, D, F = C.c_int64, C.c_int, C.c_double, C.c_float
             _lib.ora_pairs.argtypes = [I64, P, I32, P, I32, I64, P, P, P, P, P, P, P]
-            _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P]
-            _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P, P]
-            _lib.ora_trace_pixel.argtypes = [I64, P, P, P, I32, P, D, I32, I32, I64, P, P, P, P, P]
+            _lib.ora_render.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P, I32]
+            _lib.ora_render_backward.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P, P, I32]
+            _lib.ora_trace_pixel.argtypes = [I64, P, P, P, I32, P, D, I32, I32, I64, P, P, P, P, P, I32]
             _lib.ora_prune.argtypes = [I64, P, P, P, P, P, I32, I64, F, F, F, F, I64, I64, I64, P, P, P, P,
                                        I32, I64, I64, P, P, F, P, F, F, F, F, P]
             _lib.ora_prune_q_bin.argtypes = [I64, I64, I64, I32, I32]
@@ -140,8 +140,11 @@ def _npix(cams):
 
 
 def render(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, brute: bool = False,
-           crop=None) -> dict:
+           crop=None, segment: bool = False) -> dict:
     """FP64 forward render (Eq. 1-5) of all views; outputs over all views' pixels.
+
+    segment: the exact-segment-integration variant (sample density = mean of
+    the trilinear field over the chord) instead of the chord-midpoint value.
 
     bound_rgb / bound_depth / bound_T: admissible FP32-vs-FP64 difference of
     each pixel from the sensitivity of its samples to FP32 geometry rounding;
@@ -162,13 +165,13 @@ def render(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, br
     bnd = np.zeros((P, 3), np.float64)
     cr = None if crop is None else _c(np.asarray(crop).reshape(-1, 4), np.int32)
     lib().ora_render(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, int(brute),
-                     _p(cr), _p(rgb), _p(depth), _p(T), _p(nh), _p(ns), _p(wm), _p(wa), _p(bnd))
+                     _p(cr), _p(rgb), _p(depth), _p(T), _p(nh), _p(ns), _p(wm), _p(wa), _p(bnd), int(segment))
     return {"rgb": rgb, "depth": depth, "T": T, "n_hit": nh, "near_stop": ns, "w_max": wm, "w_arg": wa,
             "bound_rgb": bnd[:, 0], "bound_depth": bnd[:, 1], "bound_T": bnd[:, 2]}
 
 
 def render_backward(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None, t_stop: float = 1e-4,
-                    sh_degree: int = 3, crop=None) -> dict:
+                    sh_degree: int = 3, crop=None, segment: bool = False) -> dict:
     """FP64 gradients of sum(g_C . rgb + g_D depth + g_T T) w.r.t. corner densities and SH."""
     geom = _c(scene["geom"], np.float32)
     dens = _c(scene["density"], np.float32)
@@ -181,12 +184,12 @@ def render_backward(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None
     ds = np.zeros((n, 48), np.float64)
     cr = None if crop is None else _c(np.asarray(crop).reshape(-1, 4), np.int32)
     lib().ora_render_backward(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, _p(cr),
-                              _p(gC), _p(gD), _p(gT), _p(dd), _p(ds))
+                              _p(gC), _p(gD), _p(gT), _p(dd), _p(ds), int(segment))
     return {"d_density": dd, "d_sh": ds}
 
 
 def trace_pixel(scene: dict, cam: dict, x: int, y: int, t_stop: float = 1e-4, sh_degree: int = 3,
-                max_out: int = 4096) -> dict:
+                max_out: int = 4096, segment: bool = False) -> dict:
     geom = _c(scene["geom"], np.float32)
     dens = _c(scene["density"], np.float32)
     sh = _c(scene["sh"], np.float32)
@@ -197,7 +200,7 @@ def trace_pixel(scene: dict, cam: dict, x: int, y: int, t_stop: float = 1e-4, sh
     ll = np.zeros(max_out, np.float64)
     k = C.c_int64(0)
     lib().ora_trace_pixel(n, _p(geom), _p(dens), _p(sh), sh_degree, _cams([cam]), t_stop, x, y, max_out,
-                          _p(ids), _p(w), _p(Ta), _p(ll), C.byref(k))
+                          _p(ids), _p(w), _p(Ta), _p(ll), C.byref(k), int(segment))
     m = min(k.value, max_out)
     return {"ids": ids[:m], "w": w[:m], "T_after": Ta[:m], "l": ll[:m], "n": k.value}
 
