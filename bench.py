@@ -407,12 +407,16 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
         sc = scene_np
         cams = [synth.orbit_camera(980, 545, 60.0, 3.0, 45.0 * i, 15.0) for i in range(8)]
         dd, sd = torch.float16, torch.bfloat16
+    elif kind == "exact_segment_fp32":  # the plain view with the exact-segment density variant
+        sc = scene_np
+        cams = [camera_for(0)]
+        dd, sd = torch.float32, torch.float32
     else:  # semi_transparent_fp32: the plain view of the same octree with peak density 10 per unit
         sc = synth.scene_360(opaque=False)
         cams = [camera_for(0)]
         dd, sd = torch.float32, torch.float32
     scene = Scene.from_numpy(sc, "cuda", dd, sd)
-    ctx = RasterContext(cams, scene.n)
+    ctx = RasterContext(cams, scene.n, exact_segment=(kind == "exact_segment_fp32"))
     vox = scene.voxels()
     ctx.fit_capacity(vox)
     g = torch.randn((ctx.n_pix, 3), device="cuda") * 1e-3
@@ -654,7 +658,8 @@ def run_ours(args, rank, world, local):
         if not args.no_variants:
             try:
                 out["variants"] = {k: run_variant(torch, synth, k, scene_np)
-                                   for k in ("batched16_fp32", "batched8_mixed", "semi_transparent_fp32")}
+                                   for k in ("batched16_fp32", "batched8_mixed", "semi_transparent_fp32",
+                                             "exact_segment_fp32")}
                 out["variants"]["plain_fp32_fwd_bwd_only"] = {
                     "value": wl.npix / ((stage_ms["forward"] + stage_ms["backward"] + stage_ms["sh_backward"] +
                                          stage_ms["reset"]) / 1e3) / 1e6, "unit": UNIT}

@@ -62,6 +62,12 @@ typedef enum {
 typedef enum { LV_F32 = 0, LV_F16 = 1, LV_BF16 = 2 } lv_dtype;
 
 #define LV_FLAG_SYNC_CHECK 1u  /* synchronise and return the device status */
+/* Density-model variant: a sample's density is the mean of the voxel's
+ * trilinear corner field over the chord instead of its value at the chord
+ * midpoint (the exact integral of the cubic profile, by Simpson's rule over
+ * the chord ends and midpoint), sigma = max(0, mean), alpha = 1 - exp(-sigma l)
+ * (Eq. 2-4).  Forward and backward of one step must use the same flags. */
+#define LV_FLAG_EXACT_SEGMENT 2u
 
 /* Voxel set (all device pointers). density_dtype: LV_F32 or LV_F16; sh_dtype: LV_F32 or LV_BF16. */
 typedef struct {

@@ -549,12 +549,11 @@ __device__ __forceinline__ bool chord(const Ray& r, float4 g, float& t_in, float
 }
 
 // local coordinates u = (p - (c - h)) / (2h) = (t d - rc) / (2h) + 1/2 of the
-// chord midpoint, clamped to [0,1]^3, and the trilinear density there
-__device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, float4 d1, float i2h, float tm,
-                                             float* u) {
-  u[0] = __saturatef(fmaf(fmaf(tm, r.dx, -g.x), i2h, 0.5f));
-  u[1] = __saturatef(fmaf(fmaf(tm, r.dy, -g.y), i2h, 0.5f));
-  u[2] = __saturatef(fmaf(fmaf(tm, r.dz, -g.z), i2h, 0.5f));
+// ray point at t, clamped to [0,1]^3, and the trilinear density there
+__device__ __forceinline__ float trilin(const Ray& r, float4 g, float4 d0, float4 d1, float i2h, float t, float* u) {
+  u[0] = __saturatef(fmaf(fmaf(t, r.dx, -g.x), i2h, 0.5f));
+  u[1] = __saturatef(fmaf(fmaf(t, r.dy, -g.y), i2h, 0.5f));
+  u[2] = __saturatef(fmaf(fmaf(t, r.dz, -g.z), i2h, 0.5f));
   float c00 = fmaf(u[0], d0.y - d0.x, d0.x);
   float c10 = fmaf(u[0], d0.w - d0.z, d0.z);
   float c01 = fmaf(u[0], d1.y - d1.x, d1.x);
@@ -562,6 +561,34 @@ __device__ __forceinline__ float mid_density(const Ray& r, float4 g, float4 d0, 
   float c0 = fmaf(u[1], c10 - c00, c00);
   float c1 = fmaf(u[1], c11 - c01, c01);
   return fmaf(u[2], c1 - c0, c0);
+}
+
+// Raw density of a sample: the trilinear field at the chord midpoint (u[0..2]),
+// or, for the exact-segment variant (SEG), its mean over the chord: along a
+// line the field is a cubic in t, so Simpson's rule (f_in + 4 f_mid + f_out) / 6
+// is exact (u[3..5] at t_in, u[6..8] at t_out).
+template <bool SEG>
+__device__ __forceinline__ float sample_density(const Ray& r, float4 g, float4 d0, float4 d1, float i2h, float t_in,
+                                                float tm, float t_out, float* u) {
+  const float fm = trilin(r, g, d0, d1, i2h, tm, u);
+  if constexpr (!SEG) {
+    return fm;
+  } else {
+    const float fa = trilin(r, g, d0, d1, i2h, t_in, u + 3);
+    const float fb = trilin(r, g, d0, d1, i2h, t_out, u + 6);
+    return (fa + 4.f * fm + fb) * (1.f / 6.f);
+  }
+}
+
+// v[c] = s * (trilinear weight of corner c at u), or += with ADD
+template <bool ADD>
+__device__ __forceinline__ void corner_weights(float* v, float s, const float* u) {
+  const float ux = u[0], uy = u[1], uz = u[2];
+  const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
+  const float a00 = s * my * mz, a10 = s * uy * mz, a01 = s * my * uz, a11 = s * uy * uz;
+  const float w[8] = {mx * a00, ux * a00, mx * a10, ux * a10, mx * a01, ux * a01, mx * a11, ux * a11};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = ADD ? v[c] + w[c] : w[c];
 }
 
 // 1 - exp(-x) given e = exp(-x): a 5-term series below 1/8 (relative error
@@ -617,7 +644,7 @@ constexpr size_t BWD_SLICE = 32 * 64 + 32 * 4 * 3;
 template <int TS>
 constexpr int min_blocks() { return TS == 16 ? 5 : (TS == 8 ? 16 : 1); }
 
-template <int TS>
+template <int TS, bool SEG>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -676,8 +703,8 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
       if (hit) {
         const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
         const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-        float u[3];
-        const float sigma = fmaxf(mid_density(r, g, d0, d1, col.w, tm, u), 0.f);
+        float u[SEG ? 9 : 3];
+        const float sigma = fmaxf(sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u), 0.f);
         const float x = sigma * l;
         const float ex = __expf(-x);
         const float alpha = one_minus_exp(x, ex);
@@ -754,7 +781,7 @@ __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
 // any of its pixels used, in the same 32-entry chunks and with the same
 // compaction as the forward; the per-record gradients (8 corners + colour) are
 // reduced over the warp and sent with three 16-byte global reductions.
-template <int TS>
+template <int TS, bool SEG>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -834,8 +861,8 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
       if (hit) {
         const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
         const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-        float u[3];
-        const float sraw = mid_density(r, g, d0, d1, col.w, tm, u);
+        float u[SEG ? 9 : 3];
+        const float sraw = sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u);
         const float sigma = fmaxf(sraw, 0.f);
         const float x = sigma * l;
         const float Tk = Tcur;  // transmittance after this sample: the previous step's T_prev
@@ -849,17 +876,11 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
         S = fmaf(w, a, S);
         tau = tau_prev;
         const float dr = sraw > 0.f ? ds : 0.f;
-        const float ux = u[0], uy = u[1], uz = u[2];
-        const float mx = 1.f - ux, my = 1.f - uy, mz = 1.f - uz;
-        const float a00 = dr * my * mz, a10 = dr * uy * mz, a01 = dr * my * uz, a11 = dr * uy * uz;
-        v[0] = mx * a00;
-        v[1] = ux * a00;
-        v[2] = mx * a10;
-        v[3] = ux * a10;
-        v[4] = mx * a01;
-        v[5] = ux * a01;
-        v[6] = mx * a11;
-        v[7] = ux * a11;
+        corner_weights<false>(v, SEG ? dr * (4.f / 6.f) : dr, u);
+        if constexpr (SEG) {
+          corner_weights<true>(v, dr * (1.f / 6.f), u + 3);
+          corner_weights<true>(v, dr * (1.f / 6.f), u + 6);
+        }
         v[8] = w * gr;
         v[9] = w * gg;
         v[10] = w * gb;
@@ -1018,7 +1039,7 @@ __global__ void k_render_f64(const __grid_constant__ ViewSet vs, const uint32_t*
                              const uint32_t* __restrict__ svals, const uint32_t* __restrict__ slot_vox,
                              const float4* __restrict__ geom, const DT* __restrict__ dens, const ST* __restrict__ sh,
                              int sh_nb, const int64_t* __restrict__ pixels, int64_t n_px, double t_stop,
-                             double* __restrict__ rgb_out, double* __restrict__ T_out) {
+                             int segment, double* __restrict__ rgb_out, double* __restrict__ T_out) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_px) return;
   const long long gp = pixels[q];
@@ -1062,12 +1083,18 @@ __global__ void k_render_f64(const __grid_constant__ ViewSet vs, const uint32_t*
     }
     if (miss || !(hi_t - lo_t > 0.0)) continue;
     const double l = hi_t - lo_t, tm = 0.5 * (lo_t + hi_t);
-    double u[3];
-    for (int a = 0; a < 3; ++a) u[a] = fmin(fmax((o[a] + tm * d[a] - (cc[a] - h)) / (2.0 * h), 0.0), 1.0);
+    // the trilinear field at the midpoint, or its mean over the chord (Simpson, exact for the cubic)
+    const double ts3[3] = {tm, lo_t, hi_t}, ws3[3] = {segment ? 4.0 / 6.0 : 1.0, 1.0 / 6.0, 1.0 / 6.0};
     double sr = 0.0;
-    for (int i = 0; i < 8; ++i) {
-      const double w = ((i & 1) ? u[0] : 1.0 - u[0]) * ((i & 2) ? u[1] : 1.0 - u[1]) * ((i & 4) ? u[2] : 1.0 - u[2]);
-      sr += w * (double)to_f32(dens[8 * (size_t)vox + i]);
+    for (int q3 = 0; q3 < (segment ? 3 : 1); ++q3) {
+      double u[3];
+      for (int a = 0; a < 3; ++a)
+        u[a] = fmin(fmax((o[a] + ts3[q3] * d[a] - (cc[a] - h)) / (2.0 * h), 0.0), 1.0);
+      for (int i = 0; i < 8; ++i) {
+        const double w =
+            ((i & 1) ? u[0] : 1.0 - u[0]) * ((i & 2) ? u[1] : 1.0 - u[1]) * ((i & 4) ? u[2] : 1.0 - u[2]);
+        sr += ws3[q3] * w * (double)to_f32(dens[8 * (size_t)vox + i]);
+      }
     }
     const double sigma = fmax(sr, 0.0);
     const double alpha = -expm1(-sigma * l);
@@ -1132,31 +1159,57 @@ static lv_status finish(lv_status st, uint32_t flags, int32_t* d_status, cudaStr
   return LV_OK;
 }
 
-template <int TS>
-static void launch_fwd(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                       float t_stop, const lv_fwd_out* out) {
+template <int TS, bool SEG>
+static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+                         float t_stop, const lv_fwd_out* out) {
   const size_t smem = FWD_SLICE * (TS * TS / 32);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fwd<TS, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_fwd<TS><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop, out->rgb,
-                                                 out->depth, out->T, out->n_contrib, out->n_samples, w.tau,
-                                                 out->wmax_packed);
+  k_fwd<TS, SEG><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
+                                                        out->rgb, out->depth, out->T, out->n_contrib, out->n_samples,
+                                                        w.tau, out->wmax_packed);
 }
 
-template <int TS>
-static void launch_bwd(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                       const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
+template <int TS, bool SEG>
+static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
+                         const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
   const size_t smem = BWD_SLICE * (TS * TS / 32);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_bwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_bwd<TS, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_bwd<TS><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T, w.tau,
-                                                 fwd->n_contrib, gC, gD, gT, dd, w.d_rgb);
+  k_bwd<TS, SEG><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T, w.tau,
+                                                        fwd->n_contrib, gC, gD, gT, dd, w.d_rgb);
+}
+
+// tile size and density model (midpoint, or the exact-segment variant) from the options
+static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
+                       const uint32_t* sv, const lv_fwd_out* out) {
+  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0;
+#define LV_FWD(TS)                                                             \
+  if (seg) launch_fwd_t<TS, true>(tiles, s, vs, w, sv, o->t_stop, out);        \
+  else launch_fwd_t<TS, false>(tiles, s, vs, w, sv, o->t_stop, out)
+  if (o->tile == 8) { LV_FWD(8); }
+  else if (o->tile == 16) { LV_FWD(16); }
+  else { LV_FWD(32); }
+#undef LV_FWD
+}
+
+static void launch_bwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
+                       const uint32_t* sv, const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT,
+                       float* dd) {
+  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0;
+#define LV_BWD(TS)                                                                 \
+  if (seg) launch_bwd_t<TS, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);       \
+  else launch_bwd_t<TS, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd)
+  if (o->tile == 8) { LV_BWD(8); }
+  else if (o->tile == 16) { LV_BWD(16); }
+  else { LV_BWD(32); }
+#undef LV_BWD
 }
 
 }  // namespace lv
@@ -1225,9 +1278,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   const uint32_t* sk = sorted_pair_tiles(w, tiles);
   const uint32_t* sv = sorted_pair_slots(w, tiles);
   k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
-  if (opts->tile == 8) launch_fwd<8>(tiles, s, vs, w, sv, opts->t_stop, out);
-  else if (opts->tile == 16) launch_fwd<16>(tiles, s, vs, w, sv, opts->t_stop, out);
-  else launch_fwd<32>(tiles, s, vs, w, sv, opts->t_stop, out);
+  launch_fwd(opts, tiles, s, vs, w, sv, out);
   count_launch(2);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
 }
@@ -1276,9 +1327,7 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
   const int64_t n = vox->n;
   const uint32_t* sv = sorted_pair_slots(w, tiles);
   if (!accumulate && n > 0) cudaMemsetAsync(d_density, 0, sizeof(float) * 8 * n, s);
-  if (opts->tile == 8) launch_bwd<8>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
-  else if (opts->tile == 16) launch_bwd<16>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
-  else launch_bwd<32>(tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  launch_bwd(opts, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
   count_launch(1);
   if (d_sh) launch_sh_bwd(vox, vs, w, d_sh, accumulate, s);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_backward");
@@ -1361,7 +1410,8 @@ extern "C" lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera*
 #define LV_F64(DT, ST)                                                                                            \
   k_render_f64<DT, ST><<<grid, 128, 0, s>>>(vs, w.ranges, sv, w.slot_vox, (const float4*)vox->geom,              \
                                             (const DT*)vox->density, (const ST*)vox->sh, nb, pixels, n_px,       \
-                                            (double)opts->t_stop, rgb, T)
+                                            (double)opts->t_stop, (opts->flags & LV_FLAG_EXACT_SEGMENT) ? 1 : 0,  \
+                                            rgb, T)
   if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_F64(float, float);
   else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_F64(__half, float);
   else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_F64(float, __nv_bfloat16);

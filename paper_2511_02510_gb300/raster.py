@@ -18,16 +18,20 @@ from . import litevoxel as L
 class RasterContext:
     """Workspace and outputs for one camera set and a voxel count.
 
+    exact_segment selects the density-model variant in which a sample's
+    density is the mean of the trilinear field over the chord.
+
     The pair capacity (sorted (tile, voxel) pairs) is sized once, with
     headroom, by :meth:`fit_capacity`; a later forward that overflows it
     reports LV_ERR_CAPACITY (checked by :meth:`check`).
     """
 
-    def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda"):
+    def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda",
+                 exact_segment=False):
         self.cams = list(cams)
         self.n_views = len(self.cams)
         self.cams_arr = L.make_cameras(self.cams)
-        self.opts = L.make_opts(tile, batch, t_stop)
+        self.opts = L.make_opts(tile, batch, t_stop, exact_segment=exact_segment)
         self.device = torch.device(device)
         self.n = int(n_voxels)
         self.sizes = [(int(c["width"]), int(c["height"])) for c in self.cams]
