@@ -516,6 +516,34 @@ def run_next_rows(torch, L, wl, reps, hbm_peak):
 
     ms_plain = _time_ms(torch, plain, reps)
     ms_guard = _time_ms(torch, guarded, reps)
+    # shared grid-vertex densities: index build, then forward + backward + vertex-gradient scatter
+    from paper_2511_02510_gb300.raster import RasterContext
+    unit = float(wl.scene.geom[:, 3].min())
+    vidx = torch.empty((n, 8), dtype=torch.int32, device=dev)
+    nvt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms_index = _time_ms(torch, lambda: L.lv_build_vertex_index(wl.scene.geom, unit, vidx, nvt), 3, warm=1)
+    n_vert = int(nvt.item())
+    vsum, vcnt = torch.zeros(n_vert, device=dev), torch.zeros(n_vert, device=dev)
+    L.lv_vertex_scatter_add(vidx, wl.scene.density, vsum, vcnt)
+    vdens = vsum / vcnt.clamp_min(1.0)
+    vvox = L.make_voxels(wl.scene.geom, vdens, wl.scene.sh, vidx=vidx)
+    vctx = RasterContext(wl.cams, n)
+    vctx.fit_capacity(vvox)
+    gvert = torch.zeros(n_vert, device=dev)
+    dcorner = torch.empty((n, 8), device=dev)
+    dsh = torch.empty((n, 48), device=dev)
+
+    def vstep():
+        vctx.reset_stats()
+        vctx.forward(vvox)
+        vctx.backward(vvox, wl.dL, d_density=dcorner, d_sh=dsh)
+        gvert.zero_()
+        L.lv_vertex_scatter_add(vidx, dcorner, gvert)
+
+    ms_vstep = _time_ms(torch, vstep, reps)
+    out["vertex_densities"] = {"vertices": n_vert, "ms_build_index": ms_index,
+                               "ms_fwd_bwd_scatter": ms_vstep, "mpix_s": wl.npix / (ms_vstep / 1e3) / 1e6,
+                               "step": "stats reset + forward + backward (composite + SH) + vertex scatter"}
     out["prune_guards"] = {"ms_loss_and_prune": ms_plain, "ms_loss_and_prune_with_guards": ms_guard,
                            "overhead_ms": ms_guard - ms_plain,
                            "guards": "keep-halo (size + edge), annealed relaxed q_b, running percentiles"}

@@ -69,7 +69,13 @@ typedef enum { LV_F32 = 0, LV_F16 = 1, LV_BF16 = 2 } lv_dtype;
  * (Eq. 2-4).  Forward and backward of one step must use the same flags. */
 #define LV_FLAG_EXACT_SEGMENT 2u
 
-/* Voxel set (all device pointers). density_dtype: LV_F32 or LV_F16; sh_dtype: LV_F32 or LV_BF16. */
+/* Voxel set (all device pointers). density_dtype: LV_F32 or LV_F16; sh_dtype: LV_F32 or LV_BF16.
+ * density is [n][8] corner densities (corner c = x + 2y + 4z), or, when vidx
+ * is given, the shared grid-vertex variant: density is a vertex array and
+ * corner c of voxel v reads density[vidx[8 v + c]] (see lv_build_vertex_index;
+ * the rasterizer's d_density output stays per voxel corner [n][8], turned into
+ * the vertex gradient by lv_vertex_scatter_add).  Subdivision needs per-voxel
+ * corners (vidx NULL). */
 typedef struct {
   int64_t n;
   const float* geom;
@@ -79,6 +85,7 @@ typedef struct {
   const void* sh;
   int32_t sh_dtype;
   int32_t sh_degree; /* 0..3; coefficients beyond (degree+1)^2 are ignored */
+  const uint32_t* vidx; /* NULL, or [n][8] vertex ids (16-byte aligned) */
 } lv_voxels;
 
 /* Pinhole camera (host struct, passed by value to the kernels).
@@ -431,6 +438,33 @@ lv_status lv_adam_voxels(int64_t n, void* density, lv_dtype density_dtype, void*
                          const float* d_density, const float* d_sh, float* m_density, float* v_density,
                          float* m_sh, float* v_sh, const lv_adam_params* p, float* tv_loss, void* workspace,
                          size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* shared grid-vertex densities (density-model variant)                */
+/* ------------------------------------------------------------------ */
+
+size_t lv_vertex_index_workspace_size(int64_t n);
+
+/* Corner -> vertex numbering.  Corner c of voxel v lies at centre +- h; its
+ * coordinates in units of `unit` (the finest half-size, e.g. root edge /
+ * 2^(l_max + 1)) must be integers in [-2^20, 2^20), else the status word gets
+ * LV_ERR_INVALID_ARG.  Corners at the same point share a vertex; vertex ids
+ * are the ranks of the distinct points in (z, y, x) key order, so they do not
+ * depend on scheduling.  vidx: device [n][8] u32 (written); d_n_vert: device
+ * int64 (the vertex count). */
+lv_status lv_build_vertex_index(const float* geom, int64_t n, double unit, uint32_t* vidx, int64_t* d_n_vert,
+                                void* workspace, size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* corners[8 v + c] = vertex_values[vidx[8 v + c]] as FP32 (dtype LV_F32 or LV_F16). */
+lv_status lv_vertex_gather(const uint32_t* vidx, int64_t n, const void* vertex_values, lv_dtype dtype,
+                           float* corners, void* stream);
+
+/* vertex_sum[vidx[8 v + c]] += corners[8 v + c] (atomics across the voxels
+ * that share a vertex), and vertex_count[...] += 1 when vertex_count is given
+ * (for averaging per-voxel corners into vertices).  Both device FP32 arrays
+ * of the vertex count, accumulated (the caller zeroes them). */
+lv_status lv_vertex_scatter_add(const uint32_t* vidx, int64_t n, const float* corners, float* vertex_sum,
+                                float* vertex_count, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* misc                                                                 */

@@ -702,6 +702,7 @@ static lv_status check_sub(const lv_voxels* in, const lv_subdiv_params* p, int n
   const int64_t n = in->n;
   if (n < 0 || n > 0x7fffffffLL) { set_error("bad voxel count"); return LV_ERR_INVALID_ARG; }
   if (n > 0 && (!in->geom || !in->level || !in->density || !in->sh)) { set_error("null voxel array"); return LV_ERR_INVALID_ARG; }
+  if (in->vidx) { set_error("subdivision needs per-voxel corner densities (vidx must be NULL)"); return LV_ERR_UNSUPPORTED; }
   if (in->density_dtype != LV_F32 && in->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
   if (in->sh_dtype != LV_F32 && in->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
   if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||

@@ -169,7 +169,8 @@ __device__ __forceinline__ int64_t rs_count(const unsigned long long* d_count, i
   return c <= (unsigned long long)cap ? (int64_t)c : 0;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* keys, const unsigned long long* d_count,
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const K* keys, const unsigned long long* d_count,
                                                           int64_t cap, int shift, uint32_t* hist) {
   __shared__ uint32_t sh[RS_WARPS][RADIX];
   const int warp = threadIdx.x >> 5;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* keys,
   int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   for (int64_t i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
-    uint32_t d = (keys[i] >> shift) & (RADIX - 1);
+    uint32_t d = (uint32_t)(keys[i] >> shift) & (RADIX - 1);
     atomicAdd(&sh[warp][d], 1u);
   }
   __syncthreads();
@@ -222,8 +223,9 @@ __global__ void __launch_bounds__(SORT_BLOCKS) k_rs_scan_digits(uint32_t* hist, 
   if (t == SORT_BLOCKS - 1) digit_tot[blockIdx.x] = sw[NW - 1];
 }
 
-__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* kin, const uint32_t* vin,
-                                                            uint32_t* kout, uint32_t* vout,
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const K* kin, const uint32_t* vin,
+                                                            K* kout, uint32_t* vout,
                                                             const unsigned long long* d_count, int64_t cap,
                                                             int shift, const uint32_t* hist,
                                                             const uint32_t* digit_tot) {
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* 
   __shared__ uint32_t s_wh[RS_WARPS][RADIX];  // per-warp digit counts -> warp prefixes
   __shared__ uint32_t s_cnt[RADIX];           // sub-tile digit counts
   __shared__ uint32_t s_start[RADIX];         // sub-tile digit start offsets
-  __shared__ uint32_t s_k[RS_TILE];
+  __shared__ K s_k[RS_TILE];
   __shared__ uint32_t s_v[RS_TILE];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -257,15 +259,16 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* 
   for (int64_t base = lo; base < hi; base += RS_TILE) {
     for (int i = t; i < RS_WARPS * RADIX; i += RS_THREADS) (&s_wh[0][0])[i] = 0;
     __syncthreads();
-    uint32_t k[RS_ITEMS], v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
+    K k[RS_ITEMS];
+    uint32_t v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
     const int64_t wbase = base + (int64_t)warp * (32 * RS_ITEMS);
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
       int64_t i = wbase + j * 32 + lane;
       bool ok = i < hi;
-      k[j] = ok ? kin[i] : 0u;
+      k[j] = ok ? kin[i] : (K)0;
       v[j] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;  // no values: the item's position
-      dg[j] = ok ? ((k[j] >> shift) & (RADIX - 1)) : RADIX;
+      dg[j] = ok ? ((uint32_t)(k[j] >> shift) & (RADIX - 1)) : RADIX;
     }
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
@@ -317,8 +320,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* 
     __syncthreads();
     int m = (int)min((int64_t)RS_TILE, hi - base);
     for (int q = t; q < m; q += RS_THREADS) {
-      uint32_t kk = s_k[q];
-      uint32_t d = (kk >> shift) & (RADIX - 1);
+      const K kk = s_k[q];
+      uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
       uint32_t g = s_goff[d] + (uint32_t)q - s_start[d];
       kout[g] = kk;
       vout[g] = s_v[q];
@@ -334,25 +337,37 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const uint32_t* 
 size_t sort_hist_bytes() { return sizeof(uint32_t) * (RADIX * SORT_BLOCKS + RADIX); }
 int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 
-int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     cudaStream_t s) {
+template <typename K>
+static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t* hist,
+                        const unsigned long long* d_count, int64_t cap, int end_bit, cudaStream_t s) {
   const int passes = sort_passes(end_bit);
-  uint32_t* kb[2] = {k0, k1};
+  K* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
   uint32_t* digit_tot = hist + RADIX * SORT_BLOCKS;
   for (int p = 0; p < passes; ++p) {
     // pass 0 reads the input (kept intact unless it is k0 / v0), pass p writes buffer (p + 1) & 1
-    const uint32_t* ks = p == 0 ? kin : kb[p & 1];
+    const K* ks = p == 0 ? kin : kb[p & 1];
     const uint32_t* vs = p == 0 ? vin : vb[p & 1];
     const int dst = (p + 1) & 1;
-    k_rs_upsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, d_count, cap, 8 * p, hist);
+    k_rs_upsweep<K><<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, d_count, cap, 8 * p, hist);
     k_rs_scan_digits<<<RADIX, SORT_BLOCKS, 0, s>>>(hist, digit_tot);
-    k_rs_downsweep<<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, 8 * p, hist,
-                                                      digit_tot);
+    k_rs_downsweep<K><<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, 8 * p, hist,
+                                                         digit_tot);
   }
   count_launch(3 * passes);
   return passes & 1;
+}
+
+int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     cudaStream_t s) {
+  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, hist, d_count, cap, end_bit, s);
+}
+
+int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
+                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     cudaStream_t s) {
+  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, hist, d_count, cap, end_bit, s);
 }
 
 // ============================================================ grouped select

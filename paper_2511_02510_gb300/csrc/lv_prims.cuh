@@ -30,6 +30,10 @@ int sort_passes(int end_bit);
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                      uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
                      cudaStream_t s);
+// the same with 64-bit keys (end_bit up to 64)
+int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
+                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     cudaStream_t s);
 
 // ---------------------------------------------------------------- grouped select
 // For each query q (group g_q, 1-based rank k_q), find the k-th smallest

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const uint32_t* __restrict__ dkey,
                                               const uint32_t* __restrict__ slot, float4* __restrict__ rec,
                                               float4* __restrict__ d_rgb, uint4* __restrict__ s_tiles,
-                                              uint32_t* __restrict__ s_dkey) {
+                                              uint32_t* __restrict__ s_dkey, const uint32_t* __restrict__ vidx) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * vs.n) return;
   if (!vis[i]) return;
@@ -364,8 +364,14 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   float raw[3];
   sh_raw(coef, 1, sh_nb, Y, raw);
   float d[8];
+  if (vidx) {  // shared grid-vertex densities
+    const uint4 i0 = *(const uint4*)(vidx + 8 * vox), i1 = *(const uint4*)(vidx + 8 * vox + 4);
+    d[0] = to_f32(dens[i0.x]); d[1] = to_f32(dens[i0.y]); d[2] = to_f32(dens[i0.z]); d[3] = to_f32(dens[i0.w]);
+    d[4] = to_f32(dens[i1.x]); d[5] = to_f32(dens[i1.y]); d[6] = to_f32(dens[i1.z]); d[7] = to_f32(dens[i1.w]);
+  } else {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * vox + k]);
+    for (int k = 0; k < 8; ++k) d[k] = to_f32(dens[8 * vox + k]);
+  }
   float4* r = rec + 4 * (int64_t)s;
   r[0] = make_float4(rx, ry, rz, g.w);
   r[1] = make_float4(d[0], d[1], d[2], d[3]);
@@ -1039,7 +1045,8 @@ __global__ void k_render_f64(const __grid_constant__ ViewSet vs, const uint32_t*
                              const uint32_t* __restrict__ svals, const uint32_t* __restrict__ slot_vox,
                              const float4* __restrict__ geom, const DT* __restrict__ dens, const ST* __restrict__ sh,
                              int sh_nb, const int64_t* __restrict__ pixels, int64_t n_px, double t_stop,
-                             int segment, double* __restrict__ rgb_out, double* __restrict__ T_out) {
+                             int segment, const uint32_t* __restrict__ vidx, double* __restrict__ rgb_out,
+                             double* __restrict__ T_out) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n_px) return;
   const long long gp = pixels[q];
@@ -1093,7 +1100,8 @@ __global__ void k_render_f64(const __grid_constant__ ViewSet vs, const uint32_t*
       for (int i = 0; i < 8; ++i) {
         const double w =
             ((i & 1) ? u[0] : 1.0 - u[0]) * ((i & 2) ? u[1] : 1.0 - u[1]) * ((i & 4) ? u[2] : 1.0 - u[2]);
-        sr += ws3[q3] * w * (double)to_f32(dens[8 * (size_t)vox + i]);
+        const size_t di = vidx ? (size_t)vidx[8 * (size_t)vox + i] : 8 * (size_t)vox + i;
+        sr += ws3[q3] * w * (double)to_f32(dens[di]);
       }
     }
     const double sigma = fmax(sr, 0.0);
@@ -1128,6 +1136,7 @@ static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int n
   if (vox->density_dtype != LV_F32 && vox->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
   if (vox->sh_dtype != LV_F32 && vox->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
   if (vox->sh_degree < 0 || vox->sh_degree > 3) { set_error("sh_degree must be 0..3"); return LV_ERR_INVALID_ARG; }
+  if (vox->vidx && ((uintptr_t)vox->vidx & 15)) { set_error("vidx must be 16-byte aligned"); return LV_ERR_INVALID_ARG; }
   if (o->tile != 8 && o->tile != 16 && o->tile != 32) { set_error("tile must be 8, 16 or 32"); return LV_ERR_INVALID_ARG; }
   if (o->batch != 64 && o->batch != 128 && o->batch != 256) { set_error("batch must be 64, 128 or 256"); return LV_ERR_INVALID_ARG; }
   if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) { set_error("t_stop must be in [0, 1)"); return LV_ERR_INVALID_ARG; }
@@ -1254,7 +1263,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
 #define LV_EMIT(DT, ST)                                                                                               \
   k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
                                         vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey, w.slot,      \
-                                        w.rec, w.d_rgb, w.s_tiles, w.s_dkey)
+                                        w.rec, w.d_rgb, w.s_tiles, w.s_dkey, vox->vidx)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
@@ -1411,7 +1420,7 @@ extern "C" lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera*
   k_render_f64<DT, ST><<<grid, 128, 0, s>>>(vs, w.ranges, sv, w.slot_vox, (const float4*)vox->geom,              \
                                             (const DT*)vox->density, (const ST*)vox->sh, nb, pixels, n_px,       \
                                             (double)opts->t_stop, (opts->flags & LV_FLAG_EXACT_SEGMENT) ? 1 : 0,  \
-                                            rgb, T)
+                                            vox->vidx, rgb, T)
   if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_F64(float, float);
   else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_F64(__half, float);
   else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_F64(float, __nv_bfloat16);

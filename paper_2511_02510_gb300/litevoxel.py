@@ -34,7 +34,8 @@ class LvError(RuntimeError):
 # ------------------------------------------------------------------ structs
 class lv_voxels(C.Structure):
     _fields_ = [("n", C.c_int64), ("geom", C.c_void_p), ("level", C.c_void_p), ("density", C.c_void_p),
-                ("density_dtype", C.c_int32), ("sh", C.c_void_p), ("sh_dtype", C.c_int32), ("sh_degree", C.c_int32)]
+                ("density_dtype", C.c_int32), ("sh", C.c_void_p), ("sh_dtype", C.c_int32), ("sh_degree", C.c_int32),
+                ("vidx", C.c_void_p)]
 
 
 class lv_camera(C.Structure):
@@ -103,6 +104,10 @@ SIGNATURES = {
     "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
     "lv_gather_edge": (C.c_int, [_P, _I64, _P, _I64, _P, _P]),
     "lv_train_workspace_size": (_SZ, []),
+    "lv_vertex_index_workspace_size": (_SZ, [_I64]),
+    "lv_build_vertex_index": (C.c_int, [_P, _I64, C.c_double, _P, _P, _P, _SZ, _P, _P]),
+    "lv_vertex_gather": (C.c_int, [_P, _I64, _P, C.c_int, _P, _P]),
+    "lv_vertex_scatter_add": (C.c_int, [_P, _I64, _P, _P, _P, _P]),
     "lv_transmittance_loss": (C.c_int, [_P, _I64, _F, _P, _P, C.c_int, _P, _SZ, _P]),
     "lv_adam_voxels": (C.c_int, [_I64, _P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P,
                                  C.POINTER(lv_adam_params), _P, _P, _SZ, _P]),
@@ -178,8 +183,10 @@ def _stream():
 _DT = {torch.float32: LV_F32, torch.float16: LV_F16, torch.bfloat16: LV_BF16}
 
 
-def make_voxels(geom, density, sh, level=None, sh_degree=3) -> lv_voxels:
+def make_voxels(geom, density, sh, level=None, sh_degree=3, vidx=None) -> lv_voxels:
+    """vidx (int32 [n, 8]) selects the shared grid-vertex variant: density is then the vertex array."""
     v = lv_voxels()
+    v.vidx = _ptr(vidx)
     v.n = int(geom.shape[0])
     v.geom = _ptr(geom)
     v.level = _ptr(level)
@@ -258,6 +265,24 @@ def lv_unpack_wmax(packed, w_max, argmax=None):
 def lv_gather_edge(argmax, edge_map, edge):
     _check(load().lv_gather_edge(_ptr(argmax), int(argmax.numel()), _ptr(edge_map), int(edge_map.numel()),
                                  _ptr(edge), _stream()), "lv_gather_edge")
+
+
+def lv_build_vertex_index(geom, unit, vidx, n_vert, d_status=None):
+    """Vertex ids [n, 8] (int32 tensor, written) and the vertex count (int64 device tensor)."""
+    n = int(geom.shape[0])
+    ws = torch.empty(max(int(load().lv_vertex_index_workspace_size(n)), 256), dtype=torch.uint8, device=geom.device)
+    _check(load().lv_build_vertex_index(_ptr(geom), n, float(unit), _ptr(vidx), _ptr(n_vert), _ptr(ws),
+                                        ws.numel(), _ptr(d_status), _stream()), "lv_build_vertex_index")
+
+
+def lv_vertex_gather(vidx, vertex_values, corners):
+    _check(load().lv_vertex_gather(_ptr(vidx), int(vidx.shape[0]), _ptr(vertex_values), _DT[vertex_values.dtype],
+                                   _ptr(corners), _stream()), "lv_vertex_gather")
+
+
+def lv_vertex_scatter_add(vidx, corners, vertex_sum, vertex_count=None):
+    _check(load().lv_vertex_scatter_add(_ptr(vidx), int(vidx.shape[0]), _ptr(corners), _ptr(vertex_sum),
+                                        _ptr(vertex_count), _stream()), "lv_vertex_scatter_add")
 
 
 def lv_train_workspace_size():
