@@ -439,6 +439,13 @@ lv_status lv_adam_voxels(int64_t n, void* density, lv_dtype density_dtype, void*
                          float* m_sh, float* v_sh, const lv_adam_params* p, float* tv_loss, void* workspace,
                          size_t ws_bytes, void* stream);
 
+/* One Adam step (as lv_adam_voxels, learning rate lr; p->lr_* and
+ * p->tv_weight unused) on a flat parameter array of `count` elements, in
+ * place: e.g. the vertex densities of the shared grid-vertex variant.
+ * param: device F32 / F16 / BF16; grad, m, v: device FP32, 16-byte aligned. */
+lv_status lv_adam_array(int64_t count, void* param, lv_dtype dtype, const float* grad, float* m, float* v, float lr,
+                        const lv_adam_params* p, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* shared grid-vertex densities (density-model variant)                */
 /* ------------------------------------------------------------------ */

@@ -167,6 +167,19 @@ __global__ void __launch_bounds__(TPB) k_adam_flat<float>(int64_t n4, float* __r
   }
 }
 
+// the count % 4 elements after the last whole float4
+template <typename ST>
+__global__ void k_adam_tail(int64_t first, int64_t count, ST* __restrict__ p, const float* __restrict__ grad,
+                            float* __restrict__ m, float* __restrict__ v, const AdamK k) {
+  const int64_t i = first + threadIdx.x;
+  if (i < count) {
+    float mm = m[i], vv = v[i];
+    store_f(p + i, adam1(to_f32(p[i]), grad[i], mm, vv, k));
+    m[i] = mm;
+    v[i] = vv;
+  }
+}
+
 AdamK make_adam(float lr, const lv_adam_params* p) {
   AdamK k;
   k.lr = lr;
@@ -252,4 +265,34 @@ extern "C" lv_status lv_adam_voxels(int64_t n, void* density, lv_dtype density_d
     count_launch(1);
   }
   return cuda_check(cudaGetLastError(), "lv_adam_voxels");
+}
+
+extern "C" lv_status lv_adam_array(int64_t count, void* param, lv_dtype dtype, const float* grad, float* m, float* v,
+                                   float lr, const lv_adam_params* p, void* stream) {
+  if (!p || count < 0 || (count > 0 && (!param || !grad || !m || !v))) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (p->step < 1 || !(p->beta1 >= 0.f && p->beta1 < 1.f) || !(p->beta2 >= 0.f && p->beta2 < 1.f) ||
+      !(p->eps >= 0.f)) { set_error("bad Adam parameters"); return LV_ERR_INVALID_ARG; }
+  if (dtype != LV_F32 && dtype != LV_F16 && dtype != LV_BF16) { set_error("bad dtype"); return LV_ERR_INVALID_ARG; }
+  if (!aligned16(grad) || !aligned16(m) || !aligned16(v) || (dtype == LV_F32 && !aligned16(param))) {
+    set_error("gradient, moments and FP32 parameters must be 16-byte aligned"); return LV_ERR_INVALID_ARG;
+  }
+  if (count == 0) return LV_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const AdamK k = make_adam(lr, p);
+  const int64_t n4 = count / 4, first = 4 * n4;
+  if (dtype == LV_F32) {
+    if (n4) k_adam_flat<float><<<grid_for(n4), TPB, 0, s>>>(n4, (float*)param, (const float4*)grad, (float4*)m,
+                                                           (float4*)v, k);
+    if (first < count) k_adam_tail<float><<<1, 32, 0, s>>>(first, count, (float*)param, grad, m, v, k);
+  } else if (dtype == LV_F16) {
+    if (n4) k_adam_flat<__half><<<grid_for(n4), TPB, 0, s>>>(n4, (__half*)param, (const float4*)grad, (float4*)m,
+                                                            (float4*)v, k);
+    if (first < count) k_adam_tail<__half><<<1, 32, 0, s>>>(first, count, (__half*)param, grad, m, v, k);
+  } else {
+    if (n4) k_adam_flat<__nv_bfloat16><<<grid_for(n4), TPB, 0, s>>>(n4, (__nv_bfloat16*)param, (const float4*)grad,
+                                                                    (float4*)m, (float4*)v, k);
+    if (first < count) k_adam_tail<__nv_bfloat16><<<1, 32, 0, s>>>(first, count, (__nv_bfloat16*)param, grad, m, v, k);
+  }
+  count_launch(2);
+  return cuda_check(cudaGetLastError(), "lv_adam_array");
 }

@@ -104,6 +104,7 @@ SIGNATURES = {
     "lv_unpack_wmax": (C.c_int, [_P, _I64, _P, _P, _P]),
     "lv_gather_edge": (C.c_int, [_P, _I64, _P, _I64, _P, _P]),
     "lv_train_workspace_size": (_SZ, []),
+    "lv_adam_array": (C.c_int, [_I64, _P, C.c_int, _P, _P, _P, _F, C.POINTER(lv_adam_params), _P]),
     "lv_vertex_index_workspace_size": (_SZ, [_I64]),
     "lv_build_vertex_index": (C.c_int, [_P, _I64, C.c_double, _P, _P, _P, _SZ, _P, _P]),
     "lv_vertex_gather": (C.c_int, [_P, _I64, _P, C.c_int, _P, _P]),
@@ -265,6 +266,11 @@ def lv_unpack_wmax(packed, w_max, argmax=None):
 def lv_gather_edge(argmax, edge_map, edge):
     _check(load().lv_gather_edge(_ptr(argmax), int(argmax.numel()), _ptr(edge_map), int(edge_map.numel()),
                                  _ptr(edge), _stream()), "lv_gather_edge")
+
+
+def lv_adam_array(param, grad, m, v, lr, params):
+    _check(load().lv_adam_array(int(param.numel()), _ptr(param), _DT[param.dtype], _ptr(grad), _ptr(m), _ptr(v),
+                                float(lr), C.byref(params), _stream()), "lv_adam_array")
 
 
 def lv_build_vertex_index(geom, unit, vidx, n_vert, d_status=None):

@@ -172,3 +172,27 @@ def test_training_iterations_reduce_the_loss():
     ctx.check()
     assert hist[-1] < 0.95 * hist[0], hist
     assert sum(b < a for a, b in zip(hist, hist[1:])) >= 25        # decreasing almost every iteration
+
+
+@pytest.mark.parametrize("count,dtype", [(1, torch.float32), (1003, torch.float32), (4096, torch.float16),
+                                         (777, torch.bfloat16)])
+def test_adam_array(count, dtype):
+    rng = np.random.default_rng(count)
+    p0 = rng.normal(size=count).astype(np.float32)
+    g = (rng.normal(size=count) * 1e-2).astype(np.float32)
+    m = (rng.normal(size=count) * 1e-3).astype(np.float32)
+    v = (np.abs(rng.normal(size=count)) * 1e-5).astype(np.float32)
+    pt, mt, vt = cu(p0, dtype), cu(m), cu(v)
+    L.lv_adam_array(pt, cu(g), mt, vt, 0.01, params(4, 0.0))
+    torch.cuda.synchronize()
+    base = torch.as_tensor(p0).to(dtype).float().numpy()
+    r, rm, rv = TA.adam(base, g, m, v, F(0.01), B1, B2, EPS, 4)
+    np.testing.assert_allclose(np_(mt), rm, rtol=1e-6, atol=4 * np.spacing(np.float32(np.abs(rm).max())))
+    np.testing.assert_allclose(np_(vt), rv, rtol=1e-6, atol=4 * np.spacing(np.float32(np.abs(rv).max())))
+    if dtype == torch.float32:
+        np.testing.assert_allclose(np_(pt), r, rtol=1e-6, atol=2e-6 * 0.01)
+    else:
+        bits = {torch.float16: torch.int16, torch.bfloat16: torch.int16}[dtype]
+        got = pt.cpu().view(bits).numpy().astype(np.int32)
+        want = torch.as_tensor(r.astype(np.float32)).to(dtype).view(bits).numpy().astype(np.int32)
+        assert np.abs(got - want).max() <= 1
