@@ -46,7 +46,6 @@ struct PruneState {
   uint32_t c_lt;          // candidates strictly below the cap threshold
   uint32_t c_eq;          // candidates at the cap threshold
   uint32_t all;           // 1 when every candidate is pruned (n_cand <= cap)
-  uint32_t all_ties;      // 1 when every candidate at the threshold is pruned
   float p_lo, p_hi;       // depth normalisation of this step (Eq. 14, running or not)
   uint32_t bin_cnt[SELECT_MAX_QUERIES];
 };
@@ -58,6 +57,7 @@ struct PruneWs {
   uint16_t* grp;
   uint32_t* zkey;
   uint32_t* wkey;
+  uint32_t* blk;  // per-block tie counts -> offsets
   size_t bytes;
 };
 
@@ -70,6 +70,7 @@ PruneWs carve_prune(void* base, int64_t n) {
   w.grp = c.take<uint16_t>(n);
   w.zkey = c.take<uint32_t>(n);
   w.wkey = c.take<uint32_t>(n);
+  w.blk = c.take<uint32_t>(n / TPB + 1);
   w.bytes = c.off + 256;
   return w;
 }
@@ -209,48 +210,44 @@ __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
   }
 }
 
-// candidates strictly below the threshold; the ties at it compete by id
-__global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr, uint16_t* cand_grp,
-                          PruneState* st) {
+// candidates strictly below the threshold, and per block the candidates at it
+// (the ties compete by id: the need = cap - c_lt smallest ids among them go)
+__global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
+                          const uint8_t* __restrict__ cand, uint32_t* blk, PruneState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool lt = false, eq = false;
-  if (i < n && cand_grp[i] == 0 && thr[0].k != 0) {
+  if (i < n && cand[i] && thr[0].k != 0) {
     const uint32_t v = thr[0].result;
     lt = wkey[i] < v;
     eq = wkey[i] == v;
-    cand_grp[i] = eq ? 0 : GROUP_NONE;
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const int bl = __syncthreads_count(lt);
   const int be = __syncthreads_count(eq);
-  if (threadIdx.x == 0 && bl) atomicAdd(&st->c_lt, (unsigned)bl);
-  if (threadIdx.x == 0 && be) atomicAdd(&st->c_eq, (unsigned)be);
-}
-
-// need = cap - c_lt ties are pruned; when that is all of them no id selection is needed
-__global__ void k_pr_tie_query(SelectQuery* q, const SelectQuery* thr, PruneState* st, uint32_t cap) {
   if (threadIdx.x == 0) {
-    const uint32_t need = (thr[0].k != 0 && cap > st->c_lt) ? cap - st->c_lt : 0u;
-    st->all_ties = (need != 0 && need == st->c_eq) ? 1u : 0u;
-    q[0].group = 0;
-    q[0].k = st->all_ties ? 0u : need;
+    if (bl) atomicAdd(&st->c_lt, (unsigned)bl);
+    blk[blockIdx.x] = (uint32_t)be;
   }
 }
 
-// mask holds the candidate flags on entry and the pruning decision on exit
+// mask holds the candidate flags on entry and the pruning decision on exit;
+// a tie's rank among the ties (in id order) is its block's offset plus its
+// rank inside the block
 __global__ void k_pr_mask(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
-                          const SelectQuery* tie, const PruneState* st, uint8_t* mask, int64_t* n_pruned,
-                          uint32_t cap) {
+                          const uint32_t* __restrict__ blk_off, const PruneState* st, uint8_t* mask,
+                          int64_t* n_pruned, uint32_t cap) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  const bool c = i < n && mask[i];
+  bool lt = false, eq = false;
+  if (c && !st->all && thr[0].k != 0) {
+    const uint32_t v = thr[0].result;
+    lt = wkey[i] < v;
+    eq = wkey[i] == v;
+  }
+  const uint32_t r = block_excl_rank(eq);  // every thread of the block takes part
   if (i < n) {
-    bool p = false;
-    if (mask[i]) {
-      if (st->all) p = true;
-      else if (thr[0].k != 0) {
-        const uint32_t v = thr[0].result;
-        p = wkey[i] < v || (wkey[i] == v && (st->all_ties || (tie[0].k != 0 && (uint32_t)i <= tie[0].result)));
-      }
-    }
+    const uint32_t need = cap > st->c_lt ? cap - st->c_lt : 0u;
+    const bool p = c && (st->all || lt || (eq && blk_off[blockIdx.x] + r < need));
     mask[i] = p ? 1 : 0;
   }
   if (i == 0 && n_pruned) *n_pruned = st->all ? (int64_t)st->n_cand : (int64_t)cap;
@@ -263,7 +260,6 @@ struct SubState {
   uint32_t k;
   uint32_t c_gt;      // eligible voxels with a strictly higher priority than the k-th
   uint32_t c_eq;      // eligible voxels tied with the k-th
-  uint32_t all_ties;  // 1 when every tie is split
   uint32_t fits;      // output capacity suffices
   float p_lo, p_hi;   // depth normalisation of this step (Eq. 14, running or not)
 };
@@ -280,6 +276,7 @@ struct SubWs {
   unsigned long long* surv_pos;
   uint32_t* sel_rank;
   uint32_t* sel_list;  // [k] selected parent ids in id order
+  uint32_t* blk;       // per-block tie counts -> offsets
   unsigned long long* totals;
   void* scan_tmp;
   size_t bytes;
@@ -299,6 +296,7 @@ SubWs carve_sub(void* base, int64_t n) {
   w.surv_pos = c.take<unsigned long long>(n);
   w.sel_rank = c.take<uint32_t>(n);
   w.sel_list = c.take<uint32_t>(n);
+  w.blk = c.take<uint32_t>(n / TPB + 1);
   w.totals = c.take<unsigned long long>(4);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.bytes = c.off + 256;
@@ -378,49 +376,44 @@ __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long
   }
 }
 
-__global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const SelectQuery* thr, uint16_t* grp,
-                          SubState* st) {
+// eligible voxels above the k-th priority, and per block those tied with it
+// (the ties compete by id: the need = k - c_gt smallest ids among them split)
+__global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const SelectQuery* thr,
+                          const uint16_t* __restrict__ grp, uint32_t* blk, SubState* st) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   bool gt = false, eq = false;
-  if (i < n && grp[i] == 0) {
-    if (thr->k != 0) {
-      gt = pkey[i] < thr->result;
-      eq = pkey[i] == thr->result;
-      grp[i] = eq ? 0 : GROUP_NONE;
-    } else {
-      grp[i] = GROUP_NONE;
-    }
+  if (i < n && grp[i] == 0 && thr->k != 0) {
+    gt = pkey[i] < thr->result;
+    eq = pkey[i] == thr->result;
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const int bg = __syncthreads_count(gt);
   const int be = __syncthreads_count(eq);
-  if (threadIdx.x == 0 && bg) atomicAdd(&st->c_gt, (unsigned)bg);
-  if (threadIdx.x == 0 && be) atomicAdd(&st->c_eq, (unsigned)be);
-}
-
-// need = k - c_gt ties are split; when that is all of them no id selection is needed
-__global__ void k_sd_tie_query(SelectQuery* q, SubState* st) {
   if (threadIdx.x == 0) {
-    const uint32_t need = (q[2].k != 0 && st->k > st->c_gt) ? st->k - st->c_gt : 0u;
-    st->all_ties = (need != 0 && need == st->c_eq) ? 1u : 0u;
-    q[3].group = 0;
-    q[3].k = st->all_ties ? 0u : need;
+    if (bg) atomicAdd(&st->c_gt, (unsigned)bg);
+    blk[blockIdx.x] = (uint32_t)be;
   }
 }
 
-__global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
-                            const uint8_t* __restrict__ level, const float4* __restrict__ geom,
-                            const float* __restrict__ delta, const uint32_t* __restrict__ pkey,
-                            const SelectQuery* q, const SubState* st, float kappa, int l_max, uint8_t* selected,
+// grp == 0 marks the eligible voxels (set by the priority kernel); a tie's
+// rank among the ties is its block's offset plus its rank inside the block
+__global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uint16_t* __restrict__ grp,
+                            const uint32_t* __restrict__ pkey, const SelectQuery* q,
+                            const uint32_t* __restrict__ blk_off, const SubState* st, uint8_t* selected,
                             uint32_t* surv, uint32_t* sel) {
   int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i >= n) return;
-  const bool alive = pm ? pm[i] == 0 : true;
-  bool s = false;
-  if (alive && seen[i] && q[2].k != 0 && (int)level[i] < l_max && geom[i].w > __fmul_rn(kappa, delta[i])) {
+  const bool el = i < n && grp[i] == 0 && q[2].k != 0;
+  bool gt = false, eq = false;
+  if (el) {
     const uint32_t v = q[2].result;
-    s = pkey[i] < v || (pkey[i] == v && (st->all_ties || (q[3].k != 0 && (uint32_t)i <= q[3].result)));
+    gt = pkey[i] < v;
+    eq = pkey[i] == v;
   }
+  const uint32_t r = block_excl_rank(eq);  // every thread of the block takes part
+  if (i >= n) return;
+  const uint32_t need = st->k > st->c_gt ? st->k - st->c_gt : 0u;
+  const bool s = gt || (eq && blk_off[blockIdx.x] + r < need);
+  const bool alive = pm ? pm[i] == 0 : true;
   selected[i] = s ? 1 : 0;
   sel[i] = s ? 1u : 0u;
   surv[i] = (alive && !s) ? 1u : 0u;
@@ -680,13 +673,11 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, halo,
                                       prune_mask, cand, w.st);
   SelectQuery* qc = w.q + SELECT_MAX_QUERIES - 2;  // cap threshold
-  SelectQuery* qi = w.q + SELECT_MAX_QUERIES - 1;  // tie id
   k_pr_cap_query<<<1, 32, 0, s>>>(qc, w.st, cap);
   select_kth(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
-  k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, cand, w.st);
-  k_pr_tie_query<<<1, 32, 0, s>>>(qi, qc, w.st, cap);
-  select_kth(nullptr, cand, n, qi, 1, w.sel_tmp, s);
-  k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, qi, w.st, prune_mask, d_n_pruned, cap);
+  k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, prune_mask, w.blk, w.st);
+  scan_block_counts(w.blk, blocks, &w.st->c_eq, s);
+  k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, w.blk, w.st, prune_mask, d_n_pruned, cap);
   count_launch(9);
   return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
 }
@@ -754,11 +745,9 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
                                         p->l_max, w.grp, w.pkey, w.st);
   k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);
   select_kth(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
-  k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.st);
-  k_sd_tie_query<<<1, 32, 0, s>>>(w.q, w.st);
-  select_kth(nullptr, w.grp, n, w.q + 3, 1, w.sel_tmp, s);
-  k_sd_select<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, in->level, (const float4*)in->geom, delta, w.pkey, w.q,
-                                      w.st, p->kappa, p->l_max, selected, w.surv, w.sel);
+  k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.blk, w.st);
+  scan_block_counts(w.blk, blocks, &w.st->c_eq, s);
+  k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
   k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
