@@ -87,43 +87,73 @@ __device__ __forceinline__ void store_f(float* p, float x) { *p = x; }
 __device__ __forceinline__ void store_f(__half* p, float x) { *p = __float2half_rn(x); }
 __device__ __forceinline__ void store_f(__nv_bfloat16* p, float x) { *p = __float2bfloat16_rn(x); }
 
-// One thread per voxel: the 8 corner densities, their gradient plus the L_tv
-// gradient 2 lambda / N sum_{j adjacent} (d_i - d_j), and the Adam update.
+// Two lanes per voxel, one float4 (4 corners, corner c = x + 2y + 4z: lane 0
+// of the pair holds z = 0, lane 1 z = 1) of every array each, so all loads and
+// stores are coalesced 16-byte words.  The L_tv gradient 2 lambda / N sum over
+// adjacent corners (d_i - d_j) takes the x and y neighbours from the lane's own
+// four corners and the z neighbour from the partner lane (one shuffle).
+template <typename DT> struct Quad;
+template <> struct Quad<float> {
+  static __device__ __forceinline__ float4 load(const float* p) { return *(const float4*)p; }
+  static __device__ __forceinline__ void store(float* p, float4 x) { *(float4*)p = x; }
+};
+template <> struct Quad<__half> {
+  static __device__ __forceinline__ float4 load(const __half* p) {
+    const uint2 u = *(const uint2*)p;
+    const float2 a = __half22float2(*(const __half2*)&u.x), b = __half22float2(*(const __half2*)&u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ void store(__half* p, float4 x) {
+    const __half2 a = __floats2half2_rn(x.x, x.y), b = __floats2half2_rn(x.z, x.w);
+    uint2 u;
+    u.x = *(const uint32_t*)&a;
+    u.y = *(const uint32_t*)&b;
+    *(uint2*)p = u;
+  }
+};
+
 template <typename DT>
 __global__ void __launch_bounds__(TPB) k_adam_density(int64_t n, DT* __restrict__ dens,
                                                      const float4* __restrict__ grad, float4* __restrict__ m4,
                                                      float4* __restrict__ v4, const AdamK k, float tv2,
                                                      double* tv_acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = 2 * n;  // float4 words, two per voxel
+  const int64_t stride = (int64_t)gridDim.x * TPB;
   float part = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
-    float d[8], g[8], m[8], v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) d[c] = to_f32(dens[8 * i + c]);
-    const float4 g0 = grad[2 * i], g1 = grad[2 * i + 1];
-    const float4 m0 = m4[2 * i], m1 = m4[2 * i + 1];
-    const float4 v0 = v4[2 * i], v1 = v4[2 * i + 1];
-    g[0] = g0.x; g[1] = g0.y; g[2] = g0.z; g[3] = g0.w; g[4] = g1.x; g[5] = g1.y; g[6] = g1.z; g[7] = g1.w;
-    m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w; m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
-    v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w; v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
-    if (tv2 != 0.f || tv_acc) {
-#pragma unroll
-      for (int b = 1; b < 8; b <<= 1) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c & b) continue;
-          const float diff = d[c] - d[c | b];
-          part += diff * diff;
-          g[c] += tv2 * diff;
-          g[c | b] -= tv2 * diff;
-        }
-      }
+  for (int64_t b = blockIdx.x * (int64_t)TPB + (threadIdx.x & ~31); b < total; b += stride) {  // warp-uniform
+    const int64_t j = b + lane;
+    const bool ok = j < total;  // pairs are whole: total and b are even
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f), g = d, m = d, v = d;
+    if (ok) {
+      d = Quad<DT>::load(dens + 4 * j);
+      g = grad[j];
+      m = m4[j];
+      v = v4[j];
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) store_f(dens + 8 * i + c, adam1(d[c], g[c], m[c], v[c], k));
-    m4[2 * i] = make_float4(m[0], m[1], m[2], m[3]);
-    m4[2 * i + 1] = make_float4(m[4], m[5], m[6], m[7]);
-    v4[2 * i] = make_float4(v[0], v[1], v[2], v[3]);
-    v4[2 * i + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    // the partner's corners at the same (x, y): the z neighbours
+    const float4 o = make_float4(__shfl_xor_sync(FULL, d.x, 1), __shfl_xor_sync(FULL, d.y, 1),
+                                 __shfl_xor_sync(FULL, d.z, 1), __shfl_xor_sync(FULL, d.w, 1));
+    if (ok && (tv2 != 0.f || tv_acc)) {
+      // own corners (x, y) = (0,0) (1,0) (0,1) (1,1): x edges d.x-d.y, d.z-d.w; y edges d.x-d.z, d.y-d.w
+      const float ex0 = d.x - d.y, ex1 = d.z - d.w, ey0 = d.x - d.z, ey1 = d.y - d.w;
+      const float ez0 = d.x - o.x, ez1 = d.y - o.y, ez2 = d.z - o.z, ez3 = d.w - o.w;
+      part += ex0 * ex0 + ex1 * ex1 + ey0 * ey0 + ey1 * ey1;
+      if (!(j & 1)) part += ez0 * ez0 + ez1 * ez1 + ez2 * ez2 + ez3 * ez3;  // each z edge once
+      g.x += tv2 * (ex0 + ey0 + ez0);
+      g.y += tv2 * (-ex0 + ey1 + ez1);
+      g.z += tv2 * (ex1 - ey0 + ez2);
+      g.w += tv2 * (-ex1 - ey1 + ez3);
+    }
+    if (ok) {
+      d.x = adam1(d.x, g.x, m.x, v.x, k);
+      d.y = adam1(d.y, g.y, m.y, v.y, k);
+      d.z = adam1(d.z, g.z, m.z, v.z, k);
+      d.w = adam1(d.w, g.w, m.w, v.w, k);
+      Quad<DT>::store(dens + 4 * j, d);
+      m4[j] = m;
+      v4[j] = v;
+    }
   }
   if (tv_acc) block_add(part, tv_acc);
 }
@@ -154,9 +184,14 @@ __global__ void __launch_bounds__(TPB) k_adam_flat<float>(int64_t n4, float* __r
                                                          const float4* __restrict__ grad, float4* __restrict__ m4,
                                                          float4* __restrict__ v4, const AdamK k) {
   float4* p4 = (float4*)p;
-  for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n4; i += (int64_t)gridDim.x * TPB) {
-    const float4 g = grad[i];
+  const int64_t stride = (int64_t)gridDim.x * TPB;
+  // two independent words per step: more loads in flight
+  for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n4; i += 2 * stride) {
+    const int64_t i2 = i + stride;
+    const bool two = i2 < n4;
+    const float4 g = grad[i], g2 = two ? grad[i2] : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 m = m4[i], v = v4[i], x = p4[i];
+    float4 mb = two ? m4[i2] : g2, vb = two ? v4[i2] : g2, xb = two ? p4[i2] : g2;
     x.x = adam1(x.x, g.x, m.x, v.x, k);
     x.y = adam1(x.y, g.y, m.y, v.y, k);
     x.z = adam1(x.z, g.z, m.z, v.z, k);
@@ -164,6 +199,15 @@ __global__ void __launch_bounds__(TPB) k_adam_flat<float>(int64_t n4, float* __r
     p4[i] = x;
     m4[i] = m;
     v4[i] = v;
+    if (two) {
+      xb.x = adam1(xb.x, g2.x, mb.x, vb.x, k);
+      xb.y = adam1(xb.y, g2.y, mb.y, vb.y, k);
+      xb.z = adam1(xb.z, g2.z, mb.z, vb.z, k);
+      xb.w = adam1(xb.w, g2.w, mb.w, vb.w, k);
+      p4[i2] = xb;
+      m4[i2] = mb;
+      v4[i2] = vb;
+    }
   }
 }
 
@@ -242,10 +286,10 @@ extern "C" lv_status lv_adam_voxels(int64_t n, void* density, lv_dtype density_d
   if (n > 0) {
     const AdamK kd = make_adam(p->lr_density, p);
     if (density_dtype == LV_F32)
-      k_adam_density<float><<<grid_for(n), TPB, 0, s>>>(n, (float*)density, (const float4*)d_density,
+      k_adam_density<float><<<grid_for(2 * n), TPB, 0, s>>>(n, (float*)density, (const float4*)d_density,
                                                         (float4*)m_density, (float4*)v_density, kd, tv2, tv_acc);
     else
-      k_adam_density<__half><<<grid_for(n), TPB, 0, s>>>(n, (__half*)density, (const float4*)d_density,
+      k_adam_density<__half><<<grid_for(2 * n), TPB, 0, s>>>(n, (__half*)density, (const float4*)d_density,
                                                          (float4*)m_density, (float4*)v_density, kd, tv2, tv_acc);
     count_launch(1);
     if (d_sh) {
