@@ -406,18 +406,38 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
   int digit = -1;
   uint32_t newk = 0;
   if (ball) {
+    // lane L's PER digits hold the k-th item: the warp loads them together (PER / 32 each),
+    // scans them and finds the digit by ballot
     const int L = __ffs(ball) - 1;
-    if (lane == L) {
-      uint32_t cum = excl;
-      const uint32_t* h = (const uint32_t*)hrow;
-      for (int i = 0; i < PER; ++i) {
-        const uint32_t c = h[i];
-        if (cum + c >= s.k) { digit = lane * PER + i; newk = s.k - cum; break; }
-        cum += c;
+    const uint32_t base = __shfl_sync(FULL, excl, L);
+    const uint32_t* h = hist + (size_t)j * RADIX + L * PER;
+    constexpr int EPL = PER / 32 > 0 ? PER / 32 : 1;  // digits per lane: 2 (RADIX 2048) or 1 (256: lanes 0-7)
+    uint32_t c[EPL];
+    uint32_t my = 0;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int idx = lane * EPL + e;
+      c[e] = idx < PER ? h[idx] : 0u;
+      my += c[e];
+    }
+    uint32_t inc = my;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const uint32_t b2 = __ballot_sync(FULL, base + inc >= s.k);  // nonzero: the chunk holds the k-th item
+    const int L2 = __ffs(b2) - 1;
+    if (lane == L2) {
+      uint32_t cum = base + inc - my;
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        if (digit < 0 && cum + c[e] >= s.k) { digit = L * PER + lane * EPL + e; newk = s.k - cum; }
+        cum += c[e];
       }
     }
-    digit = __shfl_sync(FULL, digit, L);
-    newk = __shfl_sync(FULL, newk, L);
+    digit = __shfl_sync(FULL, digit, L2);
+    newk = __shfl_sync(FULL, newk, L2);
   }
 #pragma unroll 4
   for (int i = 0; i < PER / 4; ++i) hrow[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -576,13 +596,19 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
 
 namespace {
 __global__ void __launch_bounds__(1024) k_scan_block_counts(uint32_t* cnt, int64_t m, uint32_t* total) {
+  constexpr int IT = 8;  // consecutive entries per thread
   __shared__ uint32_t ws[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint32_t carry = 0;
-  for (int64_t base = 0; base < m; base += 1024) {  // block-uniform
-    const int64_t i = base + t;
-    const uint32_t c = i < m ? cnt[i] : 0u;
-    uint32_t x = c;
+  for (int64_t base = 0; base < m; base += 1024 * IT) {  // block-uniform
+    const int64_t i0 = base + (int64_t)t * IT;
+    uint32_t c[IT], sum = 0;
+#pragma unroll
+    for (int e = 0; e < IT; ++e) {
+      c[e] = i0 + e < m ? cnt[i0 + e] : 0u;
+      sum += c[e];
+    }
+    uint32_t x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(FULL, x, o);
@@ -600,8 +626,12 @@ __global__ void __launch_bounds__(1024) k_scan_block_counts(uint32_t* cnt, int64
       ws[lane] = w;
     }
     __syncthreads();
-    const uint32_t pre = warp ? ws[warp - 1] : 0u;
-    if (i < m) cnt[i] = carry + pre + x - c;
+    uint32_t run = carry + (warp ? ws[warp - 1] : 0u) + x - sum;
+#pragma unroll
+    for (int e = 0; e < IT; ++e) {
+      if (i0 + e < m) cnt[i0 + e] = run;
+      run += c[e];
+    }
     carry += ws[31];
     __syncthreads();
   }
