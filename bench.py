@@ -616,24 +616,57 @@ def run_ours(args, rank, world, local):
     ms_max = max_over_ranks(ms, world, "cuda")
     value = world * wl.npix / (ms_max / 1e3) / 1e6
 
-    # ---- end to end through the API with host buffers: the captured step plus, every step, the
-    # host-to-device copy of the step's ground-truth image from pinned memory and the read-back of
-    # the loss (both inside the graph), then a synchronisation with the host
+    # ---- end to end through the API with host buffers: every step copies its ground-truth image from
+    # pinned host memory to the device and reads its loss back into pinned host memory, and the host
+    # reads every step's loss.  Like a training loop that logs its loss asynchronously, the host reads
+    # step k's loss while step k+1 runs, and step k+1's image uploads (on a copy stream) while step k
+    # computes; two device image buffers and two host loss buffers, one captured graph per pair.
+    gt_bufs = (wl.gt, torch.empty_like(wl.gt))
+    loss_bufs = (wl.loss_host, torch.zeros_like(wl.loss_host).pin_memory())
+
     def e2e_body():
-        wl.gt.copy_(wl.gt_host, non_blocking=True)
         wl.step()
         wl.loss_host.copy_(wl.loss, non_blocking=True)
 
-    e2e_step = CapturedStep(e2e_body)
-    for _ in range(2):
-        e2e_step()
-        torch.cuda.current_stream().synchronize()
+    e2e_graphs = []
+    for buf, lbuf in zip(gt_bufs, loss_bufs):
+        wl.gt, wl.loss_host = buf, lbuf
+        buf.copy_(wl.gt_host)
+        e2e_graphs.append(CapturedStep(e2e_body))
+    wl.gt, wl.loss_host = gt_bufs[0], loss_bufs[0]
+    main_s = torch.cuda.current_stream()
+    copy_s = torch.cuda.Stream()
+    ev_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+    losses = []
+
+    def e2e_run(steps):
+        with torch.cuda.stream(copy_s):
+            gt_bufs[0].copy_(wl.gt_host, non_blocking=True)
+            ev_ready[0].record(copy_s)
+        for k in range(steps):
+            b = k % 2
+            if k + 1 < steps:  # upload the next step's image while this one computes
+                nb = 1 - b
+                with torch.cuda.stream(copy_s):
+                    if k >= 1:
+                        copy_s.wait_event(ev_used[nb])
+                    gt_bufs[nb].copy_(wl.gt_host, non_blocking=True)
+                    ev_ready[nb].record(copy_s)
+            main_s.wait_event(ev_ready[b])
+            e2e_graphs[b]()
+            ev_used[b].record(main_s)
+            if k >= 1:  # the previous step's loss, read while this step runs
+                ev_used[1 - b].synchronize()
+                losses.append(float(loss_bufs[1 - b][0]))
+        ev_used[(steps - 1) % 2].synchronize()
+        losses.append(float(loss_bufs[(steps - 1) % 2][0]))
+        copy_s.synchronize()
+
+    e2e_run(3)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(K):
-        e2e_step()
-        torch.cuda.current_stream().synchronize()
-        _ = float(wl.loss_host[0])
+    e2e_run(K)
     e2e_s = (time.perf_counter() - t0) / K
     e2e_val = world * wl.npix / max_over_ranks(e2e_s, world, "cuda") / 1e6
 
@@ -678,8 +711,10 @@ def run_ours(args, rank, world, local):
                          "stages_ms from K eager steps with an event at every stage boundary",
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(wl.gt_host.numel() * 4),
                        "d2h_bytes_per_step": 4,
-                       "how": "host wall clock of K replays of the captured step with the ground-truth H2D copy "
-                              "and the loss D2H copy inside, each followed by a host synchronisation"},
+                       "how": "host wall clock of K steps through the API: each step's ground-truth image is "
+                              "copied from pinned host memory (on a copy stream, overlapping the previous step) and "
+                              "its loss is copied back to pinned host memory and read by the host while the next "
+                              "step runs"},
                "gpu_launches": int(launches),
                "clocks": clocks,
                "step_counters": cnt}
