@@ -77,6 +77,7 @@ static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64
 }
 
 // ------------------------------------------------------------------ workspace
+// items are (view, voxel) pairs in view-major order: item = view * n + voxel
 struct FwdWs {
   unsigned long long* counters;  // [0] pairs, [1] slots, [2..3] totals of the depth-order scan
   uint32_t* cnt;                 // [items] tiles covered
@@ -172,8 +173,10 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
                                              float* delta_min, uint8_t* seen) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * vs.n) return;
-  int64_t vox = i / vs.n;
-  int view = (int)(i - vox * vs.n);
+  // items are view-major (i = view * n + voxel): a warp's lanes share one view, so the camera
+  // fields are warp-uniform loads, and the statistics' atomics hit distinct voxels
+  const int view = (int)(i / n);
+  const int64_t vox = i - (int64_t)view * n;
   const DevView& c = vs.v[view];
   const int ts = vs.ts;
   float4 g = geom[vox];
@@ -349,8 +352,8 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * vs.n) return;
   if (!vis[i]) return;
-  int64_t vox = i / vs.n;
-  int view = (int)(i - vox * vs.n);
+  const int view = (int)(i / n);  // view-major items
+  const int64_t vox = i - (int64_t)view * n;
   const DevView& c = vs.v[view];
   uint32_t s = slot[i];
   float4 g = geom[vox];
@@ -944,7 +947,7 @@ __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom,
   if (lane < nrows) {
     const int64_t vox = v0 + lane;
     for (int view = 0; view < vs.n; ++view) {
-      const int64_t i = vox * vs.n + view;
+      const int64_t i = (int64_t)view * n + vox;  // view-major items
       if (!vis[i]) continue;
       any_vis = true;
       const DevView& c = vs.v[view];
