@@ -182,6 +182,30 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
   float4 g = geom[vox];
   float qc[3];
   cam_point32(c, g.x, g.y, g.z, qc);
+  dkey[i] = order_key(qc[2]);
+  {
+    // Early out for voxels far outside the view: the circumscribed sphere lies behind the near
+    // plane or beyond a side plane of the frustum of the tile grid (which may reach past the image
+    // edge) widened by 2 pixels, with a relative slack far above FP32 rounding.  Such a voxel's
+    // exact tile rectangle below (1-pixel margin, clamped to the tile grid) is empty, so skipping it
+    // changes no output.
+    const float r = g.w * 1.7320508f;
+    const float rs = r + 1e-4f * (fabsf(qc[0]) + fabsf(qc[1]) + fabsf(qc[2]) + r) + 1e-6f;
+    const float mL = c.cx + 2.f, mR = c.cx - (float)(c.tiles_x * ts) - 2.f;
+    const float mT = c.cy + 2.f, mB = c.cy - (float)(c.tiles_y * ts) - 2.f;
+    const bool out = qc[2] + rs < c.z_near ||
+                     c.fx * qc[0] + mL * qc[2] < -rs * sqrtf(c.fx * c.fx + mL * mL) ||
+                     c.fx * qc[0] + mR * qc[2] > rs * sqrtf(c.fx * c.fx + mR * mR) ||
+                     c.fy * qc[1] + mT * qc[2] < -rs * sqrtf(c.fy * c.fy + mT * mT) ||
+                     c.fy * qc[1] + mB * qc[2] > rs * sqrtf(c.fy * c.fy + mB * mB);
+    if (out) {
+      cnt[i] = 0u;
+      vis[i] = 0u;
+      rect[i] = make_uint2(0u, 0u);
+      pbox[i] = make_uint2(0u, 0u);
+      return;
+    }
+  }
   int n_front = 0;
   float umin = 0.f, umax = 0.f, vmin = 0.f, vmax = 0.f;
   bool first = true;
@@ -242,7 +266,6 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
   vis[i] = count ? 1u : 0u;
   rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
   pbox[i] = make_uint2((uint32_t)px0 | ((uint32_t)px1 << 16), (uint32_t)py0 | ((uint32_t)py1 << 16));
-  dkey[i] = order_key(qc[2]);
   if (count) {
     float zs = fmaxf(qc[2], c.z_near);
     float dl = __fdiv_rn(zs, c.fx);
