@@ -92,6 +92,7 @@ struct FwdWs {
   uint32_t* s_dkey;              // [slots] order key
   uint32_t *sk0, *sv0, *sk1, *sv1;  // [slots] depth sort of the slots (keys, slot ids)
   uint32_t* scnt;                // [slots] tile counts in depth order
+  uint4* st_sorted;              // [slots] s_tiles in depth order
   unsigned long long* poff;      // [slots] first pair of each slot in depth order
   void* scan_tmp;
   float4* rec;                   // [slots][4]
@@ -125,6 +126,7 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   w.sk1 = c.take<uint32_t>(items);
   w.sv1 = c.take<uint32_t>(items);
   w.scnt = c.take<uint32_t>(items);
+  w.st_sorted = c.take<uint4>(items);
   w.poff = c.take<unsigned long long>(items);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.rec = c.take<float4>(items * 4);
@@ -414,12 +416,21 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   s_dkey[s] = dkey[i];
 }
 
-// Tile counts of the slots in depth order (zero past the last slot).
+// The slots' tile rectangles gathered into depth order, and their tile counts
+// (zero past the last slot), so the pair emission reads both sequentially.
 __global__ void k_slot_counts(const uint32_t* __restrict__ sorted_slot, const uint4* __restrict__ s_tiles,
-                              const unsigned long long* __restrict__ n_slots, int64_t items, uint32_t* scnt) {
+                              const unsigned long long* __restrict__ n_slots, int64_t items, uint32_t* scnt,
+                              uint4* __restrict__ st_sorted) {
   const int64_t ns = (int64_t)*n_slots;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < items; r += (int64_t)gridDim.x * blockDim.x)
-    scnt[r] = r < ns ? s_tiles[sorted_slot[r]].w : 0u;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < items; r += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c = 0u;
+    if (r < ns) {
+      const uint4 t = s_tiles[sorted_slot[r]];
+      st_sorted[r] = t;
+      c = t.w;
+    }
+    scnt[r] = c;
+  }
 }
 
 // The (tile, slot) pairs of every slot, written in depth order so that the
@@ -454,7 +465,7 @@ __device__ __forceinline__ int64_t warp_find_slot(const unsigned long long* __re
 
 __global__ void __launch_bounds__(EP_WARPS * 32) k_emit_pairs(const __grid_constant__ ViewSet vs,
                                                             const uint32_t* __restrict__ sorted_slot,
-                                                            const uint4* __restrict__ s_tiles,
+                                                            const uint4* __restrict__ st_sorted,
                                                             const unsigned long long* __restrict__ poff,
                                                             const unsigned long long* __restrict__ counters,
                                                             int64_t pair_cap, uint32_t* __restrict__ keys,
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(EP_WARPS * 32) k_emit_pairs(const __grid_const
       unsigned long long st = ~0ull;
       if (r < ns) {
         const uint32_t sl = sorted_slot[r];
-        const uint4 t = s_tiles[sl];
+        const uint4 t = st_sorted[r];
         const DevView& c = vs.v[t.z];
         st = poff[r];
         w_rect[warp][lane] = make_uint4(t.x, t.y, (uint32_t)c.tile_off, (uint32_t)c.tiles_x);
@@ -1302,10 +1313,10 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     const uint32_t* sorted_slot = ws_ ? w.sv1 : w.sv0;
     // 2) pair offsets in that order, then the pairs themselves
     const int gb = (int)std::min<int64_t>((items + 255) / 256, 4 * 1216);
-    k_slot_counts<<<gb, 256, 0, s>>>(sorted_slot, w.s_tiles, w.counters + 1, items, w.scnt);
+    k_slot_counts<<<gb, 256, 0, s>>>(sorted_slot, w.s_tiles, w.counters + 1, items, w.scnt, w.st_sorted);
     scan2(w.scnt, nullptr, items, w.poff, nullptr, w.counters + 2, w.scan_tmp, s);
-    k_emit_pairs<<<8 * 152, EP_WARPS * 32, 0, s>>>(vs, sorted_slot, w.s_tiles, w.poff, w.counters, pair_capacity,
-                                                  w.k0, w.v0, d_status);
+    k_emit_pairs<<<8 * 152, EP_WARPS * 32, 0, s>>>(vs, sorted_slot, w.st_sorted, w.poff, w.counters,
+                                                  pair_capacity, w.k0, w.v0, d_status);
     count_launch(2);
   }
   // 3) stable sort by tile: each tile's list stays front to back
