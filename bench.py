@@ -395,6 +395,107 @@ def run_reference(args, rank):
           flush=True)
 
 
+def run_stress(torch, synth, steps=50, budget=12_000_000):
+    """The growth-budget stress workload: ~10M voxels, 8 views of 1600x1060, FP16 corners and BF16
+    SH, each step forward + LF loss (gamma ramp 0 -> 1 over the run) + backward + prune + subdivide
+    under the voxel budget, the scene growing in place of the old one (ping-pong buffers)."""
+    from paper_2511_02510_gb300 import litevoxel as L
+    from paper_2511_02510_gb300.raster import RasterContext
+    dev = "cuda"
+    sc = synth.scene_stress()
+    n0 = int(sc["geom"].shape[0])
+    W, H, V = 1600, 1060, 8
+    cams = [synth.orbit_camera(W, H, 60.0, 4.0, 45.0 * i, 15.0) for i in range(V)]
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base_mem = torch.cuda.memory_allocated()
+    cap = budget + 8
+
+    def arrays():
+        return {"geom": torch.empty((cap, 4), device=dev), "level": torch.empty(cap, dtype=torch.uint8, device=dev),
+                "density": torch.empty((cap, 8), dtype=torch.float16, device=dev),
+                "sh": torch.empty((cap, 48), dtype=torch.bfloat16, device=dev),
+                "ema": torch.empty(cap, device=dev), "state": torch.empty(cap, dtype=torch.uint8, device=dev)}
+
+    bufs = [arrays(), arrays()]
+    a = bufs[0]
+    a["geom"][:n0].copy_(torch.as_tensor(sc["geom"]))
+    a["level"][:n0].copy_(torch.as_tensor(sc["level"]))
+    a["density"][:n0].copy_(torch.as_tensor(sc["density"]).half())
+    a["sh"][:n0].copy_(torch.as_tensor(sc["sh"]).bfloat16())
+    a["ema"][:n0].fill_(1.0)
+    a["state"][:n0].fill_(1)
+    del sc
+    ctx = RasterContext(cams, cap)
+    vox0 = L.make_voxels(a["geom"], a["density"], a["sh"], a["level"])
+    vox0.n = n0
+    pairs = ctx.fit_capacity(vox0, headroom=2.0)
+    gt = torch.from_numpy(np.concatenate([synth.smooth_image(W, H, seed=i) for i in range(V)])).to(dev)
+    lp = L.lv_lf_params()
+    lp.eps, lp.gamma_max, lp.t0, lp.t1, lp.pctl_ppm = 1e-3, 1.0, 0.3 * steps, 0.6 * steps, 990000
+    lf_ws = torch.empty(L.lv_lf_workspace_size([W] * V, [H] * V), dtype=torch.uint8, device=dev)
+    loss = torch.zeros(V, device=dev)
+    dL = torch.empty((ctx.n_pix, 3), device=dev)
+    d_dens = torch.empty((cap, 8), device=dev)
+    d_sh = torch.empty((cap, 48), device=dev)
+    w_max = torch.empty(cap, device=dev)
+    pp = L.lv_prune_params()
+    pp.n_bins, pp.q_ppm, pp.ema_alpha, pp.m_low, pp.m_high, pp.cap_ppm = 16, 50000, 0.1, 0.3, 0.7, 10000
+    pp.lo_ppm, pp.hi_ppm = 50000, 950000
+    pws = torch.empty(L.lv_prune_workspace_size(cap, pp), dtype=torch.uint8, device=dev)
+    mask = torch.empty(cap, dtype=torch.uint8, device=dev)
+    npr = torch.zeros(1, dtype=torch.int64, device=dev)
+    sp = L.lv_subdiv_params()
+    sp.kappa, sp.beta, sp.top_ppm, sp.l_max, sp.budget, sp.lo_ppm, sp.hi_ppm = 1.0, 0.2, 50000, 16, budget, 50000, 950000
+    sws = torch.empty(L.lv_subdivide_workspace_size(cap, sp), dtype=torch.uint8, device=dev)
+    sel = torch.empty(cap, dtype=torch.uint8, device=dev)
+    nn = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    n = n0
+    counts = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for it in range(steps):
+        a, b = bufs[it % 2], bufs[1 - it % 2]
+        vox = L.make_voxels(a["geom"], a["density"], a["sh"], a["level"])
+        vox.n = n
+        ctx.reset_stats()
+        ctx.forward(vox)
+        L.lv_lf_weighted_loss(ctx.rgb, gt, [W] * V, [H] * V, float(it), lp, loss, dL, lf_ws)
+        L.lv_rasterize_backward(vox, ctx.cams_arr, ctx.n_views, ctx.opts, ctx.fwd_struct(False), ctx.workspace,
+                                ctx.pair_capacity, dL, None, None, d_dens[:n], d_sh[:n], False, ctx.status)
+        L.lv_unpack_wmax(ctx.wmax_packed[:n], w_max[:n])
+        L.lv_prune_depth_quantile(w_max[:n], ctx.seen[:n], ctx.z_min[:n], a["ema"][:n], a["state"][:n], pp,
+                                  mask[:n], npr, pws)
+        aux = []
+        for key, fill in (("ema", 1.0), ("state", 1)):
+            x = L.lv_aux_array()
+            x.in_, x.out, x.width = a[key].data_ptr(), b[key].data_ptr(), 1
+            x.elem_bytes = a[key].element_size()
+            x.fill = int(np.array([fill], np.float32 if key == "ema" else np.uint8).view(
+                np.uint32 if key == "ema" else np.uint8)[0])
+            aux.append(x)
+        vout = L.make_voxels(b["geom"], b["density"], b["sh"], b["level"])
+        vout.n = cap
+        L.lv_subdivide_priority(vox, ctx.delta_min[:n], ctx.z_min[:n], w_max[:n], ctx.seen[:n], mask[:n], sp, aux,
+                                vout, sel[:n], nn, sws, status)
+        n = int(nn.item())  # the next step's voxel count (one host read per step)
+        counts.append(n)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.check()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"stress: device status {int(status.item())}")
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": ctx.n_pix / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "views": V, "pixels": ctx.n_pix, "voxels_start": n0, "voxels_end": counts[-1],
+            "voxels_max": max(counts), "budget": budget, "pairs_first_step": int(pairs),
+            "peak_vram_gb": (torch.cuda.max_memory_allocated() - base_mem) / 1e9,
+            "step": "forward + LF loss (gamma ramp 0 -> 1) + backward (corners and SH) + prune + subdivide, "
+                    "growing under the budget",
+            "density_dtype": "float16", "sh_dtype": "bfloat16"}
+
+
 def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
     """Batched / mixed-precision / semi-transparent variants measured beside the plain path (same GPU)."""
     from paper_2511_02510_gb300 import litevoxel as L
@@ -723,6 +824,7 @@ def run_ours(args, rank, world, local):
                 out["variants"] = {k: run_variant(torch, synth, k, scene_np)
                                    for k in ("batched16_fp32", "batched8_mixed", "semi_transparent_fp32",
                                              "exact_segment_fp32")}
+                out["variants"]["stress_10M_growth"] = run_stress(torch, synth)
                 out["variants"]["plain_fp32_fwd_bwd_only"] = {
                     "value": wl.npix / ((stage_ms["forward"] + stage_ms["backward"] + stage_ms["sh_backward"] +
                                          stage_ms["reset"]) / 1e3) / 1e6, "unit": UNIT}
