@@ -508,7 +508,7 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
         sc = scene_np
         cams = [synth.orbit_camera(980, 545, 60.0, 3.0, 45.0 * i, 15.0) for i in range(8)]
         dd, sd = torch.float16, torch.bfloat16
-    elif kind == "exact_segment_fp32":  # the plain view with the exact-segment density variant
+    elif kind in ("exact_segment_fp32", "persistent_fp32"):  # the plain view, density variant / scheduling
         sc = scene_np
         cams = [camera_for(0)]
         dd, sd = torch.float32, torch.float32
@@ -517,7 +517,8 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
         cams = [camera_for(0)]
         dd, sd = torch.float32, torch.float32
     scene = Scene.from_numpy(sc, "cuda", dd, sd)
-    ctx = RasterContext(cams, scene.n, exact_segment=(kind == "exact_segment_fp32"))
+    ctx = RasterContext(cams, scene.n, exact_segment=(kind == "exact_segment_fp32"),
+                        persistent=(kind == "persistent_fp32"))
     vox = scene.voxels()
     ctx.fit_capacity(vox)
     g = torch.randn((ctx.n_pix, 3), device="cuda") * 1e-3
@@ -823,7 +824,7 @@ def run_ours(args, rank, world, local):
             try:
                 out["variants"] = {k: run_variant(torch, synth, k, scene_np)
                                    for k in ("batched16_fp32", "batched8_mixed", "semi_transparent_fp32",
-                                             "exact_segment_fp32")}
+                                             "exact_segment_fp32", "persistent_fp32")}
                 out["variants"]["stress_10M_growth"] = run_stress(torch, synth)
                 out["variants"]["plain_fp32_fwd_bwd_only"] = {
                     "value": wl.npix / ((stage_ms["forward"] + stage_ms["backward"] + stage_ms["sh_backward"] +

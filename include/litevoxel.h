@@ -68,6 +68,12 @@ typedef enum { LV_F32 = 0, LV_F16 = 1, LV_BF16 = 2 } lv_dtype;
  * the chord ends and midpoint), sigma = max(0, mean), alpha = 1 - exp(-sigma l)
  * (Eq. 2-4).  Forward and backward of one step must use the same flags. */
 #define LV_FLAG_EXACT_SEGMENT 2u
+/* Scheduling of the composite kernels: persistent warps, as many as are
+ * resident, each taking the next (tile, 4x8-pixel strip) from a global
+ * counter (atomicAdd, no waiting), instead of one block per tile.  Results
+ * are identical either way (per pixel the same arithmetic in the same order;
+ * gradient sums differ only in FP32 atomic order). */
+#define LV_FLAG_PERSISTENT 4u
 
 /* Voxel set (all device pointers). density_dtype: LV_F32 or LV_F16; sh_dtype: LV_F32 or LV_BF16.
  * density is [n][8] corner densities (corner c = x + 2y + 4z), or, when vidx

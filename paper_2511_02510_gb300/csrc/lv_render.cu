@@ -93,6 +93,7 @@ struct FwdWs {
   uint32_t *sk0, *sv0, *sk1, *sv1;  // [slots] depth sort of the slots (keys, slot ids)
   uint32_t* scnt;                // [slots] tile counts in depth order
   uint4* st_sorted;              // [slots] s_tiles in depth order
+  unsigned int* work;            // [2] work-item counters of the persistent composites
   unsigned long long* poff;      // [slots] first pair of each slot in depth order
   void* scan_tmp;
   float4* rec;                   // [slots][4]
@@ -111,6 +112,7 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   int64_t items = n * nv;
   w.counters = c.take<unsigned long long>(8);
   w.status = c.take<int32_t>(4);
+  w.work = c.take<unsigned int>(2);
   w.cnt = c.take<uint32_t>(items);
   w.vis = c.take<uint32_t>(items);
   w.rect = c.take<uint2>(items);
@@ -675,6 +677,17 @@ struct Strip {
   }
 };
 
+// Work items are (tile, warp strip) pairs, item = tile * (TS*TS/32) + strip.
+// Without PERSIST every warp takes the item of its own block and warp index;
+// with PERSIST a grid sized to the resident warps loops, each warp taking the
+// next item from a global counter (one atomicAdd per item, no waiting), so a
+// warp that finishes a cheap strip moves on without waiting for its block.
+__device__ __forceinline__ uint32_t next_item(unsigned int* work, int lane) {
+  uint32_t it = 0;
+  if (lane == 0) it = atomicAdd(work, 1u);
+  return __shfl_sync(FULL, it, 0);
+}
+
 // ------------------------------------------------------------------ forward composite
 // Each warp walks its strip's tile list on its own: 32 list entries at a
 // time, the entries whose pixel box meets the strip are compacted with a
@@ -687,7 +700,7 @@ constexpr size_t BWD_SLICE = 32 * 64 + 32 * 4 * 3;
 template <int TS>
 constexpr int min_blocks() { return TS == 16 ? 5 : (TS == 8 ? 16 : 1); }
 
-template <int TS, bool SEG>
+template <int TS, bool SEG, bool PERSIST>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -695,94 +708,100 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                                 float* __restrict__ rgb, float* __restrict__ depth,
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
                                                 uint32_t* __restrict__ n_samples, float* __restrict__ tau_out,
-                                                unsigned long long* __restrict__ wmax) {
+                                                unsigned long long* __restrict__ wmax, unsigned int* work,
+                                                uint32_t n_items) {
+  constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* wr = (float4*)((char*)smem_f4 + FWD_SLICE * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 128);
   uint32_t* w_ent = w_vox + 32;
-  const int gtile = blockIdx.x;
-  const int view = find_view(vs, gtile);
-  const DevView& c = vs.v[view];
-  const int lt = gtile - c.tile_off;
-  const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
-  const Strip<TS> strip(tile_x, tile_y, warp);
-  const int px = strip.px(lane), py = strip.py(lane);
-  const bool inside = px < c.W && py < c.H;
-  const Ray r = make_ray(c, px, py);
-  const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
-  const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
-  const unsigned long long gid_key = 0xffffffffull - (gid & 0xffffffffull);
-  float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
-  uint32_t last = 0, nsamp = 0;
-  bool done = !inside;
-  for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += 32) {
-    const uint32_t e = base + lane;
-    uint32_t sl = 0;
-    bool ov = false;
-    if (e < end) {
-      sl = svals[e];
-      ov = !strip.misses(rec_bb[sl]);
-    }
-    const uint32_t mask = __ballot_sync(FULL, ov);
-    if (!mask) continue;
-    if (ov) {
-      const int pos = __popc(mask & ((1u << lane) - 1u));
-      const float4* src = rec + 4 * (size_t)sl;
-      wr[4 * pos + 0] = src[0];
-      wr[4 * pos + 1] = src[1];
-      wr[4 * pos + 2] = src[2];
-      wr[4 * pos + 3] = src[3];
-      w_vox[pos] = slot_vox[sl];
-      w_ent[pos] = e;
-    }
-    __syncwarp();
-    const int m = __popc(mask);
-    for (int j = 0; j < m; ++j) {
-      const float4 g = wr[4 * j];
-      float t_in, t_out;
-      const bool hit = !done && chord(r, g, t_in, t_out);
-      float w = 0.f;
-      if (hit) {
-        const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
-        const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-        float u[SEG ? 9 : 3];
-        const float sigma = fmaxf(sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u), 0.f);
-        const float x = sigma * l;
-        const float ex = __expf(-x);
-        const float alpha = one_minus_exp(x, ex);
-        w = T * alpha;
-        cr = fmaf(w, col.x, cr);
-        cg = fmaf(w, col.y, cg);
-        cb = fmaf(w, col.z, cb);
-        dep = fmaf(w, tm, dep);
-        tau += x;
-        T *= ex;
-        last = w_ent[j] - start + 1;
-        ++nsamp;
+  for (uint32_t item = PERSIST ? next_item(work, lane) : blockIdx.x * NW + warp; item < n_items;
+       item = PERSIST ? next_item(work, lane) : n_items) {  // warp-uniform
+    const int gtile = (int)(item / NW);
+    const int view = find_view(vs, gtile);
+    const DevView& c = vs.v[view];
+    const int lt = gtile - c.tile_off;
+    const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
+    const Strip<TS> strip(tile_x, tile_y, (int)(item % NW));
+    const int px = strip.px(lane), py = strip.py(lane);
+    const bool inside = px < c.W && py < c.H;
+    const Ray r = make_ray(c, px, py);
+    const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
+    const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
+    const unsigned long long gid_key = 0xffffffffull - (gid & 0xffffffffull);
+    float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
+    uint32_t last = 0, nsamp = 0;
+    bool done = !inside;
+    for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += 32) {
+      const uint32_t e = base + lane;
+      uint32_t sl = 0;
+      bool ov = false;
+      if (e < end) {
+        sl = svals[e];
+        ov = !strip.misses(rec_bb[sl]);
       }
-      if (__any_sync(FULL, hit)) {
-        // the warp's largest w (ties to the lowest lane = smallest pixel id), one global atomic
-        const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
-        const uint32_t mx = __reduce_max_sync(FULL, v);
-        const uint32_t who = __ballot_sync(FULL, v == mx);
-        if (wmax && lane == __ffs(who) - 1)
-          atomicMax(&wmax[w_vox[j]], ((unsigned long long)(mx - 1u) << 32) | gid_key);
-        if (hit && T < t_stop) done = true;
+      const uint32_t mask = __ballot_sync(FULL, ov);
+      if (!mask) continue;
+      if (ov) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        const float4* src = rec + 4 * (size_t)sl;
+        wr[4 * pos + 0] = src[0];
+        wr[4 * pos + 1] = src[1];
+        wr[4 * pos + 2] = src[2];
+        wr[4 * pos + 3] = src[3];
+        w_vox[pos] = slot_vox[sl];
+        w_ent[pos] = e;
       }
+      __syncwarp();
+      const int m = __popc(mask);
+      for (int j = 0; j < m; ++j) {
+        const float4 g = wr[4 * j];
+        float t_in, t_out;
+        const bool hit = !done && chord(r, g, t_in, t_out);
+        float w = 0.f;
+        if (hit) {
+          const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
+          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+          float u[SEG ? 9 : 3];
+          const float sigma = fmaxf(sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u), 0.f);
+          const float x = sigma * l;
+          const float ex = __expf(-x);
+          const float alpha = one_minus_exp(x, ex);
+          w = T * alpha;
+          cr = fmaf(w, col.x, cr);
+          cg = fmaf(w, col.y, cg);
+          cb = fmaf(w, col.z, cb);
+          dep = fmaf(w, tm, dep);
+          tau += x;
+          T *= ex;
+          last = w_ent[j] - start + 1;
+          ++nsamp;
+        }
+        if (__any_sync(FULL, hit)) {
+          // the warp's largest w (ties to the lowest lane = smallest pixel id), one global atomic
+          const uint32_t v = hit ? __float_as_uint(w) + 1u : 0u;
+          const uint32_t mx = __reduce_max_sync(FULL, v);
+          const uint32_t who = __ballot_sync(FULL, v == mx);
+          if (wmax && lane == __ffs(who) - 1)
+            atomicMax(&wmax[w_vox[j]], ((unsigned long long)(mx - 1u) << 32) | gid_key);
+          if (hit && T < t_stop) done = true;
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-  }
-  if (inside) {
-    const size_t p = (size_t)gid;
-    rgb[3 * p + 0] = cr;
-    rgb[3 * p + 1] = cg;
-    rgb[3 * p + 2] = cb;
-    if (depth) depth[p] = dep;
-    T_out[p] = T;
-    n_contrib[p] = last;
-    if (n_samples) n_samples[p] = nsamp;
-    tau_out[p] = tau;
+    if (inside) {
+      const size_t p = (size_t)gid;
+      rgb[3 * p + 0] = cr;
+      rgb[3 * p + 1] = cg;
+      rgb[3 * p + 2] = cb;
+      if (depth) depth[p] = dep;
+      T_out[p] = T;
+      n_contrib[p] = last;
+      if (n_samples) n_samples[p] = nsamp;
+      tau_out[p] = tau;
+    }
+    __syncwarp();  // the slice is reused by the next item
   }
 }
 
@@ -824,7 +843,7 @@ __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
 // any of its pixels used, in the same 32-entry chunks and with the same
 // compaction as the forward; the per-record gradients (8 corners + colour) are
 // reduced over the warp and sent with three 16-byte global reductions.
-template <int TS, bool SEG>
+template <int TS, bool SEG, bool PERSIST>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -833,124 +852,128 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
                                                 const uint32_t* __restrict__ n_contrib,
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
-                                                float4* __restrict__ d_rgb) {
+                                                float4* __restrict__ d_rgb, unsigned int* work, uint32_t n_items) {
+  constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* wr = (float4*)((char*)smem_f4 + BWD_SLICE * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 128);
   uint32_t* w_slot = w_vox + 32;
   uint32_t* w_ent = w_slot + 32;
-  const int gtile = blockIdx.x;
-  const int view = find_view(vs, gtile);
-  const DevView& c = vs.v[view];
-  const int lt = gtile - c.tile_off;
-  const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
-  const Strip<TS> strip(tile_x, tile_y, warp);
-  const int px = strip.px(lane), py = strip.py(lane);
-  const bool inside = px < c.W && py < c.H;
-  const Ray r = make_ray(c, px, py);
-  const uint32_t start = ranges[2 * gtile];
-  const size_t p = (size_t)(c.pix_off + (long long)py * c.W + px);
-  uint32_t nc = 0;
-  float tau = 0.f, Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gD = 0.f, gT = 0.f;
-  if (inside) {
-    nc = n_contrib[p];
-    tau = tau_in[p];
-    Tf = T_fwd[p];
-    gr = dL_drgb[3 * p + 0];
-    gg = dL_drgb[3 * p + 1];
-    gb = dL_drgb[3 * p + 2];
-    if (dL_ddepth) gD = dL_ddepth[p];
-    if (dL_dT) gT = dL_dT[p];
-  }
-  const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
-  const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
-  const float tgT = Tf * gT;
-  float S = 0.f;
-  float Tcur = __expf(-tau);  // T after the last sample, from the stored optical depth
-  // chunks aligned as in the forward: [start + 32 k, start + 32 k + 32)
-  for (uint32_t cb = start + ((warp_hi - start + 31u) & ~31u); cb > start; cb -= 32) {
-    const uint32_t base = cb - 32;
-    const uint32_t e = base + lane;
-    uint32_t sl = 0;
-    bool ov = false;
-    if (e < warp_hi) {
-      sl = svals[e];
-      ov = !strip.misses(rec_bb[sl]);
+  for (uint32_t item = PERSIST ? next_item(work, lane) : blockIdx.x * NW + warp; item < n_items;
+       item = PERSIST ? next_item(work, lane) : n_items) {  // warp-uniform
+    const int gtile = (int)(item / NW);
+    const int view = find_view(vs, gtile);
+    const DevView& c = vs.v[view];
+    const int lt = gtile - c.tile_off;
+    const int tile_x = lt % c.tiles_x, tile_y = lt / c.tiles_x;
+    const Strip<TS> strip(tile_x, tile_y, (int)(item % NW));
+    const int px = strip.px(lane), py = strip.py(lane);
+    const bool inside = px < c.W && py < c.H;
+    const Ray r = make_ray(c, px, py);
+    const uint32_t start = ranges[2 * gtile];
+    const size_t p = (size_t)(c.pix_off + (long long)py * c.W + px);
+    uint32_t nc = 0;
+    float tau = 0.f, Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f, gD = 0.f, gT = 0.f;
+    if (inside) {
+      nc = n_contrib[p];
+      tau = tau_in[p];
+      Tf = T_fwd[p];
+      gr = dL_drgb[3 * p + 0];
+      gg = dL_drgb[3 * p + 1];
+      gb = dL_drgb[3 * p + 2];
+      if (dL_ddepth) gD = dL_ddepth[p];
+      if (dL_dT) gT = dL_dT[p];
     }
-    const uint32_t mask = __ballot_sync(FULL, ov);
-    if (!mask) continue;
-    if (ov) {
-      const int pos = __popc(mask & ((1u << lane) - 1u));
-      const float4* src = rec + 4 * (size_t)sl;
-      wr[4 * pos + 0] = src[0];
-      wr[4 * pos + 1] = src[1];
-      wr[4 * pos + 2] = src[2];
-      wr[4 * pos + 3] = src[3];
-      w_vox[pos] = slot_vox[sl];
-      w_slot[pos] = sl;
-      w_ent[pos] = e;
-    }
-    __syncwarp();
-    for (int j = __popc(mask) - 1; j >= 0; --j) {
-      const float4 g = wr[4 * j];
-      float t_in, t_out;
-      const bool hit = w_ent[j] < my_hi && chord(r, g, t_in, t_out);
-      const unsigned hb = __ballot_sync(FULL, hit);
-      if (!hb) continue;
-      float v[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = 0.f;
-      if (hit) {
-        const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
-        const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
-        float u[SEG ? 9 : 3];
-        const float sraw = sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u);
-        const float sigma = fmaxf(sraw, 0.f);
-        const float x = sigma * l;
-        const float Tk = Tcur;  // transmittance after this sample: the previous step's T_prev
-        const float tau_prev = fmaxf(tau - x, 0.f);
-        const float T_prev = __expf(-tau_prev);
-        Tcur = T_prev;
-        const float alpha = one_minus_exp(x, __expf(-x));
-        const float w = T_prev * alpha;
-        const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
-        const float ds = l * (Tk * a - S - tgT);
-        S = fmaf(w, a, S);
-        tau = tau_prev;
-        const float dr = sraw > 0.f ? ds : 0.f;
-        corner_weights<false>(v, SEG ? dr * (4.f / 6.f) : dr, u);
-        if constexpr (SEG) {
-          corner_weights<true>(v, dr * (1.f / 6.f), u + 3);
-          corner_weights<true>(v, dr * (1.f / 6.f), u + 6);
-        }
-        v[8] = w * gr;
-        v[9] = w * gg;
-        v[10] = w * gb;
+    const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
+    const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
+    const float tgT = Tf * gT;
+    float S = 0.f;
+    float Tcur = __expf(-tau);  // T after the last sample, from the stored optical depth
+    // chunks aligned as in the forward: [start + 32 k, start + 32 k + 32)
+    for (uint32_t cb = start + ((warp_hi - start + 31u) & ~31u); cb > start; cb -= 32) {
+      const uint32_t base = cb - 32;
+      const uint32_t e = base + lane;
+      uint32_t sl = 0;
+      bool ov = false;
+      if (e < warp_hi) {
+        sl = svals[e];
+        ov = !strip.misses(rec_bb[sl]);
       }
-      float* dd = d_density + 8 * (size_t)w_vox[j];
-      float* dc = (float*)(d_rgb + w_slot[j]);
-      if (__popc(hb) <= 2) {
-        // one or two lanes: each sends its own values, cheaper than the butterfly
+      const uint32_t mask = __ballot_sync(FULL, ov);
+      if (!mask) continue;
+      if (ov) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        const float4* src = rec + 4 * (size_t)sl;
+        wr[4 * pos + 0] = src[0];
+        wr[4 * pos + 1] = src[1];
+        wr[4 * pos + 2] = src[2];
+        wr[4 * pos + 3] = src[3];
+        w_vox[pos] = slot_vox[sl];
+        w_slot[pos] = sl;
+        w_ent[pos] = e;
+      }
+      __syncwarp();
+      for (int j = __popc(mask) - 1; j >= 0; --j) {
+        const float4 g = wr[4 * j];
+        float t_in, t_out;
+        const bool hit = w_ent[j] < my_hi && chord(r, g, t_in, t_out);
+        const unsigned hb = __ballot_sync(FULL, hit);
+        if (!hb) continue;
+        float v[16];
+  #pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
         if (hit) {
-          red_add_v4(dd, v[0], v[1], v[2], v[3]);
-          red_add_v4(dd + 4, v[4], v[5], v[6], v[7]);
-          red_add_v4(dc, v[8], v[9], v[10], 0.f);
+          const float4 d0 = wr[4 * j + 1], d1 = wr[4 * j + 2], col = wr[4 * j + 3];
+          const float l = t_out - t_in, tm = 0.5f * (t_in + t_out);
+          float u[SEG ? 9 : 3];
+          const float sraw = sample_density<SEG>(r, g, d0, d1, col.w, t_in, tm, t_out, u);
+          const float sigma = fmaxf(sraw, 0.f);
+          const float x = sigma * l;
+          const float Tk = Tcur;  // transmittance after this sample: the previous step's T_prev
+          const float tau_prev = fmaxf(tau - x, 0.f);
+          const float T_prev = __expf(-tau_prev);
+          Tcur = T_prev;
+          const float alpha = one_minus_exp(x, __expf(-x));
+          const float w = T_prev * alpha;
+          const float a = fmaf(gr, col.x, fmaf(gg, col.y, fmaf(gb, col.z, gD * tm)));
+          const float ds = l * (Tk * a - S - tgT);
+          S = fmaf(w, a, S);
+          tau = tau_prev;
+          const float dr = sraw > 0.f ? ds : 0.f;
+          corner_weights<false>(v, SEG ? dr * (4.f / 6.f) : dr, u);
+          if constexpr (SEG) {
+            corner_weights<true>(v, dr * (1.f / 6.f), u + 3);
+            corner_weights<true>(v, dr * (1.f / 6.f), u + 6);
+          }
+          v[8] = w * gr;
+          v[9] = w * gg;
+          v[10] = w * gb;
         }
-      } else {
-        const float sum = warp_reduce16(v, lane);  // value (l >> 1) on even lane l
-        // gather four values each into lanes 0 (corners 0-3), 1 (corners 4-7) and 2 (colour)
-        const int src0 = lane == 0 ? 0 : (lane == 1 ? 8 : 16);
-        const float q0 = __shfl_sync(FULL, sum, src0 + 0);
-        const float q1 = __shfl_sync(FULL, sum, src0 + 2);
-        const float q2 = __shfl_sync(FULL, sum, src0 + 4);
-        const float q3 = __shfl_sync(FULL, sum, src0 + 6);
-        if (lane == 0) red_add_v4(dd, q0, q1, q2, q3);
-        else if (lane == 1) red_add_v4(dd + 4, q0, q1, q2, q3);
-        else if (lane == 2) red_add_v4(dc, q0, q1, q2, 0.f);
+        float* dd = d_density + 8 * (size_t)w_vox[j];
+        float* dc = (float*)(d_rgb + w_slot[j]);
+        if (__popc(hb) <= 2) {
+          // one or two lanes: each sends its own values, cheaper than the butterfly
+          if (hit) {
+            red_add_v4(dd, v[0], v[1], v[2], v[3]);
+            red_add_v4(dd + 4, v[4], v[5], v[6], v[7]);
+            red_add_v4(dc, v[8], v[9], v[10], 0.f);
+          }
+        } else {
+          const float sum = warp_reduce16(v, lane);  // value (l >> 1) on even lane l
+          // gather four values each into lanes 0 (corners 0-3), 1 (corners 4-7) and 2 (colour)
+          const int src0 = lane == 0 ? 0 : (lane == 1 ? 8 : 16);
+          const float q0 = __shfl_sync(FULL, sum, src0 + 0);
+          const float q1 = __shfl_sync(FULL, sum, src0 + 2);
+          const float q2 = __shfl_sync(FULL, sum, src0 + 4);
+          const float q3 = __shfl_sync(FULL, sum, src0 + 6);
+          if (lane == 0) red_add_v4(dd, q0, q1, q2, q3);
+          else if (lane == 1) red_add_v4(dd + 4, q0, q1, q2, q3);
+          else if (lane == 2) red_add_v4(dc, q0, q1, q2, 0.f);
+        }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -1205,40 +1228,70 @@ static lv_status finish(lv_status st, uint32_t flags, int32_t* d_status, cudaStr
   return LV_OK;
 }
 
-template <int TS, bool SEG>
+// resident blocks of a persistent composite (once per kernel)
+template <typename K>
+static int persistent_blocks(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
+template <int TS, bool SEG, bool PERSIST>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          float t_stop, const lv_fwd_out* out) {
   const size_t smem = FWD_SLICE * (TS * TS / 32);
+  static int pblocks = 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fwd<TS, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (PERSIST) pblocks = persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
     attr = true;
   }
-  k_fwd<TS, SEG><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
-                                                        out->rgb, out->depth, out->T, out->n_contrib, out->n_samples,
-                                                        w.tau, out->wmax_packed);
+  const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
+  unsigned grid = (unsigned)tiles;
+  if (PERSIST) {
+    cudaMemsetAsync(w.work, 0, sizeof(unsigned int), s);
+    grid = (unsigned)(tiles < pblocks ? tiles : pblocks);
+  }
+  k_fwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
+                                                       out->rgb, out->depth, out->T, out->n_contrib,
+                                                       out->n_samples, w.tau, out->wmax_packed, w.work, n_items);
 }
 
-template <int TS, bool SEG>
+template <int TS, bool SEG, bool PERSIST>
 static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
   const size_t smem = BWD_SLICE * (TS * TS / 32);
+  static int pblocks = 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_bwd<TS, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (PERSIST) pblocks = persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
     attr = true;
   }
-  k_bwd<TS, SEG><<<(unsigned)tiles, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T, w.tau,
-                                                        fwd->n_contrib, gC, gD, gT, dd, w.d_rgb);
+  const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
+  unsigned grid = (unsigned)tiles;
+  if (PERSIST) {
+    cudaMemsetAsync(w.work + 1, 0, sizeof(unsigned int), s);
+    grid = (unsigned)(tiles < pblocks ? tiles : pblocks);
+  }
+  k_bwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
+                                                       w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
+                                                       n_items);
 }
 
-// tile size and density model (midpoint, or the exact-segment variant) from the options
+// tile size, density model (midpoint, or the exact-segment variant) and scheduling
+// (one block per tile, or persistent warps on a work counter) from the options
 static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* out) {
-  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0;
-#define LV_FWD(TS)                                                             \
-  if (seg) launch_fwd_t<TS, true>(tiles, s, vs, w, sv, o->t_stop, out);        \
-  else launch_fwd_t<TS, false>(tiles, s, vs, w, sv, o->t_stop, out)
+  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
+#define LV_FWD(TS)                                                                   \
+  if (seg && per) launch_fwd_t<TS, true, true>(tiles, s, vs, w, sv, o->t_stop, out);  \
+  else if (seg) launch_fwd_t<TS, true, false>(tiles, s, vs, w, sv, o->t_stop, out);  \
+  else if (per) launch_fwd_t<TS, false, true>(tiles, s, vs, w, sv, o->t_stop, out);  \
+  else launch_fwd_t<TS, false, false>(tiles, s, vs, w, sv, o->t_stop, out)
   if (o->tile == 8) { LV_FWD(8); }
   else if (o->tile == 16) { LV_FWD(16); }
   else { LV_FWD(32); }
@@ -1248,10 +1301,12 @@ static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, c
 static void launch_bwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT,
                        float* dd) {
-  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0;
-#define LV_BWD(TS)                                                                 \
-  if (seg) launch_bwd_t<TS, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);       \
-  else launch_bwd_t<TS, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd)
+  const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
+#define LV_BWD(TS)                                                                         \
+  if (seg && per) launch_bwd_t<TS, true, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
+  else if (seg) launch_bwd_t<TS, true, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
+  else if (per) launch_bwd_t<TS, false, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
+  else launch_bwd_t<TS, false, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd)
   if (o->tile == 8) { LV_BWD(8); }
   else if (o->tile == 16) { LV_BWD(16); }
   else { LV_BWD(32); }

@@ -20,6 +20,7 @@ LV_OK, LV_ERR_INVALID_ARG, LV_ERR_WORKSPACE, LV_ERR_CAPACITY, LV_ERR_CUDA, LV_ER
 LV_F32, LV_F16, LV_BF16 = 0, 1, 2
 LV_FLAG_SYNC_CHECK = 1
 LV_FLAG_EXACT_SEGMENT = 2
+LV_FLAG_PERSISTENT = 4
 LV_MAX_VIEWS = 64
 STATUS_NAMES = {0: "LV_OK", 1: "LV_ERR_INVALID_ARG", 2: "LV_ERR_WORKSPACE", 3: "LV_ERR_CAPACITY", 4: "LV_ERR_CUDA",
                 5: "LV_ERR_TIMEOUT", 6: "LV_ERR_UNSUPPORTED"}
@@ -210,10 +211,12 @@ def make_cameras(cams) -> C.Array:
     return arr
 
 
-def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=False) -> lv_raster_opts:
+def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=False,
+              persistent=False) -> lv_raster_opts:
     o = lv_raster_opts()
     o.tile, o.batch, o.threads_per_px, o.t_stop = tile, batch, 1, t_stop
-    o.flags = (LV_FLAG_SYNC_CHECK if sync_check else 0) | (LV_FLAG_EXACT_SEGMENT if exact_segment else 0)
+    o.flags = ((LV_FLAG_SYNC_CHECK if sync_check else 0) | (LV_FLAG_EXACT_SEGMENT if exact_segment else 0) |
+               (LV_FLAG_PERSISTENT if persistent else 0))
     return o
 
 

@@ -19,7 +19,8 @@ class RasterContext:
     """Workspace and outputs for one camera set and a voxel count.
 
     exact_segment selects the density-model variant in which a sample's
-    density is the mean of the trilinear field over the chord.
+    density is the mean of the trilinear field over the chord; persistent
+    runs the composites as resident warps on a work counter.
 
     The pair capacity (sorted (tile, voxel) pairs) is sized once, with
     headroom, by :meth:`fit_capacity`; a later forward that overflows it
@@ -27,11 +28,11 @@ class RasterContext:
     """
 
     def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda",
-                 exact_segment=False):
+                 exact_segment=False, persistent=False):
         self.cams = list(cams)
         self.n_views = len(self.cams)
         self.cams_arr = L.make_cameras(self.cams)
-        self.opts = L.make_opts(tile, batch, t_stop, exact_segment=exact_segment)
+        self.opts = L.make_opts(tile, batch, t_stop, exact_segment=exact_segment, persistent=persistent)
         self.device = torch.device(device)
         self.n = int(n_voxels)
         self.sizes = [(int(c["width"]), int(c["height"])) for c in self.cams]
@@ -198,13 +199,15 @@ class CapturedStep:
         self.graph.replay()
 
 
-def autotune_tile(scene: Scene, cams, tiles=(8, 16, 32), steps=5, cache_path=None, t_stop=1e-4):
-    """Pick the tile size with the fastest forward + backward for this scene and camera set.
+def autotune_tile(scene: Scene, cams, tiles=(8, 16, 32), steps=5, cache_path=None, t_stop=1e-4,
+                  schedules=(False, True)):
+    """Pick the tile size and composite scheduling (one block per tile, or persistent warps on a
+    work counter) with the fastest forward + backward for this scene and camera set.
 
-    Each candidate is timed with CUDA events over ``steps`` forward + backward
-    passes after one warm-up.  With ``cache_path`` the choice is stored in a
-    JSON file keyed by the GPU name, voxel count and view sizes, and reused.
-    Returns (best_tile, {tile: ms per forward + backward}).
+    Each candidate is timed with CUDA events over ``steps`` forward + backward passes after one
+    warm-up.  With ``cache_path`` the choice is stored in a JSON file keyed by the GPU name, voxel
+    count and view sizes, and reused.  Returns (best_tile, {tile: ms}) where each tile's time is
+    that of its faster schedule; ``autotune_tile.last_persistent`` holds the chosen schedule.
     """
     key = "|".join([torch.cuda.get_device_name(), str(scene.n)] +
                    [f"{int(c['width'])}x{int(c['height'])}" for c in cams])
@@ -213,30 +216,38 @@ def autotune_tile(scene: Scene, cams, tiles=(8, 16, 32), steps=5, cache_path=Non
         with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
+            autotune_tile.last_persistent = bool(cache[key].get("persistent", False))
             return int(cache[key]["tile"]), {int(k): v for k, v in cache[key]["ms"].items()}
     vox = scene.voxels()
-    times = {}
+    times, sched = {}, {}
     for ts in tiles:
-        ctx = RasterContext(cams, scene.n, tile=ts, t_stop=t_stop)
-        ctx.fit_capacity(vox)
-        g = torch.full((ctx.n_pix, 3), 1e-3, device=ctx.device)
-        dd = torch.empty((scene.n, 8), device=ctx.device)
-        ds = torch.empty((scene.n, 48), device=ctx.device)
-        ctx.forward(vox)
-        ctx.backward(vox, g, d_density=dd, d_sh=ds)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
+        for per in schedules:
+            ctx = RasterContext(cams, scene.n, tile=ts, t_stop=t_stop, persistent=per)
+            ctx.fit_capacity(vox)
+            g = torch.full((ctx.n_pix, 3), 1e-3, device=ctx.device)
+            dd = torch.empty((scene.n, 8), device=ctx.device)
+            ds = torch.empty((scene.n, 48), device=ctx.device)
             ctx.forward(vox)
             ctx.backward(vox, g, d_density=dd, d_sh=ds)
-        e1.record()
-        torch.cuda.synchronize()
-        ctx.check()
-        times[ts] = e0.elapsed_time(e1) / steps
-        del ctx
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                ctx.forward(vox)
+                ctx.backward(vox, g, d_density=dd, d_sh=ds)
+            e1.record()
+            torch.cuda.synchronize()
+            ctx.check()
+            ms = e0.elapsed_time(e1) / steps
+            if ts not in times or ms < times[ts]:
+                times[ts], sched[ts] = ms, per
+            del ctx
     best = min(times, key=times.get)
+    autotune_tile.last_persistent = sched[best]
     if cache_path:
-        cache[key] = {"tile": best, "ms": times}
+        cache[key] = {"tile": best, "persistent": sched[best], "ms": times}
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return best, times
+
+
+autotune_tile.last_persistent = False
