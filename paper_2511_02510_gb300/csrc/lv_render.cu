@@ -1199,6 +1199,7 @@ static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int n
   if (vox->vidx && ((uintptr_t)vox->vidx & 15)) { set_error("vidx must be 16-byte aligned"); return LV_ERR_INVALID_ARG; }
   if (o->tile != 8 && o->tile != 16 && o->tile != 32) { set_error("tile must be 8, 16 or 32"); return LV_ERR_INVALID_ARG; }
   if (o->batch != 64 && o->batch != 128 && o->batch != 256) { set_error("batch must be 64, 128 or 256"); return LV_ERR_INVALID_ARG; }
+  if (o->threads_per_px != 1) { set_error("threads_per_px must be 1 (one thread owns a pixel's sample chain)"); return LV_ERR_UNSUPPORTED; }
   if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) { set_error("t_stop must be in [0, 1)"); return LV_ERR_INVALID_ARG; }
   int64_t tiles = 0, pixels = 0;
   for (int i = 0; i < nv; ++i) {

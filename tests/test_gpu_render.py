@@ -126,7 +126,12 @@ def test_mixed_precision_storage(ora, tiny):
     scene, ctx, vox = gpu_forward(tiny, cams, density_dtype=torch.float16, sh_dtype=torch.bfloat16)
     ref_scene = dequantized(tiny, torch.float16, torch.bfloat16)
     r = ora.render(ref_scene, cams)
-    compare_images(r, ctx)
+    e_rgb, e_T = compare_images(r, ctx)
+    compare_wmax(ora, ref_scene, cams, r, ctx)
+    w, _ = ctx.unpack_wmax()
+    hit = r["w_arg"] >= 0
+    print("mixed-precision storage, tiny scene: rgb", e_rgb, "T", e_T, "w_max",
+          float(np.abs(np_(w)[hit] - r["w_max"][hit]).max()))
 
 
 @pytest.mark.parametrize("deg", [0, 1, 2])
