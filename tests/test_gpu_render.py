@@ -296,3 +296,25 @@ def test_full_size_360_sampled_crops(ora):
     ref = ora.pairs(sc, [cam])
     np.testing.assert_array_equal(np_(ctx.seen), ref["seen"])
     np.testing.assert_array_equal(np_(ctx.z_min).view(np.uint32), ref["z_min"].view(np.uint32))
+
+
+def test_max_views_and_limits(ora, tiny):
+    # LV_MAX_VIEWS small views in one launch match the oracle; one more is refused, as is
+    # threads_per_px != 1
+    cams = [synth.orbit_camera(24 + (i % 5) * 4, 18 + (i % 3) * 6, 60.0, 1.6, 360.0 * i / 64, 20.0 + (i % 7),
+                               target=(0.5, 0.4, 0.5)) for i in range(L.LV_MAX_VIEWS)]
+    scene, ctx, vox = gpu_forward(tiny, cams)
+    r = ora.render(tiny, cams)
+    compare_images(r, ctx)
+    keys, vox_ids, ranges, pairs = gpu_pairs(ctx, scene.n)
+    ref = ora.pairs(tiny, cams, ts=16)
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(vox_ids, ref["vals"])
+    too_many = L.make_cameras(cams + [cams[0]])
+    assert L.lv_forward_workspace_size(scene.n, too_many, L.LV_MAX_VIEWS + 1, ctx.opts, 1024) == 0
+    bad = L.make_opts()
+    bad.threads_per_px = 2
+    with pytest.raises(L.LvError) as ei:
+        L.lv_rasterize_forward(vox, ctx.cams_arr, ctx.n_views, bad, ctx.fwd_struct(), ctx.workspace,
+                               ctx.pair_capacity)
+    assert ei.value.status == L.LV_ERR_UNSUPPORTED

@@ -121,3 +121,14 @@ def test_subdivide_rejects_vertex_densities():
         L.lv_subdivide_select(vox, one, one, one, torch.ones(n, dtype=torch.uint8, device="cuda"), None, p, 8 * n,
                               torch.zeros(n, dtype=torch.uint8, device="cuda"),
                               torch.zeros(1, dtype=torch.int64, device="cuda"), ws)
+
+
+def test_vertex_calls_with_no_voxels():
+    geom = torch.zeros((0, 4), device="cuda")
+    vidx = torch.zeros((0, 8), dtype=torch.int32, device="cuda")
+    nv = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    L.lv_build_vertex_index(geom, 0.5, vidx, nv)
+    torch.cuda.synchronize()
+    assert int(nv.item()) == 0
+    L.lv_vertex_gather(vidx, torch.zeros(1, device="cuda"), torch.zeros((0, 8), device="cuda"))
+    L.lv_vertex_scatter_add(vidx, torch.zeros((0, 8), device="cuda"), torch.zeros(1, device="cuda"))
