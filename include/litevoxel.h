@@ -379,6 +379,21 @@ lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* 
                               int n_views, float t, const lv_lf_params* p, float* loss, float* dL_drgb,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* The two halves of lv_lf_weighted_loss.  The weight map w (Eq. 7-9) and its
+ * per-view sum depend on the ground truth and gamma(t) only, so a caller can
+ * compute them on a second stream while the forward pass renders rgb.
+ * lv_lf_weights writes them into `workspace`; lv_lf_loss_from_weights then
+ * reads them from the same workspace (same widths / heights) and writes loss
+ * and dL_drgb exactly as lv_lf_weighted_loss does (bit-identical results).
+ * lv_lf_weighted_loss is lv_lf_weights followed by lv_lf_loss_from_weights
+ * on one stream.  The caller orders the two calls (an event when they run on
+ * different streams) and keeps the workspace for the pair. */
+lv_status lv_lf_weights(const float* gt, const int32_t* widths, const int32_t* heights, int n_views, float t,
+                        const lv_lf_params* p, void* workspace, size_t ws_bytes, void* stream);
+lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, const int32_t* widths, const int32_t* heights,
+                                  int n_views, float* loss, float* dL_drgb, void* workspace, size_t ws_bytes,
+                                  void* stream);
+
 /* Allocation-free variant of lv_lf_weighted_loss.  The paper has no
  * counterpart: it exists for callers that cannot allocate device memory
  * themselves -- for instance code running as a plugin inside a host

@@ -142,6 +142,70 @@ __global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict
   block_add_f64((double)acc, &lsum[v]);
 }
 
+// k_lf_loss over groups of four pixels: three 16-byte loads of rgb and of gt,
+// one of w, three 16-byte stores of the gradient.  The pixels of the view
+// before the first group boundary (global pixel index a multiple of 4) and
+// after the last one go through the scalar path of thread 0 of block 0.  The
+// per-pixel arithmetic is that of k_lf_loss; only the summation order of the
+// partial sums differs.
+__global__ void k_lf_loss4(const float* __restrict__ rgb, const float* __restrict__ gt, const float* __restrict__ w,
+                           const __grid_constant__ ViewPix vp, int v, const double* wsum, double* lsum,
+                           float* __restrict__ grad) {
+  const long long lo = vp.off[v], hi = vp.off[v + 1];
+  const long long np = hi - lo;
+  const float mean = (float)(wsum[v] / (double)np);
+  const float gscale = (float)(2.0 / (3.0 * (double)np));
+  const long long g0 = (lo + 3) >> 2, g1 = hi >> 2;  // whole groups [4 g0, 4 g1)
+  float acc = 0.f;
+  auto one = [&](long long p) {
+    const float wt = w[p] / mean;
+    const float r0 = rgb[3 * p] - gt[3 * p], r1 = rgb[3 * p + 1] - gt[3 * p + 1], r2 = rgb[3 * p + 2] - gt[3 * p + 2];
+    acc += wt * (r0 * r0 + r1 * r1 + r2 * r2);
+    if (grad) {
+      const float c = gscale * wt;
+      grad[3 * p] = c * r0;
+      grad[3 * p + 1] = c * r1;
+      grad[3 * p + 2] = c * r2;
+    }
+  };
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (g1 <= g0) {
+      for (long long p = lo; p < hi; ++p) one(p);
+    } else {
+      for (long long p = lo; p < 4 * g0; ++p) one(p);
+      for (long long p = 4 * g1; p < hi; ++p) one(p);
+    }
+  }
+  const float4* r4 = (const float4*)rgb;
+  const float4* t4 = (const float4*)gt;
+  const float4* w4 = (const float4*)w;
+  float4* d4 = (float4*)grad;
+  for (long long g = g0 + blockIdx.x * (long long)TPB + threadIdx.x; g < g1; g += (long long)gridDim.x * TPB) {
+    const float4 a0 = r4[3 * g], a1 = r4[3 * g + 1], a2 = r4[3 * g + 2];
+    const float4 b0 = t4[3 * g], b1 = t4[3 * g + 1], b2 = t4[3 * g + 2];
+    const float4 wv = w4[g];
+    const float r[12] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z, a0.w - b0.w, a1.x - b1.x, a1.y - b1.y,
+                         a1.z - b1.z, a1.w - b1.w, a2.x - b2.x, a2.y - b2.y, a2.z - b2.z, a2.w - b2.w};
+    const float wt[4] = {wv.x / mean, wv.y / mean, wv.z / mean, wv.w / mean};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc += wt[k] * (r[3 * k] * r[3 * k] + r[3 * k + 1] * r[3 * k + 1] + r[3 * k + 2] * r[3 * k + 2]);
+    if (grad) {
+      float o[12];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float c = gscale * wt[k];
+        o[3 * k] = c * r[3 * k];
+        o[3 * k + 1] = c * r[3 * k + 1];
+        o[3 * k + 2] = c * r[3 * k + 2];
+      }
+      d4[3 * g] = make_float4(o[0], o[1], o[2], o[3]);
+      d4[3 * g + 1] = make_float4(o[4], o[5], o[6], o[7]);
+      d4[3 * g + 2] = make_float4(o[8], o[9], o[10], o[11]);
+    }
+  }
+  block_add_f64((double)acc, &lsum[v]);
+}
+
 __global__ void k_lf_finish(const __grid_constant__ ViewPix vp, const double* lsum, float* loss) {
   int v = threadIdx.x;
   if (v < vp.n) {
@@ -189,40 +253,77 @@ extern "C" size_t lv_lf_workspace_size(const int32_t* widths, const int32_t* hei
   return carve_lf(nullptr, n_views, vp.off[n_views]).bytes;
 }
 
+namespace {
+unsigned blocks_for(long long np) {
+  const long long b = (np + 4 * TPB - 1) / (4 * TPB);  // about four pixels per thread
+  return (unsigned)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+}
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+lv_status lf_setup(const int32_t* widths, const int32_t* heights, int n_views, int32_t pctl_ppm, void* workspace,
+                   size_t ws_bytes, ViewPix* vp, LfWs* w) {
+  if (!make_viewpix(widths, heights, n_views, pctl_ppm, vp)) { set_error("bad view sizes"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  *w = carve_lf(workspace, n_views, vp->off[n_views]);
+  if (ws_bytes < w->bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w->bytes); return LV_ERR_WORKSPACE; }
+  return LV_OK;
+}
+}  // namespace
+
+extern "C" lv_status lv_lf_weights(const float* gt, const int32_t* widths, const int32_t* heights, int n_views,
+                                   float t, const lv_lf_params* p, void* workspace, size_t ws_bytes, void* stream) {
+  if (!gt || !p) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (p->pctl_ppm < 0 || p->pctl_ppm > 1000000) { set_error("pctl_ppm must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->eps > 0.f) || !(p->t1 > p->t0) || !(p->gamma_max >= 0.f)) { set_error("need eps > 0, t1 > t0, gamma_max >= 0"); return LV_ERR_INVALID_ARG; }
+  ViewPix vp;
+  LfWs w;
+  lv_status e = lf_setup(widths, heights, n_views, p->pctl_ppm, workspace, ws_bytes, &vp, &w);
+  if (e != LV_OK) return e;
+  const int64_t P = vp.off[n_views];
+  cudaStream_t s = (cudaStream_t)stream;
+  const float gamma = lv_lf_gamma(t, p);
+  cudaMemsetAsync(w.wsum, 0, sizeof(double) * LV_MAX_VIEWS, s);
+  k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
+  k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
+  select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
+  for (int v = 0; v < n_views; ++v) {
+    const long long np = vp.off[v + 1] - vp.off[v];
+    k_lf_weight<<<blocks_for(np), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum, p->edge_out);
+  }
+  count_launch(2 + n_views);
+  return cuda_check(cudaGetLastError(), "lv_lf_weights");
+}
+
+extern "C" lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, const int32_t* widths,
+                                             const int32_t* heights, int n_views, float* loss, float* dL_drgb,
+                                             void* workspace, size_t ws_bytes, void* stream) {
+  if (!rgb || !gt || !loss) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  ViewPix vp;
+  LfWs w;
+  lv_status e = lf_setup(widths, heights, n_views, 990000, workspace, ws_bytes, &vp, &w);
+  if (e != LV_OK) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(w.lsum, 0, sizeof(double) * LV_MAX_VIEWS, s);
+  // four pixels (three 16-byte words of rgb, gt and dL_drgb) per step where the buffers allow it
+  const bool vec = aligned16(rgb) && aligned16(gt) && aligned16(w.w) && (!dL_drgb || aligned16(dL_drgb));
+  for (int v = 0; v < n_views; ++v) {
+    const long long np = vp.off[v + 1] - vp.off[v];
+    if (vec) k_lf_loss4<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
+    else k_lf_loss<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
+  }
+  k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
+  count_launch(1 + n_views);
+  return cuda_check(cudaGetLastError(), "lv_lf_loss_from_weights");
+}
+
 extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* widths,
                                          const int32_t* heights, int n_views, float t, const lv_lf_params* p,
                                          float* loss, float* dL_drgb, void* workspace, size_t ws_bytes,
                                          void* stream) {
   if (!rgb || !gt || !p || !loss) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
-  if (p->pctl_ppm < 0 || p->pctl_ppm > 1000000) { set_error("pctl_ppm must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
-  if (!(p->eps > 0.f) || !(p->t1 > p->t0) || !(p->gamma_max >= 0.f)) { set_error("need eps > 0, t1 > t0, gamma_max >= 0"); return LV_ERR_INVALID_ARG; }
-  ViewPix vp;
-  if (!make_viewpix(widths, heights, n_views, p->pctl_ppm, &vp)) { set_error("bad view sizes"); return LV_ERR_INVALID_ARG; }
-  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
-  const int64_t P = vp.off[n_views];
-  LfWs w = carve_lf(workspace, n_views, P);
-  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
-  cudaStream_t s = (cudaStream_t)stream;
-  const float gamma = lv_lf_gamma(t, p);
-  cudaMemsetAsync(w.wsum, 0, sizeof(double) * 2 * LV_MAX_VIEWS, s);
-  k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
-  k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
-  select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
-  auto blocks_for = [](long long np) {
-    const long long b = (np + 4 * TPB - 1) / (4 * TPB);  // about four pixels per thread
-    return (unsigned)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
-  };
-  for (int v = 0; v < n_views; ++v) {
-    const long long np = vp.off[v + 1] - vp.off[v];
-    k_lf_weight<<<blocks_for(np), TPB, 0, s>>>(w.mkey, w.q, vp, v, p->eps, gamma, w.w, w.wsum, p->edge_out);
-  }
-  for (int v = 0; v < n_views; ++v) {
-    const long long np = vp.off[v + 1] - vp.off[v];
-    k_lf_loss<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
-  }
-  k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
-  count_launch(3 + 2 * n_views);
-  return cuda_check(cudaGetLastError(), "lv_lf_weighted_loss");
+  lv_status e = lv_lf_weights(gt, widths, heights, n_views, t, p, workspace, ws_bytes, stream);
+  if (e != LV_OK) return e;
+  return lv_lf_loss_from_weights(rgb, gt, widths, heights, n_views, loss, dL_drgb, workspace, ws_bytes, stream);
 }
 
 // ---------------------------------------------------------------- allocation-free variant

@@ -153,13 +153,44 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
 }
 
 // ============================================================ radix sort
+// LSD radix sort with 8-bit digits and one kernel per digit pass (a
+// "one-sweep" schedule).  One histogram kernel first counts every pass's
+// digits over all items.  Each pass kernel then takes tiles of Os<K>::TILE items
+// in ticket order (an atomic counter, so a tile's predecessors are already
+// running or done), ranks its items by digit in shared memory (a warp-private
+// match_any histogram per warp, stable), publishes its per-digit counts, and
+// finds the number of items with each digit in all earlier tiles by looking
+// back through their published words (decoupled look-back: a tile that has
+// published its inclusive prefix ends the walk).  A published word packs a
+// 2-bit flag (0 not yet, 1 tile count, 2 inclusive prefix) and a 62-bit
+// count, so one 64-bit load reads both.  Every wait is bounded: a walk that
+// gives up reports LV_ERR_TIMEOUT and counts the missing word as zero.
 namespace {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 8;                       // per lane per sub-tile
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2048 items
+constexpr int OS_ITEMS = 8;                      // per lane
 constexpr int RADIX = 256;
+constexpr int OS_MAX_PASSES = 8;
+constexpr int OS_HIST_BLOCKS = 2 * 152;
+constexpr unsigned long long OS_FLAG_AGG = 1ull << 62;
+constexpr unsigned long long OS_FLAG_INC = 2ull << 62;
+constexpr unsigned long long OS_VALUE = (1ull << 62) - 1;
+constexpr unsigned OS_SPIN_LIMIT = 1u << 20;     // polls per look-back walk before giving up
+constexpr int OS_LOOK_WINDOW = 8;                // earlier tiles' words loaded together
+constexpr int OS_HIST_THREADS = 256;
+
+// Tile shape of the pass kernel: 512 threads (4096 items) for 32-bit keys,
+// 256 (2048 items) for 64-bit keys, so that the static shared memory stays
+// under 48 KB; 64 registers a thread either way.  Threads d < RADIX look
+// after digit d.
+template <typename K>
+struct Os {
+  static constexpr int THREADS = sizeof(K) == 4 ? 512 : 256;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * OS_ITEMS;
+  static constexpr int MIN_BLOCKS = 1024 / THREADS;
+  static_assert(THREADS >= RADIX && THREADS % 32 == 0, "one thread per digit");
+};
+constexpr int OS_MIN_TILE = 256 * OS_ITEMS;  // the look-back words are sized for the smaller tile
 
 // On overflow (more pairs than capacity) the list is treated as empty: the
 // emit step then left holes in the buffers, and the caller's status word
@@ -169,205 +200,269 @@ __device__ __forceinline__ int64_t rs_count(const unsigned long long* d_count, i
   return c <= (unsigned long long)cap ? (int64_t)c : 0;
 }
 
-template <typename K>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const K* keys, const unsigned long long* d_count,
-                                                          int64_t cap, int shift, uint32_t* hist) {
-  __shared__ uint32_t sh[RS_WARPS][RADIX];
-  const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  int64_t n = rs_count(d_count, cap);
-  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  for (int64_t i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
-    uint32_t d = (uint32_t)(keys[i] >> shift) & (RADIX - 1);
-    atomicAdd(&sh[warp][d], 1u);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
-    uint32_t t = 0;
-#pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) t += sh[w][d];
-    hist[d * gridDim.x + blockIdx.x] = t;
-  }
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Per digit d (one block each): exclusive scan over the blocks' counts
-// hist[d * G + b] in place, and the digit's total in digit_tot[d].  The
-// downsweep adds the exclusive scan of the digit totals itself.
-__global__ void __launch_bounds__(SORT_BLOCKS) k_rs_scan_digits(uint32_t* hist, uint32_t* digit_tot) {
-  constexpr int NW = SORT_BLOCKS / 32;
-  __shared__ uint32_t sw[NW];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t* h = hist + (size_t)blockIdx.x * SORT_BLOCKS;
-  const uint32_t c = h[t];
+struct SortTmp {
+  uint32_t* ghist;               // [OS_MAX_PASSES][RADIX] digit counts of every pass
+  uint32_t* ticket;              // [2] tile tickets (pass p uses p & 1)
+  unsigned long long* look[2];   // [tiles][RADIX] published words (pass p uses p & 1)
+  size_t bytes;
+};
+
+SortTmp carve_sort(void* base, int64_t cap) {
+  SortTmp t;
+  Carve c(base);
+  const int64_t tiles = (cap + OS_MIN_TILE - 1) / OS_MIN_TILE;
+  t.ghist = c.take<uint32_t>(OS_MAX_PASSES * RADIX + 64);  // the tickets follow the counts
+  t.ticket = t.ghist ? t.ghist + OS_MAX_PASSES * RADIX : nullptr;
+  t.look[0] = c.take<unsigned long long>(tiles * RADIX);
+  t.look[1] = c.take<unsigned long long>(tiles * RADIX);
+  t.bytes = c.off;
+  return t;
+}
+
+// Digit counts of all passes (block-private shared histograms, one global
+// atomic per nonzero bin), and clears the look-back words of the first pass.
+template <typename K>
+__global__ void __launch_bounds__(OS_HIST_THREADS) k_os_hist(const K* __restrict__ keys, const unsigned long long* d_count,
+                                                       int64_t cap, int passes, uint32_t* __restrict__ ghist,
+                                                       unsigned long long* __restrict__ look0) {
+  __shared__ uint32_t sh[OS_MAX_PASSES * RADIX];
+  for (int i = threadIdx.x; i < passes * RADIX; i += OS_HIST_THREADS) sh[i] = 0;
+  __syncthreads();
+  const int64_t n = rs_count(d_count, cap);
+  const int64_t ntiles = (n + Os<K>::TILE - 1) / Os<K>::TILE;
+  const int64_t stride = (int64_t)gridDim.x * OS_HIST_THREADS;
+  for (int64_t i = blockIdx.x * (int64_t)OS_HIST_THREADS + threadIdx.x; i < ntiles * RADIX; i += stride) look0[i] = 0ull;
+  int64_t i = blockIdx.x * (int64_t)OS_HIST_THREADS + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    K k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = keys[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + ((uint32_t)(k[u] >> (8 * p)) & (RADIX - 1))], 1u);
+  }
+  for (; i < n; i += stride) {
+    const K k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + ((uint32_t)(k >> (8 * p)) & (RADIX - 1))], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < passes * RADIX; b += OS_HIST_THREADS)
+    if (sh[b]) atomicAdd(&ghist[b], sh[b]);
+}
+
+// exclusive scan of one value per thread over the block of WARPS warps
+template <int WARPS>
+__device__ __forceinline__ uint32_t os_block_excl(uint32_t c, uint32_t* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(FULL, x, o);
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) sw[warp] = x;
+  if (lane == 31) s_w[warp] = x;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < NW ? sw[lane] : 0u;
+  uint32_t pre = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < NW) sw[lane] = w;
-  }
-  __syncthreads();
-  h[t] = (warp ? sw[warp - 1] : 0u) + x - c;
-  if (t == SORT_BLOCKS - 1) digit_tot[blockIdx.x] = sw[NW - 1];
+  for (int w = 0; w < WARPS; ++w) pre += w < warp ? s_w[w] : 0u;
+  return pre + x - c;
 }
 
 template <typename K>
-__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_downsweep(const K* kin, const uint32_t* vin,
-                                                            K* kout, uint32_t* vout,
-                                                            const unsigned long long* d_count, int64_t cap,
-                                                            int shift, const uint32_t* hist,
-                                                            const uint32_t* digit_tot) {
-  __shared__ uint32_t s_goff[RADIX];          // next global slot per digit for this block
-  __shared__ uint32_t s_wh[RS_WARPS][RADIX];  // per-warp digit counts -> warp prefixes
-  __shared__ uint32_t s_cnt[RADIX];           // sub-tile digit counts
-  __shared__ uint32_t s_start[RADIX];         // sub-tile digit start offsets
-  __shared__ K s_k[RS_TILE];
-  __shared__ uint32_t s_v[RS_TILE];
+__global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                         K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         const unsigned long long* d_count, int64_t cap, int pass,
+                                                         const uint32_t* __restrict__ ghist, uint32_t* ticket,
+                                                         unsigned long long* look, unsigned long long* look_next,
+                                                         int32_t* status) {
+  constexpr int OS_THREADS = Os<K>::THREADS, OS_WARPS = Os<K>::WARPS, OS_TILE = Os<K>::TILE;
+  __shared__ uint32_t s_wh[OS_WARPS][RADIX + 1];  // warp digit counts -> warp prefixes (bin RADIX: padding items)
+  __shared__ uint32_t s_start[RADIX];             // tile-local start of each digit
+  __shared__ long long s_off[RADIX];              // global position of the digit's first item minus s_start
+  __shared__ uint32_t s_w[2][OS_WARPS];
+  __shared__ K s_k[OS_TILE];
+  __shared__ uint32_t s_v[OS_TILE];
+  __shared__ uint32_t s_tile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  {
-    // digit base = exclusive scan of the digit totals (RS_THREADS == RADIX)
-    __shared__ uint32_t sw0[RS_WARPS];
-    const uint32_t c = digit_tot[t];
-    uint32_t x = c;
+  const int shift = 8 * pass;
+  if (t == 0) s_tile = atomicAdd(&ticket[pass & 1], 1u);
+  for (int i = t; i < OS_WARPS * (RADIX + 1); i += OS_THREADS) (&s_wh[0][0])[i] = 0u;
+  __syncthreads();
+  const int64_t n = rs_count(d_count, cap);
+  const int64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+  const int64_t tile = s_tile;
+  if (tile >= ntiles) return;  // block-uniform
+  if (tile == 0 && t == 0) ticket[(pass + 1) & 1] = 0u;  // the next pass's counter (last used two passes ago)
+  if (t < RADIX) look_next[tile * RADIX + t] = 0ull;      // and its look-back words
+
+  // ---- load (warp-striped: lane l of warp w holds items w*256 + j*32 + l)
+  const int64_t base = tile * OS_TILE;
+  const int m = (int)min((int64_t)OS_TILE, n - base);
+  K k[OS_ITEMS];
+  uint32_t v[OS_ITEMS], dr[OS_ITEMS];  // digit (RADIX for padding) in bits 0-8, then the warp rank
+  const int wofs = warp * (32 * OS_ITEMS) + lane;
+  if (m == OS_TILE) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
+    for (int j = 0; j < OS_ITEMS; ++j) {
+      const int64_t i = base + wofs + j * 32;
+      k[j] = kin[i];
+      v[j] = vin ? vin[i] : (uint32_t)i;  // no values: the item's position
     }
-    if (lane == 31) sw0[warp] = x;
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; ++w) pre += sw0[w];
-    s_goff[t] = pre + x - c + hist[t * gridDim.x + blockIdx.x];
-  }
-  int64_t n = rs_count(d_count, cap);
-  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  for (int64_t base = lo; base < hi; base += RS_TILE) {
-    for (int i = t; i < RS_WARPS * RADIX; i += RS_THREADS) (&s_wh[0][0])[i] = 0;
-    __syncthreads();
-    K k[RS_ITEMS];
-    uint32_t v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
-    const int64_t wbase = base + (int64_t)warp * (32 * RS_ITEMS);
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-      int64_t i = wbase + j * 32 + lane;
-      bool ok = i < hi;
+    for (int j = 0; j < OS_ITEMS; ++j) dr[j] = (uint32_t)(k[j] >> shift) & (RADIX - 1);
+  } else {
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {
+      const int q = wofs + j * 32;
+      const int64_t i = base + q;
+      const bool ok = q < m;
       k[j] = ok ? kin[i] : (K)0;
-      v[j] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;  // no values: the item's position
-      dg[j] = ok ? ((uint32_t)(k[j] >> shift) & (RADIX - 1)) : RADIX;
+      v[j] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
+      dr[j] = ok ? ((uint32_t)(k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
     }
+  }
+  // ---- digit base of this pass: exclusive scan of the global counts
+  const uint32_t gbase = os_block_excl<OS_WARPS>(t < RADIX ? ghist[pass * RADIX + t] : 0u, s_w[0]);
+
+  // ---- stable rank inside each warp (items in j-major, lane-minor order)
+  const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-      uint32_t peers = __match_any_sync(FULL, dg[j]);
-      uint32_t before = __popc(peers & lt_mask);
-      uint32_t cur = dg[j] < RADIX ? s_wh[warp][dg[j]] : 0u;
-      rk[j] = cur + before;
-      __syncwarp();
-      if (dg[j] < RADIX && before == 0) s_wh[warp][dg[j]] = cur + __popc(peers);
-      __syncwarp();
+  for (int j = 0; j < OS_ITEMS; ++j) {
+    const uint32_t d = dr[j];
+    const uint32_t peers = __match_any_sync(FULL, d);
+    const uint32_t cur = s_wh[warp][d];
+    dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
+    __syncwarp();
+    if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- per digit: warp prefixes and the tile count, published at once
+  uint32_t cnt = 0;
+  if (t < RADIX) {
+#pragma unroll
+    for (int w = 0; w < OS_WARPS; ++w) {
+      const uint32_t c = s_wh[w][t];
+      s_wh[w][t] = cnt;
+      cnt += c;
     }
-    __syncthreads();
-    for (int d = t; d < RADIX; d += RS_THREADS) {
-      uint32_t run = 0;
+    st_relaxed(&look[tile * RADIX + t], (tile == 0 ? OS_FLAG_INC : OS_FLAG_AGG) | cnt);
+  }
+  const uint32_t start = os_block_excl<OS_WARPS>(cnt, s_w[1]);
+  if (t < RADIX) s_start[t] = start;
+  __syncthreads();
+  // ---- scatter into shared memory in (digit, rank) order
 #pragma unroll
-      for (int w = 0; w < RS_WARPS; ++w) {
-        uint32_t c = s_wh[w][d];
-        s_wh[w][d] = run;
-        run += c;
+  for (int j = 0; j < OS_ITEMS; ++j) {
+    const uint32_t d = dr[j] & 511u;
+    if (d < RADIX) {
+      const uint32_t pos = s_start[d] + s_wh[warp][d] + (dr[j] >> 9);
+      s_k[pos] = k[j];
+      s_v[pos] = v[j];
+    }
+  }
+  // ---- look back: items of digit t in all earlier tiles, OS_LOOK_WINDOW words per round trip
+  unsigned long long excl = 0;
+  if (tile > 0 && t < RADIX) {
+    int64_t j = tile - 1;  // nearest word not summed yet
+    unsigned spins = 0;    // polls of unpublished words over the whole walk
+    bool done = false;
+    while (!done) {
+      unsigned long long wv[OS_LOOK_WINDOW];
+#pragma unroll
+      for (int u = 0; u < OS_LOOK_WINDOW; ++u)  // before tile 0: an inclusive zero
+        wv[u] = j - u >= 0 ? ld_relaxed(&look[(j - u) * RADIX + t]) : OS_FLAG_INC;
+      int u = 0;
+#pragma unroll
+      for (; u < OS_LOOK_WINDOW; ++u) {
+        if ((wv[u] >> 62) == 0ull) break;
+        excl += wv[u] & OS_VALUE;
+        if (wv[u] & OS_FLAG_INC) { done = true; break; }
       }
-      s_cnt[d] = run;
-    }
-    __syncthreads();
-    // exclusive scan of s_cnt over the 256 digits (RS_THREADS == RADIX)
-    {
-      uint32_t c = s_cnt[t];
-      uint32_t x = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-      }
-      __shared__ uint32_t sw[RS_WARPS];
-      if (lane == 31) sw[warp] = x;
-      __syncthreads();
-      uint32_t pre = 0;
-      for (int w = 0; w < warp; ++w) pre += sw[w];
-      s_start[t] = pre + x - c;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
-      if (dg[j] < RADIX) {
-        uint32_t pos = s_start[dg[j]] + s_wh[warp][dg[j]] + rk[j];
-        s_k[pos] = k[j];
-        s_v[pos] = v[j];
+      if (done) break;
+      j -= u;
+      if (u < OS_LOOK_WINDOW) {
+        // word j is not published yet: wait for it alone
+        while (true) {
+          if (spins >= OS_SPIN_LIMIT) {
+            // out of patience: report once, count this and any further unpublished word as zero
+            if (spins++ == OS_SPIN_LIMIT) report(status, LV_ERR_TIMEOUT);
+            --j;
+            break;
+          }
+          ++spins;
+          __nanosleep(32);
+          if ((ld_relaxed(&look[j * RADIX + t]) >> 62) != 0ull) break;
+        }
       }
     }
-    __syncthreads();
-    int m = (int)min((int64_t)RS_TILE, hi - base);
-    for (int q = t; q < m; q += RS_THREADS) {
+    st_relaxed(&look[tile * RADIX + t], OS_FLAG_INC | (excl + cnt));
+  }
+  if (t < RADIX) s_off[t] = (long long)gbase + (long long)excl - (long long)start;
+  __syncthreads();
+  // ---- write out: consecutive threads take consecutive sorted items
+#pragma unroll
+  for (int j = 0; j < OS_ITEMS; ++j) {
+    const int q = j * OS_THREADS + t;
+    if (q < m) {
       const K kk = s_k[q];
-      uint32_t d = (uint32_t)(kk >> shift) & (RADIX - 1);
-      uint32_t g = s_goff[d] + (uint32_t)q - s_start[d];
+      const int64_t g = s_off[(uint32_t)(kk >> shift) & (RADIX - 1)] + q;
       kout[g] = kk;
       vout[g] = s_v[q];
     }
-    __syncthreads();
-    for (int d = t; d < RADIX; d += RS_THREADS) s_goff[d] += s_cnt[d];
-    __syncthreads();
   }
 }
 
 }  // namespace
 
-size_t sort_hist_bytes() { return sizeof(uint32_t) * (RADIX * SORT_BLOCKS + RADIX); }
+size_t sort_tmp_bytes(int64_t cap) { return carve_sort(nullptr, cap > 0 ? cap : 1).bytes; }
 int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 
 template <typename K>
-static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, K* k1, uint32_t* v1, uint32_t* hist,
-                        const unsigned long long* d_count, int64_t cap, int end_bit, cudaStream_t s) {
-  const int passes = sort_passes(end_bit);
+static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, K* k1, uint32_t* v1, void* tmp,
+                        const unsigned long long* d_count, int64_t cap, int end_bit, int32_t* status,
+                        cudaStream_t s) {
+  int passes = sort_passes(end_bit);
+  if (passes > (int)sizeof(K)) passes = (int)sizeof(K);
+  if (passes == 0 || cap <= 0) return 0;
+  SortTmp st = carve_sort(tmp, cap);
   K* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
-  uint32_t* digit_tot = hist + RADIX * SORT_BLOCKS;
+  const int64_t tiles = (cap + Os<K>::TILE - 1) / Os<K>::TILE;
+  cudaMemsetAsync(st.ghist, 0, sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2), s);  // counts and tickets
+  const int hb = (int)min((int64_t)OS_HIST_BLOCKS, tiles);
+  k_os_hist<K><<<hb, OS_HIST_THREADS, 0, s>>>(kin, d_count, cap, passes, st.ghist, st.look[0]);
   for (int p = 0; p < passes; ++p) {
     // pass 0 reads the input (kept intact unless it is k0 / v0), pass p writes buffer (p + 1) & 1
     const K* ks = p == 0 ? kin : kb[p & 1];
     const uint32_t* vs = p == 0 ? vin : vb[p & 1];
     const int dst = (p + 1) & 1;
-    k_rs_upsweep<K><<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, d_count, cap, 8 * p, hist);
-    k_rs_scan_digits<<<RADIX, SORT_BLOCKS, 0, s>>>(hist, digit_tot);
-    k_rs_downsweep<K><<<SORT_BLOCKS, RS_THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, 8 * p, hist,
-                                                         digit_tot);
+    k_os_pass<K><<<(unsigned)tiles, Os<K>::THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, p, st.ghist,
+                                                       st.ticket, st.look[p & 1], st.look[(p + 1) & 1], status);
   }
-  count_launch(3 * passes);
+  count_launch(1 + passes);
   return passes & 1;
 }
 
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     cudaStream_t s) {
-  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, hist, d_count, cap, end_bit, s);
+                     uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     int32_t* status, cudaStream_t s) {
+  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s);
 }
 
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
-                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     cudaStream_t s) {
-  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, hist, d_count, cap, end_bit, s);
+                     uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     int32_t* status, cudaStream_t s) {
+  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s);
 }
 
 // ============================================================ grouped select

@@ -1,6 +1,7 @@
 // lv_prims.cuh -- device primitives: two-channel exclusive scan, LSD radix sort
-// of (u32 key, u32 value) pairs, grouped radix select.  No CUB: every kernel
-// here is written for this library (reduce-then-scan, no inter-block waits).
+// of (key, u32 value) pairs, grouped radix select.  No CUB: every kernel here
+// is written for this library.  The scan and the select are reduce-then-scan
+// with no inter-block waits; the sort's look-back waits are bounded.
 #pragma once
 
 #include "lv_common.cuh"
@@ -17,23 +18,24 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
            unsigned long long* totals, void* tmp, cudaStream_t s);
 
 // ---------------------------------------------------------------- radix sort
-// Stable LSD sort of the first *d_count (key, value) pairs, 32-bit keys, on
-// bits [0, end_bit) with 8-bit digits; nothing is sorted when *d_count > cap
-// (an overflowed emit leaves holes).  The first pass reads (kin, vin), which
-// may be (k0, v0); vin == nullptr stands for the values 0, 1, 2, ... (the
-// items' positions).  Returns 0 when the result is in (k0, v0) and 1 when it is
-// in (k1, v1).  With end_bit == 0 nothing runs and 0 is returned, so a caller
-// that may sort no bits passes kin == k0 and vin == v0.
-constexpr int SORT_BLOCKS = 512;
-size_t sort_hist_bytes();
+// Stable LSD sort of the first *d_count (key, value) pairs, 32- or 64-bit
+// keys, on bits [0, end_bit) with 8-bit digits; nothing is sorted when
+// *d_count > cap (an overflowed emit leaves holes).  The first pass reads
+// (kin, vin), which may be (k0, v0); vin == nullptr stands for the values 0,
+// 1, 2, ... (the items' positions).  Returns 0 when the result is in (k0, v0)
+// and 1 when it is in (k1, v1).  With end_bit == 0 nothing runs and 0 is
+// returned, so a caller that may sort no bits passes kin == k0 and vin == v0.
+// tmp: sort_tmp_bytes(cap) bytes, 256-byte aligned, no initial contents.
+// A bounded inter-block wait that gives up reports LV_ERR_TIMEOUT in *status
+// (nullable).
+size_t sort_tmp_bytes(int64_t cap);
 int sort_passes(int end_bit);
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     cudaStream_t s);
-// the same with 64-bit keys (end_bit up to 64)
+                     uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     int32_t* status, cudaStream_t s);
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
-                     uint32_t* v1, uint32_t* hist, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     cudaStream_t s);
+                     uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
+                     int32_t* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- grouped select
 // For each query q (group g_q, 1-based rank k_q), find the k-th smallest

@@ -100,7 +100,7 @@ struct FwdWs {
   float4* d_rgb;                 // [slots] colour gradient (xyz) scratch of the backward; w = clamp mask
   uint32_t* ranges;              // [tiles][2]
   float* tau;                    // [pixels] final optical depth
-  uint32_t* hist;
+  void* sort_tmp;                // radix sort scratch (both sorts, one after the other)
   int32_t* status;               // fallback status word
   uint32_t *k0, *v0, *k1, *v1;   // [pair capacity] (tile, slot) pairs, sorted by tile
   size_t bytes;
@@ -135,7 +135,7 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   w.d_rgb = c.take<float4>(items);
   w.ranges = c.take<uint32_t>(tiles * 2);
   w.tau = c.take<float>(pixels);
-  w.hist = c.take<uint32_t>(sort_hist_bytes() / 4);
+  w.sort_tmp = c.take<char>(sort_tmp_bytes(items > pair_cap ? items : pair_cap));
   w.k0 = c.take<uint32_t>(pair_cap);
   w.v0 = c.take<uint32_t>(pair_cap);
   w.k1 = c.take<uint32_t>(pair_cap);
@@ -1364,8 +1364,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
 #undef LV_EMIT
     count_launch(2);
     // 1) the slots front to back: stable sort by order key (ties keep slot = voxel-id order)
-    const int ws_ = radix_sort_pairs(w.s_dkey, nullptr, w.sk0, w.sv0, w.sk1, w.sv1, w.hist, w.counters + 1, items,
-                                     32, s);
+    const int ws_ = radix_sort_pairs(w.s_dkey, nullptr, w.sk0, w.sv0, w.sk1, w.sv1, w.sort_tmp, w.counters + 1,
+                                     items, 32, d_status, s);
     const uint32_t* sorted_slot = ws_ ? w.sv1 : w.sv0;
     // 2) pair offsets in that order, then the pairs themselves
     const int gb = (int)std::min<int64_t>((items + 255) / 256, 4 * 1216);
@@ -1376,7 +1376,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     count_launch(2);
   }
   // 3) stable sort by tile: each tile's list stays front to back
-  radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.hist, w.counters, pair_capacity, tile_bits(tiles), s);
+  radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.sort_tmp, w.counters, pair_capacity, tile_bits(tiles),
+                   d_status, s);
   const uint32_t* sk = sorted_pair_tiles(w, tiles);
   const uint32_t* sv = sorted_pair_slots(w, tiles);
   k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);

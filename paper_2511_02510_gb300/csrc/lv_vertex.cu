@@ -30,7 +30,7 @@ struct VxWs {
   uint32_t *v0, *v1;
   uint32_t* flag;
   uint32_t* rank;
-  uint32_t* hist;
+  void* sort_tmp;
   void* scan_tmp;
   size_t bytes;
 };
@@ -46,7 +46,7 @@ VxWs carve_vx(void* base, int64_t n) {
   w.v1 = c.take<uint32_t>(m);
   w.flag = c.take<uint32_t>(m);
   w.rank = c.take<uint32_t>(m);
-  w.hist = c.take<uint32_t>(sort_hist_bytes() / 4);
+  w.sort_tmp = c.take<char>(sort_tmp_bytes(m));
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.bytes = c.off + 256;
   return w;
@@ -151,8 +151,8 @@ extern "C" lv_status lv_build_vertex_index(const float* geom, int64_t n, double 
   if (!d_status) cudaMemsetAsync(st, 0, sizeof(int32_t), s);
   const unsigned blocks = (unsigned)((m + TPB - 1) / TPB);
   k_vx_keys<<<blocks, TPB, 0, s>>>((const float4*)geom, n, 1.0 / unit, w.k0, st);
-  const int which = radix_sort_pairs(w.k0, nullptr, w.k0, w.v0, w.k1, w.v1, w.hist, w.counters, m, 3 * COORD_BITS,
-                                     s);
+  const int which = radix_sort_pairs(w.k0, nullptr, w.k0, w.v0, w.k1, w.v1, w.sort_tmp, w.counters, m,
+                                     3 * COORD_BITS, st, s);
   const uint64_t* sk = which ? w.k1 : w.k0;
   const uint32_t* sv = which ? w.v1 : w.v0;
   k_vx_flags<<<blocks, TPB, 0, s>>>(sk, m, w.flag);

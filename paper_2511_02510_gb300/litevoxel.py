@@ -130,6 +130,8 @@ SIGNATURES = {
     "lv_lf_workspace_size": (_SZ, [_P, _P, C.c_int]),
     "lv_lf_weighted_loss": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P, _SZ, _P]),
     "lv_lf_weighted_loss_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P]),
+    "lv_lf_weights": (C.c_int, [_P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _SZ, _P]),
+    "lv_lf_loss_from_weights": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P, _SZ, _P]),
     "lv_last_error": (C.c_char_p, []),
     "lv_version": (C.c_int32, []),
     "lv_launch_count": (C.c_int64, []),
@@ -386,6 +388,23 @@ def lv_lf_weighted_loss(rgb, gt, widths, heights, t, params, loss, dL_drgb, work
     _check(load().lv_lf_weighted_loss(_ptr(rgb), _ptr(gt), w, h, len(widths), float(t), C.byref(params), _ptr(loss),
                                       _ptr(dL_drgb), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                       _stream()), "lv_lf_weighted_loss")
+
+
+def lv_lf_weights(gt, widths, heights, t, params, workspace):
+    """Eq. 7-9 weight map of the ground truth into the workspace (first half of lv_lf_weighted_loss)."""
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    _check(load().lv_lf_weights(_ptr(gt), w, h, len(widths), float(t), C.byref(params), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream()), "lv_lf_weights")
+
+
+def lv_lf_loss_from_weights(rgb, gt, widths, heights, loss, dL_drgb, workspace):
+    """Loss and dL/drgb from the weight map lv_lf_weights left in the workspace (second half)."""
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    _check(load().lv_lf_loss_from_weights(_ptr(rgb), _ptr(gt), w, h, len(widths), _ptr(loss), _ptr(dL_drgb),
+                                          _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+           "lv_lf_loss_from_weights")
 
 
 LV_LF_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -306,3 +306,34 @@ def test_lf_loss_constant_target():
     loss, grad, _ = gpu_lf(rgb, gt, sizes, 1e9)
     mse = np.mean((rgb.astype(np.float64) - gt) ** 2)
     assert abs(loss[0] - mse) <= 1e-6 * mse
+
+
+def test_lf_split_calls_match_fused_across_streams(ora):
+    """lv_lf_weights on a side stream, then lv_lf_loss_from_weights on the main
+    stream after an event: the same bits as the one-call loss.  Tiny views put
+    view boundaries inside and between 4-pixel groups."""
+    sizes = [(2, 3), (1, 1), (3, 1), (77, 45), (128, 96)]
+    W = [s[0] for s in sizes]
+    H = [s[1] for s in sizes]
+    P = sum(w * h for w, h in sizes)
+    rng = np.random.default_rng(11)
+    gt = np.concatenate([synth.smooth_image(w, h, seed=i) for i, (w, h) in enumerate(sizes)])
+    rgb = np.clip(gt + rng.normal(0, 0.1, gt.shape), 0, 1).astype(np.float32)
+    loss_a, grad_a, gamma = gpu_lf(rgb, gt, sizes, 450.0)
+    p = lf_params()
+    ws = torch.empty(L.lv_lf_workspace_size(W, H), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(len(sizes), dtype=torch.float32, device="cuda")
+    g = torch.zeros((P, 3), dtype=torch.float32, device="cuda")
+    gt_d, rgb_d = cu(gt), cu(rgb)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        L.lv_lf_weights(gt_d, W, H, 450.0, p, ws)
+    torch.cuda.current_stream().wait_stream(side)
+    L.lv_lf_loss_from_weights(rgb_d, gt_d, W, H, loss, g, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(np_(loss), loss_a)
+    np.testing.assert_array_equal(np_(g), grad_a)
+    r = ora.lf_loss(rgb.astype(np.float64), gt.astype(np.float64), sizes, gamma=gamma)
+    np.testing.assert_allclose(loss_a, r["loss"], rtol=1e-5)
+    assert np.abs(grad_a - r["dL_drgb"]).max() <= 1e-5 * np.abs(r["dL_drgb"]).max()
