@@ -207,6 +207,20 @@ lv_status lv_debug_pairs(int64_t n, const lv_camera* cams, int n_views, const lv
                          const void* workspace, size_t ws_bytes, int64_t pair_capacity, uint64_t* keys,
                          uint32_t* voxel, uint32_t* ranges, void* stream);
 
+/* Check of the radix sort's bounded wait.  The pair sort's pass kernel
+ * finds each tile's global offsets by waiting for the digit counts that
+ * earlier tiles publish (a decoupled look-back).  This call runs one pass
+ * over two 4096-item tiles with only the second tile's block launched, so
+ * its wait for the first tile can never end.  The wait gives up after
+ * spin_limit polls (1 .. 1048576, the limit the sort uses; 32 ns sleep
+ * between polls), writes LV_ERR_TIMEOUT into *d_status (device int32,
+ * cleared by the call first) and returns; the stream stays usable.
+ * workspace: lv_debug_sort_timeout_workspace_size() bytes, 256-byte
+ * aligned.  For tests. */
+size_t lv_debug_sort_timeout_workspace_size(void);
+lv_status lv_debug_sort_timeout(int32_t spin_limit, void* workspace, size_t ws_bytes, int32_t* d_status,
+                                void* stream);
+
 /* FP64 re-render of chosen pixels for finite-difference gradient checks (the
  * only FP64 arithmetic of the library): pixels [n_px] are global pixel ids
  * (device int64); for each, the tile list of a forward workspace is walked

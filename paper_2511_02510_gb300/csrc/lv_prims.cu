@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
                                                          const unsigned long long* d_count, int64_t cap, int pass,
                                                          const uint32_t* __restrict__ ghist, uint32_t* ticket,
                                                          unsigned long long* look, unsigned long long* look_next,
-                                                         int32_t* status) {
+                                                         int32_t* status, unsigned spin_limit) {
   constexpr int OS_THREADS = Os<K>::THREADS, OS_WARPS = Os<K>::WARPS, OS_TILE = Os<K>::TILE;
   __shared__ uint32_t s_wh[OS_WARPS][RADIX + 1];  // warp digit counts -> warp prefixes (bin RADIX: padding items)
   __shared__ uint32_t s_start[RADIX];             // tile-local start of each digit
@@ -393,9 +393,9 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
       if (u < OS_LOOK_WINDOW) {
         // word j is not published yet: wait for it alone
         while (true) {
-          if (spins >= OS_SPIN_LIMIT) {
+          if (spins >= spin_limit) {
             // out of patience: report once, count this and any further unpublished word as zero
-            if (spins++ == OS_SPIN_LIMIT) report(status, LV_ERR_TIMEOUT);
+            if (spins++ == spin_limit) report(status, LV_ERR_TIMEOUT);
             --j;
             break;
           }
@@ -447,7 +447,8 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
     const uint32_t* vs = p == 0 ? vin : vb[p & 1];
     const int dst = (p + 1) & 1;
     k_os_pass<K><<<(unsigned)tiles, Os<K>::THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, p, st.ghist,
-                                                       st.ticket, st.look[p & 1], st.look[(p + 1) & 1], status);
+                                                       st.ticket, st.look[p & 1], st.look[(p + 1) & 1], status,
+                                                       OS_SPIN_LIMIT);
   }
   count_launch(1 + passes);
   return passes & 1;
@@ -464,6 +465,62 @@ int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uin
                      int32_t* status, cudaStream_t s) {
   return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s);
 }
+
+// ---- bounded-wait check: one pass over two tiles where only the second tile's
+// block runs (its ticket counter starts at 1), so the first tile's counts are
+// never published and the look-back must give up.
+namespace {
+constexpr int64_t DBG_ITEMS = 2 * Os<uint32_t>::TILE;
+
+struct DbgWs {
+  uint32_t *k0, *k1, *v1;
+  unsigned long long* count;
+  void* tmp;
+  size_t bytes;
+};
+DbgWs carve_dbg(void* base) {
+  DbgWs w;
+  Carve c(base);
+  w.k0 = c.take<uint32_t>(DBG_ITEMS);
+  w.k1 = c.take<uint32_t>(DBG_ITEMS);
+  w.v1 = c.take<uint32_t>(DBG_ITEMS);
+  w.count = c.take<unsigned long long>(1);
+  w.tmp = c.take<char>(sort_tmp_bytes(DBG_ITEMS));
+  w.bytes = c.off;
+  return w;
+}
+__global__ void k_dbg_setup(unsigned long long* count, uint32_t* ticket) {
+  if (threadIdx.x == 0) {
+    *count = (unsigned long long)DBG_ITEMS;
+    ticket[0] = 1u;  // the one block launched takes tile 1
+  }
+}
+}  // namespace
+
+}  // namespace lv
+
+extern "C" size_t lv_debug_sort_timeout_workspace_size(void) { return lv::carve_dbg(nullptr).bytes; }
+
+extern "C" lv_status lv_debug_sort_timeout(int32_t spin_limit, void* workspace, size_t ws_bytes, int32_t* d_status,
+                                           void* stream) {
+  using namespace lv;
+  if (spin_limit < 1 || spin_limit > (int32_t)OS_SPIN_LIMIT || !d_status) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  DbgWs w = carve_dbg(workspace);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  SortTmp st = carve_sort(w.tmp, DBG_ITEMS);
+  cudaMemsetAsync(workspace, 0, w.bytes, s);  // keys, counts, tickets and look-back words
+  cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+  k_dbg_setup<<<1, 32, 0, s>>>(w.count, st.ticket);
+  k_os_pass<uint32_t><<<1, Os<uint32_t>::THREADS, 0, s>>>(w.k0, nullptr, w.k1, w.v1, w.count, DBG_ITEMS, 0, st.ghist,
+                                                          st.ticket, st.look[0], st.look[1], d_status,
+                                                          (unsigned)spin_limit);
+  count_launch(2);
+  return cuda_check(cudaGetLastError(), "lv_debug_sort_timeout");
+}
+
+namespace lv {
 
 // ============================================================ grouped select
 namespace {

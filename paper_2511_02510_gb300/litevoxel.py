@@ -115,6 +115,8 @@ SIGNATURES = {
                                  C.POINTER(lv_adam_params), _P, _P, _SZ, _P]),
     "lv_prune_anneal_ppm": (_I32, [C.c_double, C.c_double, C.c_double]),
     "lv_debug_pairs": (C.c_int, [_I64, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _P, _P, _P]),
+    "lv_debug_sort_timeout_workspace_size": (_SZ, []),
+    "lv_debug_sort_timeout": (C.c_int, [C.c_int32, _P, _SZ, _P, _P]),
     "lv_render_pixels_f64": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _I64, _P, _P, _P]),
     "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
     "lv_prune_depth_quantile": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.POINTER(lv_prune_params), _P, _P, _P, _SZ, _P,
@@ -319,6 +321,16 @@ def lv_adam_voxels(density, sh, d_density, d_sh, m_density, v_density, m_sh, v_s
 
 def lv_prune_anneal_ppm(t, t0, t1):
     return int(load().lv_prune_anneal_ppm(float(t), float(t0), float(t1)))
+
+
+def lv_debug_sort_timeout(spin_limit, workspace, status):
+    """One sort pass whose look-back wait can never end: it must give up and report LV_ERR_TIMEOUT."""
+    _check(load().lv_debug_sort_timeout(int(spin_limit), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                        _ptr(status), _stream()), "lv_debug_sort_timeout")
+
+
+def lv_debug_sort_timeout_workspace_size() -> int:
+    return int(load().lv_debug_sort_timeout_workspace_size())
 
 
 def lv_debug_pairs(n, cams_arr, n_views, opts, workspace, pair_capacity, keys=None, voxel=None, ranges=None):
