@@ -185,6 +185,29 @@ lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_view
                          void* workspace, size_t ws_bytes, int64_t pair_capacity, float* d_sh, int accumulate,
                          void* stream);
 
+/* Autotuner of the composite schedule (batched views in one launch: tile
+ * size and scheduling chosen per scene and view set).  Each candidate --
+ * tile edge 8, 16, 32, each with one block per tile and with persistent
+ * warps (LV_FLAG_PERSISTENT) -- runs one warm-up forward + backward and then
+ * `reps` (1 .. 1000) timed ones on the caller's scene and views, timed with
+ * CUDA events on `stream`; the call synchronises the stream.  *best receives
+ * *base with the fastest tile and LV_FLAG_PERSISTENT choice.  ms_out (host
+ * float[6], nullable) receives each candidate's mean forward + backward
+ * time in ms in the order (8, block), (8, persistent), (16, block),
+ * (16, persistent), (32, block), (32, persistent); -1 for a candidate that
+ * needs more than pair_capacity pairs (skipped), and -1 everywhere on a
+ * cache hit.  cache_path (nullable) is a text file of "key tile persistent"
+ * lines keyed by device name, voxel count, view sizes and the other flags:
+ * a hit returns at once, a tuned result is appended.  workspace:
+ * lv_autotune_workspace_size(n, cams, n_views, base, pair_capacity) bytes
+ * (forward workspace for the largest need, outputs and gradients).
+ * LV_ERR_CAPACITY when no candidate fits the pair capacity. */
+size_t lv_autotune_workspace_size(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* base,
+                                  int64_t pair_capacity);
+lv_status lv_autotune(const lv_voxels* vox, const lv_camera* cams, int n_views, const lv_raster_opts* base,
+                      int64_t pair_capacity, int reps, lv_raster_opts* best, float* ms_out, const char* cache_path,
+                      void* workspace, size_t ws_bytes, void* stream);
+
 /* Unpack lv_fwd_out.wmax_packed: w_max[i] (0 if never hit) and the smallest
  * global pixel id attaining it (-1 if never hit).  argmax is nullable. */
 lv_status lv_unpack_wmax(const unsigned long long* packed, int64_t n, float* w_max, int64_t* argmax, void* stream);
@@ -351,6 +374,21 @@ lv_status lv_subdivide_priority(const lv_voxels* in, const float* delta, const f
                                 int64_t* d_n_new, void* workspace, size_t ws_bytes, int32_t* d_status,
                                 void* stream);
 
+/* Stable compaction without a split, e.g. to drop pruned voxels on steps
+ * that do not subdivide.  Rows i with keep[i] != 0 (device [n] u8) are
+ * written in id order to out (geom, level, corner densities, SH, in the
+ * input dtypes) and to every auxiliary array (lv_aux_array.fill unused);
+ * d_n_new (device int64, nullable) receives the number kept.  out->n is the
+ * output capacity: fewer rows than kept sets LV_ERR_CAPACITY in d_status
+ * and writes nothing.  The same as lv_subdivide_priority with no voxel
+ * selected and prune_mask = !keep.  Shared-vertex scenes (in->vidx) are not
+ * supported here (LV_ERR_UNSUPPORTED): pass the per-voxel index rows as an
+ * auxiliary array instead.  workspace: lv_compact_workspace_size(n). */
+size_t lv_compact_workspace_size(int64_t n);
+lv_status lv_compact(const lv_voxels* in, const uint8_t* keep, const lv_aux_array* aux, int n_aux,
+                     const lv_voxels* out, int64_t* d_n_new, void* workspace, size_t ws_bytes, int32_t* d_status,
+                     void* stream);
+
 /* The two halves of lv_subdivide_priority, for callers that want to look at
  * the selection (selected, d_n_new) before the arrays are written, or to time
  * the halves separately.  lv_subdivide_select takes the selection and
@@ -514,6 +552,12 @@ lv_status lv_vertex_scatter_add(const uint32_t* vidx, int64_t n, const float* co
 
 /* Human-readable description of the calling thread's last error ("" if none). */
 const char* lv_last_error(void);
+
+/* Synchronise `stream` and return the status word a call left on the device
+ * (*d_status, an lv_status code; LV_OK when no kernel reported anything).
+ * LV_ERR_CUDA when the copy or the synchronisation fails, or when the word
+ * holds no lv_status code.  The word is not cleared. */
+lv_status lv_check_status(const int32_t* d_status, void* stream);
 
 /* (major << 16) | minor */
 int32_t lv_version(void);

@@ -316,6 +316,18 @@ def subdivide(scene: dict, delta, z, u, seen, prune_mask=None, kappa=1.0, beta=0
     return res
 
 
+def compact(scene: dict, keep, aux=None) -> dict:
+    """Removal of the voxels a step prunes (Sec. IV-C) without a split: the
+    rows with keep != 0, in id order, of the voxel arrays and of every
+    auxiliary array (optimizer moments, EMA state) -- the survivors part of
+    the topology change that subdivide() writes."""
+    k = np.asarray(keep).astype(bool)
+    res = {name: np.ascontiguousarray(np.asarray(scene[name])[k]) for name in ("geom", "level", "density", "sh")}
+    res["aux"] = [np.ascontiguousarray(np.asarray(a)[k]) for a in (aux or [])]
+    res["n_new"] = int(k.sum())
+    return res
+
+
 def lf_gamma(t, t0, t1, gamma_max) -> float:
     return float(lib().ora_lf_gamma(float(t), float(t0), float(t1), float(gamma_max)))
 

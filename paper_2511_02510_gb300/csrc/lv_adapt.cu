@@ -514,6 +514,11 @@ __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
   return __fadd_rn(__fmul_rn(a, __fsub_rn(1.0f, t)), __fmul_rn(b, t));
 }
 
+__global__ void k_cp_flags(int64_t n, const uint8_t* __restrict__ keep, uint32_t* __restrict__ surv) {
+  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i < n) surv[i] = keep[i] ? 1u : 0u;
+}
+
 __global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uint32_t* __restrict__ rank,
                           uint32_t* __restrict__ list) {
   const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
@@ -687,18 +692,26 @@ extern "C" size_t lv_subdivide_workspace_size(int64_t n, const lv_subdiv_params*
   return carve_sub(nullptr, n).bytes;
 }
 
+static lv_status check_arrays(const lv_voxels* in, int n_aux, const lv_aux_array* aux, const lv_voxels* out);
+
 static lv_status check_sub(const lv_voxels* in, const lv_subdiv_params* p, int n_aux, const lv_aux_array* aux,
                            const lv_voxels* out) {
   if (!in || !p) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||
+      p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
+  if (!(p->pct_ema >= 0.f && p->pct_ema <= 1.f)) { set_error("pct_ema must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
+  return check_arrays(in, n_aux, aux, out);
+}
+
+// the voxel, output and auxiliary arrays of a topology change
+static lv_status check_arrays(const lv_voxels* in, int n_aux, const lv_aux_array* aux, const lv_voxels* out) {
+  if (!in) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
   const int64_t n = in->n;
   if (n < 0 || n > 0x7fffffffLL) { set_error("bad voxel count"); return LV_ERR_INVALID_ARG; }
   if (n > 0 && (!in->geom || !in->level || !in->density || !in->sh)) { set_error("null voxel array"); return LV_ERR_INVALID_ARG; }
   if (in->vidx) { set_error("subdivision needs per-voxel corner densities (vidx must be NULL)"); return LV_ERR_UNSUPPORTED; }
   if (in->density_dtype != LV_F32 && in->density_dtype != LV_F16) { set_error("density dtype must be F32 or F16"); return LV_ERR_INVALID_ARG; }
   if (in->sh_dtype != LV_F32 && in->sh_dtype != LV_BF16) { set_error("sh dtype must be F32 or BF16"); return LV_ERR_INVALID_ARG; }
-  if (p->top_ppm < 0 || p->top_ppm > 1000000 || p->lo_ppm < 0 || p->lo_ppm > 1000000 || p->hi_ppm < 0 ||
-      p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
-  if (!(p->pct_ema >= 0.f && p->pct_ema <= 1.f)) { set_error("pct_ema must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
   if (out) {
     if (out->n < 0) { set_error("bad output capacity"); return LV_ERR_INVALID_ARG; }
     if (out->n > 0 && (!out->geom || !out->level || !out->density || !out->sh)) { set_error("null output array"); return LV_ERR_INVALID_ARG; }
@@ -800,4 +813,48 @@ extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* del
                           d_status, stream);
   if (e != LV_OK) return e;
   return lv_subdivide_apply(in, p, aux, n_aux, out, workspace, ws_bytes, stream);
+}
+
+extern "C" size_t lv_compact_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  return carve_sub(nullptr, n).bytes;
+}
+
+extern "C" lv_status lv_compact(const lv_voxels* in, const uint8_t* keep, const lv_aux_array* aux, int n_aux,
+                                const lv_voxels* out, int64_t* d_n_new, void* workspace, size_t ws_bytes,
+                                int32_t* d_status, void* stream) {
+  lv_status e = check_arrays(in, n_aux, aux, out);
+  if (e != LV_OK) return e;
+  if (!out) { set_error("null output"); return LV_ERR_INVALID_ARG; }
+  const int64_t n = in->n;
+  if (n > 0 && !keep) { set_error("null keep mask"); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  SubWs w = carve_sub(workspace, n);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
+    return cuda_check(cudaGetLastError(), "lv_compact");
+  }
+  AuxSet as;
+  as.n = n_aux;
+  for (int a = 0; a < n_aux; ++a) as.a[a] = aux[a];
+  cudaMemsetAsync(w.st, 0, sizeof(SubState), s);
+  const int blocks = blocks_for(n);
+  k_cp_flags<<<blocks, TPB, 0, s>>>(n, keep, w.surv);
+  scan2(w.surv, nullptr, n, w.surv_pos, nullptr, w.totals, w.scan_tmp, s);  // totals[1] = 0: no children
+  k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out->n, d_n_new, d_status);
+  const unsigned grid = (unsigned)((((n + 31) / 32) * 32 + TPB - 1) / TPB);  // one warp per 32 voxels
+#define LV_CP(DT, ST)                                                                                         \
+  k_sd_write<DT, ST><<<grid, TPB, 0, s>>>(n, 0, w.surv, w.surv_pos, w.sel_list, w.totals, w.st,            \
+                                          (const float4*)in->geom, in->level, (const DT*)in->density,       \
+                                          (const ST*)in->sh, (float4*)out->geom, (uint8_t*)out->level,      \
+                                          (DT*)out->density, (ST*)out->sh, as)
+  if (in->density_dtype == LV_F32 && in->sh_dtype == LV_F32) LV_CP(float, float);
+  else if (in->density_dtype == LV_F16 && in->sh_dtype == LV_F32) LV_CP(__half, float);
+  else if (in->density_dtype == LV_F32 && in->sh_dtype == LV_BF16) LV_CP(float, __nv_bfloat16);
+  else LV_CP(__half, __nv_bfloat16);
+#undef LV_CP
+  count_launch(3);
+  return cuda_check(cudaGetLastError(), "lv_compact");
 }

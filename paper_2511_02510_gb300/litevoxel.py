@@ -128,6 +128,12 @@ SIGNATURES = {
                                       _P, _P]),
     "lv_subdivide_apply": (C.c_int, [_PV, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array), C.c_int, _PV, _P,
                                      _SZ, _P]),
+    "lv_compact_workspace_size": (_SZ, [_I64]),
+    "lv_compact": (C.c_int, [_PV, _P, C.POINTER(lv_aux_array), C.c_int, _PV, _P, _P, _SZ, _P, _P]),
+    "lv_check_status": (C.c_int, [_P, _P]),
+    "lv_autotune_workspace_size": (_SZ, [_I64, _PC, C.c_int, _PO, _I64]),
+    "lv_autotune": (C.c_int, [_PV, _PC, C.c_int, _PO, _I64, C.c_int, _PO, C.POINTER(C.c_float), C.c_char_p, _P, _SZ,
+                              _P]),
     "lv_lf_gamma": (_F, [_F, C.POINTER(lv_lf_params)]),
     "lv_lf_workspace_size": (_SZ, [_P, _P, C.c_int]),
     "lv_lf_weighted_loss": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P, _SZ, _P]),
@@ -382,6 +388,37 @@ def lv_subdivide_apply(vin, params, aux, vout, workspace):
     _check(load().lv_subdivide_apply(C.byref(vin), C.byref(params), aux_arr, len(aux), C.byref(vout),
                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
            "lv_subdivide_apply")
+
+
+def lv_compact_workspace_size(n) -> int:
+    return int(load().lv_compact_workspace_size(int(n)))
+
+
+def lv_compact(vin, keep, aux, vout, n_new, workspace, d_status=None):
+    """Rows with keep != 0, in id order, into vout and every auxiliary array."""
+    aux_arr = (lv_aux_array * max(1, len(aux)))(*aux)
+    _check(load().lv_compact(C.byref(vin), _ptr(keep), aux_arr, len(aux), C.byref(vout), _ptr(n_new), _ptr(workspace),
+                             workspace.numel() * workspace.element_size(), _ptr(d_status), _stream()), "lv_compact")
+
+
+def lv_autotune_workspace_size(n, cams_arr, n_views, base, pair_capacity) -> int:
+    return int(load().lv_autotune_workspace_size(int(n), cams_arr, n_views, C.byref(base), int(pair_capacity)))
+
+
+def lv_autotune(vox, cams_arr, n_views, base, pair_capacity, reps, workspace, cache_path=None):
+    """Time every (tile, schedule) candidate; returns (best lv_raster_opts, [6] ms per candidate, -1 = skipped)."""
+    best = lv_raster_opts()
+    ms = (C.c_float * 6)()
+    path = cache_path.encode() if cache_path else None
+    _check(load().lv_autotune(C.byref(vox), cams_arr, n_views, C.byref(base), int(pair_capacity), int(reps),
+                              C.byref(best), ms, path, _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream()), "lv_autotune")
+    return best, [float(x) for x in ms]
+
+
+def lv_check_status(d_status) -> int:
+    """Synchronise the current stream and return the device status word as an lv_status code."""
+    return int(load().lv_check_status(_ptr(d_status), _stream()))
 
 
 def lv_lf_gamma(t, params) -> float:

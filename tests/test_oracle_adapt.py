@@ -320,6 +320,30 @@ def test_subdivide_eligibility(ora):
     assert list(r["selected"]) == [1, 0, 0, 0]
 
 
+def test_compact_is_subdivision_without_splits(ora):
+    """Compaction (removing pruned voxels) equals the C subdivision with no
+    split allowed and prune_mask = !keep, for the voxel and auxiliary arrays."""
+    n = 300
+    sc = _scene_rand(n, 5)
+    rng = np.random.default_rng(5)
+    keep = (rng.uniform(size=n) < 0.7).astype(np.uint8)
+    aux = [rng.normal(size=(n, 8)).astype(np.float32), rng.integers(0, 255, size=n).astype(np.uint8),
+           rng.integers(0, 60000, size=(n, 3)).astype(np.uint16)]
+    c = ora.compact(sc, keep, aux)
+    r = ora.subdivide(sc, np.zeros(n, np.float32), np.ones(n, np.float32), np.ones(n, np.float32),
+                      np.ones(n, np.uint8), prune_mask=1 - keep, top_ppm=0, aux=[(a, 0) for a in aux])
+    assert r["k"] == 0 and c["n_new"] == r["n_new"] == int(keep.sum())
+    for name in ("geom", "level", "density", "sh"):
+        np.testing.assert_array_equal(c[name], r[name])
+    for x, y in zip(c["aux"], r["aux"]):
+        np.testing.assert_array_equal(x, y)
+    # order: the i-th kept row is the i-th index with keep set
+    np.testing.assert_array_equal(c["geom"], np.asarray(sc["geom"])[np.flatnonzero(keep)])
+    # degenerate masks
+    assert ora.compact(sc, np.zeros(n, np.uint8))["n_new"] == 0
+    np.testing.assert_array_equal(ora.compact(sc, np.ones(n, np.uint8))["sh"], sc["sh"])
+
+
 # --------------------------------------------------------------------- LF loss
 
 def test_gamma_schedule(ora):
