@@ -158,7 +158,7 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
 // digits over all items.  Each pass kernel then takes tiles of Os<K>::TILE items
 // in ticket order (an atomic counter, so a tile's predecessors are already
 // running or done), ranks its items by digit in shared memory (a warp-private
-// match_any histogram per warp, stable), publishes its per-digit counts, and
+// histogram per warp, stable ranks from bit ballots), publishes its per-digit counts, and
 // finds the number of items with each digit in all earlier tiles by looking
 // back through their published words (decoupled look-back: a tile that has
 // published its inclusive prefix ends the walk).  A published word packs a
@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
   if (tile == 0 && t == 0) ticket[(pass + 1) & 1] = 0u;  // the next pass's counter (last used two passes ago)
   if (t < RADIX) look_next[tile * RADIX + t] = 0ull;      // and its look-back words
 
+  const uint32_t gcount = t < RADIX ? ghist[pass * RADIX + t] : 0u;  // read early: its latency overlaps the loads
   // ---- load (warp-striped: lane l of warp w holds items w*256 + j*32 + l)
   const int64_t base = tile * OS_TILE;
   const int m = (int)min((int64_t)OS_TILE, n - base);
@@ -331,14 +332,22 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
     }
   }
   // ---- digit base of this pass: exclusive scan of the global counts
-  const uint32_t gbase = os_block_excl<OS_WARPS>(t < RADIX ? ghist[pass * RADIX + t] : 0u, s_w[0]);
+  const uint32_t gbase = os_block_excl<OS_WARPS>(gcount, s_w[0]);
 
   // ---- stable rank inside each warp (items in j-major, lane-minor order)
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int j = 0; j < OS_ITEMS; ++j) {
     const uint32_t d = dr[j];
-    const uint32_t peers = __match_any_sync(FULL, d);
+    // lanes holding the same digit: eight bit ballots intersected (cheaper
+    // here than __match_any_sync, which the profile showed as the bottleneck)
+    const uint32_t valid = __ballot_sync(FULL, d < RADIX);
+    uint32_t peers = d < RADIX ? valid : ~valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t m = __ballot_sync(FULL, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? m : ~m;
+    }
     const uint32_t cur = s_wh[warp][d];
     dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
     __syncwarp();
@@ -607,9 +616,9 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
 }
 
 // Histogram of the current digit (bits [shift, shift + width)) of every item
-// whose bits above the digit match its query's prefix.  Lanes of a warp that
-// add to the same (query, digit) bin combine first (__match_any_sync), so
-// clustered keys do not serialise on one bin.  When
+// whose bits above the digit match its query's prefix, by shared-memory
+// atomics (combining the lanes of a bin first with __match_any_sync measured
+// slower: the match costs more than the serialised atomics it saves).  When
 // every query is in group 0 (at most two queries) a lean per-item path runs;
 // otherwise queries of a group are contiguous, at most two per group.
 template <int RADIX>
@@ -638,7 +647,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int top = shift + width;
   const uint32_t hi_mask = top >= 32 ? 0u : (0xffffffffu << top);
   const uint32_t dmask = (1u << width) - 1u;
@@ -660,15 +668,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
         const bool in = gv[u] == 0;
         const uint32_t key = kv[u], hk = key & hi_mask, d = (key >> shift) & dmask;
         int h = (in && k0 != 0 && hk == p0) ? (int)d : -1;
-        if (__any_sync(FULL, h >= 0)) {
-          const uint32_t peers = __match_any_sync(FULL, h);
-          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
-        }
+        if (h >= 0) atomicAdd(&sh[h], 1u);
         h = (in && k1 != 0 && hk == p1) ? RADIX + (int)d : -1;
-        if (__any_sync(FULL, h >= 0)) {
-          const uint32_t peers = __match_any_sync(FULL, h);
-          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
-        }
+        if (h >= 0) atomicAdd(&sh[h], 1u);
       }
     }
   } else {
@@ -692,10 +694,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, 
             const int j = qfirst[g] + a;
             if (sq[j].k != 0 && (key & hi_mask) == sq[j].prefix) h = j * RADIX + (int)d;
           }
-          // after the first digit most items miss their query's prefix: whole warps skip the match
-          if (!__any_sync(FULL, h >= 0)) continue;
-          const uint32_t peers = __match_any_sync(FULL, h);
-          if (h >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[h], (uint32_t)__popc(peers));
+          if (h >= 0) atomicAdd(&sh[h], 1u);
         }
       }
     }

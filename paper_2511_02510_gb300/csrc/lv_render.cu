@@ -376,11 +376,15 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const uint32_t* __restrict__ slot, float4* __restrict__ rec,
                                               float4* __restrict__ d_rgb, uint4* __restrict__ s_tiles,
                                               uint32_t* __restrict__ s_dkey, const uint32_t* __restrict__ vidx) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n * vs.n) return;
+  // Block b covers 256 consecutive voxels of view b % views, so the blocks of
+  // all views of one voxel range run side by side: a voxel's SH row comes
+  // from HBM once and from L2 for its other views.  Items are view-major
+  // (i = view * n + voxel), so each block still writes consecutive slots.
+  const int view = (int)(blockIdx.x % (unsigned)vs.n);
+  const int64_t vox = (int64_t)(blockIdx.x / (unsigned)vs.n) * 256 + threadIdx.x;
+  if (vox >= n) return;
+  const int64_t i = (int64_t)view * n + vox;
   if (!vis[i]) return;
-  const int view = (int)(i / n);  // view-major items
-  const int64_t vox = i - (int64_t)view * n;
   const DevView& c = vs.v[view];
   uint32_t s = slot[i];
   float4 g = geom[vox];
@@ -1349,14 +1353,15 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   if (!d_status || d_status == w.status) cudaMemsetAsync(w.status, 0, sizeof(int32_t), s);
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
+    const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
     k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.dkey, out->z_min,
                                  out->delta_min, out->seen);
     scan2(w.cnt, w.vis, items, nullptr, w.slot, w.counters, w.scan_tmp, s);
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
-#define LV_EMIT(DT, ST)                                                                                               \
-  k_emit<DT, ST><<<blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, nb, n, \
-                                        vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey, w.slot,      \
-                                        w.rec, w.d_rgb, w.s_tiles, w.s_dkey, vox->vidx)
+#define LV_EMIT(DT, ST)                                                                                             \
+  k_emit<DT, ST><<<emit_blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, \
+                                             nb, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey,   \
+                                             w.slot, w.rec, w.d_rgb, w.s_tiles, w.s_dkey, vox->vidx)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
