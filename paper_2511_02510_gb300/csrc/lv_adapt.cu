@@ -17,6 +17,86 @@ inline int blocks_for(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// The per-voxel kernels give each thread IPT consecutive voxels (block b owns
+// voxels [b EB, (b + 1) EB)), issue all the thread's loads before its stores,
+// and combine counts once per block.  Thread order then equals id order
+// inside a block, which the tie ranks rely on.
+constexpr int IPT = 4;
+constexpr int EB = TPB * IPT;
+inline int eblocks(int64_t n) {
+  int64_t b = (n + EB - 1) / EB;
+  return (int)(b < 1 ? 1 : b);
+}
+__device__ __forceinline__ int64_t first_item() { return blockIdx.x * (int64_t)EB + (int64_t)threadIdx.x * IPT; }
+
+// A thread's IPT (= 4) consecutive elements in one 4-, 8- or 16-byte access
+// when they are all in range and the array is aligned for it, else one by one
+// (out-of-range elements read as `fill`, are not written).
+template <typename T> struct Vec4T;
+template <> struct Vec4T<uint8_t> { using V = uchar4; };
+template <> struct Vec4T<uint16_t> { using V = ushort4; };
+template <> struct Vec4T<uint32_t> { using V = uint4; };
+template <> struct Vec4T<float> { using V = float4; };
+static_assert(IPT == 4, "the vector accesses move four elements");
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ p, int64_t i0, int64_t n, T* v, T fill) {
+  using V = typename Vec4T<T>::V;
+  if (i0 + 3 < n && ((uintptr_t)p & (sizeof(V) - 1)) == 0) {
+    const V q = *(const V*)(p + i0);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = i0 + u < n ? p[i0 + u] : fill;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* __restrict__ p, int64_t i0, int64_t n, const T* v) {
+  using V = typename Vec4T<T>::V;
+  if (i0 + 3 < n && ((uintptr_t)p & (sizeof(V) - 1)) == 0) {
+    V q;
+    q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3];
+    *(V*)(p + i0) = q;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n) p[i0 + u] = v[u];
+  }
+}
+
+// sum of one count per thread over the block (every thread calls; all get it)
+__device__ __forceinline__ uint32_t block_total(uint32_t c) {
+  __shared__ uint32_t s_part[TPB / 32];
+  c = __reduce_add_sync(FULL, c);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  uint32_t t = 0;
+#pragma unroll
+  for (int w = 0; w < TPB / 32; ++w) t += s_part[w];
+  __syncthreads();  // s_part is reused by the next call
+  return t;
+}
+
+// exclusive prefix of one count per thread, in thread order (every thread calls)
+__device__ __forceinline__ uint32_t block_excl_count(uint32_t c) {
+  __shared__ uint32_t s_part[TPB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_part[warp] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+#pragma unroll
+  for (int w = 0; w < TPB / 32; ++w) pre += w < warp ? s_part[w] : 0u;
+  __syncthreads();
+  return pre + x - c;
+}
+
 __device__ __forceinline__ float key_to_float(uint32_t k) {
   uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
   return __uint_as_float(u);
@@ -78,17 +158,28 @@ PruneWs carve_prune(void* base, int64_t n) {
 __global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z,
                           const float* __restrict__ w_max, uint16_t* grp, uint32_t* zkey, uint32_t* wkey,
                           PruneState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool s = false;
-  if (i < n) {
-    s = seen[i] != 0;
-    grp[i] = s ? 0 : GROUP_NONE;
-    zkey[i] = order_key(z[i]);
-    wkey[i] = order_key(w_max[i]);
+  const int64_t i0 = first_item();
+  uint8_t sv[IPT];
+  float zv[IPT], wv[IPT];
+  load4(seen, i0, n, sv, (uint8_t)0);
+  load4(z, i0, n, zv, 0.f);
+  load4(w_max, i0, n, wv, 0.f);
+  uint16_t gv[IPT];
+  uint32_t zk[IPT], wk[IPT];
+  uint32_t c = 0;
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    gv[u] = sv[u] ? 0 : GROUP_NONE;
+    zk[u] = order_key(zv[u]);
+    wk[u] = order_key(wv[u]);
+    c += sv[u] ? 1u : 0u;  // padding reads 0
   }
+  store4(grp, i0, n, gv);
+  store4(zkey, i0, n, zk);
+  store4(wkey, i0, n, wk);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int b = __syncthreads_count(s);
-  if (threadIdx.x == 0 && b) atomicAdd(&st->ns, (unsigned)b);
+  const uint32_t b = block_total(c);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->ns, b);
 }
 
 __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm) {
@@ -129,12 +220,18 @@ __global__ void k_pr_bin(int64_t n, const uint8_t* __restrict__ seen, const floa
   if (threadIdx.x < SELECT_MAX_QUERIES) sh[threadIdx.x] = 0;
   __syncthreads();
   const float p_lo = st->p_lo, p_hi = st->p_hi;
-  for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
-    if (!seen[i]) continue;
-    const float zt = depth_norm(z[i], p_lo, p_hi);
+  const int64_t i0 = first_item();
+  uint8_t sv[IPT];
+  float zv[IPT];
+  load4(seen, i0, n, sv, (uint8_t)0);
+  load4(z, i0, n, zv, 0.f);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    if (!sv[u]) continue;  // padding reads 0
+    const float zt = depth_norm(zv[u], p_lo, p_hi);
     int b = (int)floorf(__fmul_rn((float)nb, zt));
     if (b > nb - 1) b = nb - 1;
-    grp[i] = (uint16_t)b;
+    grp[i0 + u] = (uint16_t)b;
     atomicAdd(&sh[b], 1u);
   }
   __syncthreads();
@@ -176,30 +273,49 @@ struct Halo {
 __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const uint32_t* __restrict__ wkey,
                             const SelectQuery* tau, float alpha, float oma, float m_low, float m_high, float* ema_m,
                             uint8_t* state, const Halo halo, uint8_t* mask, uint16_t* cand_grp, PruneState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool cand = false;
-  if (i < n) {
-    uint16_t b = grp[i];
+  const int64_t i0 = first_item();
+  uint16_t gv[IPT];
+  uint32_t kv[IPT];
+  float mv[IPT];
+  uint8_t stv[IPT];
+  load4(grp, i0, n, gv, GROUP_NONE);
+  load4(wkey, i0, n, kv, 0u);
+  load4((const float*)ema_m, i0, n, mv, 0.f);
+  load4((const uint8_t*)state, i0, n, stv, (uint8_t)0);
+  uint16_t cg[IPT];
+  uint8_t mk[IPT];
+  uint32_t c = 0;
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const int64_t i = i0 + u;
+    bool cand = false;
+    const uint16_t b = gv[u];  // padding reads GROUP_NONE
     if (b != GROUP_NONE) {
       const uint32_t t = tau[b].result;
-      const float x = (t == 0xffffffffu || wkey[i] > t) ? 1.f : 0.f;  // no threshold: votes in
-      const float m = __fadd_rn(__fmul_rn(oma, ema_m[i]), __fmul_rn(alpha, x));
-      ema_m[i] = m;
-      uint8_t s = state[i];
+      const float x = (t == 0xffffffffu || kv[u] > t) ? 1.f : 0.f;  // no threshold: votes in
+      const float m = __fadd_rn(__fmul_rn(oma, mv[u]), __fmul_rn(alpha, x));
+      mv[u] = m;
+      uint8_t s = stv[u];
       if (m < m_low) s = 0;
       else if (m > m_high) s = 1;
-      state[i] = s;
+      stv[u] = s;
       bool prot = false;
       if (halo.small > 0.f && halo.geom && halo.delta) prot = halo.geom[i].w < __fmul_rn(halo.small, halo.delta[i]);
       if (halo.edge_score) prot = prot || (halo.w_max[i] >= halo.w && halo.edge_score[i] >= halo.edge);
       cand = s == 0 && !prot;
     }
-    cand_grp[i] = cand ? 0 : GROUP_NONE;
-    mask[i] = cand ? 1 : 0;
+    cg[u] = cand ? 0 : GROUP_NONE;
+    mk[u] = cand ? 1 : 0;
+    c += cand ? 1u : 0u;
   }
+  // unseen voxels keep their EMA and state: the stores write their loaded values back
+  store4(ema_m, i0, n, mv);
+  store4(state, i0, n, stv);
+  store4(cand_grp, i0, n, cg);
+  store4(mask, i0, n, mk);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int bl = __syncthreads_count(cand);
-  if (threadIdx.x == 0 && bl) atomicAdd(&st->n_cand, (unsigned)bl);
+  const uint32_t bl = block_total(c);
+  if (threadIdx.x == 0 && bl) atomicAdd(&st->n_cand, bl);
 }
 
 __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
@@ -214,19 +330,28 @@ __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
 // (the ties compete by id: the need = cap - c_lt smallest ids among them go)
 __global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
                           const uint8_t* __restrict__ cand, uint32_t* blk, PruneState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool lt = false, eq = false;
-  if (i < n && cand[i] && thr[0].k != 0) {
+  const int64_t i0 = first_item();
+  uint32_t clt = 0, ceq = 0;
+  if (thr[0].k != 0) {
     const uint32_t v = thr[0].result;
-    lt = wkey[i] < v;
-    eq = wkey[i] == v;
+    uint8_t cv[IPT];
+    uint32_t kv[IPT];
+    load4(cand, i0, n, cv, (uint8_t)0);
+    load4(wkey, i0, n, kv, 0u);
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      if (!cv[u]) continue;  // padding reads 0
+      const uint32_t k = kv[u];
+      clt += k < v ? 1u : 0u;
+      ceq += k == v ? 1u : 0u;
+    }
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int bl = __syncthreads_count(lt);
-  const int be = __syncthreads_count(eq);
+  const uint32_t bl = block_total(clt);
+  const uint32_t be = block_total(ceq);
   if (threadIdx.x == 0) {
-    if (bl) atomicAdd(&st->c_lt, (unsigned)bl);
-    blk[blockIdx.x] = (uint32_t)be;
+    if (bl) atomicAdd(&st->c_lt, bl);
+    blk[blockIdx.x] = be;
   }
 }
 
@@ -236,21 +361,36 @@ __global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const Se
 __global__ void k_pr_mask(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
                           const uint32_t* __restrict__ blk_off, const PruneState* st, uint8_t* mask,
                           int64_t* n_pruned, uint32_t cap) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  const bool c = i < n && mask[i];
-  bool lt = false, eq = false;
-  if (c && !st->all && thr[0].k != 0) {
-    const uint32_t v = thr[0].result;
-    lt = wkey[i] < v;
-    eq = wkey[i] == v;
+  const int64_t i0 = first_item();
+  const bool all = st->all != 0;
+  const bool thr_ok = thr[0].k != 0;
+  const uint32_t v = thr[0].result;
+  bool lt[IPT], eq[IPT];
+  uint8_t c[IPT];
+  uint32_t kv[IPT];
+  uint32_t ceq = 0;
+  load4((const uint8_t*)mask, i0, n, c, (uint8_t)0);
+  load4(wkey, i0, n, kv, 0u);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    lt[u] = eq[u] = false;
+    if (c[u] && !all && thr_ok) {  // padding reads 0
+      lt[u] = kv[u] < v;
+      eq[u] = kv[u] == v;
+    }
+    ceq += eq[u] ? 1u : 0u;
   }
-  const uint32_t r = block_excl_rank(eq);  // every thread of the block takes part
-  if (i < n) {
-    const uint32_t need = cap > st->c_lt ? cap - st->c_lt : 0u;
-    const bool p = c && (st->all || lt || (eq && blk_off[blockIdx.x] + r < need));
-    mask[i] = p ? 1 : 0;
+  uint32_t r = block_excl_count(ceq) + blk_off[blockIdx.x];  // every thread of the block takes part
+  const uint32_t need = cap > st->c_lt ? cap - st->c_lt : 0u;
+  uint8_t out[IPT];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const bool p = c[u] && (all || lt[u] || (eq[u] && r < need));
+    r += eq[u] ? 1u : 0u;
+    out[u] = p ? 1 : 0;
   }
-  if (i == 0 && n_pruned) *n_pruned = st->all ? (int64_t)st->n_cand : (int64_t)cap;
+  store4(mask, i0, n, out);
+  if (i0 == 0 && n_pruned) *n_pruned = all ? (int64_t)st->n_cand : (int64_t)cap;
 }
 
 // ------------------------------------------------------------------ subdivision
@@ -305,16 +445,27 @@ SubWs carve_sub(void* base, int64_t n) {
 
 __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
                            const float* __restrict__ z, uint16_t* grp, uint32_t* zkey, SubState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool alive = false;
-  if (i < n) {
-    alive = pm ? pm[i] == 0 : true;
-    grp[i] = (alive && seen[i]) ? 0 : GROUP_NONE;
-    zkey[i] = order_key(z[i]);
+  const int64_t i0 = first_item();
+  uint8_t pv[IPT] = {0, 0, 0, 0}, sv[IPT];
+  float zv[IPT];
+  if (pm) load4(pm, i0, n, pv, (uint8_t)0);
+  load4(seen, i0, n, sv, (uint8_t)0);
+  load4(z, i0, n, zv, 0.f);
+  uint16_t gv[IPT];
+  uint32_t zk[IPT];
+  uint32_t c = 0;
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const bool alive = pv[u] == 0;
+    gv[u] = (alive && sv[u]) ? 0 : GROUP_NONE;
+    zk[u] = order_key(zv[u]);
+    c += (alive && i0 + u < n) ? 1u : 0u;
   }
+  store4(grp, i0, n, gv);
+  store4(zkey, i0, n, zk);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int b = __syncthreads_count(alive);
-  if (threadIdx.x == 0 && b) atomicAdd(&st->n_alive, (unsigned)b);
+  const uint32_t b = block_total(c);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->n_alive, b);
 }
 
 __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter) {
@@ -331,11 +482,15 @@ __global__ void k_sd_pct_apply(const SelectQuery* pct, SubState* st, const uint3
 }
 
 __global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, uint32_t* counter) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool f = i < n && grp[i] == 0;
+  const int64_t i0 = first_item();
+  uint16_t gv[IPT];
+  load4(grp, i0, n, gv, GROUP_NONE);
+  uint32_t c = 0;
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) c += gv[u] == 0 ? 1u : 0u;
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int b = __syncthreads_count(f);
-  if (threadIdx.x == 0 && b) atomicAdd(counter, (unsigned)b);
+  const uint32_t b = block_total(c);
+  if (threadIdx.x == 0 && b) atomicAdd(counter, b);
 }
 
 // Eq. 13 eligibility and Eq. 15-16 priority; pkey orders by descending priority
@@ -343,24 +498,41 @@ __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const 
                               const float* __restrict__ delta, const float* __restrict__ z,
                               const float* __restrict__ u, float kappa, float beta, int l_max, uint16_t* grp,
                               uint32_t* pkey, SubState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool el = false;
-  if (i < n) {
-    if (grp[i] == 0 && (int)level[i] < l_max) {
-      const float thr = __fmul_rn(kappa, delta[i]);
+  const int64_t i0 = first_item();
+  const float p_lo = st->p_lo, p_hi = st->p_hi;
+  uint16_t gv[IPT];
+  uint8_t lv[IPT];
+  float dv[IPT], zv[IPT], uv[IPT];
+  load4((const uint16_t*)grp, i0, n, gv, GROUP_NONE);
+  load4(level, i0, n, lv, (uint8_t)0);
+  load4(delta, i0, n, dv, 0.f);
+  load4(z, i0, n, zv, 0.f);
+  load4(u, i0, n, uv, 0.f);
+  uint32_t pk[IPT];
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int64_t i = i0 + k;
+    bool el = false;
+    pk[k] = 0xffffffffu;  // read only for eligible voxels
+    if (gv[k] == 0 && (int)lv[k] < l_max) {  // padding reads GROUP_NONE
+      const float thr = __fmul_rn(kappa, dv[k]);
       if (geom[i].w > thr) {
         el = true;
-        const float zt = depth_norm(z[i], st->p_lo, st->p_hi);
+        const float zt = depth_norm(zv[k], p_lo, p_hi);
         const float b = __fadd_rn(1.0f, __fmul_rn(beta, zt));
-        const float p = __fmul_rn(u[i], b);
-        pkey[i] = ~order_key(p);
+        const float p = __fmul_rn(uv[k], b);
+        pk[k] = ~order_key(p);
       }
     }
-    grp[i] = el ? 0 : GROUP_NONE;
+    gv[k] = el ? 0 : GROUP_NONE;
+    c += el ? 1u : 0u;
   }
+  store4(pkey, i0, n, pk);
+  store4(grp, i0, n, gv);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int b = __syncthreads_count(el);
-  if (threadIdx.x == 0 && b) atomicAdd(&st->n_el, (unsigned)b);
+  const uint32_t b = block_total(c);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->n_el, b);
 }
 
 __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget) {
@@ -380,18 +552,28 @@ __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long
 // (the ties compete by id: the need = k - c_gt smallest ids among them split)
 __global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const SelectQuery* thr,
                           const uint16_t* __restrict__ grp, uint32_t* blk, SubState* st) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  bool gt = false, eq = false;
-  if (i < n && grp[i] == 0 && thr->k != 0) {
-    gt = pkey[i] < thr->result;
-    eq = pkey[i] == thr->result;
+  const int64_t i0 = first_item();
+  uint32_t cgt = 0, ceq = 0;
+  if (thr->k != 0) {
+    const uint32_t v = thr->result;
+    uint16_t gv[IPT];
+    uint32_t kv[IPT];
+    load4(grp, i0, n, gv, GROUP_NONE);
+    load4(pkey, i0, n, kv, 0u);
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      if (gv[u] != 0) continue;  // padding reads GROUP_NONE
+      const uint32_t k = kv[u];
+      cgt += k < v ? 1u : 0u;
+      ceq += k == v ? 1u : 0u;
+    }
   }
   // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const int bg = __syncthreads_count(gt);
-  const int be = __syncthreads_count(eq);
+  const uint32_t bg = block_total(cgt);
+  const uint32_t be = block_total(ceq);
   if (threadIdx.x == 0) {
-    if (bg) atomicAdd(&st->c_gt, (unsigned)bg);
-    blk[blockIdx.x] = (uint32_t)be;
+    if (bg) atomicAdd(&st->c_gt, bg);
+    blk[blockIdx.x] = be;
   }
 }
 
@@ -401,22 +583,41 @@ __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uin
                             const uint32_t* __restrict__ pkey, const SelectQuery* q,
                             const uint32_t* __restrict__ blk_off, const SubState* st, uint8_t* selected,
                             uint32_t* surv, uint32_t* sel) {
-  int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  const bool el = i < n && grp[i] == 0 && q[2].k != 0;
-  bool gt = false, eq = false;
-  if (el) {
-    const uint32_t v = q[2].result;
-    gt = pkey[i] < v;
-    eq = pkey[i] == v;
+  const int64_t i0 = first_item();
+  const bool any_k = q[2].k != 0;
+  const uint32_t v = q[2].result;
+  bool gt[IPT], eq[IPT];
+  uint8_t pv[IPT] = {0, 0, 0, 0};
+  uint16_t gv[IPT];
+  uint32_t kv[IPT];
+  uint32_t ceq = 0;
+  if (pm) load4(pm, i0, n, pv, (uint8_t)0);
+  load4(grp, i0, n, gv, GROUP_NONE);
+  load4(pkey, i0, n, kv, 0u);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    gt[u] = eq[u] = false;
+    if (any_k && gv[u] == 0) {  // padding reads GROUP_NONE
+      gt[u] = kv[u] < v;
+      eq[u] = kv[u] == v;
+    }
+    ceq += eq[u] ? 1u : 0u;
   }
-  const uint32_t r = block_excl_rank(eq);  // every thread of the block takes part
-  if (i >= n) return;
+  uint32_t r = block_excl_count(ceq) + blk_off[blockIdx.x];  // every thread of the block takes part
   const uint32_t need = st->k > st->c_gt ? st->k - st->c_gt : 0u;
-  const bool s = gt || (eq && blk_off[blockIdx.x] + r < need);
-  const bool alive = pm ? pm[i] == 0 : true;
-  selected[i] = s ? 1 : 0;
-  sel[i] = s ? 1u : 0u;
-  surv[i] = (alive && !s) ? 1u : 0u;
+  uint8_t so[IPT];
+  uint32_t sl[IPT], sv[IPT];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const bool s = gt[u] || (eq[u] && r < need);
+    r += eq[u] ? 1u : 0u;
+    so[u] = s ? 1 : 0;
+    sl[u] = s ? 1u : 0u;
+    sv[u] = (pv[u] == 0 && !s) ? 1u : 0u;
+  }
+  store4(selected, i0, n, so);
+  store4(sel, i0, n, sl);
+  store4(surv, i0, n, sv);
 }
 
 __global__ void k_sd_check(const unsigned long long* totals, SubState* st, int64_t capacity, int64_t* n_new,
@@ -653,14 +854,14 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   const uint32_t cap = (uint32_t)(((unsigned long long)p->cap_ppm * (unsigned long long)n) / 1000000ull);
   const float alpha = p->ema_alpha;
   const float oma = 1.0f - alpha;  // rounded to FP32 once, as the oracle does
-  const int blocks = blocks_for(n);
+  const int blocks = eblocks(n);  // IPT voxels per thread
   cudaMemsetAsync(w.st, 0, sizeof(PruneState), s);
   k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w_max, w.grp, w.zkey, w.wkey, w.st);
   k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
   const float r = p->pct_ema, omr = 1.0f - r;  // rounded to FP32 once, as the oracle does
   k_pr_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, r, omr);
-  k_pr_bin<<<blocks < 1216 ? blocks : 1216, TPB, 0, s>>>(n, seen, z, nb, w.grp, w.st);
+  k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, nb, w.grp, w.st);
   // the percentiles in q[0..1] are consumed: q is reused per bin
   k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal,
                                                     (uint32_t)p->anneal_ppm, (uint32_t)p->relax_ppm);
@@ -746,7 +947,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
     if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
     return cuda_check(cudaGetLastError(), "lv_subdivide_select");
   }
-  const int blocks = blocks_for(n);
+  const int blocks = eblocks(n);  // IPT voxels per thread
   k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st);
   uint32_t* cnt_seen = &w.st->n_el;  // temporarily counts alive & seen voxels
   k_sd_count_group0<<<blocks, TPB, 0, s>>>(n, w.grp, cnt_seen);
@@ -763,7 +964,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
-  k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
+  k_sd_list<<<blocks_for(n), TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
   count_launch(13);
   return cuda_check(cudaGetLastError(), "lv_subdivide_select");
 }
