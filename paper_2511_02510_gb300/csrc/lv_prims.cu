@@ -176,6 +176,7 @@ constexpr unsigned long long OS_FLAG_INC = 2ull << 62;
 constexpr unsigned long long OS_VALUE = (1ull << 62) - 1;
 constexpr unsigned OS_SPIN_LIMIT = 1u << 20;     // polls per look-back walk before giving up
 constexpr int OS_LOOK_WINDOW = 8;                // earlier tiles' words loaded together
+constexpr float OS_MATCH_BELOW = 6.f;            // expected distinct digits per warp below which match_any ranks
 constexpr int OS_HIST_THREADS = 256;
 
 // Tile shape of the pass kernel: 512 threads (4096 items) for 32-bit keys,
@@ -333,26 +334,59 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
   }
   // ---- digit base of this pass: exclusive scan of the global counts
   const uint32_t gbase = os_block_excl<OS_WARPS>(gcount, s_w[0]);
+  // Expected number of distinct digits among 32 items of this pass, from the
+  // global counts: sum over digits of 1 - (1 - p_d)^32.  __match_any_sync
+  // finds the lanes of a digit fastest when a warp holds few distinct digits
+  // (clustered keys such as the high bytes of depths); eight bit ballots cost
+  // the same for any keys and win when they are spread.
+  bool use_match;
+  {
+    __shared__ float s_e[OS_WARPS];
+    float q = t < RADIX ? 1.f - (float)gcount / (float)n : 1.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q *= q;  // (1 - p)^32
+    float e = 1.f - q;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+    if (lane == 0) s_e[warp] = e;
+    __syncthreads();
+    float tot = 0.f;
+#pragma unroll
+    for (int w = 0; w < OS_WARPS; ++w) tot += s_e[w];
+    use_match = tot < OS_MATCH_BELOW;  // block-uniform
+  }
 
   // ---- stable rank inside each warp (items in j-major, lane-minor order)
   const uint32_t lt_mask = (1u << lane) - 1u;
+  if (use_match) {
 #pragma unroll
-  for (int j = 0; j < OS_ITEMS; ++j) {
-    const uint32_t d = dr[j];
-    // lanes holding the same digit: eight bit ballots intersected (cheaper
-    // here than __match_any_sync, which the profile showed as the bottleneck)
-    const uint32_t valid = __ballot_sync(FULL, d < RADIX);
-    uint32_t peers = d < RADIX ? valid : ~valid;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const uint32_t m = __ballot_sync(FULL, (d >> b) & 1u);
-      peers &= ((d >> b) & 1u) ? m : ~m;
+    for (int j = 0; j < OS_ITEMS; ++j) {
+      const uint32_t d = dr[j];
+      const uint32_t peers = __match_any_sync(FULL, d);
+      const uint32_t cur = s_wh[warp][d];
+      dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
+      __syncwarp();
+      if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
+      __syncwarp();
     }
-    const uint32_t cur = s_wh[warp][d];
-    dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
-    __syncwarp();
-    if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
-    __syncwarp();
+  } else {
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {
+      const uint32_t d = dr[j];
+      // lanes holding the same digit: eight bit ballots intersected
+      const uint32_t valid = __ballot_sync(FULL, d < RADIX);
+      uint32_t peers = d < RADIX ? valid : ~valid;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const uint32_t m = __ballot_sync(FULL, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? m : ~m;
+      }
+      const uint32_t cur = s_wh[warp][d];
+      dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
+      __syncwarp();
+      if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
+      __syncwarp();
+    }
   }
   __syncthreads();
   // ---- per digit: warp prefixes and the tile count, published at once

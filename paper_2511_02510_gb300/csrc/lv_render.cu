@@ -369,7 +369,7 @@ template <typename DT, typename ST>
 __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, const DT* __restrict__ dens,
                                               const ST* __restrict__ sh, int sh_nb, int64_t n,
                                               const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ cnt,
-                                              const uint32_t* __restrict__ vis, const uint2* __restrict__ rect,
+                                              const uint2* __restrict__ rect,
                                               const uint2* __restrict__ pbox, uint2* __restrict__ rec_bb,
                                               uint32_t* __restrict__ slot_vox,
                                               const uint32_t* __restrict__ dkey,
@@ -384,11 +384,12 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   const int64_t vox = (int64_t)(blockIdx.x / (unsigned)vs.n) * 256 + threadIdx.x;
   if (vox >= n) return;
   const int64_t i = (int64_t)view * n + vox;
-  if (!vis[i]) return;
+  const uint32_t cn = cnt[i];  // nonzero exactly for the visible items
+  if (!cn) return;
   const DevView& c = vs.v[view];
-  uint32_t s = slot[i];
-  float4 g = geom[vox];
-  float rx = g.x - c.o[0], ry = g.y - c.o[1], rz = g.z - c.o[2];
+  const uint32_t s = slot[i];
+  const float4 g = geom[vox];
+  const float rx = g.x - c.o[0], ry = g.y - c.o[1], rz = g.z - c.o[2];
   float dir[3];
   unit_dir(rx, ry, rz, dir);
   float Y[16];
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                          (float)((raw[0] > 0.f ? 1 : 0) | (raw[1] > 0.f ? 2 : 0) | (raw[2] > 0.f ? 4 : 0)));
   rec_bb[s] = pbox[i];
   const uint2 rc = rect[i];
-  s_tiles[s] = make_uint4(rc.x, rc.y, (uint32_t)view, cnt[i]);
+  s_tiles[s] = make_uint4(rc.x, rc.y, (uint32_t)view, cn);
   s_dkey[s] = dkey[i];
 }
 
@@ -1360,7 +1361,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                             \
   k_emit<DT, ST><<<emit_blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, \
-                                             nb, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey,   \
+                                             nb, n, vs, w.cnt, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey,          \
                                              w.slot, w.rec, w.d_rgb, w.s_tiles, w.s_dkey, vox->vidx)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
