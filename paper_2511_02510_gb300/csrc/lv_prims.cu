@@ -177,6 +177,7 @@ constexpr unsigned long long OS_VALUE = (1ull << 62) - 1;
 constexpr unsigned OS_SPIN_LIMIT = 1u << 20;     // polls per look-back walk before giving up
 constexpr int OS_LOOK_WINDOW = 8;                // earlier tiles' words loaded together
 constexpr float OS_MATCH_BELOW = 6.f;            // expected distinct digits per warp below which match_any ranks
+constexpr int OS_MATCH_MAX_GROUPS = 16;          // distinct digits in a warp's round up to which match_any ranks next
 constexpr int OS_HIST_THREADS = 256;
 
 // Tile shape of the pass kernel: 512 threads (4096 items) for 32-bit keys,
@@ -357,36 +358,34 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
   }
 
   // ---- stable rank inside each warp (items in j-major, lane-minor order)
+  // The histogram's guess starts each warp off; after every round the warp
+  // switches by the number of distinct digits that round held, since
+  // neighbouring items are often alike (pairs of one voxel, depths of nearby
+  // voxels) in ways the global counts do not show.
   const uint32_t lt_mask = (1u << lane) - 1u;
-  if (use_match) {
 #pragma unroll
-    for (int j = 0; j < OS_ITEMS; ++j) {
-      const uint32_t d = dr[j];
-      const uint32_t peers = __match_any_sync(FULL, d);
-      const uint32_t cur = s_wh[warp][d];
-      dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
-      __syncwarp();
-      if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
-      __syncwarp();
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < OS_ITEMS; ++j) {
-      const uint32_t d = dr[j];
+  for (int j = 0; j < OS_ITEMS; ++j) {
+    const uint32_t d = dr[j];
+    uint32_t peers;
+    if (use_match) {  // warp-uniform
+      peers = __match_any_sync(FULL, d);
+    } else {
       // lanes holding the same digit: eight bit ballots intersected
       const uint32_t valid = __ballot_sync(FULL, d < RADIX);
-      uint32_t peers = d < RADIX ? valid : ~valid;
+      peers = d < RADIX ? valid : ~valid;
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const uint32_t m = __ballot_sync(FULL, (d >> b) & 1u);
         peers &= ((d >> b) & 1u) ? m : ~m;
       }
-      const uint32_t cur = s_wh[warp][d];
-      dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
-      __syncwarp();
-      if ((peers & lt_mask) == 0) s_wh[warp][d] = cur + __popc(peers);
-      __syncwarp();
     }
+    const bool leader = (peers & lt_mask) == 0;
+    use_match = __popc(__ballot_sync(FULL, leader)) <= OS_MATCH_MAX_GROUPS;
+    const uint32_t cur = s_wh[warp][d];
+    dr[j] = d | ((cur + __popc(peers & lt_mask)) << 9);
+    __syncwarp();
+    if (leader) s_wh[warp][d] = cur + __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
   // ---- per digit: warp prefixes and the tile count, published at once
