@@ -244,8 +244,9 @@ static void bin_voxel32(const float* g, const ora_cam* c, int ts, bin32* b) {
     px[i] = p[0]; py[i] = p[1]; pz[i] = p[2];
     if (p[2] >= c->z_near) {
       ++n_front;
-      float rx = p[0] / p[2];
-      float ry = p[1] / p[2];
+      float iz = 1.0f / p[2]; /* one correctly rounded reciprocal per corner */
+      float rx = p[0] * iz;
+      float ry = p[1] * iz;
       float u = c->fx * rx;
       float v = c->fy * ry;
       u = u + c->cx;

@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     px[k] = p[0]; py[k] = p[1]; pz[k] = p[2];
     if (p[2] >= c.z_near) {
       ++n_front;
-      float u = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(p[0], p[2])), c.cx);
-      float v = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(p[1], p[2])), c.cy);
+      const float iz = __frcp_rn(p[2]);  // one correctly rounded reciprocal per corner
+      float u = __fadd_rn(__fmul_rn(c.fx, __fmul_rn(p[0], iz)), c.cx);
+      float v = __fadd_rn(__fmul_rn(c.fy, __fmul_rn(p[1], iz)), c.cy);
       if (first) { umin = umax = u; vmin = vmax = v; first = false; }
       else { umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v); }
     }
@@ -251,11 +252,12 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
         }
       }
     }
-    const float fts = (float)ts;
-    const float a0 = floorf(__fdiv_rn(__fsub_rn(umin, 1.0f), fts));
-    const float a1 = ceilf(__fdiv_rn(__fadd_rn(umax, 1.0f), fts));
-    const float b0 = floorf(__fdiv_rn(__fsub_rn(vmin, 1.0f), fts));
-    const float b1 = ceilf(__fdiv_rn(__fadd_rn(vmax, 1.0f), fts));
+    // ts is a power of two, so multiplying by 1/ts rounds exactly as dividing by ts
+    const float its = 1.0f / (float)ts;
+    const float a0 = floorf(__fmul_rn(__fsub_rn(umin, 1.0f), its));
+    const float a1 = ceilf(__fmul_rn(__fadd_rn(umax, 1.0f), its));
+    const float b0 = floorf(__fmul_rn(__fsub_rn(vmin, 1.0f), its));
+    const float b1 = ceilf(__fmul_rn(__fadd_rn(vmax, 1.0f), its));
     tx0 = (int)fminf(fmaxf(a0, 0.0f), (float)c.tiles_x);
     tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)c.tiles_x);
     ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)c.tiles_y);
