@@ -26,6 +26,11 @@ lv_status cuda_check(cudaError_t e, const char* what) {
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+std::mutex& setup_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 }  // namespace lv
 
 extern "C" const char* lv_last_error(void) { return lv::g_err; }

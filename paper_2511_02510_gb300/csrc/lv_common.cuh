@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "litevoxel.h"
@@ -21,6 +23,25 @@ lv_status cuda_check(cudaError_t e, const char* what);
 void count_launch(int k = 1);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Host-side one-time set-up per call site and device (kernel attributes,
+// occupancy): f() runs once for each device that reaches the call site,
+// under a library-wide lock, and before any caller of that device passes.
+std::mutex& setup_mutex();
+inline int current_device() {
+  int dev = 0;
+  return cudaGetDevice(&dev) == cudaSuccess ? dev : 0;
+}
+template <class F>
+void once_per_device(std::atomic<unsigned long long>& done, F&& f) {
+  const int dev = current_device();
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;  // beyond 64 devices: every time
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  std::lock_guard<std::mutex> lock(setup_mutex());
+  if (bit && (done.load(std::memory_order_relaxed) & bit)) return;
+  f();
+  if (bit) done.fetch_or(bit, std::memory_order_release);
+}
 
 // Bump allocator over a caller-owned workspace (also used to size it).
 struct Carve {

@@ -758,12 +758,11 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
   int blocks = (int)(want < cap_blocks ? want : cap_blocks);
   if (blocks < 1) blocks = 1;
   const size_t smem = sizeof(uint32_t) * RADIX * nq;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_sel_hist<RADIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(uint32_t) * 256 * SELECT_MAX_QUERIES));
-    attr_set = true;
-  }
+  });
   // digits from the top: the first one takes the remainder bits, the rest `width` each
   const int npass = (key_bits + width - 1) / width;
   int shift = key_bits;

@@ -57,25 +57,11 @@ size_t select_tmp_bytes(int n_queries);
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s);
 
-// ---------------------------------------------------------------- block ranks
-// Exclusive rank of `flag` among the threads of the block in thread order
-// (every thread of the block calls; blockDim.x a multiple of 32, <= 1024).
-__device__ __forceinline__ uint32_t block_excl_rank(bool flag) {
-  __shared__ uint32_t warp_cnt[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t b = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) warp_cnt[warp] = __popc(b);
-  __syncthreads();
-  uint32_t before = 0;
-  for (int w = 0; w < warp; ++w) before += warp_cnt[w];
-  __syncthreads();  // warp_cnt is reused by the next call
-  return before + __popc(b & ((1u << lane) - 1u));
-}
-
+// ---------------------------------------------------------------- block counts
 // In-place exclusive scan of cnt[0..m) (one block of 1024 threads, any m);
-// *total receives the sum.  Used for per-block counts of a flag, so that
-// block_excl_rank plus the block's offset ranks an item among all flagged
-// items in index order.
+// *total receives the sum.  Used for per-block counts of a flag, so that an
+// item's rank inside its block plus its block's offset ranks it among all
+// flagged items in index order.
 void scan_block_counts(uint32_t* cnt, int64_t m, uint32_t* total, cudaStream_t s);
 
 }  // namespace lv

@@ -1250,18 +1250,19 @@ template <int TS, bool SEG, bool PERSIST>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          float t_stop, const lv_fwd_out* out) {
   const size_t smem = FWD_SLICE * (TS * TS / 32);
-  static int pblocks = 0;
-  static bool attr = false;
-  if (!attr) {
+  static int pblocks[64];  // per device
+  static std::atomic<unsigned long long> done{0};
+  const int dev = current_device();
+  once_per_device(done, [&] {
     cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (PERSIST) pblocks = persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
-    attr = true;
-  }
+    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
+  });
+  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
     cudaMemsetAsync(w.work, 0, sizeof(unsigned int), s);
-    grid = (unsigned)(tiles < pblocks ? tiles : pblocks);
+    grid = (unsigned)(tiles < pb ? tiles : pb);
   }
   k_fwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
@@ -1272,18 +1273,19 @@ template <int TS, bool SEG, bool PERSIST>
 static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
   const size_t smem = BWD_SLICE * (TS * TS / 32);
-  static int pblocks = 0;
-  static bool attr = false;
-  if (!attr) {
+  static int pblocks[64];  // per device
+  static std::atomic<unsigned long long> done{0};
+  const int dev = current_device();
+  once_per_device(done, [&] {
     cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (PERSIST) pblocks = persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
-    attr = true;
-  }
+    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
+  });
+  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
     cudaMemsetAsync(w.work + 1, 0, sizeof(unsigned int), s);
-    grid = (unsigned)(tiles < pblocks ? tiles : pblocks);
+    grid = (unsigned)(tiles < pb ? tiles : pb);
   }
   k_bwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
                                                        w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
