@@ -187,7 +187,7 @@ class Workload:
         L.lv_subdivide_apply(self.vox, self.sp, self.aux, self.vout, self.sd_ws)
         mark(9)
 
-    def step_concurrent(self):
+    def step_concurrent(self, apply_events=None):
         """The same work as step(), in three streams.  The LF weight map depends on the ground
         truth only, and pruning and the subdivision selection on the forward statistics only, so
         they run beside the forward and the backward respectively (side streams at high priority,
@@ -223,7 +223,11 @@ class Workload:
                                 r.pair_capacity, self.dL, None, None, self.d_dens, None, True, r.status)
         L.lv_sh_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.workspace, r.pair_capacity, self.d_sh, False)
         main.wait_event(e_b)
+        if apply_events:
+            apply_events[0].record(main)
         L.lv_subdivide_apply(self.vox, self.sp, self.aux, self.vout, self.sd_ws)
+        if apply_events:
+            apply_events[1].record(main)
 
     def e2e_step(self):
         """The same step through the public API with host buffers: the step's ground-truth
@@ -734,9 +738,11 @@ def run_ours(args, rank, world, local):
     for k in range(K):
         wl.step(evs[k])
     torch.cuda.synchronize()
-    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]))
+    # medians over the K steps: one step that the host delays (a launch held up by the scheduler)
+    # must not move a stage's time
+    stage_ms = {s: float(np.median([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]))
                 for i, s in enumerate(Workload.STAGES)}
-    eager_ms = float(np.mean([evs[k][0].elapsed_time(evs[k][-1]) for k in range(K)]))
+    eager_ms = float(np.median([evs[k][0].elapsed_time(evs[k][-1]) for k in range(K)]))
 
     # ---- timed region: K replays of the step captured in one CUDA graph
     from paper_2511_02510_gb300.raster import CapturedStep
@@ -815,12 +821,30 @@ def run_ours(args, rank, world, local):
     e2e_s = (time.perf_counter() - t0) / K
     e2e_val = world * wl.npix / max_over_ranks(e2e_s, world, "cuda") / 1e6
 
+    # the dominant kernel inside graph replays of the same step: timing events captured around the
+    # subdivision write, read after each of K more replays (the write is the only launch between them)
+    apply_ms_graph = None
+    try:
+        # external: recorded as event nodes of the graph (rather than turned into a stream dependency)
+        ea = torch.cuda.Event(enable_timing=True, external=True)
+        eb = torch.cuda.Event(enable_timing=True, external=True)
+        g_marked = CapturedStep(lambda: wl.step_concurrent(apply_events=(ea, eb)))
+        samples = []
+        for _ in range(K):
+            g_marked()
+            torch.cuda.synchronize()
+            samples.append(ea.elapsed_time(eb))
+        apply_ms_graph = float(np.median(samples))
+    except Exception as e:  # event nodes in a graph: keep the eager stage time if the runtime refuses
+        print(f"graph-timed subdivision write unavailable: {e!r}", file=sys.stderr)
+        apply_ms_graph = None
+
     cnt = wl.counters()
     if rank == 0:
         hbm_peak, peak_src = peaks()
         # dominant kernel: the subdivision write (one launch, alone in the "subdivide_apply" stage),
         # an HBM-bound copy of every surviving voxel's state plus the children
-        t_apply = stage_ms["subdivide_apply"]
+        t_apply = apply_ms_graph if apply_ms_graph else stage_ms["subdivide_apply"]
         row = wl.row_bytes()
         parent_row = 16 + 1 + 8 * wl.scene.density.element_size() + 48 * wl.scene.sh.element_size()
         bytes_apply = algorithmic_bytes("subdivide_apply", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix,
@@ -843,6 +867,10 @@ def run_ours(args, rank, world, local):
                "roofline": {"bound": "hbm", "kernel": "k_sd_write (subdivision: survivor and child rows)",
                             "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                             "traffic": traffic, "peak_source": peak_src, "algorithmic_bytes": bytes_apply,
+                            "kernel_ms": t_apply,
+                            "kernel_timing": ("events captured around the launch in graph replays of the step "
+                                              "(median of K)") if apply_ms_graph else
+                                             "events around the launch in K eager steps (median)",
                             "row_bytes": row,
                             "backward_composite": {
                                 "bound": "alu", "achieved_tflops": bwd_flops / (t_bwd / 1e3) / 1e12,

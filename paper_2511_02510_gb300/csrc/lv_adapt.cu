@@ -78,6 +78,14 @@ __device__ __forceinline__ uint32_t block_total(uint32_t c) {
   return t;
 }
 
+// sum of the per-block counts of all earlier blocks (every thread calls): the
+// block's offset among the flagged items, read straight from the counts
+__device__ __forceinline__ uint32_t block_offset(const uint32_t* __restrict__ blk) {
+  uint32_t c = 0;
+  for (unsigned k = threadIdx.x; k < blockIdx.x; k += TPB) c += blk[k];
+  return block_total(c);
+}
+
 // exclusive prefix of one count per thread, in thread order (every thread calls)
 __device__ __forceinline__ uint32_t block_excl_count(uint32_t c) {
   __shared__ uint32_t s_part[TPB / 32];
@@ -124,7 +132,6 @@ struct PruneState {
   uint32_t ns;            // seen voxels
   uint32_t n_cand;        // out-state candidates after the update
   uint32_t c_lt;          // candidates strictly below the cap threshold
-  uint32_t c_eq;          // candidates at the cap threshold
   uint32_t all;           // 1 when every candidate is pruned (n_cand <= cap)
   float p_lo, p_hi;       // depth normalisation of this step (Eq. 14, running or not)
   uint32_t bin_cnt[SELECT_MAX_QUERIES];
@@ -359,7 +366,7 @@ __global__ void k_pr_ties(int64_t n, const uint32_t* __restrict__ wkey, const Se
 // a tie's rank among the ties (in id order) is its block's offset plus its
 // rank inside the block
 __global__ void k_pr_mask(int64_t n, const uint32_t* __restrict__ wkey, const SelectQuery* thr,
-                          const uint32_t* __restrict__ blk_off, const PruneState* st, uint8_t* mask,
+                          const uint32_t* __restrict__ blk, const PruneState* st, uint8_t* mask,
                           int64_t* n_pruned, uint32_t cap) {
   const int64_t i0 = first_item();
   const bool all = st->all != 0;
@@ -380,7 +387,7 @@ __global__ void k_pr_mask(int64_t n, const uint32_t* __restrict__ wkey, const Se
     }
     ceq += eq[u] ? 1u : 0u;
   }
-  uint32_t r = block_excl_count(ceq) + blk_off[blockIdx.x];  // every thread of the block takes part
+  uint32_t r = block_excl_count(ceq) + block_offset(blk);  // every thread of the block takes part
   const uint32_t need = cap > st->c_lt ? cap - st->c_lt : 0u;
   uint8_t out[IPT];
 #pragma unroll
@@ -399,7 +406,6 @@ struct SubState {
   uint32_t n_el;
   uint32_t k;
   uint32_t c_gt;      // eligible voxels with a strictly higher priority than the k-th
-  uint32_t c_eq;      // eligible voxels tied with the k-th
   uint32_t fits;      // output capacity suffices
   float p_lo, p_hi;   // depth normalisation of this step (Eq. 14, running or not)
 };
@@ -581,7 +587,7 @@ __global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const Se
 // rank among the ties is its block's offset plus its rank inside the block
 __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uint16_t* __restrict__ grp,
                             const uint32_t* __restrict__ pkey, const SelectQuery* q,
-                            const uint32_t* __restrict__ blk_off, const SubState* st, uint8_t* selected,
+                            const uint32_t* __restrict__ blk, const SubState* st, uint8_t* selected,
                             uint32_t* surv, uint32_t* sel) {
   const int64_t i0 = first_item();
   const bool any_k = q[2].k != 0;
@@ -603,7 +609,7 @@ __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uin
     }
     ceq += eq[u] ? 1u : 0u;
   }
-  uint32_t r = block_excl_count(ceq) + blk_off[blockIdx.x];  // every thread of the block takes part
+  uint32_t r = block_excl_count(ceq) + block_offset(blk);  // every thread of the block takes part
   const uint32_t need = st->k > st->c_gt ? st->k - st->c_gt : 0u;
   uint8_t so[IPT];
   uint32_t sl[IPT], sv[IPT];
@@ -882,7 +888,6 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   k_pr_cap_query<<<1, 32, 0, s>>>(qc, w.st, cap);
   select_kth(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
   k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, prune_mask, w.blk, w.st);
-  scan_block_counts(w.blk, blocks, &w.st->c_eq, s);
   k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, w.blk, w.st, prune_mask, d_n_pruned, cap);
   count_launch(9);
   return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
@@ -960,7 +965,6 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);
   select_kth(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
   k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.blk, w.st);
-  scan_block_counts(w.blk, blocks, &w.st->c_eq, s);
   k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);

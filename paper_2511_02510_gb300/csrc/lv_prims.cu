@@ -777,56 +777,6 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
 
 }  // namespace
 
-namespace {
-__global__ void __launch_bounds__(1024) k_scan_block_counts(uint32_t* cnt, int64_t m, uint32_t* total) {
-  constexpr int IT = 8;  // consecutive entries per thread
-  __shared__ uint32_t ws[32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t carry = 0;
-  for (int64_t base = 0; base < m; base += 1024 * IT) {  // block-uniform
-    const int64_t i0 = base + (int64_t)t * IT;
-    uint32_t c[IT], sum = 0;
-#pragma unroll
-    for (int e = 0; e < IT; ++e) {
-      c[e] = i0 + e < m ? cnt[i0 + e] : 0u;
-      sum += c[e];
-    }
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = ws[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, w, o);
-        if (lane >= o) w += y;
-      }
-      ws[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = carry + (warp ? ws[warp - 1] : 0u) + x - sum;
-#pragma unroll
-    for (int e = 0; e < IT; ++e) {
-      if (i0 + e < m) cnt[i0 + e] = run;
-      run += c[e];
-    }
-    carry += ws[31];
-    __syncthreads();
-  }
-  if (t == 0 && total) *total = carry;
-}
-}  // namespace
-
-void scan_block_counts(uint32_t* cnt, int64_t m, uint32_t* total, cudaStream_t s) {
-  k_scan_block_counts<<<1, 1024, 0, s>>>(cnt, m, total);
-  count_launch(1);
-}
-
 size_t select_tmp_bytes(int n_queries) {
   const size_t narrow = 256 * (size_t)n_queries;
   const size_t wide = 2048 * (size_t)(n_queries < SEL_WIDE_MAX_Q ? n_queries : SEL_WIDE_MAX_Q);

@@ -57,11 +57,4 @@ size_t select_tmp_bytes(int n_queries);
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s);
 
-// ---------------------------------------------------------------- block counts
-// In-place exclusive scan of cnt[0..m) (one block of 1024 threads, any m);
-// *total receives the sum.  Used for per-block counts of a flag, so that an
-// item's rank inside its block plus its block's offset ranks it among all
-// flagged items in index order.
-void scan_block_counts(uint32_t* cnt, int64_t m, uint32_t* total, cudaStream_t s);
-
 }  // namespace lv
