@@ -69,6 +69,27 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def tuned_schedule(scene, cams):
+    """Tile size and composite schedule from the library's autotuner (lv_autotune: every tile
+    size with and without persistent warps, forward + backward timed with CUDA events on this
+    scene and these views), as a user of the library would pick them."""
+    import torch
+
+    from paper_2511_02510_gb300 import litevoxel as L
+    from paper_2511_02510_gb300.raster import RasterContext
+    vox = scene.voxels()
+    probe = RasterContext(cams, scene.n)
+    probe.fit_capacity(vox)  # the pair capacity the default tile needs
+    cap = 2 * probe.pair_capacity  # smaller tiles cut voxels into more pairs
+    base = L.make_opts()
+    ws = torch.empty(L.lv_autotune_workspace_size(scene.n, probe.cams_arr, len(cams), base, cap),
+                     dtype=torch.uint8, device="cuda")
+    best, ms = L.lv_autotune(vox, probe.cams_arr, len(cams), base, cap, 3, ws)
+    del ws, probe
+    torch.cuda.empty_cache()
+    return int(best.tile), bool(best.flags & L.LV_FLAG_PERSISTENT), ms
+
+
 def camera_for(rank: int):
     from paper_2511_02510_gb300 import synth
     return synth.orbit_camera(W_IMG, H_IMG, 60.0, 3.0, 37.0 + 45.0 * rank, 15.0)
@@ -78,7 +99,7 @@ def camera_for(rank: int):
 class Workload:
     """Device-resident training state for one view and the buffers of one step."""
 
-    def __init__(self, scene_np, cam, gt_np, density_dtype=None, sh_dtype=None, t_iter=450.0):
+    def __init__(self, scene_np, cam, gt_np, density_dtype=None, sh_dtype=None, t_iter=450.0, tuned=False):
         import torch
 
         from paper_2511_02510_gb300 import litevoxel as L
@@ -91,7 +112,10 @@ class Workload:
         n = self.scene.n
         self.n = n
         self.cams = [cam]
-        self.rctx = RasterContext(self.cams, n)
+        self.tile, self.persistent, self.tune_ms = 16, False, None
+        if tuned:
+            self.tile, self.persistent, self.tune_ms = tuned_schedule(self.scene, self.cams)
+        self.rctx = RasterContext(self.cams, n, tile=self.tile, persistent=self.persistent)
         self.vox = self.scene.voxels()
         self.rctx.fit_capacity(self.vox)
         self.npix = self.rctx.n_pix
@@ -559,8 +583,11 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
         cams = [camera_for(0)]
         dd, sd = torch.float32, torch.float32
     scene = Scene.from_numpy(sc, "cuda", dd, sd)
-    ctx = RasterContext(cams, scene.n, exact_segment=(kind == "exact_segment_fp32"),
-                        persistent=(kind == "persistent_fp32"))
+    tile, persistent = 16, kind == "persistent_fp32"
+    if kind in ("plain_fp32", "batched16_fp32", "batched8_mixed"):  # the autotuned schedule, as the bench step
+        tile, persistent, _ = tuned_schedule(scene, cams)
+    ctx = RasterContext(cams, scene.n, tile=tile, exact_segment=(kind == "exact_segment_fp32"),
+                        persistent=persistent)
     vox = scene.voxels()
     ctx.fit_capacity(vox)
     g = torch.randn((ctx.n_pix, 3), device="cuda") * 1e-3
@@ -589,7 +616,7 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
     ctx.check()
     ms = e0.elapsed_time(e1) / steps
     return {"value": ctx.n_pix / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "views": len(cams),
-            "pixels": ctx.n_pix, "density_dtype": str(dd).split(".")[-1], "sh_dtype": str(sd).split(".")[-1],
+            "pixels": ctx.n_pix, "tile": tile, "persistent": persistent, "density_dtype": str(dd).split(".")[-1], "sh_dtype": str(sd).split(".")[-1],
             "step": "stats reset + forward + backward (composite + SH), replayed as one CUDA graph"}
 
 
@@ -720,7 +747,7 @@ def run_ours(args, rank, world, local):
     scene_np = synth.scene_360(seed=args.seed)
     cam = camera_for(rank)
     gt_np = synth.random_image(W_IMG, H_IMG, seed=1 + rank)
-    wl = Workload(scene_np, cam, gt_np)
+    wl = Workload(scene_np, cam, gt_np, tuned=True)
     for _ in range(max(3, args.warmup)):
         wl.step()
     torch.cuda.synchronize()
@@ -862,7 +889,9 @@ def run_ours(args, rank, world, local):
                "config": {"workload": WORKLOAD, "model": "LiteVoxel sparse-voxel tile rasterizer",
                           "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                           "voxels": wl.n, "pixels_per_rank": wl.npix, "pairs": cnt["pairs"],
-                          "visible_slots": cnt["visible_slots"], "tile": 16, "batch": 256,
+                          "visible_slots": cnt["visible_slots"], "tile": wl.tile,
+                          "schedule": "persistent warps" if wl.persistent else "one block per tile",
+                          "autotune_ms": wl.tune_ms,
                           "l2": "inputs larger than L2 (scene arrays 480 MB, per-step outputs > 600 MB)"},
                "roofline": {"bound": "hbm", "kernel": "k_sd_write (subdivision: survivor and child rows)",
                             "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
