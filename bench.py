@@ -215,14 +215,17 @@ class Workload:
         """The same work as step(), in three streams.  The LF weight map depends on the ground
         truth only, and pruning and the subdivision selection on the forward statistics only, so
         they run beside the forward and the backward respectively (side streams at high priority,
-        joined by events); the subdivision write runs last, alone."""
+        joined by events): the depth bins of the pruning start as soon as the forward has binned
+        the voxels (its statistics event), the rest once w_max is out.  The subdivision write
+        runs last, alone."""
         torch, L, r = self.torch, self.L, self.rctx
         if not hasattr(self, "_side"):
             hi = torch.cuda.Stream.priority_range()[1]
             self._side = (torch.cuda.Stream(priority=hi), torch.cuda.Stream(priority=hi))
-            self._evs = [torch.cuda.Event() for _ in range(4)]
+            self._evs = [torch.cuda.Event() for _ in range(5)]
+            self._evs[4].record()  # the statistics event must exist before the library records it
         sw, sb = self._side
-        e_start, e_w, e_fwd, e_b = self._evs
+        e_start, e_w, e_fwd, e_b, e_stats = self._evs
         main = torch.cuda.current_stream()
         e_start.record(main)
         sw.wait_event(e_start)
@@ -231,13 +234,16 @@ class Workload:
             L.lv_lf_weights(self.gt, [W_IMG], [H_IMG], self.t_iter, self.lfp, self.lf_ws)
             e_w.record(sw)
         r.reset_stats()
-        r.forward(self.vox, stats=True)
+        r.forward(self.vox, stats=True, stats_event=e_stats)
         e_fwd.record(main)
+        sb.wait_event(e_stats)
+        with torch.cuda.stream(sb):
+            L.lv_prune_bins(r.seen, r.z_min, self.pp, self.pr_ws)
         sb.wait_event(e_fwd)
         with torch.cuda.stream(sb):
             L.lv_unpack_wmax(r.wmax_packed, self.w_max, self.w_arg)
-            L.lv_prune_depth_quantile(self.w_max, r.seen, r.z_min, self.ema, self.state, self.pp, self.pmask,
-                                      self.n_pruned, self.pr_ws)
+            L.lv_prune_finish(self.w_max, r.seen, r.z_min, self.ema, self.state, self.pp, self.pmask,
+                              self.n_pruned, self.pr_ws)
             L.lv_subdivide_select(self.vox, r.delta_min, r.z_min, self.w_max, r.seen, self.pmask, self.sp,
                                   self.cap, self.selected, self.n_new, self.sd_ws, self.status)
             e_b.record(sb)
@@ -329,16 +335,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------- roofline
 def dram_traffic(kernel):
     """DRAM bytes per launch of ``kernel`` from the committed ncu capture, or None
-    when none was taken or the kernel's source file changed since it was."""
+    when none was taken or the kernel's source changed since it was: the hash
+    covers the region of the source file that holds the kernel and its device
+    helpers (``source_region``: first and end marker), else the whole file."""
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tp):
         return None
     rec = json.load(open(tp)).get(kernel)
     if not rec:
         return None
-    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+    with open(os.path.join(ROOT, rec["source"]), encoding="utf-8") as f:
+        text = f.read()
+    if rec.get("source_region"):
+        first, end = rec["source_region"]
+        i = text.find(first)
+        j = text.find(end, i) if i >= 0 else -1
+        if i < 0 or j < 0:
             return None
+        text = text[i:j]
+    if hashlib.sha256(text.encode("utf-8")).hexdigest() != rec["source_sha256"]:
+        return None
     return int(rec["dram_bytes_per_launch"])
 
 

@@ -127,6 +127,9 @@ typedef struct {
                                         spacing at the voxel (Sec. III); caller sets +inf; nullable */
   uint8_t* seen;                     /* [n] set to 1 when the voxel covers >= 1 tile of some view; nullable */
   uint32_t* n_samples;               /* [P] samples composited per pixel (hits of Eq. 2-4); nullable */
+  void* stats_event;                 /* cudaEvent_t (nullable): recorded on the stream as soon as z_min,
+                                        delta_min and seen are final (after binning, before sorting and
+                                        compositing), so another stream can start on them early */
 } lv_fwd_out;
 
 /* ------------------------------------------------------------------ */
@@ -316,6 +319,20 @@ size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p);
  * are updated in place; prune_mask [n] u8 is written; d_n_pruned (int64
  * device) receives the count.  Unseen voxels are unchanged and never pruned.
  * With no seen voxel nothing changes (pct_state included). */
+/* The two halves of lv_prune_depth_quantile, for callers that want to start
+ * on the depth statistics before w_max exists (see lv_fwd_out.stats_event).
+ * lv_prune_bins takes the percentiles of z over the seen voxels (Eq. 14,
+ * with the running update when pct_state is set) and bins the seen voxels
+ * into n_bins depth bins; lv_prune_finish takes the per-bin quantiles of
+ * w_max (Eq. 11-12) and applies guards i-iii.  Same arguments, same
+ * workspace, bins first; lv_prune_depth_quantile is bins + finish on one
+ * stream, and the split calls give the same bits. */
+lv_status lv_prune_bins(int64_t n, const uint8_t* seen, const float* z, const lv_prune_params* p, void* workspace,
+                        size_t ws_bytes, void* stream);
+lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_t* seen, const float* z, float* ema_m,
+                          uint8_t* state, const lv_prune_params* p, uint8_t* prune_mask, int64_t* d_n_pruned,
+                          void* workspace, size_t ws_bytes, int32_t* d_status, void* stream);
+
 lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
                                   float* ema_m, uint8_t* state, const lv_prune_params* p, uint8_t* prune_mask,
                                   int64_t* d_n_pruned, void* workspace, size_t ws_bytes, int32_t* d_status,

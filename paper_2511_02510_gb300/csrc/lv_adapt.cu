@@ -162,31 +162,38 @@ PruneWs carve_prune(void* base, int64_t n) {
   return w;
 }
 
-__global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z,
-                          const float* __restrict__ w_max, uint16_t* grp, uint32_t* zkey, uint32_t* wkey,
-                          PruneState* st) {
+__global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const float* __restrict__ z, uint16_t* grp,
+                          uint32_t* zkey, PruneState* st) {
   const int64_t i0 = first_item();
   uint8_t sv[IPT];
-  float zv[IPT], wv[IPT];
+  float zv[IPT];
   load4(seen, i0, n, sv, (uint8_t)0);
   load4(z, i0, n, zv, 0.f);
-  load4(w_max, i0, n, wv, 0.f);
   uint16_t gv[IPT];
-  uint32_t zk[IPT], wk[IPT];
+  uint32_t zk[IPT];
   uint32_t c = 0;
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     gv[u] = sv[u] ? 0 : GROUP_NONE;
     zk[u] = order_key(zv[u]);
-    wk[u] = order_key(wv[u]);
     c += sv[u] ? 1u : 0u;  // padding reads 0
   }
   store4(grp, i0, n, gv);
   store4(zkey, i0, n, zk);
-  store4(wkey, i0, n, wk);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const uint32_t b = block_total(c);
   if (threadIdx.x == 0 && b) atomicAdd(&st->ns, b);
+}
+
+// order keys of w_max for the per-bin quantiles and the cap
+__global__ void k_pr_wkey(int64_t n, const float* __restrict__ w_max, uint32_t* __restrict__ wkey) {
+  const int64_t i0 = first_item();
+  float wv[IPT];
+  load4(w_max, i0, n, wv, 0.f);
+  uint32_t wk[IPT];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) wk[u] = order_key(wv[u]);
+  store4(wkey, i0, n, wk);
 }
 
 __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm) {
@@ -832,13 +839,8 @@ extern "C" size_t lv_prune_workspace_size(int64_t n, const lv_prune_params* p) {
   return carve_prune(nullptr, n).bytes;
 }
 
-extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
-                                             float* ema_m, uint8_t* state, const lv_prune_params* p,
-                                             uint8_t* prune_mask, int64_t* d_n_pruned, void* workspace,
-                                             size_t ws_bytes, int32_t* d_status, void* stream) {
-  (void)d_status;
+static lv_status check_prune(int64_t n, const lv_prune_params* p, void* workspace, size_t ws_bytes) {
   if (!p || n < 0 || n > 0x7fffffffLL) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
-  if (n > 0 && (!w_max || !seen || !z || !ema_m || !state || !prune_mask)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
   if (p->n_bins < 1 || p->n_bins > SELECT_MAX_QUERIES) { set_error("n_bins must be 1..%d", SELECT_MAX_QUERIES); return LV_ERR_INVALID_ARG; }
   if (p->q_ppm < 0 || p->q_ppm > 1000000 || p->cap_ppm < 0 || p->cap_ppm > 1000000 || p->lo_ppm < 0 ||
       p->lo_ppm > 1000000 || p->hi_ppm < 0 || p->hi_ppm > 1000000) { set_error("ppm parameters must be in [0, 1e6]"); return LV_ERR_INVALID_ARG; }
@@ -849,25 +851,55 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   if (!(p->pct_ema >= 0.f && p->pct_ema <= 1.f)) { set_error("pct_ema must be in [0, 1]"); return LV_ERR_INVALID_ARG; }
   if (!(p->halo_small >= 0.f) || isnan(p->halo_w) || isnan(p->halo_edge)) { set_error("bad keep-halo parameters"); return LV_ERR_INVALID_ARG; }
   if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  if (ws_bytes < carve_prune(nullptr, n).bytes) {
+    set_error("workspace %zu < %zu bytes", ws_bytes, carve_prune(nullptr, n).bytes);
+    return LV_ERR_WORKSPACE;
+  }
+  return LV_OK;
+}
+
+extern "C" lv_status lv_prune_bins(int64_t n, const uint8_t* seen, const float* z, const lv_prune_params* p,
+                                   void* workspace, size_t ws_bytes, void* stream) {
+  lv_status e = check_prune(n, p, workspace, ws_bytes);
+  if (e != LV_OK) return e;
+  if (n > 0 && (!seen || !z)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
+  if (n == 0) return LV_OK;
   PruneWs w = carve_prune(workspace, n);
-  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = eblocks(n);  // IPT voxels per thread
+  cudaMemsetAsync(w.st, 0, sizeof(PruneState), s);
+  k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w.grp, w.zkey, w.st);
+  k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
+  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  const float r = p->pct_ema, omr = 1.0f - r;  // rounded to FP32 once, as the oracle does
+  k_pr_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, r, omr);
+  k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, p->n_bins, w.grp, w.st);
+  count_launch(4);
+  return cuda_check(cudaGetLastError(), "lv_prune_bins");
+}
+
+extern "C" lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
+                                     float* ema_m, uint8_t* state, const lv_prune_params* p, uint8_t* prune_mask,
+                                     int64_t* d_n_pruned, void* workspace, size_t ws_bytes, int32_t* d_status,
+                                     void* stream) {
+  (void)d_status;
+  (void)seen;
+  (void)z;
+  lv_status e = check_prune(n, p, workspace, ws_bytes);
+  if (e != LV_OK) return e;
+  if (n > 0 && (!w_max || !ema_m || !state || !prune_mask)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   if (n == 0) {
     if (d_n_pruned) cudaMemsetAsync(d_n_pruned, 0, sizeof(int64_t), s);
-    return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
+    return cuda_check(cudaGetLastError(), "lv_prune_finish");
   }
+  PruneWs w = carve_prune(workspace, n);
   const int nb = p->n_bins;
   const uint32_t cap = (uint32_t)(((unsigned long long)p->cap_ppm * (unsigned long long)n) / 1000000ull);
   const float alpha = p->ema_alpha;
   const float oma = 1.0f - alpha;  // rounded to FP32 once, as the oracle does
   const int blocks = eblocks(n);  // IPT voxels per thread
-  cudaMemsetAsync(w.st, 0, sizeof(PruneState), s);
-  k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w_max, w.grp, w.zkey, w.wkey, w.st);
-  k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
-  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
-  const float r = p->pct_ema, omr = 1.0f - r;  // rounded to FP32 once, as the oracle does
-  k_pr_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, r, omr);
-  k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, nb, w.grp, w.st);
+  k_pr_wkey<<<blocks, TPB, 0, s>>>(n, w_max, w.wkey);
   // the percentiles in q[0..1] are consumed: q is reused per bin
   k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal,
                                                     (uint32_t)p->anneal_ppm, (uint32_t)p->relax_ppm);
@@ -889,8 +921,19 @@ extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, cons
   select_kth(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
   k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, prune_mask, w.blk, w.st);
   k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, w.blk, w.st, prune_mask, d_n_pruned, cap);
-  count_launch(9);
-  return cuda_check(cudaGetLastError(), "lv_prune_depth_quantile");
+  count_launch(7);
+  return cuda_check(cudaGetLastError(), "lv_prune_finish");
+}
+
+extern "C" lv_status lv_prune_depth_quantile(int64_t n, const float* w_max, const uint8_t* seen, const float* z,
+                                             float* ema_m, uint8_t* state, const lv_prune_params* p,
+                                             uint8_t* prune_mask, int64_t* d_n_pruned, void* workspace,
+                                             size_t ws_bytes, int32_t* d_status, void* stream) {
+  if (n > 0 && (!w_max || !seen || !z || !ema_m || !state || !prune_mask)) { set_error("null array"); return LV_ERR_INVALID_ARG; }
+  lv_status e = lv_prune_bins(n, seen, z, p, workspace, ws_bytes, stream);
+  if (e != LV_OK) return e;
+  return lv_prune_finish(n, w_max, seen, z, ema_m, state, p, prune_mask, d_n_pruned, workspace, ws_bytes, d_status,
+                         stream);
 }
 
 extern "C" size_t lv_subdivide_workspace_size(int64_t n, const lv_subdiv_params* p) {

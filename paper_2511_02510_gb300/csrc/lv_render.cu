@@ -1361,6 +1361,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
     k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.dkey, out->z_min,
                                  out->delta_min, out->seen);
+    if (out->stats_event) cudaEventRecord((cudaEvent_t)out->stats_event, s);  // statistics final
     scan2(w.cnt, w.vis, items, nullptr, w.slot, w.counters, w.scan_tmp, s);
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                             \
@@ -1384,6 +1385,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     k_emit_pairs<<<8 * 152, EP_WARPS * 32, 0, s>>>(vs, sorted_slot, w.st_sorted, w.poff, w.counters,
                                                   pair_capacity, w.k0, w.v0, d_status);
     count_launch(2);
+  } else if (out->stats_event) {
+    cudaEventRecord((cudaEvent_t)out->stats_event, s);  // no voxel: nothing to bin
   }
   // 3) stable sort by tile: each tile's list stays front to back
   radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.sort_tmp, w.counters, pair_capacity, tile_bits(tiles),

@@ -52,7 +52,7 @@ class lv_raster_opts(C.Structure):
 class lv_fwd_out(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p),
-                ("n_samples", C.c_void_p)]
+                ("n_samples", C.c_void_p), ("stats_event", C.c_void_p)]
 
 
 class lv_prune_params(C.Structure):
@@ -119,6 +119,9 @@ SIGNATURES = {
     "lv_debug_sort_timeout": (C.c_int, [C.c_int32, _P, _SZ, _P, _P]),
     "lv_render_pixels_f64": (C.c_int, [_PV, _PC, C.c_int, _PO, _P, _SZ, _I64, _P, _I64, _P, _P, _P]),
     "lv_prune_workspace_size": (_SZ, [_I64, C.POINTER(lv_prune_params)]),
+    "lv_prune_bins": (C.c_int, [_I64, _P, _P, C.POINTER(lv_prune_params), _P, _SZ, _P]),
+    "lv_prune_finish": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.POINTER(lv_prune_params), _P, _P, _P, _SZ, _P,
+                                  _P]),
     "lv_prune_depth_quantile": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.POINTER(lv_prune_params), _P, _P, _P, _SZ, _P,
                                           _P]),
     "lv_subdivide_workspace_size": (_SZ, [_I64, C.POINTER(lv_subdiv_params)]),
@@ -231,11 +234,14 @@ def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=F
 
 
 def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None,
-                 n_samples=None) -> lv_fwd_out:
+                 n_samples=None, stats_event=None) -> lv_fwd_out:
+    """stats_event: a torch.cuda.Event (recorded once before, so that it exists) that the forward
+    records as soon as the per-voxel statistics are final."""
     o = lv_fwd_out()
     o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
     o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)
     o.n_samples = _ptr(n_samples)
+    o.stats_event = stats_event.cuda_event if stats_event is not None else None
     return o
 
 
@@ -360,6 +366,20 @@ def lv_prune_depth_quantile(w_max, seen, z, ema_m, state, params, prune_mask, n_
                                           _ptr(state), C.byref(params), _ptr(prune_mask), _ptr(n_pruned),
                                           _ptr(workspace), workspace.numel() * workspace.element_size(),
                                           _ptr(d_status), _stream()), "lv_prune_depth_quantile")
+
+
+def lv_prune_bins(seen, z, params, workspace):
+    """First half of lv_prune_depth_quantile: percentiles of z over the seen voxels and depth bins."""
+    _check(load().lv_prune_bins(int(z.numel()), _ptr(seen), _ptr(z), C.byref(params), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream()), "lv_prune_bins")
+
+
+def lv_prune_finish(w_max, seen, z, ema_m, state, params, prune_mask, n_pruned, workspace, d_status=None):
+    """Second half: per-bin quantiles of w_max, guards, cap; the workspace lv_prune_bins filled."""
+    _check(load().lv_prune_finish(int(w_max.numel()), _ptr(w_max), _ptr(seen), _ptr(z), _ptr(ema_m), _ptr(state),
+                                  C.byref(params), _ptr(prune_mask), _ptr(n_pruned), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _ptr(d_status), _stream()),
+           "lv_prune_finish")
 
 
 def lv_subdivide_workspace_size(n, params) -> int:

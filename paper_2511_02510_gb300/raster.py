@@ -73,17 +73,18 @@ class RasterContext:
         self.delta_min.fill_(math.inf)
         self.seen.zero_()
 
-    def fwd_struct(self, stats=True):
+    def fwd_struct(self, stats=True, stats_event=None):
         return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
                               self.wmax_packed if stats else None, self.z_min if stats else None,
                               self.delta_min if stats else None, self.seen if stats else None,
-                              self.n_samples if stats else None)
+                              self.n_samples if stats else None, stats_event)
 
     # ---------------------------------------------------------------- calls
-    def forward(self, vox: L.lv_voxels, stats=True):
-        """Launch the forward pass (asynchronous).  Returns (rgb, depth, T)."""
-        L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(stats), self.workspace,
-                               self.pair_capacity, self.status)
+    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None):
+        """Launch the forward pass (asynchronous).  Returns (rgb, depth, T).  stats_event (a
+        torch.cuda.Event recorded once before) is recorded when the voxel statistics are final."""
+        L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(stats, stats_event),
+                               self.workspace, self.pair_capacity, self.status)
         return self.rgb, self.depth, self.T
 
     def backward(self, vox: L.lv_voxels, dL_drgb, dL_ddepth=None, dL_dT=None, d_density=None, d_sh=None,

@@ -337,3 +337,36 @@ def test_lf_split_calls_match_fused_across_streams(ora):
     r = ora.lf_loss(rgb.astype(np.float64), gt.astype(np.float64), sizes, gamma=gamma)
     np.testing.assert_allclose(loss_a, r["loss"], rtol=1e-5)
     assert np.abs(grad_a - r["dL_drgb"]).max() <= 1e-5 * np.abs(r["dL_drgb"]).max()
+
+
+def test_prune_halves_match_one_call_across_streams(ora):
+    """lv_prune_bins on a side stream, lv_prune_finish after an event: the
+    same bits as lv_prune_depth_quantile (masks, EMA, states, count)."""
+    n = 20000
+    rng = np.random.default_rng(21)
+    w = rng.uniform(0, 1, n).astype(np.float32)
+    w[: n // 10] = np.float32(0.25)
+    seen = (rng.uniform(size=n) < 0.9).astype(np.uint8)
+    z = rng.uniform(0.5, 20, n).astype(np.float32)
+    m0 = rng.uniform(size=n).astype(np.float32)
+    s0 = (rng.uniform(size=n) < 0.5).astype(np.uint8)
+    ref_mask, ref_n, ref_m, ref_s = gpu_prune(w, seen, z, m0, s0)
+    r = ora.prune(w, seen, z, m0, s0)
+    np.testing.assert_array_equal(ref_mask, r["mask"])
+    p = prune_params()
+    ws = torch.empty(L.lv_prune_workspace_size(n, p), dtype=torch.uint8, device="cuda")
+    m, s = cu(m0), cu(s0)
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    npr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    seen_d, z_d, w_d = cu(seen), cu(z), cu(w)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        L.lv_prune_bins(seen_d, z_d, p, ws)
+    torch.cuda.current_stream().wait_stream(side)
+    L.lv_prune_finish(w_d, seen_d, z_d, m, s, p, mask, npr, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(np_(mask), ref_mask)
+    np.testing.assert_array_equal(np_(m).view(np.uint32), ref_m.view(np.uint32))
+    np.testing.assert_array_equal(np_(s), ref_s)
+    assert int(npr.item()) == ref_n
