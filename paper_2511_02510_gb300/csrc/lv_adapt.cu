@@ -867,7 +867,7 @@ extern "C" lv_status lv_prune_bins(int64_t n, const uint8_t* seen, const float* 
   PruneWs w = carve_prune(workspace, n);
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = eblocks(n);  // IPT voxels per thread
-  cudaMemsetAsync(w.st, 0, sizeof(PruneState), s);
+  zero_async(s, w.st, sizeof(PruneState));
   k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w.grp, w.zkey, w.st);
   k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
@@ -989,7 +989,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   SubWs w = carve_sub(workspace, n);
   if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemsetAsync(w.st, 0, sizeof(SubState), s);
+  zero_async(s, w.st, sizeof(SubState));
   if (n == 0) {
     cudaMemsetAsync(w.totals, 0, 4 * sizeof(unsigned long long), s);
     if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
@@ -1002,7 +1002,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_pct_queries<<<1, 32, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, cnt_seen);
   select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
   k_sd_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, cnt_seen, p->pct_state, p->pct_ema, 1.0f - p->pct_ema);
-  cudaMemsetAsync(cnt_seen, 0, sizeof(uint32_t), s);
+  zero_async(s, cnt_seen, sizeof(uint32_t));
   k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, p->kappa, p->beta,
                                         p->l_max, w.grp, w.pkey, w.st);
   k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);

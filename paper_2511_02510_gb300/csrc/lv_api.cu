@@ -26,6 +26,43 @@ lv_status cuda_check(cudaError_t e, const char* what) {
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+namespace {
+// 16-byte words where the range allows, bytes at the ragged ends
+__global__ void k_zero(const ZeroRanges r) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    char* p = (char*)r.p[k];
+    const size_t n = r.bytes[k];
+    if (!p || !n) continue;
+    const size_t head = ((16 - ((uintptr_t)p & 15)) & 15) < n ? ((16 - ((uintptr_t)p & 15)) & 15) : n;
+    const size_t words = (n - head) / 16;
+    for (size_t i = t; i < head; i += stride) p[i] = 0;
+    uint4* w = (uint4*)(p + head);
+    for (size_t i = t; i < words; i += stride) w[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (size_t i = head + 16 * words + t; i < n; i += stride) p[i] = 0;
+  }
+}
+}  // namespace
+
+void zero_async(cudaStream_t s, void* p0, size_t b0, void* p1, size_t b1, void* p2, size_t b2, void* p3,
+                size_t b3) {
+  ZeroRanges r;
+  r.p[0] = p0; r.bytes[0] = p0 ? b0 : 0;
+  r.p[1] = p1; r.bytes[1] = p1 ? b1 : 0;
+  r.p[2] = p2; r.bytes[2] = p2 ? b2 : 0;
+  r.p[3] = p3; r.bytes[3] = p3 ? b3 : 0;
+  size_t most = 0;
+  for (int k = 0; k < 4; ++k) most = r.bytes[k] > most ? r.bytes[k] : most;
+  if (most == 0) return;
+  size_t blocks = (most / 16 + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1216) blocks = 1216;
+  k_zero<<<(unsigned)blocks, 256, 0, s>>>(r);
+  count_launch(1);
+}
+
 std::mutex& setup_mutex() {
   static std::mutex mu;
   return mu;

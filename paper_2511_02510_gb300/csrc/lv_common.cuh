@@ -57,6 +57,18 @@ struct Carve {
   }
 };
 
+// Zero up to four small device ranges with one kernel launch.  In a CUDA
+// graph a memset node delays the kernel after it by several microseconds
+// (measured), a kernel node by well under one, so the hot path clears its
+// counters, status words and tile ranges this way.  Null or empty ranges
+// are skipped.
+struct ZeroRanges {
+  void* p[4];
+  size_t bytes[4];
+};
+void zero_async(cudaStream_t s, void* p0, size_t b0, void* p1 = nullptr, size_t b1 = 0, void* p2 = nullptr,
+                size_t b2 = 0, void* p3 = nullptr, size_t b3 = 0);
+
 // ---------------------------------------------------------------- device-side
 __device__ __forceinline__ void report(int32_t* st, int code) {
   if (st) atomicCAS(st, 0, code);

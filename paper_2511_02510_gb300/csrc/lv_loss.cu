@@ -282,7 +282,7 @@ extern "C" lv_status lv_lf_weights(const float* gt, const int32_t* widths, const
   const int64_t P = vp.off[n_views];
   cudaStream_t s = (cudaStream_t)stream;
   const float gamma = lv_lf_gamma(t, p);
-  cudaMemsetAsync(w.wsum, 0, sizeof(double) * LV_MAX_VIEWS, s);
+  zero_async(s, w.wsum, sizeof(double) * LV_MAX_VIEWS);
   k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
   k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
   select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
@@ -303,7 +303,7 @@ extern "C" lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, 
   lv_status e = lf_setup(widths, heights, n_views, 990000, workspace, ws_bytes, &vp, &w);
   if (e != LV_OK) return e;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemsetAsync(w.lsum, 0, sizeof(double) * LV_MAX_VIEWS, s);
+  zero_async(s, w.lsum, sizeof(double) * LV_MAX_VIEWS);
   // four pixels (three 16-byte words of rgb, gt and dL_drgb) per step where the buffers allow it
   const bool vec = aligned16(rgb) && aligned16(gt) && aligned16(w.w) && (!dL_drgb || aligned16(dL_drgb));
   for (int v = 0; v < n_views; ++v) {

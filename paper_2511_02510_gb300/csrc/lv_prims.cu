@@ -480,7 +480,7 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
   K* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
   const int64_t tiles = (cap + Os<K>::TILE - 1) / Os<K>::TILE;
-  cudaMemsetAsync(st.ghist, 0, sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2), s);  // counts and tickets
+  zero_async(s, st.ghist, sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2));  // counts and tickets
   const int hb = (int)min((int64_t)OS_HIST_BLOCKS, tiles);
   k_os_hist<K><<<hb, OS_HIST_THREADS, 0, s>>>(kin, d_count, cap, passes, st.ghist, st.look[0]);
   for (int p = 0; p < passes; ++p) {

@@ -1260,10 +1260,7 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
-  if (PERSIST) {
-    cudaMemsetAsync(w.work, 0, sizeof(unsigned int), s);
-    grid = (unsigned)(tiles < pb ? tiles : pb);
-  }
+  if (PERSIST) grid = (unsigned)(tiles < pb ? tiles : pb);  // work[0] was cleared at the start of the forward
   k_fwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
                                                        out->n_samples, w.tau, out->wmax_packed, w.work, n_items);
@@ -1284,7 +1281,7 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
-    cudaMemsetAsync(w.work + 1, 0, sizeof(unsigned int), s);
+    zero_async(s, w.work + 1, sizeof(unsigned int));
     grid = (unsigned)(tiles < pb ? tiles : pb);
   }
   k_bwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
@@ -1353,9 +1350,9 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
   const int64_t n = vox->n, items = n * n_views;
-  cudaMemsetAsync(w.counters, 0, 8 * sizeof(unsigned long long), s);
-  cudaMemsetAsync(w.ranges, 0, sizeof(uint32_t) * 2 * tiles, s);
-  if (!d_status || d_status == w.status) cudaMemsetAsync(w.status, 0, sizeof(int32_t), s);
+  // counters, tile ranges, the fallback status word and the persistent forward's work counter
+  zero_async(s, w.counters, 8 * sizeof(unsigned long long), w.ranges, sizeof(uint32_t) * 2 * tiles,
+             d_status == w.status ? w.status : nullptr, sizeof(int32_t), w.work, sizeof(unsigned int));
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
     const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
