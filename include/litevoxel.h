@@ -155,6 +155,12 @@ lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera* cams, int 
                                const lv_fwd_out* out, void* workspace, size_t ws_bytes, int64_t pair_capacity,
                                int32_t* d_status, void* stream);
 
+/* Start a new accumulation window of the per-voxel statistics in one
+ * launch: wmax_packed[i] = 0, z_min[i] = delta_min[i] = +inf, seen[i] = 0
+ * for i < n (device arrays as in lv_fwd_out; any may be NULL). */
+lv_status lv_reset_stats(int64_t n, unsigned long long* wmax_packed, float* z_min, float* delta_min, uint8_t* seen,
+                         void* stream);
+
 /* Synchronously read the forward counters from a workspace: out2[0] = pairs
  * the last forward emitted (may exceed its capacity), out2[1] = visible
  * (voxel, view) slots. */

@@ -1396,6 +1396,49 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
 }
 
+namespace lv {
+namespace {
+// four voxels per thread: one 32-byte store of w_max, 16-byte stores of the
+// depths, one 4-byte store of seen (scalar at a ragged end or misaligned arrays)
+__global__ void k_reset_stats(int64_t n, unsigned long long* wmax, float* z_min, float* delta_min, uint8_t* seen) {
+  const float inf = __int_as_float(0x7f800000);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  const bool vec = (((uintptr_t)wmax | (uintptr_t)z_min | (uintptr_t)delta_min) & 15) == 0 &&
+                   ((uintptr_t)seen & 3) == 0;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+    if (vec && i0 + 3 < n) {
+      if (wmax) {
+        ((uint4*)(wmax + i0))[0] = make_uint4(0u, 0u, 0u, 0u);
+        ((uint4*)(wmax + i0))[1] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      if (z_min) *(float4*)(z_min + i0) = make_float4(inf, inf, inf, inf);
+      if (delta_min) *(float4*)(delta_min + i0) = make_float4(inf, inf, inf, inf);
+      if (seen) *(uint32_t*)(seen + i0) = 0u;
+    } else {
+      for (int64_t i = i0; i < n && i < i0 + 4; ++i) {
+        if (wmax) wmax[i] = 0ull;
+        if (z_min) z_min[i] = inf;
+        if (delta_min) delta_min[i] = inf;
+        if (seen) seen[i] = 0;
+      }
+    }
+  }
+}
+}  // namespace
+}  // namespace lv
+
+extern "C" lv_status lv_reset_stats(int64_t n, unsigned long long* wmax_packed, float* z_min, float* delta_min,
+                                    uint8_t* seen, void* stream) {
+  if (n < 0) { set_error("bad voxel count"); return LV_ERR_INVALID_ARG; }
+  if (n == 0) return LV_OK;
+  int64_t blocks = (n / 4 + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4 * 1216) blocks = 4 * 1216;
+  k_reset_stats<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, wmax_packed, z_min, delta_min, seen);
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_reset_stats");
+}
+
 extern "C" lv_status lv_workspace_counters(const void* workspace, size_t ws_bytes, int64_t* out2, void* stream) {
   if (!workspace || !out2 || ws_bytes < 64) { set_error("bad arguments"); return LV_ERR_INVALID_ARG; }
   unsigned long long h[2];

@@ -134,6 +134,7 @@ SIGNATURES = {
     "lv_compact_workspace_size": (_SZ, [_I64]),
     "lv_compact": (C.c_int, [_PV, _P, C.POINTER(lv_aux_array), C.c_int, _PV, _P, _P, _SZ, _P, _P]),
     "lv_check_status": (C.c_int, [_P, _P]),
+    "lv_reset_stats": (C.c_int, [_I64, _P, _P, _P, _P, _P]),
     "lv_autotune_workspace_size": (_SZ, [_I64, _PC, C.c_int, _PO, _I64]),
     "lv_autotune": (C.c_int, [_PV, _PC, C.c_int, _PO, _I64, C.c_int, _PO, C.POINTER(C.c_float), C.c_char_p, _P, _SZ,
                               _P]),
@@ -434,6 +435,13 @@ def lv_autotune(vox, cams_arr, n_views, base, pair_capacity, reps, workspace, ca
                               C.byref(best), ms, path, _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream()), "lv_autotune")
     return best, [float(x) for x in ms]
+
+
+def lv_reset_stats(wmax_packed, z_min, delta_min, seen):
+    """One launch: w_max 0, z_min and delta_min +inf, seen 0."""
+    n = next(t.numel() for t in (wmax_packed, z_min, delta_min, seen) if t is not None)
+    _check(load().lv_reset_stats(int(n), _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen), _stream()),
+           "lv_reset_stats")
 
 
 def lv_check_status(d_status) -> int:

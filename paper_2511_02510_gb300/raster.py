@@ -68,10 +68,7 @@ class RasterContext:
 
     def reset_stats(self):
         """Zero w_max and reset z_min / delta_min / seen before a new accumulation window."""
-        self.wmax_packed.zero_()
-        self.z_min.fill_(math.inf)
-        self.delta_min.fill_(math.inf)
-        self.seen.zero_()
+        L.lv_reset_stats(self.wmax_packed, self.z_min, self.delta_min, self.seen)
 
     def fwd_struct(self, stats=True, stats_event=None):
         return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
