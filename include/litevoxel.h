@@ -112,6 +112,8 @@ typedef struct {
   int32_t threads_per_px; /* 1 (reserved) */
   float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
   uint32_t flags;         /* LV_FLAG_* */
+  int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: size the resident grid for this many SMs (0 = all),
+                             leaving the rest to kernels of other streams that run beside the composites */
 } lv_raster_opts;
 
 /* Forward outputs (device).  P = total pixels of all views. */

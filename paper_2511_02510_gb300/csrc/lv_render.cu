@@ -1208,6 +1208,7 @@ static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int n
   if (o->batch != 64 && o->batch != 128 && o->batch != 256) { set_error("batch must be 64, 128 or 256"); return LV_ERR_INVALID_ARG; }
   if (o->threads_per_px != 1) { set_error("threads_per_px must be 1 (one thread owns a pixel's sample chain)"); return LV_ERR_UNSUPPORTED; }
   if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) { set_error("t_stop must be in [0, 1)"); return LV_ERR_INVALID_ARG; }
+  if (o->persistent_sms < 0) { set_error("persistent_sms must be >= 0"); return LV_ERR_INVALID_ARG; }
   int64_t tiles = 0, pixels = 0;
   for (int i = 0; i < nv; ++i) {
     const lv_camera& c = cams[i];
@@ -1246,9 +1247,19 @@ static int persistent_blocks(K kernel, int threads, size_t smem) {
   return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
 }
 
+// a persistent grid of pb blocks over all SMs, cut to sm_limit SMs (0: all)
+static int limit_to_sms(int pb, int sm_limit, int dev) {
+  if (sm_limit <= 0) return pb;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0 || sm_limit >= sms) return pb;
+  const int per_sm = pb / sms > 0 ? pb / sms : 1;
+  return per_sm * sm_limit;
+}
+
 template <int TS, bool SEG, bool PERSIST>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                         float t_stop, const lv_fwd_out* out) {
+                         float t_stop, const lv_fwd_out* out, int sm_limit) {
   const size_t smem = FWD_SLICE * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
@@ -1257,7 +1268,8 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
     cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
   });
-  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
+  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
+  if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) grid = (unsigned)(tiles < pb ? tiles : pb);  // work[0] was cleared at the start of the forward
@@ -1268,7 +1280,8 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
 
 template <int TS, bool SEG, bool PERSIST>
 static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                         const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd) {
+                         const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd,
+                         int sm_limit) {
   const size_t smem = BWD_SLICE * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
@@ -1277,7 +1290,8 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
     cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
   });
-  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
+  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
+  if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
@@ -1295,10 +1309,10 @@ static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, c
                        const uint32_t* sv, const lv_fwd_out* out) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
 #define LV_FWD(TS)                                                                   \
-  if (seg && per) launch_fwd_t<TS, true, true>(tiles, s, vs, w, sv, o->t_stop, out);  \
-  else if (seg) launch_fwd_t<TS, true, false>(tiles, s, vs, w, sv, o->t_stop, out);  \
-  else if (per) launch_fwd_t<TS, false, true>(tiles, s, vs, w, sv, o->t_stop, out);  \
-  else launch_fwd_t<TS, false, false>(tiles, s, vs, w, sv, o->t_stop, out)
+  if (seg && per) launch_fwd_t<TS, true, true>(tiles, s, vs, w, sv, o->t_stop, out, o->persistent_sms);  \
+  else if (seg) launch_fwd_t<TS, true, false>(tiles, s, vs, w, sv, o->t_stop, out, 0);                   \
+  else if (per) launch_fwd_t<TS, false, true>(tiles, s, vs, w, sv, o->t_stop, out, o->persistent_sms);  \
+  else launch_fwd_t<TS, false, false>(tiles, s, vs, w, sv, o->t_stop, out, 0)
   if (o->tile == 8) { LV_FWD(8); }
   else if (o->tile == 16) { LV_FWD(16); }
   else { LV_FWD(32); }
@@ -1310,10 +1324,10 @@ static void launch_bwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, c
                        float* dd) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
 #define LV_BWD(TS)                                                                         \
-  if (seg && per) launch_bwd_t<TS, true, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
-  else if (seg) launch_bwd_t<TS, true, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
-  else if (per) launch_bwd_t<TS, false, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd);   \
-  else launch_bwd_t<TS, false, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd)
+  if (seg && per) launch_bwd_t<TS, true, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, o->persistent_sms);  \
+  else if (seg) launch_bwd_t<TS, true, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0);                   \
+  else if (per) launch_bwd_t<TS, false, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, o->persistent_sms);  \
+  else launch_bwd_t<TS, false, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0)
   if (o->tile == 8) { LV_BWD(8); }
   else if (o->tile == 16) { LV_BWD(16); }
   else { LV_BWD(32); }

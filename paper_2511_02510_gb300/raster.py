@@ -28,11 +28,12 @@ class RasterContext:
     """
 
     def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda",
-                 exact_segment=False, persistent=False):
+                 exact_segment=False, persistent=False, persistent_sms=0):
         self.cams = list(cams)
         self.n_views = len(self.cams)
         self.cams_arr = L.make_cameras(self.cams)
-        self.opts = L.make_opts(tile, batch, t_stop, exact_segment=exact_segment, persistent=persistent)
+        self.opts = L.make_opts(tile, batch, t_stop, exact_segment=exact_segment, persistent=persistent,
+                                persistent_sms=persistent_sms)
         self.device = torch.device(device)
         self.n = int(n_voxels)
         self.sizes = [(int(c["width"]), int(c["height"])) for c in self.cams]

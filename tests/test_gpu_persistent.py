@@ -16,10 +16,11 @@ from test_gpu_render import GRAD_TOL, _grad_err, cam_far, cam_near, compare_imag
 pytestmark = pytest.mark.gpu
 
 
-def run(sc, cams, tile, persistent, g=None, exact_segment=False):
+def run(sc, cams, tile, persistent, g=None, exact_segment=False, persistent_sms=0):
     from gpu_helpers import to_scene
     scene = to_scene(sc)
-    ctx = RasterContext(cams, scene.n, tile=tile, persistent=persistent, exact_segment=exact_segment)
+    ctx = RasterContext(cams, scene.n, tile=tile, persistent=persistent, exact_segment=exact_segment,
+                        persistent_sms=persistent_sms)
     vox = scene.voxels()
     ctx.fit_capacity(vox)
     ctx.reset_stats()
@@ -53,6 +54,20 @@ def test_persistent_full_size_view():
     g = np.random.default_rng(0).normal(size=(1237 * 822, 3)).astype(np.float32) * 1e-3
     a, _ = run(sc, [cam], 16, False, g)
     b, _ = run(sc, [cam], 16, True, g)
+    for k in ("rgb", "T", "depth", "n_contrib", "wmax_packed"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert _grad_err(b["dd"], a["dd"]) < GRAD_TOL and _grad_err(b["ds"], a["ds"]) < GRAD_TOL
+
+
+@pytest.mark.parametrize("sms", [1, 7, 120])
+def test_persistent_on_fewer_sms(sms):
+    """persistent_sms only sizes the resident grid: the same bits on any SM count."""
+    sc = synth.scene_tiny()
+    cams = [cam_near(100, 70, az=80.0), cam_far(64, 48, az=200.0)]
+    P = sum(c["width"] * c["height"] for c in cams)
+    g = np.random.default_rng(sms).normal(size=(P, 3)).astype(np.float32)
+    a, _ = run(sc, cams, 32, True, g)
+    b, _ = run(sc, cams, 32, True, g, persistent_sms=sms)
     for k in ("rgb", "T", "depth", "n_contrib", "wmax_packed"):
         np.testing.assert_array_equal(a[k], b[k])
     assert _grad_err(b["dd"], a["dd"]) < GRAD_TOL and _grad_err(b["ds"], a["ds"]) < GRAD_TOL
