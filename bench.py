@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    # a fixed composite schedule instead of the autotuner's choice (for profiler runs, whose
+    # distorted timings would steer the autotuner elsewhere): tile edge and 0 / 1 for persistent
+    ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None)
+    ap.add_argument("--persistent", type=int, choices=[0, 1], default=None)
     return ap.parse_args()
 
 
@@ -99,7 +103,8 @@ def camera_for(rank: int):
 class Workload:
     """Device-resident training state for one view and the buffers of one step."""
 
-    def __init__(self, scene_np, cam, gt_np, density_dtype=None, sh_dtype=None, t_iter=450.0, tuned=False):
+    def __init__(self, scene_np, cam, gt_np, density_dtype=None, sh_dtype=None, t_iter=450.0, tuned=False,
+                 schedule=None):
         import torch
 
         from paper_2511_02510_gb300 import litevoxel as L
@@ -113,7 +118,9 @@ class Workload:
         self.n = n
         self.cams = [cam]
         self.tile, self.persistent, self.tune_ms = 16, False, None
-        if tuned:
+        if schedule is not None:
+            self.tile, self.persistent = schedule
+        elif tuned:
             self.tile, self.persistent, self.tune_ms = tuned_schedule(self.scene, self.cams)
         # persistent composites leave 32 SMs to the pruning and selection kernels that the
         # three-stream step runs beside them (a full-GPU resident grid starves them: measured
@@ -770,7 +777,8 @@ def run_ours(args, rank, world, local):
     scene_np = synth.scene_360(seed=args.seed)
     cam = camera_for(rank)
     gt_np = synth.random_image(W_IMG, H_IMG, seed=1 + rank)
-    wl = Workload(scene_np, cam, gt_np, tuned=True)
+    fixed = (args.tile, bool(args.persistent)) if args.tile is not None and args.persistent is not None else None
+    wl = Workload(scene_np, cam, gt_np, tuned=True, schedule=fixed)
     for _ in range(max(3, args.warmup)):
         wl.step()
     torch.cuda.synchronize()
