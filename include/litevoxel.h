@@ -22,9 +22,10 @@
  *  - Host-detectable argument errors return LV_ERR_INVALID_ARG (nothing is
  *    launched); `lv_last_error()` describes the most recent failure of the
  *    calling thread.  Errors found on the device (pair or voxel capacity
- *    overflow) are written to `d_status` (int32 device word, first error
- *    wins, the caller zeroes it) and the affected outputs are left
- *    unspecified.  A launch failure returns LV_ERR_CUDA.
+ *    overflow, a bounded inter-block wait of the radix sort that gave up)
+ *    are written to `d_status` (int32 device word, first error wins, the
+ *    caller zeroes it; lv_check_status reads it) and the affected outputs
+ *    are left unspecified.  A launch failure returns LV_ERR_CUDA.
  *  - Pixels of all views are concatenated view-major, each view row-major:
  *    pixel (view v, x, y) has global id pix_off[v] + y * width_v + x.
  *  - Voxel arrays are structure-of-arrays, one row per voxel:
