@@ -123,14 +123,15 @@ class Workload:
             self.tile, self.persistent = schedule
         elif tuned:
             self.tile, self.persistent, self.tune_ms = tuned_schedule(self.scene, self.cams)
-        # persistent composites leave 32 SMs to the pruning and selection kernels that the
-        # three-stream step runs beside them (a full-GPU resident grid starves them: measured
-        # 1.335 ms per step against 1.315 ms with 120 of 152 SMs)
+        # the persistent backward composite leaves 32 SMs to the pruning and selection kernels
+        # that the three-stream step runs beside it (a full-GPU resident grid starves them:
+        # measured 1.335 ms per step against 1.315 ms with 120 of 152 SMs); the forward
+        # composite runs alone and keeps every SM
         self.persistent_sms = 0
         if self.persistent:
             self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 32)
-        self.rctx = RasterContext(self.cams, n, tile=self.tile, persistent=self.persistent,
-                                  persistent_sms=self.persistent_sms)
+        self.rctx = RasterContext(self.cams, n, tile=self.tile, persistent=self.persistent)
+        self.bwd_opts = L.make_opts(self.tile, persistent=self.persistent, persistent_sms=self.persistent_sms)
         self.vox = self.scene.voxels()
         self.rctx.fit_capacity(self.vox)
         self.npix = self.rctx.n_pix
@@ -264,7 +265,7 @@ class Workload:
             e_b.record(sb)
         main.wait_event(e_w)
         L.lv_lf_loss_from_weights(r.rgb, self.gt, [W_IMG], [H_IMG], self.loss, self.dL, self.lf_ws)
-        L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.fwd_struct(False), r.workspace,
+        L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, self.bwd_opts, r.fwd_struct(False), r.workspace,
                                 r.pair_capacity, self.dL, None, None, self.d_dens, None, True, r.status)
         L.lv_sh_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.workspace, r.pair_capacity, self.d_sh, False)
         main.wait_event(e_b)
@@ -924,7 +925,7 @@ def run_ours(args, rank, world, local):
                           "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                           "voxels": wl.n, "pixels_per_rank": wl.npix, "pairs": cnt["pairs"],
                           "visible_slots": cnt["visible_slots"], "tile": wl.tile,
-                          "schedule": (f"persistent warps on {wl.persistent_sms} SMs" if wl.persistent
+                          "schedule": (f"persistent warps (backward on {wl.persistent_sms} SMs)" if wl.persistent
                                        else "one block per tile"),
                           "autotune_ms": wl.tune_ms,
                           "l2": "inputs larger than L2 (scene arrays 480 MB, per-step outputs > 600 MB)"},

@@ -114,7 +114,8 @@ typedef struct {
   float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
   uint32_t flags;         /* LV_FLAG_* */
   int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: size the resident grid for this many SMs (0 = all),
-                             leaving the rest to kernels of other streams that run beside the composites */
+                             leaving the rest to kernels of other streams that run beside the composites;
+                             it changes no result and may differ between the forward and backward calls */
 } lv_raster_opts;
 
 /* Forward outputs (device).  P = total pixels of all views. */
