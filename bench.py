@@ -123,13 +123,13 @@ class Workload:
             self.tile, self.persistent = schedule
         elif tuned:
             self.tile, self.persistent, self.tune_ms = tuned_schedule(self.scene, self.cams)
-        # the persistent backward composite leaves 32 SMs to the pruning and selection kernels
-        # that the three-stream step runs beside it (a full-GPU resident grid starves them:
-        # measured 1.335 ms per step against 1.315 ms with 120 of 152 SMs); the forward
-        # composite runs alone and keeps every SM
+        # the persistent backward composite leaves 48 SMs to the pruning and selection kernels
+        # that the three-stream step runs beside it (a full-GPU resident grid starves them; a
+        # sweep of the backward's SMs gave 1.332 ms per step on 152, 1.303 on 120, 1.301 on
+        # 112, 1.298 on 96); the forward composite runs alone and keeps every SM
         self.persistent_sms = 0
         if self.persistent:
-            self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 32)
+            self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 48)
         self.rctx = RasterContext(self.cams, n, tile=self.tile, persistent=self.persistent)
         self.bwd_opts = L.make_opts(self.tile, persistent=self.persistent, persistent_sms=self.persistent_sms)
         self.vox = self.scene.voxels()
