@@ -158,7 +158,8 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
 // digits over all items.  Each pass kernel then takes tiles of Os<K>::TILE items
 // in ticket order (an atomic counter, so a tile's predecessors are already
 // running or done), ranks its items by digit in shared memory (a warp-private
-// histogram per warp, stable ranks from bit ballots), publishes its per-digit counts, and
+// histogram per warp; the lanes of a digit found by bit ballots or by
+// __match_any_sync, whichever suits the keys), publishes its per-digit counts, and
 // finds the number of items with each digit in all earlier tiles by looking
 // back through their published words (decoupled look-back: a tile that has
 // published its inclusive prefix ends the walk).  A published word packs a
@@ -180,10 +181,11 @@ constexpr float OS_MATCH_BELOW = 6.f;            // expected distinct digits per
 constexpr int OS_MATCH_MAX_GROUPS = 16;          // distinct digits in a warp's round up to which match_any ranks next
 constexpr int OS_HIST_THREADS = 256;
 
-// Tile shape of the pass kernel: 512 threads (4096 items) for 32-bit keys,
-// 256 (2048 items) for 64-bit keys, so that the static shared memory stays
-// under 48 KB; 64 registers a thread either way.  Threads d < RADIX look
-// after digit d.
+// Tile shape of the pass kernel: 512 threads (4096 items, about 52 KB of
+// static shared memory) for 32-bit keys, 256 threads (2048 items, about 36 KB)
+// for 64-bit keys, whose staged keys are twice as large; 64 registers a thread
+// either way, so 2048 threads fit on an SM.  Threads d < RADIX look after
+// digit d.
 template <typename K>
 struct Os {
   static constexpr int THREADS = sizeof(K) == 4 ? 512 : 256;
