@@ -142,7 +142,10 @@ typedef struct {
 
 /* Bytes of forward/backward workspace for n voxels, the given views and at
  * most pair_capacity (tile, voxel) pairs.  The same workspace must be passed
- * unchanged from lv_rasterize_forward to lv_rasterize_backward. */
+ * unchanged from lv_rasterize_forward to lv_rasterize_backward.  Returns 0
+ * for a configuration the forward pass would refuse on its size arguments
+ * (no view or more than LV_MAX_VIEWS, n < 0, a tile edge other than 8 / 16 /
+ * 32, pair_capacity outside [0, 2^32 - 1]). */
 size_t lv_forward_workspace_size(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
                                  int64_t pair_capacity);
 

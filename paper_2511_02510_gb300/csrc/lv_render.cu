@@ -1340,11 +1340,13 @@ using namespace lv;
 
 extern "C" size_t lv_forward_workspace_size(int64_t n, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
                                             int64_t pair_capacity) {
-  if (!cams || !opts || n_views < 1 || n_views > LV_MAX_VIEWS || n < 0 || pair_capacity < 0) return 0;
+  if (!cams || !opts || n_views < 1 || n_views > LV_MAX_VIEWS || n < 0 || pair_capacity < 0 ||
+      pair_capacity > 0xffffffffLL)
+    return 0;
+  if (opts->tile != 8 && opts->tile != 16 && opts->tile != 32) return 0;
   ViewSet vs;
   int64_t tiles, pixels;
-  int ts = opts->tile == 8 || opts->tile == 32 ? opts->tile : 16;
-  make_views(cams, n_views, ts, &vs, &tiles, &pixels);
+  make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
   return carve_fwd(nullptr, n, n_views, tiles, pixels, pair_capacity).bytes;
 }
 
