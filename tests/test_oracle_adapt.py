@@ -104,6 +104,25 @@ def test_pairs_statistics(ora):
     assert np.all(np.isinf(pr["z_min"][~seen]))
 
 
+def test_footprint_floor_at_the_near_plane(ora):
+    # delta_v is the ray spacing at the voxel's depth, and no seen voxel sits closer than the near plane:
+    # every footprint is at least z_near / f_x, and a voxel whose centre lies in front of the near plane
+    # (seen through its far part) gets exactly that floor, with z_min = z_near.
+    rng = np.random.default_rng(8)
+    n = 200
+    centers = np.c_[rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n), rng.uniform(-0.2, 1.5, n)]
+    sc = synth.constant_voxel_scene(centers, rng.uniform(0.05, 0.4, n), np.ones(n), np.ones((n, 3)) * 0.5)
+    cam = {"width": 48, "height": 40, "fx": 30.0, "fy": 30.0, "cx": 24.0, "cy": 20.0,
+           "w2c": [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], "z_near": 0.3}
+    pr = ora.pairs(sc, [cam], ts=8)
+    seen = pr["seen"].astype(bool)
+    floor_ = np.float32(np.float32(0.3) / np.float32(30.0))
+    behind = seen & (sc["geom"][:, 2] < np.float32(0.3))
+    assert seen.sum() > 50 and behind.sum() > 5
+    assert np.all(pr["delta_min"][seen] >= floor_) and np.all(pr["z_min"][seen] >= np.float32(0.3))
+    assert np.all(pr["delta_min"][behind] == floor_) and np.all(pr["z_min"][behind] == np.float32(0.3))
+
+
 # --------------------------------------------------------------------- pruning
 
 def test_ema_hysteresis_hand_trace(ora):
@@ -200,6 +219,11 @@ def test_cap_prunes_smallest(ora):
     expect = np.zeros(n, np.uint8)
     expect[order[:8]] = 1
     np.testing.assert_array_equal(r["mask"], expect)
+    assert set(np.where(r["mask"])[0]) == {0, 1, 2, 3, 4, 10, 11, 12}
+    # the cap is a fraction of all voxels, not of those seen this step: with 300 unseen voxels it stays 8
+    seen[600:900] = 0
+    r = ora.prune(w, seen, z, m, s, cap_ppm=8000)
+    assert r["n_pruned"] == 8
     assert set(np.where(r["mask"])[0]) == {0, 1, 2, 3, 4, 10, 11, 12}
 
 
@@ -318,6 +342,25 @@ def test_subdivide_eligibility(ora):
     r = ora.subdivide(sc, delta, np.ones(4, np.float32), np.ones(4, np.float32), seen, top_ppm=1000000,
                       kappa=1.0, l_max=16)
     assert list(r["selected"]) == [1, 0, 0, 0]
+    # the inequality is strict: h = kappa * delta exactly (kappa a power of two) is not eligible
+    for kappa in (1.0, 2.0, 0.5):
+        d = np.array([0.1 / kappa, 0.1 / kappa * 0.999, 0.1 / kappa * 1.001, 0.05 / kappa], np.float32)
+        assert np.float32(kappa) * d[0] == sc["geom"][0, 3]
+        r = ora.subdivide(sc, d, np.ones(4, np.float32), np.ones(4, np.float32), np.ones(4, np.uint8),
+                          top_ppm=1000000, kappa=kappa, l_max=17)
+        assert list(r["selected"]) == [0, 1, 0, 1]
+
+
+def test_subdivide_equal_priorities_take_the_smallest_ids(ora):
+    # With every priority equal, the budgeted top-k is the k eligible voxels with the smallest ids.
+    n = 100
+    sc = _scene_rand(n, 31)
+    sc["level"][:] = 4
+    sc["level"][[2, 5, 11]] = 16                        # at l_max: not eligible
+    r = ora.subdivide(sc, np.zeros(n, np.float32), np.full(n, 3.0, np.float32), np.full(n, 0.25, np.float32),
+                      np.ones(n, np.uint8), top_ppm=100000, l_max=16)
+    assert r["k"] == 10
+    assert list(np.where(r["selected"])[0]) == [0, 1, 3, 4, 6, 7, 8, 9, 10, 12]
 
 
 def test_compact_is_subdivision_without_splits(ora):
@@ -393,6 +436,22 @@ def test_lf_sobel_ramp_and_weights(ora):
     assert abs(r["w_tilde"].mean() - 1.0) < 1e-12
     # flat pixels weigh more than edges once gamma > 0
     assert np.all(r["w_tilde"].reshape(H, W)[:, 1] > r["w_tilde"].reshape(H, W)[:, W // 2])
+
+
+@pytest.mark.parametrize("W,H,pctl", [(23, 17, 990000), (8, 5, 900000), (1, 7, 500000)])
+def test_lf_edge_map_against_scipy(ora, W, H, pctl):
+    # s = clip(|Sobel Y| / P, 0, 1) with Y the channel mean, scipy's Sobel with a replicated border, and P the
+    # nearest-rank percentile (numpy's "inverted_cdf"); then w~ = (eps + 1 - s)^gamma / mean (Eq. 7-8).
+    from scipy import ndimage
+    gt = synth.random_image(W, H, seed=W + H).astype(np.float64)
+    Y = gt.reshape(H, W, 3).mean(axis=2)
+    mag = np.hypot(ndimage.sobel(Y, axis=1, mode="nearest"), ndimage.sobel(Y, axis=0, mode="nearest"))
+    P = np.percentile(mag.ravel(), pctl / 1e4, method="inverted_cdf")
+    s = np.clip(mag / P, 0, 1) if P > 0 else np.zeros_like(mag)
+    r = ora.lf_loss(gt + 0.05, gt, [(W, H)], gamma=0.7, eps=1e-3, pctl_ppm=pctl)
+    np.testing.assert_allclose(r["s"].reshape(H, W), s, rtol=1e-12, atol=1e-14)
+    w = (1e-3 + 1 - s) ** 0.7
+    np.testing.assert_allclose(r["w_tilde"].reshape(H, W), w / w.mean(), rtol=1e-12)
 
 
 def test_lf_gradient_central_differences(ora):

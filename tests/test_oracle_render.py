@@ -73,14 +73,16 @@ def test_single_voxel_axis_aligned(ora):
     np.testing.assert_allclose(r["w_max"][0], alpha, rtol=1e-12)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_single_voxel_oblique_chord(ora, seed):
-    # alpha = 1 - exp(-sigma * l) with l measured by bisection on the inside predicate.
+@pytest.mark.parametrize("seed,aspect", [(0, 1.0), (1, 1.0), (2, 1.0), (3, 1.37), (0, 0.71)])
+def test_single_voxel_oblique_chord(ora, seed, aspect):
+    # alpha = 1 - exp(-sigma * l) with l measured by bisection on the inside predicate;
+    # aspect != 1: non-square pixels (fy = aspect * fx).
     rng = np.random.default_rng(seed)
     center = rng.uniform(-0.3, 0.3, 3)
     h = 0.4
     cam = synth.look_at_camera(rng.uniform(-1, 1, 3) + np.array([0, 0, -4.0]), center + rng.uniform(-.1, .1, 3),
                                16, 16, 40.0)
+    cam["fy"] = float(np.float32(cam["fx"] * aspect))
     c = 1.7
     sc = synth.constant_voxel_scene([center], h, [c], [(1.0, 1.0, 1.0)])
     r = ora.render(sc, [cam], sh_degree=0)
@@ -206,6 +208,48 @@ def test_early_stop_rule(ora):
     assert r2["n_hit"][p] == 2
 
 
+def test_stop_count_at_the_threshold(ora):
+    # Six equal voxels on the centre ray, each of chord 0.5: T after k samples is exp(-k sigma / 2).
+    # sigma puts T_4 between t_stop / 2 and t_stop, so the ray stops after exactly four samples.
+    t_stop = 1e-4
+    sigma = float(np.float32(-math.log(0.75 * t_stop) / 2.0))
+    T = [math.exp(-k * 0.5 * sigma) for k in range(7)]
+    assert T[3] > t_stop and 0.5 * t_stop < T[4] < t_stop
+    cam = axis_camera()
+    sc = synth.constant_voxel_scene([[0, 0, z] for z in (2.0, 3.0, 4.0, 5.0, 6.0, 7.0)], 0.25, [sigma] * 6,
+                                    [(1, 1, 1)] * 6)
+    r = ora.render(sc, [cam], sh_degree=0, t_stop=t_stop)
+    assert r["n_hit"][4] == 4
+    assert abs(r["T"][4] - T[4]) < 1e-15
+    assert list(r["w_arg"][4:] >= 0) == [False, False]      # the voxels behind the stop are never reached
+    # a threshold just below T_4 takes one more sample, and one just above T_3 stops after three
+    assert ora.render(sc, [cam], sh_degree=0, t_stop=0.99 * T[4])["n_hit"][4] == 5
+    assert ora.render(sc, [cam], sh_degree=0, t_stop=1.01 * T[3])["n_hit"][4] == 3
+
+
+def test_w_max_ties_go_to_the_smallest_pixel(ora):
+    # A voxel so dense that alpha rounds to exactly 1 on every ray with a chord above 0.01: w = 1 ties on all
+    # of them, and the argmax is the smallest pixel id whose ray crosses it (chords by bisection).
+    W, H = 12, 10
+    cam = axis_camera(W, H, 8.0)
+    center, h = np.array([0.9, 0.35, 6.0]), 1.5
+    sc = synth.constant_voxel_scene([center], h, [1.0e4], [(1, 1, 1)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    c32, h32 = center.astype(np.float32).astype(np.float64), float(np.float32(h))
+    chords = []
+    for y in range(H):
+        for x in range(W):
+            o, d = ray_of(cam, x, y)
+            ch = chord_by_bisection(o, d, c32, h32, t_max=12.0, steps=6001)
+            chords.append(0.0 if ch is None else ch[1] - ch[0])
+    chords = np.array(chords)
+    first = int(np.argmax(chords > 0.01))
+    assert first > 0 and np.all(chords[:first] == 0.0)      # no grazing ray before it: the tie is well defined
+    assert (chords > 0.01).sum() > 10
+    assert r["w_max"][0] == 1.0
+    assert r["w_arg"][0] == first
+
+
 def test_culling_near_plane(ora):
     # A voxel entirely in front of z_near is culled even though the ray (t >= 0) crosses it.
     cam = axis_camera()
@@ -321,6 +365,44 @@ def test_backward_matches_central_differences(ora):
     assert checked >= 16
 
 
+def test_backward_through_the_clamps(ora):
+    # sigma = max(0, trilinear) and c = max(0, SH + 0.5): a voxel whose corners are all negative has zero density
+    # gradient, and a colour channel clamped at 0 has zero SH gradient -- both by finite differences (the loss
+    # does not move) and in the reverse pass; the unclamped channels of the same voxel still match.
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(24, 24, 45.0, 1.4, 75.0, 30.0, target=(0.5, 0.3, 0.5))
+    r0 = ora.render(sc, [cam])
+    vis = np.where(r0["w_arg"] >= 0)[0]
+    rng = np.random.default_rng(3)
+    dark, dim = (int(v) for v in rng.choice(vis, size=2, replace=False))
+    sc["density"][dark] = -np.abs(sc["density"][dark]) - np.float32(0.5)
+    sc["sh"][dim, 0::3] = 0.0
+    sc["sh"][dim, 0] = np.float32(-4.0)                   # red: 0.5 - 4 Y_0 < 0 in every direction
+    P = 24 * 24
+    gC = rng.normal(size=(P, 3))
+    gT = rng.normal(size=P)
+    r = ora.render(sc, [cam])
+    assert r["w_arg"][dim] >= 0                            # the dimmed voxel is still seen
+    bw = ora.render_backward(sc, [cam], gC, None, gT)
+
+    def loss(kind, v, idx, e):
+        sc2 = {k: np.array(a, copy=True) for k, a in sc.items()}
+        sc2[kind][v, idx] = np.float32(sc2[kind][v, idx] + e)
+        rr = ora.render(sc2, [cam])
+        return float((rr["rgb"] * gC).sum() + (rr["T"] * gT).sum()), float(sc2[kind][v, idx]) - float(sc[kind][v, idx])
+
+    for i in range(8):
+        assert bw["d_density"][dark, i] == 0.0
+        assert loss("density", dark, i, 1e-2)[0] == loss("density", dark, i, -1e-2)[0]
+    for j in range(16):
+        assert bw["d_sh"][dim, 3 * j] == 0.0
+    assert loss("sh", dim, 0, 1e-2)[0] == loss("sh", dim, 0, -1e-2)[0]
+    lp, hp = loss("sh", dim, 1, 1e-3)
+    lm, hm = loss("sh", dim, 1, -1e-3)
+    fd = (lp - lm) / (hp - hm)
+    assert abs(fd) > 1e-6 and abs(fd - bw["d_sh"][dim, 1]) <= 1e-4 * abs(fd)
+
+
 def test_fp32_sensitivity_bound_covers_ulp_perturbations(ora):
     # The per-pixel bound must cover what one-ulp FP32 perturbations of the voxel
     # positions and of the camera actually do to the FP64 image.
@@ -391,3 +473,78 @@ def test_near_plane_straddler_tiles_cover_hits(ora):
     assert checked > 50
     # and a straddler no longer covers the whole image
     assert any(len(cover.get(i, ())) < ((48 + 7) // 8) * ((40 + 7) // 8) for i in straddlers)
+
+
+@pytest.mark.parametrize("rotated", [False, True])
+def test_straddler_tiles_are_tight(ora, rotated):
+    # The FP32 tile rectangle of each voxel is that of the exact footprint of its part beyond the near plane,
+    # widened by the 1-pixel margin: the footprint's bounding box comes from the vertices of the clipped box
+    # in camera space (scipy's half-space intersection; a ratio of linear functions peaks at a vertex), and
+    # the rectangle's edges must sit on the tiles of that box +- 1 pixel, within 5e-3 pixel of rounding.
+    # The rotated camera sees the boxes' edges obliquely, so edges of every direction cross the near plane.
+    from scipy.spatial import HalfspaceIntersection
+    rng = np.random.default_rng(21)
+    n, ts, W, H, z_near = 60, 8, 48, 40, 0.3
+    if rotated:
+        cam = synth.look_at_camera([0.35, -0.25, -0.6], [0.05, 0.1, 0.5], W, H, 77.0, z_near=z_near)
+    else:
+        cam = axis_camera(W, H, 30.0)
+        cam["z_near"] = z_near
+    M = np.asarray(cam["w2c"], np.float64).reshape(3, 4)
+    R, t = M[:, :3], M[:, 3]
+    cc = np.c_[rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n), rng.uniform(0.1, 1.2, n)]
+    centers = (cc - t) @ R                               # camera-space centres mapped to the world
+    half = rng.uniform(0.05, 0.3, n)
+    sc = synth.constant_voxel_scene(centers, half, np.ones(n), np.ones((n, 3)) * 0.5)
+    pr = ora.pairs(sc, [cam], ts=ts)
+    tiles_x, tiles_y = (W + ts - 1) // ts, (H + ts - 1) // ts
+    rect = {}
+    for k, v in zip(pr["keys"], pr["vals"]):
+        tile = int(k >> np.uint64(32))
+        tx, ty = tile % tiles_x, tile // tiles_x
+        a = rect.setdefault(int(v), [tx, ty, tx, ty])
+        a[:] = [min(a[0], tx), min(a[1], ty), max(a[2], tx), max(a[3], ty)]
+    M = np.asarray(np.float32(cam["w2c"]), np.float64).reshape(3, 4)  # the FP32 camera both sides use
+    R, t = M[:, :3], M[:, 3]
+    g = sc["geom"].astype(np.float64)
+    zn = float(np.float32(z_near))
+    eps = 5e-3
+    lo = lambda a, e, m: min(max(math.floor((a - 1 + e) / ts), 0), m)
+    hi = lambda a, e, m: min(max(math.ceil((a + 1 + e) / ts), 0), m)
+    checked = straddling = 0
+    for i in range(n):
+        c, h = g[i, :3], g[i, 3]
+        corners = np.array([[c[0] + sx * h, c[1] + sy * h, c[2] + sz * h]
+                            for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]) @ R.T + t
+        zc = corners[:, 2]
+        if zc.max() < zn + 1e-3:
+            if zc.max() < zn - 1e-3:
+                assert i not in rect                 # wholly in front of the near plane: culled
+            continue
+        # world box a.x <= b as camera-space rows (R a, -(R a).t - b), plus z_cam >= z_near
+        rows = []
+        for ax in range(3):
+            for sgn in (-1.0, 1.0):
+                a = np.zeros(3)
+                a[ax] = sgn
+                b = sgn * c[ax] + h
+                ra = R @ a
+                rows.append(np.r_[ra, -ra @ t - b])
+        rows.append([0.0, 0.0, -1.0, zn])
+        far = corners[int(np.argmax(zc))]
+        inner = 0.97 * far + 0.03 * (np.asarray(c) @ R.T + t)
+        vx = HalfspaceIntersection(np.asarray(rows), inner).intersections
+        u = cam["fx"] * vx[:, 0] / vx[:, 2] + cam["cx"]
+        v = cam["fy"] * vx[:, 1] / vx[:, 2] + cam["cy"]
+        want = [(lo(u.min(), -eps, tiles_x), lo(u.min(), eps, tiles_x)),
+                (lo(v.min(), -eps, tiles_y), lo(v.min(), eps, tiles_y)),
+                (hi(u.max(), -eps, tiles_x), hi(u.max(), eps, tiles_x)),
+                (hi(v.max(), -eps, tiles_y), hi(v.max(), eps, tiles_y))]
+        if want[0][1] >= want[2][0] or want[1][1] >= want[3][0]:
+            continue                                  # off screen or empty: no pairs expected either way
+        got = rect[i][:2] + [rect[i][2] + 1, rect[i][3] + 1]
+        for e, (a, b) in zip(got, want):
+            assert a <= e <= b, (i, got, want)
+        checked += 1
+        straddling += zc.min() < zn
+    assert checked > 30 and straddling > 5
