@@ -330,24 +330,34 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        with open(self.path) as f:
+            return clock_summary(f)
+
+
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def clock_summary(lines):
+    """Median SM clock, the highest max clock and the throttle reasons seen active, from nvidia-smi CSV
+    lines in ``ClockSampler.FIELDS`` order (no header, no units); lines that do not parse are skipped.
+    None without a sample."""
+    sm, mx, reasons = [], [], set()
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            clock, max_clock = float(parts[1]), float(parts[2])
+        except ValueError:
+            continue
+        sm.append(clock)
+        mx.append(max_clock)
+        for name, v in zip(CLOCK_REASONS, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------------------- roofline
