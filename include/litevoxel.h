@@ -4,7 +4,7 @@
  * The library implements the data-parallel hot path of LiteVoxel's training
  * loop (arXiv 2511.02510): forward and backward passes of the differentiable
  * tile rasterizer for sparse octree voxels (Sec. III, Eq. 1-5), depth-quantile
- * pruning (Sec. IV-C, Eq. 11-12 with guards i and iii), priority-driven
+ * pruning (Sec. IV-C, Eq. 11-12 with guards i-iii), priority-driven
  * subdivision (Sec. IV-D, Eq. 13-16) and the low-frequency-weighted
  * photometric loss (Sec. IV-B, Eq. 7-10 and Eq. 18).
  *
@@ -19,9 +19,10 @@
  *    asynchronous on that stream unless `LV_FLAG_SYNC_CHECK` is set in the
  *    options, in which case the call synchronises the stream and returns the
  *    device-side status.
- *  - Host-detectable argument errors return LV_ERR_INVALID_ARG (nothing is
- *    launched); `lv_last_error()` describes the most recent failure of the
- *    calling thread.  Errors found on the device (pair or voxel capacity
+ *  - Host-detectable argument errors return LV_ERR_INVALID_ARG (a workspace
+ *    smaller than its size query: LV_ERR_WORKSPACE; an option that is not
+ *    built in: LV_ERR_UNSUPPORTED) and nothing is launched; `lv_last_error()`
+ *    describes the most recent failure of the calling thread.  Errors found on the device (pair or voxel capacity
  *    overflow, a bounded inter-block wait of the radix sort that gave up)
  *    are written to `d_status` (int32 device word, first error wins, the
  *    caller zeroes it; lv_check_status reads it) and the affected outputs
@@ -273,7 +274,7 @@ lv_status lv_render_pixels_f64(const lv_voxels* vox, const lv_camera* cams, int 
                                int64_t n_px, double* rgb, double* T, void* stream);
 
 /* ------------------------------------------------------------------ */
-/* depth-quantile pruning (Sec. IV-C, Eq. 11-12, guards i and iii)      */
+/* depth-quantile pruning (Sec. IV-C, Eq. 11-12, guards i-iii)          */
 /* ------------------------------------------------------------------ */
 
 typedef struct {

@@ -16,8 +16,10 @@
  *       statistics, FP32 with a fixed operation order (the binning step of the
  *       "differentiable tile rasterizer", Sec. II-A / Fig. 1).
  *   ora_prune   : Sec. IV-C, Eq. 11-12 (per-bin empirical-CDF quantile) with
- *       guard i (EMA + hysteresis) and guard iii (per-step cap); Eq. 14 depth
- *       normalisation for the bins.  FP32, fixed operation order.
+ *       guard i (EMA + hysteresis), guard ii (keep-halo) and guard iii
+ *       (per-step cap); the annealed, near/far-relaxed q_b; Eq. 14 depth
+ *       normalisation for the bins, optionally with running percentiles.
+ *       FP32, fixed operation order.
  *   ora_subdivide : Sec. IV-D, Eq. 13 (footprint eligibility), Eq. 14-16
  *       (depth-normalised far bias on the usefulness score), budgeted top-k
  *       and optimizer-state re-initialisation.  FP32, fixed operation order.

@@ -1,5 +1,5 @@
 // lv_adapt.cu -- depth-quantile pruning (LiteVoxel Sec. IV-C, Eq. 11-12 with
-// guards i and iii) and priority-driven subdivision (Sec. IV-D, Eq. 13-16)
+// guards i-iii) and priority-driven subdivision (Sec. IV-D, Eq. 13-16)
 // for sm_103a.  Every selection (percentiles, per-bin quantiles, the cap, the
 // top-k) is an exact radix select on order-preserving 32-bit keys, so the
 // integer outputs do not depend on thread scheduling; all FP32 decisions use
