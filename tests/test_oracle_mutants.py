@@ -1,7 +1,7 @@
 """Mutation check of the oracle's pins.
 
 Each mutant below is a copy of one oracle source (``oracle/lv_oracle.c``,
-``oracle/train_aux.py`` or ``oracle/vertex.py``) with one plausible mistake
+``oracle/train_aux.py``, ``oracle/vertex.py`` or ``oracle/inplace.py``) with one plausible mistake
 planted in it: a dropped term, a flipped sign, a swapped index or operand, an
 off-by-one rank, a strict comparison made loose.  Every mutant is built on its
 own (gcc for the C file; the numpy modules are loaded in place of the real
@@ -23,8 +23,9 @@ from concurrent.futures import ThreadPoolExecutor
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_FILES = ["tests/test_oracle_train.py", "tests/test_oracle_vertex.py", "tests/test_oracle_guards.py",
-             "tests/test_oracle_adapt.py", "tests/test_oracle_render.py", "tests/test_oracle_segment.py"]
+PIN_FILES = ["tests/test_oracle_train.py", "tests/test_oracle_vertex.py", "tests/test_oracle_inplace.py",
+             "tests/test_oracle_guards.py", "tests/test_oracle_adapt.py", "tests/test_oracle_render.py",
+             "tests/test_oracle_segment.py"]
 
 # (name, text in lv_oracle.c, replacement)
 MUTANTS = [
@@ -136,6 +137,13 @@ PY_MUTANTS = [
      "g = np.asarray(d_density, np.float64).reshape(-1, 8) - g_tv"),
     ("vertex key drops a coordinate", "vertex.py", "(q[..., 2] << (2 * COORD_BITS))", "(q[..., 2] << COORD_BITS)"),
     ("corner y bit read from z", "vertex.py", "1 if c & 2 else -1, 1 if c & 4", "1 if c & 4 else -1, 1 if c & 4"),
+    ("tail rows move in decreasing order", "inplace.py", "move_from = np.flatnonzero(occupied[n_new:]) + n_new",
+     "move_from = (np.flatnonzero(occupied[n_new:]) + n_new)[::-1]"),
+    ("children appended before the holes fill", "inplace.py",
+     "slots = np.concatenate([pruned[:min(h, others)], n + np.arange(max(0, others - h))])",
+     "slots = np.concatenate([n + np.arange(max(0, others - h)), pruned[:min(h, others)]])"),
+    ("child 0 not kept in the parent's row", "inplace.py", "child_dest[:, 0] = parents",
+     "child_dest[:, 0] = parents[::-1]"),
     ("scatter overwrites", "vertex.py", "np.add.at(out, np.asarray(vidx).ravel(), np.asarray(corners, np.float64).ravel())",
      "out[np.asarray(vidx).ravel()] = np.asarray(corners, np.float64).ravel()"),
 ]
