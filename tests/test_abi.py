@@ -51,3 +51,22 @@ def test_host_only_queries_work_without_gpu(lib):
     # look-back words (two 8-byte words per digit value and 2048 items: 2 bytes per pair)
     assert a > 0 and a + 10000 * 16 <= b <= a + 10000 * 18 + 8192
     assert L.lv_forward_workspace_size(1000, cams, 0, opts, 0) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library every call raises: there is no CPU fallback (checked in a child process
+    whose binding points at a path that does not exist)."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2511_02510_gb300 import litevoxel as L\n"
+        "L.LIB_PATH = %r\n"
+        "try:\n"
+        "    L.lv_prune_anneal_ppm(1.0, 0.0, 2.0)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(3)\n" % (ROOT, str(tmp_path / "nowhere" / "liblitevoxel.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "missing" in r.stdout, r.stdout + r.stderr
