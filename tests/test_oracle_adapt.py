@@ -479,3 +479,24 @@ def test_lf_per_view_independence(ora):
     a = ora.lf_loss(rgb[:48], gt[:48], [sizes[0]], gamma=0.5)
     b = ora.lf_loss(rgb[48:], gt[48:], [sizes[1]], gamma=0.5)
     np.testing.assert_allclose(both["loss"], [a["loss"][0], b["loss"][0]], rtol=1e-14)
+
+
+def test_pairs_of_two_views(ora):
+    # Binning two views at once: the second view's tiles follow the first view's, every pair of a single-view
+    # list appears with its tile id shifted by that offset, and the statistics are the per-view minima (z_min,
+    # delta_min) and the union (seen).
+    sc = synth.scene_tiny()
+    a = synth.orbit_camera(40, 28, 60.0, 1.6, 30.0, 25.0, target=(0.5, 0.4, 0.5))
+    b = synth.orbit_camera(24, 36, 50.0, 1.8, 140.0, 10.0, target=(0.5, 0.4, 0.5))
+    pa, pb, both = ora.pairs(sc, [a], ts=8), ora.pairs(sc, [b], ts=8), ora.pairs(sc, [a, b], ts=8)
+    ta = ((40 + 7) // 8) * ((28 + 7) // 8)
+    shift = np.uint64(ta) << np.uint64(32)
+    keys = np.concatenate([pa["keys"], pb["keys"] + shift])
+    vals = np.concatenate([pa["vals"], pb["vals"]])
+    order = np.lexsort((vals, keys))
+    np.testing.assert_array_equal(both["keys"], keys[order])
+    np.testing.assert_array_equal(both["vals"], vals[order])
+    np.testing.assert_array_equal(both["z_min"], np.minimum(pa["z_min"], pb["z_min"]))
+    np.testing.assert_array_equal(both["delta_min"], np.minimum(pa["delta_min"], pb["delta_min"]))
+    np.testing.assert_array_equal(both["seen"], pa["seen"] | pb["seen"])
+    assert (pa["z_min"] < pb["z_min"]).sum() > 10 and (pb["z_min"] < pa["z_min"]).sum() > 10

@@ -51,7 +51,12 @@ MUTANTS = [
     ("camera centre sign", "d->o[k] = -(d->R[0 * 3 + k] * d->t[0]", "d->o[k] = (d->R[0 * 3 + k] * d->t[0]"),
     ("exact segment: midpoint weight 2", "w8[i] = (wa[i] + 4.0 * w8[i] + wb[i]) / 6.0;",
      "w8[i] = (wa[i] + 2.0 * w8[i] + wb[i]) / 4.0;"),
+    ("second view's pixels start one early", "    free_lists(&L);\n    pix_off += (int64_t)cd.W * cd.H;\n  }\n  if (w_max) {",
+     "    free_lists(&L);\n    pix_off += (int64_t)cd.W * cd.H - 1;\n  }\n  if (w_max) {"),
     # backward
+    ("backward: second view's pixels start one early",
+     "    pix_off += (int64_t)cd.W * cd.H;\n  }\n  free(colors);\n  free(raw);",
+     "    pix_off += (int64_t)cd.W * cd.H - 1;\n  }\n  free(colors);\n  free(raw);"),
     ("backward drops the later samples", "double ds = q->l * (Tk * a - S - Tf * gT);",
      "double ds = q->l * (Tk * a - Tf * gT);"),
     ("backward T-gradient sign", "double ds = q->l * (Tk * a - S - Tf * gT);",
@@ -69,6 +74,10 @@ MUTANTS = [
      "if (x->val != y->val) return x->val > y->val ? -1 : 1;\n  return 0;\n}\n\n/*\n * Sorted"),
     ("delta from the centre depth without the near clamp", "float dl = zs / c->fx;", "float dl = b.zc / c->fx;"),
     ("near-plane crossing parameter", "float f = (c->z_near - pz[i]) / dz;", "float f = (c->z_near - pz[j]) / dz;"),
+    ("second view's tiles start one early", "tile_off += (int64_t)tiles_x * tiles_y;",
+     "tile_off += (int64_t)tiles_x * tiles_y - 1;"),
+    ("z_min from the last view", "if (zs < z_min[i]) z_min[i] = zs;", "if (1) z_min[i] = zs;"),
+    ("delta_min from the last view", "if (dl < delta_min[i]) delta_min[i] = dl;", "if (1) delta_min[i] = dl;"),
     # pruning, Eq. 11-12 and guards i-iii
     ("EMA weights swapped", "float a = one_minus_alpha * m[i];\n    float c = alpha * x;",
      "float a = alpha * m[i];\n    float c = one_minus_alpha * x;"),

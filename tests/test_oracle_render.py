@@ -548,3 +548,44 @@ def test_straddler_tiles_are_tight(ora, rotated):
         checked += 1
         straddling += zc.min() < zn
     assert checked > 30 and straddling > 5
+
+
+def _two_views():
+    sc = synth.scene_tiny()
+    a = synth.orbit_camera(40, 28, 60.0, 1.6, 30.0, 25.0, target=(0.5, 0.4, 0.5))
+    b = synth.orbit_camera(24, 36, 50.0, 1.8, 140.0, 10.0, target=(0.5, 0.4, 0.5))
+    return sc, a, b
+
+
+def test_views_render_independently(ora):
+    # Views are independent: rendering two at once gives each view's image in view-major order, and
+    # w_max accumulates over both -- the larger of the two, at the global id (offset + local id) of its pixel.
+    sc, a, b = _two_views()
+    both = ora.render(sc, [a, b])
+    ra, rb = ora.render(sc, [a]), ora.render(sc, [b])
+    na = 40 * 28
+    for k in ("rgb", "depth", "T", "n_hit"):
+        np.testing.assert_array_equal(both[k][:na], ra[k])
+        np.testing.assert_array_equal(both[k][na:], rb[k])
+    wa, wb = ra["w_max"], rb["w_max"]
+    ga = ra["w_arg"]
+    gb = np.where(rb["w_arg"] >= 0, rb["w_arg"] + na, -1)
+    take_b = (wb > wa) | ((ga < 0) & (gb >= 0))
+    np.testing.assert_array_equal(both["w_max"], np.where(take_b, wb, wa))
+    np.testing.assert_array_equal(both["w_arg"], np.where(take_b, gb, ga))
+    assert take_b.sum() > 10 and (~take_b & (ga >= 0)).sum() > 10       # both views contribute maxima
+
+
+def test_views_backward_add_up(ora):
+    # The gradient of a loss over two views is the sum of the two single-view gradients.
+    sc, a, b = _two_views()
+    na, nb = 40 * 28, 24 * 36
+    rng = np.random.default_rng(11)
+    gC, gT = rng.normal(size=(na + nb, 3)), rng.normal(size=na + nb)
+    both = ora.render_backward(sc, [a, b], gC, None, gT)
+    sa = ora.render_backward(sc, [a], gC[:na], None, gT[:na])
+    sb = ora.render_backward(sc, [b], gC[na:], None, gT[na:])
+    for k in ("d_density", "d_sh"):
+        ref = sa[k] + sb[k]
+        np.testing.assert_allclose(both[k], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+        assert np.abs(sa[k]).max() > 0 and np.abs(sb[k]).max() > 0
