@@ -225,6 +225,8 @@ def test_cap_prunes_smallest(ora):
     r = ora.prune(w, seen, z, m, s, cap_ppm=8000)
     assert r["n_pruned"] == 8
     assert set(np.where(r["mask"])[0]) == {0, 1, 2, 3, 4, 10, 11, 12}
+    # "at most" the fraction: 0.85 % of 1000 voxels prunes 8, never 9
+    assert ora.prune(w, seen, z, m, s, cap_ppm=8500)["n_pruned"] == 8
 
 
 def test_prune_degenerate_cases(ora):

@@ -39,6 +39,13 @@ MUTANTS = [
     ("SH basis repeats a function", "Y[4] = c2a * x * y;", "Y[4] = c2a * x * z;"),
     ("SH degree-3 constant", "double c3d = sqrt(7.0 / (16.0 * pi));", "double c3d = sqrt(7.0 / (4.0 * pi));"),
     ("colour offset dropped", "raw[c] = s + 0.5;", "raw[c] = s;"),
+    ("SH count of degree 3 is 10", "static int sh_count(int degree) { return (degree + 1) * (degree + 1); }",
+     "static int sh_count(int degree) { return degree * degree + 1; }"),
+    ("view direction reversed",
+     "double d[3] = {(double)geom[4 * i] - cd->o[0], (double)geom[4 * i + 1] - cd->o[1],\n                   (double)geom[4 * i + 2] - cd->o[2]};",
+     "double d[3] = {cd->o[0] - (double)geom[4 * i], cd->o[1] - (double)geom[4 * i + 1],\n                   cd->o[2] - (double)geom[4 * i + 2]};"),
+    ("near-plane parameter taken as depth", "return c->z_near / dz;", "return c->z_near;"),
+    ("candidates ordered by the near face", "    dkey[i] = f32_order_key(b.zc);\n", "    dkey[i] = f32_order_key(b.zc - g[3]);\n"),
     ("depth at chord entry", "*depth += w * tm;", "*depth += w * t_in;"),
     ("stop threshold halved", "if (T < t_stop) break;", "if (T < 0.5 * t_stop) break;"),
     ("w_max stores alpha", "wmax[id] = w;\n        warg[id] = gid;", "wmax[id] = alpha;\n        warg[id] = gid;"),
@@ -88,6 +95,7 @@ MUTANTS = [
     ("cap prunes the largest", "for (int64_t r = 0; r < cap; ++r) prune_mask[list[r].val] = 1;",
      "for (int64_t r = 0; r < cap; ++r) prune_mask[list[n_cand - 1 - r].val] = 1;"),
     ("cap counted over seen voxels", "int64_t cap = ppm_floor(cap_ppm, n);", "int64_t cap = ppm_floor(cap_ppm, ns);"),
+    ("cap rounded up", "int64_t cap = ppm_floor(cap_ppm, n);", "int64_t cap = ppm_ceil(cap_ppm, n);"),
     ("depth bins reversed", "float num = z - p_lo;", "float num = p_hi - z;"),
     ("percentile rank rounded down", "int64_t k_lo = ppm_ceil(lo_ppm, m), k_hi = ppm_ceil(hi_ppm, m);",
      "int64_t k_lo = ppm_floor(lo_ppm, m), k_hi = ppm_floor(hi_ppm, m);"),

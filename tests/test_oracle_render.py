@@ -589,3 +589,71 @@ def test_views_backward_add_up(ora):
         ref = sa[k] + sb[k]
         np.testing.assert_allclose(both[k], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
         assert np.abs(sa[k]).max() > 0 and np.abs(sb[k]).max() > 0
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_sh_colour_uses_every_coefficient_of_the_degree(ora, degree):
+    # c = max(0, 0.5 + sum_{j < (degree+1)^2} sh_j Y_j(dir)), dir from the camera centre to the voxel centre:
+    # a voxel whose only nonzero coefficient is the last one of its degree shows 0.5 + sh Y_last(dir), and
+    # coefficients beyond the degree are ignored.  Y comes from the basis pinned by orthonormality.
+    cam = synth.look_at_camera([2.5, -0.4, -1.5], [0.15, 0.1, 0.05], 9, 9, 40.0)
+    center = np.array([0.15, 0.1, 0.05])
+    sc = synth.constant_voxel_scene([center], 0.6, [50.0], [(0.5, 0.5, 0.5)])   # opaque: rgb ~ colour
+    last = (degree + 1) ** 2 - 1
+    sc["sh"][0, :] = 0.0
+    sc["sh"][0, 3 * last:3 * last + 3] = np.float32([0.9, -0.7, 0.4])
+    if last + 1 < 16:
+        sc["sh"][0, 3 * (last + 1):] = np.float32(5.0)                   # beyond the degree: unused
+    r = ora.render(sc, [cam], sh_degree=degree)
+    o, _ = ray_of(cam, 4, 4)
+    c32 = center.astype(np.float32).astype(np.float64)
+    direction = (c32 - o) / np.linalg.norm(c32 - o)
+    Y = ora.sh_basis(direction)[last]
+    col = np.maximum(0.0, 0.5 + np.float32([0.9, -0.7, 0.4]).astype(np.float64) * Y)
+    p = 4 * 9 + 4
+    alpha = 1.0 - r["T"][p]
+    assert alpha > 0.999
+    np.testing.assert_allclose(r["rgb"][p], alpha * col, rtol=0, atol=1e-7)
+    assert abs(Y) > 0.05                                  # the test direction does exercise the coefficient
+
+
+def test_near_plane_clips_oblique_chords(ora):
+    # Off the axis the chord starts where the ray's camera depth reaches z_near, at t = z_near / d_z.
+    cam = axis_camera(11, 9, 4.0)
+    cam["z_near"] = 0.5
+    center, h, sigma = np.array([0.1, -0.05, 0.62]), 0.3, 2.0
+    sc = synth.constant_voxel_scene([center], h, [sigma], [(1, 1, 1)])
+    r = ora.render(sc, [cam], sh_degree=0)
+    c32, h32 = center.astype(np.float32).astype(np.float64), float(np.float32(h))
+    zn = float(np.float32(0.5))
+    checked = 0
+    for y in range(9):
+        for x in range(11):
+            o, d = ray_of(cam, x, y)
+            ch = chord_by_bisection(o, d, c32, h32, t_max=3.0, steps=30001)
+            p = y * 11 + x
+            if ch is None:
+                continue
+            t0 = max(ch[0], zn / d[2])
+            l = max(0.0, ch[1] - t0)
+            assert abs(r["T"][p] - math.exp(-float(np.float32(sigma)) * l)) < 1e-6, (x, y)
+            checked += abs(d[2] - 1.0) > 1e-3 and l > 0
+    assert checked > 15
+
+
+def test_samples_are_ordered_by_centre_depth(ora):
+    # Eq. 2 composites front to back in the order of the voxels' camera-space centre depth (ties by id),
+    # whatever order the rays enter them: every traced pixel's samples come sorted by that depth.
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(32, 32, 60.0, 1.6, 200.0, 35.0, target=(0.5, 0.4, 0.5))
+    M = np.asarray(cam["w2c"], np.float64).reshape(3, 4)
+    zc = sc["geom"][:, :3].astype(np.float64) @ M[2, :3] + M[2, 3]
+    traced = 0
+    for (x, y) in [(16, 16), (10, 20), (20, 8), (5, 5), (28, 30), (12, 3), (3, 25)]:
+        tr = ora.trace_pixel(sc, cam, x, y, t_stop=1e-12)
+        ids = np.asarray(tr["ids"], np.int64)
+        if len(ids) < 2:
+            continue
+        np.testing.assert_array_equal(ids, ids[np.lexsort((ids, zc[ids]))])
+        traced += len(ids) >= 4
+    assert traced >= 3
