@@ -502,3 +502,35 @@ def test_pairs_of_two_views(ora):
     np.testing.assert_array_equal(both["delta_min"], np.minimum(pa["delta_min"], pb["delta_min"]))
     np.testing.assert_array_equal(both["seen"], pa["seen"] | pb["seen"])
     assert (pa["z_min"] < pb["z_min"]).sum() > 10 and (pb["z_min"] < pa["z_min"]).sum() > 10
+
+
+def test_seen_means_at_least_one_pair(ora):
+    # A voxel is seen when it covers at least one tile of some view: exactly the voxels with a pair.  Many
+    # voxels of this scene lie beside the narrow view (in front of the camera, not culled, but off screen).
+    sc = synth.scene_tiny()
+    cam = synth.orbit_camera(40, 30, 25.0, 1.2, 60.0, 20.0, target=(0.45, 0.35, 0.5))
+    pr = ora.pairs(sc, [cam], ts=8)
+    has_pair = np.isin(np.arange(sc["geom"].shape[0]), pr["vals"])
+    np.testing.assert_array_equal(pr["seen"].astype(bool), has_pair)
+    np.testing.assert_array_equal(np.isfinite(pr["z_min"]), has_pair)
+    M = np.asarray(cam["w2c"], np.float64).reshape(3, 4)
+    z = sc["geom"][:, :3].astype(np.float64) @ M[2, :3] + M[2, 3]
+    assert ((z > 0.2) & ~has_pair).sum() > 100 and has_pair.sum() > 100
+
+
+def test_depth_keys_order_negative_centre_depths(ora):
+    # A large voxel whose centre lies behind the camera (negative depth) but whose far part is beyond the near
+    # plane comes first in its tiles: the depth key orders negative depths below positive ones.
+    cam = {"width": 32, "height": 32, "fx": 20.0, "fy": 20.0, "cx": 16.0, "cy": 16.0,
+           "w2c": [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], "z_near": 0.05}
+    centers = [[0.0, 0.0, -0.3], [0.05, 0.02, 0.8], [-0.1, 0.05, 1.6], [0.02, -0.03, -0.1]]
+    sc = synth.constant_voxel_scene(centers, [0.5, 0.1, 0.2, 0.25], np.ones(4), np.ones((4, 3)) * 0.5)
+    pr = ora.pairs(sc, [cam], ts=8)
+    zc = np.array([c[2] for c in centers])
+    tile = (pr["keys"] >> np.uint64(32)).astype(np.int64)
+    multi = 0
+    for t in np.unique(tile):
+        ids = pr["vals"][tile == t].astype(np.int64)
+        np.testing.assert_array_equal(ids, ids[np.argsort(zc[ids], kind="stable")])
+        multi += len(ids) >= 3 and (zc[ids] < 0).sum() == 2
+    assert multi > 0                               # some tile holds both negative-depth voxels and a positive one

@@ -81,6 +81,11 @@ MUTANTS = [
      "if (x->val != y->val) return x->val > y->val ? -1 : 1;\n  return 0;\n}\n\n/*\n * Sorted"),
     ("delta from the centre depth without the near clamp", "float dl = zs / c->fx;", "float dl = b.zc / c->fx;"),
     ("near-plane crossing parameter", "float f = (c->z_near - pz[i]) / dz;", "float f = (c->z_near - pz[j]) / dz;"),
+    ("off-screen voxels marked seen", "      if (b.count == 0) continue;\n      float zs",
+     "      if (b.culled) continue;\n      float zs"),
+    ("depth key wrong for negative depths", "return (u & 0x80000000u) ? ~u : (u | 0x80000000u);",
+     "return u | 0x80000000u;"),
+    ("tile range end one short", "ranges[2 * g + 1] = (uint32_t)(q + 1);", "ranges[2 * g + 1] = (uint32_t)q;"),
     ("second view's tiles start one early", "tile_off += (int64_t)tiles_x * tiles_y;",
      "tile_off += (int64_t)tiles_x * tiles_y - 1;"),
     ("z_min from the last view", "if (zs < z_min[i]) z_min[i] = zs;", "if (1) z_min[i] = zs;"),
