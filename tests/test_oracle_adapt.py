@@ -160,6 +160,12 @@ def test_hysteresis_band_holds_state(ora):
     np.testing.assert_allclose(r1["m"], [0.45, 0.55, 0.55], rtol=1e-6)
     assert list(r1["s"]) == [1, 1, 1] and list(r2["s"]) == [0, 0, 0]
     assert r1["n_pruned"] == 0 and r2["n_pruned"] == 3
+    # the band is closed: m landing exactly on m_low or m_high (exact in FP32 with alpha = 1/2) keeps the state
+    m_edge = np.array([0.6, 0.4, 0.4], np.float32)             # 0.6 / 2 = 0.3 ; 0.4 / 2 + 1/2 = 0.7
+    r3 = ora.prune(w, seen, z, m_edge, s_in, q_ppm=330000, cap_ppm=1000000, ema_alpha=0.5)
+    r4 = ora.prune(w, seen, z, m_edge, s_out, q_ppm=330000, cap_ppm=1000000, ema_alpha=0.5)
+    assert r3["m"][0] == np.float32(0.3) and r3["m"][1] == np.float32(0.7)
+    assert list(r3["s"]) == [1, 1, 1] and list(r4["s"]) == [0, 0, 0]
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])

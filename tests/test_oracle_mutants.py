@@ -95,6 +95,8 @@ MUTANTS = [
      "float a = alpha * m[i];\n    float c = one_minus_alpha * x;"),
     ("hysteresis thresholds swapped", "if (mm < m_low) s[i] = 0;\n    else if (mm > m_high) s[i] = 1;",
      "if (mm < m_high) s[i] = 0;\n    else if (mm > m_low) s[i] = 1;"),
+    ("hysteresis band open at m_low", "if (mm < m_low) s[i] = 0;", "if (mm <= m_low) s[i] = 0;"),
+    ("hysteresis band open at m_high", "else if (mm > m_high) s[i] = 1;", "else if (mm >= m_high) s[i] = 1;"),
     ("quantile rank rounded down", "int64_t k = ppm_ceil(qb, cnt[b]);", "int64_t k = ppm_floor(qb, cnt[b]);"),
     ("inside score at the threshold", "w_max[i] > tau[bin[i]]", "w_max[i] >= tau[bin[i]]"),
     ("cap prunes the largest", "for (int64_t r = 0; r < cap; ++r) prune_mask[list[r].val] = 1;",
