@@ -7,7 +7,6 @@ so masks, EMA values, states, selections and child arrays must match bit for
 bit.  The loss is compared with the FP64 oracle at 1e-5 relative (FP32
 per-pixel terms, FP64 sums).
 """
-import math
 
 import numpy as np
 import pytest

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import gpu_forward, np_
+from gpu_helpers import np_
 from paper_2511_02510_gb300 import synth
 from paper_2511_02510_gb300.raster import RasterContext
 from test_gpu_render import GRAD_TOL, _grad_err, cam_far, cam_near, compare_images

@@ -11,7 +11,6 @@ Tolerances (from the arithmetic):
  - gradients: within 1e-4 of the oracle's, relative to the largest gradient
    magnitude (FP32 atomics reorder the sums).
 """
-import math
 
 import numpy as np
 import pytest

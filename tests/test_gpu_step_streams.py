@@ -2,7 +2,6 @@
 and the subdivision selection beside the backward) computes what the one-stream
 step computes: the same bits for every output that has a fixed summation order,
 and the same gradients up to the order of the FP32 atomic sums."""
-import numpy as np
 import pytest
 import torch
 

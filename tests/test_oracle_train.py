@@ -8,7 +8,6 @@ hand-traced two-step Adam sequence.
 import math
 
 import numpy as np
-import pytest
 
 from oracle import train_aux as TA
 
