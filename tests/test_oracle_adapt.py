@@ -301,8 +301,10 @@ def test_subdivide_children_geometry_and_fields(ora):
     aux_m = np.array([[0.3] * 8], np.float32)
     aux_e = np.array([0.42], np.float32)
     aux_s = np.array([0], np.uint8)
+    aux_h = np.array([[7, 9, 11]], np.uint16)            # 2-byte elements: FP16 moments, for example
     r = ora.subdivide(sc, np.zeros(1, np.float32), np.ones(1, np.float32), np.ones(1, np.float32),
-                      np.ones(1, np.uint8), top_ppm=1000000, aux=[(aux_m, 0.0), (aux_e, 1.0), (aux_s, 1)])
+                      np.ones(1, np.uint8), top_ppm=1000000,
+                      aux=[(aux_m, 0.0), (aux_e, 1.0), (aux_s, 1), (aux_h, 0x3C00)])
     assert r["n_new"] == 8
     g = r["geom"]
     np.testing.assert_array_equal(g[:, 3], 0.25)
@@ -314,6 +316,7 @@ def test_subdivide_children_geometry_and_fields(ora):
         np.testing.assert_allclose(r["density"][i], cc @ a + b, atol=1e-5)
     assert np.all(r["sh"] == sc["sh"][0])
     assert np.all(r["aux"][0] == 0) and np.all(r["aux"][1] == 1.0) and np.all(r["aux"][2] == 1)
+    assert r["aux"][3].shape == (8, 3) and np.all(r["aux"][3] == 0x3C00)   # each child element takes the fill
     # volumes add up
     assert abs((8 * g[:, 3] ** 3).sum() - 8 * 0.5 ** 3) < 1e-12
 

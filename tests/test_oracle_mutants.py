@@ -129,6 +129,12 @@ MUTANTS = [
      "q[1] = (float)((j >> 1) & 1);"),
     ("child lerp order y before x", "float cy0 = lerp32(cx[0], cx[1], q[1]);", "float cy0 = lerp32(cx[0], cx[2], q[1]);"),
     ("child half size", "float hc = g[3] * 0.5f;", "float hc = g[3] * 0.25f;"),
+    ("2-byte child fill dropped",
+     "else if (aux_bytes[a] == 2) { uint16_t f = (uint16_t)aux_fill[a]; memcpy(dst, &f, 2); }",
+     "else if (aux_bytes[a] == 2) { uint16_t f = 0; memcpy(dst, &f, 2); }"),
+    ("survivor aux rows from the wrong voxel",
+     "memcpy((char*)aux_out[a] + eb * (size_t)o, (const char*)aux_in[a] + eb * (size_t)i, eb);",
+     "memcpy((char*)aux_out[a] + eb * (size_t)o, (const char*)aux_in[a] + eb * (size_t)o, eb);"),
     # LF-weighted loss, Eq. 7-10 and 18
     ("weight not inverted", "w[p] = pow(eps + 1.0 - s, gamma);", "w[p] = pow(eps + s, gamma);"),
     ("weight mean normalisation dropped", "double wt = w[p] / mean;", "double wt = w[p];"),
