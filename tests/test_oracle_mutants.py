@@ -165,6 +165,9 @@ PY_MUTANTS = [
      "m = beta1 * np.asarray(m, np.float64) + (1.0 - beta2) * g"),
     ("L_tv gradient subtracted", "g = np.asarray(d_density, np.float64).reshape(-1, 8) + g_tv",
      "g = np.asarray(d_density, np.float64).reshape(-1, 8) - g_tv"),
+    ("vertex ids ordered by x first", "vertex.py",
+     "keys = q[..., 0] | (q[..., 1] << COORD_BITS) | (q[..., 2] << (2 * COORD_BITS))",
+     "keys = q[..., 2] | (q[..., 1] << COORD_BITS) | (q[..., 0] << (2 * COORD_BITS))"),
     ("vertex key drops a coordinate", "vertex.py", "(q[..., 2] << (2 * COORD_BITS))", "(q[..., 2] << COORD_BITS)"),
     ("corner y bit read from z", "vertex.py", "1 if c & 2 else -1, 1 if c & 4", "1 if c & 4 else -1, 1 if c & 4"),
     ("tail rows move in decreasing order", "inplace.py", "move_from = np.flatnonzero(occupied[n_new:]) + n_new",

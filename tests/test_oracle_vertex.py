@@ -36,6 +36,21 @@ def test_regular_block_counts_and_sharing():
             assert shared == {1: 4, 2: 2, 3: 1}[int(d.sum())]
 
 
+def test_vertex_ids_are_ranks_in_z_y_x_order():
+    # On a 2 x 2 x 2 block the vertices form a 3 x 3 x 3 grid; ids are the ranks of the points ordered by
+    # z, then y, then x: grid point (i, j, k) has id i + 3 j + 9 k.  Corner c of a voxel is at bits
+    # (c & 1, c & 2, c & 4) = (+x, +y, +z).
+    h = 0.25
+    sc = block(2, h)
+    vidx, nv = VX.vertex_index(sc["geom"], h)
+    assert nv == 27
+    for v, (a, b, c) in enumerate(itertools.product(range(2), repeat=3)):
+        # block() lays voxels out with the last index fastest: voxel v sits at grid cell (a, b, c) = (x, y, z)
+        for corner in range(8):
+            i, j, k = a + (corner & 1), b + ((corner >> 1) & 1), c + ((corner >> 2) & 1)
+            assert vidx[v, corner] == i + 3 * j + 9 * k, (v, corner)
+
+
 def test_level_change_shares_coincident_corners():
     # a coarse voxel (h = 1/4) beside a face of four fine voxels (h = 1/8): the coarse face's 4 corners
     # coincide with fine corners; the fine face's centre and edge midpoints are fine-only
