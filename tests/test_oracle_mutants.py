@@ -149,6 +149,15 @@ MUTANTS = [
     ("luminance weights", "Y[p] = (G[3 * p] + G[3 * p + 1] + G[3 * p + 2]) / 3.0;",
      "Y[p] = (G[3 * p] + G[3 * p + 1] + G[3 * p + 1]) / 3.0;"),
     ("gamma ramp normalised by t1", "return gamma_max * (t - t0) / (t1 - t0);", "return gamma_max * (t - t0) / t1;"),
+    ("Sobel wraps the bottom border", "int ym = y > 0 ? y - 1 : 0, yp = y < H - 1 ? y + 1 : H - 1;",
+     "int ym = y > 0 ? y - 1 : 0, yp = y < H - 1 ? y + 1 : 0;"),
+    ("loss gradient sign", "        double r = R[3 * p + c] - G[3 * p + c];", "        double r = G[3 * p + c] - R[3 * p + c];"),
+    # a few more across the path
+    ("z_min without the near clamp", "      float zs = fmaxf(b.zc, c->z_near);", "      float zs = b.zc;"),
+    ("keep-halo ignored", "    if (s[i] == 0 && !prot) {", "    if (s[i] == 0) {"),
+    ("trilinear z weight flipped", "double wz = (i & 4) ? u[2] : 1.0 - u[2];", "double wz = (i & 4) ? 1.0 - u[2] : u[2];"),
+    ("backward colour gradient without the weight", "atomic_add(&dcol[3 * (int64_t)q->id + ch], w * gC[ch]);",
+     "atomic_add(&dcol[3 * (int64_t)q->id + ch], gC[ch]);"),
 ]
 
 # the numpy parts of the oracle: (name, file under oracle/, text, replacement)
