@@ -406,29 +406,64 @@ static int slab64x(const double* o, const double* d, double t_near, const float*
 }
 
 /*
- * Sensitivity of one sample to FP32 geometry.  An FP32 implementation sees a
- * ray and voxel positions perturbed by a few units of the last place: a
- * lateral displacement of about U * t at distance t, U = 2^-21.  A slab plane
- * crossing t_a = (p_a - o_a) / d_a then moves by U t / |d_a|, so the chord
- * moves by up to dl = U (t_in / |d_in| + t_out / |d_out| + t_out), and the
- * midpoint by dp = U (t_mid + t_in / |d_in| + t_out / |d_out|).  The optical
- * depth x = sigma l moves by dx <= sigma dl + l |grad sigma| dp with
- * |grad sigma| <= sqrt(3) (max - min corner) / (2h).  Used only to bound the
- * admissible FP32-vs-FP64 difference of a pixel; it changes no result.
+ * FP32 shifts of one chord (test tolerances only), for a slab test evaluated
+ * in FP32 from a rounded camera-relative centre and a rounded ray direction:
+ * with u = 2^-24, each direction component within (7u / |d_a| + 5u) relative
+ * (camera transform, normalisation, reciprocal), each centre coordinate within
+ * u (|g_a - o_a| + 2 |o_a|), each crossing rounded at its own magnitude, a
+ * near-plane entry within 4u.  Entry and exit through the same pair of slab
+ * planes share the rounded centre, which cancels from the chord.
+ *   dl: how far the chord may move; dp: how far the midpoint sample position
+ *   may move; res: the largest t_in - t_out at which an FP32 test may still
+ *   report a hit.
  */
-#define ORA_FP32_U (1.0 / 2097152.0)
-static double fp32_dx(const float* g, const float* dens8, double sigma, double l, double t_in, double t_out,
-                      double din, double dout) {
-  double S = (din > 0.0 ? t_in / din : 0.0) + (dout > 0.0 ? t_out / dout : 0.0);
-  double dl = ORA_FP32_U * (S + t_out);
-  double dmin = dens8[0], dmax = dens8[0];
-  for (int i = 1; i < 8; ++i) {
-    if (dens8[i] < dmin) dmin = dens8[i];
-    if (dens8[i] > dmax) dmax = dens8[i];
+#define ORA_U32 (1.0 / 16777216.0)
+static void chord_shifts(const double* o, const double* d, double t_near, const float* g, double t_in, double t_out,
+                         double* dl, double* dp, double* res) {
+  const double u = ORA_U32;
+  int ain = -1, aout = -1;
+  double tn_best = -INFINITY, tf_best = INFINITY, q[3] = {0, 0, 0}, eta[3] = {0, 0, 0}, gam[3], ad[3];
+  double gmax = 0.0, gn = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double ga = (double)g[a] - o[a];
+    gam[a] = u * (fabs(ga) + 2.0 * fabs(o[a]));
+    gmax = gam[a] > gmax ? gam[a] : gmax;
+    gn += ga * ga;
+    ad[a] = fabs(d[a]);
+    if (d[a] == 0.0) continue;
+    q[a] = fabs(ga / d[a]);
+    eta[a] = 7.0 * u / ad[a] + 5.0 * u;
+    double t1 = (ga - (double)g[3]) / d[a], t2 = (ga + (double)g[3]) / d[a];
+    double tn = t1 < t2 ? t1 : t2, tf = t1 < t2 ? t2 : t1;
+    if (tn > tn_best) { tn_best = tn; ain = a; }
+    if (tf < tf_best) { tf_best = tf; aout = a; }
   }
-  double grad = 1.7320508075688772 * (dmax - dmin) / (2.0 * (double)g[3]);
-  double dp = ORA_FP32_U * (0.5 * (t_in + t_out) + S);
-  return sigma * dl + (l > 0.0 ? l : dl) * grad * dp;
+  int clamped = !(tn_best >= t_near);
+  double e_in = clamped || ain < 0 ? 4.0 * u * fabs(t_in)
+                                   : fabs(t_in) * eta[ain] + gam[ain] / ad[ain] + u * (q[ain] + fabs(t_in));
+  double e_out = aout < 0 ? 0.0 : fabs(t_out) * eta[aout] + gam[aout] / ad[aout] + u * (q[aout] + fabs(t_out));
+  double l = fabs(t_out - t_in);
+  if (!clamped && ain >= 0 && ain == aout)
+    *dl = l * eta[ain] + u * (fabs(t_in) + fabs(t_out) + l);
+  else
+    *dl = e_in + e_out + u * l;
+  double tm = 0.5 * fabs(t_in + t_out);
+  *dp = 0.5 * (e_in + e_out) + 13.0 * u * tm + gmax + 2.0 * u * (tm + sqrt(gn));
+  *res = e_in + e_out;
+}
+
+/* FP32 shifts of a sample (test tolerances only): chord (dl), midpoint (dp) and optical depth x = sigma l
+ * (dx): the chord shift times sigma plus the chord times the largest density gradient of the trilinear
+ * field, sqrt(3) (max - min corner) / (2h), times the midpoint shift */
+static void sample_shift(const double* o, const double* d, double t_near, const float* g, const float* d8,
+                         double sigma, double l, double t_in, double t_out, double* dl, double* dp, double* dx) {
+  double res, cmin = d8[0], cmx = d8[0];
+  chord_shifts(o, d, t_near, g, t_in, t_out, dl, dp, &res);
+  for (int i = 1; i < 8; ++i) {
+    cmin = d8[i] < cmin ? d8[i] : cmin;
+    cmx = d8[i] > cmx ? d8[i] : cmx;
+  }
+  *dx = sigma * *dl + l * 1.7320508075688772 * ((double)cmx - (double)cmin) / (2.0 * (double)g[3]) * *dp;
 }
 
 /* trilinear weights of the 8 corners at local coordinates u in [0,1]^3 */
@@ -552,6 +587,15 @@ typedef struct {
   uint32_t id;
   double l, t_mid, sigma_raw, alpha, T_before;
   double w8[8]; /* d sigma_raw / d corner_i */
+  /* Test tolerances only (no result depends on them): how far an FP32
+   * evaluation may move the chord (dl), the midpoint (dp) and the optical depth
+   * sigma*l (dx; sample_shift); the largest |corner density| (dmax) and the voxel's
+   * half size (h).  ghost = 1 marks a near miss, a voxel the FP64 ray misses by
+   * less than an FP32 chord test can resolve (l = 0, alpha = 0, dl = the
+   * resolution): such entries are recorded only on request and never enter a
+   * result. */
+  double dl, dp, dx, dmax, dabs, h; /* dabs: sum_i w8_i |corner_i|, the scale of the trilinear rounding */
+  int ghost;
 } sample;
 
 /* local coordinates (clamped to [0,1]^3) of the point o + t d in the voxel g */
@@ -589,15 +633,15 @@ static void sample_weights(const double* o, const double* d, double t_in, double
 
 /* march one pixel (Eq. 2-4); returns the number of samples processed, fills s[] if non-null.
  * bnd (nullable) receives the FP32 sensitivity bound of rgb, depth and T
- * (see fp32_dx); cmax is the largest colour channel of the view. */
+ * (see chord_shifts and sample_shift); cmax is the largest colour channel of the view. */
 static int64_t march(const double* o, const double* d, double t_near, const cand* items, int64_t cnt,
                      const float* geom, int segment,
                      const float* dens, const double* colors, double t_stop, sample* s, double* rgb,
                      double* depth, double* T_out, int* near_stop, double* wmax, int64_t* warg, int64_t gid,
-                     double cmax, double* bnd) {
+                     double cmax, double* bnd, int ghosts, int64_t* n_entries) {
   double T = 1.0;
-  int64_t k = 0;
-  double A = 0.0, X = 0.0, tmax = 0.0;
+  int64_t k = 0, ks = 0; /* samples processed; entries written to s (samples and, with ghosts, near misses) */
+  double A = 0.0, X = 0.0, tmax = 0.0, cpix = 0.0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
   *depth = 0.0;
   *near_stop = 0;
@@ -607,14 +651,26 @@ static int64_t march(const double* o, const double* d, double t_near, const cand
     const float* d8 = dens + 8 * (int64_t)id;
     double t_in, t_out, din, dout;
     if (!slab64x(o, d, t_near, g, &t_in, &t_out, &din, &dout)) {
-      /* a near miss that FP32 could count as a hit */
-      if (bnd && t_out > 0.0 && t_in - t_out <= ORA_FP32_U * 4.0 * (t_out + 1.0) / (dout > 0.0 ? dout : 1.0)) {
+      /* a near miss that FP32 could count as a hit (chord_shifts' resolution) */
+      double gl, gq, res;
+      if ((bnd || (s && ghosts)) && t_out > 0.0) chord_shifts(o, d, t_near, g, t_in, t_out, &gl, &gq, &res);
+      if ((bnd || (s && ghosts)) && t_out > 0.0 && t_in - t_out < res) {
         double dm = 0.0;
         for (int i = 0; i < 8; ++i) dm = d8[i] > dm ? d8[i] : dm;
-        double dx = dm * ORA_FP32_U * 4.0 * (t_out + 1.0) / (dout > 0.0 ? dout : 1.0);
-        A += T * dx;
-        X += dx;
-        if (t_out > tmax) tmax = t_out;
+        if (bnd) {
+          const double* cg = colors + 3 * (int64_t)id;
+          A += T * dm * (res - (t_in - t_out));
+          X += dm * (res - (t_in - t_out));
+          if (t_out > tmax) tmax = t_out;
+          for (int ch = 0; ch < 3; ++ch) cpix = cg[ch] > cpix ? cg[ch] : cpix;
+        }
+        if (s && ghosts) {
+          sample* q = &s[ks++];
+          memset(q, 0, sizeof(sample));
+          q->id = id; q->T_before = T; q->t_mid = 0.5 * (t_in + t_out);
+          q->dl = res - (t_in - t_out); /* the longest chord an FP32 test could find */
+          q->dp = gq; q->dx = dm * q->dl; q->dmax = dm; q->h = (double)g[3]; q->ghost = 1;
+        }
       }
       continue;
     }
@@ -639,23 +695,35 @@ static int64_t march(const double* o, const double* d, double t_near, const cand
     rgb[2] += w * c[2];
     *depth += w * tm;
     if (s) {
-      s[k].id = id; s[k].l = l; s[k].t_mid = tm; s[k].sigma_raw = sr; s[k].alpha = alpha; s[k].T_before = T;
-      for (int i = 0; i < 8; ++i) s[k].w8[i] = w8[i];
+      sample* q = &s[ks++];
+      q->id = id; q->l = l; q->t_mid = tm; q->sigma_raw = sr; q->alpha = alpha; q->T_before = T;
+      for (int i = 0; i < 8; ++i) q->w8[i] = w8[i];
+      double dm = 0.0;
+      sample_shift(o, d, t_near, g, d8, sigma, l, t_in, t_out, &q->dl, &q->dp, &q->dx);
+      for (int i = 0; i < 8; ++i) dm = fabs((double)d8[i]) > dm ? fabs((double)d8[i]) : dm;
+      double da = 0.0;
+      for (int i = 0; i < 8; ++i) da += w8[i] * fabs((double)d8[i]);
+      q->dmax = dm; q->dabs = da; q->h = (double)g[3]; q->ghost = 0;
     }
+    double sdx = 0.0;
     if (bnd) {
-      double dx = fp32_dx(g, d8, sigma, l, t_in, t_out, din, dout);
-      A += T * dx;
-      X += dx;
+      double sdl, sdp;
+      sample_shift(o, d, t_near, g, d8, sigma, l, t_in, t_out, &sdl, &sdp, &sdx);
+      X += sdx;
       if (t_out > tmax) tmax = t_out;
+      for (int ch = 0; ch < 3; ++ch) cpix = c[ch] > cpix ? c[ch] : cpix;
     }
     T = T * exp(-sigma * l);
+    /* d rgb / d x_k = T_k c_k - sum_{j>k} w_j c_j: at most 2 max(c) T_k, T_k the transmittance after the sample */
+    A += T * sdx;
     ++k;
     if (fabs(log(T / t_stop)) <= 1e-4 + X) *near_stop = 1;
     if (T < t_stop) break;
   }
   *T_out = T;
+  if (n_entries) *n_entries = ks;
   if (bnd) {
-    bnd[0] = 2.0 * cmax * A;
+    bnd[0] = 2.0 * (cpix < cmax ? cpix : cmax) * A;
     bnd[1] = 2.0 * tmax * A;
     bnd[2] = T * X;
   }
@@ -687,7 +755,7 @@ static void view_colors(int64_t n, const float* geom, const float* sh, int degre
  *   brute != 0: every non-culled voxel is a candidate of every pixel.
  *   bound[3*P] (nullable): per pixel, how far an FP32 evaluation of the same
  *   pixel may legitimately differ in rgb (max channel), depth and T, from the
- *   sensitivity of each sample to FP32 geometry rounding (fp32_dx); near_stop
+ *   sensitivity of each sample to FP32 geometry rounding (sample_shift); near_stop
  *   marks pixels where such a perturbation can change the stop decision.
  */
 int ora_render(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
@@ -726,7 +794,7 @@ int ora_render(int64_t n, const float* geom, const float* dens, const float* sh,
         double Tp;
         int64_t k = march(cd.o, d, tn, L.items + L.start[p], L.start[p + 1] - L.start[p], geom, segment, dens, colors,
                           t_stop, NULL, rgb + 3 * gp, depth + gp, &Tp, &ns, twm ? twm + (int64_t)tid * n : NULL,
-                          twa ? twa + (int64_t)tid * n : NULL, gp, cmax, bound ? bound + 3 * gp : NULL);
+                          twa ? twa + (int64_t)tid * n : NULL, gp, cmax, bound ? bound + 3 * gp : NULL, 0, NULL);
         T[gp] = Tp;
         if (n_hit) n_hit[gp] = (int32_t)k;
         if (near_stop) near_stop[gp] = (uint8_t)ns;
@@ -804,7 +872,7 @@ int ora_render_backward(int64_t n, const float* geom, const float* dens, const f
           int ns;
           double tn = cam_ray(&cd, x, y, d);
           int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp, &dp,
-                            &Tf, &ns, NULL, NULL, gp, 0.0, NULL);
+                            &Tf, &ns, NULL, NULL, gp, 0.0, NULL, 0, NULL);
           const double* gC = dL_drgb + 3 * gp;
           double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
           double gT = dL_dT ? dL_dT[gp] : 0.0;
@@ -864,7 +932,7 @@ int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float
   int ns;
   double tn = cam_ray(&cd, x, y, d);
   int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp, &dp, &Tf,
-                    &ns, NULL, NULL, 0, 0.0, NULL);
+                    &ns, NULL, NULL, 0, 0.0, NULL, 0, NULL);
   int64_t m = K < max_out ? K : max_out;
   for (int64_t k = 0; k < m; ++k) {
     ids[k] = s[k].id;
@@ -876,6 +944,543 @@ int ora_trace_pixel(int64_t n, const float* geom, const float* dens, const float
   free(s);
   free_lists(&L);
   free(colors);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP32 error bounds and kink margins for the parity tests             */
+/* ------------------------------------------------------------------ */
+/*
+ * None of these functions changes a result of the method: they compute how far
+ * an FP32 evaluation of the same quantities may legitimately land from the FP64
+ * values above, and where a finite difference would straddle a kink.  The error
+ * model (first order, each term bounded in magnitude):
+ *   - geometry: the chord and midpoint shifts of chord_shifts (dl, dp), the
+ *     optical-depth shift they cause (dx), and near misses ("ghosts") that an
+ *     FP32 chord test may count;
+ *   - arithmetic, with u = 2^-24: the trilinear density within 8u sum_i w_i |corner_i|,
+ *     each product and sum within u, exp(-x) within (2 + 1.2 x) units of 2u
+ *     (the fast exponential), 1 - exp(-x) within 8u relative below x = 1/8 and
+ *     within the error of exp(-x) above it;
+ *   - transmittance: the relative errors of its factors add up along the ray;
+ *     recomputed from an FP32 optical depth, as a backward pass does, it gains
+ *     2u K tau + 2u (2 + 1.2 tau) for K samples of total optical depth tau;
+ *   - sums in arbitrary order (atomics): n terms within (n + 1) u sum |term|
+ *     (the classical bound for recursive summation in any order).
+ * Weights take a factor 2 on their first-order bound for the neglected
+ * higher-order terms.
+ */
+/* one sample's optical depth x = sigma l, the FP32 bound of its error dxk
+ * (geometry, trilinear rounding, product) and the bound of the error of alpha */
+static void entry_terms(const sample* q, double* x, double* dxk, double* ea) {
+  *x = q->l * (q->sigma_raw > 0.0 ? q->sigma_raw : 0.0);
+  *dxk = q->dx + q->l * 8.0 * ORA_U32 * q->dabs + 2.0 * ORA_U32 * *x;
+  double e = exp(-*x);
+  *ea = e * *dxk + 8.0 * ORA_U32 * q->alpha + (*x >= 0.125 ? 2.0 * ORA_U32 * (2.0 + 1.2 * *x) * e : 0.0);
+}
+
+/* FP32 bound of each entry's weight w = T_before alpha (ew), front to back, for
+ * a transmittance formed as the product of the factors exp(-x) (a forward
+ * pass); returns the relative error bound of the final transmittance */
+static double weight_bounds(const sample* s, int64_t ne, double* ew) {
+  double ET = 0.0;
+  for (int64_t k = 0; k < ne; ++k) {
+    const sample* q = &s[k];
+    if (q->ghost) {
+      ew[k] = 2.0 * q->T_before * q->dmax * q->dl; /* the largest weight an FP32 hit could carry */
+      ET += q->dx;
+      continue;
+    }
+    double x, dxk, ea;
+    entry_terms(q, &x, &dxk, &ea);
+    double w = q->T_before * q->alpha;
+    ew[k] = 2.0 * (w * ET + q->T_before * ea + ORA_U32 * w);
+    ET += dxk + 2.0 * ORA_U32 * (3.0 + 1.2 * x);
+  }
+  return ET;
+}
+
+void ora_free(void* p) { free(p); }
+
+typedef struct {
+  int64_t v, pix;
+  double w, e;
+} set_entry;
+
+typedef struct {
+  set_entry* a;
+  int64_t n, cap;
+} set_buf;
+
+static void set_push(set_buf* b, int64_t v, int64_t pix, double w, double e) {
+  if (b->n == b->cap) {
+    b->cap = b->cap ? 2 * b->cap : 1024;
+    b->a = (set_entry*)realloc(b->a, sizeof(set_entry) * (size_t)b->cap);
+  }
+  b->a[b->n].v = v; b->a[b->n].pix = pix; b->a[b->n].w = w; b->a[b->n].e = e;
+  b->n++;
+}
+
+/* top-2 of (w, pixel) with the w_max tie rule (equal weights: the smaller pixel id is the larger) */
+typedef struct {
+  double w1, e1, w2, e2;
+  int64_t a1;
+} top2;
+
+static void top2_add(top2* t, double w, int64_t pix, double e) {
+  if (t->a1 < 0 || w > t->w1 || (w == t->w1 && pix < t->a1)) {
+    if (t->a1 >= 0 && (t->w2 < 0.0 || t->w1 > t->w2)) { t->w2 = t->w1; t->e2 = t->e1; }
+    t->w1 = w; t->e1 = e; t->a1 = pix;
+  } else if (t->w2 < 0.0 || w > t->w2) {
+    t->w2 = w; t->e2 = e;
+  }
+}
+
+/*
+ * w_max (Eq. 5) with its FP32 ambiguity, for the argmax parity test.  Per voxel:
+ *   w1, a1, e1: the FP64 maximum weight, its pixel (global id, -1 if never hit)
+ *     and the FP32 bound of that weight;
+ *   w2, e2: the largest weight on any other ray (-1 if none) and its bound;
+ *   n_certain: samples whose chord exceeds twice its FP32 shift, on rays whose
+ *     stop decision FP32 rounding cannot change (an FP32 pass must hit these).
+ * The near-max set: every (voxel, pixel) entry, sample or near miss, whose weight
+ * can reach the maximum's lower bound (w + e >= w1 - e1), in arrays allocated
+ * here (release with ora_free).  Two passes over all views' pixels.
+ */
+int ora_wmax_sets(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
+                  const ora_cam* cams, double t_stop, int segment, double* w1, int64_t* a1, double* e1, double* w2,
+                  double* e2, int32_t* n_certain, int64_t* n_set, int64_t** set_v, int64_t** set_pix,
+                  double** set_w, double** set_e) {
+  int nt = ora_threads();
+  int64_t nn = n > 0 ? n : 1;
+  top2* tt = (top2*)malloc(sizeof(top2) * (size_t)nt * (size_t)nn);
+  int32_t* tc = (int32_t*)calloc((size_t)nt * (size_t)nn, sizeof(int32_t));
+  for (int64_t q = 0; q < (int64_t)nt * nn; ++q) { tt[q].w1 = 0.0; tt[q].e1 = 0.0; tt[q].w2 = -1.0; tt[q].e2 = 0.0; tt[q].a1 = -1; }
+  set_buf* bufs = (set_buf*)calloc((size_t)nt, sizeof(set_buf));
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t pix_off = 0;
+    for (int v = 0; v < n_views; ++v) {
+      cam64 cd;
+      cam_derive(&cams[v], &cd);
+      view_colors(n, geom, sh, sh_degree, &cd, colors, NULL, NULL);
+      pixlists L;
+      build_lists(n, geom, &cams[v], &cd, 0, NULL, &L);
+#pragma omp parallel
+      {
+        int tid = ora_tid();
+        int64_t cap = 64;
+        sample* s = (sample*)malloc(sizeof(sample) * (size_t)cap);
+        double* ew = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+        for (int y = 0; y < cd.H; ++y) {
+          for (int x = 0; x < cd.W; ++x) {
+            int64_t p = (int64_t)y * cd.W + x;
+            int64_t gp = pix_off + p;
+            int64_t cnt = L.start[p + 1] - L.start[p];
+            if (cnt > cap) {
+              cap = cnt;
+              s = (sample*)realloc(s, sizeof(sample) * (size_t)cap);
+              ew = (double*)realloc(ew, sizeof(double) * (size_t)cap);
+            }
+            double d[3], rgbp[3], dep, Tf;
+            int ns;
+            int64_t ne = 0;
+            double tn = cam_ray(&cd, x, y, d);
+            march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp, &dep, &Tf,
+                  &ns, NULL, NULL, gp, 0.0, NULL, 1, &ne);
+            weight_bounds(s, ne, ew);
+            for (int64_t k = 0; k < ne; ++k) {
+              const sample* q = &s[k];
+              double w = q->T_before * q->alpha;
+              if (pass == 0) {
+                if (q->ghost) continue;
+                top2_add(&tt[(int64_t)tid * nn + q->id], w, gp, ew[k]);
+                if (!ns && q->l > 2.0 * q->dl) tc[(int64_t)tid * nn + q->id] += 1;
+              } else if (w + ew[k] >= w1[q->id] - e1[q->id]) {
+                set_push(&bufs[tid], (int64_t)q->id, gp, q->ghost ? 0.0 : w, ew[k]);
+              }
+            }
+          }
+        }
+        free(s);
+        free(ew);
+      }
+      free_lists(&L);
+      pix_off += (int64_t)cd.W * cd.H;
+    }
+    if (pass == 0) {
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < n; ++i) {
+        top2 m = tt[i];
+        int32_t c = tc[i];
+        for (int t = 1; t < nt; ++t) {
+          const top2* o = &tt[(int64_t)t * nn + i];
+          c += tc[(int64_t)t * nn + i];
+          if (o->a1 < 0) continue;
+          /* merge: the better first wins, the rest compete for second */
+          top2 r = m;
+          top2_add(&r, o->w1, o->a1, o->e1);
+          if (o->w2 >= 0.0 && (r.w2 < 0.0 || o->w2 > r.w2)) { r.w2 = o->w2; r.e2 = o->e2; }
+          m = r;
+        }
+        w1[i] = m.w1; a1[i] = m.a1; e1[i] = m.e1; w2[i] = m.w2; e2[i] = m.e2;
+        n_certain[i] = c;
+      }
+    }
+  }
+  int64_t tot = 0;
+  for (int t = 0; t < nt; ++t) tot += bufs[t].n;
+  int64_t m = tot > 0 ? tot : 1;
+  *set_v = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+  *set_pix = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+  *set_w = (double*)malloc(sizeof(double) * (size_t)m);
+  *set_e = (double*)malloc(sizeof(double) * (size_t)m);
+  int64_t o = 0;
+  for (int t = 0; t < nt; ++t) {
+    for (int64_t k = 0; k < bufs[t].n; ++k, ++o) {
+      (*set_v)[o] = bufs[t].a[k].v; (*set_pix)[o] = bufs[t].a[k].pix;
+      (*set_w)[o] = bufs[t].a[k].w; (*set_e)[o] = bufs[t].a[k].e;
+    }
+    free(bufs[t].a);
+  }
+  *n_set = tot;
+  free(bufs);
+  free(tt);
+  free(tc);
+  free(colors);
+  return 0;
+}
+
+/* per voxel and channel: 0.5 + sum_j |SH_j Y_j|, the scale of the FP32 rounding of the colour sum (cabs);
+ * per voxel the FP32 shift of the viewing direction, from the rounded centre and camera origin (the
+ * centre within u (|c - o| + 2 |o|), as in chord_shifts) and the normalisation (3u), times 4, a bound of
+ * the gradient of each real SH function of degree <= 3 on the sphere (dY); per voxel and channel the
+ * colour shift that direction shift can cause, sum_j |SH_j| dY (cgeo) */
+static void color_scales(int64_t n, const float* geom, const float* sh, int degree, const cam64* cd, double* cabs,
+                         double* dY, double* cgeo) {
+  int nb = sh_count(degree);
+  double on = sqrt(cd->o[0] * cd->o[0] + cd->o[1] * cd->o[1] + cd->o[2] * cd->o[2]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double d[3] = {(double)geom[4 * i] - cd->o[0], (double)geom[4 * i + 1] - cd->o[1], (double)geom[4 * i + 2] - cd->o[2]};
+    double nr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (nr > 0) { d[0] /= nr; d[1] /= nr; d[2] /= nr; } else { d[0] = 0; d[1] = 0; d[2] = 1; }
+    double Y[16];
+    ora_sh_basis(d, Y);
+    double ddir = nr > 0 ? ORA_U32 * (nr + 2.0 * on) * 1.7320508075688772 / nr + 3.0 * ORA_U32 : 1.0;
+    dY[i] = 4.0 * ddir;
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.5, b = 0.0;
+      for (int j = 0; j < nb; ++j) {
+        a += fabs((double)sh[48 * i + j * 3 + c] * Y[j]);
+        b += fabs((double)sh[48 * i + j * 3 + c]);
+      }
+      cabs[3 * i + c] = a;
+      cgeo[3 * i + c] = b * dY[i];
+    }
+  }
+}
+
+/*
+ * Absolute FP32 error floors of the gradients of ora_render_backward (same
+ * arguments), accumulated into e_density[8n] and e_sh[48n] (caller zeroes):
+ * the per-sample errors of the reverse pass (chord, midpoint, transmittance
+ * recomputed from the stored optical depth, the suffix sums, the colour),
+ * near misses an FP32 pass may count, density and colour clamps within their
+ * rounding, and the order of the atomic sums, (n + 1) u sum |term| for n terms.
+ * A gradient g of the FP64 value ref is within |g - ref| <= e of any FP32
+ * evaluation that follows the model above.  arith_only != 0 leaves out every
+ * geometric term (exact chords, midpoints and hit decisions): what remains is
+ * the rounding of the arithmetic and of the summation order.
+ */
+int ora_backward_bounds(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree,
+                        int n_views, const ora_cam* cams, double t_stop, const int* crop, const double* dL_drgb,
+                        const double* dL_ddepth, const double* dL_dT, double* e_density, double* e_sh, int segment,
+                        int arith_only) {
+  const double u = ORA_U32;
+  int64_t nn = n > 0 ? n : 1;
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* raw = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* dirs = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* cabs = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* cgeo = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* dY = (double*)malloc(sizeof(double) * (size_t)nn);
+  double* dcol = (double*)malloc(sizeof(double) * 3 * (size_t)nn);     /* colour gradient (FP64) */
+  double* dcol_abs = (double*)malloc(sizeof(double) * 3 * (size_t)nn); /* sum of |terms| */
+  double* dcol_err = (double*)malloc(sizeof(double) * 3 * (size_t)nn); /* per-term error bounds */
+  double* dd_abs = (double*)calloc(8 * (size_t)nn, sizeof(double));
+  int64_t* terms = (int64_t*)calloc((size_t)nn, sizeof(int64_t));
+  int64_t* cterms = (int64_t*)malloc(sizeof(int64_t) * (size_t)nn);
+  int64_t* views_seen = (int64_t*)calloc((size_t)nn, sizeof(int64_t));
+  int64_t pix_off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    cam64 cd;
+    cam_derive(&cams[v], &cd);
+    view_colors(n, geom, sh, sh_degree, &cd, colors, raw, dirs);
+    color_scales(n, geom, sh, sh_degree, &cd, cabs, dY, cgeo);
+    if (arith_only)
+      for (int64_t i = 0; i < n; ++i) { dY[i] = 0.0; cgeo[3 * i] = cgeo[3 * i + 1] = cgeo[3 * i + 2] = 0.0; }
+    for (int64_t i = 0; i < 3 * n; ++i) { dcol[i] = 0.0; dcol_abs[i] = 0.0; dcol_err[i] = 0.0; }
+    for (int64_t i = 0; i < n; ++i) cterms[i] = 0;
+    const int* cr = crop ? crop + 4 * v : NULL;
+    int x0 = cr ? cr[0] : 0, y0 = cr ? cr[1] : 0, x1 = cr ? cr[2] : cd.W, y1 = cr ? cr[3] : cd.H;
+    pixlists L;
+    build_lists(n, geom, &cams[v], &cd, 0, cr, &L);
+#pragma omp parallel
+    {
+      int64_t cap = 64;
+      sample* s = (sample*)malloc(sizeof(sample) * (size_t)cap);
+      double* ew = (double*)malloc(sizeof(double) * (size_t)cap);
+      double* ETb = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+      for (int y = y0; y < y1; ++y) {
+        for (int x = x0; x < x1; ++x) {
+          int64_t p = (int64_t)y * cd.W + x;
+          int64_t gp = pix_off + p;
+          int64_t cnt = L.start[p + 1] - L.start[p];
+          if (cnt > cap) {
+            cap = cnt;
+            s = (sample*)realloc(s, sizeof(sample) * (size_t)cap);
+            ew = (double*)realloc(ew, sizeof(double) * (size_t)cap);
+            ETb = (double*)realloc(ETb, sizeof(double) * (size_t)cap);
+          }
+          double d[3], rgbp[3], dep, Tf;
+          int ns;
+          int64_t ne = 0;
+          double tn = cam_ray(&cd, x, y, d);
+          int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp,
+                            &dep, &Tf, &ns, NULL, NULL, gp, 0.0, NULL, !arith_only, &ne);
+          if (arith_only)
+            for (int64_t k = 0; k < ne; ++k) { s[k].dl = 0.0; s[k].dp = 0.0; s[k].dx = 0.0; }
+          /* the final transmittance comes from the forward pass (a product of factors); every other one is
+           * recomputed from the stored optical depth: its relative error is the optical-depth error of the
+           * samples before it (Xg) plus the rounding of the FP32 optical-depth sums, forward and back
+           * (EBsum), plus that of the exponential */
+          double ETf = weight_bounds(s, ne, ew);
+          double tau = 0.0, tsum = 0.0, Xg = 0.0;
+          for (int64_t k = 0; k < ne; ++k) {
+            if (s[k].ghost) continue;
+            tau += s[k].l * (s[k].sigma_raw > 0.0 ? s[k].sigma_raw : 0.0);
+            tsum += tau;
+          }
+          double EBsum = 2.0 * u * tsum;
+          tau = 0.0;
+          for (int64_t k = 0; k < ne; ++k) {
+            const sample* q = &s[k];
+            if (q->ghost) {
+              ETb[k] = Xg; /* unused for ghosts */
+              Xg += q->dx;
+              continue;
+            }
+            double x, dxk, ea;
+            entry_terms(q, &x, &dxk, &ea);
+            double ETbefore = Xg + EBsum + 2.0 * u * (2.0 + 1.2 * tau);
+            double w = q->T_before * q->alpha;
+            ew[k] = 2.0 * (w * ETbefore + q->T_before * ea + u * w);
+            Xg += dxk;
+            tau += x;
+            ETb[k] = Xg + EBsum + 2.0 * u * (2.0 + 1.2 * tau); /* of the transmittance after the sample */
+          }
+          const double* gC = dL_drgb + 3 * gp;
+          double gD = dL_ddepth ? dL_ddepth[gp] : 0.0;
+          double gT = dL_dT ? dL_dT[gp] : 0.0;
+          double S = 0.0, S_abs = 0.0, S_err = 0.0;
+          for (int64_t k = ne - 1; k >= 0; --k) {
+            const sample* q = &s[k];
+            const double* c = colors + 3 * (int64_t)q->id;
+            const double* ca = cabs + 3 * (int64_t)q->id;
+            double a_k = gC[0] * c[0] + gC[1] * c[1] + gC[2] * c[2] + q->t_mid * gD;
+            double a_abs = fabs(gC[0] * c[0]) + fabs(gC[1] * c[1]) + fabs(gC[2] * c[2]) + fabs(q->t_mid * gD);
+            const double* cgq = cgeo + 3 * (int64_t)q->id;
+            double da = fabs(gC[0]) * (64.0 * u * ca[0] + cgq[0]) + fabs(gC[1]) * (64.0 * u * ca[1] + cgq[1]) +
+                        fabs(gC[2]) * (64.0 * u * ca[2] + cgq[2]) + fabs(gD) * q->dp;
+            double* ed = e_density + 8 * (int64_t)q->id;
+            double* dda = dd_abs + 8 * (int64_t)q->id;
+            double Tb = q->T_before;
+            if (q->ghost) {
+              /* an FP32 pass may count this near miss: a chord of at most dl */
+              double gterm = q->dl * (Tb * a_abs + S_abs + Tf * fabs(gT));
+#pragma omp atomic
+              terms[q->id] += 1;
+              for (int i = 0; i < 8; ++i) {
+#pragma omp atomic
+                ed[i] += gterm;
+              }
+              for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+                dcol_err[3 * (int64_t)q->id + ch] += ew[k] * fabs(gC[ch]);
+              }
+#pragma omp atomic
+              cterms[q->id] += 1;
+              S_err += a_abs * ew[k];
+              continue;
+            }
+            double w = Tb * q->alpha;
+            double T_k = Tb * (1.0 - q->alpha);
+            double ETa = ETb[k];
+            double inner = T_k * a_k - S - Tf * gT;
+            double ds_k = q->l * inner;
+            double M = T_k * a_abs + S_abs + Tf * fabs(gT);
+            double d_inner = T_k * (fabs(a_k) * ETa + da) + S_err + fabs(gT) * Tf * ETf +
+                             u * ((double)K + 8.0) * M;
+            double d_ds = q->dl * fabs(inner) + q->l * d_inner + u * fabs(ds_k);
+            double dsig = 1.7320508075688772 * q->dmax / q->h * q->dp + 8.0 * u * q->dabs;
+            int clamp_amb = fabs(q->sigma_raw) <= dsig;
+            double dw8 = 3.0 * q->dp / (2.0 * q->h) + 4.0 * u;
+#pragma omp atomic
+            terms[q->id] += 1;
+            for (int i = 0; i < 8; ++i) {
+              double t_i = ds_k * q->w8[i];
+              double e_i;
+              if (q->sigma_raw > 0.0) {
+                e_i = d_ds * q->w8[i] + fabs(ds_k) * dw8 + (clamp_amb ? fabs(t_i) : 0.0);
+#pragma omp atomic
+                dda[i] += fabs(t_i);
+              } else {
+                e_i = clamp_amb ? (fabs(ds_k) + d_ds) * q->w8[i] : 0.0;
+              }
+#pragma omp atomic
+              ed[i] += e_i;
+            }
+            for (int ch = 0; ch < 3; ++ch) {
+              double tc = w * gC[ch];
+#pragma omp atomic
+              dcol[3 * (int64_t)q->id + ch] += tc;
+#pragma omp atomic
+              dcol_abs[3 * (int64_t)q->id + ch] += fabs(tc);
+#pragma omp atomic
+              dcol_err[3 * (int64_t)q->id + ch] += ew[k] * fabs(gC[ch]) + u * fabs(tc);
+            }
+#pragma omp atomic
+            cterms[q->id] += 1;
+            S += w * a_k;
+            S_abs += w * a_abs;
+            S_err += fabs(a_k) * ew[k] + w * da;
+          }
+        }
+      }
+      free(s);
+      free(ew);
+      free(ETb);
+    }
+    free_lists(&L);
+    int nb = sh_count(sh_degree);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      if (cterms[i] == 0) continue;
+      views_seen[i] += 1;
+      double Y[16];
+      ora_sh_basis(dirs + 3 * i, Y);
+      for (int ch = 0; ch < 3; ++ch) {
+        double g = dcol[3 * i + ch];
+        double eg = dcol_err[3 * i + ch] + u * (double)(cterms[i] + 1) * dcol_abs[3 * i + ch];
+        int amb = fabs(raw[3 * i + ch]) <= 64.0 * u * cabs[3 * i + ch] + cgeo[3 * i + ch];
+        if (!(raw[3 * i + ch] > 0.0) && !amb) continue;
+        for (int j = 0; j < nb; ++j) {
+          double e = fabs(Y[j]) * (eg + 32.0 * u * fabs(g)) + (32.0 * u + dY[i]) * fabs(g) +
+                     (amb ? fabs(Y[j] * g) : 0.0);
+          e_sh[48 * i + 3 * j + ch] += e;
+        }
+      }
+    }
+    pix_off += (int64_t)cd.W * cd.H;
+  }
+  /* the order of the atomic sums: over the samples of each voxel, then over views for the SH rows */
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 8; ++k) e_density[8 * i + k] += u * (double)(terms[i] + 1) * dd_abs[8 * i + k];
+    if (views_seen[i] > 1)
+      for (int k = 0; k < 48; ++k) e_sh[48 * i + k] *= 1.0 + u * (double)(views_seen[i] + 1);
+  }
+  free(colors); free(raw); free(dirs); free(cabs); free(cgeo); free(dY); free(dcol); free(dcol_abs); free(dcol_err);
+  free(dd_abs); free(terms); free(cterms); free(views_seen);
+  return 0;
+}
+
+/*
+ * Kink margins for finite differences of the render.  Per voxel:
+ *   m_sigma: the smallest |sigma_raw| over its samples (a corner step of size
+ *     h moves sigma_raw by at most h, so |sigma_raw| > h keeps the clamp
+ *     max(0, .) on one side);
+ *   m_stop: the smallest corner step that can move the stop decision of a ray
+ *     through it, min over its samples k_v of min_{k >= k_v} |tau_k - ln(1/t_stop)| / l_v
+ *     (the optical depth after sample k shifts by at most l_v h);
+ *   m_color[3]: the smallest |pre-clamp colour| over the views that sample it
+ *     (an SH step of size h moves it by at most |Y_j| h <= 1.2 h).
+ * +inf where the voxel is never sampled.
+ */
+int ora_fd_margins(int64_t n, const float* geom, const float* dens, const float* sh, int sh_degree, int n_views,
+                   const ora_cam* cams, double t_stop, int segment, double* m_sigma, double* m_stop, double* m_color) {
+  int64_t nn = n > 0 ? n : 1;
+  double* colors = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  double* raw = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+  uint8_t* hit = (uint8_t*)malloc((size_t)nn);
+  for (int64_t i = 0; i < n; ++i) { m_sigma[i] = INFINITY; m_stop[i] = INFINITY; }
+  for (int64_t i = 0; i < 3 * n; ++i) m_color[i] = INFINITY;
+  double Ls = log(1.0 / t_stop);
+  for (int v = 0; v < n_views; ++v) {
+    cam64 cd;
+    cam_derive(&cams[v], &cd);
+    view_colors(n, geom, sh, sh_degree, &cd, colors, raw, NULL);
+    memset(hit, 0, (size_t)nn);
+    pixlists L;
+    build_lists(n, geom, &cams[v], &cd, 0, NULL, &L);
+#pragma omp parallel
+    {
+      int64_t cap = 64;
+      sample* s = (sample*)malloc(sizeof(sample) * (size_t)cap);
+      double* tail = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+      for (int y = 0; y < cd.H; ++y) {
+        for (int x = 0; x < cd.W; ++x) {
+          int64_t p = (int64_t)y * cd.W + x;
+          int64_t cnt = L.start[p + 1] - L.start[p];
+          if (cnt > cap) {
+            cap = cnt;
+            s = (sample*)realloc(s, sizeof(sample) * (size_t)cap);
+            tail = (double*)realloc(tail, sizeof(double) * (size_t)cap);
+          }
+          double d[3], rgbp[3], dep, Tf;
+          int ns;
+          double tn = cam_ray(&cd, x, y, d);
+          int64_t K = march(cd.o, d, tn, L.items + L.start[p], cnt, geom, segment, dens, colors, t_stop, s, rgbp,
+                            &dep, &Tf, &ns, NULL, NULL, 0, 0.0, NULL, 0, NULL);
+          /* tail[k] = min_{j >= k} |tau_j - ln(1/t_stop)|, tau_j the optical depth after sample j */
+          double tau = 0.0;
+          for (int64_t k = 0; k < K; ++k) {
+            tau += s[k].l * (s[k].sigma_raw > 0.0 ? s[k].sigma_raw : 0.0);
+            tail[k] = fabs(tau - Ls);
+          }
+          for (int64_t k = K - 2; k >= 0; --k) tail[k] = tail[k] < tail[k + 1] ? tail[k] : tail[k + 1];
+          for (int64_t k = 0; k < K; ++k) {
+            uint32_t id = s[k].id;
+            double ms = fabs(s[k].sigma_raw);
+            double mt = s[k].l > 0.0 ? tail[k] / s[k].l : INFINITY;
+            hit[id] = 1;
+#pragma omp critical(ora_fd_margins_min)
+            {
+              if (ms < m_sigma[id]) m_sigma[id] = ms;
+              if (mt < m_stop[id]) m_stop[id] = mt;
+            }
+          }
+        }
+      }
+      free(s);
+      free(tail);
+    }
+    free_lists(&L);
+    for (int64_t i = 0; i < n; ++i) {
+      if (!hit[i]) continue;
+      for (int c = 0; c < 3; ++c) {
+        double r = fabs(raw[3 * i + c]);
+        if (r < m_color[3 * i + c]) m_color[3 * i + c] = r;
+      }
+    }
+  }
+  free(colors);
+  free(raw);
+  free(hit);
   return 0;
 }
 

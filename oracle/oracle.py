@@ -77,6 +77,10 @@ def lib():
             _lib.ora_lf_gamma.argtypes = [D, D, D, D]
             _lib.ora_lf_gamma.restype = D
             _lib.ora_sh_basis.argtypes = [P, P]
+            _lib.ora_wmax_sets.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P, P, P, P, P, P, P, P, P]
+            _lib.ora_backward_bounds.argtypes = [I64, P, P, P, I32, I32, P, D, P, P, P, P, P, P, I32, I32]
+            _lib.ora_fd_margins.argtypes = [I64, P, P, P, I32, I32, P, D, I32, P, P, P]
+            _lib.ora_free.argtypes = [P]
             _lib.ora_num_threads.restype = C.c_int
         return _lib
 
@@ -203,6 +207,90 @@ def trace_pixel(scene: dict, cam: dict, x: int, y: int, t_stop: float = 1e-4, sh
                           _p(ids), _p(w), _p(Ta), _p(ll), C.byref(k), int(segment))
     m = min(k.value, max_out)
     return {"ids": ids[:m], "w": w[:m], "T_after": Ta[:m], "l": ll[:m], "n": k.value}
+
+
+def wmax_sets(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, segment: bool = False) -> dict:
+    """w_max (Eq. 5) with the FP32 ambiguity of its argmax, for the parity test.
+
+    Per voxel: w1 / a1 / e1 (FP64 maximum weight, its global pixel id or -1, the
+    FP32 error bound of that weight), w2 / e2 (largest weight on any other ray,
+    -1 if none), n_certain (samples that any FP32 pass must hit).  The near-max
+    set: every (voxel, pixel) sample or near miss whose weight can reach
+    w1 - e1, as arrays sorted by (voxel, pixel): set_v, set_pix, set_w, set_e.
+    """
+    geom = _c(scene["geom"], np.float32)
+    dens = _c(scene["density"], np.float32)
+    sh = _c(scene["sh"], np.float32)
+    n = geom.shape[0]
+    w1 = np.zeros(n, np.float64)
+    a1 = np.full(n, -1, np.int64)
+    e1 = np.zeros(n, np.float64)
+    w2 = np.zeros(n, np.float64)
+    e2 = np.zeros(n, np.float64)
+    nc = np.zeros(n, np.int32)
+    ns = C.c_int64(0)
+    pv, pp, pw, pe = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    lib().ora_wmax_sets(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, int(segment),
+                        _p(w1), _p(a1), _p(e1), _p(w2), _p(e2), _p(nc), C.byref(ns), C.byref(pv), C.byref(pp),
+                        C.byref(pw), C.byref(pe))
+    m = ns.value
+
+    def take(ptr, ctype, dtype):
+        out = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=(max(m, 1),))[:m].astype(dtype, copy=True)
+        lib().ora_free(ptr)
+        return out
+
+    sv = take(pv, C.c_int64, np.int64)
+    sp = take(pp, C.c_int64, np.int64)
+    sw = take(pw, C.c_double, np.float64)
+    se = take(pe, C.c_double, np.float64)
+    order = np.lexsort((sp, sv))
+    return {"w1": w1, "a1": a1, "e1": e1, "w2": w2, "e2": e2, "n_certain": nc, "set_v": sv[order],
+            "set_pix": sp[order], "set_w": sw[order], "set_e": se[order]}
+
+
+def backward_bounds(scene: dict, cams: list, dL_drgb, dL_ddepth=None, dL_dT=None, t_stop: float = 1e-4,
+                    sh_degree: int = 3, crop=None, segment: bool = False) -> dict:
+    """Absolute FP32 error floors of render_backward's gradients (same arguments):
+    e_density [n, 8] and e_sh [n, 48]; an FP32 evaluation g of a gradient whose
+    FP64 value is ref stays within |g - ref| <= e under the error model of
+    lv_oracle.c (geometry rounding, arithmetic, atomic summation order).
+    a_density / a_sh: the same bound without the geometric terms (exact chords
+    and hit decisions): arithmetic and summation order only."""
+    geom = _c(scene["geom"], np.float32)
+    dens = _c(scene["density"], np.float32)
+    sh = _c(scene["sh"], np.float32)
+    n = geom.shape[0]
+    gC = _c(dL_drgb, np.float64)
+    gD = None if dL_ddepth is None else _c(dL_ddepth, np.float64)
+    gT = None if dL_dT is None else _c(dL_dT, np.float64)
+    ed = np.zeros((n, 8), np.float64)
+    es = np.zeros((n, 48), np.float64)
+    cr = None if crop is None else _c(np.asarray(crop).reshape(-1, 4), np.int32)
+    ad = np.zeros((n, 8), np.float64)
+    as_ = np.zeros((n, 48), np.float64)
+    for e_d, e_s, arith in ((ed, es, 0), (ad, as_, 1)):
+        lib().ora_backward_bounds(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, _p(cr),
+                                  _p(gC), _p(gD), _p(gT), _p(e_d), _p(e_s), int(segment), arith)
+    return {"e_density": ed, "e_sh": es, "a_density": ad, "a_sh": as_}
+
+
+def fd_margins(scene: dict, cams: list, t_stop: float = 1e-4, sh_degree: int = 3, segment: bool = False) -> dict:
+    """Kink margins of the render for finite differences: per voxel the smallest
+    |sigma_raw| of its samples (m_sigma), the smallest corner step that can move a
+    stop decision of a ray through it (m_stop), and per channel the smallest
+    |pre-clamp colour| over the views that sample it (m_color [n, 3]); inf if
+    never sampled."""
+    geom = _c(scene["geom"], np.float32)
+    dens = _c(scene["density"], np.float32)
+    sh = _c(scene["sh"], np.float32)
+    n = geom.shape[0]
+    ms = np.zeros(n, np.float64)
+    mt = np.zeros(n, np.float64)
+    mc = np.zeros((n, 3), np.float64)
+    lib().ora_fd_margins(n, _p(geom), _p(dens), _p(sh), sh_degree, len(cams), _cams(cams), t_stop, int(segment),
+                         _p(ms), _p(mt), _p(mc))
+    return {"m_sigma": ms, "m_stop": mt, "m_color": mc}
 
 
 def prune(w_max, seen, z, m, s, n_bins=16, q_ppm=50000, ema_alpha=0.1, m_low=0.3, m_high=0.7, cap_ppm=10000,

@@ -40,6 +40,8 @@ class RasterContext:
         self.n_pix = sum(w * h for w, h in self.sizes)
         self.pair_capacity = int(pair_capacity) if pair_capacity is not None else max(1024, 4 * self.n * self.n_views)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        # forward passes launched so far: the workspace, T and n_contrib belong to the latest one
+        self.generation = 0
         self._alloc_outputs()
         self._alloc_workspace()
 
@@ -83,6 +85,7 @@ class RasterContext:
         torch.cuda.Event recorded once before) is recorded when the voxel statistics are final."""
         L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(stats, stats_event),
                                self.workspace, self.pair_capacity, self.status)
+        self.generation += 1
         return self.rgb, self.depth, self.T
 
     def backward(self, vox: L.lv_voxels, dL_drgb, dL_ddepth=None, dL_dT=None, d_density=None, d_sh=None,
@@ -153,17 +156,24 @@ class Scene:
 class _RasterFn(torch.autograd.Function):
     """rgb, depth, T = raster(density, sh); the backward re-walks the sorted
     lists back to front (no per-sample storage), using only the context's
-    workspace, T and n_contrib."""
+    workspace, T and n_contrib.  Those belong to the context's latest forward
+    pass, so a backward whose context has run another forward since raises
+    instead of returning the other pass's gradients."""
 
     @staticmethod
     def forward(ctx, density, sh, scene, rctx):
         vox = L.make_voxels(scene.geom, density, sh, scene.level, scene.sh_degree)
         rgb, depth, T = rctx.forward(vox, stats=True)
         ctx.scene, ctx.rctx, ctx.vox_keep = scene, rctx, (density, sh)
+        ctx.generation = rctx.generation
         return rgb.clone(), depth.clone(), T.clone()
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_T):
+        if ctx.rctx.generation != ctx.generation:
+            raise RuntimeError("rasterize: the RasterContext ran another forward pass after this one; its "
+                               "workspace no longer holds this pass's sorted lists (use one context per "
+                               "pending backward)")
         density, sh = ctx.vox_keep
         vox = L.make_voxels(ctx.scene.geom, density, sh, ctx.scene.level, ctx.scene.sh_degree)
         g_rgb = torch.zeros_like(ctx.rctx.rgb) if g_rgb is None else g_rgb.float().contiguous()

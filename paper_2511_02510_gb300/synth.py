@@ -195,13 +195,19 @@ def scene_360(seed: int = 0, band: float = 2.0, halo: float = 1.0, opaque: bool 
     return make_scene(spec)
 
 
-def scene_tt(seed: int = 0, band: float = 1.5, halo: float = 0.85, opaque: bool = True) -> dict:
-    """Tanks-and-Temples-shaped scene: ~6M voxels, levels 6-13, wider foreground extent."""
+def scene_tt(seed: int = 0, band: float = 1.5, halo: float = 0.85, opaque: bool = True, clean: bool = False) -> dict:
+    """Tanks-and-Temples-shaped scene: ~6M voxels, levels 6-13, wider foreground extent.
+
+    clean=True leaves the N(0, 0.1) noise out of the corner densities (the same
+    random draws are still taken, so the SH coefficients are those of the noisy
+    scene): the noise-free scene whose render is the PSNR target."""
     spec = SceneSpec(seed=seed, root_min=(-16, -16, -16), root_edge=32.0, l_min=6, l_max_fg=13, l_max_bg=8,
                      band=band, halo=halo, fg_center=(0.0, 0.0, 0.0), fg_scale=3.0, fg_box_half=0.5,
                      shell=(12.0, 16.0))
     if opaque:
         spec.density_peak = _opaque_peak(spec)
+    if clean:
+        spec.density_noise = 0.0
     return make_scene(spec)
 
 

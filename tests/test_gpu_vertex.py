@@ -13,7 +13,8 @@ from oracle import vertex as VX
 from paper_2511_02510_gb300 import litevoxel as L
 from paper_2511_02510_gb300 import synth
 from paper_2511_02510_gb300.raster import RasterContext
-from test_gpu_render import GRAD_TOL, _grad_err, _loss_grads, cam_near, compare_images
+from parity import check_grads
+from test_gpu_render import _loss_grads, cam_near, compare_images
 
 pytestmark = pytest.mark.gpu
 
@@ -95,8 +96,16 @@ def test_vertex_render_forward_backward(ora):
     gv = torch.zeros(nv, device="cuda")
     L.lv_vertex_scatter_add(vidx, d_corner, gv)
     torch.cuda.synchronize()
-    bw = ora.render_backward(ref_sc, cams, gC.astype(np.float64), gD.astype(np.float64), gT.astype(np.float64))
-    assert _grad_err(np_(gv), VX.scatter_add(ref_vidx, bw["d_density"], nv)) < GRAD_TOL
+    f64 = lambda x: x.astype(np.float64)
+    bw = ora.render_backward(ref_sc, cams, f64(gC), f64(gD), f64(gT))
+    eb = ora.backward_bounds(ref_sc, cams, f64(gC), f64(gD), f64(gT))
+    # a vertex sums the corners that share it: their floors add, plus the order of that sum
+    cnt = np.bincount(ref_vidx.ravel(), minlength=nv).astype(np.float64)
+    ref_v = VX.scatter_add(ref_vidx, bw["d_density"], nv)
+    abs_v = VX.scatter_add(ref_vidx, np.abs(bw["d_density"]), nv)
+    e_v = VX.scatter_add(ref_vidx, eb["e_density"], nv) + 2.0 ** -24 * (cnt + 1) * abs_v
+    a_v = VX.scatter_add(ref_vidx, eb["a_density"], nv) + 2.0 ** -24 * (cnt + 1) * abs_v
+    print("vertex gradients:", check_grads("d_vertex", np_(gv), ref_v, e_v, a_v))
     # FP64 re-render reads the vertices too
     px = torch.arange(ctx.n_pix, dtype=torch.int64, device="cuda")
     rgb = torch.zeros((ctx.n_pix, 3), dtype=torch.float64, device="cuda")
