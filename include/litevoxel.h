@@ -135,6 +135,12 @@ typedef struct {
   void* stats_event;                 /* cudaEvent_t (nullable): recorded on the stream as soon as z_min,
                                         delta_min and seen are final (after binning, before sorting and
                                         compositing), so another stream can start on them early */
+  void* composite_event;             /* cudaEvent_t (nullable): recorded on the stream right before the
+                                        front-to-back composite is launched (the last launch of the
+                                        call), so that an event recorded after the call times the
+                                        composite alone; inside a stream capture it is recorded as an
+                                        external event node (cudaEventRecordExternal), a timing mark
+                                        of every replay rather than a dependency */
 } lv_fwd_out;
 
 /* ------------------------------------------------------------------ */
@@ -433,6 +439,30 @@ lv_status lv_subdivide_select(const lv_voxels* in, const float* delta, const flo
                               size_t ws_bytes, int32_t* d_status, void* stream);
 lv_status lv_subdivide_apply(const lv_voxels* in, const lv_subdiv_params* p, const lv_aux_array* aux, int n_aux,
                              const lv_voxels* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* The topology change of the step (Sec. IV-D, Eq. 13-16 with the optimizer
+ * refresh, and the removal of the voxels pruned by Sec. IV-C) written in
+ * place: only the rows that change are read or written, instead of every
+ * survivor being copied to new arrays.  Call after lv_subdivide_select on
+ * the same workspace and stream, with out_capacity = capacity and the same
+ * prune mask.  vox: the n = vox->n current rows, in arrays that hold
+ * `capacity` rows (geom, level, density, sh); the result holds n' = n - h +
+ * 7k rows (h pruned, k split; d_n_new of the select step), the same rows as
+ * lv_subdivide_apply writes, placed as follows:
+ *   - a split parent's row becomes its child 0;
+ *   - children 1..7 of the r-th split parent (id order) take slots 7r .. 7r+6
+ *     of [the pruned rows in increasing index, then rows n, n + 1, ...];
+ *   - if 7k < h, the occupied rows at index >= n' then move, in increasing
+ *     index, into the rows below n' still empty, in increasing index;
+ *   - every other row keeps its index and its bytes.
+ * Child values and auxiliary fills are those of lv_subdivide_apply.  aux[a].out
+ * is updated in place (aux[a].in must be NULL or equal to out); every array
+ * must hold `capacity` rows.  If capacity < n' the select step has set
+ * LV_ERR_CAPACITY and nothing is written.  Host errors: LV_ERR_INVALID_ARG
+ * (null or inconsistent arrays, capacity < n), LV_ERR_WORKSPACE. */
+lv_status lv_subdivide_apply_inplace(const lv_voxels* vox, int64_t capacity, const lv_subdiv_params* p,
+                                     const lv_aux_array* aux, int n_aux, void* workspace, size_t ws_bytes,
+                                     void* stream);
 
 /* ------------------------------------------------------------------ */
 /* LF-weighted photometric loss (Sec. IV-B, Eq. 7-10, 18)               */

@@ -4,6 +4,8 @@
 // top-k) is an exact radix select on order-preserving 32-bit keys, so the
 // integer outputs do not depend on thread scheduling; all FP32 decisions use
 // a fixed operation order (__fmul_rn / __fadd_rn / __fdiv_rn).
+#include <algorithm>
+
 #include "lv_prims.cuh"
 
 namespace lv {
@@ -821,6 +823,173 @@ __global__ void k_sd_write(int64_t n, int64_t max_children, const uint32_t* __re
   }
 }
 
+// ------------------------------------------------------------------ in-place topology change
+// The rows a subdivision changes, rewritten where they are (Sec. IV-D): a
+// split parent's row becomes its child 0; children 1..7 of the r-th parent (id
+// order) take slots 7r .. 7r + 6 of [the pruned rows in index order, then rows
+// n, n + 1, ...]; with fewer children than pruned rows, the occupied rows at
+// index >= n' then move into the empty rows below n', both in index order.
+// Rows the step does not change are neither read nor written.
+
+// the pruned rows (neither survivor nor split parent) in index order: the
+// number of pruned rows before i is i - (survivors before i) - (parents before i)
+__global__ void k_ip_holes(int64_t n, const uint32_t* __restrict__ surv, const uint32_t* __restrict__ sel,
+                           const unsigned long long* __restrict__ surv_pos, const uint32_t* __restrict__ sel_rank,
+                           uint32_t* __restrict__ holes) {
+  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i < n && !surv[i] && !sel[i]) holes[i - (int64_t)surv_pos[i] - (int64_t)sel_rank[i]] = (uint32_t)i;
+}
+
+// row of child c of the parent of rank r (at row `parent`)
+__device__ __forceinline__ int64_t ip_child_row(int64_t r, int c, int64_t parent, const uint32_t* __restrict__ holes,
+                                                int64_t h, int64_t n) {
+  if (c == 0) return parent;
+  const int64_t s = 7 * r + (c - 1);
+  return s < h ? (int64_t)holes[s] : n + (s - h);
+}
+
+// A warp writes the 8 children of 4 consecutive parents (children t0 .. t0 + 31,
+// one lane each for the geometry, level and interpolated corners).  Every lane
+// reads its parent's geometry, level and corners, and the warp stages its
+// parents' SH rows in shared memory, before any child is written: child 0
+// overwrites the parent's own row.  The SH and auxiliary rows then go out in
+// 16-byte words spread over the lanes.
+template <typename DT, typename ST>
+__global__ void __launch_bounds__(TPB) k_ip_children(int64_t n, const uint32_t* __restrict__ list,
+                                                     const uint32_t* __restrict__ holes,
+                                                     const unsigned long long* totals, const SubState* st,
+                                                     float4* geom, uint8_t* level, DT* dens, ST* sh,
+                                                     const __grid_constant__ AuxSet aux) {
+  constexpr int WPR = (int)(48 * sizeof(ST) / 16);  // 16-byte words per SH row
+  __shared__ uint4 s_sh[TPB / 32][4 * WPR];
+  __shared__ int64_t s_dst[TPB / 32][32];
+  if (!st->fits) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t t0 = ((blockIdx.x * (int64_t)TPB + threadIdx.x) >> 5) * 32;
+  const int64_t k = (int64_t)totals[1];
+  const int64_t nchild = 8 * k;
+  if (t0 >= nchild) return;  // warp-uniform
+  const int64_t h = n - (int64_t)totals[0] - k;
+  const int nrows = (int)min((int64_t)32, nchild - t0);
+  const bool act = lane < nrows;
+  const int64_t t = t0 + lane;
+  const int64_t r = t >> 3;
+  const int c = (int)(t & 7);
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint8_t lvl = 0;
+  float d[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = 0.f;
+  int64_t dst = 0;
+  if (act) {
+    const int64_t parent = list[r];
+    dst = ip_child_row(r, c, parent, holes, h, n);
+    g = geom[parent];
+    lvl = level[parent];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = to_f32(dens[8 * parent + q]);
+  }
+  s_dst[warp][lane] = dst;
+  const int np = (nrows + 7) >> 3;
+  const uint4* ssrc = (const uint4*)sh;
+  for (int w = lane; w < np * WPR; w += 32) {
+    const int pr = w / WPR, kk = w - pr * WPR;
+    s_sh[warp][w] = ssrc[(size_t)list[(t0 >> 3) + pr] * WPR + kk];
+  }
+  __syncwarp();
+  if (act) {
+    const float hc = __fmul_rn(g.w, 0.5f);
+    geom[dst] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
+                            __fadd_rn(g.z, (c & 4) ? hc : -hc), hc);
+    level[dst] = (uint8_t)(lvl + 1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
+      const float qy = (float)(((c >> 1) & 1) + ((j >> 1) & 1)) * 0.5f;
+      const float qz = (float)(((c >> 2) & 1) + ((j >> 2) & 1)) * 0.5f;
+      const float x0 = lerp_rn(d[0], d[1], qx), x1 = lerp_rn(d[2], d[3], qx);
+      const float x2 = lerp_rn(d[4], d[5], qx), x3 = lerp_rn(d[6], d[7], qx);
+      const float y0 = lerp_rn(x0, x1, qy), y1 = lerp_rn(x2, x3, qy);
+      dens[8 * dst + j] = from_f32<DT>(lerp_rn(y0, y1, qz));
+    }
+  }
+  uint4* sdst = (uint4*)sh;
+  for (int w = lane; w < nrows * WPR; w += 32) {
+    const int rr = w / WPR, kk = w - rr * WPR;
+    sdst[(size_t)s_dst[warp][rr] * WPR + kk] = s_sh[warp][(rr >> 3) * WPR + kk];
+  }
+  // auxiliary rows: the child fill pattern
+  for (int a = 0; a < aux.n; ++a) {
+    const lv_aux_array& A = aux.a[a];
+    const size_t row = (size_t)A.width * A.elem_bytes;
+    if (A.elem_bytes == 4 && (row & 15) == 0 && ((uintptr_t)A.out & 15) == 0) {
+      const uint4 f = make_uint4(A.fill, A.fill, A.fill, A.fill);
+      const int wpr = (int)(row / 16);
+      for (int w = lane; w < nrows * wpr; w += 32) {
+        const int rr = w / wpr, kk = w - rr * wpr;
+        ((uint4*)A.out)[(size_t)s_dst[warp][rr] * wpr + kk] = f;
+      }
+    } else if (act) {
+      aux_fill(A, dst);
+    }
+  }
+}
+
+// first index in [lo, hi) of the sorted holes[] whose value is >= v
+__device__ __forceinline__ int64_t ip_lower_bound(const uint32_t* __restrict__ holes, int64_t lo, int64_t hi,
+                                                  int64_t v) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)holes[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// one array row moved by a warp, in 4-byte words where aligned
+__device__ __forceinline__ void ip_move_row(char* base, size_t row, int64_t src, int64_t dst, int lane) {
+  char* s = base + row * (size_t)src;
+  char* d = base + row * (size_t)dst;
+  if ((row & 3) == 0 && ((uintptr_t)base & 3) == 0) {
+    for (size_t w = lane; w < row / 4; w += 32) ((uint32_t*)d)[w] = ((const uint32_t*)s)[w];
+  } else {
+    for (size_t w = lane; w < row; w += 32) d[w] = s[w];
+  }
+}
+
+// Shrinking step (7k < h): the occupied rows at index >= n' move into the empty
+// rows below n'.  The empty rows are the unfilled holes holes[7k .. h); the
+// first m of them lie below n'.  An occupied row i in [n', n) has rank
+// (i - n') - (unfilled holes in [n', i)) and moves to holes[7k + rank].  One
+// warp per row, grid-stride over [n', n); it runs after the children are
+// written, since a moved row may be one of them.
+template <typename DT, typename ST>
+__global__ void __launch_bounds__(TPB) k_ip_tail(int64_t n, const uint32_t* __restrict__ holes,
+                                                 const unsigned long long* totals, const SubState* st, float4* geom,
+                                                 uint8_t* level, DT* dens, ST* sh, const __grid_constant__ AuxSet aux) {
+  if (!st->fits) return;
+  const int64_t k = (int64_t)totals[1];
+  const int64_t h = n - (int64_t)totals[0] - k;
+  if (7 * k >= h) return;
+  const int64_t nn = n - h + 7 * k;
+  const int64_t f0 = 7 * k;
+  const int64_t fm = ip_lower_bound(holes, f0, h, nn);  // f0 + m
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)TPB + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * TPB) >> 5;
+  for (int64_t i = nn + gw; i < n; i += nw) {
+    const int64_t pos = ip_lower_bound(holes, fm, h, i);
+    if (pos < h && (int64_t)holes[pos] == i) continue;  // an empty row: nothing moves
+    const int64_t dst = holes[f0 + (i - nn) - (pos - fm)];
+    ip_move_row((char*)geom, 16, i, dst, lane);
+    ip_move_row((char*)level, 1, i, dst, lane);
+    ip_move_row((char*)dens, 8 * sizeof(DT), i, dst, lane);
+    ip_move_row((char*)sh, 48 * sizeof(ST), i, dst, lane);
+    for (int a = 0; a < aux.n; ++a)
+      ip_move_row((char*)aux.a[a].out, (size_t)aux.a[a].width * aux.a[a].elem_bytes, i, dst, lane);
+  }
+}
+
 }  // namespace
 
 }  // namespace lv
@@ -1061,6 +1230,45 @@ extern "C" lv_status lv_subdivide_priority(const lv_voxels* in, const float* del
                           d_status, stream);
   if (e != LV_OK) return e;
   return lv_subdivide_apply(in, p, aux, n_aux, out, workspace, ws_bytes, stream);
+}
+
+extern "C" lv_status lv_subdivide_apply_inplace(const lv_voxels* vox, int64_t capacity, const lv_subdiv_params* p,
+                                                const lv_aux_array* aux, int n_aux, void* workspace, size_t ws_bytes,
+                                                void* stream) {
+  lv_status e = check_sub(vox, p, n_aux, aux, nullptr);
+  if (e != LV_OK) return e;
+  const int64_t n = vox->n;
+  if (capacity < n) { set_error("capacity %lld < voxel count %lld", (long long)capacity, (long long)n); return LV_ERR_INVALID_ARG; }
+  for (int a = 0; a < n_aux; ++a)
+    if (aux[a].in && aux[a].in != aux[a].out) { set_error("aux array %d: in place, in must be NULL or equal out", a); return LV_ERR_INVALID_ARG; }
+  if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
+  SubWs w = carve_sub(workspace, n);
+  if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
+  if (n == 0) return LV_OK;
+  AuxSet as;
+  as.n = n_aux;
+  for (int a = 0; a < n_aux; ++a) as.a[a] = aux[a];
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* holes = w.zkey;  // free once the selection is done
+  k_ip_holes<<<blocks_for(n), TPB, 0, s>>>(n, w.surv, w.sel, w.surv_pos, w.sel_rank, holes);
+  const int64_t max_children = 8 * (int64_t)(((unsigned long long)p->top_ppm * (unsigned long long)n) / 1000000ull);
+  const unsigned grid = (unsigned)((max_children + TPB - 1) / TPB);  // one warp per 32 children
+  const unsigned tail_grid = (unsigned)std::min<int64_t>((n + TPB / 32 - 1) / (TPB / 32), 1216);
+#define LV_IP(DT, ST)                                                                                                  \
+  do {                                                                                                                \
+    if (grid > 0)                                                                                                     \
+      k_ip_children<DT, ST><<<grid, TPB, 0, s>>>(n, w.sel_list, holes, w.totals, w.st, (float4*)vox->geom,            \
+                                                 (uint8_t*)vox->level, (DT*)vox->density, (ST*)vox->sh, as);          \
+    k_ip_tail<DT, ST><<<tail_grid, TPB, 0, s>>>(n, holes, w.totals, w.st, (float4*)vox->geom, (uint8_t*)vox->level,   \
+                                                (DT*)vox->density, (ST*)vox->sh, as);                                 \
+  } while (0)
+  if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_IP(float, float);
+  else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_IP(__half, float);
+  else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_IP(float, __nv_bfloat16);
+  else LV_IP(__half, __nv_bfloat16);
+#undef LV_IP
+  count_launch(grid > 0 ? 3 : 2);
+  return cuda_check(cudaGetLastError(), "lv_subdivide_apply_inplace");
 }
 
 extern "C" size_t lv_compact_workspace_size(int64_t n) {

@@ -1407,6 +1407,15 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   const uint32_t* sk = sorted_pair_tiles(w, tiles);
   const uint32_t* sv = sorted_pair_slots(w, tiles);
   k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
+  if (out->composite_event) {
+    // a timing mark: inside a stream capture it becomes an event record node of the graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags((cudaEvent_t)out->composite_event, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord((cudaEvent_t)out->composite_event, s);
+  }
   launch_fwd(opts, tiles, s, vs, w, sv, out);
   count_launch(2);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");

@@ -52,7 +52,7 @@ class lv_raster_opts(C.Structure):
 class lv_fwd_out(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p),
-                ("n_samples", C.c_void_p), ("stats_event", C.c_void_p)]
+                ("n_samples", C.c_void_p), ("stats_event", C.c_void_p), ("composite_event", C.c_void_p)]
 
 
 class lv_prune_params(C.Structure):
@@ -131,6 +131,8 @@ SIGNATURES = {
                                       _P, _P]),
     "lv_subdivide_apply": (C.c_int, [_PV, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array), C.c_int, _PV, _P,
                                      _SZ, _P]),
+    "lv_subdivide_apply_inplace": (C.c_int, [_PV, C.c_int64, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array),
+                                             C.c_int, _P, _SZ, _P]),
     "lv_compact_workspace_size": (_SZ, [_I64]),
     "lv_compact": (C.c_int, [_PV, _P, C.POINTER(lv_aux_array), C.c_int, _PV, _P, _P, _SZ, _P, _P]),
     "lv_check_status": (C.c_int, [_P, _P]),
@@ -236,14 +238,16 @@ def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=F
 
 
 def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None,
-                 n_samples=None, stats_event=None) -> lv_fwd_out:
+                 n_samples=None, stats_event=None, composite_event=None) -> lv_fwd_out:
     """stats_event: a torch.cuda.Event (recorded once before, so that it exists) that the forward
-    records as soon as the per-voxel statistics are final."""
+    records as soon as the per-voxel statistics are final; composite_event: one it records right
+    before launching the composite."""
     o = lv_fwd_out()
     o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
     o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)
     o.n_samples = _ptr(n_samples)
     o.stats_event = stats_event.cuda_event if stats_event is not None else None
+    o.composite_event = composite_event.cuda_event if composite_event is not None else None
     return o
 
 
@@ -410,6 +414,15 @@ def lv_subdivide_apply(vin, params, aux, vout, workspace):
     _check(load().lv_subdivide_apply(C.byref(vin), C.byref(params), aux_arr, len(aux), C.byref(vout),
                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
            "lv_subdivide_apply")
+
+
+def lv_subdivide_apply_inplace(vox, capacity, params, aux, workspace):
+    """The topology change written where the rows are (after lv_subdivide_select with
+    out_capacity = capacity); vox's arrays hold `capacity` rows, aux arrays are updated in place."""
+    aux_arr = (lv_aux_array * max(1, len(aux)))(*aux)
+    _check(load().lv_subdivide_apply_inplace(C.byref(vox), int(capacity), C.byref(params), aux_arr, len(aux),
+                                             _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+           "lv_subdivide_apply_inplace")
 
 
 def lv_compact_workspace_size(n) -> int:

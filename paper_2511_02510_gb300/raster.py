@@ -73,17 +73,19 @@ class RasterContext:
         """Zero w_max and reset z_min / delta_min / seen before a new accumulation window."""
         L.lv_reset_stats(self.wmax_packed, self.z_min, self.delta_min, self.seen)
 
-    def fwd_struct(self, stats=True, stats_event=None):
+    def fwd_struct(self, stats=True, stats_event=None, composite_event=None):
         return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
                               self.wmax_packed if stats else None, self.z_min if stats else None,
                               self.delta_min if stats else None, self.seen if stats else None,
-                              self.n_samples if stats else None, stats_event)
+                              self.n_samples if stats else None, stats_event, composite_event)
 
     # ---------------------------------------------------------------- calls
-    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None):
+    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None, composite_event=None):
         """Launch the forward pass (asynchronous).  Returns (rgb, depth, T).  stats_event (a
-        torch.cuda.Event recorded once before) is recorded when the voxel statistics are final."""
-        L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(stats, stats_event),
+        torch.cuda.Event recorded once before) is recorded when the voxel statistics are final;
+        composite_event right before the composite is launched."""
+        L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts,
+                               self.fwd_struct(stats, stats_event, composite_event),
                                self.workspace, self.pair_capacity, self.status)
         self.generation += 1
         return self.rgb, self.depth, self.T
