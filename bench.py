@@ -113,9 +113,19 @@ class Workload:
         self.torch, self.L = torch, L
         dd = density_dtype or torch.float32
         sd = sh_dtype or torch.float32
-        self.scene = Scene.from_numpy(scene_np, "cuda", dd, sd)
-        n = self.scene.n
+        n = int(scene_np["geom"].shape[0])
         self.n = n
+        # the voxel arrays hold room for the step's growth: the topology change is written in place
+        # (top 5 % split: at most n + 7 * 0.05 n rows)
+        cap = n + 7 * (n * 50000 // 1000000) + 16
+        self.cap = cap
+        src = Scene.from_numpy(scene_np, "cuda", dd, sd)
+        big = [torch.empty((cap,) + tuple(t.shape[1:]), dtype=t.dtype, device="cuda")
+               for t in (src.geom, src.level, src.density, src.sh)]
+        for b, t in zip(big, (src.geom, src.level, src.density, src.sh)):
+            b[:n].copy_(t)
+        del src
+        self.scene = Scene(big[0][:n], big[1][:n], big[2][:n], big[3][:n])
         self.cams = [cam]
         self.tile, self.persistent, self.tune_ms = 16, False, None
         if schedule is not None:
@@ -154,46 +164,72 @@ class Workload:
         self.pp.n_bins, self.pp.q_ppm, self.pp.ema_alpha, self.pp.m_low, self.pp.m_high = 16, 50000, 0.1, 0.3, 0.7
         self.pp.cap_ppm, self.pp.lo_ppm, self.pp.hi_ppm = 10000, 50000, 950000
         self.pr_ws = torch.empty(L.lv_prune_workspace_size(n, self.pp), dtype=torch.uint8, device=dev)
-        self.ema = torch.ones(n, dtype=torch.float32, device=dev)
-        self.state = torch.ones(n, dtype=torch.uint8, device=dev)
+        # EMA state of a voxel set that training has been pruning: every voxel just above m_low, so
+        # one out-vote moves it out and the cap (guard iii) decides how many go, from the first step
+        self.ema_cap = torch.full((cap,), 0.32, dtype=torch.float32, device=dev)
+        self.state_cap = torch.ones(cap, dtype=torch.uint8, device=dev)
+        self.ema, self.state = self.ema_cap[:n], self.state_cap[:n]
+        self.ema0, self.state0 = self.ema.clone(), self.state.clone()
         self.pmask = torch.empty(n, dtype=torch.uint8, device=dev)
         self.n_pruned = torch.zeros(1, dtype=torch.int64, device=dev)
-        # subdivision (kappa 1, beta 0.2, top 5 %) into separate output buffers
+        # subdivision (kappa 1, beta 0.2, top 5 %), written in place
         self.sp = L.lv_subdiv_params()
         self.sp.kappa, self.sp.beta, self.sp.top_ppm, self.sp.l_max = 1.0, 0.2, 50000, 16
         self.sp.budget, self.sp.lo_ppm, self.sp.hi_ppm = 1 << 40, 50000, 950000
         self.sd_ws = torch.empty(L.lv_subdivide_workspace_size(n, self.sp), dtype=torch.uint8, device=dev)
-        cap = n + 7 * (n * 50000 // 1000000) + 16
-        self.cap = cap
-        self.o_geom = torch.empty((cap, 4), dtype=torch.float32, device=dev)
-        self.o_level = torch.empty(cap, dtype=torch.uint8, device=dev)
-        self.o_dens = torch.empty((cap, 8), dtype=dd, device=dev)
-        self.o_sh = torch.empty((cap, 48), dtype=sd, device=dev)
-        self.vout = L.make_voxels(self.o_geom, self.o_dens, self.o_sh, self.o_level)
-        self.vout.n = cap
         self.selected = torch.empty(n, dtype=torch.uint8, device=dev)
         self.n_new = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        # optimizer moments and EMA state carried through the topology change
-        self.aux_in = [torch.zeros((n, 8), dtype=torch.float32, device=dev),
-                       torch.zeros((n, 8), dtype=torch.float32, device=dev),
-                       torch.zeros((n, 48), dtype=torch.float32, device=dev),
-                       torch.zeros((n, 48), dtype=torch.float32, device=dev), self.ema, self.state]
+        # optimizer moments and EMA state carried through the topology change, updated in place
+        self.aux_arrays = [torch.zeros((cap, 8), dtype=torch.float32, device=dev),
+                           torch.zeros((cap, 8), dtype=torch.float32, device=dev),
+                           torch.zeros((cap, 48), dtype=torch.float32, device=dev),
+                           torch.zeros((cap, 48), dtype=torch.float32, device=dev), self.ema_cap, self.state_cap]
         fills = [0, 0, 0, 0, int(np.array([1.0], np.float32).view(np.uint32)[0]), 1]
-        self.aux_out, self.aux = [], []
-        for t, f in zip(self.aux_in, fills):
-            o = torch.empty((cap,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+        self.aux = []
+        for t, f in zip(self.aux_arrays, fills):
             a = L.lv_aux_array()
-            a.in_, a.out = t.data_ptr(), o.data_ptr()
+            a.in_, a.out = t.data_ptr(), t.data_ptr()
             a.width = 1 if t.dim() == 1 else t.shape[1]
             a.elem_bytes = t.element_size()
             a.fill = f
-            self.aux_out.append(o)
             self.aux.append(a)
+        self.restore_idx = None
 
     # stage boundaries, for the per-kernel breakdown
     STAGES = ["reset", "forward", "loss", "backward", "sh_backward", "unpack", "prune", "subdivide_select",
-              "subdivide_apply"]
+              "subdivide_inplace", "restore"]
+
+    def _state_arrays(self):
+        """The per-voxel arrays the next step reads that an in-place topology change overwrites below
+        row n: geometry, level, corners and SH (the optimizer moments are only written by the step,
+        and the EMA and hysteresis state is restored whole)."""
+        sc = self.scene
+        return [sc.geom, sc.level, sc.density, sc.sh]
+
+    def prepare_restore(self, pristine):
+        """After one step taken from the state `pristine` (clones of _state_arrays() from before it):
+        note the rows that step's topology change overwrote (split parents and filled holes: the rows
+        selected or pruned), keep their original contents, and put the whole state back.  Every step
+        takes the same decisions from the same state, so restore() returns the state after each step."""
+        torch = self.torch
+        idx = torch.nonzero((self.selected != 0) | (self.pmask != 0)).flatten()
+        self.restore_idx = idx
+        self.restore_saved = [p.index_select(0, idx) for p in pristine]
+        for arr, p in zip(self._state_arrays(), pristine):
+            arr.copy_(p)
+        self.ema.copy_(self.ema0)
+        self.state.copy_(self.state0)
+
+    def restore(self):
+        """Put back the rows the step's in-place topology change overwrote and the pruning state, so
+        the next step starts from the same scene (inside the timed region: it is extra work)."""
+        if self.restore_idx is None:
+            return
+        for arr, saved in zip(self._state_arrays(), self.restore_saved):
+            arr.index_copy_(0, self.restore_idx, saved)
+        self.ema.copy_(self.ema0)
+        self.state.copy_(self.state0)
 
     def step(self, ev=None):
         L, r = self.L, self.rctx
@@ -223,16 +259,19 @@ class Workload:
         L.lv_subdivide_select(self.vox, r.delta_min, r.z_min, self.w_max, r.seen, self.pmask, self.sp, self.cap,
                               self.selected, self.n_new, self.sd_ws, self.status)
         mark(8)
-        L.lv_subdivide_apply(self.vox, self.sp, self.aux, self.vout, self.sd_ws)
+        L.lv_subdivide_apply_inplace(self.vox, self.cap, self.sp, self.aux, self.sd_ws)
         mark(9)
+        self.restore()
+        mark(10)
 
-    def step_concurrent(self, apply_events=None):
+    def step_concurrent(self, ev=None):
         """The same work as step(), in three streams.  The LF weight map depends on the ground
         truth only, and pruning and the subdivision selection on the forward statistics only, so
         they run beside the forward and the backward respectively (side streams at high priority,
         joined by events): the depth bins of the pruning start as soon as the forward has binned
-        the voxels (its statistics event), the rest once w_max is out.  The subdivision write
-        runs last, alone."""
+        the voxels (its statistics event), the rest once w_max is out.  The in-place topology
+        change runs last, alone, then the restore.  ev: {"composite" | "backward" | "apply":
+        (start, end)} timing events (external, so that they time graph replays)."""
         torch, L, r = self.torch, self.L, self.rctx
         if not hasattr(self, "_side"):
             hi = torch.cuda.Stream.priority_range()[1]
@@ -249,7 +288,9 @@ class Workload:
             L.lv_lf_weights(self.gt, [W_IMG], [H_IMG], self.t_iter, self.lfp, self.lf_ws)
             e_w.record(sw)
         r.reset_stats()
-        r.forward(self.vox, stats=True, stats_event=e_stats)
+        r.forward(self.vox, stats=True, stats_event=e_stats, composite_event=ev["composite"][0] if ev else None)
+        if ev:
+            ev["composite"][1].record(main)
         e_fwd.record(main)
         sb.wait_event(e_stats)
         with torch.cuda.stream(sb):
@@ -264,15 +305,20 @@ class Workload:
             e_b.record(sb)
         main.wait_event(e_w)
         L.lv_lf_loss_from_weights(r.rgb, self.gt, [W_IMG], [H_IMG], self.loss, self.dL, self.lf_ws)
+        if ev:
+            ev["backward"][0].record(main)
         L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, self.bwd_opts, r.fwd_struct(False), r.workspace,
                                 r.pair_capacity, self.dL, None, None, self.d_dens, None, True, r.status)
+        if ev:
+            ev["backward"][1].record(main)
         L.lv_sh_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.workspace, r.pair_capacity, self.d_sh, False)
         main.wait_event(e_b)
-        if apply_events:
-            apply_events[0].record(main)
-        L.lv_subdivide_apply(self.vox, self.sp, self.aux, self.vout, self.sd_ws)
-        if apply_events:
-            apply_events[1].record(main)
+        if ev:
+            ev["apply"][0].record(main)
+        L.lv_subdivide_apply_inplace(self.vox, self.cap, self.sp, self.aux, self.sd_ws)
+        if ev:
+            ev["apply"][1].record(main)
+        self.restore()
 
     def e2e_step(self):
         """The same step through the public API with host buffers: the step's ground-truth
@@ -293,7 +339,7 @@ class Workload:
     def row_bytes(self):
         """Bytes of one voxel's state rows: geometry, level, corners, SH and the auxiliary arrays."""
         b = 16 + 1 + 8 * self.scene.density.element_size() + 48 * self.scene.sh.element_size()
-        return b + sum(t[0].numel() * t.element_size() for t in self.aux_in)
+        return b + sum(t[0].numel() * t.element_size() for t in self.aux_arrays)
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -406,73 +452,72 @@ def alu_peak_tflops(sm_mhz):
     return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
-def algorithmic_bytes(stage, n, pairs, slots, npix, n_new=0, split=0, row=0, parent_row=0):
-    """Bytes a stage must move at least once (inputs read, outputs written) for one step."""
-    if stage == "backward_composite":
-        # per pair: the slot index and the 64-byte record; per pixel: dL/drgb, T, n_contrib and the
-        # optical depth (24); d_density (32 n) and the colour gradients (16 per slot) accumulated
-        return pairs * (4 + 64) + npix * 24 + 32 * n + 16 * slots
-    if stage == "subdivide_apply":
-        # survivors' rows read and written, children's rows written, split parents' rows read once
-        survivors = n_new - 8 * split
-        return survivors * row * 2 + 8 * split * row + split * parent_row
-    return 0
+def stage_work(n, slots, pairs, npix, tiles, samples, split, pruned, row, parent_row):
+    """Algorithmic bytes and FP32 operations of every stage of one step (FP32 storage): what each
+    stage must read and write at least once.  Rasterizer stages a1-a7 as the scope table of the
+    method's hot path counts them (N voxels, N_v visible slots, P (tile, slot) pairs, Npx pixels,
+    S composited samples); then the LF loss (Eq. 7-10), w_max unpack, pruning (Eq. 11-12),
+    the subdivision selection (Eq. 13-16) and the in-place topology change."""
+    N, Nv, P, Npx, S, k, h = n, slots, pairs, npix, samples, split, pruned
+    st = {
+        "a1_preprocess": (N * 16 + Nv * (192 + 28), 0),
+        "a2_scan_emit": (Nv * 8 + P * 12, 0),
+        "a3_sort": (P * 24, 0),
+        "a4_tile_ranges": (P * 8 + tiles * 8, 0),
+        "a5_forward_composite": (P * (4 + 64) + Npx * 24 + P * 8, S * FLOPS_PER_SAMPLE["forward_composite"]),
+        "a6_backward_composite": (P * (4 + 64) + Npx * 40 + P * 11 * 8, S * FLOPS_PER_SAMPLE["backward_composite"]),
+        "a7_sh_backward": (Nv * (12 + 192 + 192), 0),
+        "lf_loss": (Npx * 36, 0),                               # gt and rgb read, dL/drgb written
+        "reset_and_unpack": (N * 17 + N * 20, 0),               # statistics reset; packed w_max -> w_max, argmax
+        "prune": (N * 20, 0),                                   # w_max, seen, z, m, s read; m, s, mask written
+        "subdivide_select": (N * 32, 0),                        # geometry, level, delta, z, u, seen, mask; selected
+        "subdivide_inplace": (k * parent_row + 8 * k * row + N + 4 * h, 0),
+    }
+    return {name: {"bytes": int(b), "flops": int(f)} for name, (b, f) in st.items()}
+
+
+def step_roofline(work, ms_step, hbm_gbs, fp32_tflops):
+    """Sum over stages of max(bytes / HBM peak, flops / FP32 peak), against the measured step time."""
+    total = 0.0
+    out = {}
+    for name, w in work.items():
+        t_mem = w["bytes"] / (hbm_gbs * 1e9) * 1e3
+        t_alu = w["flops"] / (fp32_tflops * 1e12) * 1e3
+        out[name] = {"bytes": w["bytes"], "flops": w["flops"], "bound_ms": max(t_mem, t_alu),
+                     "bound": "hbm" if t_mem >= t_alu else "alu"}
+        total += max(t_mem, t_alu)
+    return {"stages": out, "sum_bound_ms": total, "ms_per_step": ms_step, "frac": total / ms_step}
 
 
 # ---------------------------------------------------------------------------- CPU baseline (oracle)
-def _oracle_pixel_work(O, scene_np, cam, gt_np, crop_px):
-    """Oracle render + LF loss + backward restricted to a centred crop; returns seconds."""
-    x0, y0 = (W_IMG - crop_px) // 2, (H_IMG - crop_px) // 2
-    crop = [x0, y0, x0 + crop_px, y0 + crop_px]
-    t0 = time.perf_counter()
-    r = O.render(scene_np, [cam], crop=crop)
-    m = np.zeros((H_IMG, W_IMG), bool)
-    m[y0:y0 + crop_px, x0:x0 + crop_px] = True
-    rgb_c = r["rgb"].reshape(H_IMG, W_IMG, 3)[y0:y0 + crop_px, x0:x0 + crop_px].reshape(-1, 3)
-    gt_c = gt_np.reshape(H_IMG, W_IMG, 3)[y0:y0 + crop_px, x0:x0 + crop_px].reshape(-1, 3)
-    lf = O.lf_loss(rgb_c, gt_c.astype(np.float64), [(crop_px, crop_px)], gamma=0.3)
-    g = np.zeros((H_IMG * W_IMG, 3))
-    g[m.ravel()] = lf["dL_drgb"]
-    O.render_backward(scene_np, [cam], g, crop=crop)
-    return time.perf_counter() - t0, r
-
-
-def oracle_step_time(scene_np, cam, gt_np, crops=(32, 160)):
-    """Oracle time of one step, extrapolated from a bounded sample.
-
-    The per-pixel work (render, LF loss, backward) is timed on two centred
-    crops; a line through the two (fixed per-view cost of binning all voxels +
-    cost per pixel) extrapolates it to the whole view.  The per-voxel work
-    (prune, subdivide) runs on the full arrays.
-    """
+def oracle_step_time(scene_np, cam, gt_np):
+    """Wall time of one step of the oracle on the whole 1237x822 view: FP64 render (Eq. 1-5), LF loss
+    (Eq. 7-10), reverse pass, FP32 binning statistics, pruning (Eq. 11-12) from the same initial EMA
+    state as the GPU step, and subdivision (Eq. 13-16) on all voxels."""
     from oracle import oracle as O
-    a, b = crops
-    ta, _ = _oracle_pixel_work(O, scene_np, cam, gt_np, a)
-    tb, r = _oracle_pixel_work(O, scene_np, cam, gt_np, b)
-    slope = max((tb - ta) / float(b * b - a * a), 1e-9)
-    fixed = max(ta - slope * a * a, 0.0)
-    t_px = fixed + slope * W_IMG * H_IMG
     n = scene_np["geom"].shape[0]
+    t0 = time.perf_counter()
+    r = O.render(scene_np, [cam])
     t1 = time.perf_counter()
-    rng = np.random.default_rng(0)
+    lf = O.lf_loss(r["rgb"], gt_np.astype(np.float64).reshape(-1, 3), [(W_IMG, H_IMG)],
+                   gamma=O.lf_gamma(450.0, 300.0, 600.0, 0.6))
+    O.render_backward(scene_np, [cam], lf["dL_drgb"])
+    t2 = time.perf_counter()
+    st = O.pairs(scene_np, [cam])
     w = r["w_max"].astype(np.float32)
-    z = rng.uniform(3, 16, n).astype(np.float32)
-    seen = np.ones(n, np.uint8)
-    pr = O.prune(w, seen, z, np.ones(n, np.float32), np.ones(n, np.uint8))
-    O.subdivide(scene_np, (z / 1071.0).astype(np.float32), z, w, seen, prune_mask=pr["mask"])
-    t_vox = time.perf_counter() - t1
-    step = t_px + t_vox
-    sample = (f"render + LF loss + backward on centred {a}x{a} and {b}x{b} crops ({ta:.2f} s, {tb:.2f} s), "
-              f"extrapolated linearly (fixed {fixed:.2f} s + {slope * 1e6:.2f} us/pixel) to the 1237x822 view; "
-              f"prune + subdivide on all {n} voxels ({t_vox:.2f} s)")
-    return step, sample
+    pr = O.prune(w, st["seen"], st["z_min"], np.full(n, 0.32, np.float32), np.ones(n, np.uint8))
+    O.subdivide(scene_np, st["delta_min"], st["z_min"], w, st["seen"], prune_mask=pr["mask"])
+    t3 = time.perf_counter()
+    sample = (f"the whole step on the whole 1237x822 view: render {t1 - t0:.2f} s, LF loss + backward "
+              f"{t2 - t1:.2f} s, binning statistics + prune + subdivide on all {n} voxels {t3 - t2:.2f} s")
+    return t3 - t0, sample
 
 
 def cpu_baseline(scene_np, cam, gt_np):
     from oracle import oracle as O
     step, sample = oracle_step_time(scene_np, cam, gt_np)
     return {"value": (W_IMG * H_IMG) / step / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": sample}
+            "sample": sample, "seconds": step}
 
 
 # ---------------------------------------------------------------------------- arms
@@ -792,12 +837,23 @@ def run_ours(args, rank, world, local):
     gt_np = synth.random_image(W_IMG, H_IMG, seed=1 + rank)
     fixed = (args.tile, bool(args.persistent)) if args.tile is not None and args.persistent is not None else None
     wl = Workload(scene_np, cam, gt_np, tuned=True, schedule=fixed)
+    # one step from the initial state shows which rows the in-place topology change overwrites; every
+    # later step restores them (and the pruning state) at its end, so all steps do the same work
+    pristine = [a.clone() for a in wl._state_arrays()]
+    wl.step()
+    torch.cuda.synchronize()
+    first = wl.counters()
+    wl.prepare_restore(pristine)
+    del pristine
+    torch.cuda.empty_cache()
     for _ in range(max(3, args.warmup)):
         wl.step()
     torch.cuda.synchronize()
     cnt = wl.counters()
     if cnt["status"] != 0:
         raise RuntimeError(f"device status {cnt['status']} during warm-up")
+    if any(cnt[k] != first[k] for k in ("n_pruned", "n_new", "split", "pairs")):
+        raise RuntimeError(f"the restored state does not repeat the first step: {first} vs {cnt}")
 
     # ---- per-stage breakdown: K eager steps with an event at every stage boundary
     K = args.steps
@@ -892,41 +948,93 @@ def run_ours(args, rank, world, local):
     e2e_s = (time.perf_counter() - t0) / K
     e2e_val = world * wl.npix / max_over_ranks(e2e_s, world, "cuda") / 1e6
 
-    # the dominant kernel inside graph replays of the same step: timing events captured around the
-    # subdivision write, read after each of K more replays (the write is the only launch between them)
-    apply_ms_graph = None
+    # kernels inside graph replays of the same step: timing events captured around the composite
+    # (from the forward's composite event), the backward composite and the in-place topology change,
+    # read after each of K more replays
+    kernel_ms = {}
     try:
         # external: recorded as event nodes of the graph (rather than turned into a stream dependency)
-        ea = torch.cuda.Event(enable_timing=True, external=True)
-        eb = torch.cuda.Event(enable_timing=True, external=True)
-        g_marked = CapturedStep(lambda: wl.step_concurrent(apply_events=(ea, eb)))
-        samples = []
+        marks = {k: (torch.cuda.Event(enable_timing=True, external=True),
+                     torch.cuda.Event(enable_timing=True, external=True)) for k in ("composite", "backward", "apply")}
+        for a, b in marks.values():
+            a.record()
+            b.record()
+        g_marked = CapturedStep(lambda: wl.step_concurrent(ev=marks))
+        samples = {k: [] for k in marks}
         for _ in range(K):
             g_marked()
             torch.cuda.synchronize()
-            samples.append(ea.elapsed_time(eb))
-        apply_ms_graph = float(np.median(samples))
-    except Exception as e:  # event nodes in a graph: keep the eager stage time if the runtime refuses
-        print(f"graph-timed subdivision write unavailable: {e!r}", file=sys.stderr)
-        apply_ms_graph = None
+            for k, (a, b) in marks.items():
+                samples[k].append(a.elapsed_time(b))
+        kernel_ms = {k: float(np.median(v)) for k, v in samples.items()}
+        del g_marked
+    except Exception as e:  # event nodes in a graph: fall back to the eager stage times if refused
+        print(f"graph-timed kernels unavailable: {e!r}", file=sys.stderr)
+        kernel_ms = {}
+
+    # the out-of-place form of the same topology change (lv_subdivide_apply: every survivor copied to
+    # new arrays), on the last step's selection, for comparison
+    oop_ms = None
+    try:
+        cap = wl.cap
+        og = [torch.empty((cap,) + tuple(t.shape[1:]), dtype=t.dtype, device="cuda")
+              for t in (wl.scene.geom, wl.scene.level, wl.scene.density, wl.scene.sh)]
+        vout = L.make_voxels(og[0], og[2], og[3], og[1])
+        vout.n = cap
+        aux_o, keep_o = [], []
+        for a, t in zip(wl.aux, wl.aux_arrays):
+            o = torch.empty_like(t)
+            x = L.lv_aux_array()
+            x.in_, x.out, x.width, x.elem_bytes, x.fill = t.data_ptr(), o.data_ptr(), a.width, a.elem_bytes, a.fill
+            aux_o.append(x)
+            keep_o.append(o)
+        oop_ms = _time_ms(torch, lambda: L.lv_subdivide_apply(wl.vox, wl.sp, aux_o, vout, wl.sd_ws), K)
+        del og, vout, aux_o, keep_o
+        torch.cuda.empty_cache()
+    except Exception as e:
+        print(f"out-of-place comparison unavailable: {e!r}", file=sys.stderr)
 
     cnt = wl.counters()
+    if any(cnt[k] != first[k] for k in ("n_pruned", "n_new", "split", "pairs")):
+        raise RuntimeError(f"the timed steps did not repeat the first step: {first} vs {cnt}")
     if rank == 0:
         hbm_peak, peak_src = peaks()
-        # dominant kernel: the subdivision write (one launch, alone in the "subdivide_apply" stage),
-        # an HBM-bound copy of every surviving voxel's state plus the children
-        t_apply = apply_ms_graph if apply_ms_graph else stage_ms["subdivide_apply"]
+        sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+        fp32_peak = alu_peak_tflops(sm_mhz)
         row = wl.row_bytes()
         parent_row = 16 + 1 + 8 * wl.scene.density.element_size() + 48 * wl.scene.sh.element_size()
-        bytes_apply = algorithmic_bytes("subdivide_apply", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix,
-                                        cnt["n_new"], cnt["split"], row, parent_row)
-        achieved = bytes_apply / (t_apply / 1e3) / 1e9
-        traffic = dram_traffic("k_sd_write")
-        # the composite kernels are bound by FP32 instruction issue: reported beside it
-        sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
-        t_bwd = stage_ms["backward"]
-        bwd_flops = cnt["samples"] * FLOPS_PER_SAMPLE["backward_composite"]
-        bytes_bwd = algorithmic_bytes("backward_composite", wl.n, cnt["pairs"], cnt["visible_slots"], wl.npix)
+        tiles = sum(((c["width"] + wl.tile - 1) // wl.tile) * ((c["height"] + wl.tile - 1) // wl.tile)
+                    for c in wl.cams)
+        work = stage_work(wl.n, cnt["visible_slots"], cnt["pairs"], wl.npix, tiles, cnt["samples"], cnt["split"],
+                          cnt["n_pruned"], row, parent_row)
+        # the kernels timed inside graph replays; their algorithmic bytes and FP32 operations
+        names = {"composite": ("k_fwd (front-to-back composite, Eq. 2-5)", "a5_forward_composite"),
+                 "backward": ("k_bwd (back-to-front composite, reverse of Eq. 2-4)", "a6_backward_composite"),
+                 "apply": ("k_ip_children + k_ip_holes (in-place topology change, Sec. IV-D)", "subdivide_inplace")}
+        fallback = {"composite": None, "backward": stage_ms["backward"], "apply": stage_ms["subdivide_inplace"]}
+        kernels = {}
+        for key, (label, stage) in names.items():
+            t = kernel_ms.get(key) or fallback[key]
+            if not t:
+                continue
+            w = work[stage]
+            gbs = w["bytes"] / (t / 1e3) / 1e9
+            tfl = w["flops"] / (t / 1e3) / 1e12
+            kernels[key] = {"kernel": label, "ms": t, "algorithmic_bytes": w["bytes"], "flops": w["flops"],
+                            "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak, "achieved_tflops": tfl,
+                            "fp32_frac": tfl / fp32_peak,
+                            "timing": "graph replays (event nodes, median of K)" if kernel_ms.get(key)
+                                      else "eager stage events (median of K)"}
+        dom = max(kernels, key=lambda k_: kernels[k_]["ms"])
+        d = kernels[dom]
+        traffic_key = {"composite": "k_fwd", "backward": "k_bwd", "apply": "k_ip_children"}[dom]
+        roofline = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["achieved_gbs"], "peak": hbm_peak,
+                    "unit": "GB/s", "frac": d["hbm_frac"], "traffic": dram_traffic(traffic_key),
+                    "peak_source": peak_src, "algorithmic_bytes": d["algorithmic_bytes"], "kernel_ms": d["ms"],
+                    "kernel_timing": d["timing"], "kernels": kernels,
+                    "fp32_peak_tflops": fp32_peak,
+                    "fp32_peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                    "step_level": step_roofline(work, ms_max, hbm_peak, fp32_peak)}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic",
@@ -938,26 +1046,14 @@ def run_ours(args, rank, world, local):
                                        else "one block per tile"),
                           "autotune_ms": wl.tune_ms,
                           "l2": "inputs larger than L2 (scene arrays 480 MB, per-step outputs > 600 MB)"},
-               "roofline": {"bound": "hbm", "kernel": "k_sd_write (subdivision: survivor and child rows)",
-                            "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                            "traffic": traffic, "peak_source": peak_src, "algorithmic_bytes": bytes_apply,
-                            "kernel_ms": t_apply,
-                            "kernel_timing": ("events captured around the launch in graph replays of the step "
-                                              "(median of K)") if apply_ms_graph else
-                                             "events around the launch in K eager steps (median)",
-                            "row_bytes": row,
-                            "backward_composite": {
-                                "bound": "alu", "achieved_tflops": bwd_flops / (t_bwd / 1e3) / 1e12,
-                                "peak_tflops": alu_peak_tflops(sm_mhz),
-                                "frac": bwd_flops / (t_bwd / 1e3) / 1e12 / alu_peak_tflops(sm_mhz),
-                                "samples": cnt["samples"], "flops_per_sample": FLOPS_PER_SAMPLE["backward_composite"],
-                                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
-                                "hbm_achieved_gbs": bytes_bwd / (t_bwd / 1e3) / 1e9}},
+               "roofline": roofline,
                "stages_ms": stage_ms, "eager_ms_per_step": eager_ms,
                "timing": "device time of K replays of the step captured in one CUDA graph (CUDA events); the "
                          "step runs on three streams (LF weights beside the forward, pruning and the subdivision "
-                         "selection beside the backward, joined by events before the subdivision write); "
-                         "stages_ms from K eager one-stream steps with an event at every stage boundary",
+                         "selection beside the backward, joined by events before the in-place topology change); "
+                         "every step ends by restoring the rows its topology change overwrote and the pruning "
+                         "state (torch index copies, inside the timed region), so that all steps do the same "
+                         "work; stages_ms from K eager one-stream steps with an event at every stage boundary",
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(wl.gt_host.numel() * 4),
                        "d2h_bytes_per_step": 4,
                        "how": "host wall clock of K steps through the API: each step's ground-truth image is "
@@ -965,6 +1061,15 @@ def run_ours(args, rank, world, local):
                               "its loss is copied back to pinned host memory and read by the host while the next "
                               "step runs"},
                "gpu_launches": int(launches),
+               "restore": {"rows": int(wl.restore_idx.numel()), "torch_launches_per_step": 6,
+                           "what": "index copies of the overwritten rows of the geometry, level, corner and SH "
+                                   "arrays and full copies of the EMA and hysteresis state, inside the timed "
+                                   "region (extra work, not part of the method)"},
+               "topology_change": {"inplace_ms": kernels.get("apply", {}).get("ms"),
+                                   "out_of_place_ms": oop_ms,
+                                   "inplace_bytes": work["subdivide_inplace"]["bytes"],
+                                   "out_of_place_bytes": (wl.n - cnt["n_pruned"] - cnt["split"]) * row * 2
+                                   + 8 * cnt["split"] * row + cnt["split"] * parent_row},
                "clocks": clocks,
                "step_counters": cnt}
         if not args.no_variants:

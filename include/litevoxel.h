@@ -117,6 +117,11 @@ typedef struct {
   int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: size the resident grid for this many SMs (0 = all),
                              leaving the rest to kernels of other streams that run beside the composites;
                              it changes no result and may differ between the forward and backward calls */
+  int64_t pixel_id_base;  /* global id of this call's first pixel (0): the pixel ids packed into w_max
+                             (Eq. 5's argmax and its tie rule) are pixel_id_base + the view-major index;
+                             calls or ranks that render disjoint views with disjoint bases accumulate one
+                             w_max exactly as one call over all the views; base + pixels must stay
+                             below 2^32 - 1 */
 } lv_raster_opts;
 
 /* Forward outputs (device).  P = total pixels of all views. */

@@ -44,12 +44,14 @@ struct DevView {
 struct ViewSet {
   int n;
   int ts;
+  long long id_base;  // global id of the call's first pixel (w_max argmax ids)
   DevView v[LV_MAX_VIEWS];
 };
 
 static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64_t* tiles, int64_t* pixels) {
   vs->n = nv;
   vs->ts = ts;
+  vs->id_base = 0;
   int64_t to = 0, po = 0;
   for (int i = 0; i < nv; ++i) {
     const lv_camera& c = cams[i];
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
     const Ray r = make_ray(c, px, py);
     const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
     const unsigned long long gid = (unsigned long long)(c.pix_off + (long long)py * c.W + px);
-    const unsigned long long gid_key = 0xffffffffull - (gid & 0xffffffffull);
+    const unsigned long long gid_key = 0xffffffffull - ((gid + (unsigned long long)vs.id_base) & 0xffffffffull);
     float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
     uint32_t last = 0, nsamp = 0;
     bool done = !inside;
@@ -1218,6 +1220,10 @@ static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int n
     pixels += (int64_t)c.width * c.height;
   }
   if (tiles > 0x7fffffffLL || pixels > 0xfffffffeLL) { set_error("too many tiles or pixels"); return LV_ERR_INVALID_ARG; }
+  if (o->pixel_id_base < 0 || o->pixel_id_base + pixels > 0xfffffffeLL) {
+    set_error("pixel_id_base %lld: the pixel ids must stay in [0, 2^32 - 1)", (long long)o->pixel_id_base);
+    return LV_ERR_INVALID_ARG;
+  }
   if (vox->n * nv > 0x7fffffffLL) { set_error("voxels x views exceeds 2^31"); return LV_ERR_INVALID_ARG; }
   return LV_OK;
 }
@@ -1362,6 +1368,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   ViewSet vs;
   int64_t tiles, pixels;
   make_views(cams, n_views, opts->tile, &vs, &tiles, &pixels);
+  vs.id_base = opts->pixel_id_base;
   FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;

@@ -46,7 +46,7 @@ class lv_camera(C.Structure):
 
 class lv_raster_opts(C.Structure):
     _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("threads_per_px", C.c_int32), ("t_stop", C.c_float),
-                ("flags", C.c_uint32), ("persistent_sms", C.c_int32)]
+                ("flags", C.c_uint32), ("persistent_sms", C.c_int32), ("pixel_id_base", C.c_int64)]
 
 
 class lv_fwd_out(C.Structure):
@@ -228,10 +228,11 @@ def make_cameras(cams) -> C.Array:
 
 
 def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=False,
-              persistent=False, persistent_sms=0) -> lv_raster_opts:
+              persistent=False, persistent_sms=0, pixel_id_base=0) -> lv_raster_opts:
     o = lv_raster_opts()
     o.tile, o.batch, o.threads_per_px, o.t_stop = tile, batch, 1, t_stop
     o.persistent_sms = int(persistent_sms)
+    o.pixel_id_base = int(pixel_id_base)
     o.flags = ((LV_FLAG_SYNC_CHECK if sync_check else 0) | (LV_FLAG_EXACT_SEGMENT if exact_segment else 0) |
                (LV_FLAG_PERSISTENT if persistent else 0))
     return o

@@ -54,12 +54,19 @@ def test_committed_traffic_record_is_well_formed():
         assert "--clock-control none" in r.get("command", "--clock-control none")
 
 
-def test_algorithmic_bytes_of_the_subdivision_write():
-    # 10 output rows of which 8 are the children of one split parent: 2 survivors read and written,
-    # 8 children written, the parent's row read once
-    assert bench.algorithmic_bytes("subdivide_apply", n=5, pairs=0, slots=0, npix=0, n_new=10, split=1, row=694,
-                                   parent_row=241) == 2 * 2 * 694 + 8 * 694 + 241
-    assert bench.algorithmic_bytes("unknown", 1, 1, 1, 1) == 0
+def test_stage_work_and_step_roofline():
+    w = bench.stage_work(n=10, slots=4, pairs=6, npix=3, tiles=2, samples=5, split=1, pruned=2, row=694,
+                         parent_row=241)
+    # per pair the slot index and the 64-byte record, per pixel the 24 output bytes, one w_max word per pair
+    assert w["a5_forward_composite"] == {"bytes": 6 * 68 + 3 * 24 + 6 * 8, "flops": 5 * 68}
+    assert w["a6_backward_composite"] == {"bytes": 6 * 68 + 3 * 40 + 6 * 88, "flops": 5 * 102}
+    # in place: the split parent's row read once, its 8 children written, the mask and the hole list
+    assert w["subdivide_inplace"]["bytes"] == 241 + 8 * 694 + 10 + 4 * 2
+    r = bench.step_roofline({"x": {"bytes": 2e9, "flops": 0}, "y": {"bytes": 1e6, "flops": 1e12}}, ms_step=24.0,
+                            hbm_gbs=1000.0, fp32_tflops=100.0)
+    # x: 2 ms of HBM; y: 10 ms of FP32 against 0.001 ms of HBM
+    assert r["stages"]["x"]["bound"] == "hbm" and r["stages"]["y"]["bound"] == "alu"
+    assert r["sum_bound_ms"] == pytest.approx(12.0) and r["frac"] == pytest.approx(0.5)
 
 
 def test_alu_peak():
