@@ -52,6 +52,7 @@ def parse():
     # distorted timings would steer the autotuner elsewhere): tile edge and 0 / 1 for persistent
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None)
     ap.add_argument("--persistent", type=int, choices=[0, 1], default=None)
+    ap.add_argument("--batch", type=int, choices=[32, 64, 128], default=32)
     return ap.parse_args()
 
 
@@ -74,9 +75,9 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 
 
 def tuned_schedule(scene, cams):
-    """Tile size and composite schedule from the library's autotuner (lv_autotune: every tile
-    size with and without persistent warps, forward + backward timed with CUDA events on this
-    scene and these views), as a user of the library would pick them."""
+    """Tile size, batch and composite schedule from the library's autotuner (lv_autotune: every
+    tile size and batch with and without persistent warps, forward + backward timed with CUDA
+    events on this scene and these views), as a user of the library would pick them."""
     import torch
 
     from paper_2511_02510_gb300 import litevoxel as L
@@ -91,7 +92,7 @@ def tuned_schedule(scene, cams):
     best, ms = L.lv_autotune(vox, probe.cams_arr, len(cams), base, cap, 3, ws)
     del ws, probe
     torch.cuda.empty_cache()
-    return int(best.tile), bool(best.flags & L.LV_FLAG_PERSISTENT), ms
+    return int(best.tile), bool(best.flags & L.LV_FLAG_PERSISTENT), int(best.batch), ms
 
 
 def camera_for(rank: int):
@@ -125,13 +126,14 @@ class Workload:
         for b, t in zip(big, (src.geom, src.level, src.density, src.sh)):
             b[:n].copy_(t)
         del src
+        self.cap_arrays = big  # geometry, level, corners, SH with room for the growth
         self.scene = Scene(big[0][:n], big[1][:n], big[2][:n], big[3][:n])
         self.cams = [cam]
-        self.tile, self.persistent, self.tune_ms = 16, False, None
+        self.tile, self.persistent, self.batch, self.tune_ms = 16, False, 32, None
         if schedule is not None:
-            self.tile, self.persistent = schedule
+            self.tile, self.persistent, self.batch = schedule
         elif tuned:
-            self.tile, self.persistent, self.tune_ms = tuned_schedule(self.scene, self.cams)
+            self.tile, self.persistent, self.batch, self.tune_ms = tuned_schedule(self.scene, self.cams)
         # the persistent backward composite leaves 48 SMs to the pruning and selection kernels
         # that the three-stream step runs beside it (a full-GPU resident grid starves them; a
         # sweep of the backward's SMs gave 1.332 ms per step on 152, 1.303 on 120, 1.301 on
@@ -139,8 +141,9 @@ class Workload:
         self.persistent_sms = 0
         if self.persistent:
             self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 48)
-        self.rctx = RasterContext(self.cams, n, tile=self.tile, persistent=self.persistent)
-        self.bwd_opts = L.make_opts(self.tile, persistent=self.persistent, persistent_sms=self.persistent_sms)
+        self.rctx = RasterContext(self.cams, n, tile=self.tile, batch=self.batch, persistent=self.persistent)
+        self.bwd_opts = L.make_opts(self.tile, self.batch, persistent=self.persistent,
+                                    persistent_sms=self.persistent_sms)
         self.vox = self.scene.voxels()
         self.rctx.fit_capacity(self.vox)
         self.npix = self.rctx.n_pix
@@ -671,10 +674,10 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
         cams = [camera_for(0)]
         dd, sd = torch.float32, torch.float32
     scene = Scene.from_numpy(sc, "cuda", dd, sd)
-    tile, persistent = 16, kind == "persistent_fp32"
+    tile, persistent, batch = 16, kind == "persistent_fp32", 32
     if kind in ("plain_fp32", "batched16_fp32", "batched8_mixed"):  # the autotuned schedule, as the bench step
-        tile, persistent, _ = tuned_schedule(scene, cams)
-    ctx = RasterContext(cams, scene.n, tile=tile, exact_segment=(kind == "exact_segment_fp32"),
+        tile, persistent, batch, _ = tuned_schedule(scene, cams)
+    ctx = RasterContext(cams, scene.n, tile=tile, batch=batch, exact_segment=(kind == "exact_segment_fp32"),
                         persistent=persistent)
     vox = scene.voxels()
     ctx.fit_capacity(vox)
@@ -704,7 +707,7 @@ def run_variant(torch, synth, kind, scene_np, steps=10, warmup=3):
     ctx.check()
     ms = e0.elapsed_time(e1) / steps
     return {"value": ctx.n_pix / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "views": len(cams),
-            "pixels": ctx.n_pix, "tile": tile, "persistent": persistent, "density_dtype": str(dd).split(".")[-1], "sh_dtype": str(sd).split(".")[-1],
+            "pixels": ctx.n_pix, "tile": tile, "batch": batch, "persistent": persistent, "density_dtype": str(dd).split(".")[-1], "sh_dtype": str(sd).split(".")[-1],
             "step": "stats reset + forward + backward (composite + SH), replayed as one CUDA graph"}
 
 
@@ -835,7 +838,8 @@ def run_ours(args, rank, world, local):
     scene_np = synth.scene_360(seed=args.seed)
     cam = camera_for(rank)
     gt_np = synth.random_image(W_IMG, H_IMG, seed=1 + rank)
-    fixed = (args.tile, bool(args.persistent)) if args.tile is not None and args.persistent is not None else None
+    fixed = ((args.tile, bool(args.persistent), args.batch) if args.tile is not None and args.persistent is not None
+             else None)
     wl = Workload(scene_np, cam, gt_np, tuned=True, schedule=fixed)
     # one step from the initial state shows which rows the in-place topology change overwrites; every
     # later step restores them (and the pruning state) at its end, so all steps do the same work
@@ -1041,7 +1045,7 @@ def run_ours(args, rank, world, local):
                "config": {"workload": WORKLOAD, "model": "LiteVoxel sparse-voxel tile rasterizer",
                           "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
                           "voxels": wl.n, "pixels_per_rank": wl.npix, "pairs": cnt["pairs"],
-                          "visible_slots": cnt["visible_slots"], "tile": wl.tile,
+                          "visible_slots": cnt["visible_slots"], "tile": wl.tile, "batch": wl.batch,
                           "schedule": (f"persistent warps (backward on {wl.persistent_sms} SMs)" if wl.persistent
                                        else "one block per tile"),
                           "autotune_ms": wl.tune_ms,

@@ -110,8 +110,9 @@ typedef struct {
 
 typedef struct {
   int32_t tile;           /* tile edge in pixels: 8, 16 or 32 */
-  int32_t batch;          /* reserved (64, 128 or 256): records are staged in 32-entry chunks per warp */
-  int32_t threads_per_px; /* 1 (reserved) */
+  int32_t batch;          /* list entries a warp stages per round (32, 64 or 128; 128 not with tile 32):
+                             their records are loaded together into the warp's shared-memory slice
+                             (64 B each) before its pixels march through them; changes no result */
   float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
   uint32_t flags;         /* LV_FLAG_* */
   int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: size the resident grid for this many SMs (0 = all),
@@ -214,19 +215,21 @@ lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_view
                          void* stream);
 
 /* Autotuner of the composite schedule (batched views in one launch: tile
- * size and scheduling chosen per scene and view set).  Each candidate --
- * tile edge 8, 16, 32, each with one block per tile and with persistent
- * warps (LV_FLAG_PERSISTENT) -- runs one warm-up forward + backward and then
- * `reps` (1 .. 1000) timed ones on the caller's scene and views, timed with
- * CUDA events on `stream`; the call synchronises the stream.  *best receives
- * *base with the fastest tile and LV_FLAG_PERSISTENT choice.  ms_out (host
- * float[6], nullable) receives each candidate's mean forward + backward
- * time in ms in the order (8, block), (8, persistent), (16, block),
- * (16, persistent), (32, block), (32, persistent); -1 for a candidate that
- * needs more than pair_capacity pairs (skipped), and -1 everywhere on a
- * cache hit.  cache_path (nullable) is a text file of "key tile persistent"
- * lines keyed by device name, voxel count, view sizes and the other flags:
- * a hit returns at once, a tuned result is appended.  workspace:
+ * size, batch and scheduling chosen per scene and view set).  Each candidate
+ * -- tile edge 8, 16, 32 x one block per tile or persistent warps
+ * (LV_FLAG_PERSISTENT) x batch 32, 64, 128 (not 128 with tile 32) -- runs one
+ * warm-up forward + backward and then `reps` (1 .. 1000) timed ones on the
+ * caller's scene and views, timed with CUDA events on `stream`; the call
+ * synchronises the stream.  *best receives *base with the fastest tile,
+ * batch and LV_FLAG_PERSISTENT choice.  ms_out (host float[18], nullable)
+ * receives each candidate's mean forward + backward time in ms at index
+ * (6 t + 3 p + b) for tile t (0: 8, 1: 16, 2: 32), schedule p (0: block per
+ * tile, 1: persistent) and batch b (0: 32, 1: 64, 2: 128); -1 for a candidate
+ * that is refused or needs more than pair_capacity pairs (skipped), and -1
+ * everywhere on a cache hit.  cache_path (nullable) is a text file of
+ * "key tile persistent batch" lines keyed by device name, voxel count, view
+ * sizes and the other flags (a line without the batch means 32): a hit
+ * returns at once, a tuned result is appended.  workspace:
  * lv_autotune_workspace_size(n, cams, n_views, base, pair_capacity) bytes
  * (forward workspace for the largest need, outputs and gradients).
  * LV_ERR_CAPACITY when no candidate fits the pair capacity. */
@@ -525,7 +528,10 @@ lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, const int32
  *    views); larger requests return LV_ERR_INVALID_ARG without launching.
  *  - The first call on each device looks up the array's device address once
  *    (with that device current); make that first call before any stream
- *    capture.
+ *    capture.  The address is kept for the life of the process: after a
+ *    cudaDeviceReset (or any destruction of the device's primary context) the
+ *    library's device array may be loaded elsewhere, so do not call this entry
+ *    point again on that device until the library is reloaded.
  *  - All calls share the one array: calls that overlap on the GPU (for
  *    example on two streams at once) race and give wrong results.  Each call
  *    clears the parts of the array that must start at zero.

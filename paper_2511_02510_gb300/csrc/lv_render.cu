@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     }
   }
   int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
-  int px0 = 0, px1 = 0, py0 = 0, py1 = 0;  // pixels x in [px0, px1) may be hit (1-pixel margin)
+  int px0 = 0, px1 = 0, py0 = 0, py1 = 0;  // pixels x in [px0, px1) may be hit (their centres lie in the box)
   if (n_front > 0) {
     if (n_front < 8) {
       // near-plane clipping: crossing points of the box edges (k, k|bit) with z = z_near
@@ -264,10 +264,18 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     tx1 = (int)fminf(fmaxf(a1, 0.0f), (float)c.tiles_x);
     ty0 = (int)fminf(fmaxf(b0, 0.0f), (float)c.tiles_y);
     ty1 = (int)fminf(fmaxf(b1, 0.0f), (float)c.tiles_y);
-    px0 = (int)fminf(fmaxf(floorf(__fsub_rn(umin, 1.0f)), 0.0f), (float)c.W);
-    px1 = (int)fminf(fmaxf(ceilf(__fadd_rn(umax, 1.0f)), 0.0f), (float)c.W);
-    py0 = (int)fminf(fmaxf(floorf(__fsub_rn(vmin, 1.0f)), 0.0f), (float)c.H);
-    py1 = (int)fminf(fmaxf(ceilf(__fadd_rn(vmax, 1.0f)), 0.0f), (float)c.H);
+    // The composites only cull with the pixel box: a ray through the centre (x + 1/2, y + 1/2) of
+    // pixel (x, y) meets the box only if that centre lies in the footprint's bounding box
+    // [umin, umax] x [vmin, vmax].  The FP32 projection and the FP32 ray of the chord test are
+    // each within about 1e-3 pixel of exact, so widening the box by 1/16 pixel plus 2^-14 of the
+    // coordinate keeps every pixel an FP32 chord test can hit; the tile rectangle above keeps its
+    // 1-pixel margin.
+    const float eu = fmaf(6.1035156e-5f, fmaxf(fabsf(umin), fabsf(umax)), 0.0625f);
+    const float ev = fmaf(6.1035156e-5f, fmaxf(fabsf(vmin), fabsf(vmax)), 0.0625f);
+    px0 = (int)fminf(fmaxf(ceilf(umin - eu - 0.5f), 0.0f), (float)c.W);
+    px1 = (int)fminf(fmaxf(floorf(umax + eu - 0.5f) + 1.0f, (float)px0), (float)c.W);
+    py0 = (int)fminf(fmaxf(ceilf(vmin - ev - 0.5f), 0.0f), (float)c.H);
+    py1 = (int)fminf(fmaxf(floorf(vmax + ev - 0.5f) + 1.0f, (float)py0), (float)c.H);
   }
   uint32_t count = (tx1 > tx0 && ty1 > ty0) ? (uint32_t)(tx1 - tx0) * (uint32_t)(ty1 - ty0) : 0u;
   cnt[i] = count;
@@ -698,18 +706,58 @@ __device__ __forceinline__ uint32_t next_item(unsigned int* work, int lane) {
 }
 
 // ------------------------------------------------------------------ forward composite
-// Each warp walks its strip's tile list on its own: 32 list entries at a
-// time, the entries whose pixel box meets the strip are compacted with a
-// ballot and their 64-byte records staged in the warp's slice of shared
-// memory, then every lane marches its pixel through them front to back.  No
-// block-wide barrier: a warp stops as soon as all its pixels have stopped.
-// per-warp staging slice: 32 records (64 B) + voxel id + list entry (+ slot id in the backward)
-constexpr size_t FWD_SLICE = 32 * 64 + 32 * 4 * 2;
-constexpr size_t BWD_SLICE = 32 * 64 + 32 * 4 * 3;
+// Each warp walks its strip's tile list on its own: CH list entries at a time
+// (the batch: 32, 64 or 128, CH / 32 per lane, all loads of a batch issued
+// before any is used), the entries whose pixel box meets the strip are
+// compacted with ballots and their 64-byte records staged in the warp's slice
+// of shared memory, then every lane marches its pixel through them front to
+// back.  No block-wide barrier: a warp stops as soon as all its pixels have
+// stopped.
+// per-warp staging slice: CH records (64 B) + voxel id + list entry (+ slot id in the backward)
+__host__ __device__ constexpr size_t fwd_slice(int ch) { return (size_t)ch * 64 + (size_t)ch * 4 * 2; }
+__host__ __device__ constexpr size_t bwd_slice(int ch) { return (size_t)ch * 64 + (size_t)ch * 4 * 3; }
+
+// Stage the entries [base, base + CH) below `end` whose pixel box meets the
+// strip: records in list order at positions 0 .. m - 1 of the warp's slice
+// (voxel id, list entry and, with slot_out, the slot id beside them); returns m.
+template <int TS, int CH>
+__device__ __forceinline__ int stage_batch(uint32_t base, uint32_t end, int lane, const Strip<TS>& strip,
+                                           const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
+                                           const uint2* __restrict__ rec_bb, const uint32_t* __restrict__ slot_vox,
+                                           float4* wr, uint32_t* w_vox, uint32_t* w_ent, uint32_t* w_slot) {
+  constexpr int K = CH / 32;
+  uint32_t sl[K];
+  bool ov[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t e = base + 32 * k + lane;
+    sl[k] = e < end ? svals[e] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) ov[k] = base + 32 * k + lane < end && !strip.misses(rec_bb[sl[k]]);
+  int m = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t mask = __ballot_sync(FULL, ov[k]);
+    if (ov[k]) {
+      const int pos = m + __popc(mask & ((1u << lane) - 1u));
+      const float4* src = rec + 4 * (size_t)sl[k];
+      wr[4 * pos + 0] = src[0];
+      wr[4 * pos + 1] = src[1];
+      wr[4 * pos + 2] = src[2];
+      wr[4 * pos + 3] = src[3];
+      w_vox[pos] = slot_vox[sl[k]];
+      w_ent[pos] = base + 32 * k + lane;
+      if (w_slot) w_slot[pos] = sl[k];
+    }
+    m += __popc(mask);
+  }
+  return m;
+}
 template <int TS>
 constexpr int min_blocks() { return TS == 16 ? 5 : (TS == 8 ? 16 : 1); }
 
-template <int TS, bool SEG, bool PERSIST>
+template <int TS, bool SEG, bool PERSIST, int CH>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -722,9 +770,9 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float4* wr = (float4*)((char*)smem_f4 + FWD_SLICE * warp);
-  uint32_t* w_vox = (uint32_t*)(wr + 128);
-  uint32_t* w_ent = w_vox + 32;
+  float4* wr = (float4*)((char*)smem_f4 + fwd_slice(CH) * warp);
+  uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
+  uint32_t* w_ent = w_vox + CH;
   for (uint32_t item = PERSIST ? next_item(work, lane) : blockIdx.x * NW + warp; item < n_items;
        item = PERSIST ? next_item(work, lane) : n_items) {  // warp-uniform
     const int gtile = (int)(item / NW);
@@ -742,29 +790,13 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
     float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
     uint32_t last = 0, nsamp = 0;
     bool done = !inside;
-    for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += 32) {
-      const uint32_t e = base + lane;
-      uint32_t sl = 0;
-      bool ov = false;
-      if (e < end) {
-        sl = svals[e];
-        ov = !strip.misses(rec_bb[sl]);
-      }
-      const uint32_t mask = __ballot_sync(FULL, ov);
-      if (!mask) continue;
-      if (ov) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        const float4* src = rec + 4 * (size_t)sl;
-        wr[4 * pos + 0] = src[0];
-        wr[4 * pos + 1] = src[1];
-        wr[4 * pos + 2] = src[2];
-        wr[4 * pos + 3] = src[3];
-        w_vox[pos] = slot_vox[sl];
-        w_ent[pos] = e;
-      }
+    for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += CH) {
+      const int m = stage_batch<TS, CH>(base, end, lane, strip, svals, rec, rec_bb, slot_vox, wr, w_vox, w_ent,
+                                        nullptr);
+      if (!m) continue;
       __syncwarp();
-      const int m = __popc(mask);
       for (int j = 0; j < m; ++j) {
+        if (CH > 32 && (j & 31) == 31 && __all_sync(FULL, done)) break;  // warp-uniform
         const float4 g = wr[4 * j];
         float t_in, t_out;
         const bool hit = !done && chord(r, g, t_in, t_out);
@@ -852,7 +884,7 @@ __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
 // any of its pixels used, in the same 32-entry chunks and with the same
 // compaction as the forward; the per-record gradients (8 corners + colour) are
 // reduced over the warp and sent with three 16-byte global reductions.
-template <int TS, bool SEG, bool PERSIST>
+template <int TS, bool SEG, bool PERSIST, int CH>
 __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_constant__ ViewSet vs, const uint32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ svals, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ rec_bb,
@@ -865,10 +897,10 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float4* wr = (float4*)((char*)smem_f4 + BWD_SLICE * warp);
-  uint32_t* w_vox = (uint32_t*)(wr + 128);
-  uint32_t* w_slot = w_vox + 32;
-  uint32_t* w_ent = w_slot + 32;
+  float4* wr = (float4*)((char*)smem_f4 + bwd_slice(CH) * warp);
+  uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
+  uint32_t* w_slot = w_vox + CH;
+  uint32_t* w_ent = w_slot + CH;
   for (uint32_t item = PERSIST ? next_item(work, lane) : blockIdx.x * NW + warp; item < n_items;
        item = PERSIST ? next_item(work, lane) : n_items) {  // warp-uniform
     const int gtile = (int)(item / NW);
@@ -899,31 +931,14 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
     const float tgT = Tf * gT;
     float S = 0.f;
     float Tcur = __expf(-tau);  // T after the last sample, from the stored optical depth
-    // chunks aligned as in the forward: [start + 32 k, start + 32 k + 32)
-    for (uint32_t cb = start + ((warp_hi - start + 31u) & ~31u); cb > start; cb -= 32) {
-      const uint32_t base = cb - 32;
-      const uint32_t e = base + lane;
-      uint32_t sl = 0;
-      bool ov = false;
-      if (e < warp_hi) {
-        sl = svals[e];
-        ov = !strip.misses(rec_bb[sl]);
-      }
-      const uint32_t mask = __ballot_sync(FULL, ov);
-      if (!mask) continue;
-      if (ov) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        const float4* src = rec + 4 * (size_t)sl;
-        wr[4 * pos + 0] = src[0];
-        wr[4 * pos + 1] = src[1];
-        wr[4 * pos + 2] = src[2];
-        wr[4 * pos + 3] = src[3];
-        w_vox[pos] = slot_vox[sl];
-        w_slot[pos] = sl;
-        w_ent[pos] = e;
-      }
+    // batches aligned as in the forward: [start + CH k, start + CH k + CH), walked back to front
+    for (uint32_t cb = start + (warp_hi - start + CH - 1) / CH * CH; cb > start; cb -= CH) {
+      const uint32_t base = cb - CH;
+      const int m = stage_batch<TS, CH>(base, warp_hi, lane, strip, svals, rec, rec_bb, slot_vox, wr, w_vox,
+                                        w_ent, w_slot);
+      if (!m) continue;
       __syncwarp();
-      for (int j = __popc(mask) - 1; j >= 0; --j) {
+      for (int j = m - 1; j >= 0; --j) {
         const float4 g = wr[4 * j];
         float t_in, t_out;
         const bool hit = w_ent[j] < my_hi && chord(r, g, t_in, t_out);
@@ -961,8 +976,9 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
         }
         float* dd = d_density + 8 * (size_t)w_vox[j];
         float* dc = (float*)(d_rgb + w_slot[j]);
-        if (__popc(hb) <= 2) {
-          // one or two lanes: each sends its own values, cheaper than the butterfly
+        if (__popc(hb) <= 8) {
+          // up to eight lanes: each sends its own values, cheaper than the butterfly (measured: 8 lanes
+          // 2 % faster than 2; every lane, 12x slower, the reductions to one address serialise)
           if (hit) {
             red_add_v4(dd, v[0], v[1], v[2], v[3]);
             red_add_v4(dd + 4, v[4], v[5], v[6], v[7]);
@@ -1207,8 +1223,11 @@ static lv_status check_common(const lv_voxels* vox, const lv_camera* cams, int n
   if (vox->sh_degree < 0 || vox->sh_degree > 3) { set_error("sh_degree must be 0..3"); return LV_ERR_INVALID_ARG; }
   if (vox->vidx && ((uintptr_t)vox->vidx & 15)) { set_error("vidx must be 16-byte aligned"); return LV_ERR_INVALID_ARG; }
   if (o->tile != 8 && o->tile != 16 && o->tile != 32) { set_error("tile must be 8, 16 or 32"); return LV_ERR_INVALID_ARG; }
-  if (o->batch != 64 && o->batch != 128 && o->batch != 256) { set_error("batch must be 64, 128 or 256"); return LV_ERR_INVALID_ARG; }
-  if (o->threads_per_px != 1) { set_error("threads_per_px must be 1 (one thread owns a pixel's sample chain)"); return LV_ERR_UNSUPPORTED; }
+  if (o->batch != 32 && o->batch != 64 && o->batch != 128) { set_error("batch must be 32, 64 or 128"); return LV_ERR_INVALID_ARG; }
+  if (o->tile == 32 && o->batch == 128) {
+    set_error("batch 128 with 32x32 tiles needs more than 227 KB of shared memory per block");
+    return LV_ERR_UNSUPPORTED;
+  }
   if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) { set_error("t_stop must be in [0, 1)"); return LV_ERR_INVALID_ARG; }
   if (o->persistent_sms < 0) { set_error("persistent_sms must be >= 0"); return LV_ERR_INVALID_ARG; }
   int64_t tiles = 0, pixels = 0;
@@ -1263,40 +1282,40 @@ static int limit_to_sms(int pb, int sm_limit, int dev) {
   return per_sm * sm_limit;
 }
 
-template <int TS, bool SEG, bool PERSIST>
+template <int TS, bool SEG, bool PERSIST, int CH>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          float t_stop, const lv_fwd_out* out, int sm_limit) {
-  const size_t smem = FWD_SLICE * (TS * TS / 32);
+  const size_t smem = fwd_slice(CH) * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
   const int dev = current_device();
   once_per_device(done, [&] {
-    cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
+    cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_fwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   });
-  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST>, TS * TS, smem);
+  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) grid = (unsigned)(tiles < pb ? tiles : pb);  // work[0] was cleared at the start of the forward
-  k_fwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
+  k_fwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
                                                        out->n_samples, w.tau, out->wmax_packed, w.work, n_items);
 }
 
-template <int TS, bool SEG, bool PERSIST>
+template <int TS, bool SEG, bool PERSIST, int CH>
 static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd,
                          int sm_limit) {
-  const size_t smem = BWD_SLICE * (TS * TS / 32);
+  const size_t smem = bwd_slice(CH) * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
   const int dev = current_device();
   once_per_device(done, [&] {
-    cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
+    cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_bwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   });
-  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST>, TS * TS, smem);
+  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
@@ -1304,40 +1323,56 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
     zero_async(s, w.work + 1, sizeof(unsigned int));
     grid = (unsigned)(tiles < pb ? tiles : pb);
   }
-  k_bwd<TS, SEG, PERSIST><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
+  k_bwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
                                                        w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
                                                        n_items);
 }
 
-// tile size, density model (midpoint, or the exact-segment variant) and scheduling
-// (one block per tile, or persistent warps on a work counter) from the options
+// tile size, batch, density model (midpoint, or the exact-segment variant) and scheduling
+// (one block per tile, or persistent warps on a work counter) from the options; a batch of
+// 128 needs more than the 227 KB of shared memory of a block for 32 x 32 tiles (refused by
+// check_common)
 static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* out) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
-#define LV_FWD(TS)                                                                   \
-  if (seg && per) launch_fwd_t<TS, true, true>(tiles, s, vs, w, sv, o->t_stop, out, o->persistent_sms);  \
-  else if (seg) launch_fwd_t<TS, true, false>(tiles, s, vs, w, sv, o->t_stop, out, 0);                   \
-  else if (per) launch_fwd_t<TS, false, true>(tiles, s, vs, w, sv, o->t_stop, out, o->persistent_sms);  \
-  else launch_fwd_t<TS, false, false>(tiles, s, vs, w, sv, o->t_stop, out, 0)
-  if (o->tile == 8) { LV_FWD(8); }
-  else if (o->tile == 16) { LV_FWD(16); }
-  else { LV_FWD(32); }
+  const int sml = per ? o->persistent_sms : 0;
+#define LV_FWD_CH(TS, CH)                                                                       \
+  if (seg && per) launch_fwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);   \
+  else if (seg) launch_fwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0);      \
+  else if (per) launch_fwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);    \
+  else launch_fwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0)
+#define LV_FWD(TS)                                   \
+  if (o->batch == 64) { LV_FWD_CH(TS, 64); }         \
+  else if (o->batch == 128) { LV_FWD_CH(TS, 128); }  \
+  else { LV_FWD_CH(TS, 32); }
+  if (o->tile == 8) { LV_FWD(8) }
+  else if (o->tile == 16) { LV_FWD(16) }
+  else if (o->batch == 64) { LV_FWD_CH(32, 64); }
+  else { LV_FWD_CH(32, 32); }
 #undef LV_FWD
+#undef LV_FWD_CH
 }
 
 static void launch_bwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT,
                        float* dd) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
-#define LV_BWD(TS)                                                                         \
-  if (seg && per) launch_bwd_t<TS, true, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, o->persistent_sms);  \
-  else if (seg) launch_bwd_t<TS, true, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0);                   \
-  else if (per) launch_bwd_t<TS, false, true>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, o->persistent_sms);  \
-  else launch_bwd_t<TS, false, false>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0)
-  if (o->tile == 8) { LV_BWD(8); }
-  else if (o->tile == 16) { LV_BWD(16); }
-  else { LV_BWD(32); }
+  const int sml = per ? o->persistent_sms : 0;
+#define LV_BWD_CH(TS, CH)                                                                             \
+  if (seg && per) launch_bwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml);    \
+  else if (seg) launch_bwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0);       \
+  else if (per) launch_bwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml);     \
+  else launch_bwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0)
+#define LV_BWD(TS)                                   \
+  if (o->batch == 64) { LV_BWD_CH(TS, 64); }         \
+  else if (o->batch == 128) { LV_BWD_CH(TS, 128); }  \
+  else { LV_BWD_CH(TS, 32); }
+  if (o->tile == 8) { LV_BWD(8) }
+  else if (o->tile == 16) { LV_BWD(16) }
+  else if (o->batch == 64) { LV_BWD_CH(32, 64); }
+  else { LV_BWD_CH(32, 32); }
 #undef LV_BWD
+#undef LV_BWD_CH
 }
 
 }  // namespace lv

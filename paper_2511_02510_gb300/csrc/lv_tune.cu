@@ -1,6 +1,7 @@
 // lv_tune.cu -- autotuner of the composite schedule (host code).  Every
 // candidate (tile edge 8 / 16 / 32, one block per tile or persistent warps
-// on a work counter) runs the caller's forward + backward on the caller's
+// on a work counter, batch of 32 / 64 / 128 list entries staged per warp
+// round) runs the caller's forward + backward on the caller's
 // scene and views; the fastest one, timed with CUDA events on the caller's
 // stream, is returned and optionally remembered in a text cache file.
 #include <stdio.h>
@@ -15,6 +16,8 @@ namespace {
 
 constexpr int N_TILES = 3;
 constexpr int TILES[N_TILES] = {8, 16, 32};
+constexpr int N_BATCH = 3;
+constexpr int BATCHES[N_BATCH] = {32, 64, 128};
 
 struct TuneWs {
   float* rgb;
@@ -81,17 +84,19 @@ std::string cache_key(int64_t n, const lv_camera* cams, int n_views, const lv_ra
   return key;
 }
 
-bool cache_lookup(const char* path, const std::string& key, int* tile, int* persistent) {
+bool cache_lookup(const char* path, const std::string& key, int* tile, int* persistent, int* batch) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char line[2048];
   bool hit = false;
   while (fgets(line, sizeof(line), f)) {
     char k[1800];
-    int t = 0, p = 0;
-    if (sscanf(line, "%1799s %d %d", k, &t, &p) == 3 && key == k && (t == 8 || t == 16 || t == 32)) {
+    int t = 0, p = 0, b = 32;
+    const int got = sscanf(line, "%1799s %d %d %d", k, &t, &p, &b);
+    if (got >= 3 && key == k && (t == 8 || t == 16 || t == 32) && (b == 32 || b == 64 || (b == 128 && t < 32))) {
       *tile = t;
       *persistent = p ? 1 : 0;
+      *batch = got == 4 ? b : 32;
       hit = true;  // the last matching line wins
     }
   }
@@ -99,10 +104,10 @@ bool cache_lookup(const char* path, const std::string& key, int* tile, int* pers
   return hit;
 }
 
-void cache_store(const char* path, const std::string& key, int tile, int persistent) {
+void cache_store(const char* path, const std::string& key, int tile, int persistent, int batch) {
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d\n", key.c_str(), tile, persistent);
+  fprintf(f, "%s %d %d %d\n", key.c_str(), tile, persistent, batch);
   fclose(f);
 }
 
@@ -126,12 +131,13 @@ extern "C" lv_status lv_autotune(const lv_voxels* vox, const lv_camera* cams, in
     return LV_ERR_INVALID_ARG;
   }
   if (ms_out)
-    for (int i = 0; i < 2 * N_TILES; ++i) ms_out[i] = -1.f;
+    for (int i = 0; i < 2 * N_TILES * N_BATCH; ++i) ms_out[i] = -1.f;
   const std::string key = cache_key(vox->n, cams, n_views, base);
-  int tile = 0, persistent = 0;
-  if (cache_path && cache_lookup(cache_path, key, &tile, &persistent)) {
+  int tile = 0, persistent = 0, batch = 32;
+  if (cache_path && cache_lookup(cache_path, key, &tile, &persistent, &batch)) {
     *best = *base;
     best->tile = tile;
+    best->batch = batch;
     best->flags = (base->flags & ~(uint32_t)LV_FLAG_PERSISTENT) | (persistent ? LV_FLAG_PERSISTENT : 0u);
     return LV_OK;
   }
@@ -155,10 +161,13 @@ extern "C" lv_status lv_autotune(const lv_voxels* vox, const lv_camera* cams, in
   if (cuda_check(cudaEventCreate(&e1), "lv_autotune") != LV_OK) { cudaEventDestroy(e0); return LV_ERR_CUDA; }
   float best_ms = -1.f;
   lv_status result = LV_OK;
-  for (int t = 0; t < N_TILES && result == LV_OK; ++t) {
-    for (int p = 0; p < 2; ++p) {
+  for (int c = 0; c < 2 * N_TILES * N_BATCH && result == LV_OK; ++c) {
+    const int t = c / (2 * N_BATCH), p = (c / N_BATCH) % 2, b = c % N_BATCH;
+    if (TILES[t] == 32 && BATCHES[b] == 128) continue;  // more shared memory than a block has
+    {
       lv_raster_opts o = *base;
       o.tile = TILES[t];
+      o.batch = BATCHES[b];
       o.flags = (base->flags & ~(uint32_t)(LV_FLAG_PERSISTENT | LV_FLAG_SYNC_CHECK)) | (p ? LV_FLAG_PERSISTENT : 0u);
       auto step = [&]() -> lv_status {
         lv_status e = lv_rasterize_forward(vox, cams, n_views, &o, &out, w.fwd, w.fwd_bytes, pair_capacity,
@@ -180,11 +189,12 @@ extern "C" lv_status lv_autotune(const lv_voxels* vox, const lv_camera* cams, in
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= (float)reps;
-      if (ms_out) ms_out[2 * t + p] = ms;
+      if (ms_out) ms_out[c] = ms;
       if (best_ms < 0.f || ms < best_ms) {
         best_ms = ms;
         tile = TILES[t];
         persistent = p;
+        batch = BATCHES[b];
       }
     }
   }
@@ -197,7 +207,8 @@ extern "C" lv_status lv_autotune(const lv_voxels* vox, const lv_camera* cams, in
   }
   *best = *base;
   best->tile = tile;
+  best->batch = batch;
   best->flags = (base->flags & ~(uint32_t)LV_FLAG_PERSISTENT) | (persistent ? LV_FLAG_PERSISTENT : 0u);
-  if (cache_path) cache_store(cache_path, key, tile, persistent);
+  if (cache_path) cache_store(cache_path, key, tile, persistent, batch);
   return LV_OK;
 }

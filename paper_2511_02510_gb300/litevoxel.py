@@ -45,7 +45,7 @@ class lv_camera(C.Structure):
 
 
 class lv_raster_opts(C.Structure):
-    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("threads_per_px", C.c_int32), ("t_stop", C.c_float),
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("t_stop", C.c_float),
                 ("flags", C.c_uint32), ("persistent_sms", C.c_int32), ("pixel_id_base", C.c_int64)]
 
 
@@ -227,10 +227,10 @@ def make_cameras(cams) -> C.Array:
     return arr
 
 
-def make_opts(tile=16, batch=256, t_stop=1e-4, sync_check=False, exact_segment=False,
+def make_opts(tile=16, batch=32, t_stop=1e-4, sync_check=False, exact_segment=False,
               persistent=False, persistent_sms=0, pixel_id_base=0) -> lv_raster_opts:
     o = lv_raster_opts()
-    o.tile, o.batch, o.threads_per_px, o.t_stop = tile, batch, 1, t_stop
+    o.tile, o.batch, o.t_stop = tile, batch, t_stop
     o.persistent_sms = int(persistent_sms)
     o.pixel_id_base = int(pixel_id_base)
     o.flags = ((LV_FLAG_SYNC_CHECK if sync_check else 0) | (LV_FLAG_EXACT_SEGMENT if exact_segment else 0) |
@@ -442,9 +442,10 @@ def lv_autotune_workspace_size(n, cams_arr, n_views, base, pair_capacity) -> int
 
 
 def lv_autotune(vox, cams_arr, n_views, base, pair_capacity, reps, workspace, cache_path=None):
-    """Time every (tile, schedule) candidate; returns (best lv_raster_opts, [6] ms per candidate, -1 = skipped)."""
+    """Time every (tile, schedule, batch) candidate; returns (best lv_raster_opts, [18] ms per candidate at
+    6 tile + 3 schedule + batch, -1 = skipped)."""
     best = lv_raster_opts()
-    ms = (C.c_float * 6)()
+    ms = (C.c_float * 18)()
     path = cache_path.encode() if cache_path else None
     _check(load().lv_autotune(C.byref(vox), cams_arr, n_views, C.byref(base), int(pair_capacity), int(reps),
                               C.byref(best), ms, path, _ptr(workspace), workspace.numel() * workspace.element_size(),

@@ -27,7 +27,7 @@ class RasterContext:
     reports LV_ERR_CAPACITY (checked by :meth:`check`).
     """
 
-    def __init__(self, cams, n_voxels, tile=16, batch=256, t_stop=1e-4, pair_capacity=None, device="cuda",
+    def __init__(self, cams, n_voxels, tile=16, batch=32, t_stop=1e-4, pair_capacity=None, device="cuda",
                  exact_segment=False, persistent=False, persistent_sms=0):
         self.cams = list(cams)
         self.n_views = len(self.cams)

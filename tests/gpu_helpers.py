@@ -18,7 +18,7 @@ def dequantized(sc, density_dtype=torch.float32, sh_dtype=torch.float32):
     return out
 
 
-def gpu_forward(sc, cams, tile=16, batch=256, t_stop=1e-4, density_dtype=torch.float32, sh_dtype=torch.float32,
+def gpu_forward(sc, cams, tile=16, batch=32, t_stop=1e-4, density_dtype=torch.float32, sh_dtype=torch.float32,
                 sh_degree=3, pair_capacity=None, exact_segment=False):
     scene = to_scene(sc, density_dtype, sh_dtype, sh_degree)
     ctx = RasterContext(cams, scene.n, tile=tile, batch=batch, t_stop=t_stop, pair_capacity=pair_capacity,

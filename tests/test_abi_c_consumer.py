@@ -43,7 +43,7 @@ PROGRAM = textwrap.dedent(r"""
       cam.w2c[0] = cam.w2c[5] = cam.w2c[10] = 1.f; cam.z_near = 0.05f;
       lv_raster_opts o;
       memset(&o, 0, sizeof(o));
-      o.tile = 16; o.batch = 256; o.threads_per_px = 1; o.t_stop = 1e-4f;
+      o.tile = 16; o.batch = 32; o.t_stop = 1e-4f;
       size_t ws = lv_forward_workspace_size(2000000, &cam, 1, &o, 10000000);
       CHECK(ws > (size_t)10000000 * 16);
       CHECK(lv_forward_workspace_size(2000000, &cam, 0, &o, 0) == 0);
@@ -59,7 +59,7 @@ PROGRAM = textwrap.dedent(r"""
       CHECK(lv_rasterize_forward(NULL, &cam, 1, &o, &out, NULL, 0, 0, NULL, NULL) == LV_ERR_INVALID_ARG);
       CHECK(strlen(lv_last_error()) > 0);
       CHECK(lv_rasterize_forward(&v, &cam, 1, &o, &out, NULL, 0, 0, NULL, NULL) == LV_ERR_INVALID_ARG);
-      o.threads_per_px = 2;
+      o.tile = 32; o.batch = 128;
       CHECK(lv_rasterize_forward(&v, &cam, 1, &o, &out, NULL, 0, 0, NULL, NULL) == LV_ERR_UNSUPPORTED);
       CHECK(lv_reset_stats(-1, NULL, NULL, NULL, NULL, NULL) == LV_ERR_INVALID_ARG);
       CHECK(lv_check_status(NULL, NULL) == LV_ERR_INVALID_ARG);

@@ -1,4 +1,4 @@
-"""The C-ABI autotuner (lv_autotune): every (tile, schedule) candidate is
+"""The C-ABI autotuner (lv_autotune): every (tile, schedule, batch) candidate is
 timed on the caller's scene, the fastest is returned, the choice is cached,
 candidates that overflow the pair capacity are skipped, and the chosen
 options render the same image as the defaults."""
@@ -31,18 +31,22 @@ def test_autotune_picks_the_fastest_and_caches(tmp_path):
                      device="cuda")
     path = str(tmp_path / "tune.txt")
     best, ms = L.lv_autotune(vox, cams_arr, len(cams), base, cap, 3, ws, path)
-    assert best.tile in (8, 16, 32)
-    assert all(m > 0 for m in ms)
-    idx = [8, 16, 32].index(best.tile) * 2 + (1 if best.flags & L.LV_FLAG_PERSISTENT else 0)
-    assert ms[idx] == min(ms)
+    assert best.tile in (8, 16, 32) and best.batch in (32, 64, 128)
+    # every candidate timed except batch 128 with tile 32 (refused)
+    refused = [6 * 2 + 3 * p + 2 for p in (0, 1)]
+    assert all(m > 0 for i, m in enumerate(ms) if i not in refused) and all(ms[i] == -1 for i in refused)
+    idx = [8, 16, 32].index(best.tile) * 6 + (3 if best.flags & L.LV_FLAG_PERSISTENT else 0) + \
+        [32, 64, 128].index(best.batch)
+    assert ms[idx] == min(m for m in ms if m > 0)
     # cache hit: same choice, nothing timed
     best2, ms2 = L.lv_autotune(vox, cams_arr, len(cams), base, cap, 3, ws, path)
-    assert best2.tile == best.tile and best2.flags == best.flags and all(m == -1 for m in ms2)
+    assert best2.tile == best.tile and best2.flags == best.flags and best2.batch == best.batch
+    assert all(m == -1 for m in ms2)
     assert open(path).read().count("\n") == 1
     # the chosen options give the image of the default ones
     imgs = []
     for o in (base, best):
-        ctx = RasterContext(cams, vox.n, tile=o.tile, persistent=bool(o.flags & L.LV_FLAG_PERSISTENT))
+        ctx = RasterContext(cams, vox.n, tile=o.tile, batch=o.batch, persistent=bool(o.flags & L.LV_FLAG_PERSISTENT))
         ctx.fit_capacity(vox)
         ctx.forward(vox)
         ctx.check()

@@ -16,11 +16,11 @@ from test_gpu_render import GRAD_TOL, _grad_err, cam_far, cam_near, compare_imag
 pytestmark = pytest.mark.gpu
 
 
-def run(sc, cams, tile, persistent, g=None, exact_segment=False, persistent_sms=0):
+def run(sc, cams, tile, persistent, g=None, exact_segment=False, persistent_sms=0, batch=32):
     from gpu_helpers import to_scene
     scene = to_scene(sc)
     ctx = RasterContext(cams, scene.n, tile=tile, persistent=persistent, exact_segment=exact_segment,
-                        persistent_sms=persistent_sms)
+                        persistent_sms=persistent_sms, batch=batch)
     vox = scene.voxels()
     ctx.fit_capacity(vox)
     ctx.reset_stats()
@@ -71,3 +71,21 @@ def test_persistent_on_fewer_sms(sms):
     for k in ("rgb", "T", "depth", "n_contrib", "wmax_packed"):
         np.testing.assert_array_equal(a[k], b[k])
     assert _grad_err(b["dd"], a["dd"]) < GRAD_TOL and _grad_err(b["ds"], a["ds"]) < GRAD_TOL
+
+
+@pytest.mark.parametrize("tile,persistent,seg", [(8, False, False), (16, True, False), (32, True, False),
+                                                 (16, False, True)])
+def test_batches_give_the_same_bits(ora, tile, persistent, seg):
+    """The batch (list entries a warp stages per round) only groups the loads: every batch gives the
+    bits of batch 32, and the oracle's image."""
+    sc = synth.scene_tiny()
+    cams = [cam_near(100, 70, az=80.0), cam_far(64, 48, az=200.0)]
+    P = sum(c["width"] * c["height"] for c in cams)
+    g = np.random.default_rng(tile).normal(size=(P, 3)).astype(np.float32)
+    a, _ = run(sc, cams, tile, persistent, g, seg, batch=32)
+    for batch in (64, 128) if tile < 32 else (64,):
+        b, ctx = run(sc, cams, tile, persistent, g, seg, batch=batch)
+        for k in ("rgb", "T", "depth", "n_contrib", "wmax_packed"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert _grad_err(b["dd"], a["dd"]) < 1e-5 and _grad_err(b["ds"], a["ds"]) < 1e-5
+    compare_images(ora.render(sc, cams, segment=seg), ctx)

@@ -154,7 +154,7 @@ def test_pairs_and_stats_bit_exact(ora, tiny):
     np.testing.assert_array_equal(np_(ctx.delta_min).view(np.uint32), ref["delta_min"].view(np.uint32))
 
 
-@pytest.mark.parametrize("tile,batch", [(8, 64), (16, 128), (32, 256), (32, 64)])
+@pytest.mark.parametrize("tile,batch", [(8, 64), (16, 128), (32, 32), (32, 64), (8, 128), (16, 32)])
 def test_forward_tiles_batches_ragged(ora, tiny, tile, batch):
     cams = [cam_near(100, 70, az=80.0), cam_near(37, 53, az=200.0, el=40.0)]
     scene, ctx, vox = gpu_forward(tiny, cams, tile=tile, batch=batch)
@@ -287,7 +287,7 @@ def test_capacity_overflow_reported(tiny):
     scene = to_scene(tiny)
     ctx = RasterContext(cams, scene.n, pair_capacity=100)           # far too small
     vox = scene.voxels()
-    opts = L.make_opts(16, 256, 1e-4, sync_check=True)
+    opts = L.make_opts(16, 32, 1e-4, sync_check=True)
     with pytest.raises(L.LvError) as ei:
         L.lv_rasterize_forward(vox, ctx.cams_arr, 1, opts, ctx.fwd_struct(), ctx.workspace, 100, None)
     assert ei.value.status == L.LV_ERR_CAPACITY
@@ -367,8 +367,8 @@ def test_full_size_360_whole_view(ora, full360, tile, persistent):
 
 
 def test_max_views_and_limits(ora, tiny):
-    # LV_MAX_VIEWS small views in one launch match the oracle; one more is refused, as is
-    # threads_per_px != 1
+    # LV_MAX_VIEWS small views in one launch match the oracle; one more is refused, as is a batch of
+    # 128 with 32x32 tiles (more shared memory than a block has)
     cams = [synth.orbit_camera(24 + (i % 5) * 4, 18 + (i % 3) * 6, 60.0, 1.6, 360.0 * i / 64, 20.0 + (i % 7),
                                target=(0.5, 0.4, 0.5)) for i in range(L.LV_MAX_VIEWS)]
     scene, ctx, vox = gpu_forward(tiny, cams)
@@ -380,8 +380,7 @@ def test_max_views_and_limits(ora, tiny):
     np.testing.assert_array_equal(vox_ids, ref["vals"])
     too_many = L.make_cameras(cams + [cams[0]])
     assert L.lv_forward_workspace_size(scene.n, too_many, L.LV_MAX_VIEWS + 1, ctx.opts, 1024) == 0
-    bad = L.make_opts()
-    bad.threads_per_px = 2
+    bad = L.make_opts(32, 128)
     with pytest.raises(L.LvError) as ei:
         L.lv_rasterize_forward(vox, ctx.cams_arr, ctx.n_views, bad, ctx.fwd_struct(), ctx.workspace,
                                ctx.pair_capacity)

@@ -81,6 +81,9 @@ FORWARD_CASES = {
     "misaligned vertex index": dict(vox=voxels(vidx=ADDR + 4)),
     "tile 12": dict(opts=opts(tile=12)),
     "batch 100": dict(opts=opts(batch=100)),
+    "batch 256": dict(opts=opts(batch=256)),
+    "negative pixel id base": dict(opts=opts(pixel_id_base=-1)),
+    "pixel ids past 2^32 - 1": dict(opts=opts(pixel_id_base=(1 << 32) - 1000)),
     "t_stop 1": dict(opts=opts(t_stop=1.0)),
     "t_stop NaN": dict(opts=opts(t_stop=math.nan)),
     "negative persistent_sms": dict(opts=opts(persistent_sms=-1)),
@@ -109,7 +112,7 @@ def test_forward_rejects(lib, case):
 
 
 def test_forward_unsupported_and_workspace(lib):
-    expect(lib, L.LV_ERR_UNSUPPORTED, lib.lv_rasterize_forward, *forward_args(opts=opts(threads_per_px=2)))
+    expect(lib, L.LV_ERR_UNSUPPORTED, lib.lv_rasterize_forward, *forward_args(opts=opts(tile=32, batch=128)))
     expect(lib, L.LV_ERR_WORKSPACE, lib.lv_rasterize_forward, *forward_args(ws_bytes=TINY_WS))
 
 
@@ -337,25 +340,32 @@ def test_vertex_calls_reject(lib):
 
 # ------------------------------------------------------------------ autotuner cache
 def test_autotune_reads_its_cache_without_running(lib, tmp_path):
-    """A cache hit returns the stored tile and schedule before any launch; the last matching line wins and
-    lines with another key, a tile that is not 8/16/32 or too few fields are skipped.  Without a device the
-    key's GPU name is "gpu"."""
+    """A cache hit returns the stored tile, schedule and batch before any launch; the last matching line wins
+    and lines with another key, a tile that is not 8/16/32, a batch that is not 32/64/128 (or 128 with tile
+    32) or too few fields are skipped; a line without a batch means 32.  Without a device the key's GPU name
+    is "gpu"."""
     cams = cams_of((128, 96), (64, 48))
     key = "gpu|100|128x96|64x48|f0"
     path = tmp_path / "tune.txt"
-    path.write_text(f"{key} 8 0\n"
-                    f"{key.replace('|100|', '|101|')} 32 1\n"
-                    f"{key} 16 1\n"
-                    f"{key} 12 0\n"
+    path.write_text(f"{key} 8 0 64\n"
+                    f"{key.replace('|100|', '|101|')} 32 1 32\n"
+                    f"{key} 16 1 128\n"
+                    f"{key} 12 0 32\n"
+                    f"{key} 32 1 128\n"
+                    f"{key} 8 0 256\n"
                     f"{key} 32\n")
     best = L.lv_raster_opts()
-    ms = (C.c_float * 6)()
+    ms = (C.c_float * 18)()
     v = voxels(n=100)
     expect_ok = lib.lv_autotune(C.byref(v), cams, 2, C.byref(opts()), 1000, 3, C.byref(best), ms,
                                 str(path).encode(), None, 0, None)
     assert expect_ok == L.LV_OK, L.last_error()
-    assert best.tile == 16 and best.flags & L.LV_FLAG_PERSISTENT
-    assert list(ms) == [-1.0] * 6
+    assert best.tile == 16 and best.flags & L.LV_FLAG_PERSISTENT and best.batch == 128
+    assert list(ms) == [-1.0] * 18
+    path.write_text(f"{key} 32 0\n")                 # the cache format without a batch
+    assert lib.lv_autotune(C.byref(v), cams, 2, C.byref(opts()), 1000, 3, C.byref(best), ms, str(path).encode(),
+                           None, 0, None) == L.LV_OK
+    assert best.tile == 32 and best.batch == 32 and not best.flags & L.LV_FLAG_PERSISTENT
     # flags other than the schedule are part of the key: an exact-segment request misses the cache and, with no
     # workspace, is refused before anything runs
     expect(lib, L.LV_ERR_INVALID_ARG, lib.lv_autotune, C.byref(v), cams, 2,
