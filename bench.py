@@ -134,13 +134,14 @@ class Workload:
             self.tile, self.persistent, self.batch = schedule
         elif tuned:
             self.tile, self.persistent, self.batch, self.tune_ms = tuned_schedule(self.scene, self.cams)
-        # the persistent backward composite leaves 48 SMs to the pruning and selection kernels
-        # that the three-stream step runs beside it (a full-GPU resident grid starves them; a
-        # sweep of the backward's SMs gave 1.332 ms per step on 152, 1.303 on 120, 1.301 on
-        # 112, 1.298 on 96); the forward composite runs alone and keeps every SM
+        # the persistent backward composite leaves 80 SMs to the pruning and selection kernels
+        # that the three-stream step runs beside it: that chain, not the backward, ends last
+        # before the topology change (graph-replay marks: 0.960 ms per step with the backward on
+        # 104 SMs, 0.951 on 88, 0.943 on 72, 0.959 on 56, 0.992 on all 152); the forward
+        # composite runs alone and keeps every SM
         self.persistent_sms = 0
         if self.persistent:
-            self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 48)
+            self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 80)
         self.rctx = RasterContext(self.cams, n, tile=self.tile, batch=self.batch, persistent=self.persistent)
         self.bwd_opts = L.make_opts(self.tile, self.batch, persistent=self.persistent,
                                     persistent_sms=self.persistent_sms)
@@ -218,11 +219,19 @@ class Workload:
         torch = self.torch
         idx = torch.nonzero((self.selected != 0) | (self.pmask != 0)).flatten()
         self.restore_idx = idx
-        self.restore_saved = [p.index_select(0, idx) for p in pristine]
+        self.restore_saved = [self._wide(p).index_select(0, idx) for p in pristine]
         for arr, p in zip(self._state_arrays(), pristine):
             arr.copy_(p)
         self.ema.copy_(self.ema0)
         self.state.copy_(self.state0)
+
+    def _wide(self, t):
+        """Rows of 16-byte multiples seen as 16-byte elements, so an index copy moves a row in a few
+        elements rather than one element per float."""
+        row = t[0].numel() * t.element_size() if t.dim() > 1 else t.element_size()
+        if t.dim() > 1 and row % 16 == 0 and t.is_contiguous():
+            return t.view(self.torch.complex128)
+        return t
 
     def restore(self):
         """Put back the rows the step's in-place topology change overwrote and the pruning state, so
@@ -230,7 +239,7 @@ class Workload:
         if self.restore_idx is None:
             return
         for arr, saved in zip(self._state_arrays(), self.restore_saved):
-            arr.index_copy_(0, self.restore_idx, saved)
+            self._wide(arr).index_copy_(0, self.restore_idx, saved)
         self.ema.copy_(self.ema0)
         self.state.copy_(self.state0)
 

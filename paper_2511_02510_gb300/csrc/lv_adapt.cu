@@ -735,10 +735,18 @@ __global__ void k_cp_flags(int64_t n, const uint8_t* __restrict__ keep, uint32_t
   if (i < n) surv[i] = keep[i] ? 1u : 0u;
 }
 
+// The split parents in id order (list), and the pruned rows -- neither survivor
+// nor parent -- in id order (holes, for the in-place topology change): the
+// number of pruned rows before i is i - (survivors before i) - (parents before i).
+// It runs with the selection (on the caller's side stream in a training step)
+// so that the in-place write does not read these arrays again.
 __global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uint32_t* __restrict__ rank,
-                          uint32_t* __restrict__ list) {
+                          const uint32_t* __restrict__ surv, const unsigned long long* __restrict__ surv_pos,
+                          uint32_t* __restrict__ list, uint32_t* __restrict__ holes) {
   const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i < n && sel[i]) list[rank[i]] = (uint32_t)i;
+  if (i >= n) return;
+  if (sel[i]) list[rank[i]] = (uint32_t)i;
+  else if (!surv[i]) holes[i - (int64_t)surv_pos[i] - (int64_t)rank[i]] = (uint32_t)i;
 }
 
 // A warp writes 32 consecutive children (output rows o0 .. o0 + 31): one lane
@@ -831,13 +839,34 @@ __global__ void k_sd_write(int64_t n, int64_t max_children, const uint32_t* __re
 // index >= n' then move into the empty rows below n', both in index order.
 // Rows the step does not change are neither read nor written.
 
-// the pruned rows (neither survivor nor split parent) in index order: the
-// number of pruned rows before i is i - (survivors before i) - (parents before i)
-__global__ void k_ip_holes(int64_t n, const uint32_t* __restrict__ surv, const uint32_t* __restrict__ sel,
-                           const unsigned long long* __restrict__ surv_pos, const uint32_t* __restrict__ sel_rank,
-                           uint32_t* __restrict__ holes) {
-  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i < n && !surv[i] && !sel[i]) holes[i - (int64_t)surv_pos[i] - (int64_t)sel_rank[i]] = (uint32_t)i;
+// a voxel's 8 corners: 16-byte stores where the row is 16-byte aligned (it is in
+// a 16-byte aligned array), element stores otherwise
+template <typename DT>
+__device__ __forceinline__ void store_corners(DT* row, const float* v);
+template <>
+__device__ __forceinline__ void store_corners<float>(float* row, const float* v) {
+  if (((uintptr_t)row & 15) == 0) {
+    ((float4*)row)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    ((float4*)row)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) row[j] = v[j];
+  }
+}
+template <>
+__device__ __forceinline__ void store_corners<__half>(__half* row, const float* v) {
+  __half2 h[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h[q] = __halves2half2(__float2half_rn(v[2 * q]), __float2half_rn(v[2 * q + 1]));
+  if (((uintptr_t)row & 15) == 0) {
+    uint4 u;
+    u.x = *(const uint32_t*)&h[0]; u.y = *(const uint32_t*)&h[1];
+    u.z = *(const uint32_t*)&h[2]; u.w = *(const uint32_t*)&h[3];
+    *(uint4*)row = u;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) row[j] = __float2half_rn(v[j]);
+  }
 }
 
 // row of child c of the parent of rank r (at row `parent`)
@@ -902,6 +931,7 @@ __global__ void __launch_bounds__(TPB) k_ip_children(int64_t n, const uint32_t* 
     geom[dst] = make_float4(__fadd_rn(g.x, (c & 1) ? hc : -hc), __fadd_rn(g.y, (c & 2) ? hc : -hc),
                             __fadd_rn(g.z, (c & 4) ? hc : -hc), hc);
     level[dst] = (uint8_t)(lvl + 1);
+    float cd[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float qx = (float)(((c >> 0) & 1) + ((j >> 0) & 1)) * 0.5f;
@@ -910,8 +940,9 @@ __global__ void __launch_bounds__(TPB) k_ip_children(int64_t n, const uint32_t* 
       const float x0 = lerp_rn(d[0], d[1], qx), x1 = lerp_rn(d[2], d[3], qx);
       const float x2 = lerp_rn(d[4], d[5], qx), x3 = lerp_rn(d[6], d[7], qx);
       const float y0 = lerp_rn(x0, x1, qy), y1 = lerp_rn(x2, x3, qy);
-      dens[8 * dst + j] = from_f32<DT>(lerp_rn(y0, y1, qz));
+      cd[j] = lerp_rn(y0, y1, qz);
     }
+    store_corners<DT>(dens + 8 * dst, cd);
   }
   uint4* sdst = (uint4*)sh;
   for (int w = lane; w < nrows * WPR; w += 32) {
@@ -1180,7 +1211,7 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel);
   scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
   k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
-  k_sd_list<<<blocks_for(n), TPB, 0, s>>>(n, w.sel, w.sel_rank, w.sel_list);
+  k_sd_list<<<blocks_for(n), TPB, 0, s>>>(n, w.sel, w.sel_rank, w.surv, w.surv_pos, w.sel_list, w.zkey);
   count_launch(13);
   return cuda_check(cudaGetLastError(), "lv_subdivide_select");
 }
@@ -1249,8 +1280,7 @@ extern "C" lv_status lv_subdivide_apply_inplace(const lv_voxels* vox, int64_t ca
   as.n = n_aux;
   for (int a = 0; a < n_aux; ++a) as.a[a] = aux[a];
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t* holes = w.zkey;  // free once the selection is done
-  k_ip_holes<<<blocks_for(n), TPB, 0, s>>>(n, w.surv, w.sel, w.surv_pos, w.sel_rank, holes);
+  const uint32_t* holes = w.zkey;  // the pruned rows in id order, from the selection (k_sd_list)
   const int64_t max_children = 8 * (int64_t)(((unsigned long long)p->top_ppm * (unsigned long long)n) / 1000000ull);
   const unsigned grid = (unsigned)((max_children + TPB - 1) / TPB);  // one warp per 32 children
   const unsigned tail_grid = (unsigned)std::min<int64_t>((n + TPB / 32 - 1) / (TPB / 32), 1216);
@@ -1267,7 +1297,7 @@ extern "C" lv_status lv_subdivide_apply_inplace(const lv_voxels* vox, int64_t ca
   else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_IP(float, __nv_bfloat16);
   else LV_IP(__half, __nv_bfloat16);
 #undef LV_IP
-  count_launch(grid > 0 ? 3 : 2);
+  count_launch(grid > 0 ? 2 : 1);
   return cuda_check(cudaGetLastError(), "lv_subdivide_apply_inplace");
 }
 

@@ -576,15 +576,12 @@ constexpr int SEL_ITEMS = 4;        // items per thread per iteration, loads iss
 constexpr int SEL_WIDE_MAX_Q = 4;   // up to this many queries use 11-bit digits
 
 // One warp per query: find the digit holding the k-th item (warp scan over
-// RADIX / 32 digits per lane), extend the prefix, clear the query's histogram row.
+// RADIX / 32 digits per lane) and extend the prefix; returns the updated query.
 template <int RADIX>
-__global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
+__device__ __forceinline__ SelectQuery warp_pick(const uint32_t* __restrict__ row, SelectQuery s, int shift,
+                                                 int lane) {
   constexpr int PER = RADIX / 32;  // 8 or 64 digits per lane, contiguous
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= nq) return;  // warp-uniform
-  SelectQuery s = q[j];
-  uint4* hrow = (uint4*)(hist + (size_t)j * RADIX + lane * PER);
+  const uint4* hrow = (const uint4*)(row + lane * PER);
   uint32_t lsum = 0;
 #pragma unroll 4
   for (int i = 0; i < PER / 4; ++i) {
@@ -606,7 +603,7 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
     // scans them and finds the digit by ballot
     const int L = __ffs(ball) - 1;
     const uint32_t base = __shfl_sync(FULL, excl, L);
-    const uint32_t* h = hist + (size_t)j * RADIX + L * PER;
+    const uint32_t* h = row + L * PER;
     constexpr int EPL = PER / 32 > 0 ? PER / 32 : 1;  // digits per lane: 2 (RADIX 2048) or 1 (256: lanes 0-7)
     uint32_t c[EPL];
     uint32_t my = 0;
@@ -635,19 +632,29 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
     digit = __shfl_sync(FULL, digit, L2);
     newk = __shfl_sync(FULL, newk, L2);
   }
-#pragma unroll 4
-  for (int i = 0; i < PER / 4; ++i) hrow[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (lane == 0) {
-    if (s.k == 0 || digit < 0) {
-      s.k = 0;
-      s.result = 0xffffffffu;
-    } else {
-      s.k = newk;
-      s.prefix |= (uint32_t)digit << shift;
-      if (shift == 0) s.result = s.prefix;
-    }
-    q[j] = s;
+  if (s.k == 0 || digit < 0) {
+    s.k = 0;
+    s.result = 0xffffffffu;
+  } else {
+    s.k = newk;
+    s.prefix |= (uint32_t)digit << shift;
+    if (shift == 0) s.result = s.prefix;
   }
+  return s;
+}
+
+// The last digit's pick: one warp per query, q_in -> q (the two may be the same), and the
+// histogram row cleared.
+template <int RADIX>
+__global__ void k_sel_pick(const SelectQuery* q_in, SelectQuery* q, int nq, int shift, uint32_t* hist) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= nq) return;  // warp-uniform
+  const SelectQuery s = warp_pick<RADIX>(hist + (size_t)j * RADIX, q_in[j], shift, lane);
+  uint4* hrow = (uint4*)(hist + (size_t)j * RADIX + lane * (RADIX / 32));
+#pragma unroll 4
+  for (int i = 0; i < RADIX / 128; ++i) hrow[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (lane == 0) q[j] = s;
 }
 
 // Histogram of the current digit (bits [shift, shift + width)) of every item
@@ -656,24 +663,45 @@ __global__ void k_sel_pick(SelectQuery* q, int nq, int shift, uint32_t* hist) {
 // slower: the match costs more than the serialised atomics it saves).  When
 // every query is in group 0 (at most two queries) a lean per-item path runs;
 // otherwise queries of a group are contiguous, at most two per group.
+// With hist_prev, every block first takes the previous digit's pick step from
+// q_in and hist_prev itself, one warp per query (one launch less per digit than
+// a separate pick kernel), and block 0 stores the picked queries in q_out.  clear (nullable)
+// is zeroed by the grid for a later pass: nothing reads or writes it here.
 template <int RADIX>
 __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const uint32_t* keys, const uint16_t* grp, int64_t n,
                                                          const SelectQuery* q, int nq, int shift, int width,
-                                                         uint32_t* hist) {
+                                                         uint32_t* hist, const uint32_t* hist_prev, int prev_shift,
+                                                         SelectQuery* q_out, uint32_t* clear, int clear_words) {
   extern __shared__ uint4 sh4[];  // nq * RADIX counters
   uint32_t* sh = (uint32_t*)sh4;
   __shared__ SelectQuery sq[SELECT_MAX_QUERIES];
   __shared__ uint8_t qfirst[SELECT_MAX_QUERIES], qcount[SELECT_MAX_QUERIES];
-  // nothing to do when every query is finished (k == 0): skip the whole pass
+  if (clear)
+    for (int64_t i = blockIdx.x * (int64_t)SEL_THREADS + threadIdx.x; i < clear_words;
+         i += (int64_t)gridDim.x * SEL_THREADS)
+      clear[i] = 0u;
+  for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
+  __syncthreads();
+  if (hist_prev) {
+    // one warp per query, the block's warps in parallel
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x >> 5; j < nq; j += SEL_THREADS / 32) {
+      const SelectQuery r = warp_pick<RADIX>(hist_prev + (size_t)j * RADIX, sq[j], prev_shift, lane);
+      if (lane == 0) sq[j] = r;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < nq; i += SEL_THREADS) q_out[i] = sq[i];
+  }
+  // nothing to do when every query is finished (k == 0): skip the rest of the pass
   int active = 0, all0 = nq <= SEL_MAX_Q_PER_GROUP;
   for (int j = 0; j < nq; ++j) {
-    active |= q[j].k != 0;
-    all0 &= q[j].group == 0;
+    active |= sq[j].k != 0;
+    all0 &= sq[j].group == 0;
   }
   if (!active) return;  // uniform over the grid
   for (int i = threadIdx.x; i < nq * RADIX / 4; i += SEL_THREADS) sh4[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = threadIdx.x; i < SELECT_MAX_QUERIES; i += SEL_THREADS) qcount[i] = 0;
-  for (int i = threadIdx.x; i < nq; i += SEL_THREADS) sq[i] = q[i];
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int j = nq - 1; j >= 0; --j) {
@@ -752,7 +780,7 @@ __global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist, int hist_word
 
 template <int RADIX>
 void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int nq,
-                   uint32_t* hist, int key_bits, int width, cudaStream_t s) {
+                   uint32_t* hist, SelectQuery* qs, int key_bits, int width, cudaStream_t s) {
   // enough blocks to keep many loads in flight; fewer when every block must
   // clear and flush a large histogram (wide digits or many queries)
   const int64_t want = (n + SEL_THREADS * SEL_ITEMS - 1) / (SEL_THREADS * SEL_ITEMS);
@@ -765,16 +793,25 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
     cudaFuncSetAttribute(k_sel_hist<RADIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(uint32_t) * 256 * SELECT_MAX_QUERIES));
   });
+  // three histogram buffers: pass p writes H[p % 3], reads H[(p - 1) % 3] for its pick step and
+  // clears H[(p + 1) % 3] for pass p + 1 (k_sel_init cleared H[0]); the queries after p picks
+  // are A[p]: A[0] = d_queries, then the two scratch copies in turn; the last pick writes d_queries
+  const int words = nq * RADIX;
+  uint32_t* H[3] = {hist, hist + words, hist + 2 * words};
+  auto A = [&](int p) { return p == 0 ? d_queries : qs + ((p - 1) % 2) * nq; };
   // digits from the top: the first one takes the remainder bits, the rest `width` each
   const int npass = (key_bits + width - 1) / width;
-  int shift = key_bits;
+  int shift = key_bits, prev_shift = 0;
   for (int p = 0; p < npass; ++p) {
     const int wbits = p == 0 ? key_bits - width * (npass - 1) : width;
     shift -= wbits;
-    k_sel_hist<RADIX><<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, d_queries, nq, shift, wbits, hist);
-    k_sel_pick<RADIX><<<(nq + 7) / 8, 256, 0, s>>>(d_queries, nq, shift, hist);
+    k_sel_hist<RADIX><<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, A(p > 0 ? p - 1 : 0), nq, shift, wbits,
+                                                        H[p % 3], p > 0 ? H[(p - 1) % 3] : nullptr, prev_shift,
+                                                        p > 0 ? A(p) : nullptr, H[(p + 1) % 3], words);
+    prev_shift = shift;
   }
-  count_launch(2 * npass);
+  k_sel_pick<RADIX><<<(nq + 7) / 8, 256, 0, s>>>(A(npass - 1), d_queries, nq, 0, H[(npass - 1) % 3]);
+  count_launch(npass + 1);
 }
 
 }  // namespace
@@ -782,14 +819,17 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
 size_t select_tmp_bytes(int n_queries) {
   const size_t narrow = 256 * (size_t)n_queries;
   const size_t wide = 2048 * (size_t)(n_queries < SEL_WIDE_MAX_Q ? n_queries : SEL_WIDE_MAX_Q);
-  return sizeof(uint32_t) * (narrow > wide ? narrow : wide) + 256;
+  // three histogram buffers, then two copies of the queries
+  return 3 * sizeof(uint32_t) * (narrow > wide ? narrow : wide) + 2 * sizeof(SelectQuery) * (size_t)n_queries + 512;
 }
 
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s) {
-  uint32_t* hist = (uint32_t*)tmp;
   const bool wide = n_queries <= SEL_WIDE_MAX_Q;
-  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist, (wide ? 2048 : 256) * n_queries);
+  const int words = (wide ? 2048 : 256) * n_queries;
+  uint32_t* hist = (uint32_t*)tmp;
+  SelectQuery* qs = (SelectQuery*)(hist + 3 * (size_t)words);
+  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist, words);
   count_launch(1);
   // ranking by index needs only the bits of n - 1 (at least one)
   int key_bits = 32;
@@ -797,8 +837,8 @@ void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuer
     key_bits = 1;
     while (key_bits < 32 && ((int64_t)1 << key_bits) < n) ++key_bits;
   }
-  if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, key_bits, 11, s);
-  else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, key_bits, 8, s);
+  if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 11, s);
+  else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 8, s);
 }
 
 }  // namespace lv
