@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
                                                          const unsigned long long* d_count, int64_t cap, int pass,
                                                          const uint32_t* __restrict__ ghist, uint32_t* ticket,
                                                          unsigned long long* look, unsigned long long* look_next,
-                                                         int32_t* status, unsigned spin_limit) {
+                                                         int32_t* status, unsigned spin_limit,
+                                                         uint32_t* __restrict__ key_ranges) {
   constexpr int OS_THREADS = Os<K>::THREADS, OS_WARPS = Os<K>::WARPS, OS_TILE = Os<K>::TILE;
   __shared__ uint32_t s_wh[OS_WARPS][RADIX + 1];  // warp digit counts -> warp prefixes (bin RADIX: padding items)
   __shared__ uint32_t s_start[RADIX];             // tile-local start of each digit
@@ -462,6 +463,12 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
       const int64_t g = s_off[(uint32_t)(kk >> shift) & (RADIX - 1)] + q;
       kout[g] = kk;
       vout[g] = s_v[q];
+      if (key_ranges) {
+        // items of one digit are consecutive here and in the output, so a key's first and last
+        // item in this tile bound its positions; the extremes over all tiles are its range
+        if (q == 0 || s_k[q - 1] != kk) atomicMin(&key_ranges[2 * (uint64_t)kk], (uint32_t)g);
+        if (q == m - 1 || s_k[q + 1] != kk) atomicMax(&key_ranges[2 * (uint64_t)kk + 1], (uint32_t)(g + 1));
+      }
     }
   }
 }
@@ -474,7 +481,7 @@ int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 template <typename K>
 static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, K* k1, uint32_t* v1, void* tmp,
                         const unsigned long long* d_count, int64_t cap, int end_bit, int32_t* status,
-                        cudaStream_t s) {
+                        cudaStream_t s, uint32_t* key_ranges) {
   int passes = sort_passes(end_bit);
   if (passes > (int)sizeof(K)) passes = (int)sizeof(K);
   if (passes == 0 || cap <= 0) return 0;
@@ -492,7 +499,7 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
     const int dst = (p + 1) & 1;
     k_os_pass<K><<<(unsigned)tiles, Os<K>::THREADS, 0, s>>>(ks, vs, kb[dst], vb[dst], d_count, cap, p, st.ghist,
                                                        st.ticket, st.look[p & 1], st.look[(p + 1) & 1], status,
-                                                       OS_SPIN_LIMIT);
+                                                       OS_SPIN_LIMIT, p == passes - 1 ? key_ranges : nullptr);
   }
   count_launch(1 + passes);
   return passes & 1;
@@ -500,14 +507,14 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
 
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     int32_t* status, cudaStream_t s) {
-  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s);
+                     int32_t* status, cudaStream_t s, uint32_t* key_ranges) {
+  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, key_ranges);
 }
 
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
                      int32_t* status, cudaStream_t s) {
-  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s);
+  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, nullptr);
 }
 
 // ---- bounded-wait check: one pass over two tiles where only the second tile's
@@ -559,7 +566,7 @@ extern "C" lv_status lv_debug_sort_timeout(int32_t spin_limit, void* workspace, 
   k_dbg_setup<<<1, 32, 0, s>>>(w.count, st.ticket);
   k_os_pass<uint32_t><<<1, Os<uint32_t>::THREADS, 0, s>>>(w.k0, nullptr, w.k1, w.v1, w.count, DBG_ITEMS, 0, st.ghist,
                                                           st.ticket, st.look[0], st.look[1], d_status,
-                                                          (unsigned)spin_limit);
+                                                          (unsigned)spin_limit, nullptr);
   count_launch(2);
   return cuda_check(cudaGetLastError(), "lv_debug_sort_timeout");
 }

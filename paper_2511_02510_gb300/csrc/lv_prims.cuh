@@ -27,12 +27,15 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
 // returned, so a caller that may sort no bits passes kin == k0 and vin == v0.
 // tmp: sort_tmp_bytes(cap) bytes, 256-byte aligned, no initial contents.
 // A bounded inter-block wait that gives up reports LV_ERR_TIMEOUT in *status
-// (nullable).
+// (nullable).  key_ranges (32-bit keys, nullable): the last pass also writes
+// the [first, end) positions of every key k it places into key_ranges[2k] by
+// atomicMin and key_ranges[2k + 1] by atomicMax, so the caller sets them to
+// (0xffffffff, 0) beforehand and keys absent from the list keep those values.
 size_t sort_tmp_bytes(int64_t cap);
 int sort_passes(int end_bit);
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     int32_t* status, cudaStream_t s);
+                     int32_t* status, cudaStream_t s, uint32_t* key_ranges = nullptr);
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
                      int32_t* status, cudaStream_t s);

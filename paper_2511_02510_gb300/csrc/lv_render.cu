@@ -5,18 +5,20 @@
 //   k_bin       per (voxel, view): FP32 cull / near-plane clipping / corner
 //               projection / tile rect / depth key with a fixed operation
 //               order; depth statistics.
-//   scan2       visible-slot ids and the total pair count.
-//   k_emit      per visible (voxel, view): 64-byte render record (centre
-//               relative to the camera, half-size, 8 corner densities, SH
-//               colour, 1 / (2 h)), its pixel box, voxel id, tile rectangle
-//               and depth key.
-//   radix sort  the slots by depth key (32 bits, stable: ties by voxel id).
-//   k_emit_pairs  (tile, slot) pairs written in that depth order after a scan
-//               of the tile counts; a stable radix sort on the tile bits then
-//               leaves every tile's list front to back.  This sorts the
-//               depth keys once per slot rather than once per pair, and
-//               moves 8-byte pairs instead of 12-byte (tile << 32 | key) ones.
-//   k_ranges    [start, end) of every tile in the sorted list.
+//   scan2       visible-slot ids and each item's first pair (item order),
+//               with the slot and pair totals.
+//   k_emit      per (voxel, view): the item's (tile, slot) pairs, written in
+//               item order by whole warps; per visible item the 64-byte render
+//               record (centre relative to the camera, half-size, 8 corner
+//               densities, SH colour, 1 / (2 h)), its pixel box, voxel id and
+//               depth key.
+//   radix sort  the pairs by tile id (stable: each tile's list stays in
+//               voxel-id order); its last pass also notes every tile's range.
+//   k_tile_sort_warp, k_tile_sort, k_tile_merge  per tile: its slots sorted by depth key in
+//               shared memory (stable), so every tile's list ends front to back
+//               with ties by voxel id.  The depth keys are sorted per tile,
+//               where they fit in shared memory, instead of by global passes
+//               over all slots.
 //   k_fwd       per tile, one thread per pixel: each warp stages the records
 //               that meet its pixel strip through shared memory and marches
 //               front to back (Eq. 2-4); w_max (Eq. 5) is reduced over the
@@ -81,28 +83,30 @@ static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64
 // ------------------------------------------------------------------ workspace
 // items are (view, voxel) pairs in view-major order: item = view * n + voxel
 struct FwdWs {
-  unsigned long long* counters;  // [0] pairs, [1] slots, [2..3] totals of the depth-order scan
+  unsigned long long* counters;  // [0] pairs, [1] slots
   uint32_t* cnt;                 // [items] tiles covered
   uint32_t* vis;                 // [items] 1 if cnt > 0
   uint2* rect;                   // [items] (tx0 | tx1 << 16, ty0 | ty1 << 16)
   uint2* pbox;                   // [items] conservative pixel box (x0 | x1 << 16, y0 | y1 << 16), [x0, x1)
   uint32_t* dkey;                // [items] order key of z_centre
   uint32_t* slot;                // [items] render slot of a visible item
+  unsigned long long* poff;      // [items] first pair of the item (pairs in item order)
   uint2* rec_bb;                 // [slots] pixel box of the render record
   uint32_t* slot_vox;            // [slots] voxel id of the render record
-  uint4* s_tiles;                // [slots] (rect.x, rect.y, view, tile count)
   uint32_t* s_dkey;              // [slots] order key
-  uint32_t *sk0, *sv0, *sk1, *sv1;  // [slots] depth sort of the slots (keys, slot ids)
-  uint32_t* scnt;                // [slots] tile counts in depth order
-  uint4* st_sorted;              // [slots] s_tiles in depth order
-  unsigned int* work;            // [2] work-item counters of the persistent composites
-  unsigned long long* poff;      // [slots] first pair of each slot in depth order
+  unsigned int* work;            // [8] work-item counters: [0..1] the persistent composites, [2] count
+                                 // of the long tiles' chunks, [3] the merge's work counter, [4..5] count
+                                 // of the medium tiles and k_tile_sort's work counter, [6] count of the
+                                 // long tiles
+  uint2* chunks;                 // [pair capacity / TS_CHUNK + tiles] (tile, chunk) of the long tiles
+  uint32_t* mid_tiles;           // [tiles] tiles of medium-length lists
+  uint32_t* long_tiles;          // [tiles] tiles of long lists
   void* scan_tmp;
   float4* rec;                   // [slots][4]
   float4* d_rgb;                 // [slots] colour gradient (xyz) scratch of the backward; w = clamp mask
   uint32_t* ranges;              // [tiles][2]
   float* tau;                    // [pixels] final optical depth
-  void* sort_tmp;                // radix sort scratch (both sorts, one after the other)
+  void* sort_tmp;                // scratch of the sort by tile
   int32_t* status;               // fallback status word
   uint32_t *k0, *v0, *k1, *v1;   // [pair capacity] (tile, slot) pairs, sorted by tile
   size_t bytes;
@@ -114,30 +118,26 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   int64_t items = n * nv;
   w.counters = c.take<unsigned long long>(8);
   w.status = c.take<int32_t>(4);
-  w.work = c.take<unsigned int>(2);
+  w.work = c.take<unsigned int>(8);
   w.cnt = c.take<uint32_t>(items);
   w.vis = c.take<uint32_t>(items);
   w.rect = c.take<uint2>(items);
   w.pbox = c.take<uint2>(items);
   w.dkey = c.take<uint32_t>(items);
   w.slot = c.take<uint32_t>(items);
+  w.poff = c.take<unsigned long long>(items);
   w.rec_bb = c.take<uint2>(items);
   w.slot_vox = c.take<uint32_t>(items);
-  w.s_tiles = c.take<uint4>(items);
   w.s_dkey = c.take<uint32_t>(items);
-  w.sk0 = c.take<uint32_t>(items);
-  w.sv0 = c.take<uint32_t>(items);
-  w.sk1 = c.take<uint32_t>(items);
-  w.sv1 = c.take<uint32_t>(items);
-  w.scnt = c.take<uint32_t>(items);
-  w.st_sorted = c.take<uint4>(items);
-  w.poff = c.take<unsigned long long>(items);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.rec = c.take<float4>(items * 4);
   w.d_rgb = c.take<float4>(items);
   w.ranges = c.take<uint32_t>(tiles * 2);
+  w.chunks = c.take<uint2>(pair_cap / 4096 + tiles);
+  w.mid_tiles = c.take<uint32_t>(tiles);
+  w.long_tiles = c.take<uint32_t>(tiles);
   w.tau = c.take<float>(pixels);
-  w.sort_tmp = c.take<char>(sort_tmp_bytes(items > pair_cap ? items : pair_cap));
+  w.sort_tmp = c.take<char>(sort_tmp_bytes(pair_cap));
   w.k0 = c.take<uint32_t>(pair_cap);
   w.v0 = c.take<uint32_t>(pair_cap);
   w.k1 = c.take<uint32_t>(pair_cap);
@@ -158,6 +158,7 @@ static const uint32_t* sorted_pair_slots(const FwdWs& w, int64_t tiles) {
 static const uint32_t* sorted_pair_tiles(const FwdWs& w, int64_t tiles) {
   return (sort_passes(tile_bits(tiles)) & 1) ? w.k1 : w.k0;
 }
+static void launch_tile_sort(const FwdWs& w, int64_t tiles, int64_t pair_cap, cudaStream_t s);
 
 
 // ------------------------------------------------------------------ binning (FP32, fixed op order)
@@ -373,10 +374,15 @@ __device__ __forceinline__ void unit_dir(float rx, float ry, float rz, float* d)
 }
 
 // ------------------------------------------------------------------ emit
-// One thread per visible (voxel, view) item: the render record of its slot
-// (camera-relative centre and h | 8 corner densities | clamped SH colour and
-// 1/(2h)), the slot's tile rectangle and order key for the depth sort, and the
-// colour-gradient scratch (cleared; w = clamp mask).
+// One thread per (voxel, view) item.  First the warp writes the (tile, slot)
+// pairs of its 32 items: items are consecutive, so their pairs form one
+// contiguous range in item order (view-major, voxel id within a view), which
+// the warp fills 32 pairs per step, each lane finding the item of its pair by
+// a 5-step search over the lanes' first pairs.  More pairs than capacity:
+// none are written and the status word says LV_ERR_CAPACITY.  Then each
+// visible item writes the render record of its slot (camera-relative centre
+// and h | 8 corner densities | clamped SH colour and 1/(2h)), the slot's order
+// key, and the colour-gradient scratch (cleared; w = clamp mask).
 template <typename DT, typename ST>
 __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, const DT* __restrict__ dens,
                                               const ST* __restrict__ sh, int sh_nb, int64_t n,
@@ -385,18 +391,67 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const uint2* __restrict__ pbox, uint2* __restrict__ rec_bb,
                                               uint32_t* __restrict__ slot_vox,
                                               const uint32_t* __restrict__ dkey,
-                                              const uint32_t* __restrict__ slot, float4* __restrict__ rec,
-                                              float4* __restrict__ d_rgb, uint4* __restrict__ s_tiles,
-                                              uint32_t* __restrict__ s_dkey, const uint32_t* __restrict__ vidx) {
+                                              const uint32_t* __restrict__ slot,
+                                              const unsigned long long* __restrict__ poff,
+                                              const unsigned long long* __restrict__ counters, int64_t pair_cap,
+                                              uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_slot,
+                                              int32_t* status, uint2* __restrict__ ranges, int64_t tiles,
+                                              float4* __restrict__ rec,
+                                              float4* __restrict__ d_rgb, uint32_t* __restrict__ s_dkey,
+                                              const uint32_t* __restrict__ vidx) {
   // Block b covers 256 consecutive voxels of view b % views, so the blocks of
   // all views of one voxel range run side by side: a voxel's SH row comes
   // from HBM once and from L2 for its other views.  Items are view-major
   // (i = view * n + voxel), so each block still writes consecutive slots.
   const int view = (int)(blockIdx.x % (unsigned)vs.n);
   const int64_t vox = (int64_t)(blockIdx.x / (unsigned)vs.n) * 256 + threadIdx.x;
-  if (vox >= n) return;
   const int64_t i = (int64_t)view * n + vox;
-  const uint32_t cn = cnt[i];  // nonzero exactly for the visible items
+  const bool in = vox < n;
+  // the sort by tile's last pass reduces every tile's [first, end) into ranges
+  for (int64_t x = blockIdx.x * 256ll + threadIdx.x; x < tiles; x += (int64_t)gridDim.x * 256)
+    ranges[x] = make_uint2(~0u, 0u);
+  const uint32_t cn = in ? cnt[i] : 0u;  // nonzero exactly for the visible items
+  const unsigned long long total = counters[0];
+  if (total > (unsigned long long)pair_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) report(status, LV_ERR_CAPACITY);
+  } else {
+    const int lane = threadIdx.x & 31;
+    const uint32_t inm = __ballot_sync(FULL, in);  // a prefix of the lanes
+    if (inm) {                                     // warp-uniform
+      const int last = 31 - __clz(inm);
+      // lanes past the last voxel start after every pair, so the search never picks them
+      const unsigned long long po = in ? poff[i] : ~0ull;
+      uint32_t rx = 0u, ry = 0u, sl = 0u;
+      if (cn) {
+        const uint2 rc = rect[i];
+        rx = rc.x;
+        ry = rc.y;
+        sl = slot[i];
+      }
+      const unsigned long long p_begin = __shfl_sync(FULL, po, 0);
+      const unsigned long long p_end = __shfl_sync(FULL, po + cn, last);
+      const DevView& c = vs.v[view];
+      const uint32_t toff = (uint32_t)c.tile_off, tiles_x = (uint32_t)c.tiles_x;
+      for (unsigned long long p0 = p_begin; p0 < p_end; p0 += 32) {  // warp-uniform
+        const unsigned long long e = p0 + lane;
+        int j = 0;  // the largest lane whose first pair is <= e (lane 0's is <= p0)
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const unsigned long long x = __shfl_sync(FULL, po, (j + step) & 31);
+          if (j + step < 32 && x <= e) j += step;
+        }
+        const unsigned long long pj = __shfl_sync(FULL, po, j);
+        const uint32_t jx = __shfl_sync(FULL, rx, j), jy = __shfl_sync(FULL, ry, j);
+        const uint32_t js = __shfl_sync(FULL, sl, j);
+        if (e < p_end) {
+          const uint32_t q = (uint32_t)(e - pj);
+          const uint32_t tx0 = jx & 0xffffu, wx = (jx >> 16) - tx0, ty0 = jy & 0xffffu;
+          pair_tile[e] = toff + (ty0 + q / wx) * tiles_x + tx0 + q % wx;
+          pair_slot[e] = js;
+        }
+      }
+    }
+  }
   if (!cn) return;
   const DevView& c = vs.v[view];
   const uint32_t s = slot[i];
@@ -430,119 +485,7 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
   d_rgb[s] = make_float4(0.f, 0.f, 0.f,
                          (float)((raw[0] > 0.f ? 1 : 0) | (raw[1] > 0.f ? 2 : 0) | (raw[2] > 0.f ? 4 : 0)));
   rec_bb[s] = pbox[i];
-  const uint2 rc = rect[i];
-  s_tiles[s] = make_uint4(rc.x, rc.y, (uint32_t)view, cn);
   s_dkey[s] = dkey[i];
-}
-
-// The slots' tile rectangles gathered into depth order, and their tile counts
-// (zero past the last slot), so the pair emission reads both sequentially.
-__global__ void k_slot_counts(const uint32_t* __restrict__ sorted_slot, const uint4* __restrict__ s_tiles,
-                              const unsigned long long* __restrict__ n_slots, int64_t items, uint32_t* scnt,
-                              uint4* __restrict__ st_sorted) {
-  const int64_t ns = (int64_t)*n_slots;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < items; r += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t c = 0u;
-    if (r < ns) {
-      const uint4 t = s_tiles[sorted_slot[r]];
-      st_sorted[r] = t;
-      c = t.w;
-    }
-    scnt[r] = c;
-  }
-}
-
-// The (tile, slot) pairs of every slot, written in depth order so that the
-// stable sort by tile keeps each tile's list front to back (ties in the order
-// key by slot, i.e. by voxel id).  Pairs are shared out evenly: each warp owns
-// a contiguous range of pair positions, finds the slot holding its first pair
-// by a 32-way search over the slot offsets, then writes 32 consecutive pairs
-// per step (coalesced).  A step's pairs lie in at most 32 consecutive slots
-// from the slot of its first pair, whose offsets, rectangles and ids sit in a
-// per-warp window in shared memory;
-// each lane finds its slot there by a 5-step binary search.  So neither a slot
-// with thousands of tiles nor a run of such slots serialises one lane or one
-// warp.  More pairs than capacity: nothing is written and the status word says
-// LV_ERR_CAPACITY.
-constexpr int EP_WARPS = 8;
-
-// largest s in [0, ns) with poff[s] <= p; poff strictly increases, poff[0] = 0
-__device__ __forceinline__ int64_t warp_find_slot(const unsigned long long* __restrict__ poff, int64_t ns,
-                                                  unsigned long long p, int lane) {
-  int64_t lo = 0, hi = ns;
-  while (hi - lo > 1) {  // warp-uniform
-    const int64_t step = (hi - lo + 31) / 32;
-    const int64_t probe = lo + lane * step;
-    const bool le = probe < hi && poff[probe] <= p;
-    const int k = __popc(__ballot_sync(FULL, le));  // lanes 0..k-1 (lane 0 always)
-    const int64_t nlo = lo + (int64_t)(k - 1) * step;
-    hi = min(hi, nlo + step);
-    lo = nlo;
-  }
-  return lo;
-}
-
-__global__ void __launch_bounds__(EP_WARPS * 32) k_emit_pairs(const __grid_constant__ ViewSet vs,
-                                                            const uint32_t* __restrict__ sorted_slot,
-                                                            const uint4* __restrict__ st_sorted,
-                                                            const unsigned long long* __restrict__ poff,
-                                                            const unsigned long long* __restrict__ counters,
-                                                            int64_t pair_cap, uint32_t* __restrict__ keys,
-                                                            uint32_t* __restrict__ vals, int32_t* status) {
-  __shared__ unsigned long long w_start[EP_WARPS][33];  // [32]: start of the slot after the window
-  __shared__ uint4 w_rect[EP_WARPS][32];  // (rect.x, rect.y, tile offset of the view, tiles_x)
-  __shared__ uint32_t w_slot[EP_WARPS][32];
-  const unsigned long long total = counters[0];
-  if (total > (unsigned long long)pair_cap) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) report(status, LV_ERR_CAPACITY);
-    return;
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ns = (int64_t)counters[1];
-  const unsigned long long nwarps = (unsigned long long)gridDim.x * EP_WARPS;
-  const unsigned long long gw = (unsigned long long)blockIdx.x * EP_WARPS + warp;
-  const unsigned long long chunk = ((total + nwarps - 1) / nwarps + 31) & ~31ull;
-  const unsigned long long p_begin = gw * chunk;
-  const unsigned long long p_end = min(total, p_begin + chunk);
-  if (p_begin >= p_end) return;  // warp-uniform
-  int64_t s0 = warp_find_slot(poff, ns, p_begin, lane);
-  int64_t loaded = -1;
-  for (unsigned long long p0 = p_begin; p0 < p_end; p0 += 32) {  // warp-uniform
-    if (s0 != loaded) {
-      __syncwarp();
-      const int64_t r = s0 + lane;
-      unsigned long long st = ~0ull;
-      if (r < ns) {
-        const uint32_t sl = sorted_slot[r];
-        const uint4 t = st_sorted[r];
-        const DevView& c = vs.v[t.z];
-        st = poff[r];
-        w_rect[warp][lane] = make_uint4(t.x, t.y, (uint32_t)c.tile_off, (uint32_t)c.tiles_x);
-        w_slot[warp][lane] = sl;
-      }
-      w_start[warp][lane] = st;
-      if (lane == 0) w_start[warp][32] = s0 + 32 < ns ? poff[s0 + 32] : ~0ull;
-      __syncwarp();
-      loaded = s0;
-    }
-    const unsigned long long e = p0 + lane;
-    int j = 0;  // largest j with w_start[j] <= e; w_start[0] <= p0 <= e
-#pragma unroll
-    for (int step = 16; step; step >>= 1)
-      if (w_start[warp][j + step] <= e) j += step;
-    if (e < p_end) {
-      const uint4 rc = w_rect[warp][j];
-      const uint32_t q = (uint32_t)(e - w_start[warp][j]);
-      const int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff;
-      const uint32_t wx = (uint32_t)(tx1 - tx0);
-      const int ty = ty0 + (int)(q / wx), tx = tx0 + (int)(q % wx);
-      keys[e] = rc.z + (uint32_t)(ty * (int)rc.w + tx);
-      vals[e] = w_slot[warp][j];
-    }
-    // the next window starts at the slot of pair p0 + 32: this step's last slot, or the one after it
-    const int j31 = __shfl_sync(FULL, j, 31);
-    s0 += j31 + (w_start[warp][j31 + 1] <= p0 + 32 ? 1 : 0);
-  }
 }
 
 // pairs usable by the later stages: all of them, or none after an overflow
@@ -551,14 +494,511 @@ __device__ __forceinline__ int64_t usable_pairs(const unsigned long long* d_coun
   return c <= (unsigned long long)cap ? (int64_t)c : 0;
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_count, int64_t cap,
-                         int64_t tiles, uint32_t* ranges) {
-  const int64_t n = usable_pairs(d_count, cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = keys[i];
-    if (t >= tiles) continue;
-    if (i == 0 || keys[i - 1] != t) ranges[2 * t] = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+// ------------------------------------------------------------------ per-tile depth order
+// After the stable sort by tile id, each tile's pairs are in item order (voxel
+// id within a view), and the sort's last pass has left every tile's range in
+// ranges (empty tiles: (0xffffffff, 0)).  Each tile's slots are then sorted by
+// order key: an LSD radix sort of 9-bit digits of the key minus the tile's
+// smallest key (a tile whose keys span less than 2^27 takes 3 passes).  Each
+// pass ranks stably (warp-private digit counts; the lanes holding a digit
+// found by bit ballots or by __match_any_sync), so equal keys keep item order,
+// and each tile's list ends front to back with ties by voxel id: the order one
+// stable sort of (tile, order key) pairs in voxel-id order gives.  The tiles
+// are shared out by list length:
+//   k_tile_sort_warp  one warp per tile: lists of up to TW_MAX pairs; it also
+//                     writes every tile's range in final form (empty: (0, 0))
+//                     and lists the longer tiles;
+//   k_tile_sort       persistent blocks of 512 threads: lists of up to
+//                     TS_CHUNK pairs in place, and longer lists cut into
+//                     chunks of TS_CHUNK pairs, each sorted into a scratch
+//                     copy of the pair arrays;
+//   k_tile_merge      persistent blocks over the long tiles: the sorted chunks
+//                     merged stably (equal keys of earlier chunks first).
+constexpr int TS_BITS = 9, TS_BINS = 1 << TS_BITS;
+constexpr int TS_THREADS = 512, TS_WARPS = TS_THREADS / 32, TS_ITEMS = 8, TS_CHUNK = TS_THREADS * TS_ITEMS;
+constexpr int TW_MAX = 256, TW_ITEMS = TW_MAX / 32, TW_WARPS = 16;
+static_assert(TS_THREADS == TS_BINS, "a thread for each digit");
+
+struct TileSortSmem {
+  uint32_t k[TS_CHUNK];                // keys
+  uint32_t v[TS_CHUNK];                // slots
+  uint16_t wc[TS_WARPS][TS_BINS + 2];  // warp digit counts -> warp prefixes (bin TS_BINS: padding)
+  uint32_t base[TS_BINS];              // start of each digit
+  uint32_t w[TS_WARPS];
+  uint32_t item, kmin, kmax;
+};
+struct WarpSortSmem {
+  uint32_t k[2][TW_MAX];     // keys, ping-pong
+  uint32_t v[2][TW_MAX];     // slots, ping-pong
+  uint16_t wc[TS_BINS + 2];  // digit counts (bin TS_BINS: padding)
+  uint16_t base[TS_BINS];    // start of each digit
+};
+struct TileSortWarpSmem {
+  WarpSortSmem w[TW_WARPS];
+};
+struct TileMergeSmem {
+  uint32_t k[2][2 * TS_CHUNK];  // two runs side by side, then the first merge's output
+  uint32_t v[2][2 * TS_CHUNK];
+  uint32_t item;
+};
+
+// exclusive scan of one value per thread over a block of WARPS warps
+template <int WARPS>
+__device__ __forceinline__ uint32_t ts_block_excl(uint32_t c, uint32_t* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) pre += w < warp ? s_w[w] : 0u;
+  return pre + x - c;
+}
+
+// Stable ranks of R rounds held warp-striped (round j of a warp holds item
+// 32 j + lane of the warp's items).  dr[j] holds the digit (TS_BINS for
+// padding) on entry; on exit also the item's rank among the warp's items of
+// its digit, from bit 10 up.  The warp's counts per digit accumulate in wc.
+template <int ITEMS>
+__device__ __forceinline__ void ts_rank(uint32_t (&dr)[ITEMS], int R, uint16_t* wc, bool use_match, int lane) {
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    if (j >= R) break;  // warp-uniform
+    const uint32_t d = dr[j];
+    uint32_t peers;
+    if (use_match) {  // warp-uniform
+      peers = __match_any_sync(FULL, d);
+    } else {
+      const uint32_t valid = __ballot_sync(FULL, d < TS_BINS);
+      peers = d < TS_BINS ? valid : ~valid;
+#pragma unroll
+      for (int b = 0; b < TS_BITS; ++b) {
+        const uint32_t m = __ballot_sync(FULL, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? m : ~m;
+      }
+    }
+    const bool leader = (peers & lt_mask) == 0;
+    use_match = __popc(__ballot_sync(FULL, leader)) <= 16;
+    const uint32_t cur = wc[d];
+    dr[j] = d | ((cur + __popc(peers & lt_mask)) << 10);
+    __syncwarp();
+    if (leader) wc[d] = (uint16_t)(cur + __popc(peers));
+    __syncwarp();
+  }
+}
+
+// smallest and largest of the per-thread values into *kmin / *kmax (set to ~0u / 0 before a barrier)
+__device__ __forceinline__ void ts_min_max(uint32_t mn, uint32_t mx, uint32_t* kmin, uint32_t* kmax) {
+  mn = __reduce_min_sync(FULL, mn);
+  mx = __reduce_max_sync(FULL, mx);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(kmin, mn);
+    atomicMax(kmax, mx);
+  }
+}
+
+// the tile's pair range: from the sort's last pass, or the whole list when no pass ran (one tile)
+__device__ __forceinline__ void ts_range(const uint32_t* ranges, uint32_t tile, int64_t n, bool ranges_ready,
+                                         uint32_t* lo, uint32_t* hi) {
+  *lo = *hi = 0u;
+  if (n <= 0) return;
+  if (!ranges_ready) {
+    *hi = (uint32_t)n;
+    return;
+  }
+  const uint2 r = reinterpret_cast<const uint2*>(ranges)[tile];
+  if (r.x < r.y) {
+    *lo = r.x;
+    *hi = r.y;
+  }
+}
+
+__device__ __forceinline__ int ts_passes(uint32_t span) {
+  return span ? (32 - __clz(span) + TS_BITS - 1) / TS_BITS : 0;
+}
+
+// ---- short lists: one warp each, TW_WARPS tiles per block
+__global__ void __launch_bounds__(TW_WARPS * 32, 2) k_tile_sort_warp(uint32_t* __restrict__ tvals,
+                                                                    const uint32_t* __restrict__ s_dkey,
+                                                                    const unsigned long long* __restrict__ d_count,
+                                                                    int64_t cap, bool ranges_ready, int64_t tiles,
+                                                                    uint32_t* __restrict__ ranges,
+                                                                    uint32_t* __restrict__ mid_tiles,
+                                                                    unsigned int* __restrict__ n_mid,
+                                                                    uint2* __restrict__ chunks,
+                                                                    unsigned int* __restrict__ n_chunks,
+                                                                    uint32_t* __restrict__ long_tiles,
+                                                                    unsigned int* __restrict__ n_long) {
+  extern __shared__ __align__(16) unsigned char tw_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpSortSmem& W = reinterpret_cast<TileSortWarpSmem*>(tw_raw)->w[warp];
+  const int64_t tile64 = (int64_t)blockIdx.x * TW_WARPS + warp;
+  if (tile64 >= tiles) return;  // warp-uniform; no block-wide barrier below
+  const uint32_t tile = (uint32_t)tile64;
+  uint32_t lo = 0, hi = 0;
+  if (lane == 0) {
+    ts_range(ranges, tile, usable_pairs(d_count, cap), ranges_ready, &lo, &hi);
+    reinterpret_cast<uint2*>(ranges)[tile] = make_uint2(lo, hi);
+    const uint32_t L = hi - lo;
+    if (L > (uint32_t)TS_CHUNK) {
+      const uint32_t nc = (L + TS_CHUNK - 1) / TS_CHUNK;
+      const uint32_t at = atomicAdd(n_chunks, nc);
+      for (uint32_t c = 0; c < nc; ++c) chunks[at + c] = make_uint2(tile, c);
+      long_tiles[atomicAdd(n_long, 1u)] = tile;
+    } else if (L > (uint32_t)TW_MAX) {
+      mid_tiles[atomicAdd(n_mid, 1u)] = tile;
+    }
+  }
+  lo = __shfl_sync(FULL, lo, 0);
+  const int L = (int)(__shfl_sync(FULL, hi, 0) - lo);
+  if (L < 2 || L > TW_MAX) return;  // warp-uniform
+  const int R = (L + 31) / 32;
+  uint32_t mn = ~0u, mx = 0u;
+  {
+    uint32_t kk[TW_ITEMS], vv[TW_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TW_ITEMS; ++j) {
+      if (j >= R) break;
+      vv[j] = j * 32 + lane < L ? tvals[lo + j * 32 + lane] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < TW_ITEMS; ++j) {
+      if (j >= R) break;
+      kk[j] = j * 32 + lane < L ? s_dkey[vv[j]] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < TW_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = j * 32 + lane;
+      if (q < L) {
+        W.k[0][q] = kk[j];
+        W.v[0][q] = vv[j];
+        mn = min(mn, kk[j]);
+        mx = max(mx, kk[j]);
+      }
+    }
+  }
+  const uint32_t kmin = __reduce_min_sync(FULL, mn);
+  const int npass = ts_passes(__reduce_max_sync(FULL, mx) - kmin);
+  if (npass == 0) return;  // warp-uniform: all keys equal, item order is the order
+  __syncwarp();
+  int cur = 0;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int shift = TS_BITS * pass;
+    uint32_t dr[TW_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TW_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = j * 32 + lane;
+      dr[j] = q < L ? ((W.k[cur][q] - kmin) >> shift) & (TS_BINS - 1) : (uint32_t)TS_BINS;
+    }
+    uint32_t* wcw = reinterpret_cast<uint32_t*>(W.wc);
+    for (int x = lane; x < (TS_BINS + 2) / 2; x += 32) wcw[x] = 0u;
+    __syncwarp();
+    ts_rank<TW_ITEMS>(dr, R, W.wc, pass > 0, lane);
+    __syncwarp();
+    // digit starts: lane l takes digits 16 l .. 16 l + 15 (8 words of two counts), the lanes'
+    // totals are scanned, then each lane writes its digits' starts
+    const uint32_t* wc2 = reinterpret_cast<const uint32_t*>(W.wc) + 8 * lane;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t c2 = wc2[i];
+      tot += (c2 & 0xffffu) + (c2 >> 16);
+    }
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    uint32_t run = x - tot;
+    uint32_t* base2 = reinterpret_cast<uint32_t*>(W.base) + 8 * lane;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t c2 = wc2[i];
+      const uint32_t b0 = run, b1 = run + (c2 & 0xffffu);
+      base2[i] = b0 | (b1 << 16);
+      run = b1 + (c2 >> 16);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < TW_ITEMS; ++j) {
+      if (j >= R) break;
+      const uint32_t d = dr[j] & 1023u;
+      if (d < TS_BINS) {
+        const int q = j * 32 + lane;
+        const uint32_t pos = W.base[d] + (dr[j] >> 10);
+        W.k[cur ^ 1][pos] = W.k[cur][q];
+        W.v[cur ^ 1][pos] = W.v[cur][q];
+      }
+    }
+    __syncwarp();
+    cur ^= 1;
+  }
+#pragma unroll
+  for (int j = 0; j < TW_ITEMS; ++j) {
+    if (j >= R) break;
+    const int q = j * 32 + lane;
+    if (q < L) tvals[lo + q] = W.v[cur][q];
+  }
+}
+
+// Sorts m <= TS_CHUNK slots src[0, m) by order key with the whole block; the
+// sorted slots go to out_v[0, m) (which may be src) and, when out_k is not
+// null, their keys to out_k[0, m).  Returns with the block in step.
+__device__ __forceinline__ void ts_sort_chunk(TileSortSmem& S, const uint32_t* src,
+                                              const uint32_t* __restrict__ s_dkey, int m, uint32_t* out_k,
+                                              uint32_t* out_v) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) {
+    S.kmin = ~0u;
+    S.kmax = 0u;
+  }
+  __syncthreads();
+  const int R = (m + TS_THREADS - 1) / TS_THREADS;  // items per thread, and rounds per warp
+  {
+    // every slot load, then every key load, in flight at once
+    uint32_t kk[TS_ITEMS], vv[TS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = t + j * TS_THREADS;
+      vv[j] = q < m ? src[q] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = t + j * TS_THREADS;
+      kk[j] = q < m ? s_dkey[vv[j]] : 0u;
+    }
+    uint32_t mn = ~0u, mx = 0u;
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = t + j * TS_THREADS;
+      if (q < m) {
+        S.k[q] = kk[j];
+        S.v[q] = vv[j];
+        mn = min(mn, kk[j]);
+        mx = max(mx, kk[j]);
+      }
+    }
+    ts_min_max(mn, mx, &S.kmin, &S.kmax);
+  }
+  __syncthreads();
+  const uint32_t kmin = S.kmin;
+  const int npass = ts_passes(S.kmax - kmin);
+  for (int pass = 0; pass < npass; ++pass) {
+    const int shift = TS_BITS * pass;
+    uint32_t kk[TS_ITEMS], vv[TS_ITEMS], dr[TS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (j >= R) break;
+      const int q = warp * 32 * R + j * 32 + lane;
+      const bool ok = q < m;
+      kk[j] = ok ? S.k[q] : 0u;
+      vv[j] = ok ? S.v[q] : 0u;
+      dr[j] = ok ? ((kk[j] - kmin) >> shift) & (TS_BINS - 1) : (uint32_t)TS_BINS;
+    }
+    {
+      uint32_t* p = reinterpret_cast<uint32_t*>(&S.wc[0][0]);
+      for (int x = t; x < TS_WARPS * (TS_BINS + 2) / 2; x += TS_THREADS) p[x] = 0u;
+    }
+    __syncthreads();
+    ts_rank<TS_ITEMS>(dr, R, S.wc[warp], pass > 0, lane);
+    __syncthreads();
+    uint32_t c = 0;  // digit t: warp counts -> warp prefixes
+#pragma unroll
+    for (int w = 0; w < TS_WARPS; ++w) {
+      const uint32_t x = S.wc[w][t];
+      S.wc[w][t] = (uint16_t)c;
+      c += x;
+    }
+    S.base[t] = ts_block_excl<TS_WARPS>(c, S.w);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (j >= R) break;
+      const uint32_t d = dr[j] & 1023u;
+      if (d < TS_BINS) {
+        const uint32_t pos = S.base[d] + S.wc[warp][d] + (dr[j] >> 10);
+        S.k[pos] = kk[j];
+        S.v[pos] = vv[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = t; q < m; q += TS_THREADS) {
+    out_v[q] = S.v[q];
+    if (out_k) out_k[q] = S.k[q];
+  }
+}
+
+// Persistent blocks over the medium tiles (sorted in place), then over the
+// chunks of the long tiles (sorted into the scratch arrays xk, xv at the
+// chunk's own positions).
+__global__ void __launch_bounds__(TS_THREADS, 2) k_tile_sort(uint32_t* __restrict__ tvals,
+                                                            uint32_t* __restrict__ xk, uint32_t* __restrict__ xv,
+                                                            const uint32_t* __restrict__ s_dkey,
+                                                            const uint32_t* __restrict__ ranges,
+                                                            const uint32_t* __restrict__ mid_tiles,
+                                                            const unsigned int* __restrict__ n_mid,
+                                                            const uint2* __restrict__ chunks,
+                                                            const unsigned int* __restrict__ n_chunks,
+                                                            unsigned int* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  TileSortSmem& S = *reinterpret_cast<TileSortSmem*>(ts_raw);
+  const unsigned int nm = *n_mid, total = nm + *n_chunks;
+  while (true) {
+    if (threadIdx.x == 0) S.item = atomicAdd(work, 1u);
+    __syncthreads();
+    const unsigned int item = S.item;
+    __syncthreads();  // everyone has read the item before it is overwritten
+    if (item >= total) return;  // block-uniform
+    uint32_t off, m;
+    const bool mid = item < nm;
+    if (mid) {
+      const uint2 r = reinterpret_cast<const uint2*>(ranges)[mid_tiles[item]];
+      off = r.x;
+      m = r.y - r.x;
+    } else {
+      const uint2 ch = chunks[item - nm];
+      const uint2 r = reinterpret_cast<const uint2*>(ranges)[ch.x];
+      off = r.x + ch.y * (uint32_t)TS_CHUNK;
+      m = min((uint32_t)TS_CHUNK, r.y - off);
+    }
+    ts_sort_chunk(S, tvals + off, s_dkey, (int)m, mid ? nullptr : xk + off, (mid ? tvals : xv) + off);
+    __syncthreads();
+  }
+}
+
+// number of entries of the ascending run[0, n) below k (or, with or_equal, not above k); n <= TS_CHUNK
+__device__ __forceinline__ uint32_t ts_count_below(const uint32_t* run, uint32_t n, uint32_t k, bool or_equal) {
+  uint32_t base = 0;
+#pragma unroll
+  for (uint32_t step = TS_CHUNK; step; step >>= 1) {
+    if (base + step <= n) {
+      const uint32_t x = run[base + step - 1];
+      if (or_equal ? x <= k : x < k) base += step;
+    }
+  }
+  return base;
+}
+
+// (dk, dv)[0, n) = (sk, sv)[0, n), n <= 2 * TS_CHUNK, with every load of a thread in flight at once
+__device__ __forceinline__ void ts_stage(uint32_t* dk, uint32_t* dv, const uint32_t* __restrict__ sk,
+                                         const uint32_t* __restrict__ sv, int n) {
+  constexpr int U = 2 * TS_CHUNK / TS_THREADS;
+  uint32_t k[U], v[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = threadIdx.x + j * TS_THREADS;
+    k[j] = q < n ? sk[q] : 0u;
+    v[j] = q < n ? sv[q] : 0u;
+  }
+  asm volatile("" ::: "memory");  // all loads before the first store
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = threadIdx.x + j * TS_THREADS;
+    if (q < n) {
+      dk[q] = k[j];
+      dv[q] = v[j];
+    }
+  }
+}
+
+// Block-wide stable merge of the ascending runs (ak, av)[0, na) and (bk, bv)[0, nb)
+// into (ok, ov)[0, na + nb) (ok may be null): equal keys take the first run's
+// entries first.  Each thread finds where its share of the output starts in
+// both runs by one binary search along the output's diagonal, then merges its
+// share sequentially.
+__device__ __forceinline__ void ts_merge2(const uint32_t* ak, const uint32_t* av, int na, const uint32_t* bk,
+                                          const uint32_t* bv, int nb, uint32_t* ok, uint32_t* ov) {
+  const int n = na + nb, per = (n + TS_THREADS - 1) / TS_THREADS;
+  const int i0 = min(n, (int)threadIdx.x * per), i1 = min(n, i0 + per);
+  int lo = max(0, i0 - nb), hi = min(i0, na);  // entries of the first run among the first i0 outputs
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (ak[mid] <= bk[i0 - mid - 1]) lo = mid + 1;
+    else hi = mid;
+  }
+  int ia = lo, ib = i0 - lo;
+  for (int i = i0; i < i1; ++i) {
+    const bool take_a = ia < na && (ib >= nb || ak[ia] <= bk[ib]);
+    const uint32_t k = take_a ? ak[ia] : bk[ib], v = take_a ? av[ia] : bv[ib];
+    if (ok) ok[i] = k;
+    ov[i] = v;
+    ia += take_a ? 1 : 0;
+    ib += take_a ? 0 : 1;
+  }
+}
+
+// Persistent blocks over the long tiles, whose chunks k_tile_sort has sorted
+// into the scratch arrays (xk, xv).  Two or three chunks are merged through
+// shared memory (the first two, then that with the third); a tile of more
+// chunks places each pair behind the pairs of earlier chunks with keys not
+// above its own and of later chunks with keys below it, found by binary
+// searches of those chunks.
+__global__ void __launch_bounds__(TS_THREADS) k_tile_merge(uint32_t* __restrict__ tvals,
+                                                          const uint32_t* __restrict__ xk,
+                                                          const uint32_t* __restrict__ xv,
+                                                          const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ long_tiles,
+                                                          const unsigned int* __restrict__ n_long,
+                                                          unsigned int* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char tm_raw[];
+  TileMergeSmem& S = *reinterpret_cast<TileMergeSmem*>(tm_raw);
+  const int t = threadIdx.x;
+  const unsigned int total = *n_long;
+  while (true) {
+    if (t == 0) S.item = atomicAdd(work, 1u);
+    __syncthreads();
+    const unsigned int item = S.item;
+    __syncthreads();
+    if (item >= total) return;  // block-uniform
+    const uint2 r = reinterpret_cast<const uint2*>(ranges)[long_tiles[item]];
+    const int L = (int)(r.y - r.x), nc = (L + TS_CHUNK - 1) / TS_CHUNK;
+    const uint32_t* ck = xk + r.x;
+    const uint32_t* cv = xv + r.x;
+    if (nc <= 3) {
+      // chunks 0 and 1 side by side in area 0
+      const int n01 = min(L, 2 * TS_CHUNK);
+      ts_stage(S.k[0], S.v[0], ck, cv, n01);
+      __syncthreads();
+      const int n1 = n01 - TS_CHUNK;
+      if (nc == 2) {
+        ts_merge2(S.k[0], S.v[0], TS_CHUNK, S.k[0] + TS_CHUNK, S.v[0] + TS_CHUNK, n1, nullptr, tvals + r.x);
+      } else {
+        ts_merge2(S.k[0], S.v[0], TS_CHUNK, S.k[0] + TS_CHUNK, S.v[0] + TS_CHUNK, n1, S.k[1], S.v[1]);
+        __syncthreads();  // area 0 is read: chunk 2 goes there
+        const int n2 = L - n01;
+        ts_stage(S.k[0], S.v[0], ck + n01, cv + n01, n2);
+        __syncthreads();
+        ts_merge2(S.k[1], S.v[1], n01, S.k[0], S.v[0], n2, nullptr, tvals + r.x);
+      }
+    } else {
+      for (int c = 0; c < nc; ++c) {
+        const int own = c * TS_CHUNK, m = min(TS_CHUNK, L - own);
+        for (int q = t; q < m; q += TS_THREADS) {
+          const uint32_t k = ck[own + q], v = cv[own + q];
+          uint32_t pos = (uint32_t)q;
+          for (int o = 0; o < nc; ++o) {
+            if (o == c) continue;
+            const int off = o * TS_CHUNK;
+            pos += ts_count_below(ck + off, (uint32_t)min(TS_CHUNK, L - off), k, o < c);
+          }
+          tvals[r.x + pos] = v;
+        }
+      }
+    }
+    __syncthreads();  // shared memory is read before the next tile's loads
   }
 }
 
@@ -1332,6 +1772,43 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
 // (one block per tile, or persistent warps on a work counter) from the options; a batch of
 // 128 needs more than the 227 KB of shared memory of a block for 32 x 32 tiles (refused by
 // check_common)
+// The tile-sorted pairs are in (k0, v0) after an even number of digit passes,
+// else in (k1, v1); the other pair of arrays is scratch.  One warp per tile
+// first (short lists, ranges, the lists of longer tiles), then persistent
+// blocks over the medium tiles and the long tiles' chunks, then the merge.
+static void launch_tile_sort(const FwdWs& w, int64_t tiles, int64_t pair_cap, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr_done{0};
+  static int sort_blocks[64], merge_blocks[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  once_per_device(attr_done, [dev] {
+    cudaFuncSetAttribute(k_tile_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSortWarpSmem));
+    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSortSmem));
+    cudaFuncSetAttribute(k_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileMergeSmem));
+    if (dev < 64) {
+      sort_blocks[dev] = persistent_blocks(k_tile_sort, TS_THREADS, sizeof(TileSortSmem));
+      merge_blocks[dev] = persistent_blocks(k_tile_merge, TS_THREADS, sizeof(TileMergeSmem));
+    }
+  });
+  const int ns = dev < 64 ? sort_blocks[dev] : persistent_blocks(k_tile_sort, TS_THREADS, sizeof(TileSortSmem));
+  const int nmg = dev < 64 ? merge_blocks[dev] : persistent_blocks(k_tile_merge, TS_THREADS, sizeof(TileMergeSmem));
+  const int passes = sort_passes(tile_bits(tiles));
+  const bool odd = passes & 1, ready = passes > 0;
+  uint32_t* sv = odd ? w.v1 : w.v0;
+  uint32_t* xk = odd ? w.k0 : w.k1;
+  uint32_t* xv = odd ? w.v0 : w.v1;
+  const unsigned wblocks = (unsigned)((tiles + TW_WARPS - 1) / TW_WARPS);
+  k_tile_sort_warp<<<wblocks, TW_WARPS * 32, sizeof(TileSortWarpSmem), s>>>(sv, w.s_dkey, w.counters, pair_cap, ready,
+                                                                          tiles, w.ranges, w.mid_tiles, w.work + 4,
+                                                                          w.chunks, w.work + 2, w.long_tiles,
+                                                                          w.work + 6);
+  k_tile_sort<<<(unsigned)ns, TS_THREADS, sizeof(TileSortSmem), s>>>(sv, xk, xv, w.s_dkey, w.ranges, w.mid_tiles,
+                                                                     w.work + 4, w.chunks, w.work + 2, w.work + 5);
+  k_tile_merge<<<(unsigned)nmg, TS_THREADS, sizeof(TileMergeSmem), s>>>(sv, xk, xv, w.ranges, w.long_tiles,
+                                                                        w.work + 6, w.work + 3);
+  count_launch(3);
+}
+
 static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* out) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
@@ -1408,47 +1885,38 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
   const int64_t n = vox->n, items = n * n_views;
-  // counters, tile ranges, the fallback status word and the persistent forward's work counter
-  zero_async(s, w.counters, 8 * sizeof(unsigned long long), w.ranges, sizeof(uint32_t) * 2 * tiles,
-             d_status == w.status ? w.status : nullptr, sizeof(int32_t), w.work, sizeof(unsigned int));
+  // counters, the fallback status word and the work counters of the persistent kernels
+  // (k_tile_sort_warp writes every tile's range)
+  zero_async(s, w.counters, 8 * sizeof(unsigned long long), d_status == w.status ? w.status : nullptr,
+             sizeof(int32_t), w.work, 8 * sizeof(unsigned int));
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
     const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
     k_bin<<<blocks, 256, 0, s>>>((const float4*)vox->geom, n, vs, w.cnt, w.vis, w.rect, w.pbox, w.dkey, out->z_min,
                                  out->delta_min, out->seen);
     if (out->stats_event) cudaEventRecord((cudaEvent_t)out->stats_event, s);  // statistics final
-    scan2(w.cnt, w.vis, items, nullptr, w.slot, w.counters, w.scan_tmp, s);
+    scan2(w.cnt, w.vis, items, w.poff, w.slot, w.counters, w.scan_tmp, s);
     const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
 #define LV_EMIT(DT, ST)                                                                                             \
   k_emit<DT, ST><<<emit_blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, \
                                              nb, n, vs, w.cnt, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey,          \
-                                             w.slot, w.rec, w.d_rgb, w.s_tiles, w.s_dkey, vox->vidx)
+                                             w.slot, w.poff, w.counters, pair_capacity, w.k0, w.v0, d_status,         \
+                                             (uint2*)w.ranges, tiles, w.rec, w.d_rgb, w.s_dkey, vox->vidx)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
     else LV_EMIT(__half, __nv_bfloat16);
 #undef LV_EMIT
     count_launch(2);
-    // 1) the slots front to back: stable sort by order key (ties keep slot = voxel-id order)
-    const int ws_ = radix_sort_pairs(w.s_dkey, nullptr, w.sk0, w.sv0, w.sk1, w.sv1, w.sort_tmp, w.counters + 1,
-                                     items, 32, d_status, s);
-    const uint32_t* sorted_slot = ws_ ? w.sv1 : w.sv0;
-    // 2) pair offsets in that order, then the pairs themselves
-    const int gb = (int)std::min<int64_t>((items + 255) / 256, 4 * 1216);
-    k_slot_counts<<<gb, 256, 0, s>>>(sorted_slot, w.s_tiles, w.counters + 1, items, w.scnt, w.st_sorted);
-    scan2(w.scnt, nullptr, items, w.poff, nullptr, w.counters + 2, w.scan_tmp, s);
-    k_emit_pairs<<<8 * 152, EP_WARPS * 32, 0, s>>>(vs, sorted_slot, w.st_sorted, w.poff, w.counters,
-                                                  pair_capacity, w.k0, w.v0, d_status);
-    count_launch(2);
   } else if (out->stats_event) {
     cudaEventRecord((cudaEvent_t)out->stats_event, s);  // no voxel: nothing to bin
   }
-  // 3) stable sort by tile: each tile's list stays front to back
+  // stable sort by tile: each tile's list stays in item order; the last pass notes every tile's range
   radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.sort_tmp, w.counters, pair_capacity, tile_bits(tiles),
-                   d_status, s);
-  const uint32_t* sk = sorted_pair_tiles(w, tiles);
+                   d_status, s, w.ranges);
+  // each tile's range, and its list front to back
+  launch_tile_sort(w, tiles, pair_capacity, s);
   const uint32_t* sv = sorted_pair_slots(w, tiles);
-  k_ranges<<<608, 256, 0, s>>>(sk, w.counters, pair_capacity, tiles, w.ranges);
   if (out->composite_event) {
     // a timing mark: inside a stream capture it becomes an event record node of the graph
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -350,10 +350,16 @@ def test_full_size_360_whole_view(ora, full360, tile, persistent):
     print("full-size images:", image_report(r, ctx))
     w, a = ctx.unpack_wmax()
     print("full-size w_max:", check_wmax(np_(w), np_(a), ws, r["near_stop"]))
-    ref = ora.pairs(sc, [cam])
+    ref = ora.pairs(sc, [cam], ts=tile)
     np.testing.assert_array_equal(np_(ctx.seen), ref["seen"])
     np.testing.assert_array_equal(np_(ctx.z_min).view(np.uint32), ref["z_min"].view(np.uint32))
     np.testing.assert_array_equal(np_(ctx.delta_min).view(np.uint32), ref["delta_min"].view(np.uint32))
+    # every pair list of the whole view, front to back (tile 32: lists of up to 11142 pairs)
+    keys, vox_ids, ranges, pairs = gpu_pairs(ctx, scene.n)
+    assert pairs == ref["n_pairs"]
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(vox_ids, ref["vals"])
+    np.testing.assert_array_equal(ranges, ref["ranges"])
     x0, y0 = 580, 380
     crop = [x0, y0, x0 + 64, y0 + 48]
     m = np.zeros((822, 1237), bool)
