@@ -198,7 +198,9 @@ __global__ void k_pr_wkey(int64_t n, const float* __restrict__ w_max, uint32_t* 
   store4(wkey, i0, n, wk);
 }
 
-__global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm) {
+__global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm,
+                                 void* sel_tmp) {
+  select_prepare(q, 2, sel_tmp);
   if (threadIdx.x == 0) {
     q[0].group = 0; q[0].k = rank_ppm(lo_ppm, st->ns);
     q[1].group = 0; q[1].k = rank_ppm(hi_ppm, st->ns);
@@ -266,7 +268,8 @@ __device__ __forceinline__ long long q_bin(long long q_ppm, long long anneal_ppm
 
 // a bin with q_b = 0 gets k = 0: no threshold (result stays 0xffffffff)
 __global__ void k_pr_tau_queries(SelectQuery* q, const PruneState* st, int nb, uint32_t q_ppm, int anneal,
-                                 uint32_t anneal_ppm, uint32_t relax_ppm) {
+                                 uint32_t anneal_ppm, uint32_t relax_ppm, void* sel_tmp) {
+  select_prepare(q, nb, sel_tmp);
   int b = threadIdx.x;
   if (b < nb) {
     const long long qb = anneal ? q_bin(q_ppm, anneal_ppm, relax_ppm, b, nb) : (long long)q_ppm;
@@ -334,7 +337,8 @@ __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const u
   if (threadIdx.x == 0 && bl) atomicAdd(&st->n_cand, bl);
 }
 
-__global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap) {
+__global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap, void* sel_tmp) {
+  select_prepare(q, 1, sel_tmp);
   if (threadIdx.x == 0) {
     st->all = st->n_cand <= cap ? 1u : 0u;
     q[0].group = 0;
@@ -429,9 +433,10 @@ struct SubWs {
   uint32_t* surv;
   uint32_t* sel;
   unsigned long long* surv_pos;
-  uint32_t* sel_rank;
   uint32_t* sel_list;  // [k] selected parent ids in id order
   uint32_t* blk;       // per-block tie counts -> offsets
+  uint32_t* blk_surv;  // per-block survivor counts (k_sd_select)
+  uint32_t* blk_sel;   // per-block parent counts (k_sd_select)
   unsigned long long* totals;
   void* scan_tmp;
   size_t bytes;
@@ -449,9 +454,10 @@ SubWs carve_sub(void* base, int64_t n) {
   w.surv = c.take<uint32_t>(n);
   w.sel = c.take<uint32_t>(n);
   w.surv_pos = c.take<unsigned long long>(n);
-  w.sel_rank = c.take<uint32_t>(n);
   w.sel_list = c.take<uint32_t>(n);
   w.blk = c.take<uint32_t>(n / TPB + 1);
+  w.blk_surv = c.take<uint32_t>(n / EB + 1);
+  w.blk_sel = c.take<uint32_t>(n / EB + 1);
   w.totals = c.take<unsigned long long>(4);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.bytes = c.off + 256;
@@ -468,22 +474,27 @@ __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const ui
   load4(z, i0, n, zv, 0.f);
   uint16_t gv[IPT];
   uint32_t zk[IPT];
-  uint32_t c = 0;
+  uint32_t c = 0, c0 = 0;
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     const bool alive = pv[u] == 0;
-    gv[u] = (alive && sv[u]) ? 0 : GROUP_NONE;
+    gv[u] = (alive && sv[u]) ? 0 : GROUP_NONE;  // padding reads seen = 0
     zk[u] = order_key(zv[u]);
     c += (alive && i0 + u < n) ? 1u : 0u;
+    c0 += gv[u] == 0 ? 1u : 0u;
   }
   store4(grp, i0, n, gv);
   store4(zkey, i0, n, zk);
-  // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const uint32_t b = block_total(c);
+  // one atomic per block and count (a same-address atomic per warp serialises at the L2); n_el
+  // counts the alive and seen voxels until the percentiles are applied
+  const uint32_t b = block_total(c), b0 = block_total(c0);
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_alive, b);
+  if (threadIdx.x == 0 && b0) atomicAdd(&st->n_el, b0);
 }
 
-__global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter) {
+__global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter,
+                                 void* sel_tmp) {
+  select_prepare(q, 2, sel_tmp);
   if (threadIdx.x == 0) {
     uint32_t m = *counter;
     q[0].group = 0; q[0].k = rank_ppm(lo_ppm, m);
@@ -491,21 +502,12 @@ __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_pp
   }
 }
 
-__global__ void k_sd_pct_apply(const SelectQuery* pct, SubState* st, const uint32_t* n_seen, float* state, float r,
-                               float omr) {
-  if (threadIdx.x == 0 && *n_seen > 0) running_pct(pct, state, r, omr, &st->p_lo);
-}
-
-__global__ void k_sd_count_group0(int64_t n, const uint16_t* __restrict__ grp, uint32_t* counter) {
-  const int64_t i0 = first_item();
-  uint16_t gv[IPT];
-  load4(grp, i0, n, gv, GROUP_NONE);
-  uint32_t c = 0;
-#pragma unroll
-  for (int u = 0; u < IPT; ++u) c += gv[u] == 0 ? 1u : 0u;
-  // one atomic per block (a same-address atomic per warp serialises at the L2)
-  const uint32_t b = block_total(c);
-  if (threadIdx.x == 0 && b) atomicAdd(counter, b);
+// also clears n_el (the alive and seen count until now) for the eligible count
+__global__ void k_sd_pct_apply(const SelectQuery* pct, SubState* st, float* state, float r, float omr) {
+  if (threadIdx.x == 0) {
+    if (st->n_el > 0) running_pct(pct, state, r, omr, &st->p_lo);
+    st->n_el = 0u;
+  }
 }
 
 // Eq. 13 eligibility and Eq. 15-16 priority; pkey orders by descending priority
@@ -550,7 +552,8 @@ __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const 
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_el, b);
 }
 
-__global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget) {
+__global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget, void* sel_tmp) {
+  select_prepare(q + 2, 1, sel_tmp);
   if (threadIdx.x == 0) {
     const unsigned long long na = st->n_alive;
     unsigned long long k = (unsigned long long)top_ppm * na / 1000000ull;
@@ -597,7 +600,7 @@ __global__ void k_sd_ties(int64_t n, const uint32_t* __restrict__ pkey, const Se
 __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uint16_t* __restrict__ grp,
                             const uint32_t* __restrict__ pkey, const SelectQuery* q,
                             const uint32_t* __restrict__ blk, const SubState* st, uint8_t* selected,
-                            uint32_t* surv, uint32_t* sel) {
+                            uint32_t* surv, uint32_t* sel, uint32_t* blk_surv, uint32_t* blk_sel) {
   const int64_t i0 = first_item();
   const bool any_k = q[2].k != 0;
   const uint32_t v = q[2].result;
@@ -621,18 +624,26 @@ __global__ void k_sd_select(int64_t n, const uint8_t* __restrict__ pm, const uin
   uint32_t r = block_excl_count(ceq) + block_offset(blk);  // every thread of the block takes part
   const uint32_t need = st->k > st->c_gt ? st->k - st->c_gt : 0u;
   uint8_t so[IPT];
-  uint32_t sl[IPT], sv[IPT];
+  uint32_t sl[IPT], sv[IPT], cs = 0, cl = 0;
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     const bool s = gt[u] || (eq[u] && r < need);
     r += eq[u] ? 1u : 0u;
     so[u] = s ? 1 : 0;
     sl[u] = s ? 1u : 0u;
-    sv[u] = (pv[u] == 0 && !s) ? 1u : 0u;
+    sv[u] = (pv[u] == 0 && !s && i0 + u < n) ? 1u : 0u;
+    cs += sv[u];
+    cl += sl[u];
   }
   store4(selected, i0, n, so);
   store4(sel, i0, n, sl);
   store4(surv, i0, n, sv);
+  // per-block survivor and parent counts: k_sd_list takes its offsets from them
+  const uint32_t bs = block_total(cs), bl = block_total(cl);
+  if (threadIdx.x == 0) {
+    blk_surv[blockIdx.x] = bs;
+    blk_sel[blockIdx.x] = bl;
+  }
 }
 
 __global__ void k_sd_check(const unsigned long long* totals, SubState* st, int64_t capacity, int64_t* n_new,
@@ -735,18 +746,52 @@ __global__ void k_cp_flags(int64_t n, const uint8_t* __restrict__ keep, uint32_t
   if (i < n) surv[i] = keep[i] ? 1u : 0u;
 }
 
-// The split parents in id order (list), and the pruned rows -- neither survivor
-// nor parent -- in id order (holes, for the in-place topology change): the
-// number of pruned rows before i is i - (survivors before i) - (parents before i).
-// It runs with the selection (on the caller's side stream in a training step)
-// so that the in-place write does not read these arrays again.
-__global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uint32_t* __restrict__ rank,
-                          const uint32_t* __restrict__ surv, const unsigned long long* __restrict__ surv_pos,
-                          uint32_t* __restrict__ list, uint32_t* __restrict__ holes) {
-  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-  if (i >= n) return;
-  if (sel[i]) list[rank[i]] = (uint32_t)i;
-  else if (!surv[i]) holes[i - (int64_t)surv_pos[i] - (int64_t)rank[i]] = (uint32_t)i;
+// The split parents in id order (list), the pruned rows -- neither survivor
+// nor parent -- in id order (holes, for the in-place topology change) and
+// every voxel's survivor position (for the out-of-place one).  Blocks cover
+// the voxels as in k_sd_select and take their offsets from its per-block
+// counts; the number of pruned rows before i is i - (survivors before i) -
+// (parents before i).  The last block also totals the survivors and the
+// parents and checks the grown count against the output capacity.  It runs
+// with the selection (on the caller's side stream in a training step) so that
+// the in-place write does not read these arrays again.
+__global__ void k_sd_list(int64_t n, const uint32_t* __restrict__ sel, const uint32_t* __restrict__ surv,
+                          const uint32_t* __restrict__ blk_surv, const uint32_t* __restrict__ blk_sel,
+                          unsigned long long* __restrict__ surv_pos, uint32_t* __restrict__ list,
+                          uint32_t* __restrict__ holes, unsigned long long* totals, SubState* st, int64_t capacity,
+                          int64_t* n_new, int32_t* status) {
+  const int64_t i0 = first_item();
+  uint32_t sl[IPT], sv[IPT], cs = 0, cl = 0;
+  load4(sel, i0, n, sl, 0u);
+  load4(surv, i0, n, sv, 0u);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    cs += sv[u];
+    cl += sl[u];
+  }
+  const uint32_t os = block_offset(blk_surv), ol = block_offset(blk_sel);
+  uint32_t rs = os + block_excl_count(cs), rl = ol + block_excl_count(cl);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const int64_t i = i0 + u;
+    if (i >= n) break;
+    surv_pos[i] = rs;
+    if (sl[u]) list[rl] = (uint32_t)i;
+    else if (!sv[u]) holes[i - (int64_t)rs - (int64_t)rl] = (uint32_t)i;
+    rs += sv[u];
+    rl += sl[u];
+  }
+  if (blockIdx.x == gridDim.x - 1) {  // block-uniform
+    const uint32_t ts = block_total(cs), tl = block_total(cl);
+    if (threadIdx.x == 0) {
+      totals[0] = (unsigned long long)os + ts;
+      totals[1] = (unsigned long long)ol + tl;
+      const long long nn = (long long)(os + ts) + 8ll * (long long)(ol + tl);
+      st->fits = nn <= capacity ? 1u : 0u;
+      if (!st->fits) report(status, LV_ERR_CAPACITY);
+      if (n_new) *n_new = nn;
+    }
+  }
 }
 
 // A warp writes 32 consecutive children (output rows o0 .. o0 + 31): one lane
@@ -1069,8 +1114,8 @@ extern "C" lv_status lv_prune_bins(int64_t n, const uint8_t* seen, const float* 
   const int blocks = eblocks(n);  // IPT voxels per thread
   zero_async(s, w.st, sizeof(PruneState));
   k_pr_seen<<<blocks, TPB, 0, s>>>(n, seen, z, w.grp, w.zkey, w.st);
-  k_pr_pct_queries<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm);
-  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  k_pr_pct_queries<<<1, 256, 0, s>>>(w.q, w.st, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, w.sel_tmp);
+  select_kth_prepared(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
   const float r = p->pct_ema, omr = 1.0f - r;  // rounded to FP32 once, as the oracle does
   k_pr_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, r, omr);
   k_pr_bin<<<blocks, TPB, 0, s>>>(n, seen, z, p->n_bins, w.grp, w.st);
@@ -1101,9 +1146,9 @@ extern "C" lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_
   const int blocks = eblocks(n);  // IPT voxels per thread
   k_pr_wkey<<<blocks, TPB, 0, s>>>(n, w_max, w.wkey);
   // the percentiles in q[0..1] are consumed: q is reused per bin
-  k_pr_tau_queries<<<1, SELECT_MAX_QUERIES, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal,
-                                                    (uint32_t)p->anneal_ppm, (uint32_t)p->relax_ppm);
-  select_kth(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
+  k_pr_tau_queries<<<1, 256, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal, (uint32_t)p->anneal_ppm,
+                                     (uint32_t)p->relax_ppm, w.sel_tmp);
+  select_kth_prepared(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
   // candidates get their own group array (zkey is free now: reuse it as u16 storage)
   uint16_t* cand = (uint16_t*)w.zkey;
   Halo halo;
@@ -1117,8 +1162,8 @@ extern "C" lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_
   k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, halo,
                                       prune_mask, cand, w.st);
   SelectQuery* qc = w.q + SELECT_MAX_QUERIES - 2;  // cap threshold
-  k_pr_cap_query<<<1, 32, 0, s>>>(qc, w.st, cap);
-  select_kth(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
+  k_pr_cap_query<<<1, 256, 0, s>>>(qc, w.st, cap, w.sel_tmp);
+  select_kth_prepared(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
   k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, prune_mask, w.blk, w.st);
   k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, w.blk, w.st, prune_mask, d_n_pruned, cap);
   count_launch(7);
@@ -1197,22 +1242,19 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   }
   const int blocks = eblocks(n);  // IPT voxels per thread
   k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st);
-  uint32_t* cnt_seen = &w.st->n_el;  // temporarily counts alive & seen voxels
-  k_sd_count_group0<<<blocks, TPB, 0, s>>>(n, w.grp, cnt_seen);
-  k_sd_pct_queries<<<1, 32, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, cnt_seen);
-  select_kth(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
-  k_sd_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, cnt_seen, p->pct_state, p->pct_ema, 1.0f - p->pct_ema);
-  zero_async(s, cnt_seen, sizeof(uint32_t));
+  k_sd_pct_queries<<<1, 256, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, &w.st->n_el, w.sel_tmp);
+  select_kth_prepared(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  k_sd_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, p->pct_ema, 1.0f - p->pct_ema);
   k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, p->kappa, p->beta,
                                         p->l_max, w.grp, w.pkey, w.st);
-  k_sd_k<<<1, 32, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget);
-  select_kth(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
+  k_sd_k<<<1, 256, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget, w.sel_tmp);
+  select_kth_prepared(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
   k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.blk, w.st);
-  k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel);
-  scan2(w.surv, w.sel, n, w.surv_pos, w.sel_rank, w.totals, w.scan_tmp, s);
-  k_sd_check<<<1, 32, 0, s>>>(w.totals, w.st, out_capacity, d_n_new, d_status);
-  k_sd_list<<<blocks_for(n), TPB, 0, s>>>(n, w.sel, w.sel_rank, w.surv, w.surv_pos, w.sel_list, w.zkey);
-  count_launch(13);
+  k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel,
+                                      w.blk_surv, w.blk_sel);
+  k_sd_list<<<blocks, TPB, 0, s>>>(n, w.sel, w.surv, w.blk_surv, w.blk_sel, w.surv_pos, w.sel_list, w.zkey,
+                                   w.totals, w.st, out_capacity, d_n_new, d_status);
+  count_launch(9);
   return cuda_check(cudaGetLastError(), "lv_subdivide_select");
 }
 

@@ -580,7 +580,6 @@ constexpr int SEL_THREADS = 256;
 constexpr int SEL_BLOCKS = 304;
 constexpr int SEL_MAX_Q_PER_GROUP = 2;
 constexpr int SEL_ITEMS = 4;        // items per thread per iteration, loads issued together
-constexpr int SEL_WIDE_MAX_Q = 4;   // up to this many queries use 11-bit digits
 
 // One warp per query: find the digit holding the k-th item (warp scan over
 // RADIX / 32 digits per lane) and extend the prefix; returns the updated query.
@@ -830,14 +829,13 @@ size_t select_tmp_bytes(int n_queries) {
   return 3 * sizeof(uint32_t) * (narrow > wide ? narrow : wide) + 2 * sizeof(SelectQuery) * (size_t)n_queries + 512;
 }
 
-void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
-                void* tmp, cudaStream_t s) {
+// the digit passes and the last pick, after the queries and the first histogram buffer are set up
+static void select_run(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                       void* tmp, cudaStream_t s) {
   const bool wide = n_queries <= SEL_WIDE_MAX_Q;
-  const int words = (wide ? 2048 : 256) * n_queries;
+  const int words = select_hist_words(n_queries);
   uint32_t* hist = (uint32_t*)tmp;
   SelectQuery* qs = (SelectQuery*)(hist + 3 * (size_t)words);
-  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, hist, words);
-  count_launch(1);
   // ranking by index needs only the bits of n - 1 (at least one)
   int key_bits = 32;
   if (!keys) {
@@ -846,6 +844,18 @@ void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuer
   }
   if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 11, s);
   else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 8, s);
+}
+
+void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                void* tmp, cudaStream_t s) {
+  k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, (uint32_t*)tmp, select_hist_words(n_queries));
+  count_launch(1);
+  select_run(keys, grp, n, d_queries, n_queries, tmp, s);
+}
+
+void select_kth_prepared(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries,
+                         int n_queries, void* tmp, cudaStream_t s) {
+  select_run(keys, grp, n, d_queries, n_queries, tmp, s);
 }
 
 }  // namespace lv

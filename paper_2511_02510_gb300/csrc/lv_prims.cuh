@@ -60,4 +60,22 @@ size_t select_tmp_bytes(int n_queries);
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s);
 
+// select_kth without its set-up launch: the kernel that writes the queries
+// also calls select_prepare (all threads of one block) for the same queries
+// and scratch, so a select costs one launch less on the caller's stream.
+constexpr int SEL_WIDE_MAX_Q = 4;  // up to this many queries use 11-bit digits
+__host__ __device__ constexpr int select_hist_words(int n_queries) {
+  return (n_queries <= SEL_WIDE_MAX_Q ? 2048 : 256) * n_queries;
+}
+__device__ __forceinline__ void select_prepare(SelectQuery* q, int n_queries, void* tmp) {
+  for (int j = threadIdx.x; j < n_queries; j += blockDim.x) {
+    q[j].prefix = 0u;
+    q[j].result = 0xffffffffu;
+  }
+  uint32_t* hist = (uint32_t*)tmp;
+  for (int i = threadIdx.x; i < select_hist_words(n_queries); i += blockDim.x) hist[i] = 0u;
+}
+void select_kth_prepared(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries,
+                         int n_queries, void* tmp, cudaStream_t s);
+
 }  // namespace lv
