@@ -219,29 +219,21 @@ class Workload:
         torch = self.torch
         idx = torch.nonzero((self.selected != 0) | (self.pmask != 0)).flatten()
         self.restore_idx = idx
-        self.restore_saved = [self._wide(p).index_select(0, idx) for p in pristine]
+        self.restore_saved = [p.index_select(0, idx) for p in pristine]
         for arr, p in zip(self._state_arrays(), pristine):
             arr.copy_(p)
         self.ema.copy_(self.ema0)
         self.state.copy_(self.state0)
 
-    def _wide(self, t):
-        """Rows of 16-byte multiples seen as 16-byte elements, so an index copy moves a row in a few
-        elements rather than one element per float."""
-        row = t[0].numel() * t.element_size() if t.dim() > 1 else t.element_size()
-        if t.dim() > 1 and row % 16 == 0 and t.is_contiguous():
-            return t.view(self.torch.complex128)
-        return t
-
     def restore(self):
         """Put back the rows the step's in-place topology change overwrote and the pruning state, so
-        the next step starts from the same scene (inside the timed region: it is extra work)."""
+        the next step starts from the same scene (inside the timed region: it is extra work), in
+        one launch of the library's row scatter."""
         if self.restore_idx is None:
             return
-        for arr, saved in zip(self._state_arrays(), self.restore_saved):
-            self._wide(arr).index_copy_(0, self.restore_idx, saved)
-        self.ema.copy_(self.ema0)
-        self.state.copy_(self.state0)
+        items = [(arr, saved, self.restore_idx) for arr, saved in zip(self._state_arrays(), self.restore_saved)]
+        items += [(self.ema, self.ema0, None), (self.state, self.state0, None)]
+        self.L.lv_rows_scatter(items)
 
     def step(self, ev=None):
         L, r = self.L, self.rctx
@@ -281,17 +273,22 @@ class Workload:
         truth only, and pruning and the subdivision selection on the forward statistics only, so
         they run beside the forward and the backward respectively (side streams at high priority,
         joined by events): the depth bins of the pruning start as soon as the forward has binned
-        the voxels (its statistics event), the rest once w_max is out.  The in-place topology
+        the voxels (its statistics event), the rest once w_max is out.  The LF loss's gradient is
+        fused into the forward composite (which waits for the weights), its value is finished on
+        the side stream.  The SH backward, which reads the forward's workspace and not the voxel
+        arrays, runs beside the topology change and the restore.  The in-place topology
         change runs last, alone, then the restore.  ev: {"composite" | "backward" | "apply":
         (start, end)} timing events (external, so that they time graph replays)."""
         torch, L, r = self.torch, self.L, self.rctx
         if not hasattr(self, "_side"):
             hi = torch.cuda.Stream.priority_range()[1]
-            self._side = (torch.cuda.Stream(priority=hi), torch.cuda.Stream(priority=hi))
-            self._evs = [torch.cuda.Event() for _ in range(5)]
+            # the SH backward gets a stream of normal priority: its many blocks must not hold up the
+            # pruning and selection chain, which ends last
+            self._side = (torch.cuda.Stream(priority=hi), torch.cuda.Stream(priority=hi), torch.cuda.Stream())
+            self._evs = [torch.cuda.Event() for _ in range(7)]
             self._evs[4].record()  # the statistics event must exist before the library records it
-        sw, sb = self._side
-        e_start, e_w, e_fwd, e_b, e_stats = self._evs
+        sw, sb, sl = self._side
+        e_start, e_w, e_fwd, e_b, e_stats, e_bwd, e_sh = self._evs
         main = torch.cuda.current_stream()
         e_start.record(main)
         sw.wait_event(e_start)
@@ -300,7 +297,9 @@ class Workload:
             L.lv_lf_weights(self.gt, [W_IMG], [H_IMG], self.t_iter, self.lfp, self.lf_ws)
             e_w.record(sw)
         r.reset_stats()
-        r.forward(self.vox, stats=True, stats_event=e_stats, composite_event=ev["composite"][0] if ev else None)
+        # the LF loss's gradient is fused into the composite, which waits for the weights (e_w)
+        r.forward(self.vox, stats=True, stats_event=e_stats, composite_event=ev["composite"][0] if ev else None,
+                  lf=(self.gt, self.lf_ws, self.dL, e_w))
         if ev:
             ev["composite"][1].record(main)
         e_fwd.record(main)
@@ -309,21 +308,28 @@ class Workload:
             L.lv_prune_bins(r.seen, r.z_min, self.pp, self.pr_ws)
         sb.wait_event(e_fwd)
         with torch.cuda.stream(sb):
+            L.lv_lf_loss_finish([W_IMG], [H_IMG], self.loss, self.lf_ws)
             L.lv_unpack_wmax(r.wmax_packed, self.w_max, self.w_arg)
             L.lv_prune_finish(self.w_max, r.seen, r.z_min, self.ema, self.state, self.pp, self.pmask,
                               self.n_pruned, self.pr_ws)
             L.lv_subdivide_select(self.vox, r.delta_min, r.z_min, self.w_max, r.seen, self.pmask, self.sp,
                                   self.cap, self.selected, self.n_new, self.sd_ws, self.status)
             e_b.record(sb)
-        main.wait_event(e_w)
-        L.lv_lf_loss_from_weights(r.rgb, self.gt, [W_IMG], [H_IMG], self.loss, self.dL, self.lf_ws)
         if ev:
             ev["backward"][0].record(main)
         L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, self.bwd_opts, r.fwd_struct(False), r.workspace,
                                 r.pair_capacity, self.dL, None, None, self.d_dens, None, True, r.status)
         if ev:
             ev["backward"][1].record(main)
-        L.lv_sh_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.workspace, r.pair_capacity, self.d_sh, False)
+        # the SH backward reads only the workspace, so it runs beside the in-place topology change;
+        # it waits for the selection too, whose memory-bound chain it would otherwise slow down
+        e_bwd.record(main)
+        sl.wait_event(e_bwd)
+        sl.wait_event(e_b)
+        with torch.cuda.stream(sl):
+            L.lv_sh_backward(self.vox, r.cams_arr, r.n_views, r.opts, r.workspace, r.pair_capacity, self.d_sh,
+                             False)
+            e_sh.record(sl)
         main.wait_event(e_b)
         if ev:
             ev["apply"][0].record(main)
@@ -331,6 +337,7 @@ class Workload:
         if ev:
             ev["apply"][1].record(main)
         self.restore()
+        main.wait_event(e_sh)
 
     def e2e_step(self):
         """The same step through the public API with host buffers: the step's ground-truth
@@ -1074,10 +1081,10 @@ def run_ours(args, rank, world, local):
                               "its loss is copied back to pinned host memory and read by the host while the next "
                               "step runs"},
                "gpu_launches": int(launches),
-               "restore": {"rows": int(wl.restore_idx.numel()), "torch_launches_per_step": 6,
-                           "what": "index copies of the overwritten rows of the geometry, level, corner and SH "
-                                   "arrays and full copies of the EMA and hysteresis state, inside the timed "
-                                   "region (extra work, not part of the method)"},
+               "restore": {"rows": int(wl.restore_idx.numel()), "launches_per_step": 1,
+                           "what": "one lv_rows_scatter launch: the overwritten rows of the geometry, level, "
+                                   "corner and SH arrays put back, and full copies of the EMA and hysteresis "
+                                   "state, inside the timed region (extra work, not part of the method)"},
                "topology_change": {"inplace_ms": kernels.get("apply", {}).get("ms"),
                                    "out_of_place_ms": oop_ms,
                                    "inplace_bytes": work["subdivide_inplace"]["bytes"],

@@ -115,9 +115,11 @@ typedef struct {
                              (64 B each) before its pixels march through them; changes no result */
   float t_stop;           /* a ray stops after the sample that takes T below t_stop (1e-4) */
   uint32_t flags;         /* LV_FLAG_* */
-  int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: size the resident grid for this many SMs (0 = all),
-                             leaving the rest to kernels of other streams that run beside the composites;
-                             it changes no result and may differ between the forward and backward calls */
+  int32_t persistent_sms; /* with LV_FLAG_PERSISTENT: run the composite on this many SMs (0 = all): the
+                             full resident grid is launched and the blocks that land on other SMs (by SM
+                             id) return at once, so those SMs stay free for kernels of other streams that
+                             run beside the composite; it changes no result and may differ between the
+                             forward and backward calls */
   int64_t pixel_id_base;  /* global id of this call's first pixel (0): the pixel ids packed into w_max
                              (Eq. 5's argmax and its tie rule) are pixel_id_base + the view-major index;
                              calls or ranks that render disjoint views with disjoint bases accumulate one
@@ -147,6 +149,23 @@ typedef struct {
                                         composite alone; inside a stream capture it is recorded as an
                                         external event node (cudaEventRecordExternal), a timing mark
                                         of every replay rather than a dependency */
+  /* Optional LF-weighted loss fused into the composite (Sec. IV-B, Eq. 8 and
+   * 18), for a caller that ran lv_lf_weights for this forward's views (their
+   * widths and heights in camera order) and ordered it before the forward on
+   * the stream.  When lf_workspace is not NULL the composite also writes
+   * every pixel's dL/drgb into lf_dL -- bit for bit what
+   * lv_lf_loss_from_weights writes -- and adds the views' loss sums into the
+   * workspace (FP64, one atomic per block and view); lv_lf_loss_finish then
+   * writes the per-view losses.  lf_gt and lf_dL must then be non-NULL.  A
+   * wrong workspace size returns LV_ERR_WORKSPACE, mismatched views
+   * LV_ERR_INVALID_ARG. */
+  const float* lf_gt;                /* [P][3] ground truth, as given to lv_lf_weights */
+  void* lf_workspace;                /* lv_lf_weights' workspace (256-byte aligned), or NULL */
+  size_t lf_ws_bytes;
+  float* lf_dL;                      /* [P][3] dL/drgb output */
+  void* lf_wait_event;               /* cudaEvent_t (nullable): the stream waits for it right before the
+                                        composite, so lv_lf_weights can run on another stream beside
+                                        the binning and sorting (inside a stream capture: a dependency) */
 } lv_fwd_out;
 
 /* ------------------------------------------------------------------ */
@@ -209,7 +228,10 @@ lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera* cams, int
  * gradients a preceding lv_rasterize_backward(d_sh = NULL) left in the
  * workspace, through c = max(0, SH(dir) + 0.5) with dir the unit vector from
  * the camera centre to the voxel centre; sums over views.  Clears the
- * workspace's colour gradients.  accumulate as in lv_rasterize_backward. */
+ * workspace's colour gradients.  accumulate as in lv_rasterize_backward.
+ * Reads only the workspace (the camera-relative centres the forward stored),
+ * not the voxel arrays, so it may run beside a topology change that rewrites
+ * them in place (lv_subdivide_apply_inplace); vox gives n and the SH degree. */
 lv_status lv_sh_backward(const lv_voxels* vox, const lv_camera* cams, int n_views, const lv_raster_opts* opts,
                          void* workspace, size_t ws_bytes, int64_t pair_capacity, float* d_sh, int accumulate,
                          void* stream);
@@ -472,6 +494,25 @@ lv_status lv_subdivide_apply_inplace(const lv_voxels* vox, int64_t capacity, con
                                      const lv_aux_array* aux, int n_aux, void* workspace, size_t ws_bytes,
                                      void* stream);
 
+/* Row scatter of up to LV_MAX_AUX arrays in one launch: for each array,
+ * dst[idx[j]] = src[j] for j < m (rows of row_bytes bytes), or, with idx =
+ * NULL, dst[j] = src[j] (a plain copy of m rows).  The paper has no
+ * counterpart: it undoes an in-place topology change from rows the caller
+ * saved before it (the rows of the split parents and of the pruned voxels),
+ * for a rollback, and lets a benchmark return to the same scene after every
+ * step.  Rows move as 16-byte words when row_bytes and both pointers allow
+ * it (a plain copy: when the whole range does), byte by byte otherwise.
+ * idx: device int64 [m], values distinct within an array and below the
+ * destination's rows.  Device pointers; src and dst must not overlap. */
+typedef struct {
+  void* dst;
+  const void* src;
+  int64_t row_bytes;
+  const int64_t* idx; /* device [m], or NULL */
+  int64_t m;
+} lv_rows;
+lv_status lv_rows_scatter(const lv_rows* arrays, int n_arrays, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* LF-weighted photometric loss (Sec. IV-B, Eq. 7-10, 18)               */
 /* ------------------------------------------------------------------ */
@@ -514,6 +555,15 @@ lv_status lv_lf_weights(const float* gt, const int32_t* widths, const int32_t* h
 lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, const int32_t* widths, const int32_t* heights,
                                   int n_views, float* loss, float* dL_drgb, void* workspace, size_t ws_bytes,
                                   void* stream);
+
+/* The per-view losses of a forward that fused the LF loss (lv_fwd_out.lf_*):
+ * loss[v] = (the view's summed weighted squared error) / (3 |P_v|), the value
+ * lv_lf_loss_from_weights writes up to the order of the FP64 sums.  Reads
+ * and then clears the sums in `workspace` (lv_lf_weights clears them too), so
+ * call it once per fused forward, after the forward on the stream.  loss:
+ * device float[n_views]. */
+lv_status lv_lf_loss_finish(const int32_t* widths, const int32_t* heights, int n_views, float* loss,
+                            void* workspace, size_t ws_bytes, void* stream);
 
 /* Allocation-free variant of lv_lf_weighted_loss.  The paper has no
  * counterpart: it exists for callers that cannot allocate device memory

@@ -107,6 +107,41 @@ __device__ __forceinline__ uint32_t block_excl_count(uint32_t c) {
   return pre + x - c;
 }
 
+// A select's first digit counted by the kernel that produces its keys
+// (select_kth_first): each block counts into shared memory, then adds its
+// nonzero counts to h0.  h0 == nullptr: nothing is counted.
+constexpr int FH_WORDS = 4096;  // rows * bins of one block's counts
+struct FirstHist {
+  uint32_t* h0;
+  int rows, shift, bins, radix;
+};
+inline FirstHist first_hist(uint32_t* h0, int n_queries, int rows) {
+  FirstHist f;
+  f.shift = select_first_shift(n_queries);
+  f.bins = 1 << (32 - f.shift);
+  f.radix = select_radix(n_queries);
+  f.rows = rows;
+  f.h0 = rows * f.bins <= FH_WORDS ? h0 : nullptr;
+  return f;
+}
+// every thread of the block calls (barriers inside)
+__device__ __forceinline__ void fh_clear(const FirstHist& f, uint32_t* sh) {
+  if (f.h0)
+    for (int i = threadIdx.x; i < f.rows * f.bins; i += TPB) sh[i] = 0u;
+  __syncthreads();
+}
+__device__ __forceinline__ void fh_count(const FirstHist& f, uint32_t* sh, int row, uint32_t key) {
+  if (f.h0 && row >= 0 && row < f.rows) atomicAdd(&sh[row * f.bins + (int)(key >> f.shift)], 1u);
+}
+__device__ __forceinline__ void fh_flush(const FirstHist& f, const uint32_t* sh) {
+  __syncthreads();
+  if (f.h0)
+    for (int i = threadIdx.x; i < f.rows * f.bins; i += TPB) {
+      const uint32_t c = sh[i];
+      if (c) atomicAdd(&f.h0[(i / f.bins) * f.radix + (i % f.bins)], c);
+    }
+}
+
 __device__ __forceinline__ float key_to_float(uint32_t k) {
   uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
   return __uint_as_float(u);
@@ -147,6 +182,8 @@ struct PruneWs {
   uint32_t* zkey;
   uint32_t* wkey;
   uint32_t* blk;  // per-block tie counts -> offsets
+  uint32_t* h0_tau;  // first-digit counts of the per-bin selection (k_pr_wkey)
+  uint32_t* h0_cap;  // first-digit counts of the cap's selection (k_pr_update)
   size_t bytes;
 };
 
@@ -160,6 +197,8 @@ PruneWs carve_prune(void* base, int64_t n) {
   w.zkey = c.take<uint32_t>(n);
   w.wkey = c.take<uint32_t>(n);
   w.blk = c.take<uint32_t>(n / TPB + 1);
+  w.h0_tau = c.take<uint32_t>(2 * FH_WORDS);  // covers select_radix(nq) * nq whenever counted
+  w.h0_cap = c.take<uint32_t>(select_radix(1));
   w.bytes = c.off + 256;
   return w;
 }
@@ -188,14 +227,24 @@ __global__ void k_pr_seen(int64_t n, const uint8_t* __restrict__ seen, const flo
 }
 
 // order keys of w_max for the per-bin quantiles and the cap
-__global__ void k_pr_wkey(int64_t n, const float* __restrict__ w_max, uint32_t* __restrict__ wkey) {
+// order keys of w_max; the per-bin selection's first digit is counted here (row = depth bin)
+__global__ void k_pr_wkey(int64_t n, const float* __restrict__ w_max, const uint16_t* __restrict__ grp,
+                          uint32_t* __restrict__ wkey, const FirstHist fh) {
+  __shared__ uint32_t sh[FH_WORDS];
+  fh_clear(fh, sh);
   const int64_t i0 = first_item();
   float wv[IPT];
+  uint16_t gv[IPT];
   load4(w_max, i0, n, wv, 0.f);
+  load4(grp, i0, n, gv, GROUP_NONE);
   uint32_t wk[IPT];
 #pragma unroll
-  for (int u = 0; u < IPT; ++u) wk[u] = order_key(wv[u]);
+  for (int u = 0; u < IPT; ++u) {
+    wk[u] = order_key(wv[u]);
+    if (gv[u] != GROUP_NONE) fh_count(fh, sh, gv[u], wk[u]);  // padding reads GROUP_NONE
+  }
   store4(wkey, i0, n, wk);
+  fh_flush(fh, sh);
 }
 
 __global__ void k_pr_pct_queries(SelectQuery* q, const PruneState* st, uint32_t lo_ppm, uint32_t hi_ppm,
@@ -291,7 +340,10 @@ struct Halo {
 
 __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const uint32_t* __restrict__ wkey,
                             const SelectQuery* tau, float alpha, float oma, float m_low, float m_high, float* ema_m,
-                            uint8_t* state, const Halo halo, uint8_t* mask, uint16_t* cand_grp, PruneState* st) {
+                            uint8_t* state, const Halo halo, uint8_t* mask, uint16_t* cand_grp, PruneState* st,
+                            const FirstHist fh) {
+  __shared__ uint32_t sh[FH_WORDS];
+  fh_clear(fh, sh);
   const int64_t i0 = first_item();
   uint16_t gv[IPT];
   uint32_t kv[IPT];
@@ -326,6 +378,7 @@ __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const u
     cg[u] = cand ? 0 : GROUP_NONE;
     mk[u] = cand ? 1 : 0;
     c += cand ? 1u : 0u;
+    if (cand) fh_count(fh, sh, 0, kv[u]);  // the cap's selection among the candidates
   }
   // unseen voxels keep their EMA and state: the stores write their loaded values back
   store4(ema_m, i0, n, mv);
@@ -335,6 +388,7 @@ __global__ void k_pr_update(int64_t n, const uint16_t* __restrict__ grp, const u
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const uint32_t bl = block_total(c);
   if (threadIdx.x == 0 && bl) atomicAdd(&st->n_cand, bl);
+  fh_flush(fh, sh);
 }
 
 __global__ void k_pr_cap_query(SelectQuery* q, PruneState* st, uint32_t cap, void* sel_tmp) {
@@ -437,6 +491,8 @@ struct SubWs {
   uint32_t* blk;       // per-block tie counts -> offsets
   uint32_t* blk_surv;  // per-block survivor counts (k_sd_select)
   uint32_t* blk_sel;   // per-block parent counts (k_sd_select)
+  uint32_t* h0_pct;    // first-digit counts of the percentiles' selection (k_sd_flags)
+  uint32_t* h0_top;    // first-digit counts of the top-k selection (k_sd_priority)
   unsigned long long* totals;
   void* scan_tmp;
   size_t bytes;
@@ -458,6 +514,8 @@ SubWs carve_sub(void* base, int64_t n) {
   w.blk = c.take<uint32_t>(n / TPB + 1);
   w.blk_surv = c.take<uint32_t>(n / EB + 1);
   w.blk_sel = c.take<uint32_t>(n / EB + 1);
+  w.h0_pct = c.take<uint32_t>(2 * select_radix(2));
+  w.h0_top = c.take<uint32_t>(select_radix(1));
   w.totals = c.take<unsigned long long>(4);
   w.scan_tmp = c.take<char>(scan2_tmp_bytes());
   w.bytes = c.off + 256;
@@ -465,7 +523,10 @@ SubWs carve_sub(void* base, int64_t n) {
 }
 
 __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const uint8_t* __restrict__ pm,
-                           const float* __restrict__ z, uint16_t* grp, uint32_t* zkey, SubState* st) {
+                           const float* __restrict__ z, uint16_t* grp, uint32_t* zkey, SubState* st,
+                           const FirstHist fh) {
+  __shared__ uint32_t sh[FH_WORDS];
+  fh_clear(fh, sh);
   const int64_t i0 = first_item();
   uint8_t pv[IPT] = {0, 0, 0, 0}, sv[IPT];
   float zv[IPT];
@@ -482,6 +543,7 @@ __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const ui
     zk[u] = order_key(zv[u]);
     c += (alive && i0 + u < n) ? 1u : 0u;
     c0 += gv[u] == 0 ? 1u : 0u;
+    if (gv[u] == 0) fh_count(fh, sh, 0, zk[u]);  // the depth percentiles' selection
   }
   store4(grp, i0, n, gv);
   store4(zkey, i0, n, zk);
@@ -490,11 +552,16 @@ __global__ void k_sd_flags(int64_t n, const uint8_t* __restrict__ seen, const ui
   const uint32_t b = block_total(c), b0 = block_total(c0);
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_alive, b);
   if (threadIdx.x == 0 && b0) atomicAdd(&st->n_el, b0);
+  fh_flush(fh, sh);
 }
 
+// both percentiles are queries of group 0: the flags kernel counted the first digit into row 0 of h0
+// (when h0 is not null), and row 1 gets a copy
 __global__ void k_sd_pct_queries(SelectQuery* q, uint32_t lo_ppm, uint32_t hi_ppm, const uint32_t* counter,
-                                 void* sel_tmp) {
+                                 void* sel_tmp, uint32_t* h0) {
   select_prepare(q, 2, sel_tmp);
+  if (h0)
+    for (int i = threadIdx.x; i < select_radix(2); i += blockDim.x) h0[select_radix(2) + i] = h0[i];
   if (threadIdx.x == 0) {
     uint32_t m = *counter;
     q[0].group = 0; q[0].k = rank_ppm(lo_ppm, m);
@@ -514,7 +581,9 @@ __global__ void k_sd_pct_apply(const SelectQuery* pct, SubState* st, float* stat
 __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const uint8_t* __restrict__ level,
                               const float* __restrict__ delta, const float* __restrict__ z,
                               const float* __restrict__ u, float kappa, float beta, int l_max, uint16_t* grp,
-                              uint32_t* pkey, SubState* st) {
+                              uint32_t* pkey, SubState* st, const FirstHist fh) {
+  __shared__ uint32_t sh[FH_WORDS];
+  fh_clear(fh, sh);
   const int64_t i0 = first_item();
   const float p_lo = st->p_lo, p_hi = st->p_hi;
   uint16_t gv[IPT];
@@ -544,12 +613,14 @@ __global__ void k_sd_priority(int64_t n, const float4* __restrict__ geom, const 
     }
     gv[k] = el ? 0 : GROUP_NONE;
     c += el ? 1u : 0u;
+    if (el) fh_count(fh, sh, 0, pk[k]);  // the top-k selection
   }
   store4(pkey, i0, n, pk);
   store4(grp, i0, n, gv);
   // one atomic per block (a same-address atomic per warp serialises at the L2)
   const uint32_t b = block_total(c);
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_el, b);
+  fh_flush(fh, sh);
 }
 
 __global__ void k_sd_k(SelectQuery* q, SubState* st, uint32_t top_ppm, long long budget, void* sel_tmp) {
@@ -1144,11 +1215,15 @@ extern "C" lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_
   const float alpha = p->ema_alpha;
   const float oma = 1.0f - alpha;  // rounded to FP32 once, as the oracle does
   const int blocks = eblocks(n);  // IPT voxels per thread
-  k_pr_wkey<<<blocks, TPB, 0, s>>>(n, w_max, w.wkey);
+  // the two selections' first digits are counted by the kernels that write their keys
+  const FirstHist fh_tau = first_hist(w.h0_tau, nb, nb), fh_cap = first_hist(w.h0_cap, 1, 1);
+  zero_async(s, w.h0_tau, sizeof(uint32_t) * 2 * FH_WORDS, w.h0_cap, sizeof(uint32_t) * select_radix(1));
+  k_pr_wkey<<<blocks, TPB, 0, s>>>(n, w_max, w.grp, w.wkey, fh_tau);
   // the percentiles in q[0..1] are consumed: q is reused per bin
   k_pr_tau_queries<<<1, 256, 0, s>>>(w.q, w.st, nb, (uint32_t)p->q_ppm, p->anneal, (uint32_t)p->anneal_ppm,
                                      (uint32_t)p->relax_ppm, w.sel_tmp);
-  select_kth_prepared(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
+  if (fh_tau.h0) select_kth_first(w.wkey, w.grp, n, w.q, nb, w.h0_tau, w.sel_tmp, s);
+  else select_kth_prepared(w.wkey, w.grp, n, w.q, nb, w.sel_tmp, s);
   // candidates get their own group array (zkey is free now: reuse it as u16 storage)
   uint16_t* cand = (uint16_t*)w.zkey;
   Halo halo;
@@ -1160,10 +1235,10 @@ extern "C" lv_status lv_prune_finish(int64_t n, const float* w_max, const uint8_
   halo.edge_score = p->edge;
   halo.w_max = w_max;
   k_pr_update<<<blocks, TPB, 0, s>>>(n, w.grp, w.wkey, w.q, alpha, oma, p->m_low, p->m_high, ema_m, state, halo,
-                                      prune_mask, cand, w.st);
+                                      prune_mask, cand, w.st, fh_cap);
   SelectQuery* qc = w.q + SELECT_MAX_QUERIES - 2;  // cap threshold
   k_pr_cap_query<<<1, 256, 0, s>>>(qc, w.st, cap, w.sel_tmp);
-  select_kth_prepared(w.wkey, cand, n, qc, 1, w.sel_tmp, s);
+  select_kth_first(w.wkey, cand, n, qc, 1, w.h0_cap, w.sel_tmp, s);
   k_pr_ties<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, prune_mask, w.blk, w.st);
   k_pr_mask<<<blocks, TPB, 0, s>>>(n, w.wkey, qc, w.blk, w.st, prune_mask, d_n_pruned, cap);
   count_launch(7);
@@ -1234,21 +1309,25 @@ extern "C" lv_status lv_subdivide_select(const lv_voxels* in, const float* delta
   SubWs w = carve_sub(workspace, n);
   if (ws_bytes < w.bytes) { set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   cudaStream_t s = (cudaStream_t)stream;
-  zero_async(s, w.st, sizeof(SubState));
+  // the state, and the first-digit counts of the two selections (counted by the kernels that
+  // write their keys)
+  zero_async(s, w.st, sizeof(SubState), w.h0_pct, sizeof(uint32_t) * 2 * select_radix(2), w.h0_top,
+             sizeof(uint32_t) * select_radix(1));
   if (n == 0) {
     cudaMemsetAsync(w.totals, 0, 4 * sizeof(unsigned long long), s);
     if (d_n_new) cudaMemsetAsync(d_n_new, 0, sizeof(int64_t), s);
     return cuda_check(cudaGetLastError(), "lv_subdivide_select");
   }
   const int blocks = eblocks(n);  // IPT voxels per thread
-  k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st);
-  k_sd_pct_queries<<<1, 256, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, &w.st->n_el, w.sel_tmp);
-  select_kth_prepared(w.zkey, w.grp, n, w.q, 2, w.sel_tmp, s);
+  k_sd_flags<<<blocks, TPB, 0, s>>>(n, seen, prune_mask, z, w.grp, w.zkey, w.st, first_hist(w.h0_pct, 2, 1));
+  k_sd_pct_queries<<<1, 256, 0, s>>>(w.q, (uint32_t)p->lo_ppm, (uint32_t)p->hi_ppm, &w.st->n_el, w.sel_tmp,
+                                     w.h0_pct);
+  select_kth_first(w.zkey, w.grp, n, w.q, 2, w.h0_pct, w.sel_tmp, s);
   k_sd_pct_apply<<<1, 32, 0, s>>>(w.q, w.st, p->pct_state, p->pct_ema, 1.0f - p->pct_ema);
   k_sd_priority<<<blocks, TPB, 0, s>>>(n, (const float4*)in->geom, in->level, delta, z, u, p->kappa, p->beta,
-                                        p->l_max, w.grp, w.pkey, w.st);
+                                        p->l_max, w.grp, w.pkey, w.st, first_hist(w.h0_top, 1, 1));
   k_sd_k<<<1, 256, 0, s>>>(w.q, w.st, (uint32_t)p->top_ppm, (long long)p->budget, w.sel_tmp);
-  select_kth_prepared(w.pkey, w.grp, n, w.q + 2, 1, w.sel_tmp, s);
+  select_kth_first(w.pkey, w.grp, n, w.q + 2, 1, w.h0_top, w.sel_tmp, s);
   k_sd_ties<<<blocks, TPB, 0, s>>>(n, w.pkey, w.q + 2, w.grp, w.blk, w.st);
   k_sd_select<<<blocks, TPB, 0, s>>>(n, prune_mask, w.grp, w.pkey, w.q, w.blk, w.st, selected, w.surv, w.sel,
                                       w.blk_surv, w.blk_sel);

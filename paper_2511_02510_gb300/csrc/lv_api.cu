@@ -46,6 +46,35 @@ __global__ void k_zero(const ZeroRanges r) {
 }
 }  // namespace
 
+namespace {
+// lv_rows_scatter: the arrays' units (16-byte words or bytes) laid end to end
+struct RowsArg {
+  int n;
+  int word[LV_MAX_AUX];         // 1: 16-byte units, 0: bytes
+  int64_t upr[LV_MAX_AUX];      // units per row (a plain copy: all units in one row)
+  int64_t start[LV_MAX_AUX + 1];
+  char* dst[LV_MAX_AUX];
+  const char* src[LV_MAX_AUX];
+  int64_t row_bytes[LV_MAX_AUX];
+  const int64_t* idx[LV_MAX_AUX];
+};
+
+__global__ void k_rows_scatter(const __grid_constant__ RowsArg r) {
+  const int64_t total = r.start[r.n];
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
+    int a = 0;
+    while (a + 1 < r.n && u >= r.start[a + 1]) ++a;
+    const int64_t l = u - r.start[a], row = l / r.upr[a], k = l - row * r.upr[a];
+    const int64_t drow = r.idx[a] ? r.idx[a][row] : row;
+    if (r.word[a]) {
+      ((uint4*)(r.dst[a] + drow * r.row_bytes[a]))[k] = ((const uint4*)(r.src[a] + row * r.row_bytes[a]))[k];
+    } else {
+      r.dst[a][drow * r.row_bytes[a] + k] = r.src[a][row * r.row_bytes[a] + k];
+    }
+  }
+}
+}  // namespace
+
 void zero_async(cudaStream_t s, void* p0, size_t b0, void* p1, size_t b1, void* p2, size_t b2, void* p3,
                 size_t b3) {
   ZeroRanges r;
@@ -90,4 +119,46 @@ extern "C" lv_status lv_check_status(const int32_t* d_status, void* stream) {
   }
   if (h != LV_OK) lv::set_error("device status %d", h);
   return (lv_status)h;
+}
+
+extern "C" lv_status lv_rows_scatter(const lv_rows* arrays, int n_arrays, void* stream) {
+  using namespace lv;
+  if (n_arrays < 0 || n_arrays > LV_MAX_AUX || (n_arrays > 0 && !arrays)) {
+    set_error("n_arrays must be 0..%d", LV_MAX_AUX);
+    return LV_ERR_INVALID_ARG;
+  }
+  RowsArg r;
+  r.n = 0;
+  r.start[0] = 0;
+  for (int i = 0; i < n_arrays; ++i) {
+    const lv_rows& a = arrays[i];
+    if (a.m < 0 || a.row_bytes < 1 || (a.m > 0 && (!a.dst || !a.src))) {
+      set_error("array %d: bad description", i);
+      return LV_ERR_INVALID_ARG;
+    }
+    if (a.m == 0) continue;
+    const int k = r.n++;
+    const bool al = (((uintptr_t)a.dst | (uintptr_t)a.src) & 15) == 0;
+    r.dst[k] = (char*)a.dst;
+    r.src[k] = (const char*)a.src;
+    r.idx[k] = a.idx;
+    if (!a.idx) {  // a plain copy: one row of all the bytes
+      r.row_bytes[k] = a.m * a.row_bytes;
+      r.word[k] = al && r.row_bytes[k] % 16 == 0;
+      r.upr[k] = r.word[k] ? r.row_bytes[k] / 16 : r.row_bytes[k];
+      r.start[k + 1] = r.start[k] + r.upr[k];
+    } else {
+      r.row_bytes[k] = a.row_bytes;
+      r.word[k] = al && a.row_bytes % 16 == 0;
+      r.upr[k] = r.word[k] ? a.row_bytes / 16 : a.row_bytes;
+      r.start[k + 1] = r.start[k] + a.m * r.upr[k];
+    }
+  }
+  if (r.n == 0) return LV_OK;
+  const int64_t total = r.start[r.n];
+  const int64_t want = (total + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 4 * 1216 ? (want < 1 ? 1 : want) : 4 * 1216);
+  k_rows_scatter<<<blocks, 256, 0, (cudaStream_t)stream>>>(r);
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_rows_scatter");
 }

@@ -21,6 +21,10 @@ constexpr unsigned FULL = 0xffffffffu;
 void set_error(const char* fmt, ...);
 lv_status cuda_check(cudaError_t e, const char* what);
 void count_launch(int k = 1);
+// The weights, their per-view sums and the loss sums in a workspace of
+// lv_lf_weights for the given views (the forward's fused LF loss).
+lv_status lf_fused_buffers(const int32_t* widths, const int32_t* heights, int n_views, void* workspace,
+                           size_t ws_bytes, const float** w, const double** wsum, double** lsum);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

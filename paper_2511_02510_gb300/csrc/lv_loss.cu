@@ -206,11 +206,13 @@ __global__ void k_lf_loss4(const float* __restrict__ rgb, const float* __restric
   block_add_f64((double)acc, &lsum[v]);
 }
 
-__global__ void k_lf_finish(const __grid_constant__ ViewPix vp, const double* lsum, float* loss) {
+// clear: the sums are zeroed once read (the fused forward's sums start from zero next time)
+__global__ void k_lf_finish(const __grid_constant__ ViewPix vp, double* lsum, float* loss, bool clear) {
   int v = threadIdx.x;
   if (v < vp.n) {
     const long long np = vp.off[v + 1] - vp.off[v];
     loss[v] = np > 0 ? (float)(lsum[v] / (3.0 * (double)np)) : 0.f;
+    if (clear) lsum[v] = 0.0;
   }
 }
 
@@ -282,7 +284,8 @@ extern "C" lv_status lv_lf_weights(const float* gt, const int32_t* widths, const
   const int64_t P = vp.off[n_views];
   cudaStream_t s = (cudaStream_t)stream;
   const float gamma = lv_lf_gamma(t, p);
-  zero_async(s, w.wsum, sizeof(double) * LV_MAX_VIEWS);
+  // the weight sums, and the loss sums a forward with the fused loss accumulates
+  zero_async(s, w.wsum, sizeof(double) * LV_MAX_VIEWS, w.lsum, sizeof(double) * LV_MAX_VIEWS);
   k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
   k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);
   select_kth(w.mkey, w.grp, P, w.q, n_views, w.sel_tmp, s);
@@ -311,10 +314,36 @@ extern "C" lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, 
     if (vec) k_lf_loss4<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
     else k_lf_loss<<<blocks_for(np), TPB, 0, s>>>(rgb, gt, w.w, vp, v, w.wsum, w.lsum, dL_drgb);
   }
-  k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss);
+  k_lf_finish<<<1, LV_MAX_VIEWS, 0, s>>>(vp, w.lsum, loss, false);
   count_launch(1 + n_views);
   return cuda_check(cudaGetLastError(), "lv_lf_loss_from_weights");
 }
+
+extern "C" lv_status lv_lf_loss_finish(const int32_t* widths, const int32_t* heights, int n_views, float* loss,
+                                       void* workspace, size_t ws_bytes, void* stream) {
+  if (!loss) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  ViewPix vp;
+  LfWs w;
+  lv_status e = lf_setup(widths, heights, n_views, 990000, workspace, ws_bytes, &vp, &w);
+  if (e != LV_OK) return e;
+  k_lf_finish<<<1, LV_MAX_VIEWS, 0, (cudaStream_t)stream>>>(vp, w.lsum, loss, true);
+  count_launch(1);
+  return cuda_check(cudaGetLastError(), "lv_lf_loss_finish");
+}
+
+namespace lv {
+lv_status lf_fused_buffers(const int32_t* widths, const int32_t* heights, int n_views, void* workspace,
+                           size_t ws_bytes, const float** w_out, const double** wsum, double** lsum) {
+  ViewPix vp;
+  LfWs w;
+  lv_status e = lf_setup(widths, heights, n_views, 990000, workspace, ws_bytes, &vp, &w);
+  if (e != LV_OK) return e;
+  *w_out = w.w;
+  *wsum = w.wsum;
+  *lsum = w.lsum;
+  return LV_OK;
+}
+}  // namespace lv
 
 extern "C" lv_status lv_lf_weighted_loss(const float* rgb, const float* gt, const int32_t* widths,
                                          const int32_t* heights, int n_views, float t, const lv_lf_params* p,

@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(Os<K>::THREADS, Os<K>::MIN_BLOCKS) k_os_pass(c
       const int64_t g = s_off[(uint32_t)(kk >> shift) & (RADIX - 1)] + q;
       kout[g] = kk;
       vout[g] = s_v[q];
-      if (key_ranges) {
+      if constexpr (sizeof(K) == 4) if (key_ranges) {
         // items of one digit are consecutive here and in the output, so a key's first and last
         // item in this tile bound its positions; the extremes over all tiles are its range
         if (q == 0 || s_k[q - 1] != kk) atomicMin(&key_ranges[2 * (uint64_t)kk], (uint32_t)g);
@@ -786,11 +786,11 @@ __global__ void k_sel_init(SelectQuery* q, int nq, uint32_t* hist, int hist_word
 
 template <int RADIX>
 void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int nq,
-                   uint32_t* hist, SelectQuery* qs, int key_bits, int width, cudaStream_t s) {
+                   uint32_t* hist, SelectQuery* qs, int key_bits, int width, cudaStream_t s, uint32_t* h0) {
   // enough blocks to keep many loads in flight; fewer when every block must
   // clear and flush a large histogram (wide digits or many queries)
   const int64_t want = (n + SEL_THREADS * SEL_ITEMS - 1) / (SEL_THREADS * SEL_ITEMS);
-  const int64_t cap_blocks = nq * RADIX <= 512 ? 2048 : 2 * SEL_BLOCKS;
+  const int64_t cap_blocks = nq * RADIX <= 512 ? 2048 : SEL_BLOCKS;
   int blocks = (int)(want < cap_blocks ? want : cap_blocks);
   if (blocks < 1) blocks = 1;
   const size_t smem = sizeof(uint32_t) * RADIX * nq;
@@ -801,9 +801,16 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
   });
   // three histogram buffers: pass p writes H[p % 3], reads H[(p - 1) % 3] for its pick step and
   // clears H[(p + 1) % 3] for pass p + 1 (k_sel_init cleared H[0]); the queries after p picks
-  // are A[p]: A[0] = d_queries, then the two scratch copies in turn; the last pick writes d_queries
+  // are A[p]: A[0] = d_queries, then the two scratch copies in turn; the last pick writes d_queries.
+  // With h0, the key producer has counted the first digit into H[0] = h0 and the query kernel
+  // cleared H[1]; the passes and the last pick leave h0 cleared.
   const int words = nq * RADIX;
   uint32_t* H[3] = {hist, hist + words, hist + 2 * words};
+  if (h0) {
+    H[0] = h0;
+    H[1] = hist;
+    H[2] = hist + words;
+  }
   auto A = [&](int p) { return p == 0 ? d_queries : qs + ((p - 1) % 2) * nq; };
   // digits from the top: the first one takes the remainder bits, the rest `width` each
   const int npass = (key_bits + width - 1) / width;
@@ -811,13 +818,14 @@ void select_passes(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQ
   for (int p = 0; p < npass; ++p) {
     const int wbits = p == 0 ? key_bits - width * (npass - 1) : width;
     shift -= wbits;
-    k_sel_hist<RADIX><<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, A(p > 0 ? p - 1 : 0), nq, shift, wbits,
-                                                        H[p % 3], p > 0 ? H[(p - 1) % 3] : nullptr, prev_shift,
-                                                        p > 0 ? A(p) : nullptr, H[(p + 1) % 3], words);
+    if (p > 0 || !h0)
+      k_sel_hist<RADIX><<<blocks, SEL_THREADS, smem, s>>>(keys, grp, n, A(p > 0 ? p - 1 : 0), nq, shift, wbits,
+                                                          H[p % 3], p > 0 ? H[(p - 1) % 3] : nullptr, prev_shift,
+                                                          p > 0 ? A(p) : nullptr, H[(p + 1) % 3], words);
     prev_shift = shift;
   }
   k_sel_pick<RADIX><<<(nq + 7) / 8, 256, 0, s>>>(A(npass - 1), d_queries, nq, 0, H[(npass - 1) % 3]);
-  count_launch(npass + 1);
+  count_launch(npass + (h0 ? 0 : 1));
 }
 
 }  // namespace
@@ -831,7 +839,7 @@ size_t select_tmp_bytes(int n_queries) {
 
 // the digit passes and the last pick, after the queries and the first histogram buffer are set up
 static void select_run(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
-                       void* tmp, cudaStream_t s) {
+                       void* tmp, cudaStream_t s, uint32_t* h0) {
   const bool wide = n_queries <= SEL_WIDE_MAX_Q;
   const int words = select_hist_words(n_queries);
   uint32_t* hist = (uint32_t*)tmp;
@@ -842,20 +850,25 @@ static void select_run(const uint32_t* keys, const uint16_t* grp, int64_t n, Sel
     key_bits = 1;
     while (key_bits < 32 && ((int64_t)1 << key_bits) < n) ++key_bits;
   }
-  if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 11, s);
-  else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 8, s);
+  if (wide) select_passes<2048>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 11, s, h0);
+  else select_passes<256>(keys, grp, n, d_queries, n_queries, hist, qs, key_bits, 8, s, h0);
 }
 
 void select_kth(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
                 void* tmp, cudaStream_t s) {
   k_sel_init<<<1, 256, 0, s>>>(d_queries, n_queries, (uint32_t*)tmp, select_hist_words(n_queries));
   count_launch(1);
-  select_run(keys, grp, n, d_queries, n_queries, tmp, s);
+  select_run(keys, grp, n, d_queries, n_queries, tmp, s, nullptr);
 }
 
 void select_kth_prepared(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries,
                          int n_queries, void* tmp, cudaStream_t s) {
-  select_run(keys, grp, n, d_queries, n_queries, tmp, s);
+  select_run(keys, grp, n, d_queries, n_queries, tmp, s, nullptr);
+}
+
+void select_kth_first(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                      uint32_t* h0, void* tmp, cudaStream_t s) {
+  select_run(keys, grp, n, d_queries, n_queries, tmp, s, h0);
 }
 
 }  // namespace lv

@@ -78,4 +78,14 @@ __device__ __forceinline__ void select_prepare(SelectQuery* q, int n_queries, vo
 void select_kth_prepared(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries,
                          int n_queries, void* tmp, cudaStream_t s);
 
+// select_kth_prepared whose first digit's histogram the kernel producing the
+// keys has already counted into h0 (select_radix(n) words per query row, row q
+// counting the items of query q's group at digit key >> select_first_shift(n)),
+// so the select runs one histogram pass less.  h0 must be zero before that
+// producer runs; the select leaves it zero again.  32-bit keys only.
+__host__ __device__ constexpr int select_radix(int n_queries) { return n_queries <= SEL_WIDE_MAX_Q ? 2048 : 256; }
+__host__ __device__ constexpr int select_first_shift(int n_queries) { return n_queries <= SEL_WIDE_MAX_Q ? 22 : 24; }
+void select_kth_first(const uint32_t* keys, const uint16_t* grp, int64_t n, SelectQuery* d_queries, int n_queries,
+                      uint32_t* h0, void* tmp, cudaStream_t s);
+
 }  // namespace lv

@@ -1145,6 +1145,19 @@ __device__ __forceinline__ uint32_t next_item(unsigned int* work, int lane) {
   return __shfl_sync(FULL, it, 0);
 }
 
+// A persistent grid limited to sm_cut of the n_sms SMs (0: all) is launched at
+// full size; a block that lands on an SM outside the first sm_cut (by SM id,
+// scaled to the id range) returns at once, so the kept SMs hold their full
+// share of blocks and the others stay free for concurrent streams.  The work
+// counter hands every item to the blocks that stay.
+__device__ __forceinline__ bool sm_excluded(int sm_cut, int n_sms) {
+  if (sm_cut <= 0) return false;
+  uint32_t smid, nsmid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+  return (unsigned long long)smid * (unsigned)n_sms >= (unsigned long long)sm_cut * nsmid;
+}
+
 // ------------------------------------------------------------------ forward composite
 // Each warp walks its strip's tile list on its own: CH list entries at a time
 // (the batch: 32, 64 or 128, CH / 32 per lane, all loads of a batch issued
@@ -1194,6 +1207,19 @@ __device__ __forceinline__ int stage_batch(uint32_t base, uint32_t end, int lane
   }
   return m;
 }
+// The LF-weighted loss fused into the forward composite (Sec. IV-B, Eq. 8 and
+// 18): per pixel dL/drgb = 2 / (3 |P_v|) * (w / <w>) * (rgb - gt), in the
+// operation order lv_lf_loss_from_weights uses, and the view's summed
+// weighted squared error (FP32 per warp, FP64 per block in shared memory, one
+// global FP64 atomic per block and view).  dL == nullptr: not fused.
+struct LfFuse {
+  const float* gt;     // [P][3]
+  const float* w;      // [P] unnormalised weights (lv_lf_weights)
+  const double* wsum;  // [views] their sums
+  double* lsum;        // [views] loss sums
+  float* dL;           // [P][3]
+};
+
 template <int TS>
 constexpr int min_blocks() { return TS == 16 ? 5 : (TS == 8 ? 16 : 1); }
 
@@ -1206,10 +1232,16 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
                                                 uint32_t* __restrict__ n_samples, float* __restrict__ tau_out,
                                                 unsigned long long* __restrict__ wmax, unsigned int* work,
-                                                uint32_t n_items) {
+                                                uint32_t n_items, const LfFuse lf, int sm_cut, int n_sms) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
+  __shared__ double s_lf[LV_MAX_VIEWS];
+  if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (lf.dL) {  // grid-uniform
+    for (int v = tid; v < LV_MAX_VIEWS; v += TS * TS) s_lf[v] = 0.0;
+    __syncthreads();
+  }
   float4* wr = (float4*)((char*)smem_f4 + fwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
   uint32_t* w_ent = w_vox + CH;
@@ -1282,7 +1314,31 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
       if (n_samples) n_samples[p] = nsamp;
       tau_out[p] = tau;
     }
+    if (lf.dL) {  // grid-uniform
+      float part = 0.f;
+      if (inside) {
+        const size_t p = (size_t)gid;
+        const double np = (double)c.W * (double)c.H;
+        const float mean = (float)(lf.wsum[view] / np);
+        const float gscale = (float)(2.0 / (3.0 * np));
+        const float wt = lf.w[p] / mean;
+        const float r0 = cr - lf.gt[3 * p], r1 = cg - lf.gt[3 * p + 1], r2 = cb - lf.gt[3 * p + 2];
+        part = wt * (r0 * r0 + r1 * r1 + r2 * r2);
+        const float cf = gscale * wt;
+        lf.dL[3 * p + 0] = cf * r0;
+        lf.dL[3 * p + 1] = cf * r1;
+        lf.dL[3 * p + 2] = cf * r2;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      if (lane == 0 && part != 0.f) atomicAdd(&s_lf[view], (double)part);
+    }
     __syncwarp();  // the slice is reused by the next item
+  }
+  if (lf.dL) {
+    __syncthreads();
+    for (int v = tid; v < vs.n; v += TS * TS)
+      if (s_lf[v] != 0.0) atomicAdd(&lf.lsum[v], s_lf[v]);
   }
 }
 
@@ -1333,9 +1389,11 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
                                                 const uint32_t* __restrict__ n_contrib,
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
-                                                float4* __restrict__ d_rgb, unsigned int* work, uint32_t n_items) {
+                                                float4* __restrict__ d_rgb, unsigned int* work, uint32_t n_items,
+                                                int sm_cut, int n_sms) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
+  if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* wr = (float4*)((char*)smem_f4 + bwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
@@ -1450,7 +1508,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
 // views; the 32 rows leave through shared memory as coalesced 16-byte stores
 // (row stride 49 floats: conflict-free per lane).  With `accumulate`, warps
 // without any visible voxel touch nothing.
-__global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom, int sh_nb, int64_t n,
+__global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ rec, int sh_nb, int64_t n,
                                                 const __grid_constant__ ViewSet vs,
                                                 const uint32_t* __restrict__ vis, const uint32_t* __restrict__ slot,
                                                 float4* __restrict__ d_rgb, float* __restrict__ d_sh,
@@ -1472,11 +1530,12 @@ __global__ void __launch_bounds__(128) k_sh_bwd(const float4* __restrict__ geom,
       const int64_t i = (int64_t)view * n + vox;  // view-major items
       if (!vis[i]) continue;
       any_vis = true;
-      const DevView& c = vs.v[view];
       const uint32_t s = slot[i];
-      const float4 g = geom[vox];
+      // the record holds the centre relative to this view's camera, as k_emit computed it, so the
+      // voxel arrays are not read (a topology change may rewrite them meanwhile)
+      const float4 g = rec[4 * (int64_t)s];
       float dir[3];
-      unit_dir(g.x - c.o[0], g.y - c.o[1], g.z - c.o[2], dir);
+      unit_dir(g.x, g.y, g.z, dir);
       float Y[16];
       sh_basis(dir[0], dir[1], dir[2], Y);
       const float4 dc = d_rgb[s];
@@ -1713,18 +1772,15 @@ static int persistent_blocks(K kernel, int threads, size_t smem) {
 }
 
 // a persistent grid of pb blocks over all SMs, cut to sm_limit SMs (0: all)
-static int limit_to_sms(int pb, int sm_limit, int dev) {
-  if (sm_limit <= 0) return pb;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0 || sm_limit >= sms) return pb;
-  const int per_sm = pb / sms > 0 ? pb / sms : 1;
-  return per_sm * sm_limit;
+// the SM count, and the cut for a persistent grid limited to sm_limit SMs (0: no limit)
+static void sm_limits(int sm_limit, int dev, int* sms, int* sm_cut) {
+  cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  *sm_cut = (sm_limit > 0 && *sms > 0 && sm_limit < *sms) ? sm_limit : 0;
 }
 
 template <int TS, bool SEG, bool PERSIST, int CH>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                         float t_stop, const lv_fwd_out* out, int sm_limit) {
+                         float t_stop, const lv_fwd_out* out, int sm_limit, const LfFuse& lf) {
   const size_t smem = fwd_slice(CH) * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
@@ -1733,14 +1789,16 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
     cudaFuncSetAttribute(k_fwd<TS, SEG, PERSIST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_fwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   });
-  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
-  if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
+  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_fwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
+  int sms = 0, sm_cut = 0;
+  sm_limits(sm_limit, dev, &sms, &sm_cut);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) grid = (unsigned)(tiles < pb ? tiles : pb);  // work[0] was cleared at the start of the forward
   k_fwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
-                                                       out->n_samples, w.tau, out->wmax_packed, w.work, n_items);
+                                                       out->n_samples, w.tau, out->wmax_packed, w.work, n_items,
+                                                       lf, sm_cut, sms);
 }
 
 template <int TS, bool SEG, bool PERSIST, int CH>
@@ -1755,8 +1813,9 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
     cudaFuncSetAttribute(k_bwd<TS, SEG, PERSIST, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (PERSIST && dev < 64) pblocks[dev] = persistent_blocks(k_bwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
   });
-  int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
-  if (PERSIST) pb = limit_to_sms(pb, sm_limit, dev);
+  const int pb = dev < 64 ? pblocks[dev] : persistent_blocks(k_bwd<TS, SEG, PERSIST, CH>, TS * TS, smem);
+  int sms = 0, sm_cut = 0;
+  sm_limits(sm_limit, dev, &sms, &sm_cut);
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
@@ -1765,7 +1824,7 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   }
   k_bwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
                                                        w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
-                                                       n_items);
+                                                       n_items, sm_cut, sms);
 }
 
 // tile size, batch, density model (midpoint, or the exact-segment variant) and scheduling
@@ -1810,14 +1869,14 @@ static void launch_tile_sort(const FwdWs& w, int64_t tiles, int64_t pair_cap, cu
 }
 
 static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
-                       const uint32_t* sv, const lv_fwd_out* out) {
+                       const uint32_t* sv, const lv_fwd_out* out, const LfFuse& lf) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
   const int sml = per ? o->persistent_sms : 0;
-#define LV_FWD_CH(TS, CH)                                                                       \
-  if (seg && per) launch_fwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);   \
-  else if (seg) launch_fwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0);      \
-  else if (per) launch_fwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);    \
-  else launch_fwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0)
+#define LV_FWD_CH(TS, CH)                                                                           \
+  if (seg && per) launch_fwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml, lf);   \
+  else if (seg) launch_fwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0, lf);      \
+  else if (per) launch_fwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml, lf);    \
+  else launch_fwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0, lf)
 #define LV_FWD(TS)                                   \
   if (o->batch == 64) { LV_FWD_CH(TS, 64); }         \
   else if (o->batch == 128) { LV_FWD_CH(TS, 128); }  \
@@ -1884,6 +1943,19 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
+  LfFuse lf = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (out->lf_workspace) {
+    if (!out->lf_gt || !out->lf_dL) { set_error("the fused LF loss needs lf_gt and lf_dL"); return LV_ERR_INVALID_ARG; }
+    int32_t wd[LV_MAX_VIEWS], ht[LV_MAX_VIEWS];
+    for (int v = 0; v < n_views; ++v) {
+      wd[v] = cams[v].width;
+      ht[v] = cams[v].height;
+    }
+    lv_status e = lf_fused_buffers(wd, ht, n_views, out->lf_workspace, out->lf_ws_bytes, &lf.w, &lf.wsum, &lf.lsum);
+    if (e != LV_OK) return e;
+    lf.gt = out->lf_gt;
+    lf.dL = out->lf_dL;
+  }
   const int64_t n = vox->n, items = n * n_views;
   // counters, the fallback status word and the work counters of the persistent kernels
   // (k_tile_sort_warp writes every tile's range)
@@ -1926,7 +1998,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     else
       cudaEventRecord((cudaEvent_t)out->composite_event, s);
   }
-  launch_fwd(opts, tiles, s, vs, w, sv, out);
+  if (out->lf_wait_event) cudaStreamWaitEvent(s, (cudaEvent_t)out->lf_wait_event, 0);  // the LF weights
+  launch_fwd(opts, tiles, s, vs, w, sv, out, lf);
   count_launch(2);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
 }
@@ -1993,7 +2066,7 @@ static lv_status launch_sh_bwd(const lv_voxels* vox, const ViewSet& vs, const Fw
   if (n == 0) return LV_OK;
   const int nb = (vox->sh_degree + 1) * (vox->sh_degree + 1);
   const int blocks = (int)((n + 127) / 128);  // 4 warps x 32 voxels
-  k_sh_bwd<<<blocks, 128, 0, s>>>((const float4*)vox->geom, nb, n, vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
+  k_sh_bwd<<<blocks, 128, 0, s>>>(w.rec, nb, n, vs, w.vis, w.slot, w.d_rgb, d_sh, accumulate);
   count_launch(1);
   return LV_OK;
 }

@@ -52,7 +52,9 @@ class lv_raster_opts(C.Structure):
 class lv_fwd_out(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("wmax_packed", C.c_void_p), ("z_min", C.c_void_p), ("delta_min", C.c_void_p), ("seen", C.c_void_p),
-                ("n_samples", C.c_void_p), ("stats_event", C.c_void_p), ("composite_event", C.c_void_p)]
+                ("n_samples", C.c_void_p), ("stats_event", C.c_void_p), ("composite_event", C.c_void_p),
+                ("lf_gt", C.c_void_p), ("lf_workspace", C.c_void_p), ("lf_ws_bytes", C.c_size_t),
+                ("lf_dL", C.c_void_p), ("lf_wait_event", C.c_void_p)]
 
 
 class lv_prune_params(C.Structure):
@@ -68,6 +70,11 @@ class lv_subdiv_params(C.Structure):
     _fields_ = [("kappa", C.c_float), ("beta", C.c_float), ("top_ppm", C.c_int32), ("l_max", C.c_int32),
                 ("budget", C.c_int64), ("lo_ppm", C.c_int32), ("hi_ppm", C.c_int32),
                 ("pct_ema", C.c_float), ("pct_state", C.c_void_p)]
+
+
+class lv_rows(C.Structure):
+    _fields_ = [("dst", C.c_void_p), ("src", C.c_void_p), ("row_bytes", C.c_int64), ("idx", C.c_void_p),
+                ("m", C.c_int64)]
 
 
 class lv_aux_array(C.Structure):
@@ -131,6 +138,7 @@ SIGNATURES = {
                                       _P, _P]),
     "lv_subdivide_apply": (C.c_int, [_PV, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array), C.c_int, _PV, _P,
                                      _SZ, _P]),
+    "lv_rows_scatter": (C.c_int, [_P, C.c_int, _P]),
     "lv_subdivide_apply_inplace": (C.c_int, [_PV, C.c_int64, C.POINTER(lv_subdiv_params), C.POINTER(lv_aux_array),
                                              C.c_int, _P, _SZ, _P]),
     "lv_compact_workspace_size": (_SZ, [_I64]),
@@ -146,6 +154,7 @@ SIGNATURES = {
     "lv_lf_weighted_loss_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _P, _P]),
     "lv_lf_weights": (C.c_int, [_P, _P, _P, C.c_int, _F, C.POINTER(lv_lf_params), _P, _SZ, _P]),
     "lv_lf_loss_from_weights": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P, _SZ, _P]),
+    "lv_lf_loss_finish": (C.c_int, [_P, _P, C.c_int, _P, _P, _SZ, _P]),
     "lv_last_error": (C.c_char_p, []),
     "lv_version": (C.c_int32, []),
     "lv_launch_count": (C.c_int64, []),
@@ -239,16 +248,23 @@ def make_opts(tile=16, batch=32, t_stop=1e-4, sync_check=False, exact_segment=Fa
 
 
 def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, delta_min=None, seen=None,
-                 n_samples=None, stats_event=None, composite_event=None) -> lv_fwd_out:
+                 n_samples=None, stats_event=None, composite_event=None, lf=None) -> lv_fwd_out:
     """stats_event: a torch.cuda.Event (recorded once before, so that it exists) that the forward
     records as soon as the per-voxel statistics are final; composite_event: one it records right
-    before launching the composite."""
+    before launching the composite.  lf: (gt, lf workspace, dL[, event]) to fuse the LF-weighted
+    loss into the composite (after lv_lf_weights on that workspace, or after the event it is
+    followed by on another stream; lv_lf_loss_finish writes the loss)."""
     o = lv_fwd_out()
     o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
     o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)
     o.n_samples = _ptr(n_samples)
     o.stats_event = stats_event.cuda_event if stats_event is not None else None
     o.composite_event = composite_event.cuda_event if composite_event is not None else None
+    if lf is not None:
+        gt, ws, dL = lf[:3]
+        o.lf_gt, o.lf_workspace, o.lf_dL = _ptr(gt), _ptr(ws), _ptr(dL)
+        o.lf_ws_bytes = ws.numel() * ws.element_size()
+        o.lf_wait_event = lf[3].cuda_event if len(lf) > 3 and lf[3] is not None else None
     return o
 
 
@@ -500,6 +516,14 @@ def lv_lf_loss_from_weights(rgb, gt, widths, heights, loss, dL_drgb, workspace):
            "lv_lf_loss_from_weights")
 
 
+def lv_lf_loss_finish(widths, heights, loss, workspace):
+    """Per-view losses of a forward that fused the LF loss (make_fwd_out(lf=...)); clears the sums."""
+    w = (C.c_int32 * len(widths))(*widths)
+    h = (C.c_int32 * len(heights))(*heights)
+    _check(load().lv_lf_loss_finish(w, h, len(widths), _ptr(loss), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream()), "lv_lf_loss_finish")
+
+
 LV_LF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -509,3 +533,15 @@ def lv_lf_weighted_loss_noalloc(rgb, gt, widths, heights, t, params, loss, dL_dr
     h = (C.c_int32 * len(heights))(*heights)
     _check(load().lv_lf_weighted_loss_noalloc(_ptr(rgb), _ptr(gt), w, h, len(widths), float(t), C.byref(params),
                                               _ptr(loss), _ptr(dL_drgb), _stream()), "lv_lf_weighted_loss_noalloc")
+
+
+def lv_rows_scatter(items):
+    """items: (dst, src, idx) per array, torch tensors whose first dimension is the row: dst[idx[j]] =
+    src[j] (idx an int64 device tensor), or dst[:len(src)] = src when idx is None.  One launch."""
+    arr = (lv_rows * max(1, len(items)))()
+    for i, (dst, src, idx) in enumerate(items):
+        arr[i].dst, arr[i].src = _ptr(dst), _ptr(src)
+        arr[i].row_bytes = (src[0].numel() if src.dim() > 1 else 1) * src.element_size()
+        arr[i].idx = _ptr(idx) if idx is not None else None
+        arr[i].m = src.shape[0]
+    _check(load().lv_rows_scatter(arr, len(items), _stream()), "lv_rows_scatter")

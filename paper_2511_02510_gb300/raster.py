@@ -73,19 +73,21 @@ class RasterContext:
         """Zero w_max and reset z_min / delta_min / seen before a new accumulation window."""
         L.lv_reset_stats(self.wmax_packed, self.z_min, self.delta_min, self.seen)
 
-    def fwd_struct(self, stats=True, stats_event=None, composite_event=None):
+    def fwd_struct(self, stats=True, stats_event=None, composite_event=None, lf=None):
         return L.make_fwd_out(self.rgb, self.T, self.n_contrib, self.depth,
                               self.wmax_packed if stats else None, self.z_min if stats else None,
                               self.delta_min if stats else None, self.seen if stats else None,
-                              self.n_samples if stats else None, stats_event, composite_event)
+                              self.n_samples if stats else None, stats_event, composite_event, lf)
 
     # ---------------------------------------------------------------- calls
-    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None, composite_event=None):
+    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None, composite_event=None, lf=None):
         """Launch the forward pass (asynchronous).  Returns (rgb, depth, T).  stats_event (a
         torch.cuda.Event recorded once before) is recorded when the voxel statistics are final;
-        composite_event right before the composite is launched."""
+        composite_event right before the composite is launched; lf = (gt, LF workspace, dL_drgb)
+        fuses the LF-weighted loss's gradient into the composite (lv_lf_weights first on that
+        workspace, lv_lf_loss_finish after for the loss)."""
         L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts,
-                               self.fwd_struct(stats, stats_event, composite_event),
+                               self.fwd_struct(stats, stats_event, composite_event, lf),
                                self.workspace, self.pair_capacity, self.status)
         self.generation += 1
         return self.rgb, self.depth, self.T

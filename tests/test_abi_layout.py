@@ -13,7 +13,7 @@ from paper_2511_02510_gb300 import litevoxel as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = ["lv_voxels", "lv_camera", "lv_raster_opts", "lv_fwd_out", "lv_prune_params", "lv_subdiv_params",
-           "lv_aux_array", "lv_adam_params", "lv_lf_params"]
+           "lv_aux_array", "lv_adam_params", "lv_lf_params", "lv_rows"]
 # ctypes names that differ from the C field names (Python keywords)
 C_NAME = {("lv_aux_array", "in_"): "in"}
 

@@ -383,3 +383,14 @@ def test_autotune_rejects(lib):
            None, None, ADDR, 1 << 40, None)
     expect(lib, L.LV_ERR_INVALID_ARG, lib.lv_autotune, C.byref(v), cams, 1, C.byref(opts()), 1000, 3, None, None,
            None, ADDR, 1 << 40, None)
+
+
+def test_rows_scatter_argument_checks():
+    arr = (L.lv_rows * 17)()
+    assert L.load().lv_rows_scatter(arr, 17, None) == L.LV_ERR_INVALID_ARG
+    arr[0].m, arr[0].row_bytes = 5, 0  # a row of no bytes
+    arr[0].dst = arr[0].src = ADDR
+    assert L.load().lv_rows_scatter(arr, 1, None) == L.LV_ERR_INVALID_ARG
+    arr[0].row_bytes, arr[0].src = 4, None  # no source
+    assert L.load().lv_rows_scatter(arr, 1, None) == L.LV_ERR_INVALID_ARG
+    assert L.load().lv_rows_scatter(arr, 0, None) == L.LV_OK
