@@ -1030,7 +1030,7 @@ def run_ours(args, rank, world, local):
         # the kernels timed inside graph replays; their algorithmic bytes and FP32 operations
         names = {"composite": ("k_fwd (front-to-back composite, Eq. 2-5)", "a5_forward_composite"),
                  "backward": ("k_bwd (back-to-front composite, reverse of Eq. 2-4)", "a6_backward_composite"),
-                 "apply": ("k_ip_children + k_ip_holes (in-place topology change, Sec. IV-D)", "subdivide_inplace")}
+                 "apply": ("k_ip_children + k_ip_tail (in-place topology change, Sec. IV-D)", "subdivide_inplace")}
         fallback = {"composite": None, "backward": stage_ms["backward"], "apply": stage_ms["subdivide_inplace"]}
         kernels = {}
         for key, (label, stage) in names.items():

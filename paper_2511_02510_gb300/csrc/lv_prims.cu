@@ -481,7 +481,7 @@ int sort_passes(int end_bit) { return (end_bit + 7) / 8; }
 template <typename K>
 static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, K* k1, uint32_t* v1, void* tmp,
                         const unsigned long long* d_count, int64_t cap, int end_bit, int32_t* status,
-                        cudaStream_t s, uint32_t* key_ranges) {
+                        cudaStream_t s, uint32_t* key_ranges, bool counted) {
   int passes = sort_passes(end_bit);
   if (passes > (int)sizeof(K)) passes = (int)sizeof(K);
   if (passes == 0 || cap <= 0) return 0;
@@ -489,9 +489,11 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
   K* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
   const int64_t tiles = (cap + Os<K>::TILE - 1) / Os<K>::TILE;
-  zero_async(s, st.ghist, sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2));  // counts and tickets
-  const int hb = (int)min((int64_t)OS_HIST_BLOCKS, tiles);
-  k_os_hist<K><<<hb, OS_HIST_THREADS, 0, s>>>(kin, d_count, cap, passes, st.ghist, st.look[0]);
+  if (!counted) {
+    zero_async(s, st.ghist, sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2));  // counts and tickets
+    const int hb = (int)min((int64_t)OS_HIST_BLOCKS, tiles);
+    k_os_hist<K><<<hb, OS_HIST_THREADS, 0, s>>>(kin, d_count, cap, passes, st.ghist, st.look[0]);
+  }
   for (int p = 0; p < passes; ++p) {
     // pass 0 reads the input (kept intact unless it is k0 / v0), pass p writes buffer (p + 1) & 1
     const K* ks = p == 0 ? kin : kb[p & 1];
@@ -501,20 +503,31 @@ static int radix_sort_t(const K* kin, const uint32_t* vin, K* k0, uint32_t* v0, 
                                                        st.ticket, st.look[p & 1], st.look[(p + 1) & 1], status,
                                                        OS_SPIN_LIMIT, p == passes - 1 ? key_ranges : nullptr);
   }
-  count_launch(1 + passes);
+  count_launch((counted ? 0 : 1) + passes);
   return passes & 1;
 }
 
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     int32_t* status, cudaStream_t s, uint32_t* key_ranges) {
-  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, key_ranges);
+                     int32_t* status, cudaStream_t s, uint32_t* key_ranges, bool counted) {
+  return radix_sort_t<uint32_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, key_ranges,
+                                counted);
+}
+
+SortCountTargets sort_count_targets(void* tmp, int64_t cap) {
+  const SortTmp st = carve_sort(tmp, cap);
+  SortCountTargets t;
+  t.counts = st.ghist;
+  t.look0 = st.look[0];
+  t.tile = Os<uint32_t>::TILE;
+  t.zero_bytes = sizeof(uint32_t) * (OS_MAX_PASSES * RADIX + 2);
+  return t;
 }
 
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
                      int32_t* status, cudaStream_t s) {
-  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, nullptr);
+  return radix_sort_t<uint64_t>(kin, vin, k0, v0, k1, v1, tmp, d_count, cap, end_bit, status, s, nullptr, false);
 }
 
 // ---- bounded-wait check: one pass over two tiles where only the second tile's
@@ -579,7 +592,7 @@ namespace {
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_BLOCKS = 304;
 constexpr int SEL_MAX_Q_PER_GROUP = 2;
-constexpr int SEL_ITEMS = 4;        // items per thread per iteration, loads issued together
+constexpr int SEL_ITEMS = 16;       // items per thread per iteration, loads issued together
 
 // One warp per query: find the digit holding the k-th item (warp scan over
 // RADIX / 32 digits per lane) and extend the prefix; returns the updated query.

@@ -31,11 +31,26 @@ void scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* 
 // the [first, end) positions of every key k it places into key_ranges[2k] by
 // atomicMin and key_ranges[2k + 1] by atomicMax, so the caller sets them to
 // (0xffffffff, 0) beforehand and keys absent from the list keep those values.
+// counted (32-bit keys): the kernel that wrote the keys has already counted
+// every pass's digits -- see sort_count_targets -- so no counting kernel runs.
 size_t sort_tmp_bytes(int64_t cap);
 int sort_passes(int end_bit);
 int radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
-                     int32_t* status, cudaStream_t s, uint32_t* key_ranges = nullptr);
+                     int32_t* status, cudaStream_t s, uint32_t* key_ranges = nullptr, bool counted = false);
+
+// What a kernel that writes the 32-bit keys does for radix_sort_pairs(counted
+// = true) on the same tmp: the first `zero_bytes` of tmp are zero before it
+// runs; it adds 1 at counts[p * 256 + ((key >> 8 p) & 255)] for every key and
+// pass p < sort_passes(end_bit), and zeroes look0[0, ceil(items / tile) * 256)
+// for the items the sort will see.
+struct SortCountTargets {
+  uint32_t* counts;
+  unsigned long long* look0;
+  int tile;
+  size_t zero_bytes;
+};
+SortCountTargets sort_count_targets(void* tmp, int64_t cap);
 int radix_sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* k0, uint32_t* v0, uint64_t* k1,
                      uint32_t* v1, void* tmp, const unsigned long long* d_count, int64_t cap, int end_bit,
                      int32_t* status, cudaStream_t s);

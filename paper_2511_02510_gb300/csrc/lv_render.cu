@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
                                               const unsigned long long* __restrict__ counters, int64_t pair_cap,
                                               uint32_t* __restrict__ pair_tile, uint32_t* __restrict__ pair_slot,
                                               int32_t* status, uint2* __restrict__ ranges, int64_t tiles,
+                                              const SortCountTargets sc, int passes,
                                               float4* __restrict__ rec,
                                               float4* __restrict__ d_rgb, uint32_t* __restrict__ s_dkey,
                                               const uint32_t* __restrict__ vidx) {
@@ -412,6 +413,14 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
     ranges[x] = make_uint2(~0u, 0u);
   const uint32_t cn = in ? cnt[i] : 0u;  // nonzero exactly for the visible items
   const unsigned long long total = counters[0];
+  // the sort by tile's digit counts (every pass) are counted here, and its first look-back words cleared
+  __shared__ uint32_t s_cnt[4 * 256];
+  for (int x = threadIdx.x; x < passes * 256; x += 256) s_cnt[x] = 0u;
+  if (total <= (unsigned long long)pair_cap) {
+    const int64_t words = (int64_t)((total + sc.tile - 1) / sc.tile) * 256;
+    for (int64_t x = blockIdx.x * 256ll + threadIdx.x; x < words; x += (int64_t)gridDim.x * 256) sc.look0[x] = 0ull;
+  }
+  __syncthreads();
   if (total > (unsigned long long)pair_cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) report(status, LV_ERR_CAPACITY);
   } else {
@@ -446,12 +455,17 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ geom, c
         if (e < p_end) {
           const uint32_t q = (uint32_t)(e - pj);
           const uint32_t tx0 = jx & 0xffffu, wx = (jx >> 16) - tx0, ty0 = jy & 0xffffu;
-          pair_tile[e] = toff + (ty0 + q / wx) * tiles_x + tx0 + q % wx;
+          const uint32_t key = toff + (ty0 + q / wx) * tiles_x + tx0 + q % wx;
+          pair_tile[e] = key;
           pair_slot[e] = js;
+          for (int p = 0; p < passes; ++p) atomicAdd(&s_cnt[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
         }
       }
     }
   }
+  __syncthreads();
+  for (int x = threadIdx.x; x < passes * 256; x += 256)
+    if (s_cnt[x]) atomicAdd(&sc.counts[x], s_cnt[x]);
   if (!cn) return;
   const DevView& c = vs.v[view];
   const uint32_t s = slot[i];
@@ -1210,8 +1224,9 @@ __device__ __forceinline__ int stage_batch(uint32_t base, uint32_t end, int lane
 // The LF-weighted loss fused into the forward composite (Sec. IV-B, Eq. 8 and
 // 18): per pixel dL/drgb = 2 / (3 |P_v|) * (w / <w>) * (rgb - gt), in the
 // operation order lv_lf_loss_from_weights uses, and the view's summed
-// weighted squared error (FP32 per warp, FP64 per block in shared memory, one
-// global FP64 atomic per block and view).  dL == nullptr: not fused.
+// weighted squared error (FP32 per warp item, FP64 per warp in shared memory,
+// summed per block, one global FP64 atomic per block and view).  dL ==
+// nullptr: not fused.
 struct LfFuse {
   const float* gt;     // [P][3]
   const float* w;      // [P] unnormalised weights (lv_lf_weights)
@@ -1235,13 +1250,11 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                                 uint32_t n_items, const LfFuse lf, int sm_cut, int n_sms) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
-  __shared__ double s_lf[LV_MAX_VIEWS];
+  __shared__ double s_lf[NW][LV_MAX_VIEWS];  // each warp's loss sums (no atomics)
   if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (lf.dL) {  // grid-uniform
-    for (int v = tid; v < LV_MAX_VIEWS; v += TS * TS) s_lf[v] = 0.0;
-    __syncthreads();
-  }
+  if (lf.dL)  // grid-uniform; a warp clears and then adds to its own row only
+    for (int v = lane; v < LV_MAX_VIEWS; v += 32) s_lf[warp][v] = 0.0;
   float4* wr = (float4*)((char*)smem_f4 + fwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
   uint32_t* w_ent = w_vox + CH;
@@ -1262,6 +1275,15 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
     float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
     uint32_t last = 0, nsamp = 0;
     bool done = !inside;
+    // the fused loss's inputs, loaded now so that their latency hides behind the compositing
+    float lf_g0 = 0.f, lf_g1 = 0.f, lf_g2 = 0.f, lf_w = 0.f;
+    if (lf.dL && inside) {
+      const size_t p = (size_t)gid;
+      lf_g0 = lf.gt[3 * p];
+      lf_g1 = lf.gt[3 * p + 1];
+      lf_g2 = lf.gt[3 * p + 2];
+      lf_w = lf.w[p];
+    }
     for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += CH) {
       const int m = stage_batch<TS, CH>(base, end, lane, strip, svals, rec, rec_bb, slot_vox, wr, w_vox, w_ent,
                                         nullptr);
@@ -1315,14 +1337,21 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
       tau_out[p] = tau;
     }
     if (lf.dL) {  // grid-uniform
+      // the view's mean weight and gradient scale, rounded from FP64 as the loss kernel rounds them;
+      // one lane computes them (FP64 division is slow on this part)
+      float mean = 0.f, gscale = 0.f;
+      if (lane == 0) {
+        const double np = (double)c.W * (double)c.H;
+        mean = (float)(lf.wsum[view] / np);
+        gscale = (float)(2.0 / (3.0 * np));
+      }
+      mean = __shfl_sync(FULL, mean, 0);
+      gscale = __shfl_sync(FULL, gscale, 0);
       float part = 0.f;
       if (inside) {
         const size_t p = (size_t)gid;
-        const double np = (double)c.W * (double)c.H;
-        const float mean = (float)(lf.wsum[view] / np);
-        const float gscale = (float)(2.0 / (3.0 * np));
-        const float wt = lf.w[p] / mean;
-        const float r0 = cr - lf.gt[3 * p], r1 = cg - lf.gt[3 * p + 1], r2 = cb - lf.gt[3 * p + 2];
+        const float wt = lf_w / mean;
+        const float r0 = cr - lf_g0, r1 = cg - lf_g1, r2 = cb - lf_g2;
         part = wt * (r0 * r0 + r1 * r1 + r2 * r2);
         const float cf = gscale * wt;
         lf.dL[3 * p + 0] = cf * r0;
@@ -1331,14 +1360,17 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-      if (lane == 0 && part != 0.f) atomicAdd(&s_lf[view], (double)part);
+      if (lane == 0) s_lf[warp][view] += (double)part;
     }
     __syncwarp();  // the slice is reused by the next item
   }
   if (lf.dL) {
     __syncthreads();
-    for (int v = tid; v < vs.n; v += TS * TS)
-      if (s_lf[v] != 0.0) atomicAdd(&lf.lsum[v], s_lf[v]);
+    for (int v = tid; v < vs.n; v += TS * TS) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s_lf[w][v];
+      if (t != 0.0) atomicAdd(&lf.lsum[v], t);
+    }
   }
 }
 
@@ -1957,10 +1989,12 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     lf.dL = out->lf_dL;
   }
   const int64_t n = vox->n, items = n * n_views;
-  // counters, the fallback status word and the work counters of the persistent kernels
-  // (k_tile_sort_warp writes every tile's range)
+  // counters, the fallback status word, the work counters of the persistent kernels and the
+  // sort by tile's digit counts, which k_emit accumulates (k_tile_sort_warp writes every tile's range)
+  const SortCountTargets sc = sort_count_targets(w.sort_tmp, pair_capacity);
+  const int passes = std::min(sort_passes(tile_bits(tiles)), 4);
   zero_async(s, w.counters, 8 * sizeof(unsigned long long), d_status == w.status ? w.status : nullptr,
-             sizeof(int32_t), w.work, 8 * sizeof(unsigned int));
+             sizeof(int32_t), w.work, 8 * sizeof(unsigned int), sc.counts, sc.zero_bytes);
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
     const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
@@ -1973,7 +2007,8 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   k_emit<DT, ST><<<emit_blocks, 256, 0, s>>>((const float4*)vox->geom, (const DT*)vox->density, (const ST*)vox->sh, \
                                              nb, n, vs, w.cnt, w.rect, w.pbox, w.rec_bb, w.slot_vox, w.dkey,          \
                                              w.slot, w.poff, w.counters, pair_capacity, w.k0, w.v0, d_status,         \
-                                             (uint2*)w.ranges, tiles, w.rec, w.d_rgb, w.s_dkey, vox->vidx)
+                                             (uint2*)w.ranges, tiles, sc, passes, w.rec, w.d_rgb, w.s_dkey,   \
+                                             vox->vidx)
     if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_F32) LV_EMIT(float, float);
     else if (vox->density_dtype == LV_F16 && vox->sh_dtype == LV_F32) LV_EMIT(__half, float);
     else if (vox->density_dtype == LV_F32 && vox->sh_dtype == LV_BF16) LV_EMIT(float, __nv_bfloat16);
@@ -1985,7 +2020,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   }
   // stable sort by tile: each tile's list stays in item order; the last pass notes every tile's range
   radix_sort_pairs(w.k0, w.v0, w.k0, w.v0, w.k1, w.v1, w.sort_tmp, w.counters, pair_capacity, tile_bits(tiles),
-                   d_status, s, w.ranges);
+                   d_status, s, w.ranges, items > 0);
   // each tile's range, and its list front to back
   launch_tile_sort(w, tiles, pair_capacity, s);
   const uint32_t* sv = sorted_pair_slots(w, tiles);
