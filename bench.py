@@ -274,8 +274,8 @@ class Workload:
         they run beside the forward and the backward respectively (side streams at high priority,
         joined by events): the depth bins of the pruning start as soon as the forward has binned
         the voxels (its statistics event), the rest once w_max is out.  The LF loss's gradient is
-        fused into the forward composite (which waits for the weights), its value is finished on
-        the side stream.  The SH backward, which reads the forward's workspace and not the voxel
+        fused into the backward composite (which waits for the weights), its value is finished
+        after it.  The SH backward, which reads the forward's workspace and not the voxel
         arrays, runs beside the topology change and the restore.  The in-place topology
         change runs last, alone, then the restore.  ev: {"composite" | "backward" | "apply":
         (start, end)} timing events (external, so that they time graph replays)."""
@@ -297,9 +297,7 @@ class Workload:
             L.lv_lf_weights(self.gt, [W_IMG], [H_IMG], self.t_iter, self.lfp, self.lf_ws)
             e_w.record(sw)
         r.reset_stats()
-        # the LF loss's gradient is fused into the composite, which waits for the weights (e_w)
-        r.forward(self.vox, stats=True, stats_event=e_stats, composite_event=ev["composite"][0] if ev else None,
-                  lf=(self.gt, self.lf_ws, self.dL, e_w))
+        r.forward(self.vox, stats=True, stats_event=e_stats, composite_event=ev["composite"][0] if ev else None)
         if ev:
             ev["composite"][1].record(main)
         e_fwd.record(main)
@@ -308,7 +306,6 @@ class Workload:
             L.lv_prune_bins(r.seen, r.z_min, self.pp, self.pr_ws)
         sb.wait_event(e_fwd)
         with torch.cuda.stream(sb):
-            L.lv_lf_loss_finish([W_IMG], [H_IMG], self.loss, self.lf_ws)
             L.lv_unpack_wmax(r.wmax_packed, self.w_max, self.w_arg)
             L.lv_prune_finish(self.w_max, r.seen, r.z_min, self.ema, self.state, self.pp, self.pmask,
                               self.n_pruned, self.pr_ws)
@@ -317,10 +314,13 @@ class Workload:
             e_b.record(sb)
         if ev:
             ev["backward"][0].record(main)
-        L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, self.bwd_opts, r.fwd_struct(False), r.workspace,
-                                r.pair_capacity, self.dL, None, None, self.d_dens, None, True, r.status)
+        # the LF loss's gradient is fused into the backward composite, which waits for the weights (e_w)
+        L.lv_rasterize_backward(self.vox, r.cams_arr, r.n_views, self.bwd_opts,
+                                r.fwd_struct(False, lf=(self.gt, self.lf_ws, self.dL, e_w)), r.workspace,
+                                r.pair_capacity, None, None, None, self.d_dens, None, True, r.status)
         if ev:
             ev["backward"][1].record(main)
+        L.lv_lf_loss_finish([W_IMG], [H_IMG], self.loss, self.lf_ws)
         # the SH backward reads only the workspace, so it runs beside the in-place topology change;
         # it waits for the selection too, whose memory-bound chain it would otherwise slow down
         e_bwd.record(main)
@@ -1072,8 +1072,8 @@ def run_ours(args, rank, world, local):
                "roofline": roofline,
                "stages_ms": stage_ms, "eager_ms_per_step": eager_ms,
                "timing": "device time of K replays of the step captured in one CUDA graph (CUDA events); the "
-                         "step runs on four streams (LF weights beside the forward, whose composite fuses the LF "
-                         "loss's gradient; pruning and the subdivision selection beside the backward; the SH "
+                         "step runs on four streams (LF weights beside the forward; the backward composite fuses "
+                         "the LF loss's gradient; pruning and the subdivision selection beside the backward; the SH "
                          "backward beside the in-place topology change); every step ends by restoring the rows "
                          "its topology change overwrote and the pruning state (one lv_rows_scatter launch, "
                          "inside the timed region), so that all steps do the same work; stages_ms from K eager "

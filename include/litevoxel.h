@@ -149,23 +149,23 @@ typedef struct {
                                         composite alone; inside a stream capture it is recorded as an
                                         external event node (cudaEventRecordExternal), a timing mark
                                         of every replay rather than a dependency */
-  /* Optional LF-weighted loss fused into the composite (Sec. IV-B, Eq. 8 and
-   * 18), for a caller that ran lv_lf_weights for this forward's views (their
-   * widths and heights in camera order) and ordered it before the forward on
-   * the stream.  When lf_workspace is not NULL the composite also writes
-   * every pixel's dL/drgb into lf_dL -- bit for bit what
-   * lv_lf_loss_from_weights writes -- and adds the views' loss sums into the
-   * workspace (FP64, one atomic per block and view); lv_lf_loss_finish then
-   * writes the per-view losses.  lf_gt and lf_dL must then be non-NULL.  A
-   * wrong workspace size returns LV_ERR_WORKSPACE, mismatched views
-   * LV_ERR_INVALID_ARG. */
+  /* Optional LF-weighted loss fused into the backward composite (Sec. IV-B,
+   * Eq. 8 and 18), for a caller that ran lv_lf_weights for these views
+   * (their widths and heights in camera order).  The forward ignores these
+   * fields.  When lf_workspace is not NULL and lv_rasterize_backward gets
+   * dL_drgb = NULL, the backward computes every pixel's dL/drgb from rgb,
+   * lf_gt and the weights -- bit for bit what lv_lf_loss_from_weights writes
+   * -- uses it, writes it into lf_dL when that is not NULL, and adds the
+   * views' loss sums into the workspace (FP64, one atomic per block and view);
+   * lv_lf_loss_finish then writes the per-view losses.  A wrong workspace size
+   * returns LV_ERR_WORKSPACE, mismatched views LV_ERR_INVALID_ARG. */
   const float* lf_gt;                /* [P][3] ground truth, as given to lv_lf_weights */
   void* lf_workspace;                /* lv_lf_weights' workspace (256-byte aligned), or NULL */
   size_t lf_ws_bytes;
-  float* lf_dL;                      /* [P][3] dL/drgb output */
-  void* lf_wait_event;               /* cudaEvent_t (nullable): the stream waits for it right before the
-                                        composite, so lv_lf_weights can run on another stream beside
-                                        the binning and sorting (inside a stream capture: a dependency) */
+  float* lf_dL;                      /* [P][3] dL/drgb output (nullable) */
+  void* lf_wait_event;               /* cudaEvent_t (nullable): the backward's stream waits for it before
+                                        the composite, so lv_lf_weights can run on another stream
+                                        (inside a stream capture: a dependency) */
 } lv_fwd_out;
 
 /* ------------------------------------------------------------------ */
@@ -212,7 +212,8 @@ lv_status lv_workspace_counters(const void* workspace, size_t ws_bytes, int64_t*
  *   a_k = g_C . c_k + g_D t_mid_k,
  * then to the 8 corners through the trilinear weights (zero where the raw
  * density is negative) and to the SH through c = max(0, SH + 0.5).
- * dL_ddepth and dL_dT may be NULL.  d_density [n][8] and d_sh [n][48] are
+ * dL_ddepth and dL_dT may be NULL; dL_drgb too when fwd->lf_workspace fuses the
+ * LF loss (see lv_fwd_out).  d_density [n][8] and d_sh [n][48] are
  * FP32; with accumulate = 0 they are overwritten, else added to.  vox, cams,
  * n_views, opts, workspace and pair_capacity must be those of the forward
  * call (the workspace's colour-gradient scratch is reused).  With d_sh = NULL
@@ -556,11 +557,11 @@ lv_status lv_lf_loss_from_weights(const float* rgb, const float* gt, const int32
                                   int n_views, float* loss, float* dL_drgb, void* workspace, size_t ws_bytes,
                                   void* stream);
 
-/* The per-view losses of a forward that fused the LF loss (lv_fwd_out.lf_*):
+/* The per-view losses of a backward that fused the LF loss (lv_fwd_out.lf_*):
  * loss[v] = (the view's summed weighted squared error) / (3 |P_v|), the value
  * lv_lf_loss_from_weights writes up to the order of the FP64 sums.  Reads
  * and then clears the sums in `workspace` (lv_lf_weights clears them too), so
- * call it once per fused forward, after the forward on the stream.  loss:
+ * call it once per fused backward, after the backward on the stream.  loss:
  * device float[n_views]. */
 lv_status lv_lf_loss_finish(const int32_t* widths, const int32_t* heights, int n_views, float* loss,
                             void* workspace, size_t ws_bytes, void* stream);

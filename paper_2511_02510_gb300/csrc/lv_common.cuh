@@ -22,7 +22,7 @@ void set_error(const char* fmt, ...);
 lv_status cuda_check(cudaError_t e, const char* what);
 void count_launch(int k = 1);
 // The weights, their per-view sums and the loss sums in a workspace of
-// lv_lf_weights for the given views (the forward's fused LF loss).
+// lv_lf_weights for the given views (the backward's fused LF loss).
 lv_status lf_fused_buffers(const int32_t* widths, const int32_t* heights, int n_views, void* workspace,
                            size_t ws_bytes, const float** w, const double** wsum, double** lsum);
 

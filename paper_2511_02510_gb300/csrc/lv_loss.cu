@@ -206,7 +206,7 @@ __global__ void k_lf_loss4(const float* __restrict__ rgb, const float* __restric
   block_add_f64((double)acc, &lsum[v]);
 }
 
-// clear: the sums are zeroed once read (the fused forward's sums start from zero next time)
+// clear: the sums are zeroed once read (the fused backward's sums start from zero next time)
 __global__ void k_lf_finish(const __grid_constant__ ViewPix vp, double* lsum, float* loss, bool clear) {
   int v = threadIdx.x;
   if (v < vp.n) {
@@ -284,7 +284,7 @@ extern "C" lv_status lv_lf_weights(const float* gt, const int32_t* widths, const
   const int64_t P = vp.off[n_views];
   cudaStream_t s = (cudaStream_t)stream;
   const float gamma = lv_lf_gamma(t, p);
-  // the weight sums, and the loss sums a forward with the fused loss accumulates
+  // the weight sums, and the loss sums a backward with the fused loss accumulates
   zero_async(s, w.wsum, sizeof(double) * LV_MAX_VIEWS, w.lsum, sizeof(double) * LV_MAX_VIEWS);
   k_lf_sobel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, s>>>(gt, vp, w.grp, w.mkey);
   k_lf_queries<<<1, LV_MAX_VIEWS, 0, s>>>(w.q, vp);

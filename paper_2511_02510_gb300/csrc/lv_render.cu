@@ -1221,18 +1221,19 @@ __device__ __forceinline__ int stage_batch(uint32_t base, uint32_t end, int lane
   }
   return m;
 }
-// The LF-weighted loss fused into the forward composite (Sec. IV-B, Eq. 8 and
+// The LF-weighted loss fused into the backward composite (Sec. IV-B, Eq. 8 and
 // 18): per pixel dL/drgb = 2 / (3 |P_v|) * (w / <w>) * (rgb - gt), in the
 // operation order lv_lf_loss_from_weights uses, and the view's summed
 // weighted squared error (FP32 per warp item, FP64 per warp in shared memory,
-// summed per block, one global FP64 atomic per block and view).  dL ==
-// nullptr: not fused.
+// summed per block, one global FP64 atomic per block and view).  w == nullptr:
+// not fused.
 struct LfFuse {
+  const float* rgb;    // [P][3] the forward's image
   const float* gt;     // [P][3]
   const float* w;      // [P] unnormalised weights (lv_lf_weights)
   const double* wsum;  // [views] their sums
   double* lsum;        // [views] loss sums
-  float* dL;           // [P][3]
+  float* dL;           // [P][3] dL/drgb, also written out (nullable)
 };
 
 template <int TS>
@@ -1247,14 +1248,11 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
                                                 uint32_t* __restrict__ n_samples, float* __restrict__ tau_out,
                                                 unsigned long long* __restrict__ wmax, unsigned int* work,
-                                                uint32_t n_items, const LfFuse lf, int sm_cut, int n_sms) {
+                                                uint32_t n_items, int sm_cut, int n_sms) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
-  __shared__ double s_lf[NW][LV_MAX_VIEWS];  // each warp's loss sums (no atomics)
   if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (lf.dL)  // grid-uniform; a warp clears and then adds to its own row only
-    for (int v = lane; v < LV_MAX_VIEWS; v += 32) s_lf[warp][v] = 0.0;
   float4* wr = (float4*)((char*)smem_f4 + fwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
   uint32_t* w_ent = w_vox + CH;
@@ -1275,15 +1273,6 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
     float T = 1.f, tau = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f;
     uint32_t last = 0, nsamp = 0;
     bool done = !inside;
-    // the fused loss's inputs, loaded now so that their latency hides behind the compositing
-    float lf_g0 = 0.f, lf_g1 = 0.f, lf_g2 = 0.f, lf_w = 0.f;
-    if (lf.dL && inside) {
-      const size_t p = (size_t)gid;
-      lf_g0 = lf.gt[3 * p];
-      lf_g1 = lf.gt[3 * p + 1];
-      lf_g2 = lf.gt[3 * p + 2];
-      lf_w = lf.w[p];
-    }
     for (uint32_t base = start; base < end && !__all_sync(FULL, done); base += CH) {
       const int m = stage_batch<TS, CH>(base, end, lane, strip, svals, rec, rec_bb, slot_vox, wr, w_vox, w_ent,
                                         nullptr);
@@ -1336,41 +1325,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
       if (n_samples) n_samples[p] = nsamp;
       tau_out[p] = tau;
     }
-    if (lf.dL) {  // grid-uniform
-      // the view's mean weight and gradient scale, rounded from FP64 as the loss kernel rounds them;
-      // one lane computes them (FP64 division is slow on this part)
-      float mean = 0.f, gscale = 0.f;
-      if (lane == 0) {
-        const double np = (double)c.W * (double)c.H;
-        mean = (float)(lf.wsum[view] / np);
-        gscale = (float)(2.0 / (3.0 * np));
-      }
-      mean = __shfl_sync(FULL, mean, 0);
-      gscale = __shfl_sync(FULL, gscale, 0);
-      float part = 0.f;
-      if (inside) {
-        const size_t p = (size_t)gid;
-        const float wt = lf_w / mean;
-        const float r0 = cr - lf_g0, r1 = cg - lf_g1, r2 = cb - lf_g2;
-        part = wt * (r0 * r0 + r1 * r1 + r2 * r2);
-        const float cf = gscale * wt;
-        lf.dL[3 * p + 0] = cf * r0;
-        lf.dL[3 * p + 1] = cf * r1;
-        lf.dL[3 * p + 2] = cf * r2;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-      if (lane == 0) s_lf[warp][view] += (double)part;
-    }
     __syncwarp();  // the slice is reused by the next item
-  }
-  if (lf.dL) {
-    __syncthreads();
-    for (int v = tid; v < vs.n; v += TS * TS) {
-      double t = 0.0;
-      for (int w = 0; w < NW; ++w) t += s_lf[w][v];
-      if (t != 0.0) atomicAdd(&lf.lsum[v], t);
-    }
   }
 }
 
@@ -1422,11 +1377,14 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
                                                 float4* __restrict__ d_rgb, unsigned int* work, uint32_t n_items,
-                                                int sm_cut, int n_sms) {
+                                                int sm_cut, int n_sms, const LfFuse lf) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
+  __shared__ double s_lf[NW][LV_MAX_VIEWS];  // each warp's loss sums (fused LF loss; no atomics)
   if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (lf.w)  // grid-uniform; a warp clears and then adds to its own row only
+    for (int v = lane; v < vs.n; v += 32) s_lf[warp][v] = 0.0;
   float4* wr = (float4*)((char*)smem_f4 + bwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
   uint32_t* w_slot = w_vox + CH;
@@ -1450,11 +1408,44 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
       nc = n_contrib[p];
       tau = tau_in[p];
       Tf = T_fwd[p];
-      gr = dL_drgb[3 * p + 0];
-      gg = dL_drgb[3 * p + 1];
-      gb = dL_drgb[3 * p + 2];
+      if (!lf.w) {
+        gr = dL_drgb[3 * p + 0];
+        gg = dL_drgb[3 * p + 1];
+        gb = dL_drgb[3 * p + 2];
+      }
       if (dL_ddepth) gD = dL_ddepth[p];
       if (dL_dT) gT = dL_dT[p];
+    }
+    if (lf.w) {  // grid-uniform: dL/drgb of the LF-weighted loss from the forward's image
+      // the view's mean weight and gradient scale, rounded from FP64 as the loss kernel rounds
+      // them; one lane computes them (FP64 division is slow on this part)
+      float mean = 0.f, gscale = 0.f;
+      if (lane == 0) {
+        const double np = (double)c.W * (double)c.H;
+        mean = (float)(lf.wsum[view] / np);
+        gscale = (float)(2.0 / (3.0 * np));
+      }
+      mean = __shfl_sync(FULL, mean, 0);
+      gscale = __shfl_sync(FULL, gscale, 0);
+      float part = 0.f;
+      if (inside) {
+        const float wt = lf.w[p] / mean;
+        const float r0 = lf.rgb[3 * p] - lf.gt[3 * p], r1 = lf.rgb[3 * p + 1] - lf.gt[3 * p + 1],
+                    r2 = lf.rgb[3 * p + 2] - lf.gt[3 * p + 2];
+        part = wt * (r0 * r0 + r1 * r1 + r2 * r2);
+        const float cf = gscale * wt;
+        gr = cf * r0;
+        gg = cf * r1;
+        gb = cf * r2;
+        if (lf.dL) {
+          lf.dL[3 * p + 0] = gr;
+          lf.dL[3 * p + 1] = gg;
+          lf.dL[3 * p + 2] = gb;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      if (lane == 0) s_lf[warp][view] += (double)part;
     }
     const uint32_t my_hi = start + nc;  // entries [start, my_hi) were used by this pixel
     const uint32_t warp_hi = start + __reduce_max_sync(FULL, nc);
@@ -1528,6 +1519,14 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
         }
       }
       __syncwarp();
+    }
+  }
+  if (lf.w) {
+    __syncthreads();
+    for (int v = tid; v < vs.n; v += TS * TS) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s_lf[w][v];
+      if (t != 0.0) atomicAdd(&lf.lsum[v], t);
     }
   }
 }
@@ -1812,7 +1811,7 @@ static void sm_limits(int sm_limit, int dev, int* sms, int* sm_cut) {
 
 template <int TS, bool SEG, bool PERSIST, int CH>
 static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
-                         float t_stop, const lv_fwd_out* out, int sm_limit, const LfFuse& lf) {
+                         float t_stop, const lv_fwd_out* out, int sm_limit) {
   const size_t smem = fwd_slice(CH) * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
@@ -1830,13 +1829,13 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   k_fwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
                                                        out->n_samples, w.tau, out->wmax_packed, w.work, n_items,
-                                                       lf, sm_cut, sms);
+                                                       sm_cut, sms);
 }
 
 template <int TS, bool SEG, bool PERSIST, int CH>
 static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w, const uint32_t* sv,
                          const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT, float* dd,
-                         int sm_limit) {
+                         int sm_limit, const LfFuse& lf) {
   const size_t smem = bwd_slice(CH) * (TS * TS / 32);
   static int pblocks[64];  // per device
   static std::atomic<unsigned long long> done{0};
@@ -1856,7 +1855,7 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   }
   k_bwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
                                                        w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
-                                                       n_items, sm_cut, sms);
+                                                       n_items, sm_cut, sms, lf);
 }
 
 // tile size, batch, density model (midpoint, or the exact-segment variant) and scheduling
@@ -1901,14 +1900,14 @@ static void launch_tile_sort(const FwdWs& w, int64_t tiles, int64_t pair_cap, cu
 }
 
 static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
-                       const uint32_t* sv, const lv_fwd_out* out, const LfFuse& lf) {
+                       const uint32_t* sv, const lv_fwd_out* out) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
   const int sml = per ? o->persistent_sms : 0;
 #define LV_FWD_CH(TS, CH)                                                                           \
-  if (seg && per) launch_fwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml, lf);   \
-  else if (seg) launch_fwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0, lf);      \
-  else if (per) launch_fwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml, lf);    \
-  else launch_fwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0, lf)
+  if (seg && per) launch_fwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);   \
+  else if (seg) launch_fwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0);      \
+  else if (per) launch_fwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, o->t_stop, out, sml);    \
+  else launch_fwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, o->t_stop, out, 0)
 #define LV_FWD(TS)                                   \
   if (o->batch == 64) { LV_FWD_CH(TS, 64); }         \
   else if (o->batch == 128) { LV_FWD_CH(TS, 128); }  \
@@ -1923,14 +1922,14 @@ static void launch_fwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, c
 
 static void launch_bwd(const lv_raster_opts* o, int64_t tiles, cudaStream_t s, const ViewSet& vs, const FwdWs& w,
                        const uint32_t* sv, const lv_fwd_out* fwd, const float* gC, const float* gD, const float* gT,
-                       float* dd) {
+                       float* dd, const LfFuse& lf) {
   const bool seg = (o->flags & LV_FLAG_EXACT_SEGMENT) != 0, per = (o->flags & LV_FLAG_PERSISTENT) != 0;
   const int sml = per ? o->persistent_sms : 0;
-#define LV_BWD_CH(TS, CH)                                                                             \
-  if (seg && per) launch_bwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml);    \
-  else if (seg) launch_bwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0);       \
-  else if (per) launch_bwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml);     \
-  else launch_bwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0)
+#define LV_BWD_CH(TS, CH)                                                                                 \
+  if (seg && per) launch_bwd_t<TS, true, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml, lf);    \
+  else if (seg) launch_bwd_t<TS, true, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0, lf);       \
+  else if (per) launch_bwd_t<TS, false, true, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, sml, lf);     \
+  else launch_bwd_t<TS, false, false, CH>(tiles, s, vs, w, sv, fwd, gC, gD, gT, dd, 0, lf)
 #define LV_BWD(TS)                                   \
   if (o->batch == 64) { LV_BWD_CH(TS, 64); }         \
   else if (o->batch == 128) { LV_BWD_CH(TS, 128); }  \
@@ -1975,19 +1974,6 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
-  LfFuse lf = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (out->lf_workspace) {
-    if (!out->lf_gt || !out->lf_dL) { set_error("the fused LF loss needs lf_gt and lf_dL"); return LV_ERR_INVALID_ARG; }
-    int32_t wd[LV_MAX_VIEWS], ht[LV_MAX_VIEWS];
-    for (int v = 0; v < n_views; ++v) {
-      wd[v] = cams[v].width;
-      ht[v] = cams[v].height;
-    }
-    lv_status e = lf_fused_buffers(wd, ht, n_views, out->lf_workspace, out->lf_ws_bytes, &lf.w, &lf.wsum, &lf.lsum);
-    if (e != LV_OK) return e;
-    lf.gt = out->lf_gt;
-    lf.dL = out->lf_dL;
-  }
   const int64_t n = vox->n, items = n * n_views;
   // counters, the fallback status word, the work counters of the persistent kernels and the
   // sort by tile's digit counts, which k_emit accumulates (k_tile_sort_warp writes every tile's range)
@@ -2033,8 +2019,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
     else
       cudaEventRecord((cudaEvent_t)out->composite_event, s);
   }
-  if (out->lf_wait_event) cudaStreamWaitEvent(s, (cudaEvent_t)out->lf_wait_event, 0);  // the LF weights
-  launch_fwd(opts, tiles, s, vs, w, sv, out, lf);
+  launch_fwd(opts, tiles, s, vs, w, sv, out);
   count_launch(2);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_forward");
 }
@@ -2113,7 +2098,7 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
                                            int accumulate, int32_t* d_status, void* stream) {
   lv_status st = check_common(vox, cams, n_views, opts);
   if (st != LV_OK) return st;
-  if (!fwd || !fwd->T || !fwd->n_contrib || !dL_drgb || !d_density) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
+  if (!fwd || !fwd->T || !fwd->n_contrib || !d_density || (!dL_drgb && !fwd->lf_workspace)) { set_error("null argument"); return LV_ERR_INVALID_ARG; }
   if (!workspace || ((uintptr_t)workspace & 255)) { set_error("workspace must be non-null and 256-byte aligned"); return LV_ERR_INVALID_ARG; }
   if (pair_capacity < 0 || pair_capacity > 0xffffffffLL) { set_error("pair_capacity out of range"); return LV_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -2123,10 +2108,26 @@ extern "C" lv_status lv_rasterize_backward(const lv_voxels* vox, const lv_camera
   FwdWs w = carve_fwd(workspace, vox->n, n_views, tiles, pixels, pair_capacity);
   if (ws_bytes < w.bytes) { set_error("workspace %zu bytes < required %zu", ws_bytes, w.bytes); return LV_ERR_WORKSPACE; }
   if (!d_status) d_status = w.status;
+  // the LF-weighted loss fused in: dL/drgb from the forward's image, the ground truth and the weights
+  LfFuse lf = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (!dL_drgb) {
+    if (!fwd->lf_gt || !fwd->rgb) { set_error("the fused LF loss needs lf_gt and the forward's rgb"); return LV_ERR_INVALID_ARG; }
+    int32_t wd[LV_MAX_VIEWS], ht[LV_MAX_VIEWS];
+    for (int v = 0; v < n_views; ++v) {
+      wd[v] = cams[v].width;
+      ht[v] = cams[v].height;
+    }
+    lv_status e = lf_fused_buffers(wd, ht, n_views, fwd->lf_workspace, fwd->lf_ws_bytes, &lf.w, &lf.wsum, &lf.lsum);
+    if (e != LV_OK) return e;
+    lf.rgb = fwd->rgb;
+    lf.gt = fwd->lf_gt;
+    lf.dL = fwd->lf_dL;
+    if (fwd->lf_wait_event) cudaStreamWaitEvent(s, (cudaEvent_t)fwd->lf_wait_event, 0);  // the weights
+  }
   const int64_t n = vox->n;
   const uint32_t* sv = sorted_pair_slots(w, tiles);
   if (!accumulate && n > 0) cudaMemsetAsync(d_density, 0, sizeof(float) * 8 * n, s);
-  launch_bwd(opts, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density);
+  launch_bwd(opts, tiles, s, vs, w, sv, fwd, dL_drgb, dL_ddepth, dL_dT, d_density, lf);
   count_launch(1);
   if (d_sh) launch_sh_bwd(vox, vs, w, d_sh, accumulate, s);
   return finish(LV_OK, opts->flags, d_status, s, "lv_rasterize_backward");

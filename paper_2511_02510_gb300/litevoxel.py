@@ -251,9 +251,10 @@ def make_fwd_out(rgb, T, n_contrib, depth=None, wmax_packed=None, z_min=None, de
                  n_samples=None, stats_event=None, composite_event=None, lf=None) -> lv_fwd_out:
     """stats_event: a torch.cuda.Event (recorded once before, so that it exists) that the forward
     records as soon as the per-voxel statistics are final; composite_event: one it records right
-    before launching the composite.  lf: (gt, lf workspace, dL[, event]) to fuse the LF-weighted
-    loss into the composite (after lv_lf_weights on that workspace, or after the event it is
-    followed by on another stream; lv_lf_loss_finish writes the loss)."""
+    before launching the composite.  lf: (gt, lf workspace, dL or None[, event]) to fuse the
+    LF-weighted loss into the backward called with this struct and dL_drgb = None (after
+    lv_lf_weights on that workspace, or after the event that follows it on another stream;
+    lv_lf_loss_finish writes the loss after the backward)."""
     o = lv_fwd_out()
     o.rgb, o.depth, o.T, o.n_contrib = _ptr(rgb), _ptr(depth), _ptr(T), _ptr(n_contrib)
     o.wmax_packed, o.z_min, o.delta_min, o.seen = _ptr(wmax_packed), _ptr(z_min), _ptr(delta_min), _ptr(seen)

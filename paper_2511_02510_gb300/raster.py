@@ -80,26 +80,28 @@ class RasterContext:
                               self.n_samples if stats else None, stats_event, composite_event, lf)
 
     # ---------------------------------------------------------------- calls
-    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None, composite_event=None, lf=None):
+    def forward(self, vox: L.lv_voxels, stats=True, stats_event=None, composite_event=None):
         """Launch the forward pass (asynchronous).  Returns (rgb, depth, T).  stats_event (a
         torch.cuda.Event recorded once before) is recorded when the voxel statistics are final;
-        composite_event right before the composite is launched; lf = (gt, LF workspace, dL_drgb)
-        fuses the LF-weighted loss's gradient into the composite (lv_lf_weights first on that
-        workspace, lv_lf_loss_finish after for the loss)."""
+        composite_event right before the composite is launched."""
         L.lv_rasterize_forward(vox, self.cams_arr, self.n_views, self.opts,
-                               self.fwd_struct(stats, stats_event, composite_event, lf),
+                               self.fwd_struct(stats, stats_event, composite_event),
                                self.workspace, self.pair_capacity, self.status)
         self.generation += 1
         return self.rgb, self.depth, self.T
 
     def backward(self, vox: L.lv_voxels, dL_drgb, dL_ddepth=None, dL_dT=None, d_density=None, d_sh=None,
-                 accumulate=False):
+                 accumulate=False, lf=None):
+        """dL_drgb = None with lf = (gt, LF workspace, dL output or None[, event]): the backward
+        computes the LF-weighted loss's gradient itself (lv_lf_weights first on that workspace,
+        lv_lf_loss_finish after for the loss)."""
         if d_density is None:
             d_density = torch.empty((self.n, 8), dtype=torch.float32, device=self.device)
         if d_sh is None:
             d_sh = torch.empty((self.n, 48), dtype=torch.float32, device=self.device)
-        L.lv_rasterize_backward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(False), self.workspace,
-                                self.pair_capacity, dL_drgb.contiguous(),
+        L.lv_rasterize_backward(vox, self.cams_arr, self.n_views, self.opts, self.fwd_struct(False, lf=lf),
+                                self.workspace, self.pair_capacity,
+                                None if dL_drgb is None else dL_drgb.contiguous(),
                                 None if dL_ddepth is None else dL_ddepth.contiguous(),
                                 None if dL_dT is None else dL_dT.contiguous(), d_density, d_sh, accumulate,
                                 self.status)

@@ -1,9 +1,10 @@
-"""The LF-weighted loss fused into the forward composite (Sec. IV-B, Eq. 8 and
+"""The LF-weighted loss fused into the backward composite (Sec. IV-B, Eq. 8 and
 18) against the separate loss call on the same rendered image: dL/drgb bit for
-bit, the per-view loss within FP32 summation order (the fused forward sums per
-warp and block, the loss kernel per thread and block), for one-block-per-tile
-and persistent schedules and several views; the sums start from zero again
-after lv_lf_loss_finish; bad fused-loss arguments are refused on the host."""
+bit, the density and SH gradients up to the order of the FP32 atomic sums, the
+per-view loss within FP32 summation order (the fused backward sums per warp and
+block, the loss kernel per thread and block), for one-block-per-tile and
+persistent schedules and several views; the sums start from zero again after
+lv_lf_loss_finish; bad fused-loss arguments are refused on the host."""
 import numpy as np
 import pytest
 import torch
@@ -42,17 +43,19 @@ def test_fused_loss_matches_the_loss_call(tile, persistent):
     ctx.reset_stats()
     ctx.forward(vox)
     L.lv_lf_weighted_loss(ctx.rgb, gt, widths, heights, 450.0, p, loss_a, dl_a, ws_a)
-    rgb_a = ctx.rgb.clone()
+    dd_a, ds_a = ctx.backward(vox, dl_a)
+    dd_a, ds_a = dd_a.clone(), ds_a.clone()
     for rep in range(2):  # the second round checks that lv_lf_loss_finish cleared the sums
         loss_b = torch.zeros(2, device="cuda")
         dl_b = torch.full((P, 3), float("nan"), device="cuda")
         L.lv_lf_weights(gt, widths, heights, 450.0, p, ws_b)
-        ctx.reset_stats()
-        ctx.forward(vox, lf=(gt, ws_b, dl_b))
+        dd_b, ds_b = ctx.backward(vox, None, lf=(gt, ws_b, dl_b))
         L.lv_lf_loss_finish(widths, heights, loss_b, ws_b)
         ctx.check()
-        assert torch.equal(ctx.rgb, rgb_a)
         assert torch.equal(dl_b, dl_a)
+        for x, y in ((dd_a, dd_b), (ds_a, ds_b)):
+            scale = float(x.abs().max())
+            assert scale > 0 and float((x - y).abs().max()) <= 1e-5 * scale
         la, lb = loss_a.cpu().numpy().astype(np.float64), loss_b.cpu().numpy().astype(np.float64)
         assert np.all(la > 0) and np.all(np.abs(la - lb) <= 2e-6 * la)
         if rep == 0:  # the loss again from the same sums: finish cleared them
@@ -66,10 +69,13 @@ def test_fused_loss_argument_checks():
     scene, ctx, vox = gpu_forward(sc, cams)
     gt = torch.zeros(64 * 48, 3, device="cuda")
     ws = torch.empty(L.lv_lf_workspace_size([64], [48]), dtype=torch.uint8, device="cuda")
-    with pytest.raises(L.LvError) as ei:  # lf_dL missing
-        ctx.forward(vox, lf=(gt, ws, None))
+    with pytest.raises(L.LvError) as ei:  # neither dL_drgb nor the fused loss
+        ctx.backward(vox, None)
+    assert ei.value.status == L.LV_ERR_INVALID_ARG
+    with pytest.raises(L.LvError) as ei:  # lf_gt missing
+        ctx.backward(vox, None, lf=(None, ws, None))
     assert ei.value.status == L.LV_ERR_INVALID_ARG
     small = torch.empty(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(L.LvError) as ei:  # workspace too small for the views
-        ctx.forward(vox, lf=(gt, small, torch.zeros_like(gt)))
+        ctx.backward(vox, None, lf=(gt, small, None))
     assert ei.value.status == L.LV_ERR_WORKSPACE

@@ -1,6 +1,7 @@
-"""The benchmark step on three streams (LF weights beside the forward, the LF
-loss's gradient fused into the forward composite, pruning and the subdivision
-selection beside the backward, the in-place topology change after both)
+"""The benchmark step on four streams (LF weights beside the forward, the LF
+loss's gradient fused into the backward composite, pruning and the subdivision
+selection beside the backward, the in-place topology change after both with
+the SH backward beside it)
 computes what the one-stream step computes: the same bits for every output
 that has a fixed summation order (dL/drgb, the rewritten voxel rows and
 auxiliary arrays included), the same loss up to the order of its sums, and the
