@@ -42,6 +42,10 @@ struct DevView {
   int W, H, tiles_x, tiles_y;
   int tile_off;       // first global tile of the view
   long long pix_off;  // first global pixel of the view
+  // k_bin's early-out planes: the frustum of the tile grid widened by 2 pixels has side planes
+  // f u - m z = 0 (u the camera x or y coordinate) with m = cx + 2, cx - tiles_x ts - 2,
+  // cy + 2, cy - tiles_y ts - 2 (cull_m), and |(f, m)| rounded up (cull_n)
+  float cull_m[4], cull_n[4];
 };
 struct ViewSet {
   int n;
@@ -73,6 +77,14 @@ static void make_views(const lv_camera* cams, int nv, int ts, ViewSet* vs, int64
     d.tiles_y = (c.height + ts - 1) / ts;
     d.tile_off = (int)to;
     d.pix_off = po;
+    d.cull_m[0] = d.cx + 2.f;
+    d.cull_m[1] = d.cx - (float)(d.tiles_x * ts) - 2.f;
+    d.cull_m[2] = d.cy + 2.f;
+    d.cull_m[3] = d.cy - (float)(d.tiles_y * ts) - 2.f;
+    for (int k = 0; k < 4; ++k) {
+      const double f = k < 2 ? (double)d.fx : (double)d.fy, m = (double)d.cull_m[k];
+      d.cull_n[k] = nextafterf((float)sqrt(f * f + m * m), INFINITY);  // at least the exact norm
+    }
     to += (int64_t)d.tiles_x * d.tiles_y;
     po += (int64_t)c.width * c.height;
   }
@@ -94,10 +106,11 @@ struct FwdWs {
   uint2* rec_bb;                 // [slots] pixel box of the render record
   uint32_t* slot_vox;            // [slots] voxel id of the render record
   uint32_t* s_dkey;              // [slots] order key
-  unsigned int* work;            // [8] work-item counters: [0..1] the persistent composites, [2] count
+  unsigned int* work;            // [16] work-item counters: [0..1] the persistent composites, [2] count
                                  // of the long tiles' chunks, [3] the merge's work counter, [4..5] count
                                  // of the medium tiles and k_tile_sort's work counter, [6] count of the
-                                 // long tiles
+                                 // long tiles; [8..9] block arrivals of the persistent forward and
+                                 // backward composites (sm_leave)
   uint2* chunks;                 // [pair capacity / TS_CHUNK + tiles] (tile, chunk) of the long tiles
   uint32_t* mid_tiles;           // [tiles] tiles of medium-length lists
   uint32_t* long_tiles;          // [tiles] tiles of long lists
@@ -118,7 +131,7 @@ static FwdWs carve_fwd(void* base, int64_t n, int nv, int64_t tiles, int64_t pix
   int64_t items = n * nv;
   w.counters = c.take<unsigned long long>(8);
   w.status = c.take<int32_t>(4);
-  w.work = c.take<unsigned int>(8);
+  w.work = c.take<unsigned int>(16);
   w.cnt = c.take<uint32_t>(items);
   w.vis = c.take<uint32_t>(items);
   w.rect = c.take<uint2>(items);
@@ -198,13 +211,12 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ geom, in
     // changes no output.
     const float r = g.w * 1.7320508f;
     const float rs = r + 1e-4f * (fabsf(qc[0]) + fabsf(qc[1]) + fabsf(qc[2]) + r) + 1e-6f;
-    const float mL = c.cx + 2.f, mR = c.cx - (float)(c.tiles_x * ts) - 2.f;
-    const float mT = c.cy + 2.f, mB = c.cy - (float)(c.tiles_y * ts) - 2.f;
+    // (the planes and their norms are per view, set up on the host)
     const bool out = qc[2] + rs < c.z_near ||
-                     c.fx * qc[0] + mL * qc[2] < -rs * sqrtf(c.fx * c.fx + mL * mL) ||
-                     c.fx * qc[0] + mR * qc[2] > rs * sqrtf(c.fx * c.fx + mR * mR) ||
-                     c.fy * qc[1] + mT * qc[2] < -rs * sqrtf(c.fy * c.fy + mT * mT) ||
-                     c.fy * qc[1] + mB * qc[2] > rs * sqrtf(c.fy * c.fy + mB * mB);
+                     c.fx * qc[0] + c.cull_m[0] * qc[2] < -rs * c.cull_n[0] ||
+                     c.fx * qc[0] + c.cull_m[1] * qc[2] > rs * c.cull_n[1] ||
+                     c.fy * qc[1] + c.cull_m[2] * qc[2] < -rs * c.cull_n[2] ||
+                     c.fy * qc[1] + c.cull_m[3] * qc[2] > rs * c.cull_n[3];
     if (out) {
       cnt[i] = 0u;
       vis[i] = 0u;
@@ -1172,6 +1184,26 @@ __device__ __forceinline__ bool sm_excluded(int sm_cut, int n_sms) {
   return (unsigned long long)smid * (unsigned)n_sms >= (unsigned long long)sm_cut * nsmid;
 }
 
+// Whether this block of a grid cut to sm_cut SMs leaves at once.  Some block must
+// stay, or the work counter's items would be taken by nobody (every block could
+// land on an excluded SM while streams of higher priority hold the kept ones), so
+// each block counts its arrival in *arrivals (zero before the launch; a block on
+// a kept SM adds 1 << 16 as well), and the grid's last block to arrive stays,
+// wherever it runs, when no block before it stayed.  Called by every thread of
+// the block (block barrier); grids of up to 65535 blocks.
+__device__ __forceinline__ bool sm_leave(int sm_cut, int n_sms, unsigned int* arrivals) {
+  if (sm_cut <= 0) return false;  // grid-uniform
+  __shared__ int s_leave;
+  if (threadIdx.x == 0) {
+    const bool excl = sm_excluded(sm_cut, n_sms);
+    const unsigned int old = atomicAdd(arrivals, excl ? 1u : 0x10001u);
+    const bool last_alone = (old & 0xffffu) == gridDim.x - 1 && (old >> 16) == 0;
+    s_leave = excl && !last_alone;
+  }
+  __syncthreads();
+  return s_leave != 0;
+}
+
 // ------------------------------------------------------------------ forward composite
 // Each warp walks its strip's tile list on its own: CH list entries at a time
 // (the batch: 32, 64 or 128, CH / 32 per lane, all loads of a batch issued
@@ -1248,10 +1280,10 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                                 float* __restrict__ T_out, uint32_t* __restrict__ n_contrib,
                                                 uint32_t* __restrict__ n_samples, float* __restrict__ tau_out,
                                                 unsigned long long* __restrict__ wmax, unsigned int* work,
-                                                uint32_t n_items, int sm_cut, int n_sms) {
+                                                uint32_t n_items, int sm_cut, int n_sms, unsigned int* arrivals) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
-  if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
+  if (PERSIST && sm_leave(sm_cut, n_sms, arrivals)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* wr = (float4*)((char*)smem_f4 + fwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
@@ -1377,11 +1409,11 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
                                                 const float* __restrict__ dL_drgb, const float* __restrict__ dL_ddepth,
                                                 const float* __restrict__ dL_dT, float* __restrict__ d_density,
                                                 float4* __restrict__ d_rgb, unsigned int* work, uint32_t n_items,
-                                                int sm_cut, int n_sms, const LfFuse lf) {
+                                                int sm_cut, int n_sms, unsigned int* arrivals, const LfFuse lf) {
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   __shared__ double s_lf[NW][LV_MAX_VIEWS];  // each warp's loss sums (fused LF loss; no atomics)
-  if (PERSIST && sm_excluded(sm_cut, n_sms)) return;  // block-uniform
+  if (PERSIST && sm_leave(sm_cut, n_sms, arrivals)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (lf.w)  // grid-uniform; a warp clears and then adds to its own row only
     for (int v = lane; v < vs.n; v += 32) s_lf[warp][v] = 0.0;
@@ -1829,7 +1861,7 @@ static void launch_fwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   k_fwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, t_stop,
                                                        out->rgb, out->depth, out->T, out->n_contrib,
                                                        out->n_samples, w.tau, out->wmax_packed, w.work, n_items,
-                                                       sm_cut, sms);
+                                                       sm_cut, sms, w.work + 8);
 }
 
 template <int TS, bool SEG, bool PERSIST, int CH>
@@ -1850,12 +1882,12 @@ static void launch_bwd_t(int64_t tiles, cudaStream_t s, const ViewSet& vs, const
   const uint32_t n_items = (uint32_t)tiles * (TS * TS / 32);
   unsigned grid = (unsigned)tiles;
   if (PERSIST) {
-    zero_async(s, w.work + 1, sizeof(unsigned int));
+    zero_async(s, w.work + 1, sizeof(unsigned int), w.work + 9, sizeof(unsigned int));
     grid = (unsigned)(tiles < pb ? tiles : pb);
   }
   k_bwd<TS, SEG, PERSIST, CH><<<grid, TS * TS, smem, s>>>(vs, w.ranges, sv, w.rec, w.rec_bb, w.slot_vox, fwd->T,
                                                        w.tau, fwd->n_contrib, gC, gD, gT, dd, w.d_rgb, w.work + 1,
-                                                       n_items, sm_cut, sms, lf);
+                                                       n_items, sm_cut, sms, w.work + 9, lf);
 }
 
 // tile size, batch, density model (midpoint, or the exact-segment variant) and scheduling
@@ -1980,7 +2012,7 @@ extern "C" lv_status lv_rasterize_forward(const lv_voxels* vox, const lv_camera*
   const SortCountTargets sc = sort_count_targets(w.sort_tmp, pair_capacity);
   const int passes = std::min(sort_passes(tile_bits(tiles)), 4);
   zero_async(s, w.counters, 8 * sizeof(unsigned long long), d_status == w.status ? w.status : nullptr,
-             sizeof(int32_t), w.work, 8 * sizeof(unsigned int), sc.counts, sc.zero_bytes);
+             sizeof(int32_t), w.work, 16 * sizeof(unsigned int), sc.counts, sc.zero_bytes);
   if (items > 0) {
     int blocks = (int)((items + 255) / 256);
     const unsigned emit_blocks = (unsigned)(((n + 255) / 256) * n_views);  // (voxel range, view) blocks
