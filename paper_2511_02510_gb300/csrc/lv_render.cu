@@ -1310,6 +1310,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
                                         nullptr);
       if (!m) continue;
       __syncwarp();
+      int last_j = -1;  // the lane's last sample of this batch (its list entry is read once, below)
       for (int j = 0; j < m; ++j) {
         if (CH > 32 && (j & 31) == 31 && __all_sync(FULL, done)) break;  // warp-uniform
         const float4 g = wr[4 * j];
@@ -1331,7 +1332,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
           dep = fmaf(w, tm, dep);
           tau += x;
           T *= ex;
-          last = w_ent[j] - start + 1;
+          last_j = j;
           ++nsamp;
         }
         if (__any_sync(FULL, hit)) {
@@ -1344,6 +1345,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_fwd(const __grid_c
           if (hit && T < t_stop) done = true;
         }
       }
+      if (last_j >= 0) last = w_ent[last_j] - start + 1;
       __syncwarp();
     }
     if (inside) {
