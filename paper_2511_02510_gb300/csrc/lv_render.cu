@@ -1415,10 +1415,20 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
   constexpr int NW = TS * TS / 32;
   extern __shared__ float4 smem_f4[];
   __shared__ double s_lf[NW][LV_MAX_VIEWS];  // each warp's loss sums (fused LF loss; no atomics)
+  __shared__ float s_mean[LV_MAX_VIEWS], s_gscale[LV_MAX_VIEWS];  // the fused LF loss's per-view constants
   if (PERSIST && sm_leave(sm_cut, n_sms, arrivals)) return;  // block-uniform
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (lf.w)  // grid-uniform; a warp clears and then adds to its own row only
+  if (lf.w) {  // grid-uniform; a warp clears and then adds to its own row only
     for (int v = lane; v < vs.n; v += 32) s_lf[warp][v] = 0.0;
+    // each view's mean weight and gradient scale, rounded from FP64 as the loss kernel rounds them,
+    // once per block (FP64 division is slow on this part)
+    for (int v = tid; v < vs.n; v += TS * TS) {
+      const double np = (double)vs.v[v].W * (double)vs.v[v].H;
+      s_mean[v] = (float)(lf.wsum[v] / np);
+      s_gscale[v] = (float)(2.0 / (3.0 * np));
+    }
+    __syncthreads();
+  }
   float4* wr = (float4*)((char*)smem_f4 + bwd_slice(CH) * warp);
   uint32_t* w_vox = (uint32_t*)(wr + 4 * CH);
   uint32_t* w_slot = w_vox + CH;
@@ -1451,16 +1461,7 @@ __global__ void __launch_bounds__(TS* TS, min_blocks<TS>()) k_bwd(const __grid_c
       if (dL_dT) gT = dL_dT[p];
     }
     if (lf.w) {  // grid-uniform: dL/drgb of the LF-weighted loss from the forward's image
-      // the view's mean weight and gradient scale, rounded from FP64 as the loss kernel rounds
-      // them; one lane computes them (FP64 division is slow on this part)
-      float mean = 0.f, gscale = 0.f;
-      if (lane == 0) {
-        const double np = (double)c.W * (double)c.H;
-        mean = (float)(lf.wsum[view] / np);
-        gscale = (float)(2.0 / (3.0 * np));
-      }
-      mean = __shfl_sync(FULL, mean, 0);
-      gscale = __shfl_sync(FULL, gscale, 0);
+      const float mean = s_mean[view], gscale = s_gscale[view];
       float part = 0.f;
       if (inside) {
         const float wt = lf.w[p] / mean;
