@@ -119,14 +119,25 @@ __global__ void k_lf_weight(const uint32_t* __restrict__ mkey, const SelectQuery
   block_add_f64((double)acc, &wsum[v]);
 }
 
+// the view's mean weight <w> and gradient scale 2 / (3 |P|), rounded to FP32 from FP64, once per
+// block (thread 0; FP64 division is slow on this part) into *mean and *gscale (shared memory)
+__device__ __forceinline__ void lf_view_constants(const double* wsum, int v, long long np, float* mean, float* gscale) {
+  if (threadIdx.x == 0) {
+    *mean = (float)(wsum[v] / (double)np);
+    *gscale = (float)(2.0 / (3.0 * (double)np));
+  }
+  __syncthreads();
+}
+
 // Eq. 8 + Eq. 18: w~ = w / <w>, L = 1/|P| sum w~ mean_c r^2, dL/drgb = 2/(3|P|) w~ r
 __global__ void k_lf_loss(const float* __restrict__ rgb, const float* __restrict__ gt, const float* __restrict__ w,
                           const __grid_constant__ ViewPix vp, int v, const double* wsum, double* lsum,
                           float* __restrict__ grad) {
   const long long lo = vp.off[v], hi = vp.off[v + 1];
   const long long np = hi - lo;
-  const float mean = (float)(wsum[v] / (double)np);
-  const float gscale = (float)(2.0 / (3.0 * (double)np));
+  __shared__ float s_mean, s_gscale;
+  lf_view_constants(wsum, v, np, &s_mean, &s_gscale);
+  const float mean = s_mean, gscale = s_gscale;
   float acc = 0.f;  // sum of w~ (r0^2 + r1^2 + r2^2) over this thread's pixels; the 1/3 is applied at the end
   for (long long p = lo + blockIdx.x * (long long)TPB + threadIdx.x; p < hi; p += (long long)gridDim.x * TPB) {
     const float wt = w[p] / mean;
@@ -153,8 +164,9 @@ __global__ void k_lf_loss4(const float* __restrict__ rgb, const float* __restric
                            float* __restrict__ grad) {
   const long long lo = vp.off[v], hi = vp.off[v + 1];
   const long long np = hi - lo;
-  const float mean = (float)(wsum[v] / (double)np);
-  const float gscale = (float)(2.0 / (3.0 * (double)np));
+  __shared__ float s_mean, s_gscale;
+  lf_view_constants(wsum, v, np, &s_mean, &s_gscale);
+  const float mean = s_mean, gscale = s_gscale;
   const long long g0 = (lo + 3) >> 2, g1 = hi >> 2;  // whole groups [4 g0, 4 g1)
   float acc = 0.f;
   auto one = [&](long long p) {
