@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py, without a GPU: the clock record summarised
 into the JSON line, the DRAM-traffic guard that drops a capture once the
-kernel's source changes, and the algorithmic byte counts of the roofline."""
+kernel's source changes, the algorithmic byte counts of the roofline, and the
+batches whose step is timed after the autotuner."""
 import hashlib
 import json
 import os
@@ -72,3 +73,20 @@ def test_stage_work_and_step_roofline():
 def test_alu_peak():
     # 152 SMs x 128 FP32 lanes x 2 (FMA) at 2070 MHz
     assert bench.alu_peak_tflops(2070.0) == pytest.approx(80.54, abs=0.01)
+
+
+def test_step_batch_candidates_follow_the_tuner_layout():
+    # lv_autotune's ms_out: index 6 t + 3 p + b, tiles (8, 16, 32), schedules (block, persistent),
+    # batches (32, 64, 128); -1 for a skipped candidate
+    ms = [-1.0] * 18
+    ms[6 * 2 + 3 + 0] = 0.5838   # tile 32, persistent, batch 32
+    ms[6 * 2 + 3 + 1] = 0.5776   # tile 32, persistent, batch 64 (the tuner's pick)
+    ms[6 * 2 + 0 + 0] = 0.40     # other schedules never enter
+    assert bench.step_batch_candidates(32, True, 64, ms) == [64, 32]
+    ms[6 * 2 + 3 + 0] = 0.60     # 3.9 % slower: left out
+    assert bench.step_batch_candidates(32, True, 64, ms) == [64]
+    ms = [-1.0] * 18
+    ms[6 * 1 + 0 + 0], ms[6 * 1 + 0 + 1], ms[6 * 1 + 0 + 2] = 0.71, 0.70, 0.72   # tile 16, block per tile
+    assert bench.step_batch_candidates(16, False, 64, ms) == [64, 32, 128]
+    assert bench.step_batch_candidates(16, False, 64, None) == [64]
+    assert bench.step_batch_candidates(16, False, 64, [-1.0] * 18) == [64]
