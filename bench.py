@@ -155,10 +155,10 @@ class Workload:
         elif tuned:
             self.tile, self.persistent, self.batch, self.tune_ms = tuned_schedule(self.scene, self.cams)
         # the persistent backward composite leaves 80 SMs to the pruning and selection kernels
-        # that the three-stream step runs beside it: that chain, not the backward, ends last
-        # before the topology change (graph-replay marks: 0.960 ms per step with the backward on
-        # 104 SMs, 0.951 on 88, 0.943 on 72, 0.959 on 56, 0.992 on all 152); the forward
-        # composite runs alone and keeps every SM
+        # that the four-stream step runs beside it; with more SMs for the backward the chain ends
+        # last, with fewer the backward (graph-replayed step, batch 32: 0.828-0.832 ms with the
+        # backward on 72 SMs, 0.832 on 68, 0.833 on 76, 0.839 on 64, 0.843 on 80, 0.847 on 88);
+        # the forward composite runs alone and keeps every SM
         self.persistent_sms = 0
         if self.persistent:
             self.persistent_sms = max(1, torch.cuda.get_device_properties(0).multi_processor_count - 80)
