@@ -16,7 +16,7 @@ from paper_2511_02510_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_three_stream_step_matches_one_stream():
+def test_four_stream_step_matches_one_stream():
     wl = bench.Workload(synth.scene_tiny(), bench.camera_for(0), synth.random_image(bench.W_IMG, bench.H_IMG, seed=3))
     state = wl.cap_arrays + wl.aux_arrays          # EMA and hysteresis state are the last two aux arrays
     start = [t.clone() for t in state]
